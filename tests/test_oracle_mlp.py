@@ -1,0 +1,103 @@
+"""Pins of the oracle's predictor MLP: finite differences, an independent NumPy forward
+pass, the uniform-logit loss and the closed form of Adam's first step."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+DIMS = (15, 8, 6, 5)
+
+
+def params(seed, dims=DIMS, scale=0.5):
+    return np.random.default_rng(seed).normal(0, scale, oracle.mlp_nparams(*dims))
+
+
+def unpack(P, dims):
+    d, h1, h2, k = dims
+    o = 0
+    out = []
+    for shape in [(h1, d), (h1,), (h2, h1), (h2,), (k, h2), (k,)]:
+        size = int(np.prod(shape))
+        out.append(P[o:o + size].reshape(shape))
+        o += size
+    return out
+
+
+def test_forward_matches_numpy_matrix_form():
+    P = params(1)
+    X = np.random.default_rng(2).normal(size=(9, 15))
+    W1, b1, W2, b2, W3, b3 = unpack(P, DIMS)
+    ref = np.maximum(np.maximum(X @ W1.T + b1, 0) @ W2.T + b2, 0) @ W3.T + b3
+    assert np.allclose(oracle.mlp_forward(P, X, DIMS), ref, rtol=1e-13, atol=1e-13)
+
+
+def test_loss_uniform_logits_is_log_k():
+    P = np.zeros(oracle.mlp_nparams(*DIMS))
+    X = np.random.default_rng(0).normal(size=(4, 15))
+    loss, g = oracle.mlp_loss_grad(P, X, [0, 1, 2, 3], DIMS)
+    assert loss == pytest.approx(math.log(5), rel=1e-15)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_gradient_central_differences(seed):
+    P = params(seed)
+    rng = np.random.default_rng(seed + 10)
+    X = rng.normal(size=(6, 15))
+    lab = rng.integers(0, 5, 6)
+    _, g = oracle.mlp_loss_grad(P, X, lab, DIMS)
+    h = 1e-6
+    num = np.empty_like(P)
+    for i in range(len(P)):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        num[i] = (oracle.mlp_loss_grad(Pp, X, lab, DIMS)[0]
+                  - oracle.mlp_loss_grad(Pm, X, lab, DIMS)[0]) / (2 * h)
+    # ReLU kinks are measure-zero for random inputs; central differences are O(h^2)
+    assert np.allclose(g, num, rtol=1e-5, atol=1e-8)
+
+
+def test_adam_first_step_closed_form():
+    """With m = v = 0 and t = 1 the bias corrections give P -= lr * g / (|g| + eps)."""
+    rng = np.random.default_rng(3)
+    P = rng.normal(size=50)
+    G = rng.normal(size=50)
+    m = np.zeros(50)
+    v = np.zeros(50)
+    P0 = P.copy()
+    oracle.adam_step(P, G, m, v, 1, lr=0.01, eps=1e-8)
+    assert np.allclose(P, P0 - 0.01 * G / (np.abs(G) + 1e-8), rtol=1e-12, atol=1e-15)
+    assert np.allclose(m, 0.1 * G) and np.allclose(v, 0.001 * G * G)
+
+
+def test_training_decreases_loss():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(64, 15))
+    lab = (X[:, 0] > 0).astype(int) + 2 * (X[:, 1] > 0).astype(int)
+    P = params(5, scale=0.3)
+    m = np.zeros_like(P)
+    v = np.zeros_like(P)
+    l0 = oracle.mlp_loss_grad(P, X, lab, DIMS)[0]
+    for t in range(1, 301):
+        loss, g = oracle.mlp_loss_grad(P, X, lab, DIMS)
+        oracle.adam_step(P, g, m, v, t, lr=0.01)
+    assert loss < 0.3 * l0
+
+
+def test_cascade_control_flow():
+    # CSR -> algorithm stage -> vector -> TpV stage
+    assert oracle.cascade([5, 0, 0, 0, 0], [0, 9, 0], [0, 0, 7, 0, 0]) == (0, 1, 2)
+    # CSR scalar: no TpV stage
+    assert oracle.cascade([5, 0, 0, 0, 0], [9, 0, 0], [0, 0, 7, 0, 0]) == (0, 0, -1)
+    # SELL: sigma stage
+    assert oracle.cascade([0, 0, 0, 5, 0], [9, 0, 0], None, [0, 3, 0, 0]) == (3, -1, 1)
+    # ELL: nothing further
+    assert oracle.cascade([0, 0, 5, 0, 0], [9, 0, 0], [1, 0, 0, 0, 0], [1, 0, 0, 0]) == (2, -1, -1)
+
+
+def test_mlp_input_transform():
+    f = np.arange(15, dtype=float)
+    z = oracle.mlp_input(f, np.zeros(15), np.ones(15))
+    assert np.allclose(z, np.log1p(f))
