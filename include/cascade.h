@@ -1,0 +1,281 @@
+/*
+ * cascade.h -- C ABI of libcascade: SpMV-based Krylov solvers with cascaded
+ * SpMV-configuration prediction and asynchronous execution, for NVIDIA B300
+ * (sm_103a).  Method: Gao et al., "Cascaded Prediction and Asynchronous
+ * Execution of Iterative Algorithms on Heterogeneous Platforms" (arXiv
+ * 2411.10143).
+ *
+ * Conventions for every entry point
+ *  - Every function returns a cp_status and never aborts the process.  On an
+ *    error, cp_last_error() returns a message for the calling thread.
+ *  - Pointers documented as "device" must point to memory of the context's
+ *    device (cudaMalloc, torch CUDA tensors); "host" pointers are ordinary
+ *    (optionally pinned) host memory.  No entry point keeps a caller pointer
+ *    after it returns unless stated.
+ *  - Index arrays are int32 (nnz <= 2^31 - 1 is checked); values are IEEE
+ *    binary64 unless a dtype argument says binary32.
+ *  - Work is issued on the context's main stream (and, for prediction, its
+ *    side stream).  Entry points that return results to the host synchronise
+ *    the streams they used before returning; cp_spmv does not (it is ordered on
+ *    the main stream like a library kernel call).
+ *  - A cp_ctx and the cp_mat objects created from it may be used by one host
+ *    thread at a time.
+ */
+#ifndef CASCADE_H
+#define CASCADE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cp_ctx cp_ctx;
+typedef struct cp_mat cp_mat;
+
+typedef enum {
+  CP_OK = 0,
+  CP_ERR_INVALID = 1,        /* bad argument or malformed CSR                      */
+  CP_ERR_OOM = 2,            /* device allocation failed                           */
+  CP_ERR_FOOTPRINT = 3,      /* a padded format would exceed its memory budget     */
+  CP_ERR_NOT_CONVERGED = 4,  /* maxit reached; x holds the last iterate            */
+  CP_ERR_BREAKDOWN = 5,      /* (Ap,p) <= 0 in CG, or a NaN/Inf appeared           */
+  CP_ERR_TIMEOUT = 6,        /* a bounded wait gave up                             */
+  CP_ERR_CUDA = 7,           /* a CUDA runtime call failed                         */
+  CP_ERR_CANCELLED = 8,      /* work cancelled before it finished                  */
+  CP_ERR_UNSUPPORTED = 9     /* configuration outside the supported space          */
+} cp_status;
+
+/* ------------------------------------------------------------------ configs */
+/* SpMV configuration space (Sec. III-B-2, Fig. 2): compression format, then the
+ * SpMV algorithm for that format, then the kernel parameter.  The paper's space
+ * is COO/CSR/ELL/DIA/HYB across three libraries with the CSR-Vector threads per
+ * vector (TpV) in {2,4,8,16,32}; this library's space is the formats below, the
+ * CSR algorithms scalar / vector / merge-path, TpV for CSR-vector and the sort
+ * window sigma for SELL-C-sigma (slicing, Sec. V-A). */
+enum {
+  CP_FMT_CSR = 0,
+  CP_FMT_COO = 1,
+  CP_FMT_ELL = 2,
+  CP_FMT_SELL = 3,
+  CP_FMT_HYB = 4,
+  CP_NUM_FMT = 5
+};
+enum { CP_ALGO_SCALAR = 0, CP_ALGO_VECTOR = 1, CP_ALGO_MERGE = 2, CP_NUM_ALGO = 3 };
+
+typedef struct {
+  int32_t fmt;        /* CP_FMT_*                                                     */
+  int32_t algo;       /* CSR only: CP_ALGO_*                                          */
+  int32_t tpv;        /* CSR-vector threads per row: 2, 4, 8, 16 or 32                */
+  int32_t sell_c;     /* SELL chunk height; only 32 is supported (one warp per chunk) */
+  int32_t sell_sigma; /* SELL sort window: 1 (no sort) or a multiple of 32, <= 8192   */
+  int32_t hyb_k;      /* HYB ELL width; 0 = ceil(mean row length)                     */
+} cp_config;
+
+/* The default configuration every solve starts from: CSR, scalar kernel (one
+ * thread per row).  (The paper's default is CUSP-COO, Sec. III-C-2.) */
+void cp_config_default(cp_config* cfg);
+
+/* ------------------------------------------------------------------ context */
+/* cp_create: a context on CUDA device `device`.  main_stream / side_stream are
+ * cudaStream_t handles owned by the caller (e.g. torch streams) or NULL, in
+ * which case the context creates (and later destroys) non-blocking streams of
+ * its own.  The side stream runs feature extraction, prediction and format
+ * conversion concurrently with the solve (Sec. III-C-2).
+ * Errors: CP_ERR_INVALID (bad device), CP_ERR_CUDA, CP_ERR_OOM. */
+cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_stream);
+cp_status cp_destroy(cp_ctx* ctx);
+
+/* Message describing the last error of the calling thread ("" if none). */
+const char* cp_last_error(void);
+
+/* Number of kernels this context has launched since creation (all streams). */
+cp_status cp_ctx_launch_count(cp_ctx* ctx, int64_t* count);
+
+/* ------------------------------------------------------------------ matrices */
+/* cp_csr_load: copies a CSR matrix into library-owned device memory and
+ * validates it on the device (rowptr[0] = 0, rowptr non-decreasing,
+ * rowptr[nrows] = nnz, 0 <= col < ncols, columns strictly increasing within
+ * each row).  rowptr[nrows+1], col[nnz], val[nnz] are host pointers when
+ * on_device = 0 and device pointers when on_device = 1; the caller keeps
+ * ownership of them.  The returned handle owns the copy and every format later
+ * converted from it.  nrows, ncols >= 1; nnz >= 0.
+ * Errors: CP_ERR_INVALID (malformed matrix, sizes out of range), CP_ERR_OOM. */
+cp_status cp_csr_load(cp_ctx* ctx, int64_t nrows, int64_t ncols, int64_t nnz,
+                      const int32_t* rowptr, const int32_t* col, const double* val,
+                      int32_t on_device, cp_mat** out);
+cp_status cp_mat_free(cp_mat* mat);
+
+/* Budget, in bytes, for one padded format (ELL, SELL, HYB's ELL part) of one
+ * matrix; conversions above it fail with CP_ERR_FOOTPRINT.  Default: 4 GiB. */
+cp_status cp_set_format_budget(cp_ctx* ctx, int64_t bytes);
+
+/* ------------------------------------------------------------------ features */
+/* cp_features: the 15 features of Table IV (Sec. III-B-1) computed on the GPU,
+ * written to host array out[15] in table order: nrows, ncols, nnz, density,
+ * mean, sd, cov, max, min, maxavg, distavg, clusteravg, fill, ndiag, diagfill.
+ * Counts and sums are exact (int64); sd is the population standard deviation
+ * from exact sums; cov = sd/mean; distavg = mean over rows of (last column -
+ * first column), empty rows adding 0; clusteravg = mean over rows of the
+ * longest run of consecutive columns; fill = nrows*max/nnz; ndiag = number of
+ * distinct (col - row) offsets; diagfill = nrows*ndiag/nnz. */
+cp_status cp_features(cp_ctx* ctx, cp_mat* mat, double* out15);
+
+/* ------------------------------------------------------------------ formats */
+/* cp_convert: materialise the format of `cfg` (CSR -> COO, ELL, SELL-C-sigma or
+ * HYB) on the main stream and wait for it; the result is cached in `mat`.
+ * Conversions copy indices and values bit for bit (Sec. III-C-1: a format
+ * change needs storage and a conversion kernel).
+ * Errors: CP_ERR_FOOTPRINT, CP_ERR_UNSUPPORTED, CP_ERR_OOM. */
+cp_status cp_convert(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg);
+
+/* Arrays of a converted format, for inspection.  Layouts:
+ *  COO : ROW[nnz] (COL and VAL are the CSR arrays), row-major order.
+ *  ELL : ELL_COL / ELL_VAL [K*ld], entry k of row i at k*ld + i, ld = nrows
+ *        rounded up to 32, padding col = -1, val = 0.0.  dims = {K, ld}.
+ *  SELL: PERM[nrows] (original row at sorted position s), CHUNK_LEN[nchunks],
+ *        CHUNK_PTR[nchunks+1] (int64), SELL_COL / SELL_VAL[slots]; rows sorted
+ *        longest-first (stable) inside windows of sigma rows; entry k of slot r
+ *        of chunk c at CHUNK_PTR[c] + k*C + r; padding col = -1, val = 0.0.
+ *        dims = {nchunks, slots, C, sigma}.
+ *  HYB : HYB_ELL_COL / HYB_ELL_VAL [K*ld] (first K entries per row, ELL layout)
+ *        and HYB_COO_ROW / HYB_COO_COL / HYB_COO_VAL [ncoo] (the remaining
+ *        entries, row-major).  dims = {K, ld, ncoo}.
+ * cp_format_dims writes up to 4 int64 dims.  cp_format_export copies one array
+ * to host memory dst (capacity bytes); *bytes receives its size. */
+enum {
+  CP_ARR_COO_ROW = 0,
+  CP_ARR_ELL_COL = 1, CP_ARR_ELL_VAL = 2,
+  CP_ARR_SELL_PERM = 3, CP_ARR_SELL_CHUNK_LEN = 4, CP_ARR_SELL_CHUNK_PTR = 5,
+  CP_ARR_SELL_COL = 6, CP_ARR_SELL_VAL = 7,
+  CP_ARR_HYB_ELL_COL = 8, CP_ARR_HYB_ELL_VAL = 9,
+  CP_ARR_HYB_COO_ROW = 10, CP_ARR_HYB_COO_COL = 11, CP_ARR_HYB_COO_VAL = 12
+};
+cp_status cp_format_dims(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int64_t dims[4]);
+cp_status cp_format_export(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32_t array_id,
+                           void* dst, int64_t capacity, int64_t* bytes);
+
+/* ------------------------------------------------------------------ SpMV */
+/* cp_spmv: y = alpha * A x + beta * y with the kernel of `cfg` (NULL: the
+ * default CSR-scalar kernel); converts the format first if needed (blocking).
+ * dtype 0: x, y are FP64 device arrays; dtype 1: FP32 device arrays and the
+ * matrix values rounded to FP32 (round-to-nearest-even).  x has ncols entries,
+ * y has nrows.  When beta = 0, y is not read.  Ordered on the main stream; does
+ * not synchronise.  SpMV dominates CG and GMRES time (Sec. I). */
+enum { CP_DTYPE_F64 = 0, CP_DTYPE_F32 = 1 };
+cp_status cp_spmv(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32_t dtype,
+                  double alpha, const void* x, double beta, void* y);
+
+/* ------------------------------------------------------------------ predictors */
+/* Each cascade stage is a small MLP classifier d -> h1 -> h2 -> k (ReLU), fed
+ * z_j = (log(1 + f_j) - mu_j) / sd_j of the 15 features (FP32).  Stages
+ * (Sec. III-C-1, Fig. 5):
+ *   CP_STAGE_FORMAT     k = 5: CSR, COO, ELL, SELL, HYB
+ *   CP_STAGE_CSR_ALGO   k = 3: scalar, vector, merge      (used if FORMAT = CSR)
+ *   CP_STAGE_CSR_TPV    k = 5: TpV 2, 4, 8, 16, 32        (used if ALGO = vector)
+ *   CP_STAGE_SELL_SIGMA k = 4: sigma 1, 32, 1024, 8192    (used if FORMAT = SELL)
+ * Flat parameter layout (FP32): W1[h1][d], b1[h1], W2[h2][h1], b2[h2],
+ * W3[k][h2], b3[k].  d = 15, h1, h2 <= 64. */
+enum {
+  CP_STAGE_FORMAT = 0, CP_STAGE_CSR_ALGO = 1, CP_STAGE_CSR_TPV = 2, CP_STAGE_SELL_SIGMA = 3,
+  CP_NUM_STAGES = 4
+};
+/* Install the weights of one stage (host arrays, copied).  Without a model a
+ * stage keeps the current choice (plain CSR is the fallback). */
+cp_status cp_model_load(cp_ctx* ctx, int32_t stage, int32_t h1, int32_t h2, int32_t k,
+                        const float* params, const float* mu, const float* sd);
+/* Read back the current weights of a stage: dims = {d, h1, h2, k}; params
+ * (capacity floats), mu[15], sd[15] are host arrays. */
+cp_status cp_model_get(cp_ctx* ctx, int32_t stage, int32_t dims[4], float* params,
+                       int64_t capacity, float* mu, float* sd);
+
+/* Predictor kernels, exposed for training and for checking (device pointers,
+ * FP32, main stream, no synchronisation):
+ *  cp_mlp_forward  : logits[N][k] for inputs X[N][d].
+ *  cp_mlp_loss_grad: mean softmax cross-entropy over the batch -> loss[1] and
+ *                    its gradient grad[nparams] (same layout as params).
+ *  cp_adam_step    : one Adam step (Kingma and Ba) on params with moments m, v
+ *                    at step t >= 1.
+ * scratch: device workspace of at least cp_mlp_scratch_floats(N, dims) floats. */
+int64_t cp_mlp_nparams(int32_t d, int32_t h1, int32_t h2, int32_t k);
+int64_t cp_mlp_scratch_floats(int64_t N, int32_t d, int32_t h1, int32_t h2, int32_t k);
+cp_status cp_mlp_forward(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_t h2, int32_t k,
+                         const float* params, const float* X, float* logits, float* scratch);
+cp_status cp_mlp_loss_grad(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_t h2, int32_t k,
+                           const float* params, const float* X, const int32_t* labels,
+                           float* loss, float* grad, float* scratch);
+cp_status cp_adam_step(cp_ctx* ctx, int64_t nparams, float* params, const float* grad, float* m,
+                       float* v, int32_t t, float lr, float beta1, float beta2, float eps);
+
+/* cp_model_train: train one stage on the GPU with the kernels above.  Host
+ * inputs: raw features F[N][15] and labels[N] in [0, k); the standardisation
+ * (mu, sd of log(1 + f)) is computed from F; weights are initialised from
+ * `seed`; full-batch Adam for `epochs` steps with learning rate lr.  The
+ * trained weights replace the stage's model.  final_loss (host, may be NULL)
+ * receives the last loss.  (Sec. III-B-3 trains one classifier per stage.) */
+cp_status cp_model_train(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
+                         const int32_t* labels, int32_t h1, int32_t h2, int32_t k,
+                         int32_t epochs, float lr, uint64_t seed, float* final_loss);
+
+/* cp_predict: the sequential cascaded prediction (SerGMRES-style, Sec. IV-C):
+ * features, then FORMAT, then the algorithm / parameter stage that applies,
+ * on the side stream, joined before returning.  out receives the predicted
+ * configuration; stage_ms (host float[4], may be NULL) receives the time of
+ * feature extraction and of the three cascade steps. */
+cp_status cp_predict(cp_ctx* ctx, cp_mat* mat, cp_config* out, float* stage_ms);
+
+/* ------------------------------------------------------------------ solvers */
+enum { CP_MODE_PLAIN = 0, CP_MODE_SEQUENTIAL = 1, CP_MODE_ASYNC = 2 };
+enum { CP_PREC_FP64 = 0, CP_PREC_FP32_IR = 1 };
+
+typedef struct {
+  double tol;            /* relative residual ||b - Ax|| / ||b|| to reach (e.g. 1e-10)   */
+  int32_t maxit;         /* iteration limit (SpMV steps; IR: inner steps in total)        */
+  int32_t restart;       /* GMRES restart length m (e.g. 30), 1..64                      */
+  int32_t mode;          /* PLAIN: default kernel throughout; SEQUENTIAL: predict, then
+                            solve; ASYNC: solve at once on the default kernel while the
+                            side stream predicts, switching kernel mid-run (Sec. III-C-2) */
+  int32_t precision;     /* FP64, or FP32 inner solves inside FP64 iterative refinement   */
+  double inner_tol;      /* FP32_IR: relative tolerance of each inner solve (e.g. 1e-5)  */
+  int32_t max_outer;     /* FP32_IR: refinement steps limit                               */
+  int32_t check_every;   /* iterations between host convergence checks (0: default 8)   */
+  int32_t profile;       /* 1: time every SpMV launch with CUDA events (t_spmv_ms)        */
+  int32_t reserved;
+  const cp_config* force;/* non-NULL: use this configuration from the first iteration    */
+} cp_solve_opts;
+
+typedef struct {
+  int32_t iters;           /* SpMV steps of the Krylov iteration (all inner steps for IR) */
+  int32_t outer_iters;     /* IR refinement steps (0 for FP64)                            */
+  int32_t switch_iter[3];  /* iteration at which the FORMAT / ALGO / PARAM prediction was
+                              applied, -1 if never (Table VII)                            */
+  int32_t n_spmv;          /* SpMV launches timed when profile = 1                        */
+  int32_t n_launches;      /* kernels launched by the solve                               */
+  int32_t status;          /* the returned cp_status                                      */
+  double relres_true;      /* ||b - A x|| / ||b|| recomputed in FP64 at exit              */
+  cp_config final_cfg;     /* configuration in use at exit                                */
+  float t_features_ms, t_predict_ms[3], t_convert_ms; /* side-stream step times           */
+  float t_total_ms;        /* wall time from entry to x ready                             */
+  float t_spmv_ms;         /* summed SpMV kernel time when profile = 1                    */
+} cp_solve_info;
+
+void cp_solve_opts_default(cp_solve_opts* opts);
+
+/* cp_solve_cg: CG (Sec. I) for SPD A.  b, x: device FP64 arrays of nrows
+ * entries; x is read as x0 and overwritten with the solution.  info (host) may
+ * be NULL.  Returns CP_OK when the true relative residual <= tol,
+ * CP_ERR_NOT_CONVERGED (x = last iterate), CP_ERR_BREAKDOWN. */
+cp_status cp_solve_cg(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
+                      const cp_solve_opts* opts, cp_solve_info* info);
+
+/* cp_solve_gmres: restarted GMRES(m) (Sec. IV-A) for nonsymmetric A; classical
+ * Gram-Schmidt with one reorthogonalisation, Givens rotations and the
+ * least-squares solve in FP64.  Arguments as cp_solve_cg. */
+cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
+                         const cp_solve_opts* opts, cp_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CASCADE_H */

@@ -1,0 +1,346 @@
+"""Python binding of libcascade (include/cascade.h): argument marshalling only.
+
+Every computation runs in the library's CUDA kernels; this module converts
+NumPy arrays and torch tensors into pointers and sizes, calls the C ABI and
+turns a non-zero cp_status into a :class:`CascadeError`.  PyTorch supplies
+device memory and streams.  There is no CPU fallback: if ``libcascade.so`` is
+missing or no GPU is present the calls raise.
+
+Names follow the C ABI without the ``cp_`` prefix: :class:`Context`
+(cp_create / cp_destroy), :meth:`Context.csr_load`, :meth:`Matrix.spmv`,
+:meth:`Matrix.features`, :meth:`Matrix.convert`, :meth:`Matrix.predict`,
+:meth:`Matrix.solve_cg`, :meth:`Matrix.solve_gmres`, ...
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, Structure, byref, c_char_p, c_double, c_float, c_int32, c_int64
+from ctypes import c_uint64, c_void_p
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "libcascade.so"
+
+OK, ERR_INVALID, ERR_OOM, ERR_FOOTPRINT, ERR_NOT_CONVERGED, ERR_BREAKDOWN = range(6)
+ERR_TIMEOUT, ERR_CUDA, ERR_CANCELLED, ERR_UNSUPPORTED = range(6, 10)
+FMT_CSR, FMT_COO, FMT_ELL, FMT_SELL, FMT_HYB = range(5)
+FORMATS = ("CSR", "COO", "ELL", "SELL", "HYB")
+ALGO_SCALAR, ALGO_VECTOR, ALGO_MERGE = range(3)
+MODE_PLAIN, MODE_SEQUENTIAL, MODE_ASYNC = range(3)
+PREC_FP64, PREC_FP32_IR = range(2)
+DTYPE_F64, DTYPE_F32 = range(2)
+STAGE_FORMAT, STAGE_CSR_ALGO, STAGE_CSR_TPV, STAGE_SELL_SIGMA = range(4)
+STAGE_CLASSES = (5, 3, 5, 4)
+TPV_CLASSES = (2, 4, 8, 16, 32)
+SIGMA_CLASSES = (1, 32, 1024, 8192)
+ARR = dict(COO_ROW=0, ELL_COL=1, ELL_VAL=2, SELL_PERM=3, SELL_CHUNK_LEN=4, SELL_CHUNK_PTR=5,
+           SELL_COL=6, SELL_VAL=7, HYB_ELL_COL=8, HYB_ELL_VAL=9, HYB_COO_ROW=10,
+           HYB_COO_COL=11, HYB_COO_VAL=12)
+
+
+class CascadeError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"cascade error {status}: {msg}")
+        self.status = status
+
+
+class Config(Structure):
+    _fields_ = [("fmt", c_int32), ("algo", c_int32), ("tpv", c_int32), ("sell_c", c_int32),
+                ("sell_sigma", c_int32), ("hyb_k", c_int32)]
+
+    def as_tuple(self):
+        return (self.fmt, self.algo, self.tpv, self.sell_c, self.sell_sigma, self.hyb_k)
+
+    def __repr__(self):
+        name = FORMATS[self.fmt]
+        if self.fmt == FMT_CSR:
+            name += ("-scalar", f"-vector{self.tpv}", "-merge")[self.algo]
+        elif self.fmt == FMT_SELL:
+            name += f"-{self.sell_c}-{self.sell_sigma}"
+        elif self.fmt == FMT_HYB:
+            name += f"-K{self.hyb_k}"
+        return name
+
+
+def config(fmt="CSR", algo=ALGO_SCALAR, tpv=8, sigma=1, hyb_k=0) -> Config:
+    """A cp_config; fmt by name or index."""
+    f = FORMATS.index(fmt) if isinstance(fmt, str) else int(fmt)
+    return Config(f, algo, tpv, 32, sigma, hyb_k)
+
+
+class SolveOpts(Structure):
+    _fields_ = [("tol", c_double), ("maxit", c_int32), ("restart", c_int32), ("mode", c_int32),
+                ("precision", c_int32), ("inner_tol", c_double), ("max_outer", c_int32),
+                ("check_every", c_int32), ("profile", c_int32), ("reserved", c_int32),
+                ("force", POINTER(Config))]
+
+
+class SolveInfo(Structure):
+    _fields_ = [("iters", c_int32), ("outer_iters", c_int32), ("switch_iter", c_int32 * 3),
+                ("n_spmv", c_int32), ("n_launches", c_int32), ("status", c_int32),
+                ("relres_true", c_double), ("final_cfg", Config), ("t_features_ms", c_float),
+                ("t_predict_ms", c_float * 3), ("t_convert_ms", c_float),
+                ("t_total_ms", c_float), ("t_spmv_ms", c_float)]
+
+    def as_dict(self):
+        return dict(iters=self.iters, outer_iters=self.outer_iters,
+                    switch_iter=list(self.switch_iter), n_spmv=self.n_spmv,
+                    n_launches=self.n_launches, status=self.status,
+                    relres_true=self.relres_true, final_cfg=repr(self.final_cfg),
+                    t_features_ms=self.t_features_ms, t_predict_ms=list(self.t_predict_ms),
+                    t_convert_ms=self.t_convert_ms, t_total_ms=self.t_total_ms,
+                    t_spmv_ms=self.t_spmv_ms)
+
+
+_p = c_void_p
+_SIGS = {
+    "cp_config_default": (None, [POINTER(Config)]),
+    "cp_solve_opts_default": (None, [POINTER(SolveOpts)]),
+    "cp_last_error": (c_char_p, []),
+    "cp_create": (c_int32, [POINTER(_p), c_int32, _p, _p]),
+    "cp_destroy": (c_int32, [_p]),
+    "cp_ctx_launch_count": (c_int32, [_p, POINTER(c_int64)]),
+    "cp_set_format_budget": (c_int32, [_p, c_int64]),
+    "cp_csr_load": (c_int32, [_p, c_int64, c_int64, c_int64, _p, _p, _p, c_int32, POINTER(_p)]),
+    "cp_mat_free": (c_int32, [_p]),
+    "cp_features": (c_int32, [_p, _p, _p]),
+    "cp_convert": (c_int32, [_p, _p, POINTER(Config)]),
+    "cp_format_dims": (c_int32, [_p, _p, POINTER(Config), _p]),
+    "cp_format_export": (c_int32, [_p, _p, POINTER(Config), c_int32, _p, c_int64,
+                                   POINTER(c_int64)]),
+    "cp_spmv": (c_int32, [_p, _p, POINTER(Config), c_int32, c_double, _p, c_double, _p]),
+    "cp_mlp_nparams": (c_int64, [c_int32, c_int32, c_int32, c_int32]),
+    "cp_mlp_scratch_floats": (c_int64, [c_int64, c_int32, c_int32, c_int32, c_int32]),
+    "cp_mlp_forward": (c_int32, [_p, c_int64, c_int32, c_int32, c_int32, c_int32, _p, _p, _p, _p]),
+    "cp_mlp_loss_grad": (c_int32, [_p, c_int64, c_int32, c_int32, c_int32, c_int32, _p, _p, _p,
+                                   _p, _p, _p]),
+    "cp_adam_step": (c_int32, [_p, c_int64, _p, _p, _p, _p, c_int32, c_float, c_float, c_float,
+                               c_float]),
+    "cp_model_load": (c_int32, [_p, c_int32, c_int32, c_int32, c_int32, _p, _p, _p]),
+    "cp_model_get": (c_int32, [_p, c_int32, _p, _p, c_int64, _p, _p]),
+    "cp_model_train": (c_int32, [_p, c_int32, c_int64, _p, _p, c_int32, c_int32, c_int32,
+                                 c_int32, c_float, c_uint64, POINTER(c_float)]),
+    "cp_predict": (c_int32, [_p, _p, POINTER(Config), _p]),
+    "cp_solve_cg": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
+    "cp_solve_gmres": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
+}
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcascade.so (built in-tree by ``paper_2411_10143_b300.build``)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise CascadeError(ERR_CUDA, f"{_LIB_PATH.name} is not built; run build.build()")
+        L = ctypes.CDLL(str(_LIB_PATH))
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != OK:
+        msg = lib().cp_last_error()
+        raise CascadeError(status, msg.decode() if msg else "")
+
+
+def _ptr(a):
+    """Address of a torch tensor or NumPy array (must stay alive during the call)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return c_void_p(a.data_ptr())
+    return a.ctypes.data_as(c_void_p)
+
+
+def _np(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def default_opts(**kw) -> SolveOpts:
+    o = SolveOpts()
+    lib().cp_solve_opts_default(byref(o))
+    for k, v in kw.items():
+        if k == "force":
+            continue
+        setattr(o, k, v)
+    return o
+
+
+class Context:
+    """cp_create / cp_destroy.  ``main_stream`` / ``side_stream`` are torch CUDA
+    streams (or None for library-owned streams)."""
+
+    def __init__(self, device: int = 0, main_stream=None, side_stream=None):
+        self._h = c_void_p()
+        self.device = device
+        self._streams = (main_stream, side_stream)  # keep them alive
+        ms = c_void_p(main_stream.cuda_stream) if main_stream is not None else None
+        ss = c_void_p(side_stream.cuda_stream) if side_stream is not None else None
+        _check(lib().cp_create(byref(self._h), device, ms, ss))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _check(lib().cp_destroy(self._h))
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        c = c_int64()
+        _check(lib().cp_ctx_launch_count(self._h, byref(c)))
+        return c.value
+
+    def set_format_budget(self, nbytes: int):
+        _check(lib().cp_set_format_budget(self._h, int(nbytes)))
+
+    def csr_load(self, nrows, ncols, rowptr, col, val) -> "Matrix":
+        """Copy a CSR matrix (NumPy host arrays or torch CUDA tensors) into the library."""
+        on_dev = hasattr(rowptr, "is_cuda") and rowptr.is_cuda
+        if not on_dev:
+            rowptr, col, val = _np(rowptr, np.int32), _np(col, np.int32), _np(val, np.float64)
+        nnz = int(col.numel() if on_dev else col.size)
+        h = c_void_p()
+        _check(lib().cp_csr_load(self._h, int(nrows), int(ncols), nnz, _ptr(rowptr), _ptr(col),
+                                 _ptr(val), 1 if on_dev else 0, byref(h)))
+        return Matrix(self, h, int(nrows), int(ncols), nnz)
+
+    def load(self, A) -> "Matrix":
+        """csr_load of a matrix object with nrows, ncols, rowptr, col, val."""
+        return self.csr_load(A.nrows, A.ncols, A.rowptr, A.col, A.val)
+
+    # ---------------------------------------------------------------- predictors
+    def model_load(self, stage, h1, h2, k, params, mu, sd):
+        params, mu, sd = _np(params, np.float32), _np(mu, np.float32), _np(sd, np.float32)
+        _check(lib().cp_model_load(self._h, stage, h1, h2, k, _ptr(params), _ptr(mu), _ptr(sd)))
+
+    def model_get(self, stage):
+        dims = np.zeros(4, np.int32)
+        _check(lib().cp_model_get(self._h, stage, _ptr(dims), None, 0, None, None))
+        n = int(lib().cp_mlp_nparams(*[int(v) for v in dims]))
+        params = np.zeros(n, np.float32)
+        mu = np.zeros(15, np.float32)
+        sd = np.zeros(15, np.float32)
+        _check(lib().cp_model_get(self._h, stage, _ptr(dims), _ptr(params), n, _ptr(mu), _ptr(sd)))
+        return dict(dims=dims.tolist(), params=params, mu=mu, sd=sd)
+
+    def model_train(self, stage, F, labels, h1=32, h2=32, epochs=2000, lr=3e-3, seed=1):
+        F = _np(F, np.float64).reshape(-1, 15)
+        lab = _np(labels, np.int32)
+        loss = c_float()
+        _check(lib().cp_model_train(self._h, stage, F.shape[0], _ptr(F), _ptr(lab), h1, h2,
+                                    STAGE_CLASSES[stage], epochs, lr, seed, byref(loss)))
+        return loss.value
+
+    def mlp_forward(self, dims, params, X, logits, scratch):
+        d, h1, h2, k = dims
+        _check(lib().cp_mlp_forward(self._h, X.shape[0], d, h1, h2, k, _ptr(params), _ptr(X),
+                                    _ptr(logits), _ptr(scratch)))
+
+    def mlp_loss_grad(self, dims, params, X, labels, loss, grad, scratch):
+        d, h1, h2, k = dims
+        _check(lib().cp_mlp_loss_grad(self._h, X.shape[0], d, h1, h2, k, _ptr(params), _ptr(X),
+                                      _ptr(labels), _ptr(loss), _ptr(grad), _ptr(scratch)))
+
+    def adam_step(self, params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        _check(lib().cp_adam_step(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m),
+                                  _ptr(v), t, lr, b1, b2, eps))
+
+    @staticmethod
+    def mlp_nparams(d, h1, h2, k):
+        return int(lib().cp_mlp_nparams(d, h1, h2, k))
+
+    @staticmethod
+    def mlp_scratch_floats(N, d, h1, h2, k):
+        return int(lib().cp_mlp_scratch_floats(N, d, h1, h2, k))
+
+
+class Matrix:
+    """A cp_mat: library-owned device copy of a CSR matrix and its converted formats."""
+
+    def __init__(self, ctx: Context, h, nrows, ncols, nnz):
+        self.ctx, self._h = ctx, h
+        self.nrows, self.ncols, self.nnz = nrows, ncols, nnz
+
+    def free(self):
+        if self._h:
+            _check(lib().cp_mat_free(self._h))
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            if self.ctx._h:
+                self.free()
+        except Exception:
+            pass
+
+    def features(self) -> np.ndarray:
+        out = np.zeros(15)
+        _check(lib().cp_features(self.ctx.handle, self._h, _ptr(out)))
+        return out
+
+    def convert(self, cfg: Config):
+        _check(lib().cp_convert(self.ctx.handle, self._h, byref(cfg)))
+
+    def format_dims(self, cfg: Config):
+        d = np.zeros(4, np.int64)
+        _check(lib().cp_format_dims(self.ctx.handle, self._h, byref(cfg), _ptr(d)))
+        return d.tolist()
+
+    def format_export(self, cfg: Config, array: str, dtype) -> np.ndarray:
+        nb = c_int64()
+        probe = np.zeros(1, np.uint8)
+        st = lib().cp_format_export(self.ctx.handle, self._h, byref(cfg), ARR[array], _ptr(probe),
+                                    0, byref(nb))
+        if st not in (OK, ERR_INVALID):
+            _check(st)
+        out = np.zeros(max(nb.value, 1), np.uint8)
+        _check(lib().cp_format_export(self.ctx.handle, self._h, byref(cfg), ARR[array], _ptr(out),
+                                      out.size, byref(nb)))
+        return out[:nb.value].view(dtype)
+
+    def spmv(self, x, y, cfg: Config | None = None, alpha=1.0, beta=0.0):
+        """y = alpha A x + beta y on torch CUDA tensors (float64 or float32)."""
+        import torch
+        dtype = DTYPE_F64 if x.dtype == torch.float64 else DTYPE_F32
+        assert y.dtype == x.dtype and x.is_cuda and y.is_cuda
+        _check(lib().cp_spmv(self.ctx.handle, self._h, byref(cfg) if cfg is not None else None,
+                             dtype, alpha, _ptr(x), beta, _ptr(y)))
+
+    def predict(self):
+        cfg = Config()
+        ms = np.zeros(4, np.float32)
+        _check(lib().cp_predict(self.ctx.handle, self._h, byref(cfg), _ptr(ms)))
+        return cfg, ms
+
+    def _solve(self, fn, b, x, opts: SolveOpts | None, force: Config | None, raise_on_error):
+        o = opts if opts is not None else default_opts()
+        if force is not None:
+            o.force = ctypes.pointer(force)
+        info = SolveInfo()
+        st = fn(self.ctx.handle, self._h, _ptr(b), _ptr(x), byref(o), byref(info))
+        if raise_on_error:
+            _check(st)
+        return info
+
+    def solve_cg(self, b, x, opts=None, force=None, raise_on_error=True) -> SolveInfo:
+        """CG on torch CUDA float64 tensors b, x (x: x0 in, solution out)."""
+        return self._solve(lib().cp_solve_cg, b, x, opts, force, raise_on_error)
+
+    def solve_gmres(self, b, x, opts=None, force=None, raise_on_error=True) -> SolveInfo:
+        """Restarted GMRES(m) on torch CUDA float64 tensors b, x."""
+        return self._solve(lib().cp_solve_gmres, b, x, opts, force, raise_on_error)

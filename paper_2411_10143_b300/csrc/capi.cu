@@ -1,0 +1,372 @@
+// The C ABI of libcascade (declared in include/cascade.h): argument checks,
+// error capture and dispatch into the runtime.  No entry point lets a C++
+// exception or a CUDA error escape; each returns a cp_status and records a
+// message for cp_last_error().
+#include <cstdarg>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace cp {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+template <typename F>
+static cp_status guard(F&& f) {
+  try {
+    g_err[0] = 0;
+    f();
+    return CP_OK;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    set_error("host allocation failed");
+    return CP_ERR_OOM;
+  } catch (...) {
+    set_error("unexpected internal error");
+    return CP_ERR_CUDA;
+  }
+}
+
+// Make ctx's device current for the calling thread.
+static void use_device(cp_ctx* ctx) { CP_CUDA(cudaSetDevice(ctx->device)); }
+
+}  // namespace cp
+
+using namespace cp;
+
+extern "C" {
+
+void cp_config_default(cp_config* c) {
+  if (!c) return;
+  c->fmt = CP_FMT_CSR;
+  c->algo = CP_ALGO_SCALAR;
+  c->tpv = 8;
+  c->sell_c = 32;
+  c->sell_sigma = 1;
+  c->hyb_k = 0;
+}
+
+void cp_solve_opts_default(cp_solve_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-10;
+  o->maxit = 100000;
+  o->restart = 30;
+  o->mode = CP_MODE_PLAIN;
+  o->precision = CP_PREC_FP64;
+  o->inner_tol = 1e-5;
+  o->max_outer = 30;
+  o->check_every = 8;
+  o->profile = 0;
+  o->force = nullptr;
+}
+
+const char* cp_last_error(void) { return g_err; }
+
+cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_stream) {
+  return guard([&] {
+    CP_REQUIRE(out, CP_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    CP_CUDA(cudaGetDeviceCount(&count));
+    CP_REQUIRE(device >= 0 && device < count, CP_ERR_INVALID, "device %d not present (%d GPUs)",
+               device, count);
+    CP_CUDA(cudaSetDevice(device));
+    cp_ctx* c = new cp_ctx();
+    c->device = device;
+    try {
+      CP_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+      int max_threads = 0;
+      CP_CUDA(cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, device));
+      c->grid_stream = c->num_sms * (max_threads / kBlock);
+      if (c->grid_stream > kMaxPartials) c->grid_stream = kMaxPartials;
+      if (main_stream) {
+        c->main = static_cast<cudaStream_t>(main_stream);
+      } else {
+        CP_CUDA(cudaStreamCreateWithFlags(&c->main, cudaStreamNonBlocking));
+        c->own_main = true;
+      }
+      if (side_stream) {
+        c->side = static_cast<cudaStream_t>(side_stream);
+      } else {
+        CP_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+        c->own_side = true;
+      }
+    } catch (...) {
+      if (c->own_main && c->main) cudaStreamDestroy(c->main);
+      if (c->own_side && c->side) cudaStreamDestroy(c->side);
+      delete c;
+      throw;
+    }
+    *out = c;
+  });
+}
+
+cp_status cp_destroy(cp_ctx* ctx) {
+  return guard([&] {
+    if (!ctx) return;
+    use_device(ctx);
+    cudaStreamSynchronize(ctx->main);
+    cudaStreamSynchronize(ctx->side);
+    for (auto& mslot : ctx->models) {
+      dfree(mslot.d_params);
+      dfree(mslot.d_mu);
+      dfree(mslot.d_sd);
+    }
+    if (ctx->own_main) cudaStreamDestroy(ctx->main);
+    if (ctx->own_side) cudaStreamDestroy(ctx->side);
+    delete ctx;
+  });
+}
+
+cp_status cp_ctx_launch_count(cp_ctx* ctx, int64_t* count) {
+  return guard([&] {
+    CP_REQUIRE(ctx && count, CP_ERR_INVALID, "NULL argument");
+    *count = ctx->launches.load();
+  });
+}
+
+cp_status cp_set_format_budget(cp_ctx* ctx, int64_t bytes) {
+  return guard([&] {
+    CP_REQUIRE(ctx && bytes > 0, CP_ERR_INVALID, "bad budget");
+    ctx->format_budget = bytes;
+  });
+}
+
+cp_status cp_csr_load(cp_ctx* ctx, int64_t nrows, int64_t ncols, int64_t nnz,
+                      const int32_t* rowptr, const int32_t* col, const double* val,
+                      int32_t on_device, cp_mat** out) {
+  return guard([&] {
+    CP_REQUIRE(ctx && out && rowptr, CP_ERR_INVALID, "NULL argument");
+    *out = nullptr;
+    CP_REQUIRE(nrows >= 1 && ncols >= 1 && nrows < (int64_t(1) << 31) &&
+                   ncols < (int64_t(1) << 31),
+               CP_ERR_INVALID, "nrows and ncols must be in 1..2^31-1");
+    CP_REQUIRE(nnz >= 0 && nnz < (int64_t(1) << 31), CP_ERR_INVALID, "nnz must be in 0..2^31-1");
+    CP_REQUIRE(nnz == 0 || (col && val), CP_ERR_INVALID, "col/val are NULL");
+    use_device(ctx);
+    cp_mat* m = new cp_mat();
+    m->ctx = ctx;
+    m->nrows = nrows;
+    m->ncols = ncols;
+    m->nnz = nnz;
+    try {
+      m->rowptr = dalloc<int32_t>(nrows + 1);
+      m->col = dalloc<int32_t>(nnz);
+      m->val = dalloc<double>(nnz);
+      const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+      CP_CUDA(cudaMemcpyAsync(m->rowptr, rowptr, (nrows + 1) * 4, kind, ctx->main));
+      if (nnz > 0) {
+        CP_CUDA(cudaMemcpyAsync(m->col, col, nnz * 4, kind, ctx->main));
+        CP_CUDA(cudaMemcpyAsync(m->val, val, nnz * 8, kind, ctx->main));
+      }
+      csr_validate(ctx, m);  // synchronises the main stream
+    } catch (...) {
+      dfree(m->rowptr);
+      dfree(m->col);
+      dfree(m->val);
+      delete m;
+      throw;
+    }
+    *out = m;
+  });
+}
+
+cp_status cp_mat_free(cp_mat* m) {
+  return guard([&] {
+    if (!m) return;
+    use_device(m->ctx);
+    cudaStreamSynchronize(m->ctx->main);
+    cudaStreamSynchronize(m->ctx->side);
+    free_formats(m);
+    dfree(m->rowptr);
+    dfree(m->col);
+    dfree(m->val);
+    delete m;
+  });
+}
+
+cp_status cp_features(cp_ctx* ctx, cp_mat* m, double* out15) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && out15, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    compute_features(ctx, m, ctx->main, out15);
+  });
+}
+
+cp_status cp_convert(cp_ctx* ctx, cp_mat* m, const cp_config* cfg) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && cfg, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    ensure_format(ctx, m, *cfg, ctx->main);
+    CP_CUDA(cudaStreamSynchronize(ctx->main));
+  });
+}
+
+cp_status cp_format_dims(cp_ctx* ctx, cp_mat* m, const cp_config* cfg, int64_t dims[4]) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && cfg && dims, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    ensure_format(ctx, m, *cfg, ctx->main);
+    format_dims(m, *cfg, dims);
+  });
+}
+
+cp_status cp_format_export(cp_ctx* ctx, cp_mat* m, const cp_config* cfg, int32_t array_id,
+                           void* dst, int64_t capacity, int64_t* bytes) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && cfg && dst && bytes, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    ensure_format(ctx, m, *cfg, ctx->main);
+    format_export(m, *cfg, array_id, dst, capacity, bytes, ctx->main);
+  });
+}
+
+cp_status cp_spmv(cp_ctx* ctx, cp_mat* m, const cp_config* cfg, int32_t dtype, double alpha,
+                  const void* x, double beta, void* y) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && x && y, CP_ERR_INVALID, "NULL argument");
+    CP_REQUIRE(dtype == CP_DTYPE_F64 || dtype == CP_DTYPE_F32, CP_ERR_INVALID, "bad dtype %d",
+               dtype);
+    use_device(ctx);
+    cp_config c;
+    cp_config_default(&c);
+    if (cfg) c = *cfg;
+    ensure_format(ctx, m, c, ctx->main);
+    if (dtype == CP_DTYPE_F64) {
+      spmv_general<double>(ctx, m, c, alpha, static_cast<const double*>(x), beta,
+                           static_cast<double*>(y), ctx->main);
+    } else {
+      ensure_val32(ctx, m, c, ctx->main);
+      spmv_general<float>(ctx, m, c, (float)alpha, static_cast<const float*>(x), (float)beta,
+                          static_cast<float*>(y), ctx->main);
+    }
+  });
+}
+
+cp_status cp_solve_cg(cp_ctx* ctx, cp_mat* m, const double* b, double* x,
+                      const cp_solve_opts* opts, cp_solve_info* info) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && b && x, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    solve(ctx, m, b, x, opts, info, false);
+  });
+}
+
+cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* m, const double* b, double* x,
+                         const cp_solve_opts* opts, cp_solve_info* info) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && b && x, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    solve(ctx, m, b, x, opts, info, true);
+  });
+}
+
+int64_t cp_mlp_nparams(int32_t d, int32_t h1, int32_t h2, int32_t k) {
+  return (int64_t)h1 * d + h1 + (int64_t)h2 * h1 + h2 + (int64_t)k * h2 + k;
+}
+
+int64_t cp_mlp_scratch_floats(int64_t N, int32_t d, int32_t h1, int32_t h2, int32_t k) {
+  return scratch_floats_api(N, d, h1, h2, k);
+}
+
+cp_status cp_mlp_forward(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_t h2, int32_t k,
+                         const float* params, const float* X, float* logits, float* scratch) {
+  return guard([&] {
+    CP_REQUIRE(ctx && params && X && logits && scratch && N >= 1, CP_ERR_INVALID, "bad argument");
+    use_device(ctx);
+    mlp_forward(ctx, N, MlpDims{d, h1, h2, k}, params, X, logits, scratch, ctx->main);
+  });
+}
+
+cp_status cp_mlp_loss_grad(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_t h2, int32_t k,
+                           const float* params, const float* X, const int32_t* labels,
+                           float* loss, float* grad, float* scratch) {
+  return guard([&] {
+    CP_REQUIRE(ctx && params && X && labels && loss && grad && scratch && N >= 1, CP_ERR_INVALID,
+               "bad argument");
+    use_device(ctx);
+    mlp_loss_grad(ctx, N, MlpDims{d, h1, h2, k}, params, X, labels, loss, grad, scratch,
+                  ctx->main);
+  });
+}
+
+cp_status cp_adam_step(cp_ctx* ctx, int64_t nparams, float* params, const float* grad, float* m,
+                       float* v, int32_t t, float lr, float beta1, float beta2, float eps) {
+  return guard([&] {
+    CP_REQUIRE(ctx && params && grad && m && v && nparams >= 1, CP_ERR_INVALID, "bad argument");
+    use_device(ctx);
+    adam_step(ctx, nparams, params, grad, m, v, t, lr, beta1, beta2, eps, ctx->main);
+  });
+}
+
+cp_status cp_model_load(cp_ctx* ctx, int32_t stage, int32_t h1, int32_t h2, int32_t k,
+                        const float* params, const float* mu, const float* sd) {
+  return guard([&] {
+    CP_REQUIRE(ctx && params && mu && sd, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    model_install(ctx, stage, h1, h2, k, params, mu, sd, ctx->main);
+  });
+}
+
+cp_status cp_model_get(cp_ctx* ctx, int32_t stage, int32_t dims[4], float* params,
+                       int64_t capacity, float* mu, float* sd) {
+  return guard([&] {
+    CP_REQUIRE(ctx && dims && stage >= 0 && stage < CP_NUM_STAGES, CP_ERR_INVALID, "bad argument");
+    use_device(ctx);
+    std::lock_guard<std::mutex> lock(ctx->model_mu);
+    const ModelSlot& s = ctx->models[stage];
+    CP_REQUIRE(s.loaded, CP_ERR_INVALID, "stage %d has no model", stage);
+    dims[0] = 15;
+    dims[1] = s.h1;
+    dims[2] = s.h2;
+    dims[3] = s.k;
+    const int64_t np = cp_mlp_nparams(15, s.h1, s.h2, s.k);
+    if (params) {
+      CP_REQUIRE(capacity >= np, CP_ERR_INVALID, "params needs %lld floats", (long long)np);
+      CP_CUDA(cudaMemcpy(params, s.d_params, np * 4, cudaMemcpyDeviceToHost));
+    }
+    if (mu) CP_CUDA(cudaMemcpy(mu, s.d_mu, 15 * 4, cudaMemcpyDeviceToHost));
+    if (sd) CP_CUDA(cudaMemcpy(sd, s.d_sd, 15 * 4, cudaMemcpyDeviceToHost));
+  });
+}
+
+cp_status cp_model_train(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
+                         const int32_t* labels, int32_t h1, int32_t h2, int32_t k,
+                         int32_t epochs, float lr, uint64_t seed, float* final_loss) {
+  return guard([&] {
+    CP_REQUIRE(ctx && F && labels && epochs >= 0, CP_ERR_INVALID, "bad argument");
+    use_device(ctx);
+    model_train(ctx, stage, N, F, labels, h1, h2, k, epochs, lr, seed, final_loss);
+  });
+}
+
+cp_status cp_predict(cp_ctx* ctx, cp_mat* m, cp_config* out, float* stage_ms) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && out, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    Channel ch;
+    run_cascade(ctx, m, ctx->side, &ch);
+    CP_REQUIRE(ch.status == CP_OK, ch.status, "%s", ch.error.c_str());
+    cp_config_default(out);
+    for (auto& p : ch.published) *out = p.second;
+    if (stage_ms) {
+      stage_ms[0] = ch.t_features_ms;
+      stage_ms[1] = ch.t_predict_ms[0];
+      stage_ms[2] = ch.t_predict_ms[1];
+      stage_ms[3] = ch.t_predict_ms[2];
+    }
+  });
+}
+
+}  // extern "C"

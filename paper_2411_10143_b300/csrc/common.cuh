@@ -1,0 +1,93 @@
+// Device-side helpers shared by the kernels: reductions and cache-hinted loads.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace cp {
+
+// Streaming load for matrix data read once per SpMV: evict-first, so the
+// Krylov vectors (which are re-read every iteration) keep their L2 lines.
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p) { return __ldcs(p); }
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ float ld_stream(const float* p) { return __ldcs(p); }
+// Read-only gather of x.
+template <typename T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  return __ldg(p);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  Every thread must call
+// it; smem holds at least blockDim.x / 32 doubles.  Fixed order: deterministic.
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();  // smem may still be read by a previous call
+  if (lane == 0) smem[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+    s = lane < nw ? smem[lane] : 0.0;
+    s = warp_sum(s);
+  }
+  return s;
+}
+
+// The same for G values at once (G small): out[g] valid in thread 0.
+template <int G>
+__device__ __forceinline__ void block_sum_multi(double (&v)[G], double* smem /*G*32*/) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int g = 0; g < G; ++g) v[g] = warp_sum(v[g]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int g = 0; g < G; ++g) smem[g * 32 + warp] = v[g];
+  }
+  __syncthreads();
+  if (warp == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      double s = lane < nw ? smem[g * 32 + lane] : 0.0;
+      v[g] = warp_sum(s);
+    }
+  }
+}
+
+// Sum of P block partials in fixed order by the whole block; the result is
+// returned to every thread.  smem holds at least blockDim.x / 32 + 1 doubles.
+__device__ __forceinline__ double reduce_partials(const double* __restrict__ partials, int P,
+                                                  double* smem) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s += partials[i];
+  s = block_sum(s, smem);
+  const int last = blockDim.x >> 5;
+  if (threadIdx.x == 0) smem[last] = s;
+  __syncthreads();
+  s = smem[last];
+  __syncthreads();
+  return s;
+}
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using type = double2;
+};
+template <>
+struct Vec2<float> {
+  using type = float2;
+};
+
+}  // namespace cp

@@ -1,0 +1,869 @@
+// CSR validation, the Table IV feature kernel, and the format conversions
+// CSR -> COO / ELL / SELL-C-sigma / HYB (Sec. III-C-1: switching format needs
+// new storage and a conversion kernel).  Conversions are integer work that
+// copies indices and values bit for bit.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace cp {
+
+static int grid_cap(cp_ctx* ctx, int64_t items, int block = kBlock) {
+  int64_t g = (items + block - 1) / block;
+  if (g > ctx->grid_stream) g = ctx->grid_stream;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// ================================================================== validation
+enum : unsigned {
+  kBadFirst = 1, kBadLast = 2, kDecreasing = 4, kRange = 8, kColRange = 16, kUnsorted = 32
+};
+
+__global__ void k_validate(int64_t n, int64_t ncols, int64_t nnz, const int32_t* __restrict__ rp,
+                           const int32_t* __restrict__ ci, unsigned* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = rp[i], e = rp[i + 1];
+    unsigned f = 0;
+    if (i == 0 && s != 0) f |= kBadFirst;
+    if (i == n - 1 && e != nnz) f |= kBadLast;
+    if (e < s) f |= kDecreasing;
+    if (s < 0 || e > nnz) f |= kRange;
+    if (!(f & (kDecreasing | kRange))) {
+      int64_t prev = -1;
+      for (int64_t k = s; k < e; ++k) {
+        const int64_t c = ci[k];
+        if (c < 0 || c >= ncols) f |= kColRange;
+        if (c <= prev) f |= kUnsorted;
+        prev = c;
+      }
+    }
+    if (f) atomicOr(err, f);
+  }
+}
+
+void csr_validate(cp_ctx* ctx, cp_mat* m) {
+  unsigned* d_err = dalloc<unsigned>(1);
+  unsigned h_err = 0;
+  try {
+    CP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(unsigned), ctx->main));
+    CP_LAUNCH(ctx, k_validate, grid_cap(ctx, m->nrows), kBlock, 0, ctx->main, m->nrows, m->ncols,
+              m->nnz, m->rowptr, m->col, d_err);
+    CP_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->main));
+    CP_CUDA(cudaStreamSynchronize(ctx->main));
+  } catch (...) {
+    dfree(d_err);
+    throw;
+  }
+  dfree(d_err);
+  CP_REQUIRE(h_err == 0, CP_ERR_INVALID,
+             "invalid CSR:%s%s%s%s%s%s", (h_err & kBadFirst) ? " rowptr[0]!=0" : "",
+             (h_err & kBadLast) ? " rowptr[n]!=nnz" : "",
+             (h_err & kDecreasing) ? " rowptr decreasing" : "",
+             (h_err & kRange) ? " rowptr out of [0,nnz]" : "",
+             (h_err & kColRange) ? " column out of range" : "",
+             (h_err & kUnsorted) ? " columns not strictly increasing" : "");
+}
+
+// ================================================================== features (Table IV)
+struct FeatAcc {
+  unsigned long long sum_r2;  // sum of squared row lengths
+  unsigned long long dist;    // sum of (last col - first col)
+  unsigned long long clus;    // sum of the longest consecutive-column runs
+  unsigned long long ndiag;   // distinct (col - row) offsets
+  unsigned maxr;              // longest row
+  unsigned minr;              // shortest row (initialised to UINT_MAX)
+};
+
+constexpr int kLongRow = 64;  // rows longer than this are handled a warp at a time
+
+__device__ __forceinline__ void mark_diag(unsigned* bitmap, int64_t off) {
+  atomicOr(bitmap + (off >> 5), 1u << (off & 31));
+}
+
+template <typename U>
+__device__ __forceinline__ U warp_sum_u(U v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Pass 1: thread per row.  Lengths, sums and extremes for every row; column
+// width, longest run and offsets for rows of at most kLongRow entries.
+__global__ void __launch_bounds__(kBlock) k_features_rows(int64_t n, const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci,
+                                                          unsigned* __restrict__ bitmap,
+                                                          FeatAcc* acc) {
+  unsigned long long r2 = 0, dist = 0, clus = 0;
+  unsigned mx = 0, mn = UINT_MAX;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = rp[i], e = rp[i + 1];
+    const unsigned len = (unsigned)(e - s);
+    r2 += (unsigned long long)len * len;
+    mx = max(mx, len);
+    mn = min(mn, len);
+    if (len == 0 || len > kLongRow) continue;
+    int32_t prev = ci[s];
+    dist += (unsigned long long)(ci[e - 1] - prev);
+    unsigned run = 1, best = 1;
+    mark_diag(bitmap, (int64_t)prev - i + (n - 1));
+    for (int64_t k = s + 1; k < e; ++k) {
+      const int32_t c = ci[k];
+      run = (c == prev + 1) ? run + 1 : 1;
+      best = max(best, run);
+      mark_diag(bitmap, (int64_t)c - i + (n - 1));
+      prev = c;
+    }
+    clus += best;
+  }
+  r2 = warp_sum_u(r2);
+  dist = warp_sum_u(dist);
+  clus = warp_sum_u(clus);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (r2) atomicAdd(&acc->sum_r2, r2);
+    if (dist) atomicAdd(&acc->dist, dist);
+    if (clus) atomicAdd(&acc->clus, clus);
+    atomicMax(&acc->maxr, mx);
+    atomicMin(&acc->minr, mn);
+  }
+}
+
+// Pass 2: rows longer than kLongRow, one warp per row.  Each lane summarises a
+// contiguous piece of the row (first/last column, leading and trailing runs,
+// longest inner run); lane 0 folds the 32 summaries left to right.
+__global__ void __launch_bounds__(kBlock) k_features_long(int64_t n, const int32_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci,
+                                                          unsigned* __restrict__ bitmap,
+                                                          FeatAcc* acc) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long dist = 0, clus = 0;
+  for (int64_t r0 = warp * 32; r0 < n; r0 += nwarps * 32) {
+    const int64_t mine = r0 + lane;
+    const int64_t len_mine = mine < n ? (int64_t)rp[mine + 1] - rp[mine] : 0;
+    unsigned longmask = __ballot_sync(0xffffffffu, len_mine > kLongRow);
+    while (longmask) {
+      const int src = __ffs(longmask) - 1;
+      longmask &= longmask - 1;
+      const int64_t i = r0 + src;
+      const int64_t s = rp[i], e = rp[i + 1], L = e - s;
+      const int64_t per = (L + 31) / 32;
+      const int64_t a = s + lane * per, b = min(e, a + per);
+      // piece summary
+      int64_t plen = b > a ? b - a : 0;
+      int32_t first = 0, last = 0;
+      unsigned pre = 0, suf = 0, best = 0;
+      bool full = false;
+      if (plen > 0) {
+        first = ci[a];
+        int32_t prev = first;
+        unsigned run = 1;
+        best = 1;
+        pre = 1;
+        bool in_prefix = true;
+        mark_diag(bitmap, (int64_t)first - i + (n - 1));
+        for (int64_t k = a + 1; k < b; ++k) {
+          const int32_t c = ci[k];
+          if (c == prev + 1) {
+            ++run;
+          } else {
+            run = 1;
+            in_prefix = false;
+          }
+          if (in_prefix) pre = run;
+          best = max(best, run);
+          mark_diag(bitmap, (int64_t)c - i + (n - 1));
+          prev = c;
+        }
+        last = prev;
+        suf = run;
+        full = in_prefix;
+      }
+      // fold the 32 piece summaries in lane order (every lane takes part)
+      int32_t c_last = __shfl_sync(0xffffffffu, last, 0);
+      unsigned c_suf = __shfl_sync(0xffffffffu, suf, 0);
+      unsigned c_best = __shfl_sync(0xffffffffu, best, 0);
+      int64_t c_len = __shfl_sync(0xffffffffu, plen, 0);
+      for (int j = 1; j < 32; ++j) {
+        const int64_t jl = __shfl_sync(0xffffffffu, plen, j);
+        const int32_t jf = __shfl_sync(0xffffffffu, first, j);
+        const int32_t jlast = __shfl_sync(0xffffffffu, last, j);
+        const unsigned jpre = __shfl_sync(0xffffffffu, pre, j);
+        const unsigned jsuf = __shfl_sync(0xffffffffu, suf, j);
+        const unsigned jbest = __shfl_sync(0xffffffffu, best, j);
+        const bool jfull = __shfl_sync(0xffffffffu, (int)full, j) != 0;
+        if (jl == 0) continue;
+        if (c_len == 0) {
+          c_last = jlast; c_suf = jsuf; c_best = jbest; c_len = jl;
+          continue;
+        }
+        const bool joined = (jf == c_last + 1);
+        if (joined) c_best = max(c_best, c_suf + jpre);
+        c_best = max(c_best, jbest);
+        c_suf = (jfull && joined) ? c_suf + (unsigned)jl : jsuf;
+        c_last = jlast;
+        c_len += jl;
+      }
+      if (lane == 0) {
+        dist += (unsigned long long)(ci[e - 1] - ci[s]);
+        clus += c_best;
+      }
+    }
+  }
+  if (lane == 0) {
+    if (dist) atomicAdd(&acc->dist, dist);
+    if (clus) atomicAdd(&acc->clus, clus);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_popcount(int64_t words, const unsigned* __restrict__ bm,
+                                                     FeatAcc* acc) {
+  unsigned long long c = 0;
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    c += __popc(bm[w]);
+  c = warp_sum_u(c);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(&acc->ndiag, c);
+}
+
+__device__ double u128_to_double(unsigned long long hi, unsigned long long lo) {
+  return (double)hi * 18446744073709551616.0 + (double)lo;
+}
+
+// One thread: the 15 features from the exact integer sums, fixed formulas.
+__global__ void k_features_final(int64_t n, int64_t ncols, int64_t nnz, const FeatAcc* acc,
+                                 double* f) {
+  const double dn = (double)n, dnnz = (double)nnz;
+  const double mean = dnnz / dn;
+  // population variance = (n * sum r^2 - nnz^2) / n^2, numerator exact in 128 bits
+  const unsigned __int128 a = (unsigned __int128)(unsigned long long)n * acc->sum_r2;
+  const unsigned __int128 b = (unsigned __int128)(unsigned long long)nnz * (unsigned long long)nnz;
+  const unsigned __int128 num = a - b;
+  const double var = u128_to_double((unsigned long long)(num >> 64), (unsigned long long)num) /
+                     (dn * dn);
+  const double sd = sqrt(var);
+  const double mx = (double)acc->maxr, mn = (double)acc->minr, nd = (double)acc->ndiag;
+  f[0] = dn;
+  f[1] = (double)ncols;
+  f[2] = dnnz;
+  f[3] = dnnz / (dn * (double)ncols);
+  f[4] = mean;
+  f[5] = sd;
+  f[6] = mean != 0.0 ? sd / mean : 0.0;
+  f[7] = mx;
+  f[8] = mn;
+  f[9] = mx - mean;
+  f[10] = (double)acc->dist / dn;
+  f[11] = (double)acc->clus / dn;
+  f[12] = nnz > 0 ? dn * mx / dnnz : 0.0;
+  f[13] = nd;
+  f[14] = nnz > 0 ? dn * nd / dnnz : 0.0;
+}
+
+void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15) {
+  if (m->has_features) {
+    std::memcpy(out15, m->features, sizeof(m->features));
+    return;
+  }
+  const int64_t n = m->nrows;
+  const int64_t words = (n + m->ncols - 1 + 31) / 32;
+  void* scratch = nullptr;
+  const size_t bytes = sizeof(FeatAcc) + 15 * sizeof(double) + words * sizeof(unsigned);
+  CP_CUDA(cudaMallocAsync(&scratch, bytes, s));
+  FeatAcc* acc = static_cast<FeatAcc*>(scratch);
+  double* f = reinterpret_cast<double*>(static_cast<char*>(scratch) + sizeof(FeatAcc));
+  unsigned* bm = reinterpret_cast<unsigned*>(f + 15);
+  try {
+    CP_CUDA(cudaMemsetAsync(scratch, 0, bytes, s));
+    CP_CUDA(cudaMemsetAsync(&acc->minr, 0xff, sizeof(unsigned), s));
+    const int g = grid_cap(ctx, n);
+    CP_LAUNCH(ctx, k_features_rows, g, kBlock, 0, s, n, m->rowptr, m->col, bm, acc);
+    CP_LAUNCH(ctx, k_features_long, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, bm, acc);
+    CP_LAUNCH(ctx, k_popcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, acc);
+    CP_LAUNCH(ctx, k_features_final, 1, 1, 0, s, n, m->ncols, m->nnz, acc, f);
+    CP_CUDA(cudaMemcpyAsync(m->features, f, 15 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaFreeAsync(scratch, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    cudaFreeAsync(scratch, s);
+    throw;
+  }
+  m->has_features = true;
+  std::memcpy(out15, m->features, sizeof(m->features));
+}
+
+// ================================================================== scan
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kBlock * kScanItems;
+
+// Exclusive scan of one tile per block; block totals to sums[] (if non-null).
+__global__ void __launch_bounds__(kBlock) k_scan_tile(const int64_t* __restrict__ in,
+                                                      int64_t* __restrict__ out, int64_t n,
+                                                      int64_t* __restrict__ sums) {
+  __shared__ int64_t warp_tot[kBlock / 32];
+  const int64_t base = blockIdx.x * (int64_t)kScanTile + threadIdx.x * kScanItems;
+  int64_t v[kScanItems];
+  int64_t t = 0;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    v[j] = base + j < n ? in[base + j] : 0;
+    t += v[j];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t inc = t;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t up = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += up;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  int64_t woff = 0;
+  for (int w = 0; w < warp; ++w) woff += warp_tot[w];
+  int64_t run = woff + inc - t;
+#pragma unroll
+  for (int j = 0; j < kScanItems; ++j) {
+    if (base + j < n) out[base + j] = run;
+    run += v[j];
+  }
+  if (sums && threadIdx.x == blockDim.x - 1) sums[blockIdx.x] = run;
+}
+
+__global__ void k_scan_add(int64_t* __restrict__ out, int64_t n, const int64_t* __restrict__ offs) {
+  const int64_t i = blockIdx.x * (int64_t)kScanTile;
+  const int64_t off = offs[blockIdx.x];
+  for (int j = threadIdx.x; j < kScanTile && i + j < n; j += blockDim.x) out[i + j] += off;
+}
+
+__global__ void k_scan_total(const int64_t* __restrict__ in, int64_t* __restrict__ out, int64_t n) {
+  out[n] = n > 0 ? out[n - 1] + in[n - 1] : 0;
+}
+
+void exclusive_scan_i64(cp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
+  const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+  if (tiles <= 1) {
+    CP_LAUNCH(ctx, k_scan_tile, 1, kBlock, 0, s, in, out, n, (int64_t*)nullptr);
+  } else {
+    int64_t* sums = nullptr;
+    CP_CUDA(cudaMallocAsync(&sums, sizeof(int64_t) * (2 * tiles + 1), s));
+    int64_t* offs = sums + tiles;
+    CP_LAUNCH(ctx, k_scan_tile, (int)tiles, kBlock, 0, s, in, out, n, sums);
+    exclusive_scan_i64(ctx, sums, offs, tiles, s);
+    CP_LAUNCH(ctx, k_scan_add, (int)tiles, kBlock, 0, s, out, n, offs);
+    CP_CUDA(cudaFreeAsync(sums, s));
+  }
+  CP_LAUNCH(ctx, k_scan_total, 1, 1, 0, s, in, out, n);
+}
+
+// ================================================================== conversions
+__global__ void k_coo_rows(int64_t n, const int32_t* __restrict__ rp, int32_t* __restrict__ row) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) row[k] = (int32_t)i;
+}
+
+// ELL part of width K for rows [0, ld): the first min(len, K) entries of row i.
+__global__ void __launch_bounds__(kBlock) k_ell_fill(int64_t n, int64_t ld, int64_t K,
+                                                     const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci,
+                                                     const double* __restrict__ v,
+                                                     int32_t* __restrict__ ec,
+                                                     double* __restrict__ ev) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ld;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i < n ? rp[i] : 0;
+    const int64_t len = i < n ? rp[i + 1] - s : 0;
+    for (int64_t k = 0; k < K; ++k) {
+      if (k < len) {
+        ec[k * ld + i] = ci[s + k];
+        ev[k * ld + i] = v[s + k];
+      } else {
+        ec[k * ld + i] = -1;
+        ev[k * ld + i] = 0.0;
+      }
+    }
+  }
+}
+
+__global__ void k_hyb_counts(int64_t n, int64_t K, const int32_t* __restrict__ rp,
+                             int64_t* __restrict__ cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t len = rp[i + 1] - rp[i];
+    cnt[i] = len > K ? len - K : 0;
+  }
+}
+
+__global__ void k_hyb_coo_fill(int64_t n, int64_t K, const int32_t* __restrict__ rp,
+                               const int32_t* __restrict__ ci, const double* __restrict__ v,
+                               const int64_t* __restrict__ off, int32_t* __restrict__ cr,
+                               int32_t* __restrict__ cc, double* __restrict__ cv) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = rp[i], e = rp[i + 1];
+    int64_t o = off[i];
+    for (int64_t k = s + K; k < e; ++k, ++o) {
+      cr[o] = (int32_t)i;
+      cc[o] = ci[k];
+      cv[o] = v[k];
+    }
+  }
+}
+
+__global__ void k_iota(int64_t n, int32_t* p) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = (int32_t)i;
+}
+
+// One block per window of sigma rows: bitonic sort of the keys
+// (INT32_MAX - length, position in window) ascending, i.e. longest first with
+// ties in original order.  Keys are padded to the next power of two.
+__global__ void __launch_bounds__(1024) k_sell_sort(int64_t n, int64_t sigma, int pow2,
+                                                    const int32_t* __restrict__ rp,
+                                                    int32_t* __restrict__ perm) {
+  extern __shared__ unsigned long long keys[];
+  const int64_t w0 = blockIdx.x * sigma;
+  const int64_t wn = (w0 + sigma < n ? w0 + sigma : n) - w0;
+  for (int j = threadIdx.x; j < pow2; j += blockDim.x) {
+    if (j < wn) {
+      const int64_t len = rp[w0 + j + 1] - rp[w0 + j];
+      keys[j] = ((unsigned long long)(0x7fffffffLL - len) << 32) | (unsigned)j;
+    } else {
+      keys[j] = ~0ull;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= pow2; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int j = threadIdx.x; j < pow2; j += blockDim.x) {
+        const int p = j ^ stride;
+        if (p > j) {
+          const bool up = (j & size) == 0;
+          const unsigned long long a = keys[j], b = keys[p];
+          if ((a > b) == up) {
+            keys[j] = b;
+            keys[p] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int j = threadIdx.x; j < wn; j += blockDim.x)
+    perm[w0 + j] = (int32_t)(w0 + (keys[j] & 0xffffffffu));
+}
+
+// Warp per chunk: width = longest row in the chunk; count = C * width.
+__global__ void __launch_bounds__(kBlock) k_sell_widths(int64_t n, int64_t nchunks,
+                                                        const int32_t* __restrict__ rp,
+                                                        const int32_t* __restrict__ perm,
+                                                        int32_t* __restrict__ clen,
+                                                        int64_t* __restrict__ cnt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < nchunks; c += nwarps) {
+    const int64_t s = c * 32 + lane;
+    int len = 0;
+    if (s < n) {
+      const int32_t r = perm[s];
+      len = rp[r + 1] - rp[r];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, o));
+    if (lane == 0) {
+      clen[c] = len;
+      cnt[c] = 32ll * len;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_sell_fill(int64_t n, int64_t nchunks,
+                                                      const int32_t* __restrict__ rp,
+                                                      const int32_t* __restrict__ ci,
+                                                      const double* __restrict__ v,
+                                                      const int32_t* __restrict__ perm,
+                                                      const int32_t* __restrict__ clen,
+                                                      const int64_t* __restrict__ cptr,
+                                                      int32_t* __restrict__ sc,
+                                                      double* __restrict__ sv) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t c = warp; c < nchunks; c += nwarps) {
+    const int64_t slot = c * 32 + lane;
+    int64_t s = 0, len = 0;
+    if (slot < n) {
+      const int32_t r = perm[slot];
+      s = rp[r];
+      len = rp[r + 1] - s;
+    }
+    const int64_t base = cptr[c] + lane;
+    const int w = clen[c];
+    for (int k = 0; k < w; ++k) {
+      if (k < len) {
+        sc[base + (int64_t)k * 32] = ci[s + k];
+        sv[base + (int64_t)k * 32] = v[s + k];
+      } else {
+        sc[base + (int64_t)k * 32] = -1;
+        sv[base + (int64_t)k * 32] = 0.0;
+      }
+    }
+  }
+}
+
+__global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+
+// ------------------------------------------------------------------ host side
+void config_check(const cp_config& c) {
+  CP_REQUIRE(c.fmt >= 0 && c.fmt < CP_NUM_FMT, CP_ERR_UNSUPPORTED, "unknown format %d", c.fmt);
+  if (c.fmt == CP_FMT_CSR) {
+    CP_REQUIRE(c.algo >= 0 && c.algo < CP_NUM_ALGO, CP_ERR_UNSUPPORTED, "unknown CSR algorithm %d",
+               c.algo);
+    if (c.algo == CP_ALGO_VECTOR)
+      CP_REQUIRE(c.tpv == 2 || c.tpv == 4 || c.tpv == 8 || c.tpv == 16 || c.tpv == 32,
+                 CP_ERR_UNSUPPORTED, "TpV must be 2, 4, 8, 16 or 32 (got %d)", c.tpv);
+  }
+  if (c.fmt == CP_FMT_SELL) {
+    CP_REQUIRE(c.sell_c == 32, CP_ERR_UNSUPPORTED, "SELL chunk height must be 32 (got %d)",
+               c.sell_c);
+    CP_REQUIRE(c.sell_sigma == 1 || (c.sell_sigma > 0 && c.sell_sigma % 32 == 0 &&
+                                     c.sell_sigma <= 8192),
+               CP_ERR_UNSUPPORTED, "SELL sigma must be 1 or a multiple of 32 up to 8192 (got %d)",
+               c.sell_sigma);
+  }
+  if (c.fmt == CP_FMT_HYB) CP_REQUIRE(c.hyb_k >= 0, CP_ERR_UNSUPPORTED, "HYB K must be >= 0");
+}
+
+bool config_equal(const cp_config& a, const cp_config& b) {
+  if (a.fmt != b.fmt) return false;
+  switch (a.fmt) {
+    case CP_FMT_CSR:
+      return a.algo == b.algo && (a.algo != CP_ALGO_VECTOR || a.tpv == b.tpv);
+    case CP_FMT_SELL:
+      return a.sell_sigma == b.sell_sigma;
+    case CP_FMT_HYB:
+      return a.hyb_k == b.hyb_k;
+    default:
+      return true;
+  }
+}
+
+int64_t hyb_width(const cp_mat* m, const cp_config& c) {
+  if (c.hyb_k > 0) return c.hyb_k;
+  // ceil(mean row length), at least 1
+  const int64_t k = (m->nnz + m->nrows - 1) / m->nrows;
+  return k < 1 ? 1 : k;
+}
+
+static void free_ell(EllPart& e) {
+  dfree(e.col);
+  dfree(e.val);
+  dfree(e.val32);
+  e = EllPart{};
+}
+static void free_coo(CooPart& c) {
+  dfree(c.row);
+  if (c.owns_colval) {
+    dfree(c.col);
+    dfree(c.val);
+  }
+  dfree(c.val32);
+  c = CooPart{};
+}
+static void free_sell(SellPart& s) {
+  dfree(s.perm);
+  dfree(s.chunk_len);
+  dfree(s.chunk_ptr);
+  dfree(s.col);
+  dfree(s.val);
+  dfree(s.val32);
+  s = SellPart{};
+}
+
+void free_formats(cp_mat* m) {
+  free_coo(m->coo);
+  free_ell(m->ell);
+  free_sell(m->sell);
+  free_ell(m->hyb_ell);
+  free_coo(m->hyb_coo);
+  m->has_coo = m->has_ell = m->has_sell = m->has_hyb = false;
+  dfree(m->merge_carry_row);
+  dfree(m->merge_carry_val);
+  m->merge_carry_row = nullptr;
+  m->merge_carry_val = nullptr;
+  m->merge_tiles = 0;
+  dfree(m->val32);
+  m->val32 = nullptr;
+}
+
+static void check_budget(cp_ctx* ctx, int64_t bytes, const char* what) {
+  CP_REQUIRE(bytes <= ctx->format_budget, CP_ERR_FOOTPRINT,
+             "%s needs %lld bytes, above the format budget of %lld bytes", what, (long long)bytes,
+             (long long)ctx->format_budget);
+}
+
+static void convert_ell(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
+  double f[15];
+  compute_features(ctx, m, s, f);
+  EllPart e;
+  e.K = (int64_t)f[7];
+  e.ld = (m->nrows + 31) / 32 * 32;
+  check_budget(ctx, e.K * e.ld * 12, "ELL");
+  try {
+    e.col = dalloc<int32_t>(e.K * e.ld);
+    e.val = dalloc<double>(e.K * e.ld);
+    CP_LAUNCH(ctx, k_ell_fill, grid_cap(ctx, e.ld), kBlock, 0, s, m->nrows, e.ld, e.K, m->rowptr,
+              m->col, m->val, e.col, e.val);
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    free_ell(e);
+    throw;
+  }
+  m->ell = e;
+  m->has_ell = true;
+}
+
+static void convert_coo(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
+  CooPart c;
+  c.n = m->nnz;
+  c.col = m->col;
+  c.val = m->val;
+  c.owns_colval = false;
+  try {
+    c.row = dalloc<int32_t>(m->nnz);
+    CP_LAUNCH(ctx, k_coo_rows, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, m->rowptr, c.row);
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    free_coo(c);
+    throw;
+  }
+  m->coo = c;
+  m->has_coo = true;
+}
+
+static void convert_sell(cp_ctx* ctx, cp_mat* m, int64_t sigma, cudaStream_t s) {
+  SellPart p;
+  p.C = 32;
+  p.sigma = sigma;
+  p.nchunks = (m->nrows + 31) / 32;
+  int64_t* cnt = nullptr;
+  try {
+    p.perm = dalloc<int32_t>(m->nrows);
+    p.chunk_len = dalloc<int32_t>(p.nchunks);
+    p.chunk_ptr = dalloc<int64_t>(p.nchunks + 1);
+    cnt = dalloc<int64_t>(p.nchunks);
+    if (sigma == 1) {
+      CP_LAUNCH(ctx, k_iota, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, p.perm);
+    } else {
+      int pow2 = 1;
+      while (pow2 < sigma) pow2 <<= 1;
+      const int smem = pow2 * (int)sizeof(unsigned long long);
+      CP_CUDA(cudaFuncSetAttribute(k_sell_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      const int64_t windows = (m->nrows + sigma - 1) / sigma;
+      CP_LAUNCH(ctx, k_sell_sort, (int)windows, 1024, smem, s, m->nrows, sigma, pow2, m->rowptr,
+                p.perm);
+    }
+    CP_LAUNCH(ctx, k_sell_widths, grid_cap(ctx, p.nchunks * 32), kBlock, 0, s, m->nrows,
+              p.nchunks, m->rowptr, p.perm, p.chunk_len, cnt);
+    exclusive_scan_i64(ctx, cnt, p.chunk_ptr, p.nchunks, s);
+    CP_CUDA(cudaMemcpyAsync(&p.slots, p.chunk_ptr + p.nchunks, sizeof(int64_t),
+                            cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+    dfree(cnt);
+    cnt = nullptr;
+    check_budget(ctx, p.slots * 12, "SELL-C-sigma");
+    p.col = dalloc<int32_t>(p.slots);
+    p.val = dalloc<double>(p.slots);
+    CP_LAUNCH(ctx, k_sell_fill, grid_cap(ctx, p.nchunks * 32), kBlock, 0, s, m->nrows, p.nchunks,
+              m->rowptr, m->col, m->val, p.perm, p.chunk_len, p.chunk_ptr, p.col, p.val);
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    dfree(cnt);
+    free_sell(p);
+    throw;
+  }
+  free_sell(m->sell);
+  m->sell = p;
+  m->has_sell = true;
+}
+
+static void convert_hyb(cp_ctx* ctx, cp_mat* m, int64_t K, cudaStream_t s) {
+  EllPart e;
+  CooPart c;
+  int64_t* cnt = nullptr;
+  int64_t* off = nullptr;
+  e.K = K;
+  e.ld = (m->nrows + 31) / 32 * 32;
+  check_budget(ctx, e.K * e.ld * 12, "HYB ELL part");
+  try {
+    e.col = dalloc<int32_t>(e.K * e.ld);
+    e.val = dalloc<double>(e.K * e.ld);
+    CP_LAUNCH(ctx, k_ell_fill, grid_cap(ctx, e.ld), kBlock, 0, s, m->nrows, e.ld, e.K, m->rowptr,
+              m->col, m->val, e.col, e.val);
+    cnt = dalloc<int64_t>(m->nrows);
+    off = dalloc<int64_t>(m->nrows + 1);
+    CP_LAUNCH(ctx, k_hyb_counts, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, K, m->rowptr,
+              cnt);
+    exclusive_scan_i64(ctx, cnt, off, m->nrows, s);
+    CP_CUDA(cudaMemcpyAsync(&c.n, off + m->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+    c.owns_colval = true;
+    c.row = dalloc<int32_t>(c.n);
+    c.col = dalloc<int32_t>(c.n);
+    c.val = dalloc<double>(c.n);
+    if (c.n > 0)
+      CP_LAUNCH(ctx, k_hyb_coo_fill, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, K,
+                m->rowptr, m->col, m->val, off, c.row, c.col, c.val);
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    dfree(cnt);
+    dfree(off);
+    free_ell(e);
+    free_coo(c);
+    throw;
+  }
+  dfree(cnt);
+  dfree(off);
+  free_ell(m->hyb_ell);
+  free_coo(m->hyb_coo);
+  m->hyb_ell = e;
+  m->hyb_coo = c;
+  m->has_hyb = true;
+}
+
+static void prepare_merge(cp_ctx* ctx, cp_mat* m) {
+  (void)ctx;
+  const int64_t tiles = (m->nrows + m->nnz + kBlock * 7 - 1) / (kBlock * 7);
+  if (m->merge_tiles == tiles && m->merge_carry_row) return;
+  dfree(m->merge_carry_row);
+  dfree(m->merge_carry_val);
+  m->merge_carry_row = dalloc<int32_t>(tiles);
+  m->merge_carry_val = dalloc<double>(tiles);
+  m->merge_tiles = tiles;
+}
+
+void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s) {
+  config_check(cfg);
+  std::lock_guard<std::mutex> lock(m->mu);
+  switch (cfg.fmt) {
+    case CP_FMT_CSR:
+      if (cfg.algo == CP_ALGO_MERGE) prepare_merge(ctx, m);
+      break;
+    case CP_FMT_COO:
+      if (!m->has_coo) convert_coo(ctx, m, s);
+      break;
+    case CP_FMT_ELL:
+      if (!m->has_ell) convert_ell(ctx, m, s);
+      break;
+    case CP_FMT_SELL:
+      if (!m->has_sell || m->sell.sigma != cfg.sell_sigma) convert_sell(ctx, m, cfg.sell_sigma, s);
+      break;
+    case CP_FMT_HYB: {
+      const int64_t K = hyb_width(m, cfg);
+      if (!m->has_hyb || m->hyb_ell.K != K) convert_hyb(ctx, m, K, s);
+      break;
+    }
+  }
+}
+
+static float* cast_copy(cp_ctx* ctx, const double* src, int64_t n, cudaStream_t s) {
+  float* d = dalloc<float>(n);
+  if (n > 0) CP_LAUNCH(ctx, k_cast_f32, grid_cap(ctx, n), kBlock, 0, s, n, src, d);
+  return d;
+}
+
+void ensure_val32(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s) {
+  std::lock_guard<std::mutex> lock(m->mu);
+  switch (cfg.fmt) {
+    case CP_FMT_CSR:
+    case CP_FMT_COO:
+      if (!m->val32) m->val32 = cast_copy(ctx, m->val, m->nnz, s);
+      break;
+    case CP_FMT_ELL:
+      if (!m->ell.val32) m->ell.val32 = cast_copy(ctx, m->ell.val, m->ell.K * m->ell.ld, s);
+      break;
+    case CP_FMT_SELL:
+      if (!m->sell.val32) m->sell.val32 = cast_copy(ctx, m->sell.val, m->sell.slots, s);
+      break;
+    case CP_FMT_HYB:
+      if (!m->hyb_ell.val32)
+        m->hyb_ell.val32 = cast_copy(ctx, m->hyb_ell.val, m->hyb_ell.K * m->hyb_ell.ld, s);
+      if (!m->hyb_coo.val32) m->hyb_coo.val32 = cast_copy(ctx, m->hyb_coo.val, m->hyb_coo.n, s);
+      break;
+  }
+  CP_CUDA(cudaStreamSynchronize(s));
+}
+
+void format_dims(cp_mat* m, const cp_config& cfg, int64_t dims[4]) {
+  dims[0] = dims[1] = dims[2] = dims[3] = 0;
+  switch (cfg.fmt) {
+    case CP_FMT_ELL:
+      dims[0] = m->ell.K;
+      dims[1] = m->ell.ld;
+      break;
+    case CP_FMT_SELL:
+      dims[0] = m->sell.nchunks;
+      dims[1] = m->sell.slots;
+      dims[2] = m->sell.C;
+      dims[3] = m->sell.sigma;
+      break;
+    case CP_FMT_HYB:
+      dims[0] = m->hyb_ell.K;
+      dims[1] = m->hyb_ell.ld;
+      dims[2] = m->hyb_coo.n;
+      break;
+    case CP_FMT_COO:
+      dims[0] = m->nnz;
+      break;
+    default:
+      break;
+  }
+}
+
+void format_export(cp_mat* m, const cp_config& cfg, int id, void* dst, int64_t cap,
+                   int64_t* bytes, cudaStream_t s) {
+  const void* src = nullptr;
+  int64_t nb = 0;
+  switch (id) {
+    case CP_ARR_COO_ROW: src = m->coo.row; nb = m->nnz * 4; break;
+    case CP_ARR_ELL_COL: src = m->ell.col; nb = m->ell.K * m->ell.ld * 4; break;
+    case CP_ARR_ELL_VAL: src = m->ell.val; nb = m->ell.K * m->ell.ld * 8; break;
+    case CP_ARR_SELL_PERM: src = m->sell.perm; nb = m->nrows * 4; break;
+    case CP_ARR_SELL_CHUNK_LEN: src = m->sell.chunk_len; nb = m->sell.nchunks * 4; break;
+    case CP_ARR_SELL_CHUNK_PTR: src = m->sell.chunk_ptr; nb = (m->sell.nchunks + 1) * 8; break;
+    case CP_ARR_SELL_COL: src = m->sell.col; nb = m->sell.slots * 4; break;
+    case CP_ARR_SELL_VAL: src = m->sell.val; nb = m->sell.slots * 8; break;
+    case CP_ARR_HYB_ELL_COL: src = m->hyb_ell.col; nb = m->hyb_ell.K * m->hyb_ell.ld * 4; break;
+    case CP_ARR_HYB_ELL_VAL: src = m->hyb_ell.val; nb = m->hyb_ell.K * m->hyb_ell.ld * 8; break;
+    case CP_ARR_HYB_COO_ROW: src = m->hyb_coo.row; nb = m->hyb_coo.n * 4; break;
+    case CP_ARR_HYB_COO_COL: src = m->hyb_coo.col; nb = m->hyb_coo.n * 4; break;
+    case CP_ARR_HYB_COO_VAL: src = m->hyb_coo.val; nb = m->hyb_coo.n * 8; break;
+    default: CP_REQUIRE(false, CP_ERR_INVALID, "unknown array id %d", id);
+  }
+  (void)cfg;
+  *bytes = nb;
+  CP_REQUIRE(nb <= cap, CP_ERR_INVALID, "export needs %lld bytes, capacity %lld", (long long)nb,
+             (long long)cap);
+  if (nb > 0) {
+    CP_CUDA(cudaMemcpyAsync(dst, src, nb, cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+  }
+}
+
+}  // namespace cp

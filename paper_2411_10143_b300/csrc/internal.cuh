@@ -1,0 +1,228 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <cstdio>
+#include <mutex>
+#include <string>
+
+#include "cascade.h"
+
+namespace cp {
+
+// ---------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+
+struct Error {
+  cp_status status;
+};
+
+#define CP_CUDA(call)                                                                 \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      ::cp::set_error("%s failed at %s:%d: %s", #call, __FILE__, __LINE__,            \
+                      cudaGetErrorString(e_));                                        \
+      throw ::cp::Error{e_ == cudaErrorMemoryAllocation ? CP_ERR_OOM : CP_ERR_CUDA};  \
+    }                                                                                 \
+  } while (0)
+
+#define CP_REQUIRE(cond, st, ...)   \
+  do {                              \
+    if (!(cond)) {                  \
+      ::cp::set_error(__VA_ARGS__); \
+      throw ::cp::Error{st};        \
+    }                               \
+  } while (0)
+
+// Every kernel launch goes through this, so the context counts launches and a
+// bad launch configuration is reported at once.
+#define CP_LAUNCH(ctx, kernel, grid, block, smem, stream, ...)  \
+  do {                                                          \
+    kernel<<<(grid), (block), (smem), (stream)>>>(__VA_ARGS__);  \
+    (ctx)->launches.fetch_add(1, std::memory_order_relaxed);    \
+    CP_CUDA(cudaGetLastError());                                \
+  } while (0)
+
+// ---------------------------------------------------------------- device memory
+template <typename T>
+T* dalloc(size_t count) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  CP_CUDA(cudaMalloc(&p, count * sizeof(T)));
+  return static_cast<T*>(p);
+}
+inline void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+constexpr int kBlock = 256;         // threads per block of the streaming kernels
+constexpr int kMaxPartials = 4096;  // capacity of one block-partials buffer
+
+struct ModelSlot {
+  bool loaded = false;
+  int h1 = 0, h2 = 0, k = 0;
+  float* d_params = nullptr;  // device, flat layout of cascade.h
+  float* d_mu = nullptr;      // device [15]
+  float* d_sd = nullptr;      // device [15]
+};
+
+struct EllPart {
+  int64_t K = 0, ld = 0;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+};
+struct CooPart {
+  int64_t n = 0;
+  int32_t* row = nullptr;
+  int32_t* col = nullptr;  // aliases the CSR array for plain COO (owns_colval false)
+  double* val = nullptr;
+  float* val32 = nullptr;
+  bool owns_colval = false;
+};
+struct SellPart {
+  int64_t C = 0, sigma = 0, nchunks = 0, slots = 0;
+  int32_t* perm = nullptr;
+  int32_t* chunk_len = nullptr;
+  int64_t* chunk_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;
+};
+
+}  // namespace cp
+
+struct cp_ctx {
+  int device = 0;
+  int num_sms = 0;
+  cudaStream_t main = nullptr, side = nullptr;
+  bool own_main = false, own_side = false;
+  std::atomic<int64_t> launches{0};
+  int64_t format_budget = int64_t(4) << 30;
+  int grid_stream = 0;  // resident blocks of kBlock threads for streaming kernels
+  cp::ModelSlot models[CP_NUM_STAGES];
+  std::mutex model_mu;
+};
+
+struct cp_mat {
+  cp_ctx* ctx = nullptr;
+  int64_t nrows = 0, ncols = 0, nnz = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  float* val32 = nullptr;  // FP32 copy of val, made on first FP32 use
+  bool has_coo = false, has_ell = false, has_sell = false, has_hyb = false;
+  cp::CooPart coo;
+  cp::EllPart ell;
+  cp::SellPart sell;
+  cp::EllPart hyb_ell;
+  cp::CooPart hyb_coo;
+  bool has_features = false;
+  double features[15] = {0};
+  // merge-path scratch: one carry (row, value) per tile
+  int32_t* merge_carry_row = nullptr;
+  double* merge_carry_val = nullptr;
+  int64_t merge_tiles = 0;
+  std::mutex mu;  // serialises conversions issued by the side thread and the caller
+};
+
+namespace cp {
+
+// ---------------------------------------------------------------- library-internal API
+void csr_validate(cp_ctx* ctx, cp_mat* m);
+void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15);
+void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s);
+void ensure_val32(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s);
+void format_dims(cp_mat* m, const cp_config& cfg, int64_t dims[4]);
+void format_export(cp_mat* m, const cp_config& cfg, int array_id, void* dst, int64_t cap,
+                   int64_t* bytes, cudaStream_t s);
+void free_formats(cp_mat* m);
+void config_check(const cp_config& c);  // throws CP_ERR_UNSUPPORTED
+bool config_equal(const cp_config& a, const cp_config& b);
+int64_t hyb_width(const cp_mat* m, const cp_config& c);
+
+// SpMV for the solvers: y = A x and, when dotv is non-null, block partial sums
+// of y .* dotv written to partials[0..P); returns P (0 without dotv).
+// The format of cfg must have been converted (and, for T = float, its FP32
+// values made).  T is double or float.
+// skip: device flag (may be null); when it is set the kernels return at once.
+template <typename T>
+int spmv_solver(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, const T* x, T* y, const T* dotv,
+                double* partials, const int* skip, cudaStream_t s);
+// Block partial sums of a .* b (one per block of the resident grid); returns P.
+template <typename T>
+int dot_partials(cp_ctx* ctx, int64_t n, const T* a, const T* b, double* partials,
+                 const int* skip, cudaStream_t s);
+// General y = alpha A x + beta y.
+template <typename T>
+void spmv_general(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, const T* x, T beta,
+                  T* y, cudaStream_t s);
+
+// Exclusive scan of int64 counts in[0..n) into out[0..n] (out[n] = total).
+void exclusive_scan_i64(cp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
+
+}  // namespace cp
+
+#include <vector>
+
+namespace cp {
+
+// Hand-off from the prediction side (feature extraction, cascade stages and
+// conversions on the side stream, driven by a host thread) to the solve loop.
+// A configuration is published only after the conversion it needs has
+// completed on the side stream, so the solve loop may use it at once.
+struct Channel {
+  std::mutex mu;
+  std::vector<std::pair<int, cp_config>> published;  // (stage, configuration) in order
+  std::atomic<int> count{0};
+  std::atomic<bool> cancel{false};
+  bool need_fp32 = false;  // the solve also needs FP32 values of every published format
+  float t_features_ms = 0.f, t_predict_ms[3] = {0.f, 0.f, 0.f}, t_convert_ms = 0.f;
+  cp_status status = CP_OK;  // first error of the side thread, if any
+  std::string error;
+
+  void publish(int stage, const cp_config& c) {
+    std::lock_guard<std::mutex> lock(mu);
+    published.emplace_back(stage, c);
+    count.store((int)published.size(), std::memory_order_release);
+  }
+};
+
+// The cascaded prediction of Sec. III-C-1 (Fig. 5) with its conversions, on
+// stream s; publishes into ch after every stage that changes the
+// configuration.  Runs until done or ch->cancel is set.
+void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch);
+// One cascade stage's classifier on the features: returns the arg-max class,
+// or -1 when the stage has no model.
+int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s);
+
+// ---------------------------------------------------------------- predictor MLP
+struct MlpDims {
+  int d, h1, h2, k;
+  __host__ __device__ int64_t nparams() const {
+    return (int64_t)h1 * d + h1 + (int64_t)h2 * h1 + h2 + (int64_t)k * h2 + k;
+  }
+};
+void mlp_forward(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const float* X, float* Z,
+                 float* scratch, cudaStream_t s);
+void mlp_loss_grad(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const float* X,
+                   const int32_t* lab, float* loss, float* grad, float* scratch, cudaStream_t s);
+void adam_step(cp_ctx* ctx, int64_t np, float* P, const float* G, float* m, float* v, int t,
+               float lr, float b1, float b2, float eps, cudaStream_t s);
+void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* params,
+                   const float* mu, const float* sd, cudaStream_t s);
+void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host,
+                 const int32_t* lab_host, int h1, int h2, int k, int epochs, float lr,
+                 uint64_t seed, float* final_loss);
+int64_t scratch_floats_api(int64_t N, int d, int h1, int h2, int k);
+
+// The solve entry (CG or GMRES; FP64 or FP32-inner refinement; plain,
+// sequential or asynchronous prediction).
+void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_opts* o,
+           cp_solve_info* info, bool gmres);
+
+}  // namespace cp

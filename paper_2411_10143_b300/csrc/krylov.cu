@@ -1,0 +1,924 @@
+// Krylov solvers around the SpMV family: CG (Hestenes-Stiefel) and restarted
+// GMRES(m), in FP64 or as FP32 inner solves inside FP64 iterative refinement,
+// with the paper's asynchronous execution (Sec. III-C-2): the solve starts at
+// once on the default kernel while the side thread extracts features, runs the
+// cascade and converts the format on the side stream; the loop adopts each
+// published configuration at the next iteration boundary (Table VII records
+// where), and cancels the side work if it converges first.
+//
+// Scalars (alpha, beta, residual norms, Givens rotations) live in device
+// memory and every reduction is a fixed-order sum of per-block partials, so the
+// host never waits on the GPU inside an iteration: it runs at most
+// check_every iterations ahead and reads a host-mapped mirror of the state.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace cp {
+
+constexpr int kMaxRestart = 64;
+
+// ================================================================== device state
+struct CgState {
+  double rr[2];  // (r, r) of the current iteration, by parity
+  double pap, alpha, beta, bb, relres;
+  int done;      // recursive residual reached tol (or breakdown): stop
+  int status;    // CP_OK / CP_ERR_BREAKDOWN
+  int iters;     // completed iterations
+};
+
+struct GmState {
+  double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
+  double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
+  double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+  double bb, beta, inv;  // ||b||^2, cycle start ||r||, 1 / current norm
+  int done;              // converged (true residual of a cycle start)
+  int halt;              // no further steps in this cycle
+  int conv_est;          // the cycle's residual estimate reached tol
+  int jdone;             // steps completed in this cycle
+  int status;
+  int iters;             // steps completed in total
+};
+
+// Host-mapped mirror written by the kernels that finish an iteration.
+struct Mirror {
+  volatile double res;  // latest residual norm (recursive / estimated / true)
+  volatile int done, halt, status, iters, jdone, conv_est;
+};
+
+// ================================================================== CG kernels
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_init(int64_t n, const T* __restrict__ b,
+                                                    const T* __restrict__ ax, T* __restrict__ r,
+                                                    T* __restrict__ p, double* __restrict__ pr,
+                                                    double* __restrict__ pb) {
+  T rr = 0, bb = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T bi = b[i];
+    const T ri = ax ? bi - ax[i] : bi;
+    r[i] = ri;
+    p[i] = ri;
+    rr = fma(ri, ri, rr);
+    bb = fma(bi, bi, bb);
+  }
+  __shared__ double red[33];
+  const double s1 = block_sum((double)rr, red);
+  if (threadIdx.x == 0) pr[blockIdx.x] = s1;
+  const double s2 = block_sum((double)bb, red);
+  if (threadIdx.x == 0) pb[blockIdx.x] = s2;
+}
+
+// One block: (r, r) and ||b||^2 into the state; converged already?
+__global__ void k_cg_init_final(const double* __restrict__ pr, const double* __restrict__ pb,
+                                int P, CgState* st, int slot, double tol2, Mirror* mir,
+                                int keep_bb) {
+  __shared__ double red[40];
+  const double rr = reduce_partials(pr, P, red);
+  const double bb = keep_bb ? st->bb : reduce_partials(pb, P, red);
+  if (threadIdx.x == 0) {
+    st->rr[slot] = rr;
+    st->bb = bb;
+    const int done = (bb == 0.0 || rr <= tol2 * bb) ? 1 : 0;
+    st->done = done;
+    st->status = CP_OK;
+    mir->res = sqrt(rr);
+    mir->done = done;
+    mir->status = CP_OK;
+    mir->iters = st->iters;
+  }
+}
+
+// alpha = (r,r)/(Ap,p); x += alpha p; r -= alpha Ap; partials of (r,r).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, T* __restrict__ x,
+                                                      T* __restrict__ r, const T* __restrict__ p,
+                                                      const T* __restrict__ ap,
+                                                      const double* __restrict__ pa, int PA,
+                                                      CgState* st, int slot,
+                                                      double* __restrict__ pb, Mirror* mir) {
+  if (*(volatile int*)&st->done) return;
+  __shared__ double red[40];
+  const double pap = reduce_partials(pa, PA, red);
+  const double rr = st->rr[slot];
+  if (!(pap > 0.0) || !isfinite(pap)) {  // A not SPD, or overflow / NaN
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->status = CP_ERR_BREAKDOWN;
+      st->done = 1;
+      mir->status = CP_ERR_BREAKDOWN;
+      mir->done = 1;
+    }
+    return;
+  }
+  const double alpha_d = rr / pap;
+  const T alpha = (T)alpha_d;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->pap = pap;
+    st->alpha = alpha_d;
+  }
+  T acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    T pv[4], av[4], xv[4], rv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      pv[u] = p[i + u * stride];
+      av[u] = ap[i + u * stride];
+      xv[u] = x[i + u * stride];
+      rv[u] = r[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      x[i + u * stride] = fma(alpha, pv[u], xv[u]);
+      const T rn = fma(-alpha, av[u], rv[u]);
+      r[i + u * stride] = rn;
+      acc = fma(rn, rn, acc);
+    }
+  }
+  for (; i < n; i += stride) {
+    x[i] = fma(alpha, p[i], x[i]);
+    const T rn = fma(-alpha, ap[i], r[i]);
+    r[i] = rn;
+    acc = fma(rn, rn, acc);
+  }
+  const double s = block_sum((double)acc, red);
+  if (threadIdx.x == 0) pb[blockIdx.x] = s;
+}
+
+// beta = (r+,r+)/(r,r); p = r + beta p, unless converged.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_direction(int64_t n, const T* __restrict__ r,
+                                                         T* __restrict__ p,
+                                                         const double* __restrict__ pb, int PB,
+                                                         CgState* st, int slot, double tol2,
+                                                         Mirror* mir) {
+  if (*(volatile int*)&st->done) return;
+  __shared__ double red[40];
+  const double rr_new = reduce_partials(pb, PB, red);
+  const double rr = st->rr[slot];
+  const bool bad = !isfinite(rr_new);
+  const bool conv = rr_new <= tol2 * st->bb;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->rr[slot ^ 1] = rr_new;
+    st->iters += 1;
+    mir->res = sqrt(rr_new);
+    mir->iters = st->iters;
+    if (bad) {
+      st->status = CP_ERR_BREAKDOWN;
+      mir->status = CP_ERR_BREAKDOWN;
+    }
+    if (conv || bad) {
+      st->done = 1;
+      mir->done = 1;
+    }
+  }
+  if (conv || bad) return;
+  const T beta = (T)(rr_new / rr);
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->beta = rr_new / rr;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {
+    T rv[4], pv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rv[u] = r[i + u * stride];
+      pv[u] = p[i + u * stride];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) p[i + u * stride] = fma(beta, pv[u], rv[u]);
+  }
+  for (; i < n; i += stride) p[i] = fma(beta, p[i], r[i]);
+}
+
+// ================================================================== shared small kernels
+// partials of ||b - y||^2 and, if out is non-null, out = b - y
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_resid(int64_t n, const T* __restrict__ b,
+                                                  const T* __restrict__ y, T* __restrict__ out,
+                                                  double* __restrict__ part, const int* skip) {
+  if (skip && *skip) return;
+  T acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T d = b[i] - y[i];
+    if (out) out[i] = d;
+    acc = fma(d, d, acc);
+  }
+  __shared__ double red[33];
+  const double s = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_to(const double* __restrict__ part, int P, double* out) {
+  __shared__ double red[40];
+  const double s = reduce_partials(part, P, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+template <typename A, typename B>
+__global__ void k_cast(int64_t n, const A* __restrict__ a, B* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (B)a[i];
+}
+template <>
+__global__ void k_cast<double, float>(int64_t n, const double* __restrict__ a,
+                                      float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = __double2float_rn(a[i]);
+}
+
+// x += (double) d
+__global__ void k_add_f32(int64_t n, double* __restrict__ x, const float* __restrict__ d) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    x[i] += (double)d[i];
+}
+
+// ================================================================== GMRES kernels
+// Multi-dot of w with columns V[0..nc): partials[c * P + block]; columns in
+// groups of 8 so each thread keeps 8 accumulators.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gm_dots(int64_t n, const T* __restrict__ V,
+                                                    int64_t ldv, int nc, const T* __restrict__ w,
+                                                    double* __restrict__ part, GmState* st) {
+  if (*(volatile int*)&st->halt) return;
+  __shared__ double red[8 * 32];
+  const int P = gridDim.x;
+  for (int c0 = 0; c0 < nc; c0 += 8) {
+    T acc[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) acc[g] = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const T wi = w[i];
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (c0 + g < nc) acc[g] = fma(V[(int64_t)(c0 + g) * ldv + i], wi, acc[g]);
+    }
+    double accd[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) accd[g] = (double)acc[g];
+    block_sum_multi<8>(accd, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int g = 0; g < 8; ++g)
+        if (c0 + g < nc) part[(int64_t)(c0 + g) * P + blockIdx.x] = accd[g];
+    }
+    __syncthreads();
+  }
+}
+
+// nc blocks: out[c] = sum of column c's partials (fixed order)
+__global__ void k_gm_reduce(const double* __restrict__ part, int P, double* out, GmState* st) {
+  if (*(volatile int*)&st->halt) return;
+  __shared__ double red[40];
+  const double s = reduce_partials(part + (int64_t)blockIdx.x * P, P, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// w -= V[:, 0..nc) h; partials of ||w||^2
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gm_sub(int64_t n, const T* __restrict__ V,
+                                                   int64_t ldv, int nc, T* __restrict__ w,
+                                                   const double* __restrict__ h,
+                                                   double* __restrict__ part, GmState* st) {
+  if (*(volatile int*)&st->halt) return;
+  __shared__ T hs[kMaxRestart + 1];
+  for (int c = threadIdx.x; c < nc; c += blockDim.x) hs[c] = (T)h[c];
+  __syncthreads();
+  T acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T wi = w[i];
+    for (int c = 0; c < nc; ++c) wi = fma(-hs[c], V[(int64_t)c * ldv + i], wi);
+    w[i] = wi;
+    acc = fma(wi, wi, acc);
+  }
+  __shared__ double red[33];
+  const double s = block_sum((double)acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// One thread: column j of H from h1 + h2 and ||w||, previous rotations, the new
+// rotation, the residual estimate; decides whether the cycle goes on.
+__global__ void k_gm_givens(const double* __restrict__ part, int P, GmState* st, int j, int m,
+                            double tol2, Mirror* mir) {
+  if (*(volatile int*)&st->halt) return;
+  __shared__ double red[40];
+  const double hn2 = reduce_partials(part, P, red);
+  if (threadIdx.x != 0) return;
+  const double hn = sqrt(hn2);
+  double* H = st->H;
+  for (int i = 0; i <= j; ++i) H[i * kMaxRestart + j] = st->h1[i] + st->h2[i];
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * kMaxRestart + j], b = H[(i + 1) * kMaxRestart + j];
+    H[i * kMaxRestart + j] = st->cs[i] * a + st->sn[i] * b;
+    H[(i + 1) * kMaxRestart + j] = -st->sn[i] * a + st->cs[i] * b;
+  }
+  const double a = H[j * kMaxRestart + j];
+  const double den = sqrt(a * a + hn2);
+  const double c = den == 0.0 ? 1.0 : a / den;
+  const double s = den == 0.0 ? 0.0 : hn / den;
+  st->cs[j] = c;
+  st->sn[j] = s;
+  H[j * kMaxRestart + j] = c * a + s * hn;
+  st->g[j + 1] = -s * st->g[j];
+  st->g[j] = c * st->g[j];
+  st->jdone = j + 1;
+  st->iters += 1;
+  const double est2 = st->g[j + 1] * st->g[j + 1];
+  const bool bad = !isfinite(est2) || !isfinite(hn);
+  const bool conv = est2 <= tol2 * st->bb;
+  st->conv_est = conv ? 1 : 0;
+  st->inv = hn > 0.0 ? 1.0 / hn : 0.0;
+  if (bad) st->status = CP_ERR_BREAKDOWN;
+  if (conv || hn == 0.0 || bad || j + 1 == m) st->halt = 1;
+  mir->res = fabs(st->g[j + 1]);
+  mir->iters = st->iters;
+  mir->jdone = st->jdone;
+  mir->halt = st->halt;
+  mir->conv_est = st->conv_est;
+  mir->status = st->status;
+}
+
+// w *= inv (normalisation of the new basis vector); runs unless halted.
+template <typename T>
+__global__ void k_gm_scale(int64_t n, T* __restrict__ w, GmState* st, int check_halt) {
+  if (check_halt && *(volatile int*)&st->halt) return;
+  if (*(volatile int*)&st->done) return;
+  const T inv = (T)st->inv;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    w[i] *= inv;
+}
+
+// One thread: cycle start from ||r0||^2 partials (r0 = b - A x already in V0).
+__global__ void k_gm_start(const double* __restrict__ part, int P, GmState* st, double tol2,
+                           Mirror* mir, int first) {
+  if (*(volatile int*)&st->done) return;
+  __shared__ double red[40];
+  const double rr = reduce_partials(part, P, red);
+  if (threadIdx.x != 0) return;
+  if (first) st->bb = st->h1[0];  // ||b||^2 staged by the host loop in h1[0]
+  const double beta = sqrt(rr);
+  st->beta = beta;
+  st->jdone = 0;
+  st->conv_est = 0;
+  for (int i = 0; i <= kMaxRestart; ++i) st->g[i] = 0.0;
+  st->g[0] = beta;
+  st->inv = beta > 0.0 ? 1.0 / beta : 0.0;
+  const bool conv = st->bb == 0.0 || rr <= tol2 * st->bb;
+  if (!isfinite(rr)) st->status = CP_ERR_BREAKDOWN;
+  st->done = (conv || !isfinite(rr)) ? 1 : 0;
+  st->halt = st->done;
+  mir->res = beta;
+  mir->done = st->done;
+  mir->halt = st->halt;
+  mir->jdone = 0;
+  mir->conv_est = 0;
+  mir->status = st->status;
+  mir->iters = st->iters;
+}
+
+// One thread: y = R^{-1} g over the cycle's jdone steps.
+__global__ void k_gm_backsub(GmState* st) {
+  if (*(volatile int*)&st->done) return;
+  const int jd = st->jdone;
+  for (int i = jd - 1; i >= 0; --i) {
+    double s = st->g[i];
+    for (int k = i + 1; k < jd; ++k) s -= st->H[i * kMaxRestart + k] * st->y[k];
+    st->y[i] = s / st->H[i * kMaxRestart + i];
+  }
+}
+
+// x += V[:, 0..jdone) y
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gm_update_x(int64_t n, const T* __restrict__ V,
+                                                        int64_t ldv, T* __restrict__ x,
+                                                        GmState* st) {
+  if (*(volatile int*)&st->done) return;
+  __shared__ T ys[kMaxRestart];
+  const int jd = st->jdone;
+  for (int c = threadIdx.x; c < jd; c += blockDim.x) ys[c] = (T)st->y[c];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    T xi = x[i];
+    for (int c = 0; c < jd; ++c) xi = fma(ys[c], V[(int64_t)c * ldv + i], xi);
+    x[i] = xi;
+  }
+}
+
+// ================================================================== host side
+using Clock = std::chrono::steady_clock;
+static double ms_since(Clock::time_point t0) {
+  return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+static int grid_n(cp_ctx* ctx, int64_t n) {
+  int64_t g = (n + kBlock - 1) / kBlock;
+  if (g > ctx->grid_stream) g = ctx->grid_stream;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <typename T>
+struct CgBufs {
+  T *r = nullptr, *p = nullptr, *ap = nullptr;
+  double *pa = nullptr, *pb = nullptr, *pc = nullptr;
+  CgState* st = nullptr;
+};
+template <typename T>
+struct GmBufs {
+  T *V = nullptr, *tmp = nullptr;
+  double *part = nullptr, *pn = nullptr;
+  GmState* st = nullptr;
+  int mrest = 0;
+};
+
+// Device and host-mapped work areas of one solve (buffers are made once and
+// reused by every inner solve of an iterative refinement).
+struct Workspace {
+  cp_ctx* ctx;
+  std::vector<void*> dev;
+  Mirror* mir = nullptr;  // host pointer
+  Mirror* mir_d = nullptr;
+  std::vector<cudaEvent_t> ring;
+  CgBufs<double> cg64;
+  CgBufs<float> cg32;
+  GmBufs<double> gm64;
+  GmBufs<float> gm32;
+  explicit Workspace(cp_ctx* c) : ctx(c) {}
+  template <typename T>
+  CgBufs<T>& cgset();
+  template <typename T>
+  GmBufs<T>& gmset();
+  template <typename T>
+  CgBufs<T>& cg(int64_t n) {
+    CgBufs<T>& B = cgset<T>();
+    if (!B.r) {
+      B.r = get<T>(n);
+      B.p = get<T>(n);
+      B.ap = get<T>(n);
+      B.pa = get<double>(kMaxPartials);
+      B.pb = get<double>(kMaxPartials);
+      B.pc = get<double>(kMaxPartials);
+      B.st = get<CgState>(1);
+    }
+    return B;
+  }
+  template <typename T>
+  GmBufs<T>& gm(int64_t n, int64_t ldv, int mrest) {
+    GmBufs<T>& B = gmset<T>();
+    if (!B.V) {
+      B.V = get<T>(ldv * (mrest + 1));
+      B.tmp = get<T>(n);
+      B.part = get<double>((int64_t)kMaxPartials * (kMaxRestart + 2));
+      B.pn = get<double>(kMaxPartials);
+      B.st = get<GmState>(1);
+      B.mrest = mrest;
+    }
+    return B;
+  }
+  template <typename U>
+  U* get(size_t count) {
+    U* p = dalloc<U>(count);
+    dev.push_back(p);
+    return p;
+  }
+  Mirror* mirror() {
+    if (!mir) {
+      CP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&mir), sizeof(Mirror), cudaHostAllocMapped));
+      std::memset((void*)mir, 0, sizeof(Mirror));
+      CP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&mir_d), mir, 0));
+    }
+    return mir_d;
+  }
+  cudaEvent_t event(int i, int depth) {
+    while ((int)ring.size() < depth) {
+      cudaEvent_t e;
+      CP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      ring.push_back(e);
+    }
+    return ring[i % depth];
+  }
+  ~Workspace() {
+    for (void* p : dev) cudaFree(p);
+    for (auto e : ring) cudaEventDestroy(e);
+    if (mir) cudaFreeHost((void*)mir);
+  }
+};
+
+template <>
+CgBufs<double>& Workspace::cgset<double>() { return cg64; }
+template <>
+CgBufs<float>& Workspace::cgset<float>() { return cg32; }
+template <>
+GmBufs<double>& Workspace::gmset<double>() { return gm64; }
+template <>
+GmBufs<float>& Workspace::gmset<float>() { return gm32; }
+
+// The configuration in force, fed by the cascade channel.
+struct ConfigSource {
+  cp_ctx* ctx;
+  cp_mat* m;
+  cp_config cur;
+  Channel* ch = nullptr;  // null: fixed configuration
+  int applied = 0;
+  int switch_iter[3] = {-1, -1, -1};
+  bool fp32 = false;
+  // profiling of SpMV launches
+  bool profile = false;
+  std::vector<cudaEvent_t> ev;
+  int n_spmv = 0;
+
+  void poll(int iter) {
+    if (!ch) return;
+    const int c = ch->count.load(std::memory_order_acquire);
+    if (c <= applied) return;
+    std::lock_guard<std::mutex> lock(ch->mu);
+    for (int k = applied; k < c; ++k) {
+      const int stage = ch->published[k].first;
+      cur = ch->published[k].second;
+      if (stage >= 0 && stage < 3 && switch_iter[stage] < 0) switch_iter[stage] = iter;
+    }
+    applied = c;
+  }
+  void before_spmv(cudaStream_t s) {
+    if (!profile) return;
+    cudaEvent_t a, b;
+    CP_CUDA(cudaEventCreate(&a));
+    CP_CUDA(cudaEventCreate(&b));
+    ev.push_back(a);
+    ev.push_back(b);
+    CP_CUDA(cudaEventRecord(a, s));
+  }
+  void after_spmv(cudaStream_t s) {
+    if (!profile) return;
+    CP_CUDA(cudaEventRecord(ev.back(), s));
+    ++n_spmv;
+  }
+  float spmv_ms() {
+    float tot = 0.f;
+    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) tot += t;
+    }
+    return tot;
+  }
+  ~ConfigSource() {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+// SpMV of the configuration in force (T selects FP64 or FP32 values).
+template <typename T>
+static int spmv_cur(ConfigSource& cs, const T* x, T* y, const T* dotv, double* part,
+                    const int* skip, cudaStream_t s) {
+  cs.before_spmv(s);
+  const int P = spmv_solver<T>(cs.ctx, cs.m, cs.cur, x, y, dotv, part, skip, s);
+  cs.after_spmv(s);
+  return P;
+}
+
+struct LoopResult {
+  int iters = 0;
+  int status = CP_OK;
+  double res = 0.0;  // last residual norm reported by the device
+};
+
+// ------------------------------------------------------------------ CG
+// Solves A x = b in precision T from x (x0, or zero when x0_zero).  Stops at
+// the recursive residual ||r|| <= tol ||b||; with true_check the FP64 true
+// residual is then recomputed and the iteration restarted from x if it is not
+// yet below tol (the FP32 inner solves skip that check).
+template <typename T>
+static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* b, T* x,
+                         bool x0_zero, double tol, int maxit, int depth, bool true_check,
+                         double* relres_true) {
+  cp_mat* m = cs.m;
+  const int64_t n = m->nrows;
+  cudaStream_t s = ctx->main;
+  auto& B = ws.cg<T>(n);
+  T *r = B.r, *p = B.p, *ap = B.ap;
+  double *pa = B.pa, *pb = B.pb, *pc = B.pc;
+  CgState* st = B.st;
+  Mirror* mir = ws.mirror();
+  CP_CUDA(cudaMemsetAsync(st, 0, sizeof(CgState), s));
+  const double tol2 = tol * tol;
+  const int G = grid_n(ctx, n);
+  const int* done = &st->done;
+  LoopResult res;
+  int it = 0;
+  bool keep_bb = false;
+  for (;;) {
+    // (re)start: r = b - A x, p = r
+    if (!x0_zero || keep_bb) spmv_cur<T>(cs, x, ap, nullptr, nullptr, nullptr, s);
+    CP_LAUNCH(ctx, k_cg_init<T>, G, kBlock, 0, s, n, b, (x0_zero && !keep_bb) ? nullptr : ap, r, p,
+              pc, pb);
+    CP_LAUNCH(ctx, k_cg_init_final, 1, kBlock, 0, s, pc, pb, G, st, it & 1, tol2, mir,
+              keep_bb ? 1 : 0);
+    keep_bb = true;
+    int issued = 0;
+    for (; it < maxit; ++it) {
+      cs.poll(it);
+      const int PA = spmv_cur<T>(cs, p, ap, p, pa, done, s);
+      CP_LAUNCH(ctx, k_cg_update<T>, G, kBlock, 0, s, n, x, r, p, ap, pa, PA, st, it & 1, pb,
+                mir);
+      CP_LAUNCH(ctx, k_cg_direction<T>, G, kBlock, 0, s, n, r, p, pb, G, st, it & 1, tol2, mir);
+      CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
+      ++issued;
+      if (issued >= depth) {
+        CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
+        if (ws.mir->done) break;
+      }
+    }
+    CP_CUDA(cudaStreamSynchronize(s));
+    res.iters = ws.mir->iters;
+    res.status = ws.mir->status;
+    res.res = ws.mir->res;
+    it = res.iters;
+    if (res.status != CP_OK) break;
+    if (!true_check) {
+      if (!ws.mir->done) res.status = CP_ERR_NOT_CONVERGED;
+      break;
+    }
+    // FP64 true residual b - A x
+    spmv_cur<T>(cs, x, ap, nullptr, nullptr, nullptr, s);
+    CP_LAUNCH(ctx, k_resid<T>, G, kBlock, 0, s, n, b, ap, (T*)nullptr, pc, (const int*)nullptr);
+    double* d_rt = reinterpret_cast<double*>(pa);
+    CP_LAUNCH(ctx, k_sum_to, 1, kBlock, 0, s, pc, G, d_rt);
+    double rt2 = 0.0, bb = 0.0;
+    CP_CUDA(cudaMemcpyAsync(&rt2, d_rt, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(&bb, &st->bb, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+    const double rel = bb > 0.0 ? std::sqrt(rt2 / bb) : 0.0;
+    if (relres_true) *relres_true = rel;
+    if (rel <= tol) break;
+    if (it >= maxit) {
+      res.status = CP_ERR_NOT_CONVERGED;
+      break;
+    }
+    x0_zero = false;  // restart from the current x
+  }
+  return res;
+}
+
+// ------------------------------------------------------------------ GMRES
+template <typename T>
+static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* b, T* x,
+                            bool x0_zero, double tol, int mrest, int maxit, int depth,
+                            bool true_check, double* relres_true) {
+  cp_mat* m = cs.m;
+  const int64_t n = m->nrows;
+  cudaStream_t s = ctx->main;
+  const int64_t ldv = (n + 31) / 32 * 32;
+  auto& B = ws.gm<T>(n, ldv, mrest);
+  T *V = B.V, *tmp = B.tmp;
+  double *part = B.part, *pn = B.pn;
+  GmState* st = B.st;
+  Mirror* mir = ws.mirror();
+  CP_CUDA(cudaMemsetAsync(st, 0, sizeof(GmState), s));
+  const double tol2 = tol * tol;
+  const int G = grid_n(ctx, n);
+  // ||b||^2 into h1[0] for the first cycle start
+  {
+    const int P = dot_partials<T>(ctx, n, b, b, pn, nullptr, s);
+    CP_LAUNCH(ctx, k_sum_to, 1, kBlock, 0, s, pn, P, &st->h1[0]);
+  }
+  LoopResult res;
+  int first = 1;
+  for (;;) {
+    // cycle start: V0 = b - A x, beta = ||V0||, V0 /= beta
+    int P0 = G;
+    if (x0_zero && first) {
+      CP_CUDA(cudaMemcpyAsync(V, b, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      P0 = dot_partials<T>(ctx, n, b, b, pn, nullptr, s);
+    } else {
+      spmv_cur<T>(cs, x, tmp, nullptr, nullptr, &st->done, s);
+      CP_LAUNCH(ctx, k_resid<T>, G, kBlock, 0, s, n, b, tmp, V, pn, &st->done);
+    }
+    CP_LAUNCH(ctx, k_gm_start, 1, kBlock, 0, s, pn, P0, st, tol2, mir, first);
+    CP_LAUNCH(ctx, k_gm_scale<T>, G, kBlock, 0, s, n, V, st, 1);
+    first = 0;
+    CP_CUDA(cudaStreamSynchronize(s));
+    res.iters = ws.mir->iters;
+    res.status = ws.mir->status;
+    res.res = ws.mir->res;
+    if (ws.mir->done || res.status != CP_OK) break;
+    if (res.iters >= maxit) {
+      res.status = CP_ERR_NOT_CONVERGED;
+      break;
+    }
+    const int steps = std::min(mrest, maxit - res.iters);
+    int issued = 0;
+    for (int j = 0; j < steps; ++j) {
+      cs.poll(res.iters + j);
+      T* vj = V + (int64_t)j * ldv;
+      T* w = V + (int64_t)(j + 1) * ldv;
+      spmv_cur<T>(cs, vj, w, nullptr, nullptr, &st->halt, s);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        double* h = pass == 0 ? st->h1 : st->h2;
+        CP_LAUNCH(ctx, k_gm_dots<T>, G, kBlock, 0, s, n, V, ldv, j + 1, w, part, st);
+        CP_LAUNCH(ctx, k_gm_reduce, j + 1, kBlock, 0, s, part, G, h, st);
+        CP_LAUNCH(ctx, k_gm_sub<T>, G, kBlock, 0, s, n, V, ldv, j + 1, w, h, pn, st);
+      }
+      CP_LAUNCH(ctx, k_gm_givens, 1, kBlock, 0, s, pn, G, st, j, steps, tol2, mir);
+      CP_LAUNCH(ctx, k_gm_scale<T>, G, kBlock, 0, s, n, w, st, 1);
+      CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
+      ++issued;
+      if (issued >= depth) {
+        CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));
+        if (ws.mir->halt) break;
+      }
+    }
+    CP_LAUNCH(ctx, k_gm_backsub, 1, 1, 0, s, st);
+    CP_LAUNCH(ctx, k_gm_update_x<T>, G, kBlock, 0, s, n, V, ldv, x, st);
+    CP_CUDA(cudaStreamSynchronize(s));
+    res.iters = ws.mir->iters;
+    res.status = ws.mir->status;
+    if (res.status != CP_OK) break;
+    if (!true_check && ws.mir->conv_est) break;
+  }
+  if (true_check) {
+    // FP64 true residual of the returned x
+    spmv_cur<T>(cs, x, tmp, nullptr, nullptr, nullptr, s);
+    CP_LAUNCH(ctx, k_resid<T>, G, kBlock, 0, s, n, b, tmp, (T*)nullptr, pn, (const int*)nullptr);
+    CP_LAUNCH(ctx, k_sum_to, 1, kBlock, 0, s, pn, G, &st->h2[0]);
+    double rt2 = 0.0, bb = 0.0;
+    CP_CUDA(cudaMemcpyAsync(&rt2, &st->h2[0], sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaMemcpyAsync(&bb, &st->bb, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+    const double rel = bb > 0.0 ? std::sqrt(rt2 / bb) : 0.0;
+    if (relres_true) *relres_true = rel;
+    if (res.status == CP_OK && rel > tol) res.status = CP_ERR_NOT_CONVERGED;
+  }
+  return res;
+}
+
+// ------------------------------------------------------------------ iterative refinement
+// x0 = the caller's x.  Loop: r = b - A x in FP64 with the configuration in
+// force; stop at ||r|| <= tol ||b||; else solve A d = r in FP32 (values and r
+// rounded to nearest) to relative inner_tol, starting from d = 0, and x += d.
+static LoopResult run_ir(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const double* b,
+                         double* x, double tol, double inner_tol, int max_outer, int maxit,
+                         int depth, bool gmres, int mrest, double* relres, int* outer_out) {
+  cp_mat* m = cs.m;
+  const int64_t n = m->nrows;
+  cudaStream_t s = ctx->main;
+  double* r = ws.get<double>(n);
+  double* ax = ws.get<double>(n);
+  float* r32 = ws.get<float>(n);
+  float* d32 = ws.get<float>(n);
+  double* part = ws.get<double>(kMaxPartials);
+  double* sums = ws.get<double>(2);
+  const int G = grid_n(ctx, n);
+  double bb = 0.0;
+  {
+    const int P = dot_partials<double>(ctx, n, b, b, part, nullptr, s);
+    CP_LAUNCH(ctx, k_sum_to, 1, kBlock, 0, s, part, P, sums);
+    CP_CUDA(cudaMemcpyAsync(&bb, sums, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+  }
+  LoopResult res;
+  int outer = 0, inner_total = 0;
+  for (;;) {
+    cs.poll(inner_total);
+    spmv_cur<double>(cs, x, ax, nullptr, nullptr, nullptr, s);
+    CP_LAUNCH(ctx, k_resid<double>, G, kBlock, 0, s, n, b, ax, r, part, (const int*)nullptr);
+    CP_LAUNCH(ctx, k_sum_to, 1, kBlock, 0, s, part, G, sums + 1);
+    double rr = 0.0;
+    CP_CUDA(cudaMemcpyAsync(&rr, sums + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+    const double rel = bb > 0.0 ? std::sqrt(rr / bb) : 0.0;
+    *relres = rel;
+    res.res = std::sqrt(rr);
+    if (!std::isfinite(rel)) {
+      res.status = CP_ERR_BREAKDOWN;
+      break;
+    }
+    if (rel <= tol) break;
+    if (outer >= max_outer || inner_total >= maxit) {
+      res.status = CP_ERR_NOT_CONVERGED;
+      break;
+    }
+    CP_LAUNCH(ctx, (k_cast<double, float>), G, kBlock, 0, s, n, r, r32);
+    CP_CUDA(cudaMemsetAsync(d32, 0, n * sizeof(float), s));
+    LoopResult in = gmres ? run_gmres<float>(ctx, cs, ws, r32, d32, true, inner_tol, mrest,
+                                             maxit - inner_total, depth, false, nullptr)
+                          : run_cg<float>(ctx, cs, ws, r32, d32, true, inner_tol,
+                                          maxit - inner_total, depth, false, nullptr);
+    inner_total += in.iters;
+    if (in.status == CP_ERR_BREAKDOWN) {
+      res.status = CP_ERR_BREAKDOWN;
+      break;
+    }
+    CP_LAUNCH(ctx, k_add_f32, G, kBlock, 0, s, n, x, d32);
+    ++outer;
+  }
+  res.iters = inner_total;
+  *outer_out = outer;
+  return res;
+}
+
+// ------------------------------------------------------------------ entry
+void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_opts* o,
+           cp_solve_info* info, bool gmres) {
+  const auto t0 = Clock::now();
+  cp_solve_opts opt;
+  cp_solve_opts_default(&opt);
+  if (o) opt = *o;
+  CP_REQUIRE(opt.tol > 0.0 && opt.maxit >= 0, CP_ERR_INVALID, "tol must be > 0, maxit >= 0");
+  CP_REQUIRE(!gmres || (opt.restart >= 1 && opt.restart <= kMaxRestart), CP_ERR_INVALID,
+             "GMRES restart must be in 1..%d", kMaxRestart);
+  CP_REQUIRE(opt.precision == CP_PREC_FP64 || opt.precision == CP_PREC_FP32_IR, CP_ERR_INVALID,
+             "unknown precision %d", opt.precision);
+  CP_REQUIRE(opt.mode >= CP_MODE_PLAIN && opt.mode <= CP_MODE_ASYNC, CP_ERR_INVALID,
+             "unknown mode %d", opt.mode);
+  CP_REQUIRE(m->nrows == m->ncols, CP_ERR_INVALID, "solvers need a square matrix");
+  const bool fp32 = opt.precision == CP_PREC_FP32_IR;
+  const int depth = opt.check_every > 0 ? opt.check_every : 8;
+  const int64_t launches0 = ctx->launches.load();
+
+  ConfigSource cs;
+  cs.ctx = ctx;
+  cs.m = m;
+  cs.fp32 = fp32;
+  cs.profile = opt.profile != 0;
+  cp_config_default(&cs.cur);
+  if (opt.force) cs.cur = *opt.force;
+  ensure_format(ctx, m, cs.cur, ctx->main);
+  if (fp32) ensure_val32(ctx, m, cs.cur, ctx->main);
+
+  Channel ch;
+  ch.need_fp32 = fp32;
+  std::thread side;
+  const bool predict = !opt.force && opt.mode != CP_MODE_PLAIN;
+  if (predict) {
+    cs.ch = &ch;
+    if (opt.mode == CP_MODE_SEQUENTIAL) {
+      run_cascade(ctx, m, ctx->side, &ch);  // predict first, then solve (SerGMRES)
+      cs.poll(0);
+    } else {
+      side = std::thread([ctx, m, &ch]() { run_cascade(ctx, m, ctx->side, &ch); });
+    }
+  }
+  auto stop_side = [&]() {
+    ch.cancel.store(true);
+    if (side.joinable()) side.join();
+  };
+
+  LoopResult res;
+  double relres = 0.0;
+  int outer = 0;
+  Workspace ws(ctx);
+  try {
+    if (!fp32) {
+      res = gmres ? run_gmres<double>(ctx, cs, ws, b, x, false, opt.tol, opt.restart, opt.maxit,
+                                      depth, true, &relres)
+                  : run_cg<double>(ctx, cs, ws, b, x, false, opt.tol, opt.maxit, depth, true,
+                                   &relres);
+    } else {
+      res = run_ir(ctx, cs, ws, b, x, opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, depth,
+                   gmres, opt.restart, &relres, &outer);
+    }
+    CP_CUDA(cudaStreamSynchronize(ctx->main));
+  } catch (...) {
+    stop_side();
+    throw;
+  }
+  const float t_total = (float)ms_since(t0);
+  stop_side();
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = res.iters;
+    info->outer_iters = outer;
+    for (int k = 0; k < 3; ++k) info->switch_iter[k] = cs.switch_iter[k];
+    info->relres_true = relres;
+    info->final_cfg = cs.cur;
+    info->t_features_ms = ch.t_features_ms;
+    for (int k = 0; k < 3; ++k) info->t_predict_ms[k] = ch.t_predict_ms[k];
+    info->t_convert_ms = ch.t_convert_ms;
+    info->t_total_ms = t_total;
+    info->t_spmv_ms = cs.spmv_ms();
+    info->n_spmv = cs.n_spmv;
+    info->n_launches = (int32_t)(ctx->launches.load() - launches0);
+    info->status = res.status;
+  }
+  if (res.status != CP_OK) {
+    if (res.status == CP_ERR_NOT_CONVERGED)
+      set_error("not converged: relative residual %.3e after %d iterations", relres, res.iters);
+    else if (res.status == CP_ERR_BREAKDOWN)
+      set_error("breakdown (non-SPD matrix for CG, or a non-finite value)");
+    throw Error{(cp_status)res.status};
+  }
+}
+
+}  // namespace cp

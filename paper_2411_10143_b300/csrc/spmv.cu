@@ -1,0 +1,481 @@
+// The SpMV family (Sec. III-B-2's configuration space, Fig. 2): CSR-scalar,
+// CSR-vector with TpV threads per row, merge-path CSR (Merrill and Garland,
+// cited in Sec. V-A), ELL, SELL-C-sigma (slicing, Sec. V-A), HYB and COO.
+//
+// Every kernel is a persistent grid-stride kernel launched with the resident
+// grid of the device (a multiple of the SM count), so a fused reduction leaves
+// one partial per block and the consumer can sum them in a fixed order.
+// Matrix arrays are read with evict-first loads; x is gathered through the
+// read-only path.  T is the value type (double, or float for the FP32 inner
+// solves).  No tensor cores: SpMV moves 12 bytes per FP64 non-zero for one
+// FMA, far below any tensor-core shape's arithmetic intensity.
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace cp {
+
+// y_i <- s (solver form) or alpha s + beta y_i (general form; y not read when beta = 0)
+template <typename T, bool GEN>
+__device__ __forceinline__ void store_row(T* y, int64_t i, T s, T alpha, T beta) {
+  if (GEN) {
+    T r = alpha * s;
+    if (beta != T(0)) r = fma(beta, y[i], r);
+    y[i] = r;
+  } else {
+    y[i] = s;
+  }
+}
+
+template <bool DOT>
+__device__ __forceinline__ void write_partial(double acc, double* partials) {
+  if (DOT) {
+    __shared__ double red[33];
+    const double s = block_sum(acc, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------------ CSR scalar
+template <typename T, bool GEN, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_csr_scalar(
+    int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
+    const T* __restrict__ dotv, double* __restrict__ partials, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  T acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int s = rp[i], e = rp[i + 1];
+    T sum = 0;
+#pragma unroll 4
+    for (int k = s; k < e; ++k) sum = fma(ld_stream(v + k), ld_ro(x + ld_stream(ci + k)), sum);
+    store_row<T, GEN>(y, i, sum, alpha, beta);
+    if (DOT) acc = fma(sum, dotv[i], acc);
+  }
+  write_partial<DOT>((double)acc, partials);
+}
+
+// ------------------------------------------------------------------ CSR vector
+// TPV lanes per row; the warp walks its rows in lock step so the shuffles of
+// the row reduction always see the full warp.
+template <typename T, int TPV, bool GEN, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_csr_vector(
+    int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
+    const T* __restrict__ dotv, double* __restrict__ partials, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  constexpr int RPW = 32 / TPV;  // rows per warp step
+  const int lane = threadIdx.x & 31;
+  const int sub = lane % TPV;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  T acc = 0;
+  for (int64_t r0 = warp * RPW; r0 < n; r0 += nwarps * RPW) {
+    const int64_t i = r0 + lane / TPV;
+    T sum = 0;
+    if (i < n) {
+      const int s = rp[i], e = rp[i + 1];
+      for (int k = s + sub; k < e; k += TPV)
+        sum = fma(ld_stream(v + k), ld_ro(x + ld_stream(ci + k)), sum);
+    }
+#pragma unroll
+    for (int o = TPV / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (sub == 0 && i < n) {
+      store_row<T, GEN>(y, i, sum, alpha, beta);
+      if (DOT) acc = fma(sum, dotv[i], acc);
+    }
+  }
+  write_partial<DOT>((double)acc, partials);
+}
+
+// ------------------------------------------------------------------ merge-path CSR
+// The merge of the row-end offsets rowptr[1..n] with the non-zero indices
+// 0..nnz-1 is cut into tiles of equal length (n + nnz items in total), so a
+// 50k-entry row costs the same per item as a 3-entry row.  A tile's start is
+// found by a binary search along its diagonal; its row ends are staged in
+// shared memory; each thread walks kMergeItems items.  Rows that a thread
+// finishes are written directly; partial rows are combined inside the block,
+// and the partial of the row still open at the tile's end becomes the tile's
+// carry, added by k_merge_fixup.
+constexpr int kMergeItems = 7;
+constexpr int kMergeTile = kBlock * kMergeItems;
+
+// First split point (i = row ends consumed, k = non-zeros consumed) on diagonal
+// d of the merge path, with ties taking the row end after the non-zeros < it.
+__device__ __forceinline__ int64_t merge_search(int64_t d, const int32_t* row_end, int64_t n,
+                                                int64_t nnz) {
+  int64_t lo = d > nnz ? d - nnz : 0;
+  int64_t hi = d < n ? d : n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if ((int64_t)row_end[mid] <= d - mid - 1) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(kBlock) k_csr_merge(
+    int64_t n, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
+    int64_t ntiles, int32_t* __restrict__ carry_row, T* __restrict__ carry_val,
+    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ int32_t s_end[kMergeTile + 1];
+  __shared__ int64_t s_bounds[2];
+  __shared__ int32_t s_row[kBlock];  // row each thread ends in (its carry row)
+  __shared__ T s_carry[kBlock];      // that row's partial in the thread
+  const int64_t total = n + nnz;
+  const int32_t* row_end = rp + 1;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t d0 = t * kMergeTile;
+    const int64_t d1 = d0 + kMergeTile < total ? d0 + kMergeTile : total;
+    if (threadIdx.x == 0) s_bounds[0] = merge_search(d0, row_end, n, nnz);
+    if (threadIdx.x == 32) s_bounds[1] = merge_search(d1, row_end, n, nnz);
+    __syncthreads();
+    const int64_t i0 = s_bounds[0], i1 = s_bounds[1];
+    const int64_t k0 = d0 - i0;
+    // stage row_end[i0 .. min(i1, n-1)]
+    const int64_t last = i1 < n ? i1 : n - 1;
+    for (int64_t r = i0 + threadIdx.x; r <= last; r += blockDim.x) s_end[r - i0] = row_end[r];
+    __syncthreads();
+    // this thread's split inside the tile
+    int64_t dt = d0 + (int64_t)threadIdx.x * kMergeItems;
+    if (dt > d1) dt = d1;
+    // search rows i in [i0, i1] with i + k = dt and k in [k0, d1 - i1]
+    const int64_t kmax = d1 - i1;
+    int64_t a = dt - kmax > i0 ? dt - kmax : i0;
+    int64_t b = dt - k0 < i1 ? dt - k0 : i1;
+    while (a < b) {
+      const int64_t mid = (a + b) >> 1;
+      if ((int64_t)s_end[mid - i0] <= dt - mid - 1) a = mid + 1;
+      else b = mid;
+    }
+    int64_t i = a, k = dt - a;
+    const int64_t start_row = i;
+    T sum = 0, head = 0;
+    bool has_head = false;
+    const int64_t dend = dt + kMergeItems < d1 ? dt + kMergeItems : d1;
+    for (int64_t d = dt; d < dend; ++d) {
+      if (k < (int64_t)s_end[i - i0]) {
+        sum = fma(ld_stream(v + k), ld_ro(x + ld_stream(ci + k)), sum);
+        ++k;
+      } else {
+        if (i == start_row) {
+          head = sum;
+          has_head = true;
+        } else {
+          store_row<T, GEN>(y, i, sum, alpha, beta);
+        }
+        sum = 0;
+        ++i;
+      }
+    }
+    s_row[threadIdx.x] = (int32_t)(i < n ? i : n);
+    s_carry[threadIdx.x] = sum;
+    __syncthreads();
+    if (has_head) {
+      // add the partials of the preceding threads that ended inside start_row
+      T c = 0;
+      for (int j = (int)threadIdx.x - 1; j >= 0 && s_row[j] == start_row; --j) c += s_carry[j];
+      store_row<T, GEN>(y, start_row, head + c, alpha, beta);
+    }
+    if (threadIdx.x == blockDim.x - 1) {
+      const int32_t r = s_row[threadIdx.x];
+      T c = 0;
+      for (int j = (int)threadIdx.x; j >= 0 && s_row[j] == r; --j) c += s_carry[j];
+      carry_row[t] = r < n ? r : -1;
+      carry_val[t] = c;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_merge_fixup(int64_t ntiles, const int32_t* __restrict__ carry_row,
+                              const T* __restrict__ carry_val, T* __restrict__ y, T alpha,
+                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = carry_row[t];
+    if (r >= 0) atomicAdd(y + r, alpha * carry_val[t]);
+  }
+}
+
+// ------------------------------------------------------------------ ELL
+template <typename T, bool GEN, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_ell(
+    int64_t n, int64_t K, int64_t ld, const int32_t* __restrict__ ec, const T* __restrict__ ev,
+    const T* __restrict__ x, T* __restrict__ y, T alpha, T beta, const T* __restrict__ dotv,
+    double* __restrict__ partials, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  T acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T sum = 0;
+#pragma unroll 4
+    for (int64_t k = 0; k < K; ++k) {
+      const int32_t c = ld_stream(ec + k * ld + i);
+      if (c < 0) break;  // padding only follows a row's entries
+      sum = fma(ld_stream(ev + k * ld + i), ld_ro(x + c), sum);
+    }
+    store_row<T, GEN>(y, i, sum, alpha, beta);
+    if (DOT) acc = fma(sum, dotv[i], acc);
+  }
+  write_partial<DOT>((double)acc, partials);
+}
+
+// ------------------------------------------------------------------ SELL-C-sigma (C = 32)
+// One warp per chunk, lane r on slot r: every load of the chunk is one
+// contiguous 128-byte (col) and 256-byte (FP64 val) transaction.
+template <typename T, bool GEN, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_sell(
+    int64_t n, int64_t nchunks, const int32_t* __restrict__ perm,
+    const int32_t* __restrict__ clen, const int64_t* __restrict__ cptr,
+    const int32_t* __restrict__ sc, const T* __restrict__ sv, const T* __restrict__ x,
+    T* __restrict__ y, T alpha, T beta, const T* __restrict__ dotv,
+    double* __restrict__ partials, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  T acc = 0;
+  for (int64_t c = warp; c < nchunks; c += nwarps) {
+    const int64_t base = cptr[c] + lane;
+    const int w = clen[c];
+    T sum = 0;
+#pragma unroll 4
+    for (int k = 0; k < w; ++k) {
+      const int32_t col = ld_stream(sc + base + (int64_t)k * 32);
+      if (col >= 0) sum = fma(ld_stream(sv + base + (int64_t)k * 32), ld_ro(x + col), sum);
+    }
+    const int64_t s = c * 32 + lane;
+    if (s < n) {
+      const int64_t row = perm ? perm[s] : s;
+      store_row<T, GEN>(y, row, sum, alpha, beta);
+      if (DOT) acc = fma(sum, dotv[row], acc);
+    }
+  }
+  write_partial<DOT>((double)acc, partials);
+}
+
+// ------------------------------------------------------------------ COO (segmented)
+// Each warp takes 32 * kCooPerLane consecutive entries; a segmented warp scan
+// by row sums each row's run and the run's last lane adds it to y atomically.
+// y must already hold the rest of the row (0, beta*y, or HYB's ELL part).
+constexpr int kCooPerLane = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_coo(
+    int64_t nnz, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+    const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, T alpha,
+    const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t chunk = 32 * kCooPerLane;
+  for (int64_t base = warp * chunk; base < nnz; base += nwarps * chunk) {
+#pragma unroll 2
+    for (int j = 0; j < kCooPerLane; ++j) {
+      const int64_t idx = base + j * 32 + lane;
+      int32_t r = -1;
+      T p = 0;
+      if (idx < nnz) {
+        r = ld_stream(row + idx);
+        p = ld_stream(val + idx) * ld_ro(x + ld_stream(col + idx));
+      }
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T up = __shfl_up_sync(0xffffffffu, p, o);
+        const int32_t rup = __shfl_up_sync(0xffffffffu, r, o);
+        if (lane >= o && rup == r) p += up;
+      }
+      const int32_t rnext = __shfl_down_sync(0xffffffffu, r, 1);
+      const bool tail = (lane == 31) || (rnext != r);
+      if (tail && r >= 0) atomicAdd(y + r, alpha * p);
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_scale(int64_t n, T* __restrict__ y, T beta, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = beta == T(0) ? T(0) : beta * y[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_dot_partials(int64_t n, const T* __restrict__ a,
+                                                         const T* __restrict__ b,
+                                                         double* __restrict__ partials,
+                                                         const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  T acc = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(a[i], b[i], acc);
+  __shared__ double red[33];
+  const double s = block_sum((double)acc, red);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------------ launchers
+template <typename T>
+struct Vals;
+template <>
+struct Vals<double> {
+  static const double* csr(const cp_mat* m) { return m->val; }
+  static const double* ell(const EllPart& e) { return e.val; }
+  static const double* sell(const SellPart& s) { return s.val; }
+  static const double* coo(const CooPart& c) { return c.val; }
+};
+template <>
+struct Vals<float> {
+  static const float* csr(const cp_mat* m) { return m->val32; }
+  static const float* ell(const EllPart& e) { return e.val32; }
+  static const float* sell(const SellPart& s) { return s.val32; }
+  static const float* coo(const CooPart& c) { return c.val32; }
+};
+
+template <typename T, bool GEN, bool DOT>
+static void launch_csr_vector(cp_ctx* ctx, int tpv, int grid, cudaStream_t s, int64_t n,
+                              const int32_t* rp, const int32_t* ci, const T* v, const T* x, T* y,
+                              T alpha, T beta, const T* dotv, double* partials, const int* skip) {
+#define CP_VEC_CASE(TPV)                                                                     \
+  case TPV:                                                                                  \
+    CP_LAUNCH(ctx, (k_csr_vector<T, TPV, GEN, DOT>), grid, kBlock, 0, s, n, rp, ci, v, x, y, \
+              alpha, beta, dotv, partials, skip);                                            \
+    break;
+  switch (tpv) {
+    CP_VEC_CASE(2)
+    CP_VEC_CASE(4)
+    CP_VEC_CASE(8)
+    CP_VEC_CASE(16)
+    CP_VEC_CASE(32)
+    default:
+      CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "TpV %d not supported", tpv);
+  }
+#undef CP_VEC_CASE
+}
+
+static int grid_for(cp_ctx* ctx, int64_t work_items) {
+  const int64_t need = (work_items + kBlock - 1) / kBlock;
+  int64_t g = need < ctx->grid_stream ? need : ctx->grid_stream;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// One routine for both forms: GEN = general alpha/beta, DOT = fused partials.
+// skip (device flag, may be null): when set at launch time the kernels return
+// at once, so a converged solve's queued iterations cost only their launch.
+template <typename T, bool GEN, bool DOT>
+static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, const T* x,
+                         T beta, T* y, const T* dotv, double* partials, const int* skip,
+                         cudaStream_t s) {
+  const int64_t n = m->nrows;
+  switch (cfg.fmt) {
+    case CP_FMT_CSR: {
+      const T* v = Vals<T>::csr(m);
+      if (cfg.algo == CP_ALGO_VECTOR) {
+        const int g = grid_for(ctx, n * cfg.tpv);
+        launch_csr_vector<T, GEN, DOT>(ctx, cfg.tpv, g, s, n, m->rowptr, m->col, v, x, y, alpha,
+                                       beta, dotv, partials, skip);
+        return DOT ? g : 0;
+      }
+      if (cfg.algo == CP_ALGO_MERGE) {
+        const int g = (int)(m->merge_tiles < ctx->grid_stream ? m->merge_tiles : ctx->grid_stream);
+        CP_LAUNCH(ctx, (k_csr_merge<T, GEN>), g > 0 ? g : 1, kBlock, 0, s, n, m->nnz, m->rowptr,
+                  m->col, v, x, y, alpha, beta, m->merge_tiles, m->merge_carry_row,
+                  reinterpret_cast<T*>(m->merge_carry_val), skip);
+        CP_LAUNCH(ctx, k_merge_fixup<T>, grid_for(ctx, m->merge_tiles), kBlock, 0, s,
+                  m->merge_tiles, m->merge_carry_row,
+                  reinterpret_cast<const T*>(m->merge_carry_val), y, GEN ? alpha : T(1), skip);
+        break;
+      }
+      const int g = grid_for(ctx, n);
+      CP_LAUNCH(ctx, (k_csr_scalar<T, GEN, DOT>), g, kBlock, 0, s, n, m->rowptr, m->col, v, x, y,
+                alpha, beta, dotv, partials, skip);
+      return DOT ? g : 0;
+    }
+    case CP_FMT_ELL: {
+      const int g = grid_for(ctx, n);
+      CP_LAUNCH(ctx, (k_ell<T, GEN, DOT>), g, kBlock, 0, s, n, m->ell.K, m->ell.ld, m->ell.col,
+                Vals<T>::ell(m->ell), x, y, alpha, beta, dotv, partials, skip);
+      return DOT ? g : 0;
+    }
+    case CP_FMT_SELL: {
+      const int g = grid_for(ctx, m->sell.nchunks * 32);
+      CP_LAUNCH(ctx, (k_sell<T, GEN, DOT>), g, kBlock, 0, s, n, m->sell.nchunks,
+                m->sell.sigma > 1 ? m->sell.perm : nullptr, m->sell.chunk_len, m->sell.chunk_ptr,
+                m->sell.col, Vals<T>::sell(m->sell), x, y, alpha, beta, dotv, partials, skip);
+      return DOT ? g : 0;
+    }
+    case CP_FMT_HYB: {
+      const int g = grid_for(ctx, n);
+      CP_LAUNCH(ctx, (k_ell<T, GEN, false>), g, kBlock, 0, s, n, m->hyb_ell.K, m->hyb_ell.ld,
+                m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, nullptr, nullptr,
+                skip);
+      if (m->hyb_coo.n > 0)
+        CP_LAUNCH(ctx, k_coo<T>, grid_for(ctx, (m->hyb_coo.n + kCooPerLane - 1) / kCooPerLane),
+                  kBlock, 0, s, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
+                  Vals<T>::coo(m->hyb_coo), x, y, GEN ? alpha : T(1), skip);
+      break;
+    }
+    case CP_FMT_COO: {
+      CP_LAUNCH(ctx, k_scale<T>, grid_for(ctx, n), kBlock, 0, s, n, y, GEN ? beta : T(0), skip);
+      if (m->nnz > 0)
+        CP_LAUNCH(ctx, k_coo<T>, grid_for(ctx, (m->nnz + kCooPerLane - 1) / kCooPerLane), kBlock,
+                  0, s, m->nnz, m->coo.row, m->col, Vals<T>::csr(m), x, y, GEN ? alpha : T(1),
+                  skip);
+      break;
+    }
+    default:
+      CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "unknown format %d", cfg.fmt);
+  }
+  // formats without a fused reduction: a separate pass for the partials
+  if (DOT) {
+    const int g = grid_for(ctx, n);
+    CP_LAUNCH(ctx, k_dot_partials<T>, g, kBlock, 0, s, n, y, dotv, partials, skip);
+    return g;
+  }
+  return 0;
+}
+
+template <typename T>
+int spmv_solver(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, const T* x, T* y, const T* dotv,
+                double* partials, const int* skip, cudaStream_t s) {
+  if (dotv)
+    return spmv_dispatch<T, false, true>(ctx, m, cfg, T(1), x, T(0), y, dotv, partials, skip, s);
+  return spmv_dispatch<T, false, false>(ctx, m, cfg, T(1), x, T(0), y, nullptr, nullptr, skip, s);
+}
+
+template <typename T>
+void spmv_general(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, const T* x, T beta,
+                  T* y, cudaStream_t s) {
+  spmv_dispatch<T, true, false>(ctx, m, cfg, alpha, x, beta, y, nullptr, nullptr, nullptr, s);
+}
+
+template <typename T>
+int dot_partials(cp_ctx* ctx, int64_t n, const T* a, const T* b, double* partials,
+                 const int* skip, cudaStream_t s) {
+  const int g = grid_for(ctx, n);
+  CP_LAUNCH(ctx, k_dot_partials<T>, g, kBlock, 0, s, n, a, b, partials, skip);
+  return g;
+}
+
+template int spmv_solver<double>(cp_ctx*, cp_mat*, const cp_config&, const double*, double*,
+                                 const double*, double*, const int*, cudaStream_t);
+template int spmv_solver<float>(cp_ctx*, cp_mat*, const cp_config&, const float*, float*,
+                                const float*, double*, const int*, cudaStream_t);
+template void spmv_general<double>(cp_ctx*, cp_mat*, const cp_config&, double, const double*,
+                                   double, double*, cudaStream_t);
+template void spmv_general<float>(cp_ctx*, cp_mat*, const cp_config&, float, const float*, float,
+                                  float*, cudaStream_t);
+template int dot_partials<double>(cp_ctx*, int64_t, const double*, const double*, double*,
+                                  const int*, cudaStream_t);
+template int dot_partials<float>(cp_ctx*, int64_t, const float*, const float*, double*,
+                                 const int*, cudaStream_t);
+
+}  // namespace cp

@@ -1,0 +1,193 @@
+"""GPU CG / GMRES(m) / FP32-inner refinement vs the oracle, and the
+asynchronous and sequential cascade modes.
+
+Acceptance: the true relative residual of the GPU solution, recomputed by the
+oracle's SpMV, is <= 1e-10, and the solution is within 1e-7 (relative) of the
+oracle's own solution at the same tolerance."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_10143_b300 import cascade as C
+from paper_2411_10143_b300 import workloads as W
+from gpu_helpers import all_configs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = C.Context(0)
+    yield c
+    c.close()
+
+
+def true_relres(A, x, b):
+    return np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+
+
+def gpu_solve(ctx, A, b, kind="cg", x0=None, **kw):
+    M = ctx.load(A)
+    force = kw.pop("force", None)
+    raise_on_error = kw.pop("raise_on_error", True)
+    opts = C.default_opts(**kw)
+    bd = torch.as_tensor(b, device="cuda")
+    xd = (torch.as_tensor(x0, device="cuda").clone() if x0 is not None
+          else torch.zeros(A.nrows, dtype=torch.float64, device="cuda"))
+    fn = M.solve_cg if kind == "cg" else M.solve_gmres
+    info = fn(bd, xd, opts, force=force, raise_on_error=raise_on_error)
+    return xd.cpu().numpy(), info
+
+
+def rhs(A, seed):
+    return oracle.spmv(A, W.vector(A.ncols, seed))
+
+
+def test_cg_poisson2d_64_plain():
+    """The 2D Poisson 64x64 system (n = 4096) with the default CSR-scalar kernel."""
+    c = C.Context(0)
+    A = W.poisson2d(64)
+    b = rhs(A, 2001)
+    x, info = gpu_solve(c, A, b, tol=1e-10)
+    ref = oracle.cg(A, b, tol=1e-10)
+    assert info.status == 0 and true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    assert abs(info.iters - ref.iters) <= 3
+    assert info.final_cfg.fmt == C.FMT_CSR
+
+
+@pytest.mark.parametrize("ci", range(len(all_configs())))
+def test_cg_every_forced_config(ctx, ci):
+    cfg = all_configs()[ci]
+    A = W.poisson3d(14)
+    b = rhs(A, 3)
+    x, info = gpu_solve(ctx, A, b, tol=1e-10, force=cfg)
+    ref = oracle.cg(A, b, tol=1e-10)
+    assert true_relres(A, x, b) <= 1e-10, repr(cfg)
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x), repr(cfg)
+
+
+def test_cg_spd_powerlaw_and_x0(ctx):
+    A = W.spd_powerlaw(20000, seed=5)
+    b = rhs(A, 4)
+    x0 = W.vector(A.nrows, 9)
+    x, info = gpu_solve(ctx, A, b, x0=x0, tol=1e-10)
+    ref = oracle.cg(A, b, tol=1e-10)
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("m", [5, 30])
+def test_gmres_convdiff(ctx, m):
+    A = W.convdiff3d(12)
+    b = rhs(A, 5)
+    x, info = gpu_solve(ctx, A, b, kind="gmres", restart=m, tol=1e-10)
+    ref = oracle.gmres(A, b, m=m, tol=1e-10)
+    assert info.status == 0 and true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("cfg", [C.config("ELL"), C.config("SELL", sigma=1024),
+                                 C.config("HYB"), C.config("COO"),
+                                 C.config("CSR", C.ALGO_MERGE)])
+def test_gmres_forced_configs(ctx, cfg):
+    A = W.diagonally_dominant(W.powerlaw(6000, lmax=400, seed=8))
+    b = rhs(A, 6)
+    x, info = gpu_solve(ctx, A, b, kind="gmres", restart=30, tol=1e-10, force=cfg)
+    ref = oracle.gmres(A, b, m=30, tol=1e-10)
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+@pytest.mark.parametrize("kind,make", [("cg", lambda: W.poisson3d(16)),
+                                       ("gmres", lambda: W.convdiff3d(14)),
+                                       ("cg", lambda: W.spd_powerlaw(8000, seed=2))])
+def test_fp32_inner_refinement(ctx, kind, make):
+    A = make()
+    b = rhs(A, 7)
+    x, info = gpu_solve(ctx, A, b, kind=kind, tol=1e-10, precision=C.PREC_FP32_IR,
+                        inner_tol=1e-5)
+    ref = oracle.ir_solve(A, b, solver=kind, tol=1e-10, inner_tol=1e-5)
+    ref64 = (oracle.cg if kind == "cg" else oracle.gmres)(A, b, tol=1e-10)
+    assert info.status == 0 and true_relres(A, x, b) <= 1e-10
+    assert info.outer_iters >= 2
+    assert np.linalg.norm(x - ref64.x) <= 1e-7 * np.linalg.norm(ref64.x)
+    assert ref.status == 0
+
+
+def test_edge_cases(ctx):
+    A = W.poisson2d(10)
+    x, info = gpu_solve(ctx, A, np.zeros(100))
+    assert not x.any() and info.status == 0
+    x, info = gpu_solve(ctx, A, rhs(A, 1), maxit=3, raise_on_error=False)
+    assert info.status == C.ERR_NOT_CONVERGED and info.iters == 3
+    neg = W.Matrix(A.nrows, A.ncols, A.rowptr, A.col, -A.val)
+    x, info = gpu_solve(ctx, neg, rhs(A, 1), raise_on_error=False)
+    assert info.status == C.ERR_BREAKDOWN
+    x, info = gpu_solve(ctx, A, np.zeros(100), kind="gmres")
+    assert not x.any() and info.status == 0
+
+
+def one_hot_model(ctx, stage, cls):
+    """A classifier that always answers `cls` (zero weights, one-hot output bias)."""
+    k = C.STAGE_CLASSES[stage]
+    n = C.Context.mlp_nparams(15, 4, 4, k)
+    P = np.zeros(n, np.float32)
+    P[n - k + cls] = 1.0
+    ctx.model_load(stage, 4, 4, k, P, np.zeros(15), np.ones(15))
+
+
+@pytest.mark.parametrize("mode", [C.MODE_ASYNC, C.MODE_SEQUENTIAL])
+@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "CSR-vector"])
+def test_cascade_switch_keeps_solution(mode, target):
+    c = C.Context(0)
+    if target == "CSR-vector":
+        one_hot_model(c, C.STAGE_FORMAT, C.FMT_CSR)
+        one_hot_model(c, C.STAGE_CSR_ALGO, C.ALGO_VECTOR)
+        one_hot_model(c, C.STAGE_CSR_TPV, 2)  # TpV 8
+    else:
+        one_hot_model(c, C.STAGE_FORMAT, C.FORMATS.index(target))
+        one_hot_model(c, C.STAGE_SELL_SIGMA, 2)  # sigma 1024
+    A = W.poisson3d(24)
+    b = rhs(A, 8)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=mode)
+    ref = oracle.cg(A, b, tol=1e-10)
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    if target == "CSR-vector":
+        assert info.final_cfg.fmt == C.FMT_CSR and info.final_cfg.algo == C.ALGO_VECTOR
+        assert info.final_cfg.tpv == 8 and info.switch_iter[1] >= 0 and info.switch_iter[2] >= 0
+    else:
+        assert C.FORMATS[info.final_cfg.fmt] == target and info.switch_iter[0] >= 0
+        if target == "SELL":
+            assert info.final_cfg.sell_sigma == 1024
+    if mode == C.MODE_SEQUENTIAL:
+        assert max(info.switch_iter) == 0
+    c.close()
+
+
+def test_async_gmres_ir_switch():
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_SELL)
+    one_hot_model(c, C.STAGE_SELL_SIGMA, 1)
+    A = W.convdiff3d(20)
+    b = rhs(A, 9)
+    x, info = gpu_solve(c, A, b, kind="gmres", tol=1e-10, mode=C.MODE_ASYNC,
+                        precision=C.PREC_FP32_IR)
+    assert true_relres(A, x, b) <= 1e-10
+    ref = oracle.gmres(A, b, m=30, tol=1e-10)
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    assert info.final_cfg.fmt == C.FMT_SELL and info.final_cfg.sell_sigma == 32
+    c.close()
+
+
+def test_predict_sequential_api():
+    c = C.Context(0)
+    M = c.load(W.poisson2d(32))
+    cfg, ms = M.predict()  # no models: CSR stays
+    assert cfg.fmt == C.FMT_CSR and cfg.algo == C.ALGO_SCALAR and ms[0] > 0
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    cfg, ms = M.predict()
+    assert cfg.fmt == C.FMT_ELL
+    c.close()
