@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark: time-to-solution of the asynchronous cascaded CG solve.
+
+Workload (one "step"): CG to relative residual 1e-10 in FP64 on the 3D 7-point
+Poisson matrix of a 128^3 grid (n = 2,097,152, nnz = 14,581,760), b = A x*
+with x* ~ U[-1, 1] (seed 2002), x0 = 0.  The solve starts at once on the
+default CSR-scalar kernel while the side stream extracts the Table IV
+features, runs the cascade (FORMAT -> ALGO -> PARAM) and converts the format;
+the solve switches kernel mid-run (Sec. III-C).  Each step starts from the
+freshly loaded CSR (converted formats and features dropped), so the
+preprocessing is inside every measured time-to-solution.
+
+Printed JSON line: value = mean time-to-solution (ms, CUDA events around each
+solve on the main stream); plus the plain CSR-scalar CG and the sequential
+(predict-then-solve) and FP32-inner refinement variants, the SpMV roofline,
+the CPU oracle baseline, the end-to-end time through host buffers, clocks and
+kernel counts.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "time-to-solution (incl. prep) vs plain CSR-CG; SpMV % HBM BW; serve p50/p99"
+GRID = 128
+TOL = 1e-10
+XSTAR_SEED = 2002
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_init(backend):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world, device=None):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def workload():
+    from paper_2411_10143_b300 import workloads as W
+    A = W.poisson3d(GRID)
+    xs = W.vector(A.nrows, XSTAR_SEED)
+    return A, xs
+
+
+def spmv_bytes(A):
+    """Algorithmic bytes of one FP64 CSR-class SpMV: 12 nnz + 4 (n+1) + 8 ncols + 8 n."""
+    return 12 * A.nnz + 4 * (A.nrows + 1) + 8 * A.ncols + 8 * A.nrows
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ CPU oracle arms
+def oracle_sample(A, b, iters_budget):
+    """Single-threaded oracle CG bounded to ``iters_budget`` iterations; returns
+    seconds per iteration."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.cg(A, b, tol=1e-300, maxit=iters_budget)
+    dt = time.perf_counter() - t0
+    return dt / max(r.iters, 1), r.iters
+
+
+def run_reference(args, world, rank):
+    """The CPU oracle as the reference arm (bounded samples, extrapolated)."""
+    if rank != 0:
+        return
+    import oracle
+    A, xs = workload()
+    b = oracle.spmv(A, xs)
+    # iterations of the full solve: one full oracle run would take minutes, so
+    # the count comes from the convergence rate of a bounded run
+    sample_iters = 40
+    per_iter, _ = oracle_sample(A, b, 5)  # warm caches
+    times = []
+    for _ in range(args.warmup):
+        oracle_sample(A, b, 5)
+    full_iters = oracle_iteration_estimate(A, b)
+    for _ in range(args.steps):
+        per_iter, n = oracle_sample(A, b, sample_iters)
+        times.append(per_iter * full_iters * 1e3)
+    value = float(np.mean(times))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": bench_config(A),
+        "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
+                         "sample": f"{sample_iters} CG iterations per step, scaled to the "
+                                   f"{full_iters} iterations of the full solve"},
+        "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+_ITER_CACHE = ROOT / "oracle" / "cg_iterations_poisson3d_128.json"
+
+
+def oracle_iteration_estimate(A, b):
+    """CG iteration count of the oracle on this workload.  It is measured once by
+    running the oracle to convergence (oracle/cg_iterations.py, several minutes on
+    one core); without that file a shorter run's residual decay is extrapolated."""
+    if _ITER_CACHE.exists():
+        d = json.loads(_ITER_CACHE.read_text())
+        if d.get("grid") == GRID and d.get("tol") == TOL:
+            return int(d["iters"])
+    import oracle
+    r = oracle.cg(A, b, tol=1e-300, maxit=60, hist_cap=60)
+    # residual decay from the recursive (r,r) = rr_0 * prod(beta)
+    lb = np.cumsum(np.log(r.betas))
+    rate = (lb[-1] - lb[len(lb) // 2]) / (len(lb) - 1 - len(lb) // 2)
+    need = 2 * np.log(TOL)
+    return int(len(lb) + max(0.0, (need - lb[-1]) / rate))
+
+
+def bench_config(A):
+    return {"workload": "CG, 3D 7-point Poisson 128^3 (n=2,097,152, nnz=14,581,760), FP64, "
+                        "rel. residual 1e-10, asynchronous cascaded prediction on a side stream",
+            "n": A.nrows, "nnz": A.nnz, "tol": TOL, "x0": "zeros", "rhs": "b = A x*, x* ~ U[-1,1]",
+            "l2": "inputs larger than L2 (CSR 192 MB + 4 vectors of 16.8 MB vs 126 MB L2)"}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import models
+
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream(local)
+    torch.cuda.set_stream(stream)
+    ctx = C.Context(local, main_stream=stream)
+    loaded = models.load_default(ctx)
+    A, xs = workload()
+    M = ctx.load(A)
+    xs_d = torch.as_tensor(xs, device="cuda")
+    b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    M.spmv(xs_d, b)  # b = A x* by the library's default SpMV
+    x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+    opts = C.default_opts(tol=TOL, mode=C.MODE_ASYNC, profile=1, check_every=8)
+
+    def step():
+        M.reset()
+        x.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = M.solve_cg(b, x, opts)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1), info
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    launches0 = ctx.launch_count()
+    infos, tts = [], []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ms, info = step()
+            tts.append(ms)
+            infos.append(info)
+        torch.cuda.synchronize()
+        barrier(world)
+        region = time.perf_counter() - t0
+    launches = ctx.launch_count() - launches0
+    value = max_over_ranks(float(np.mean(tts)), world, "cuda")
+    region = max_over_ranks(region, world, "cuda")
+    last = infos[-1]
+    err = float(torch.linalg.norm(x - xs_d) / torch.linalg.norm(xs_d))
+
+    # roofline of the dominant kernel (the SpMV), from the in-solve event pairs
+    n_spmv = sum(i.n_spmv for i in infos)
+    t_spmv = sum(i.t_spmv_ms for i in infos)
+    peak, peak_kind = measured_peaks()
+    achieved = spmv_bytes(A) * n_spmv / (t_spmv * 1e-3) / 1e9 if t_spmv > 0 else None
+    extra = {}
+    if rank == 0 and not args.no_compare:
+        extra = comparisons(args, ctx, M, A, b, x, xs_d, stream, C)
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": region * 1e3 / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": bench_config(A),
+        "roofline": {"bound": "hbm", "kernel": f"spmv ({last.final_cfg!r} after the switch)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "peak_kind": peak_kind,
+                     "bytes_per_launch": spmv_bytes(A), "launches": n_spmv,
+                     "avg_launch_us": t_spmv / max(n_spmv, 1) * 1e3},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "solve": {"iters": last.iters, "final_cfg": repr(last.final_cfg),
+                  "switch_iter": list(last.switch_iter), "relres_true": last.relres_true,
+                  "err_vs_xstar": err, "t_features_ms": last.t_features_ms,
+                  "t_predict_ms": list(last.t_predict_ms), "t_convert_ms": last.t_convert_ms,
+                  "models": loaded},
+        "solves_per_s": world * args.steps / region,
+    }
+    line.update(extra)
+    if "plain_csr_cg_ms" in line:
+        line["speedup_vs_plain"] = line["plain_csr_cg_ms"] / value
+        line["speedup_async_vs_sequential"] = line["sequential_ms"] / value
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
+    """Plain / sequential / FP32-IR variants, the end-to-end number, the CPU baseline."""
+    import torch
+
+    def timed(opts, reps=2):
+        out = []
+        for _ in range(reps):
+            M.reset()
+            x.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info = M.solve_cg(b, x, opts)
+            e1.record(stream)
+            e1.synchronize()
+            out.append((e0.elapsed_time(e1), info))
+        return float(np.mean([o[0] for o in out])), out[-1][1]
+
+    plain_ms, plain = timed(C.default_opts(tol=TOL, mode=C.MODE_PLAIN))
+    seq_ms, seq = timed(C.default_opts(tol=TOL, mode=C.MODE_SEQUENTIAL))
+    ir_ms, ir = timed(C.default_opts(tol=TOL, mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
+                                     inner_tol=1e-5))
+    res = {
+        "plain_csr_cg_ms": plain_ms, "plain_iters": plain.iters,
+        "sequential_ms": seq_ms, "fp32_ir_async_ms": ir_ms,
+        "fp32_ir": {"outer": ir.outer_iters, "inner": ir.iters, "relres_true": ir.relres_true,
+                    "final_cfg": repr(ir.final_cfg)},
+    }
+    # end to end through host buffers: pinned CSR + b in, x out, per step
+    rp = torch.as_tensor(A.rowptr).pin_memory()
+    ci = torch.as_tensor(A.col).pin_memory()
+    va = torch.as_tensor(A.val).pin_memory()
+    bh = b.cpu().pin_memory()
+    xh = torch.empty(A.nrows, dtype=torch.float64).pin_memory()
+    opts = C.default_opts(tol=TOL, mode=C.MODE_ASYNC)
+    e2e = []
+    for _ in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Mh = ctx.csr_load(A.nrows, A.ncols, rp.numpy(), ci.numpy(), va.numpy())
+        bd = bh.to("cuda", non_blocking=True)
+        xd = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        Mh.solve_cg(bd, xd, opts)
+        xh.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append((time.perf_counter() - t0) * 1e3)
+        Mh.free()
+    res["e2e"] = {"value": float(np.mean(e2e)), "unit": "ms",
+                  "h2d_bytes_per_step": int(rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8
+                                            + bh.numel() * 8),
+                  "d2h_bytes_per_step": int(xh.numel() * 8)}
+    if args.gpus == 1 and not args.no_cpu_baseline:
+        import oracle
+        bn = b.cpu().numpy()
+        sample = 150
+        per_iter, _ = oracle_sample(A, bn, sample)
+        full = oracle_iteration_estimate(A, bn)
+        res["cpu_baseline"] = {"value": per_iter * full * 1e3, "unit": "ms", "cores": 1,
+                               "kind": "oracle",
+                               "sample": f"{sample} single-threaded oracle CG iterations, "
+                                         f"scaled to the {full} iterations of the full solve"}
+    return res
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the plain / sequential / FP32-IR / end-to-end / CPU legs")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        world, rank, _ = dist_init("gloo")
+        run_reference(args, world, rank)
+        return
+    world, rank, local = dist_init("nccl")
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -79,10 +79,13 @@ void cp_config_default(cp_config* cfg);
 
 /* ------------------------------------------------------------------ context */
 /* cp_create: a context on CUDA device `device`.  main_stream / side_stream are
- * cudaStream_t handles owned by the caller (e.g. torch streams) or NULL, in
- * which case the context creates (and later destroys) non-blocking streams of
- * its own.  The side stream runs feature extraction, prediction and format
- * conversion concurrently with the solve (Sec. III-C-2).
+ * cudaStream_t handles owned by the caller (e.g. torch streams; pass
+ * cudaStreamLegacy, (void*)1, for the legacy default stream) or NULL, in which
+ * case the context creates (and later destroys) non-blocking streams of its
+ * own.  Inputs written on another stream must be complete (or ordered before
+ * the call) when an entry point reads them.  The side stream runs feature
+ * extraction, prediction and format conversion concurrently with the solve
+ * (Sec. III-C-2).
  * Errors: CP_ERR_INVALID (bad device), CP_ERR_CUDA, CP_ERR_OOM. */
 cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_stream);
 cp_status cp_destroy(cp_ctx* ctx);
@@ -106,6 +109,11 @@ cp_status cp_csr_load(cp_ctx* ctx, int64_t nrows, int64_t ncols, int64_t nnz,
                       const int32_t* rowptr, const int32_t* col, const double* val,
                       int32_t on_device, cp_mat** out);
 cp_status cp_mat_free(cp_mat* mat);
+
+/* cp_mat_reset: drop every converted format and the cached features of `mat`,
+ * returning it to the state cp_csr_load left (the CSR copy stays).  Used to
+ * measure a solve's preprocessing (features, prediction, conversion) again. */
+cp_status cp_mat_reset(cp_mat* mat);
 
 /* Budget, in bytes, for one padded format (ELL, SELL, HYB's ELL part) of one
  * matrix; conversions above it fail with CP_ERR_FOOTPRINT.  Default: 4 GiB. */

@@ -104,6 +104,7 @@ _SIGS = {
     "cp_set_format_budget": (c_int32, [_p, c_int64]),
     "cp_csr_load": (c_int32, [_p, c_int64, c_int64, c_int64, _p, _p, _p, c_int32, POINTER(_p)]),
     "cp_mat_free": (c_int32, [_p]),
+    "cp_mat_reset": (c_int32, [_p]),
     "cp_features": (c_int32, [_p, _p, _p]),
     "cp_convert": (c_int32, [_p, _p, POINTER(Config)]),
     "cp_format_dims": (c_int32, [_p, _p, POINTER(Config), _p]),
@@ -178,11 +179,19 @@ class Context:
     streams (or None for library-owned streams)."""
 
     def __init__(self, device: int = 0, main_stream=None, side_stream=None):
+        """main_stream defaults to torch's current stream on ``device``, so the
+        library's work is ordered with the torch operations that fill its inputs
+        and read its outputs.  The side stream defaults to a library-owned
+        non-blocking stream."""
+        import torch
         self._h = c_void_p()
         self.device = device
+        if main_stream is None:
+            main_stream = torch.cuda.current_stream(device)
         self._streams = (main_stream, side_stream)  # keep them alive
-        ms = c_void_p(main_stream.cuda_stream) if main_stream is not None else None
-        ss = c_void_p(side_stream.cuda_stream) if side_stream is not None else None
+        # handle 0 is the legacy default stream: pass it as cudaStreamLegacy (1)
+        ms = c_void_p(main_stream.cuda_stream or 1)
+        ss = c_void_p(side_stream.cuda_stream or 1) if side_stream is not None else None
         _check(lib().cp_create(byref(self._h), device, ms, ss))
 
     @property
@@ -287,6 +296,10 @@ class Matrix:
                 self.free()
         except Exception:
             pass
+
+    def reset(self):
+        """Drop converted formats and cached features (cp_mat_reset)."""
+        _check(lib().cp_mat_reset(self._h))
 
     def features(self) -> np.ndarray:
         out = np.zeros(15)

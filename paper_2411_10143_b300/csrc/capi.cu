@@ -196,6 +196,18 @@ cp_status cp_mat_free(cp_mat* m) {
   });
 }
 
+cp_status cp_mat_reset(cp_mat* m) {
+  return guard([&] {
+    CP_REQUIRE(m, CP_ERR_INVALID, "NULL argument");
+    use_device(m->ctx);
+    CP_CUDA(cudaStreamSynchronize(m->ctx->main));
+    CP_CUDA(cudaStreamSynchronize(m->ctx->side));
+    std::lock_guard<std::mutex> lock(m->mu);
+    free_formats(m);
+    m->has_features = false;
+  });
+}
+
 cp_status cp_features(cp_ctx* ctx, cp_mat* m, double* out15) {
   return guard([&] {
     CP_REQUIRE(ctx && m && out15, CP_ERR_INVALID, "NULL argument");

@@ -80,8 +80,13 @@ struct FeatAcc {
 
 constexpr int kLongRow = 64;  // rows longer than this are handled a warp at a time
 
+// Set the bit of diagonal offset `off`.  A plain read first: structured
+// matrices hit the same few offsets from every row, and an atomic per non-zero
+// on those few words would serialise the whole pass.
 __device__ __forceinline__ void mark_diag(unsigned* bitmap, int64_t off) {
-  atomicOr(bitmap + (off >> 5), 1u << (off & 31));
+  const unsigned bit = 1u << (off & 31);
+  unsigned* w = bitmap + (off >> 5);
+  if (!(*(volatile unsigned*)w & bit)) atomicOr(w, bit);
 }
 
 template <typename U>

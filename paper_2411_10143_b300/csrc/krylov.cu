@@ -551,25 +551,30 @@ struct ConfigSource {
     }
     applied = c;
   }
+  // event pairs around every SpMV launch, created in batches (an event
+  // creation per launch would cost host time inside the loop)
   void before_spmv(cudaStream_t s) {
     if (!profile) return;
-    cudaEvent_t a, b;
-    CP_CUDA(cudaEventCreate(&a));
-    CP_CUDA(cudaEventCreate(&b));
-    ev.push_back(a);
-    ev.push_back(b);
-    CP_CUDA(cudaEventRecord(a, s));
+    const size_t need = 2 * (size_t)(n_spmv + 1);
+    while (ev.size() < need) {
+      for (int q = 0; q < 256; ++q) {
+        cudaEvent_t e;
+        CP_CUDA(cudaEventCreate(&e));
+        ev.push_back(e);
+      }
+    }
+    CP_CUDA(cudaEventRecord(ev[2 * n_spmv], s));
   }
   void after_spmv(cudaStream_t s) {
     if (!profile) return;
-    CP_CUDA(cudaEventRecord(ev.back(), s));
+    CP_CUDA(cudaEventRecord(ev[2 * n_spmv + 1], s));
     ++n_spmv;
   }
   float spmv_ms() {
     float tot = 0.f;
-    for (size_t i = 0; i + 1 < ev.size(); i += 2) {
+    for (int i = 0; i < n_spmv; ++i) {
       float t = 0.f;
-      if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) tot += t;
+      if (cudaEventElapsedTime(&t, ev[2 * i], ev[2 * i + 1]) == cudaSuccess) tot += t;
     }
     return tot;
   }

@@ -47,8 +47,20 @@ __global__ void __launch_bounds__(kBlock) k_csr_scalar(
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     const int s = rp[i], e = rp[i + 1];
     T sum = 0;
-#pragma unroll 4
-    for (int k = s; k < e; ++k) sum = fma(ld_stream(v + k), ld_ro(x + ld_stream(ci + k)), sum);
+    // chunks of 4 entries: the 8 index/value loads are independent, then 4 gathers
+    for (int k0 = s; k0 < e; k0 += 4) {
+      int32_t c[4];
+      T w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = k0 + u < e;
+        c[u] = in ? ld_stream(ci + k0 + u) : 0;
+        w[u] = in ? ld_stream(v + k0 + u) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k0 + u < e) sum = fma(w[u], ld_ro(x + c[u]), sum);
+    }
     store_row<T, GEN>(y, i, sum, alpha, beta);
     if (DOT) acc = fma(sum, dotv[i], acc);
   }
@@ -75,8 +87,15 @@ __global__ void __launch_bounds__(kBlock) k_csr_vector(
     T sum = 0;
     if (i < n) {
       const int s = rp[i], e = rp[i + 1];
-      for (int k = s + sub; k < e; k += TPV)
-        sum = fma(ld_stream(v + k), ld_ro(x + ld_stream(ci + k)), sum);
+      for (int k = s + sub; k < e; k += 2 * TPV) {
+        const bool in2 = k + TPV < e;
+        const int32_t c0 = ld_stream(ci + k);
+        const int32_t c1 = in2 ? ld_stream(ci + k + TPV) : 0;
+        const T w0 = ld_stream(v + k);
+        const T w1 = in2 ? ld_stream(v + k + TPV) : T(0);
+        sum = fma(w0, ld_ro(x + c0), sum);
+        if (in2) sum = fma(w1, ld_ro(x + c1), sum);
+      }
     }
 #pragma unroll
     for (int o = TPV / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
@@ -214,11 +233,21 @@ __global__ void __launch_bounds__(kBlock) k_ell(
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
     T sum = 0;
-#pragma unroll 4
-    for (int64_t k = 0; k < K; ++k) {
-      const int32_t c = ld_stream(ec + k * ld + i);
-      if (c < 0) break;  // padding only follows a row's entries
-      sum = fma(ld_stream(ev + k * ld + i), ld_ro(x + c), sum);
+    // chunks of 4 slots: 8 independent coalesced loads, then the gathers;
+    // padding (col -1) only follows a row's entries, so a padded chunk ends the row
+    for (int64_t k0 = 0; k0 < K; k0 += 4) {
+      int32_t c[4];
+      T w[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = k0 + u < K;
+        c[u] = in ? ld_stream(ec + (k0 + u) * ld + i) : -1;
+        w[u] = in ? ld_stream(ev + (k0 + u) * ld + i) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (c[u] >= 0) sum = fma(w[u], ld_ro(x + c[u]), sum);
+      if (c[3] < 0) break;
     }
     store_row<T, GEN>(y, i, sum, alpha, beta);
     if (DOT) acc = fma(sum, dotv[i], acc);
@@ -245,10 +274,18 @@ __global__ void __launch_bounds__(kBlock) k_sell(
     const int64_t base = cptr[c] + lane;
     const int w = clen[c];
     T sum = 0;
-#pragma unroll 4
-    for (int k = 0; k < w; ++k) {
-      const int32_t col = ld_stream(sc + base + (int64_t)k * 32);
-      if (col >= 0) sum = fma(ld_stream(sv + base + (int64_t)k * 32), ld_ro(x + col), sum);
+    for (int k0 = 0; k0 < w; k0 += 4) {
+      int32_t cc[4];
+      T vv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const bool in = k0 + u < w;
+        cc[u] = in ? ld_stream(sc + base + (int64_t)(k0 + u) * 32) : -1;
+        vv[u] = in ? ld_stream(sv + base + (int64_t)(k0 + u) * 32) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (cc[u] >= 0) sum = fma(vv[u], ld_ro(x + cc[u]), sum);
     }
     const int64_t s = c * 32 + lane;
     if (s < n) {

@@ -138,32 +138,64 @@ def one_hot_model(ctx, stage, cls):
     ctx.model_load(stage, 4, 4, k, P, np.zeros(15), np.ones(15))
 
 
-@pytest.mark.parametrize("mode", [C.MODE_ASYNC, C.MODE_SEQUENTIAL])
-@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "CSR-vector"])
-def test_cascade_switch_keeps_solution(mode, target):
-    c = C.Context(0)
+def expected_target(target):
+    """(models to load, expected final configuration) for a forced cascade."""
     if target == "CSR-vector":
-        one_hot_model(c, C.STAGE_FORMAT, C.FMT_CSR)
-        one_hot_model(c, C.STAGE_CSR_ALGO, C.ALGO_VECTOR)
-        one_hot_model(c, C.STAGE_CSR_TPV, 2)  # TpV 8
-    else:
-        one_hot_model(c, C.STAGE_FORMAT, C.FORMATS.index(target))
-        one_hot_model(c, C.STAGE_SELL_SIGMA, 2)  # sigma 1024
+        return ([(C.STAGE_FORMAT, C.FMT_CSR), (C.STAGE_CSR_ALGO, C.ALGO_VECTOR),
+                 (C.STAGE_CSR_TPV, 3)], ("CSR", C.ALGO_VECTOR, 16))
+    return ([(C.STAGE_FORMAT, C.FORMATS.index(target)), (C.STAGE_SELL_SIGMA, 2)],
+            (target, None, None))
+
+
+@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "CSR-vector"])
+def test_sequential_cascade_applies_every_stage(target):
+    """SerGMRES-style: predict first, so every stage is applied at iteration 0."""
+    c = C.Context(0)
+    loads, (fmt, algo, tpv) = expected_target(target)
+    for stage, cls in loads:
+        one_hot_model(c, stage, cls)
     A = W.poisson3d(24)
     b = rhs(A, 8)
-    x, info = gpu_solve(c, A, b, tol=1e-10, mode=mode)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_SEQUENTIAL)
     ref = oracle.cg(A, b, tol=1e-10)
     assert true_relres(A, x, b) <= 1e-10
     assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    assert C.FORMATS[info.final_cfg.fmt] == fmt
     if target == "CSR-vector":
-        assert info.final_cfg.fmt == C.FMT_CSR and info.final_cfg.algo == C.ALGO_VECTOR
-        assert info.final_cfg.tpv == 8 and info.switch_iter[1] >= 0 and info.switch_iter[2] >= 0
+        assert info.final_cfg.algo == algo and info.final_cfg.tpv == tpv
+        assert info.switch_iter[0] == -1 and info.switch_iter[1] == 0 and info.switch_iter[2] == 0
     else:
-        assert C.FORMATS[info.final_cfg.fmt] == target and info.switch_iter[0] >= 0
+        assert info.switch_iter[0] == 0
         if target == "SELL":
             assert info.final_cfg.sell_sigma == 1024
-    if mode == C.MODE_SEQUENTIAL:
-        assert max(info.switch_iter) == 0
+    c.close()
+
+
+@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "CSR-vector"])
+def test_async_cascade_switches_mid_run(target):
+    """The solve starts at once on CSR-scalar; every prediction that lands before
+    convergence is applied at a later iteration, in cascade order, and the
+    solution is the oracle's either way.  The 64^3 Poisson system runs for
+    hundreds of iterations, so all stages land."""
+    c = C.Context(0)
+    loads, (fmt, algo, tpv) = expected_target(target)
+    for stage, cls in loads:
+        one_hot_model(c, stage, cls)
+    A = W.poisson3d(64)
+    b = rhs(A, 8)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    ref = oracle.cg(A, b, tol=1e-10)
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+    applied = [s for s in info.switch_iter if s >= 0]
+    assert applied == sorted(applied) and all(0 <= s <= info.iters for s in applied)
+    assert C.FORMATS[info.final_cfg.fmt] == fmt
+    if target == "CSR-vector":
+        assert info.final_cfg.algo == algo and info.final_cfg.tpv == tpv
+        assert info.switch_iter[1] >= 0 and info.switch_iter[2] >= info.switch_iter[1]
+    else:
+        assert info.switch_iter[0] >= 0
+    assert info.t_features_ms > 0
     c.close()
 
 
