@@ -175,6 +175,33 @@ enum { CP_DTYPE_F64 = 0, CP_DTYPE_F32 = 1 };
 cp_status cp_spmv(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32_t dtype,
                   double alpha, const void* x, double beta, void* y);
 
+/* cp_spmv_csr_merge_noalloc: y = A x with the merge-path CSR kernel, allocating
+ * nothing.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc at the point where they need an SpMV -- for
+ * example code running inside a memory-pool or arena allocator that owns all
+ * device memory, or a host callback where allocation would synchronise the
+ * device -- and so can use neither a cp_ctx nor a cp_mat (both allocate).
+ *  - rowptr[nrows+1], col[nnz], val[nnz] (FP64), x[ncols], y[nrows]: device
+ *    pointers owned by the caller; the matrix must be a valid CSR (as
+ *    cp_csr_load checks) -- this call does not validate it.
+ *  - The kernel's scratch (one carry per tile of 1,792 merge items) is a fixed
+ *    768 KiB file-scope device array that every GPU loading the library keeps
+ *    until the process exits; nrows + nnz may be at most 117,440,512
+ *    (65,536 tiles), larger inputs return CP_ERR_INVALID.
+ *  - The first call on a device looks up that array's device address
+ *    (cudaGetSymbolAddress); make it before any stream capture.
+ *  - Work is queued on `stream` (a cudaStream_t, NULL = the default stream) of
+ *    the current device; the call does not synchronise.  Every call shares the
+ *    one scratch array, so calls that overlap on the GPU (other streams or
+ *    other host threads) race and must be serialised by the caller.  Nothing in
+ *    the scratch needs to start at zero: each call writes every carry it reads.
+ * Errors: CP_ERR_INVALID (NULL pointer, sizes out of range or above the
+ * maximum), CP_ERR_CUDA (launch failure). */
+cp_status cp_spmv_csr_merge_noalloc(int64_t nrows, int64_t ncols, int64_t nnz,
+                                    const int32_t* rowptr, const int32_t* col,
+                                    const double* val, const double* x, double* y,
+                                    void* stream);
+
 /* ------------------------------------------------------------------ predictors */
 /* Each cascade stage is a small MLP classifier d -> h1 -> h2 -> k (ReLU), fed
  * z_j = (log(1 + f_j) - mu_j) / sd_j of the 15 features (FP32).  Stages

@@ -111,6 +111,7 @@ _SIGS = {
     "cp_format_export": (c_int32, [_p, _p, POINTER(Config), c_int32, _p, c_int64,
                                    POINTER(c_int64)]),
     "cp_spmv": (c_int32, [_p, _p, POINTER(Config), c_int32, c_double, _p, c_double, _p]),
+    "cp_spmv_csr_merge_noalloc": (c_int32, [c_int64, c_int64, c_int64, _p, _p, _p, _p, _p, _p]),
     "cp_mlp_nparams": (c_int64, [c_int32, c_int32, c_int32, c_int32]),
     "cp_mlp_scratch_floats": (c_int64, [c_int64, c_int32, c_int32, c_int32, c_int32]),
     "cp_mlp_forward": (c_int32, [_p, c_int64, c_int32, c_int32, c_int32, c_int32, _p, _p, _p, _p]),
@@ -162,6 +163,17 @@ def _ptr(a):
 
 def _np(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def spmv_csr_merge_noalloc(nrows, ncols, rowptr, col, val, x, y, stream=None):
+    """cp_spmv_csr_merge_noalloc on torch CUDA tensors: y = A x with no device
+    allocation (fixed library scratch; see cascade.h for its limit and for why
+    overlapping calls must be serialised)."""
+    import torch
+    s = (stream or torch.cuda.current_stream()).cuda_stream
+    _check(lib().cp_spmv_csr_merge_noalloc(int(nrows), int(ncols), int(col.numel()), _ptr(rowptr),
+                                           _ptr(col), _ptr(val), _ptr(x), _ptr(y),
+                                           c_void_p(s) if s else None))
 
 
 def default_opts(**kw) -> SolveOpts:

@@ -516,3 +516,80 @@ template int dot_partials<float>(cp_ctx*, int64_t, const float*, const float*, d
                                  const int*, cudaStream_t);
 
 }  // namespace cp
+
+// ------------------------------------------------------------------ allocation-free entry point
+// A merge-path CSR SpMV for callers that cannot allocate device memory (see
+// cp_spmv_csr_merge_noalloc in cascade.h).  Its per-tile carry scratch lives in
+// these file-scope device arrays, which every GPU that loads the library keeps
+// until the process exits.  Host code may not use the array names as device
+// addresses: each device's addresses come from cudaGetSymbolAddress below.
+namespace cp {
+
+constexpr int64_t kNoAllocMaxTiles = 65536;  // (nrows + nnz) <= 65536 * kMergeTile
+
+static __device__ __align__(256) int32_t g_noalloc_carry_row[kNoAllocMaxTiles];
+static __device__ __align__(256) double g_noalloc_carry_val[kNoAllocMaxTiles];
+
+struct NoAllocDevice {
+  bool ready = false;
+  int32_t* carry_row = nullptr;  // device addresses of the arrays above
+  double* carry_val = nullptr;
+  int num_sms = 0;
+};
+static std::mutex g_noalloc_mu;
+static NoAllocDevice g_noalloc_dev[64];
+
+// Set-up once per device, with that device current.
+static const NoAllocDevice& noalloc_setup(int dev) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocDevice& d = g_noalloc_dev[dev];
+  if (!d.ready) {
+    CP_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&d.carry_row), g_noalloc_carry_row));
+    CP_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&d.carry_val), g_noalloc_carry_val));
+    CP_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    d.ready = true;
+  }
+  return d;
+}
+
+}  // namespace cp
+
+extern "C" cp_status cp_spmv_csr_merge_noalloc(int64_t nrows, int64_t ncols, int64_t nnz,
+                                               const int32_t* rowptr, const int32_t* col,
+                                               const double* val, const double* x, double* y,
+                                               void* stream) {
+  using namespace cp;
+  try {
+    CP_REQUIRE(rowptr && x && y && (nnz == 0 || (col && val)), CP_ERR_INVALID,
+               "cp_spmv_csr_merge_noalloc: NULL pointer argument");
+    CP_REQUIRE(nrows >= 1 && ncols >= 1 && nnz >= 0 && nrows < (int64_t(1) << 31) &&
+                   nnz < (int64_t(1) << 31),
+               CP_ERR_INVALID, "cp_spmv_csr_merge_noalloc: sizes out of range");
+    const int64_t tiles = (nrows + nnz + kMergeTile - 1) / kMergeTile;
+    CP_REQUIRE(tiles <= kNoAllocMaxTiles, CP_ERR_INVALID,
+               "cp_spmv_csr_merge_noalloc: nrows + nnz = %lld exceeds the maximum %lld of its "
+               "fixed scratch; use cp_spmv instead",
+               (long long)(nrows + nnz), (long long)(kNoAllocMaxTiles * kMergeTile));
+    int dev = 0;
+    CP_CUDA(cudaGetDevice(&dev));
+    CP_REQUIRE(dev >= 0 && dev < 64, CP_ERR_INVALID, "device index %d not supported", dev);
+    const NoAllocDevice& d = noalloc_setup(dev);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t cap = (int64_t)d.num_sms * 8;
+    const int grid = (int)(tiles < cap ? tiles : cap);
+    k_csr_merge<double, false><<<grid, kBlock, 0, s>>>(nrows, nnz, rowptr, col, val, x, y, 1.0,
+                                                        0.0, tiles, d.carry_row, d.carry_val,
+                                                        nullptr);
+    CP_CUDA(cudaGetLastError());
+    const int64_t fg = (tiles + kBlock - 1) / kBlock;
+    k_merge_fixup<double><<<(int)(fg < cap ? fg : cap), kBlock, 0, s>>>(
+        tiles, d.carry_row, d.carry_val, y, 1.0, nullptr);
+    CP_CUDA(cudaGetLastError());
+    return CP_OK;
+  } catch (const Error& e) {
+    return e.status;
+  } catch (...) {
+    set_error("cp_spmv_csr_merge_noalloc: unexpected internal error");
+    return CP_ERR_CUDA;
+  }
+}
