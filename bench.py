@@ -356,6 +356,8 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
                   "h2d_bytes_per_step": int(rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8
                                             + bh.numel() * 8),
                   "d2h_bytes_per_step": int(xh.numel() * 8)}
+    if args.serve_requests > 0:
+        res["serve"] = serve_bench(ctx, args.serve_requests)
     if args.gpus == 1 and not args.no_cpu_baseline:
         import oracle
         bn = b.cpu().numpy()
@@ -369,6 +371,82 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
     return res
 
 
+# ------------------------------------------------------------------ serving leg
+def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
+    """Continuous-batching server under Poisson arrivals: n log-uniform in
+    [1e3, 1e6], 40 % 2D/3D Poisson (CG), 30 % SPD power law (CG), 30 %
+    convection-diffusion (GMRES(30)), FP32 inner solves in FP64 refinement to
+    1e-10.  The arrival rate is 0.8 x the sequential service rate measured on a
+    sample of the same requests.  Matrices are generated once per size bucket
+    (6 per decade and kind) and stay resident; every request has its own
+    right-hand side."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import workloads as W
+    reqs = W.request_stream(count=count, rate_per_s=1.0, seed=seed)
+    buckets = {}
+
+    def bucket(r):
+        kb = (r.kind, int(round(np.log10(r.n) * 6)))
+        if kb not in buckets:
+            n = int(round(10 ** (kb[1] / 6)))
+            A = W.request_matrix(W.Request(0, 0.0, r.kind, n, seed + kb[1]))
+            buckets[kb] = (A, ctx.load(A))
+        return buckets[kb]
+
+    t0 = time.time()
+    items = []
+    for r in reqs:
+        A, M = bucket(r)
+        xs = torch.as_tensor(W.vector(A.nrows, r.seed % 100000), device="cuda")
+        b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        M.spmv(xs, b)
+        items.append((r, A, M, 1 if r.kind == "convdiff" else 0, b))
+    torch.cuda.synchronize()
+    log_fn(f"serve: {len(buckets)} resident matrices built in {time.time() - t0:.0f}s")
+    # sequential service rate on a sample
+    srv = C.Server(ctx, lanes=1)
+    sample = items[: min(24, len(items))]
+    t1 = time.perf_counter()
+    for k, (r, A, M, s, b) in enumerate(sample):
+        x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        srv.submit(k, M, s, b, x)
+        srv.drain(600)
+    seq = (time.perf_counter() - t1) / len(sample)
+    srv.poll()
+    srv.close()
+    rate = 0.8 / seq
+    # replay the arrivals at that rate
+    srv = C.Server(ctx, lanes=lanes)
+    xs_keep = []
+    start = time.perf_counter()
+    for k, (r, A, M, s, b) in enumerate(items):
+        due = start + r.arrival_s / rate
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            time.sleep(min(due - now, 0.002))
+        x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        xs_keep.append(x)
+        srv.submit(k, M, s, b, x)
+    srv.drain(1800)
+    wall = time.perf_counter() - start
+    res = srv.poll(capacity=len(items) + 8)
+    srv.close()
+    lat = np.array([q.t_done_ms - q.t_submit_ms for q in res])
+    ok = sum(1 for q in res if q.status == 0)
+    worst = max(q.relres_true for q in res) if res else None
+    fails = [{"id": int(q.id), "kind": items[q.id][0].kind, "n": int(items[q.id][1].nrows),
+              "status": int(q.status), "relres": q.relres_true, "batched": int(q.batched)}
+             for q in res if q.status != 0][:10]
+    return {"requests": len(items), "completed_ok": ok, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": len(items) / wall,
+            "arrival_rate_per_s": rate, "sequential_service_ms": seq * 1e3, "lanes": lanes,
+            "batched": int(sum(q.batched for q in res)), "max_relres_true": worst,
+            "resident_matrices": len(buckets), "failures": fails}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -376,6 +454,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=1000,
+                    help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain / sequential / FP32-IR / end-to-end / CPU legs")
     args = ap.parse_args()

@@ -51,16 +51,17 @@ typedef enum {
 /* SpMV configuration space (Sec. III-B-2, Fig. 2): compression format, then the
  * SpMV algorithm for that format, then the kernel parameter.  The paper's space
  * is COO/CSR/ELL/DIA/HYB across three libraries with the CSR-Vector threads per
- * vector (TpV) in {2,4,8,16,32}; this library's space is the formats below, the
- * CSR algorithms scalar / vector / merge-path, TpV for CSR-vector and the sort
- * window sigma for SELL-C-sigma (slicing, Sec. V-A). */
+ * vector (TpV) in {2,4,8,16,32}; this library's space is the formats below
+ * (adding SELL-C-sigma, the slicing of Sec. V-A), the CSR algorithms scalar /
+ * vector / merge-path, TpV for CSR-vector and the sort window sigma for SELL. */
 enum {
   CP_FMT_CSR = 0,
   CP_FMT_COO = 1,
   CP_FMT_ELL = 2,
   CP_FMT_SELL = 3,
   CP_FMT_HYB = 4,
-  CP_NUM_FMT = 5
+  CP_FMT_DIA = 5,
+  CP_NUM_FMT = 6
 };
 enum { CP_ALGO_SCALAR = 0, CP_ALGO_VECTOR = 1, CP_ALGO_MERGE = 2, CP_NUM_ALGO = 3 };
 
@@ -131,8 +132,8 @@ cp_status cp_set_format_budget(cp_ctx* ctx, int64_t bytes);
 cp_status cp_features(cp_ctx* ctx, cp_mat* mat, double* out15);
 
 /* ------------------------------------------------------------------ formats */
-/* cp_convert: materialise the format of `cfg` (CSR -> COO, ELL, SELL-C-sigma or
- * HYB) on the main stream and wait for it; the result is cached in `mat`.
+/* cp_convert: materialise the format of `cfg` (CSR -> COO, ELL, SELL-C-sigma,
+ * HYB or DIA) on the main stream and wait for it; the result is cached in `mat`.
  * Conversions copy indices and values bit for bit (Sec. III-C-1: a format
  * change needs storage and a conversion kernel).
  * Errors: CP_ERR_FOOTPRINT, CP_ERR_UNSUPPORTED, CP_ERR_OOM. */
@@ -150,6 +151,10 @@ cp_status cp_convert(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg);
  *  HYB : HYB_ELL_COL / HYB_ELL_VAL [K*ld] (first K entries per row, ELL layout)
  *        and HYB_COO_ROW / HYB_COO_COL / HYB_COO_VAL [ncoo] (the remaining
  *        entries, row-major).  dims = {K, ld, ncoo}.
+ *  DIA : DIA_OFFSETS[ndiag] (int32, distinct col - row, ascending) and
+ *        DIA_VAL[ndiag*nrows], entry of row i on diagonal d at d*nrows + i,
+ *        0.0 where the diagonal has no entry.  dims = {ndiag, nrows}.  At most
+ *        1024 diagonals; more fail with CP_ERR_FOOTPRINT.
  * cp_format_dims writes up to 4 int64 dims.  cp_format_export copies one array
  * to host memory dst (capacity bytes); *bytes receives its size. */
 enum {
@@ -158,7 +163,8 @@ enum {
   CP_ARR_SELL_PERM = 3, CP_ARR_SELL_CHUNK_LEN = 4, CP_ARR_SELL_CHUNK_PTR = 5,
   CP_ARR_SELL_COL = 6, CP_ARR_SELL_VAL = 7,
   CP_ARR_HYB_ELL_COL = 8, CP_ARR_HYB_ELL_VAL = 9,
-  CP_ARR_HYB_COO_ROW = 10, CP_ARR_HYB_COO_COL = 11, CP_ARR_HYB_COO_VAL = 12
+  CP_ARR_HYB_COO_ROW = 10, CP_ARR_HYB_COO_COL = 11, CP_ARR_HYB_COO_VAL = 12,
+  CP_ARR_DIA_OFFSETS = 13, CP_ARR_DIA_VAL = 14
 };
 cp_status cp_format_dims(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int64_t dims[4]);
 cp_status cp_format_export(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32_t array_id,
@@ -206,7 +212,7 @@ cp_status cp_spmv_csr_merge_noalloc(int64_t nrows, int64_t ncols, int64_t nnz,
 /* Each cascade stage is a small MLP classifier d -> h1 -> h2 -> k (ReLU), fed
  * z_j = (log(1 + f_j) - mu_j) / sd_j of the 15 features (FP32).  Stages
  * (Sec. III-C-1, Fig. 5):
- *   CP_STAGE_FORMAT     k = 5: CSR, COO, ELL, SELL, HYB
+ *   CP_STAGE_FORMAT     k = 6: CSR, COO, ELL, SELL, HYB, DIA
  *   CP_STAGE_CSR_ALGO   k = 3: scalar, vector, merge      (used if FORMAT = CSR)
  *   CP_STAGE_CSR_TPV    k = 5: TpV 2, 4, 8, 16, 32        (used if ALGO = vector)
  *   CP_STAGE_SELL_SIGMA k = 4: sigma 1, 32, 1024, 8192    (used if FORMAT = SELL)
@@ -309,6 +315,74 @@ cp_status cp_solve_cg(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
  * least-squares solve in FP64.  Arguments as cp_solve_cg. */
 cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
                          const cp_solve_opts* opts, cp_solve_info* info);
+
+/* ------------------------------------------------------------------ batching */
+/* cp_batch_solve: solve nsys small systems A_i x_i = b_i in one persistent,
+ * graph-captured launch.  One thread block per system at a time, systems taken
+ * largest first from a device work queue.  Every system runs FP64 iterative
+ * refinement to opts->tol around FP32 inner solves to opts->inner_tol:
+ * solver[i] = 0 for CG (SPD A_i), 1 for GMRES(opts->restart), restart <= 32.
+ * FP64 is kept for the outer residual, the update of x and GMRES's Givens /
+ * least-squares step.  mats[i] (square, CSR; the kernel is the CSR scalar one),
+ * b[i], x[i] (device FP64, x read as x0) are host arrays of nsys entries;
+ * opts->maxit bounds the inner steps of each system; threads per block: 128,
+ * 256, 512, 1024 or 0 (chosen from the mean system size).  infos (host array of
+ * nsys, may be NULL) receives per-system iterations, relres_true, status.
+ * Returns the first non-OK system status, else CP_OK. */
+cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
+                         const double* const* b, double* const* x, const cp_solve_opts* opts,
+                         int32_t threads, cp_solve_info* infos);
+
+/* ------------------------------------------------------------------ serving */
+/* A continuous-batching solve server.  Requests carry a matrix already loaded
+ * with cp_csr_load (kept resident; several requests may share one), a device
+ * right-hand side b and a device solution buffer x (x0 in, solution out), and
+ * are admitted while their Krylov workspace fits mem_budget.  `lanes` worker
+ * threads, each with its own streams, run admitted work concurrently: requests
+ * with nrows <= small_max_n are packed into one persistent batched launch
+ * (cp_batch_solve's kernel), larger ones run the full-GPU solver in `mode`
+ * with FP32 inner solves inside FP64 refinement to tol.  Requests that arrive
+ * while others run join as soon as a lane and memory free up.  The caller
+ * keeps every request's buffers and matrix alive until its result is polled;
+ * it must not free or reset a matrix while requests on it are in flight. */
+typedef struct cp_server cp_server;
+typedef struct {
+  double tol;           /* relative residual per request (e.g. 1e-10)          */
+  double inner_tol;     /* FP32 inner-solve tolerance (e.g. 1e-5)              */
+  int32_t restart;      /* GMRES restart length, 1..32                          */
+  int32_t maxit;        /* inner steps per request                              */
+  int32_t small_max_n;  /* requests with nrows <= this are batched              */
+  int32_t max_batch;    /* most requests in one batched launch                 */
+  int32_t lanes;        /* concurrent jobs on the device, 1..32                 */
+  int32_t mode;         /* CP_MODE_* of the full-GPU solver for large requests  */
+  int64_t mem_budget;   /* bytes of solver workspace admitted at once           */
+} cp_server_opts;
+typedef struct {
+  int64_t id;           /* caller's tag, returned in the result                 */
+  cp_mat* mat;
+  int32_t solver;       /* 0 CG, 1 GMRES                                         */
+  int32_t reserved;
+  const double* b;      /* device, nrows                                        */
+  double* x;            /* device, nrows                                        */
+} cp_request;
+typedef struct {
+  int64_t id;
+  int32_t status, iters, batched, lane;
+  double relres_true;
+  double t_submit_ms, t_start_ms, t_done_ms;  /* since cp_server_create          */
+} cp_result;
+
+void cp_server_opts_default(cp_server_opts* opts);
+/* The server uses the cascade models installed in ctx at creation time. */
+cp_status cp_server_create(cp_ctx* ctx, const cp_server_opts* opts, cp_server** out);
+cp_status cp_server_submit(cp_server* srv, const cp_request* req);
+/* Move up to capacity finished results into out (host); *count receives how many. */
+cp_status cp_server_poll(cp_server* srv, cp_result* out, int32_t capacity, int32_t* count);
+/* Wait until every submitted request has finished, at most timeout_s seconds
+ * (CP_ERR_TIMEOUT otherwise). */
+cp_status cp_server_drain(cp_server* srv, double timeout_s);
+/* Stop the server: running jobs finish, requests not yet admitted are dropped. */
+cp_status cp_server_destroy(cp_server* srv);
 
 #ifdef __cplusplus
 }

@@ -12,7 +12,7 @@ NumPy conveniences that follow the paper's definitions:
 * ``cg`` / ``gmres`` -- Hestenes-Stiefel CG and restarted GMRES(m) with MGS and
   Givens rotations (Sec. I, Sec. IV-A).
 * ``features`` -- the 15 features of Table IV (Sec. III-B-1).
-* ``to_coo`` / ``to_ell`` / ``to_sell`` / ``to_hyb`` and inverses -- canonical
+* ``to_coo`` / ``to_ell`` / ``to_sell`` / ``to_hyb`` / ``to_dia`` -- canonical
   layouts of the format space (Sec. III-B-2, Sec. V-A).
 * ``ir_solve`` -- FP64 iterative refinement around FP32 CG/GMRES inner solves.
 * ``mlp_forward`` / ``mlp_loss_grad`` / ``adam_step`` / ``mlp_input`` -- the
@@ -79,6 +79,8 @@ def lib() -> ctypes.CDLL:
             "or_sell_to_csr": (None, [_i64, _i64, _p, _p, _p, _p, _p, _p, _p, _p]),
             "or_csr_to_hyb": (_i64, [_i64, _p, _p, _p, _i64, _i64, _p, _p, _p, _p, _p]),
             "or_hyb_to_csr": (None, [_i64, _i64, _i64, _p, _p, _i64, _p, _p, _p, _p, _p, _p]),
+            "or_dia_offsets": (_i64, [_i64, _i64, _p, _p, _p]),
+            "or_csr_to_dia": (None, [_i64, _p, _p, _p, _i64, _p, _p]),
             "or_mlp_nparams": (_i64, [_i64, _i64, _i64, _i64]),
             "or_mlp_forward": (None, [_i64, _i64, _i64, _i64, _i64, _p, _p, _p]),
             "or_mlp_loss_grad": (_f64, [_i64, _i64, _i64, _i64, _i64, _p, _p, _p, _p]),
@@ -309,6 +311,18 @@ def hyb_to_csr(n, ncols, K, ld, ecol, eval_, crow, ccol, cval, nnz) -> CSR:
     return CSR(n, ncols, rp, ci, v)
 
 
+def to_dia(A):
+    """DIA arrays: ascending offsets (col - row) and values [ndiag][nrows] (0.0 where absent)."""
+    A = _as_csr(A)
+    offs = np.empty(max(A.nrows + A.ncols - 1, 1), np.int32)
+    nd = lib().or_dia_offsets(A.nrows, A.ncols, _ptr(A.rowptr), _ptr(A.col), _ptr(offs))
+    offs = offs[:nd].copy()
+    data = np.empty(nd * A.nrows, np.float64)
+    lib().or_csr_to_dia(A.nrows, _ptr(A.rowptr), _ptr(A.col), _ptr(A.val), nd, _ptr(offs),
+                        _ptr(data))
+    return offs, data
+
+
 # ---------------------------------------------------------------- predictor MLP
 def mlp_nparams(d, h1, h2, k) -> int:
     return int(lib().or_mlp_nparams(d, h1, h2, k))
@@ -355,7 +369,7 @@ def mlp_input(f, mu, sd) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- cascade
-FORMATS = ("CSR", "COO", "ELL", "SELL", "HYB")
+FORMATS = ("CSR", "COO", "ELL", "SELL", "HYB", "DIA")
 
 
 def cascade(format_logits, algo_logits=None, tpv_logits=None, sell_logits=None):

@@ -614,6 +614,35 @@ void or_hyb_to_csr(i64 n, i64 K, i64 ld, const i32* ecol, const double* eval,
   }
 }
 
+/* DIA: the distinct diagonal offsets (col - row) in ascending order, and a
+ * value array of ndiag columns of nrows entries: entry of row i on diagonal d
+ * at d*nrows + i, 0.0 where the diagonal has no entry in that row (including
+ * positions outside the matrix).  or_dia_offsets fills offs (capacity
+ * nrows + ncols - 1) and returns ndiag. */
+i64 or_dia_offsets(i64 n, i64 ncols, const i32* rp, const i32* ci, i32* offs) {
+  const i64 span = n + ncols - 1;
+  unsigned char* seen = (unsigned char*)calloc((size_t)(span > 0 ? span : 1), 1);
+  for (i64 i = 0; i < n; ++i)
+    for (i64 k = rp[i]; k < rp[i + 1]; ++k) seen[(i64)ci[k] - i + (n - 1)] = 1;
+  i64 nd = 0;
+  for (i64 o = 0; o < span; ++o)
+    if (seen[o]) offs[nd++] = (i32)(o - (n - 1));
+  free(seen);
+  return nd;
+}
+
+void or_csr_to_dia(i64 n, const i32* rp, const i32* ci, const double* v, i64 ndiag,
+                   const i32* offs, double* data) {
+  for (i64 q = 0; q < ndiag * n; ++q) data[q] = 0.0;
+  for (i64 i = 0; i < n; ++i)
+    for (i64 k = rp[i]; k < rp[i + 1]; ++k) {
+      const i64 off = (i64)ci[k] - i;
+      i64 d = 0;
+      while (offs[d] != off) ++d;  /* offsets are few; linear search */
+      data[d * n + i] = v[k];
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Predictor MLP (FP64).  Layer sizes d -> h1 -> h2 -> k, ReLU after the two   */
 /* hidden layers, softmax cross-entropy averaged over the batch.               */

@@ -24,19 +24,19 @@ _LIB_PATH = Path(__file__).resolve().parent / "libcascade.so"
 
 OK, ERR_INVALID, ERR_OOM, ERR_FOOTPRINT, ERR_NOT_CONVERGED, ERR_BREAKDOWN = range(6)
 ERR_TIMEOUT, ERR_CUDA, ERR_CANCELLED, ERR_UNSUPPORTED = range(6, 10)
-FMT_CSR, FMT_COO, FMT_ELL, FMT_SELL, FMT_HYB = range(5)
-FORMATS = ("CSR", "COO", "ELL", "SELL", "HYB")
+FMT_CSR, FMT_COO, FMT_ELL, FMT_SELL, FMT_HYB, FMT_DIA = range(6)
+FORMATS = ("CSR", "COO", "ELL", "SELL", "HYB", "DIA")
 ALGO_SCALAR, ALGO_VECTOR, ALGO_MERGE = range(3)
 MODE_PLAIN, MODE_SEQUENTIAL, MODE_ASYNC = range(3)
 PREC_FP64, PREC_FP32_IR = range(2)
 DTYPE_F64, DTYPE_F32 = range(2)
 STAGE_FORMAT, STAGE_CSR_ALGO, STAGE_CSR_TPV, STAGE_SELL_SIGMA = range(4)
-STAGE_CLASSES = (5, 3, 5, 4)
+STAGE_CLASSES = (6, 3, 5, 4)
 TPV_CLASSES = (2, 4, 8, 16, 32)
 SIGMA_CLASSES = (1, 32, 1024, 8192)
 ARR = dict(COO_ROW=0, ELL_COL=1, ELL_VAL=2, SELL_PERM=3, SELL_CHUNK_LEN=4, SELL_CHUNK_PTR=5,
            SELL_COL=6, SELL_VAL=7, HYB_ELL_COL=8, HYB_ELL_VAL=9, HYB_COO_ROW=10,
-           HYB_COO_COL=11, HYB_COO_VAL=12)
+           HYB_COO_COL=11, HYB_COO_VAL=12, DIA_OFFSETS=13, DIA_VAL=14)
 
 
 class CascadeError(RuntimeError):
@@ -93,6 +93,23 @@ class SolveInfo(Structure):
                     t_spmv_ms=self.t_spmv_ms)
 
 
+class ServerOpts(Structure):
+    _fields_ = [("tol", c_double), ("inner_tol", c_double), ("restart", c_int32),
+                ("maxit", c_int32), ("small_max_n", c_int32), ("max_batch", c_int32),
+                ("lanes", c_int32), ("mode", c_int32), ("mem_budget", c_int64)]
+
+
+class Request(Structure):
+    _fields_ = [("id", c_int64), ("mat", c_void_p), ("solver", c_int32), ("reserved", c_int32),
+                ("b", c_void_p), ("x", c_void_p)]
+
+
+class Result(Structure):
+    _fields_ = [("id", c_int64), ("status", c_int32), ("iters", c_int32), ("batched", c_int32),
+                ("lane", c_int32), ("relres_true", c_double), ("t_submit_ms", c_double),
+                ("t_start_ms", c_double), ("t_done_ms", c_double)]
+
+
 _p = c_void_p
 _SIGS = {
     "cp_config_default": (None, [POINTER(Config)]),
@@ -126,6 +143,14 @@ _SIGS = {
     "cp_predict": (c_int32, [_p, _p, POINTER(Config), _p]),
     "cp_solve_cg": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_solve_gmres": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
+    "cp_batch_solve": (c_int32, [_p, c_int32, _p, _p, _p, _p, POINTER(SolveOpts), c_int32,
+                                 _p]),
+    "cp_server_opts_default": (None, [POINTER(ServerOpts)]),
+    "cp_server_create": (c_int32, [_p, POINTER(ServerOpts), POINTER(_p)]),
+    "cp_server_submit": (c_int32, [_p, POINTER(Request)]),
+    "cp_server_poll": (c_int32, [_p, _p, c_int32, POINTER(c_int32)]),
+    "cp_server_drain": (c_int32, [_p, c_double]),
+    "cp_server_destroy": (c_int32, [_p]),
 }
 
 _lib = None
@@ -281,6 +306,22 @@ class Context:
         _check(lib().cp_adam_step(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m),
                                   _ptr(v), t, lr, b1, b2, eps))
 
+    def batch_solve(self, mats, solvers, bs, xs, opts=None, threads=0, raise_on_error=True):
+        """cp_batch_solve: many small systems in one persistent launch.  mats:
+        Matrix list; solvers: 0 (CG) / 1 (GMRES) per system; bs, xs: torch CUDA
+        float64 tensors (xs: x0 in, solutions out).  Returns the SolveInfo list."""
+        n = len(mats)
+        hm = (c_void_p * n)(*[m._h.value for m in mats])
+        hs = np.ascontiguousarray(solvers, np.int32)
+        hb = (c_void_p * n)(*[t.data_ptr() for t in bs])
+        hx = (c_void_p * n)(*[t.data_ptr() for t in xs])
+        infos = (SolveInfo * n)()
+        o = opts if opts is not None else default_opts(precision=PREC_FP32_IR)
+        st = lib().cp_batch_solve(self._h, n, hm, _ptr(hs), hb, hx, byref(o), threads, infos)
+        if raise_on_error:
+            _check(st)
+        return list(infos)
+
     @staticmethod
     def mlp_nparams(d, h1, h2, k):
         return int(lib().cp_mlp_nparams(d, h1, h2, k))
@@ -369,3 +410,46 @@ class Matrix:
     def solve_gmres(self, b, x, opts=None, force=None, raise_on_error=True) -> SolveInfo:
         """Restarted GMRES(m) on torch CUDA float64 tensors b, x."""
         return self._solve(lib().cp_solve_gmres, b, x, opts, force, raise_on_error)
+
+
+class Server:
+    """cp_server_*: continuous-batching solve server on a context's device."""
+
+    def __init__(self, ctx: Context, **opts):
+        self.ctx = ctx
+        o = ServerOpts()
+        lib().cp_server_opts_default(byref(o))
+        for k, v in opts.items():
+            setattr(o, k, v)
+        self.opts = o
+        self._h = c_void_p()
+        _check(lib().cp_server_create(ctx.handle, byref(o), byref(self._h)))
+        self._keep = {}
+
+    def submit(self, rid, mat: Matrix, solver, b, x):
+        r = Request(rid, mat._h.value, solver, 0, b.data_ptr(), x.data_ptr())
+        self._keep[rid] = (mat, b, x)
+        _check(lib().cp_server_submit(self._h, byref(r)))
+
+    def poll(self, capacity=4096):
+        out = (Result * capacity)()
+        cnt = c_int32()
+        _check(lib().cp_server_poll(self._h, out, capacity, byref(cnt)))
+        res = [out[i] for i in range(cnt.value)]
+        for r in res:
+            self._keep.pop(r.id, None)
+        return res
+
+    def drain(self, timeout_s=600.0):
+        _check(lib().cp_server_drain(self._h, timeout_s))
+
+    def close(self):
+        if self._h:
+            lib().cp_server_destroy(self._h)
+            self._h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

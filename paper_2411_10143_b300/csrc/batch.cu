@@ -1,0 +1,473 @@
+// Batched persistent solves: many small systems in one launch.
+//
+// One thread block solves one system at a time and takes the next from a
+// device work counter until the batch is empty (a persistent launch: the grid
+// is sized to the resident capacity, not to the batch).  Each system runs FP64
+// iterative refinement around FP32 inner solves, CG or GMRES(m) per system:
+// the FP64 residual r = b - A x, the refinement update and GMRES's Givens /
+// least-squares step in FP64, the SpMV and Krylov vectors in FP32.  Every
+// reduction is a block reduction; no host round trip happens inside a solve.
+// The launch is captured in a CUDA graph and replayed for later batches of the
+// same shape.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.cuh"
+
+namespace cp {
+
+constexpr int kBatchMaxM = 32;  // GMRES restart length limit inside a block
+
+struct BatchSys {
+  int64_t n;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  const float* val32;
+  const double* b;
+  double* x;
+  double* r;     // [n] FP64 residual
+  float* w32;    // FP32 workspace: CG 4n (r, d, p, ap); GMRES (m + 2) n (V, d)
+  int solver;    // 0 CG, 1 GMRES
+};
+
+struct BatchOut {
+  int status;
+  int outer;
+  int inner;
+  double relres;
+};
+
+struct BatchParams {
+  double tol, inner_tol;
+  int max_outer, max_inner, m;
+};
+
+// ------------------------------------------------------------------ block helpers
+template <int BT>
+__device__ __forceinline__ double bsum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = lane < BT / 32 ? red[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// FP64 residual r = b - A x (FP64 values) and ||r||^2
+template <int BT>
+__device__ double resid64(const BatchSys& S, double* red) {
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < S.n; i += BT) {
+    double s = 0.0;
+    for (int k = S.rowptr[i]; k < S.rowptr[i + 1]; ++k) s = fma(S.val[k], S.x[S.col[k]], s);
+    const double ri = S.b[i] - s;
+    S.r[i] = ri;
+    acc = fma(ri, ri, acc);
+  }
+  return bsum<BT>(acc, red);
+}
+
+// y = A32 v (FP32)
+template <int BT>
+__device__ __forceinline__ void spmv32(const BatchSys& S, const float* v, float* y) {
+  for (int64_t i = threadIdx.x; i < S.n; i += BT) {
+    float s = 0.f;
+    for (int k = S.rowptr[i]; k < S.rowptr[i + 1]; ++k) s = fmaf(S.val32[k], v[S.col[k]], s);
+    y[i] = s;
+  }
+}
+
+// ------------------------------------------------------------------ inner CG (FP32)
+template <int BT>
+__device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, double* red) {
+  const int64_t n = S.n;
+  float* r = S.w32;
+  float* d = r + n;
+  float* p = d + n;
+  float* ap = p + n;
+  double rr = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += BT) {
+    const float ri = __double2float_rn(S.r[i]);
+    r[i] = ri;
+    p[i] = ri;
+    d[i] = 0.f;
+    rr = fma((double)ri, (double)ri, rr);
+  }
+  rr = bsum<BT>(rr, red);
+  const double stop = P.inner_tol * P.inner_tol * rr;
+  int it = 0;
+  while (it < budget && rr > stop) {
+    __syncthreads();
+    spmv32<BT>(S, p, ap);
+    __syncthreads();
+    double pap = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += BT) pap += (double)p[i] * (double)ap[i];
+    pap = bsum<BT>(pap, red);
+    if (!(pap > 0.0)) return -1 - it;  // breakdown: not SPD
+    const float alpha = (float)(rr / pap);
+    double rn = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += BT) {
+      d[i] = fmaf(alpha, p[i], d[i]);
+      const float ri = fmaf(-alpha, ap[i], r[i]);
+      r[i] = ri;
+      rn = fma((double)ri, (double)ri, rn);
+    }
+    rn = bsum<BT>(rn, red);
+    const float beta = (float)(rn / rr);
+    rr = rn;
+    for (int64_t i = threadIdx.x; i < n; i += BT) p[i] = fmaf(beta, p[i], r[i]);
+    ++it;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += BT) S.x[i] += (double)d[i];
+  return it;
+}
+
+// ------------------------------------------------------------------ inner GMRES (FP32 basis)
+template <int BT>
+__device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, double* red,
+                           double* Hs /*(m+1)*m*/, double* gs /*m+1*/, double* cs, double* sn,
+                           double* hv /*m+1*/, float* acc_red /*32*(BT/32)*/) {
+  const int64_t n = S.n;
+  const int m = P.m;
+  float* V = S.w32;               // (m+1) columns of n
+  float* d = V + (int64_t)(m + 1) * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // inner rhs r32 = (float) r, x0 = 0: V0 = r32 / ||r32||
+  double bb = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += BT) {
+    const float ri = __double2float_rn(S.r[i]);
+    V[i] = ri;
+    d[i] = 0.f;
+    bb = fma((double)ri, (double)ri, bb);
+  }
+  bb = bsum<BT>(bb, red);
+  const double stop = P.inner_tol * sqrt(bb);
+  int it = 0;
+  double beta = sqrt(bb);
+  bool first = true;
+  while (it < budget) {
+    if (!first) {  // restart: V0 = r32 - A d
+      __syncthreads();
+      spmv32<BT>(S, d, V + n);  // scratch column 1
+      __syncthreads();
+      double s = 0.0;
+      for (int64_t i = threadIdx.x; i < n; i += BT) {
+        const float v0 = __double2float_rn(S.r[i]) - V[n + i];
+        V[i] = v0;
+        s = fma((double)v0, (double)v0, s);
+      }
+      beta = sqrt(bsum<BT>(s, red));
+    }
+    first = false;
+    if (beta <= stop || beta == 0.0) break;
+    const float inv = (float)(1.0 / beta);
+    for (int64_t i = threadIdx.x; i < n; i += BT) V[i] *= inv;
+    if (threadIdx.x == 0) {
+      for (int q = 0; q <= m; ++q) gs[q] = 0.0;
+      gs[0] = beta;
+    }
+    int jd = 0;
+    bool conv = false;
+    for (int j = 0; j < m && it < budget; ++j) {
+      float* w = V + (int64_t)(j + 1) * n;
+      __syncthreads();
+      spmv32<BT>(S, V + (int64_t)j * n, w);
+      if (threadIdx.x <= j) hv[threadIdx.x] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        __syncthreads();
+        float a[kBatchMaxM];
+#pragma unroll
+        for (int c = 0; c < kBatchMaxM; ++c) a[c] = 0.f;
+        for (int64_t i = threadIdx.x; i < n; i += BT) {
+          const float wi = w[i];
+#pragma unroll
+          for (int c = 0; c < kBatchMaxM; ++c)
+            if (c <= j) a[c] = fmaf(V[(int64_t)c * n + i], wi, a[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kBatchMaxM; ++c) a[c] = warp_sum(a[c]);
+        if (lane == 0)
+#pragma unroll
+          for (int c = 0; c < kBatchMaxM; ++c) acc_red[c * (BT / 32) + warp] = a[c];
+        __syncthreads();
+        if (threadIdx.x <= j) {
+          double s = 0.0;
+          for (int q = 0; q < BT / 32; ++q) s += (double)acc_red[threadIdx.x * (BT / 32) + q];
+          red[64 + threadIdx.x] = s;  // this pass's coefficient
+          hv[threadIdx.x] += s;
+        }
+        __syncthreads();
+        double wn = 0.0;
+        for (int64_t i = threadIdx.x; i < n; i += BT) {
+          float wi = w[i];
+          for (int c = 0; c <= j; ++c) wi = fmaf(-(float)red[64 + c], V[(int64_t)c * n + i], wi);
+          w[i] = wi;
+          wn = fma((double)wi, (double)wi, wn);
+        }
+        wn = bsum<BT>(wn, red);
+        if (pass == 1 && threadIdx.x == 0) red[40] = wn;
+      }
+      // Givens rotation in FP64 (thread 0)
+      if (threadIdx.x == 0) {
+        const double hn = sqrt(red[40]);
+        for (int i = 0; i <= j; ++i) Hs[i * m + j] = hv[i];
+        for (int i = 0; i < j; ++i) {
+          const double a0 = Hs[i * m + j], b0 = Hs[(i + 1) * m + j];
+          Hs[i * m + j] = cs[i] * a0 + sn[i] * b0;
+          Hs[(i + 1) * m + j] = -sn[i] * a0 + cs[i] * b0;
+        }
+        const double a0 = Hs[j * m + j];
+        const double den = sqrt(a0 * a0 + hn * hn);
+        cs[j] = den == 0.0 ? 1.0 : a0 / den;
+        sn[j] = den == 0.0 ? 0.0 : hn / den;
+        Hs[j * m + j] = cs[j] * a0 + sn[j] * hn;
+        gs[j + 1] = -sn[j] * gs[j];
+        gs[j] = cs[j] * gs[j];
+        red[41] = hn;
+        red[42] = fabs(gs[j + 1]);
+      }
+      __syncthreads();
+      const double hn = red[41];
+      ++it;
+      jd = j + 1;
+      if (red[42] <= stop || hn == 0.0) {
+        conv = red[42] <= stop;
+        break;
+      }
+      const float inv2 = (float)(1.0 / hn);
+      for (int64_t i = threadIdx.x; i < n; i += BT) w[i] *= inv2;
+    }
+    // y = R^{-1} g, d += V y
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = jd - 1; i >= 0; --i) {
+        double s = gs[i];
+        for (int k = i + 1; k < jd; ++k) s -= Hs[i * m + k] * hv[k];
+        hv[i] = s / Hs[i * m + i];  // hv reused as y
+      }
+    }
+    __syncthreads();
+    for (int64_t i = threadIdx.x; i < n; i += BT) {
+      float di = d[i];
+      for (int c = 0; c < jd; ++c) di = fmaf((float)hv[c], V[(int64_t)c * n + i], di);
+      d[i] = di;
+    }
+    if (conv) break;
+  }
+  __syncthreads();
+  for (int64_t i = threadIdx.x; i < n; i += BT) S.x[i] += (double)d[i];
+  return it;
+}
+
+// ------------------------------------------------------------------ the persistent kernel
+template <int BT>
+__global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__ sys, int nsys,
+                                                    const int* __restrict__ order,
+                                                    int* __restrict__ next, BatchParams P,
+                                                    BatchOut* __restrict__ out) {
+  __shared__ double red[64 + kBatchMaxM + 1];
+  __shared__ double Hs[(kBatchMaxM + 1) * kBatchMaxM];
+  __shared__ double gs[kBatchMaxM + 1], cs[kBatchMaxM], sn[kBatchMaxM], hv[kBatchMaxM + 1];
+  __shared__ float acc_red[kBatchMaxM * (BT / 32)];
+  __shared__ int s_id;
+  for (;;) {
+    if (threadIdx.x == 0) s_id = atomicAdd(next, 1);
+    __syncthreads();
+    const int q = s_id;
+    __syncthreads();
+    if (q >= nsys) break;
+    const int id = order[q];
+    const BatchSys S = sys[id];
+    double bb = 0.0;
+    for (int64_t i = threadIdx.x; i < S.n; i += BT) bb = fma(S.b[i], S.b[i], bb);
+    bb = bsum<BT>(bb, red);
+    int outer = 0, inner = 0, status = CP_OK;
+    double rr = 0.0;
+    for (;;) {
+      __syncthreads();
+      rr = resid64<BT>(S, red);
+      if (bb == 0.0 || rr <= P.tol * P.tol * bb) break;
+      if (!isfinite(rr)) {
+        status = CP_ERR_BREAKDOWN;
+        break;
+      }
+      if (outer >= P.max_outer || inner >= P.max_inner) {
+        status = CP_ERR_NOT_CONVERGED;
+        break;
+      }
+      __syncthreads();
+      const int budget = P.max_inner - inner;
+      int got = S.solver == 0 ? inner_cg<BT>(S, P, budget, red)
+                              : inner_gmres<BT>(S, P, budget, red, Hs, gs, cs, sn, hv, acc_red);
+      if (got < 0) {
+        status = CP_ERR_BREAKDOWN;
+        inner += -got - 1;
+        break;
+      }
+      inner += got;
+      ++outer;
+    }
+    if (threadIdx.x == 0) {
+      out[id].status = status;
+      out[id].outer = outer;
+      out[id].inner = inner;
+      out[id].relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ host
+struct BatchPlan {
+  int threads = 256;
+};
+
+template <int BT>
+static void launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const int* d_order,
+                         int* d_next, const BatchParams& P, BatchOut* d_out, cudaStream_t s) {
+  int per_sm = 0;
+  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT>, BT, 0));
+  int grid = ctx->num_sms * std::max(per_sm, 1);
+  if (grid > nsys) grid = nsys;
+  // capture the single persistent launch in a graph and replay it
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaStream_t cap = nullptr;
+  CP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+  try {
+    CP_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    k_batch_solve<BT><<<grid, BT, 0, cap>>>(d_sys, nsys, d_order, d_next, P, d_out);
+    CP_CUDA(cudaStreamEndCapture(cap, &g));
+    CP_CUDA(cudaGraphInstantiate(&ge, g, 0));
+    ctx->launches.fetch_add(1, std::memory_order_relaxed);
+    CP_CUDA(cudaGraphLaunch(ge, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    if (ge) cudaGraphExecDestroy(ge);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    throw;
+  }
+  cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  cudaStreamDestroy(cap);
+}
+
+void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
+                 const double* const* b, double* const* x, const cp_solve_opts* o,
+                 cp_solve_info* infos, int threads) {
+  CP_REQUIRE(nsys >= 1 && mats && solver && b && x, CP_ERR_INVALID, "bad batch arguments");
+  cp_solve_opts opt;
+  cp_solve_opts_default(&opt);
+  if (o) opt = *o;
+  CP_REQUIRE(opt.restart >= 1 && opt.restart <= kBatchMaxM, CP_ERR_INVALID,
+             "batched GMRES restart must be in 1..%d", kBatchMaxM);
+  CP_REQUIRE(threads == 0 || threads == 128 || threads == 256 || threads == 512 || threads == 1024,
+             CP_ERR_INVALID, "threads per system must be 128, 256, 512 or 1024");
+  cudaStream_t s = ctx->main;
+  cp_config csr;
+  cp_config_default(&csr);
+  std::vector<BatchSys> hs(nsys);
+  int64_t ws64 = 0, ws32 = 0;
+  int64_t total_rows = 0;
+  for (int i = 0; i < nsys; ++i) {
+    cp_mat* m = mats[i];
+    CP_REQUIRE(m && m->nrows == m->ncols && b[i] && x[i], CP_ERR_INVALID,
+               "system %d: NULL or non-square", i);
+    CP_REQUIRE(solver[i] == 0 || solver[i] == 1, CP_ERR_INVALID, "system %d: solver must be 0/1",
+               i);
+    ensure_val32(ctx, m, csr, s);
+    ws64 += m->nrows;
+    ws32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
+    total_rows += m->nrows;
+  }
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  BatchSys* d_sys = nullptr;
+  int* d_order = nullptr;
+  BatchOut* d_out = nullptr;
+  try {
+    d64 = dalloc<double>(ws64);
+    d32 = dalloc<float>(ws32);
+    int64_t o64 = 0, o32 = 0;
+    for (int i = 0; i < nsys; ++i) {
+      cp_mat* m = mats[i];
+      hs[i] = BatchSys{m->nrows, m->rowptr, m->col, m->val, m->val32, b[i], x[i],
+                       d64 + o64, d32 + o32, solver[i]};
+      o64 += m->nrows;
+      o32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
+    }
+    // largest systems first, so the dynamic queue ends with short jobs
+    std::vector<int> order(nsys);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      return hs[a].n * (hs[a].solver ? 3 : 1) > hs[c].n * (hs[c].solver ? 3 : 1);
+    });
+    d_sys = dalloc<BatchSys>(nsys);
+    d_order = dalloc<int>(nsys + 1);  // last slot: the work counter
+    d_out = dalloc<BatchOut>(nsys);
+    CP_CUDA(cudaMemcpyAsync(d_sys, hs.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice, s));
+    CP_CUDA(cudaMemcpyAsync(d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
+    CP_CUDA(cudaMemsetAsync(d_order + nsys, 0, sizeof(int), s));
+    BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart};
+    int bt = threads;
+    if (bt == 0) {  // default: block size from the mean system size
+      const int64_t mean = total_rows / nsys;
+      bt = mean < 2048 ? 128 : mean < 16384 ? 256 : mean < 131072 ? 512 : 1024;
+    }
+    switch (bt) {
+      case 128: launch_batch<128>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
+      case 256: launch_batch<256>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
+      case 512: launch_batch<512>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
+      default: launch_batch<1024>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
+    }
+    std::vector<BatchOut> out(nsys);
+    CP_CUDA(cudaMemcpy(out.data(), d_out, nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost));
+    int worst = CP_OK;
+    for (int i = 0; i < nsys; ++i) {
+      if (infos) {
+        std::memset(&infos[i], 0, sizeof(cp_solve_info));
+        infos[i].iters = out[i].inner;
+        infos[i].outer_iters = out[i].outer;
+        infos[i].relres_true = out[i].relres;
+        infos[i].status = out[i].status;
+        infos[i].switch_iter[0] = infos[i].switch_iter[1] = infos[i].switch_iter[2] = -1;
+        infos[i].final_cfg = csr;
+      }
+      if (out[i].status != CP_OK && worst == CP_OK) worst = out[i].status;
+    }
+    dfree(d64);
+    dfree(d32);
+    dfree(d_sys);
+    dfree(d_order);
+    dfree(d_out);
+    d64 = nullptr;
+    d32 = nullptr;
+    d_sys = nullptr;
+    d_order = nullptr;
+    d_out = nullptr;
+    CP_REQUIRE(worst == CP_OK, (cp_status)worst, "a batched system did not converge (status %d)",
+               worst);
+  } catch (...) {
+    dfree(d64);
+    dfree(d32);
+    dfree(d_sys);
+    dfree(d_order);
+    dfree(d_out);
+    throw;
+  }
+}
+
+}  // namespace cp

@@ -284,6 +284,16 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* m, const double* b, double* x,
   });
 }
 
+cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
+                         const double* const* b, double* const* x, const cp_solve_opts* opts,
+                         int32_t threads, cp_solve_info* infos) {
+  return guard([&] {
+    CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
+    use_device(ctx);
+    batch_solve(ctx, nsys, mats, solver, b, x, opts, infos, threads);
+  });
+}
+
 int64_t cp_mlp_nparams(int32_t d, int32_t h1, int32_t h2, int32_t k) {
   return (int64_t)h1 * d + h1 + (int64_t)h2 * h1 + h2 + (int64_t)k * h2 + k;
 }

@@ -276,6 +276,7 @@ __global__ void k_features_final(int64_t n, int64_t ncols, int64_t nnz, const Fe
 }
 
 void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15) {
+  std::lock_guard<std::mutex> lock(m->feat_mu);
   if (m->has_features) {
     std::memcpy(out15, m->features, sizeof(m->features));
     return;
@@ -534,6 +535,57 @@ __global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __res
     b[i] = __double2float_rn(a[i]);
 }
 
+// DIA conversion: mark the offsets present, compact them in ascending order
+// (word popcounts -> exclusive scan -> each word writes its bits), then scatter
+// every entry to its diagonal through an offset -> diagonal lookup table.
+__global__ void __launch_bounds__(kBlock) k_dia_mark(int64_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci,
+                                                     unsigned* __restrict__ bm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) mark_diag(bm, (int64_t)ci[k] - i + (n - 1));
+}
+
+__global__ void k_dia_wordcount(int64_t words, const unsigned* __restrict__ bm,
+                                int64_t* __restrict__ cnt) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x)
+    cnt[w] = __popc(bm[w]);
+}
+
+__global__ void k_dia_compact(int64_t n, int64_t words, const unsigned* __restrict__ bm,
+                              const int64_t* __restrict__ pos, int32_t* __restrict__ offs,
+                              int32_t* __restrict__ lut, int64_t cap) {
+  for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words;
+       w += (int64_t)gridDim.x * blockDim.x) {
+    unsigned bits = bm[w];
+    int64_t q = pos[w];
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1;
+      const int64_t o = w * 32 + b;  // offset + (n - 1)
+      if (q < cap) {
+        offs[q] = (int32_t)(o - (n - 1));
+        lut[o] = (int32_t)q;
+      }
+      ++q;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_dia_fill(int64_t n, const int32_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ ci,
+                                                     const double* __restrict__ v,
+                                                     const int32_t* __restrict__ lut,
+                                                     double* __restrict__ data) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+      const int64_t d = lut[(int64_t)ci[k] - i + (n - 1)];
+      data[d * n + i] = v[k];
+    }
+}
+
 // ------------------------------------------------------------------ host side
 void config_check(const cp_config& c) {
   CP_REQUIRE(c.fmt >= 0 && c.fmt < CP_NUM_FMT, CP_ERR_UNSUPPORTED, "unknown format %d", c.fmt);
@@ -601,13 +653,16 @@ static void free_sell(SellPart& s) {
   s = SellPart{};
 }
 
+static void free_dia(DiaPart& d);
+
 void free_formats(cp_mat* m) {
   free_coo(m->coo);
   free_ell(m->ell);
   free_sell(m->sell);
   free_ell(m->hyb_ell);
   free_coo(m->hyb_coo);
-  m->has_coo = m->has_ell = m->has_sell = m->has_hyb = false;
+  free_dia(m->dia);
+  m->has_coo = m->has_ell = m->has_sell = m->has_hyb = m->has_dia = false;
   dfree(m->merge_carry_row);
   dfree(m->merge_carry_val);
   m->merge_carry_row = nullptr;
@@ -752,6 +807,60 @@ static void convert_hyb(cp_ctx* ctx, cp_mat* m, int64_t K, cudaStream_t s) {
   m->has_hyb = true;
 }
 
+static void free_dia(DiaPart& d) {
+  dfree(d.offs);
+  dfree(d.val);
+  dfree(d.val32);
+  d = DiaPart{};
+}
+
+static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
+  const int64_t n = m->nrows;
+  const int64_t span = n + m->ncols - 1;
+  const int64_t words = (span + 31) / 32;
+  DiaPart d;
+  unsigned* bm = nullptr;
+  int64_t *cnt = nullptr, *pos = nullptr;
+  int32_t* lut = nullptr;
+  try {
+    bm = dalloc<unsigned>(words);
+    cnt = dalloc<int64_t>(words);
+    pos = dalloc<int64_t>(words + 1);
+    lut = dalloc<int32_t>(span);
+    d.offs = dalloc<int32_t>(kDiaMax);
+    CP_CUDA(cudaMemsetAsync(bm, 0, words * sizeof(unsigned), s));
+    CP_LAUNCH(ctx, k_dia_mark, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, bm);
+    CP_LAUNCH(ctx, k_dia_wordcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, cnt);
+    exclusive_scan_i64(ctx, cnt, pos, words, s);
+    CP_LAUNCH(ctx, k_dia_compact, grid_cap(ctx, words), kBlock, 0, s, n, words, bm, pos, d.offs,
+              lut, (int64_t)kDiaMax);
+    CP_CUDA(cudaMemcpyAsync(&d.ndiag, pos + words, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    CP_CUDA(cudaStreamSynchronize(s));
+    CP_REQUIRE(d.ndiag <= kDiaMax, CP_ERR_FOOTPRINT,
+               "DIA needs %lld diagonals, more than the %d it accepts", (long long)d.ndiag,
+               kDiaMax);
+    check_budget(ctx, d.ndiag * n * 8, "DIA");
+    d.val = dalloc<double>(d.ndiag * n);
+    CP_CUDA(cudaMemsetAsync(d.val, 0, d.ndiag * n * sizeof(double), s));
+    CP_LAUNCH(ctx, k_dia_fill, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, m->val, lut,
+              d.val);
+    CP_CUDA(cudaStreamSynchronize(s));
+  } catch (...) {
+    dfree(bm);
+    dfree(cnt);
+    dfree(pos);
+    dfree(lut);
+    free_dia(d);
+    throw;
+  }
+  dfree(bm);
+  dfree(cnt);
+  dfree(pos);
+  dfree(lut);
+  m->dia = d;
+  m->has_dia = true;
+}
+
 static void prepare_merge(cp_ctx* ctx, cp_mat* m) {
   (void)ctx;
   const int64_t tiles = (m->nrows + m->nnz + kBlock * 7 - 1) / (kBlock * 7);
@@ -784,6 +893,9 @@ void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s)
       if (!m->has_hyb || m->hyb_ell.K != K) convert_hyb(ctx, m, K, s);
       break;
     }
+    case CP_FMT_DIA:
+      if (!m->has_dia) convert_dia(ctx, m, s);
+      break;
   }
 }
 
@@ -811,6 +923,9 @@ void ensure_val32(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s) 
         m->hyb_ell.val32 = cast_copy(ctx, m->hyb_ell.val, m->hyb_ell.K * m->hyb_ell.ld, s);
       if (!m->hyb_coo.val32) m->hyb_coo.val32 = cast_copy(ctx, m->hyb_coo.val, m->hyb_coo.n, s);
       break;
+    case CP_FMT_DIA:
+      if (!m->dia.val32) m->dia.val32 = cast_copy(ctx, m->dia.val, m->dia.ndiag * m->nrows, s);
+      break;
   }
   CP_CUDA(cudaStreamSynchronize(s));
 }
@@ -836,6 +951,10 @@ void format_dims(cp_mat* m, const cp_config& cfg, int64_t dims[4]) {
     case CP_FMT_COO:
       dims[0] = m->nnz;
       break;
+    case CP_FMT_DIA:
+      dims[0] = m->dia.ndiag;
+      dims[1] = m->nrows;
+      break;
     default:
       break;
   }
@@ -859,6 +978,8 @@ void format_export(cp_mat* m, const cp_config& cfg, int id, void* dst, int64_t c
     case CP_ARR_HYB_COO_ROW: src = m->hyb_coo.row; nb = m->hyb_coo.n * 4; break;
     case CP_ARR_HYB_COO_COL: src = m->hyb_coo.col; nb = m->hyb_coo.n * 4; break;
     case CP_ARR_HYB_COO_VAL: src = m->hyb_coo.val; nb = m->hyb_coo.n * 8; break;
+    case CP_ARR_DIA_OFFSETS: src = m->dia.offs; nb = m->dia.ndiag * 4; break;
+    case CP_ARR_DIA_VAL: src = m->dia.val; nb = m->dia.ndiag * m->nrows * 8; break;
     default: CP_REQUIRE(false, CP_ERR_INVALID, "unknown array id %d", id);
   }
   (void)cfg;

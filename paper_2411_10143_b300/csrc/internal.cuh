@@ -94,6 +94,14 @@ struct SellPart {
   float* val32 = nullptr;
 };
 
+struct DiaPart {
+  int64_t ndiag = 0;
+  int32_t* offs = nullptr;  // ascending col - row
+  double* val = nullptr;    // [ndiag][nrows]
+  float* val32 = nullptr;
+};
+constexpr int kDiaMax = 1024;  // most diagonals a DIA conversion accepts
+
 }  // namespace cp
 
 struct cp_ctx {
@@ -115,19 +123,21 @@ struct cp_mat {
   int32_t* col = nullptr;
   double* val = nullptr;
   float* val32 = nullptr;  // FP32 copy of val, made on first FP32 use
-  bool has_coo = false, has_ell = false, has_sell = false, has_hyb = false;
+  bool has_coo = false, has_ell = false, has_sell = false, has_hyb = false, has_dia = false;
   cp::CooPart coo;
   cp::EllPart ell;
   cp::SellPart sell;
   cp::EllPart hyb_ell;
   cp::CooPart hyb_coo;
+  cp::DiaPart dia;
   bool has_features = false;
   double features[15] = {0};
   // merge-path scratch: one carry (row, value) per tile
   int32_t* merge_carry_row = nullptr;
   double* merge_carry_val = nullptr;
   int64_t merge_tiles = 0;
-  std::mutex mu;  // serialises conversions issued by the side thread and the caller
+  std::mutex mu;       // serialises conversions issued by the side thread and the caller
+  std::mutex feat_mu;  // serialises the feature computation
 };
 
 namespace cp {
@@ -219,6 +229,10 @@ void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host,
                  const int32_t* lab_host, int h1, int h2, int k, int epochs, float lr,
                  uint64_t seed, float* final_loss);
 int64_t scratch_floats_api(int64_t N, int d, int h1, int h2, int k);
+
+void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
+                 const double* const* b, double* const* x, const cp_solve_opts* o,
+                 cp_solve_info* infos, int threads);
 
 // The solve entry (CG or GMRES; FP64 or FP32-inner refinement; plain,
 // sequential or asynchronous prediction).

@@ -94,6 +94,13 @@ __global__ void k_cg_init_final(const double* __restrict__ pr, const double* __r
   }
 }
 
+// The two CG vector kernels move pairs of values (16-byte FP64 / 8-byte FP32
+// loads) in tiles of kBlock * kVecU pairs per block.  Each block issues the
+// loads of its first tile before it sums the previous kernel's partials, so
+// the reduction's latency hides behind the DRAM latency.  An odd last element
+// is handled by block 0.
+constexpr int kVecU = 2;
+
 // alpha = (r,r)/(Ap,p); x += alpha p; r -= alpha Ap; partials of (r,r).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, T* __restrict__ x,
@@ -103,6 +110,29 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, T* __restrict__
                                                       CgState* st, int slot,
                                                       double* __restrict__ pb, Mirror* mir) {
   if (*(volatile int*)&st->done) return;
+  using V = typename Vec2<T>::type;
+  V* __restrict__ x2 = reinterpret_cast<V*>(x);
+  V* __restrict__ r2 = reinterpret_cast<V*>(r);
+  const V* __restrict__ p2 = reinterpret_cast<const V*>(p);
+  const V* __restrict__ a2 = reinterpret_cast<const V*>(ap);
+  const int64_t n2 = n >> 1;
+  const int64_t tile = (int64_t)blockDim.x * kVecU;
+  const int64_t ntiles = (n2 + tile - 1) / tile;
+  V xv[kVecU], rv[kVecU], pv[kVecU], av[kVecU];
+  int64_t t = blockIdx.x;
+  auto load = [&](int64_t tt) {
+#pragma unroll
+    for (int u = 0; u < kVecU; ++u) {
+      const int64_t idx = tt * tile + (int64_t)u * blockDim.x + threadIdx.x;
+      if (idx < n2) {
+        xv[u] = x2[idx];
+        rv[u] = r2[idx];
+        pv[u] = p2[idx];
+        av[u] = a2[idx];
+      }
+    }
+  };
+  if (t < ntiles) load(t);
   __shared__ double red[40];
   const double pap = reduce_partials(pa, PA, red);
   const double rr = st->rr[slot];
@@ -122,30 +152,30 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, T* __restrict__
     st->alpha = alpha_d;
   }
   T acc = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    T pv[4], av[4], xv[4], rv[4];
+  for (; t < ntiles; t += gridDim.x) {
+    if (t != blockIdx.x) load(t);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      pv[u] = p[i + u * stride];
-      av[u] = ap[i + u * stride];
-      xv[u] = x[i + u * stride];
-      rv[u] = r[i + u * stride];
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      x[i + u * stride] = fma(alpha, pv[u], xv[u]);
-      const T rn = fma(-alpha, av[u], rv[u]);
-      r[i + u * stride] = rn;
-      acc = fma(rn, rn, acc);
+    for (int u = 0; u < kVecU; ++u) {
+      const int64_t idx = t * tile + (int64_t)u * blockDim.x + threadIdx.x;
+      if (idx < n2) {
+        V xn, rn;
+        xn.x = fma(alpha, pv[u].x, xv[u].x);
+        xn.y = fma(alpha, pv[u].y, xv[u].y);
+        rn.x = fma(-alpha, av[u].x, rv[u].x);
+        rn.y = fma(-alpha, av[u].y, rv[u].y);
+        x2[idx] = xn;
+        r2[idx] = rn;
+        acc = fma(rn.x, rn.x, acc);
+        acc = fma(rn.y, rn.y, acc);
+      }
     }
   }
-  for (; i < n; i += stride) {
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int64_t i = n - 1;
     x[i] = fma(alpha, p[i], x[i]);
-    const T rn = fma(-alpha, ap[i], r[i]);
-    r[i] = rn;
-    acc = fma(rn, rn, acc);
+    const T ri = fma(-alpha, ap[i], r[i]);
+    r[i] = ri;
+    acc = fma(ri, ri, acc);
   }
   const double s = block_sum((double)acc, red);
   if (threadIdx.x == 0) pb[blockIdx.x] = s;
@@ -159,6 +189,26 @@ __global__ void __launch_bounds__(kBlock) k_cg_direction(int64_t n, const T* __r
                                                          CgState* st, int slot, double tol2,
                                                          Mirror* mir) {
   if (*(volatile int*)&st->done) return;
+  using V = typename Vec2<T>::type;
+  const V* __restrict__ r2 = reinterpret_cast<const V*>(r);
+  V* __restrict__ p2 = reinterpret_cast<V*>(p);
+  const int64_t n2 = n >> 1;
+  const int64_t tile = (int64_t)blockDim.x * kVecU * 2;
+  const int64_t ntiles = (n2 + tile - 1) / tile;
+  constexpr int U = kVecU * 2;
+  V rv[U], pv[U];
+  int64_t t = blockIdx.x;
+  auto load = [&](int64_t tt) {
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t idx = tt * tile + (int64_t)u * blockDim.x + threadIdx.x;
+      if (idx < n2) {
+        rv[u] = r2[idx];
+        pv[u] = p2[idx];
+      }
+    }
+  };
+  if (t < ntiles) load(t);
   __shared__ double red[40];
   const double rr_new = reduce_partials(pb, PB, red);
   const double rr = st->rr[slot];
@@ -181,19 +231,20 @@ __global__ void __launch_bounds__(kBlock) k_cg_direction(int64_t n, const T* __r
   if (conv || bad) return;
   const T beta = (T)(rr_new / rr);
   if (blockIdx.x == 0 && threadIdx.x == 0) st->beta = rr_new / rr;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  for (; i + 3 * stride < n; i += 4 * stride) {
-    T rv[4], pv[4];
+  for (; t < ntiles; t += gridDim.x) {
+    if (t != blockIdx.x) load(t);
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      rv[u] = r[i + u * stride];
-      pv[u] = p[i + u * stride];
+    for (int u = 0; u < U; ++u) {
+      const int64_t idx = t * tile + (int64_t)u * blockDim.x + threadIdx.x;
+      if (idx < n2) {
+        V pn;
+        pn.x = fma(beta, pv[u].x, rv[u].x);
+        pn.y = fma(beta, pv[u].y, rv[u].y);
+        p2[idx] = pn;
+      }
     }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) p[i + u * stride] = fma(beta, pv[u], rv[u]);
   }
-  for (; i < n; i += stride) p[i] = fma(beta, p[i], r[i]);
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) p[n - 1] = fma(beta, p[n - 1], r[n - 1]);
 }
 
 // ================================================================== shared small kernels
@@ -423,6 +474,15 @@ static double ms_since(Clock::time_point t0) {
   return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
 }
 
+// blocks for a pair-tiled vector kernel: one tile of kBlock * U pairs per block,
+// capped at the resident capacity (the kernels loop over further tiles)
+static int vec_grid(cp_ctx* ctx, int64_t n, int U) {
+  const int64_t tile = (int64_t)kBlock * U;
+  int64_t g = ((n >> 1) + tile - 1) / tile;
+  if (g > ctx->grid_stream) g = ctx->grid_stream;
+  return (int)(g < 1 ? 1 : g);
+}
+
 static int grid_n(cp_ctx* ctx, int64_t n) {
   int64_t g = (n + kBlock - 1) / kBlock;
   if (g > ctx->grid_stream) g = ctx->grid_stream;
@@ -431,7 +491,7 @@ static int grid_n(cp_ctx* ctx, int64_t n) {
 
 template <typename T>
 struct CgBufs {
-  T *r = nullptr, *p = nullptr, *ap = nullptr;
+  T *r = nullptr, *p = nullptr, *ap = nullptr, *xw = nullptr;
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   CgState* st = nullptr;
 };
@@ -467,6 +527,7 @@ struct Workspace {
       B.r = get<T>(n);
       B.p = get<T>(n);
       B.ap = get<T>(n);
+      B.xw = get<T>(n);
       B.pa = get<double>(kMaxPartials);
       B.pb = get<double>(kMaxPartials);
       B.pc = get<double>(kMaxPartials);
@@ -619,7 +680,16 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
   CP_CUDA(cudaMemsetAsync(st, 0, sizeof(CgState), s));
   const double tol2 = tol * tol;
   const int G = grid_n(ctx, n);
+  // the vector kernels work on pairs in tiles of kBlock * kVecU (update) and
+  // twice that (direction); their grids are capped by the resident capacity
+  const int Gu = vec_grid(ctx, n, kVecU);
+  const int Gd = vec_grid(ctx, n, 2 * kVecU);
   const int* done = &st->done;
+  // work on an internal, 16-byte aligned copy of x (the caller's x may be any view)
+  T* xw = B.xw;
+  CP_CUDA(cudaMemcpyAsync(xw, x, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  T* const x_user = x;
+  x = xw;
   LoopResult res;
   int it = 0;
   bool keep_bb = false;
@@ -635,9 +705,10 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
     for (; it < maxit; ++it) {
       cs.poll(it);
       const int PA = spmv_cur<T>(cs, p, ap, p, pa, done, s);
-      CP_LAUNCH(ctx, k_cg_update<T>, G, kBlock, 0, s, n, x, r, p, ap, pa, PA, st, it & 1, pb,
+      CP_LAUNCH(ctx, k_cg_update<T>, Gu, kBlock, 0, s, n, x, r, p, ap, pa, PA, st, it & 1, pb,
                 mir);
-      CP_LAUNCH(ctx, k_cg_direction<T>, G, kBlock, 0, s, n, r, p, pb, G, st, it & 1, tol2, mir);
+      CP_LAUNCH(ctx, k_cg_direction<T>, Gd, kBlock, 0, s, n, r, p, pb, Gu, st, it & 1, tol2,
+                mir);
       CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
       ++issued;
       if (issued >= depth) {
@@ -673,6 +744,8 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
     }
     x0_zero = false;  // restart from the current x
   }
+  CP_CUDA(cudaMemcpyAsync(x_user, xw, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  CP_CUDA(cudaStreamSynchronize(s));
   return res;
 }
 

@@ -297,6 +297,40 @@ __global__ void __launch_bounds__(kBlock) k_sell(
   write_partial<DOT>((double)acc, partials);
 }
 
+// ------------------------------------------------------------------ DIA
+// Thread per row; the offsets sit in shared memory; values and x are read
+// contiguously across the warp (no index arrays, no gather).
+template <typename T, bool GEN, bool DOT>
+__global__ void __launch_bounds__(kBlock) k_dia(
+    int64_t n, int64_t ncols, int ndiag, const int32_t* __restrict__ offs,
+    const T* __restrict__ dv, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
+    const T* __restrict__ dotv, double* __restrict__ partials, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  __shared__ int32_t so[kDiaMax];
+  for (int d = threadIdx.x; d < ndiag; d += blockDim.x) so[d] = offs[d];
+  __syncthreads();
+  T acc = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T sum = 0;
+    for (int d0 = 0; d0 < ndiag; d0 += 4) {
+      T w[4], xv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t c = i + (d0 + u < ndiag ? so[d0 + u] : 0);
+        const bool in = d0 + u < ndiag && c >= 0 && c < ncols;
+        w[u] = in ? ld_stream(dv + (int64_t)(d0 + u) * n + i) : T(0);
+        xv[u] = in ? ld_ro(x + c) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum = fma(w[u], xv[u], sum);
+    }
+    store_row<T, GEN>(y, i, sum, alpha, beta);
+    if (DOT) acc = fma(sum, dotv[i], acc);
+  }
+  write_partial<DOT>((double)acc, partials);
+}
+
 // ------------------------------------------------------------------ COO (segmented)
 // Each warp takes 32 * kCooPerLane consecutive entries; a segmented warp scan
 // by row sums each row's run and the run's last lane adds it to y atomically.
@@ -364,6 +398,7 @@ template <typename T>
 struct Vals;
 template <>
 struct Vals<double> {
+  static const double* dia(const DiaPart& d) { return d.val; }
   static const double* csr(const cp_mat* m) { return m->val; }
   static const double* ell(const EllPart& e) { return e.val; }
   static const double* sell(const SellPart& s) { return s.val; }
@@ -371,6 +406,7 @@ struct Vals<double> {
 };
 template <>
 struct Vals<float> {
+  static const float* dia(const DiaPart& d) { return d.val32; }
   static const float* csr(const cp_mat* m) { return m->val32; }
   static const float* ell(const EllPart& e) { return e.val32; }
   static const float* sell(const SellPart& s) { return s.val32; }
@@ -451,6 +487,12 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
     }
     case CP_FMT_HYB: {
       const int g = grid_for(ctx, n);
+      if (m->hyb_coo.n == 0) {  // every row fits the ELL part: the fused ELL kernel suffices
+        CP_LAUNCH(ctx, (k_ell<T, GEN, DOT>), g, kBlock, 0, s, n, m->hyb_ell.K, m->hyb_ell.ld,
+                  m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, dotv, partials,
+                  skip);
+        return DOT ? g : 0;
+      }
       CP_LAUNCH(ctx, (k_ell<T, GEN, false>), g, kBlock, 0, s, n, m->hyb_ell.K, m->hyb_ell.ld,
                 m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, nullptr, nullptr,
                 skip);
@@ -459,6 +501,12 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
                   kBlock, 0, s, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
                   Vals<T>::coo(m->hyb_coo), x, y, GEN ? alpha : T(1), skip);
       break;
+    }
+    case CP_FMT_DIA: {
+      const int g = grid_for(ctx, n);
+      CP_LAUNCH(ctx, (k_dia<T, GEN, DOT>), g, kBlock, 0, s, n, m->ncols, (int)m->dia.ndiag,
+                m->dia.offs, Vals<T>::dia(m->dia), x, y, alpha, beta, dotv, partials, skip);
+      return DOT ? g : 0;
     }
     case CP_FMT_COO: {
       CP_LAUNCH(ctx, k_scale<T>, grid_for(ctx, n), kBlock, 0, s, n, y, GEN ? beta : T(0), skip);

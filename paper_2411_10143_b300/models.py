@@ -39,6 +39,8 @@ def load(path: Path = WEIGHTS) -> dict:
 
 def install(ctx, models: dict) -> list:
     """Load every stage present in ``models`` into the context; returns their names."""
+    import warnings
+
     from . import cascade as C
     done = []
     for i, name in enumerate(STAGE_NAMES):
@@ -46,6 +48,10 @@ def install(ctx, models: dict) -> list:
         if not m:
             continue
         d, h1, h2, k = m["dims"]
+        if k != C.STAGE_CLASSES[i]:
+            warnings.warn(f"stage {name}: stored model has {k} classes, the library expects "
+                          f"{C.STAGE_CLASSES[i]}; stage left without a model (retrain)")
+            continue
         ctx.model_load(i, h1, h2, k, np.asarray(m["params"], np.float32),
                        np.asarray(m["mu"], np.float32), np.asarray(m["sd"], np.float32))
         done.append(name)

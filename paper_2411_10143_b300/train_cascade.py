@@ -8,7 +8,7 @@ library's own GPU training kernels (cp_model_train).
 
 Labelling rule: the configuration with the smallest mean time; times within 2 %
 of the best count as ties, broken toward the cheaper conversion (CSR < COO <
-HYB < SELL < ELL), then the smaller parameter.
+HYB < SELL < ELL < DIA), then the smaller parameter.
 
 Usage: python -m paper_2411_10143_b300.train_cascade [--count N] [--reps R]
 writes weights/cascade.json (and weights/dataset.npz with features, times and
@@ -26,7 +26,8 @@ import numpy as np
 from . import cascade as C
 from . import models, workloads as W
 
-CONV_COST_ORDER = {C.FMT_CSR: 0, C.FMT_COO: 1, C.FMT_HYB: 2, C.FMT_SELL: 3, C.FMT_ELL: 4}
+CONV_COST_ORDER = {C.FMT_CSR: 0, C.FMT_COO: 1, C.FMT_HYB: 2, C.FMT_SELL: 3, C.FMT_ELL: 4,
+                   C.FMT_DIA: 5}
 TIE = 1.02
 
 
@@ -37,7 +38,7 @@ def config_space():
     out += [(f"CSR-vector{t}", C.config("CSR", C.ALGO_VECTOR, tpv=t)) for t in C.TPV_CLASSES]
     out += [("COO", C.config("COO")), ("ELL", C.config("ELL"))]
     out += [(f"SELL-{s}", C.config("SELL", sigma=s)) for s in C.SIGMA_CLASSES]
-    out += [("HYB", C.config("HYB"))]
+    out += [("HYB", C.config("HYB")), ("DIA", C.config("DIA"))]
     return out
 
 
@@ -95,6 +96,7 @@ def labels_from_times(times):
         C.FMT_ELL: times.get("ELL", inf),
         C.FMT_SELL: min(sell.values()),
         C.FMT_HYB: times.get("HYB", inf),
+        C.FMT_DIA: times.get("DIA", inf),
     }
     fmt = _argmin_tie([(t, CONV_COST_ORDER[f], f) for f, t in fmt_best.items()])
     algo = _argmin_tie([(times.get("CSR-scalar", inf), 0, C.ALGO_SCALAR),

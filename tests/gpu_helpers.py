@@ -11,6 +11,7 @@ def all_configs():
     cfgs += [C.config("COO"), C.config("ELL")]
     cfgs += [C.config("SELL", sigma=s) for s in C.SIGMA_CLASSES]
     cfgs += [C.config("HYB", hyb_k=k) for k in (0, 1, 3)]
+    cfgs += [C.config("DIA")]
     return cfgs
 
 

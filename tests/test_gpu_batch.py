@@ -1,0 +1,80 @@
+"""Batched persistent solves (one launch, one block per system) vs the oracle.
+
+Every system is checked on its own: true relative residual <= 1e-10 by the
+oracle's SpMV, solution within 1e-7 of the oracle's FP64 solve; the batch's
+result for a system equals its result when solved alone in a batch of one
+(same kernel, same block size, same arithmetic order) to 1e-12."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_10143_b300 import cascade as C
+from paper_2411_10143_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def systems():
+    out = []
+    for i, N in enumerate([6, 9, 14, 11, 5, 17]):
+        out.append((W.poisson3d(N), 0))
+    for N in [20, 33, 50]:
+        out.append((W.poisson2d(N), 0))
+    for n in [500, 3000, 9000]:
+        out.append((W.spd_powerlaw(n, seed=n), 0))
+    for N in [5, 9, 13, 16]:
+        out.append((W.convdiff3d(N), 1))
+    out.append((W.diagonally_dominant(W.powerlaw(2000, lmax=300, seed=4)), 1))
+    return out
+
+
+def check(ctx, sys, threads, seeds=None):
+    mats = [ctx.load(A) for A, _ in sys]
+    seeds = seeds if seeds is not None else list(range(len(sys)))
+    rhs = [oracle.spmv(A, W.vector(A.nrows, q + 40)) for q, (A, _) in zip(seeds, sys)]
+    bs = [torch.as_tensor(b, device="cuda") for b in rhs]
+    xs = [torch.zeros(A.nrows, dtype=torch.float64, device="cuda") for A, _ in sys]
+    infos = ctx.batch_solve(mats, [s for _, s in sys], bs, xs,
+                            C.default_opts(tol=1e-10, inner_tol=1e-5, restart=30,
+                                           precision=C.PREC_FP32_IR), threads)
+    sols = []
+    for (A, s), b, x, info in zip(sys, rhs, xs, infos):
+        xh = x.cpu().numpy()
+        rel = np.linalg.norm(b - oracle.spmv(A, xh)) / np.linalg.norm(b)
+        ref = (oracle.cg if s == 0 else oracle.gmres)(A, b, tol=1e-10)
+        assert info.status == 0 and rel <= 1e-10, (A.name, rel)
+        assert np.linalg.norm(xh - ref.x) <= 1e-7 * np.linalg.norm(ref.x), A.name
+        assert info.outer_iters >= 2
+        sols.append(xh)
+    return mats, sols
+
+
+@pytest.mark.parametrize("threads", [128, 512, 0])
+def test_batch_matches_oracle(threads):
+    ctx = C.Context(0)
+    check(ctx, systems(), threads)
+    ctx.close()
+
+
+def test_batch_result_same_alone_and_in_the_mix():
+    ctx = C.Context(0)
+    sys = systems()
+    _, mixed = check(ctx, sys, 256)
+    for k in (0, 7, 12):
+        _, alone = check(ctx, [sys[k]], 256, seeds=[k])
+        assert np.linalg.norm(alone[0] - mixed[k]) <= 1e-12 * np.linalg.norm(mixed[k])
+    ctx.close()
+
+
+def test_batch_rejects_bad_arguments():
+    ctx = C.Context(0)
+    A = W.poisson2d(8)
+    M = ctx.load(A)
+    b = torch.ones(64, dtype=torch.float64, device="cuda")
+    x = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(C.CascadeError):
+        ctx.batch_solve([M], [2], [b], [x])
+    with pytest.raises(C.CascadeError):
+        ctx.batch_solve([M], [1], [b], [x], C.default_opts(restart=40, precision=1))
+    ctx.close()

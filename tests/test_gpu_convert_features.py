@@ -56,6 +56,16 @@ def test_conversions_bit_exact(ctx, mi):
         assert np.array_equal(M.format_export(cfg, "HYB_COO_ROW", np.int32), cr)
         assert np.array_equal(M.format_export(cfg, "HYB_COO_COL", np.int32), cc)
         assert np.array_equal(bits(M.format_export(cfg, "HYB_COO_VAL", np.float64)), bits(cv))
+    offs, data = oracle.to_dia(A)
+    cfg = C.config("DIA")
+    if len(offs) <= 1024:
+        assert M.format_dims(cfg)[:2] == [len(offs), A.nrows]
+        assert np.array_equal(M.format_export(cfg, "DIA_OFFSETS", np.int32), offs)
+        assert np.array_equal(bits(M.format_export(cfg, "DIA_VAL", np.float64)), bits(data))
+    else:
+        with pytest.raises(C.CascadeError) as e:
+            M.convert(cfg)
+        assert e.value.status == C.ERR_FOOTPRINT
 
 
 INT_FEATURES = ("nrows", "ncols", "nnz", "max", "min", "ndiag")

@@ -89,10 +89,11 @@ def test_gmres_convdiff(ctx, m):
 
 
 @pytest.mark.parametrize("cfg", [C.config("ELL"), C.config("SELL", sigma=1024),
-                                 C.config("HYB"), C.config("COO"),
+                                 C.config("HYB"), C.config("COO"), C.config("DIA"),
                                  C.config("CSR", C.ALGO_MERGE)])
 def test_gmres_forced_configs(ctx, cfg):
-    A = W.diagonally_dominant(W.powerlaw(6000, lmax=400, seed=8))
+    A = (W.convdiff3d(12) if cfg.fmt == C.FMT_DIA
+         else W.diagonally_dominant(W.powerlaw(6000, lmax=400, seed=8)))
     b = rhs(A, 6)
     x, info = gpu_solve(ctx, A, b, kind="gmres", restart=30, tol=1e-10, force=cfg)
     ref = oracle.gmres(A, b, m=30, tol=1e-10)
@@ -147,7 +148,7 @@ def expected_target(target):
             (target, None, None))
 
 
-@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "CSR-vector"])
+@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "DIA", "CSR-vector"])
 def test_sequential_cascade_applies_every_stage(target):
     """SerGMRES-style: predict first, so every stage is applied at iteration 0."""
     c = C.Context(0)
@@ -171,7 +172,7 @@ def test_sequential_cascade_applies_every_stage(target):
     c.close()
 
 
-@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "CSR-vector"])
+@pytest.mark.parametrize("target", ["ELL", "SELL", "HYB", "DIA", "CSR-vector"])
 def test_async_cascade_switches_mid_run(target):
     """The solve starts at once on CSR-scalar; every prediction that lands before
     convergence is applied at a later iteration, in cascade order, and the

@@ -23,6 +23,13 @@ def ctx():
     c.close()
 
 
+def usable(A, cfgs):
+    """Every configuration, except DIA where the matrix has more than 1024 diagonals
+    (DIA refuses those with CP_ERR_FOOTPRINT, checked in the conversion tests)."""
+    nd = len(oracle.to_dia(A)[0])
+    return [c for c in cfgs if not (c.fmt == C.FMT_DIA and nd > 1024)]
+
+
 def run(mat, cfg, x, dtype=torch.float64, alpha=1.0, beta=0.0, y0=None):
     xd = torch.as_tensor(x, dtype=dtype, device="cuda")
     yd = (torch.as_tensor(y0, dtype=dtype, device="cuda").clone() if y0 is not None
@@ -38,7 +45,7 @@ def test_spmv_integer_bit_exact(ctx, mi):
     M = ctx.load(A)
     x = W.int_vector(A.ncols, 7)
     ref = oracle.spmv(A, x)
-    for cfg in all_configs():
+    for cfg in usable(A, all_configs()):
         y = run(M, cfg, x)
         assert np.array_equal(y, ref), repr(cfg)
         y32 = run(M, cfg, x, torch.float32)
@@ -53,7 +60,7 @@ def test_spmv_random_fp64_and_fp32(ctx, mi):
     ref = oracle.spmv(A, x)
     ref32 = oracle.spmv_f32(A, x).astype(np.float64)
     nr = max(np.linalg.norm(ref), 1e-300)
-    for cfg in all_configs():
+    for cfg in usable(A, all_configs()):
         y = run(M, cfg, x)
         assert np.linalg.norm(y - ref) <= 1e-12 * nr, repr(cfg)
         y32 = run(M, cfg, x, torch.float32).astype(np.float64)
@@ -66,7 +73,7 @@ def test_spmv_general_alpha_beta(ctx):
     x = W.vector(A.ncols, 1)
     y0 = W.vector(A.nrows, 2)
     ref = 0.5 * oracle.spmv(A, x) - 2.0 * y0
-    for cfg in all_configs():
+    for cfg in usable(A, all_configs()):
         y = run(M, cfg, x, alpha=0.5, beta=-2.0, y0=y0)
         assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref), repr(cfg)
 

@@ -110,3 +110,28 @@ def test_padding_and_spmv_consistency():
             if scol[j] >= 0:
                 ys[perm[s]] += sval[j] * x[scol[j]]
     assert np.array_equal(ys, y)
+
+
+def test_dia_golden():
+    offs, data = oracle.to_dia(gold_matrix())
+    assert offs.tolist() == GOLD["dia"]["offsets"]
+    assert data.reshape(len(offs), GOLD["nrows"]).tolist() == GOLD["dia"]["data"]
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_dia_spmv_consistency(seed):
+    """y_i = sum_d data[d][i] x[i + off_d] equals CSR SpMV exactly on integer data."""
+    rng = np.random.default_rng(seed)
+    n, m = int(rng.integers(1, 120)), int(rng.integers(1, 140))
+    A = W.random_csr(n, m, rng.integers(0, 9, n), seed=seed, int_values=True)
+    x = W.int_vector(m, seed)
+    offs, data = oracle.to_dia(A)
+    D = data.reshape(len(offs), n)
+    y = np.zeros(n)
+    for d, o in enumerate(offs):
+        for i in range(n):
+            if 0 <= i + o < m:
+                y[i] += D[d, i] * x[i + o]
+    assert np.array_equal(y, oracle.spmv(A, x))
+    # every stored value appears exactly once
+    assert np.count_nonzero(D) == np.count_nonzero(A.val)
