@@ -282,7 +282,11 @@ typedef struct {
   int32_t max_outer;     /* FP32_IR: refinement steps limit                               */
   int32_t check_every;   /* iterations between host convergence checks (0: default 8)   */
   int32_t profile;       /* 1: time every SpMV launch with CUDA events (t_spmv_ms)        */
-  int32_t reserved;
+  int32_t iteration_kernel; /* CG: 0 = one persistent cooperative launch runs the
+                            iterations while the format has a row-parallel kernel (CSR
+                            scalar / vector, ELL, SELL, DIA, HYB without COO part),
+                            falling back to one launch per step otherwise; 1 = always
+                            one launch per step                                       */
   const cp_config* force;/* non-NULL: use this configuration from the first iteration    */
 } cp_solve_opts;
 
@@ -299,6 +303,8 @@ typedef struct {
   float t_features_ms, t_predict_ms[3], t_convert_ms; /* side-stream step times           */
   float t_total_ms;        /* wall time from entry to x ready                             */
   float t_spmv_ms;         /* summed SpMV kernel time when profile = 1                    */
+  float t_persist_ms;      /* summed duration of the persistent CG launches               */
+  int32_t persist_iters;   /* iterations those launches ran                               */
 } cp_solve_info;
 
 void cp_solve_opts_default(cp_solve_opts* opts);

@@ -72,7 +72,7 @@ def config(fmt="CSR", algo=ALGO_SCALAR, tpv=8, sigma=1, hyb_k=0) -> Config:
 class SolveOpts(Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("restart", c_int32), ("mode", c_int32),
                 ("precision", c_int32), ("inner_tol", c_double), ("max_outer", c_int32),
-                ("check_every", c_int32), ("profile", c_int32), ("reserved", c_int32),
+                ("check_every", c_int32), ("profile", c_int32), ("iteration_kernel", c_int32),
                 ("force", POINTER(Config))]
 
 
@@ -81,7 +81,8 @@ class SolveInfo(Structure):
                 ("n_spmv", c_int32), ("n_launches", c_int32), ("status", c_int32),
                 ("relres_true", c_double), ("final_cfg", Config), ("t_features_ms", c_float),
                 ("t_predict_ms", c_float * 3), ("t_convert_ms", c_float),
-                ("t_total_ms", c_float), ("t_spmv_ms", c_float)]
+                ("t_total_ms", c_float), ("t_spmv_ms", c_float), ("t_persist_ms", c_float),
+                ("persist_iters", c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, outer_iters=self.outer_iters,
@@ -90,7 +91,8 @@ class SolveInfo(Structure):
                     relres_true=self.relres_true, final_cfg=repr(self.final_cfg),
                     t_features_ms=self.t_features_ms, t_predict_ms=list(self.t_predict_ms),
                     t_convert_ms=self.t_convert_ms, t_total_ms=self.t_total_ms,
-                    t_spmv_ms=self.t_spmv_ms)
+                    t_spmv_ms=self.t_spmv_ms, t_persist_ms=self.t_persist_ms,
+                    persist_iters=self.persist_iters)
 
 
 class ServerOpts(Structure):

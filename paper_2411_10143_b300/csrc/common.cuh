@@ -18,6 +18,20 @@ __device__ __forceinline__ T ld_ro(const T* p) {
   return __ldg(p);
 }
 
+// Load that bypasses L1 (served by L2, coherent across SMs): for data that
+// other blocks of the same kernel wrote (persistent kernels), where L1 lines
+// and the read-only path may still hold an older value.
+template <typename T>
+__device__ __forceinline__ T ld_cg(const T* p) {
+  return __ldcg(p);
+}
+// x gathers: read-only path in ordinary kernels, L2 in persistent ones.
+template <bool COH, typename T>
+__device__ __forceinline__ T ld_x(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -70,6 +84,20 @@ __device__ __forceinline__ double reduce_partials(const double* __restrict__ par
                                                   double* smem) {
   double s = 0.0;
   for (int i = threadIdx.x; i < P; i += blockDim.x) s += partials[i];
+  s = block_sum(s, smem);
+  const int last = blockDim.x >> 5;
+  if (threadIdx.x == 0) smem[last] = s;
+  __syncthreads();
+  s = smem[last];
+  __syncthreads();
+  return s;
+}
+
+// reduce_partials for partials written by other blocks of the same kernel
+__device__ __forceinline__ double reduce_partials_cg(const double* __restrict__ partials, int P,
+                                                     double* smem) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s += __ldcg(partials + i);
   s = block_sum(s, smem);
   const int last = blockDim.x >> 5;
   if (threadIdx.x == 0) smem[last] = s;

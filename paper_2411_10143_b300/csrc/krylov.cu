@@ -18,20 +18,13 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "persist.cuh"
 
 namespace cp {
 
 constexpr int kMaxRestart = 64;
 
 // ================================================================== device state
-struct CgState {
-  double rr[2];  // (r, r) of the current iteration, by parity
-  double pap, alpha, beta, bb, relres;
-  int done;      // recursive residual reached tol (or breakdown): stop
-  int status;    // CP_OK / CP_ERR_BREAKDOWN
-  int iters;     // completed iterations
-};
-
 struct GmState {
   double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
   double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
@@ -43,12 +36,6 @@ struct GmState {
   int jdone;             // steps completed in this cycle
   int status;
   int iters;             // steps completed in total
-};
-
-// Host-mapped mirror written by the kernels that finish an iteration.
-struct Mirror {
-  volatile double res;  // latest residual norm (recursive / estimated / true)
-  volatile int done, halt, status, iters, jdone, conv_est;
 };
 
 // ================================================================== CG kernels
@@ -554,6 +541,16 @@ struct Workspace {
     dev.push_back(p);
     return p;
   }
+  int* yield_h = nullptr;  // host-mapped flag asking the persistent kernel to return
+  int* yield_d = nullptr;
+  int* yield() {
+    if (!yield_h) {
+      CP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&yield_h), sizeof(int), cudaHostAllocMapped));
+      *yield_h = 0;
+      CP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&yield_d), yield_h, 0));
+    }
+    return yield_d;
+  }
   Mirror* mirror() {
     if (!mir) {
       CP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&mir), sizeof(Mirror), cudaHostAllocMapped));
@@ -574,6 +571,7 @@ struct Workspace {
     for (void* p : dev) cudaFree(p);
     for (auto e : ring) cudaEventDestroy(e);
     if (mir) cudaFreeHost((void*)mir);
+    if (yield_h) cudaFreeHost(yield_h);
   }
 };
 
@@ -599,6 +597,9 @@ struct ConfigSource {
   bool profile = false;
   std::vector<cudaEvent_t> ev;
   int n_spmv = 0;
+  bool persistent = true;     // run CG iterations in the persistent kernel when it supports cfg
+  float t_persist_ms = 0.f;   // summed duration of the persistent launches
+  int persist_iters = 0;      // iterations they ran
 
   void poll(int iter) {
     if (!ch) return;
@@ -702,8 +703,51 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
               keep_bb ? 1 : 0);
     keep_bb = true;
     int issued = 0;
-    for (; it < maxit; ++it) {
+    while (it < maxit) {
       cs.poll(it);
+      if (cs.persistent && persist_supported<T>(m, cs.cur)) {
+        // one cooperative launch runs iterations [it, maxit) until convergence, a
+        // breakdown, or the host asks it to return at an iteration boundary
+        // because the cascade published a new configuration
+        *ws.yield_h = 0;
+        PersistArgs<T> pa_args;
+        pa_args.x = x;
+        pa_args.r = r;
+        pa_args.p = p;
+        pa_args.ap = ap;
+        pa_args.pa = pa;
+        pa_args.pb = pb;
+        pa_args.st = st;
+        pa_args.mir = mir;
+        pa_args.yield = ws.yield();
+        pa_args.it0 = it;
+        pa_args.itmax = maxit;
+        pa_args.tol2 = tol2;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CP_CUDA(cudaEventCreate(&e0));
+        CP_CUDA(cudaEventCreate(&e1));
+        CP_CUDA(cudaEventRecord(e0, s));
+        persist_launch<T>(ctx, m, cs.cur, pa_args, s);
+        CP_CUDA(cudaEventRecord(e1, s));
+        for (;;) {
+          const cudaError_t q = cudaEventQuery(e1);
+          if (q == cudaSuccess) break;
+          if (q != cudaErrorNotReady) CP_CUDA(q);
+          if (cs.ch && !*ws.yield_h &&
+              cs.ch->count.load(std::memory_order_acquire) > cs.applied)
+            *(volatile int*)ws.yield_h = 1;
+          std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        float t = 0.f;
+        CP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cs.t_persist_ms += t;
+        cs.persist_iters += ws.mir->iters - it;
+        it = ws.mir->iters;
+        if (ws.mir->done || ws.mir->status != CP_OK) break;
+        continue;  // returned on request: the poll above applies the new configuration
+      }
       const int PA = spmv_cur<T>(cs, p, ap, p, pa, done, s);
       CP_LAUNCH(ctx, k_cg_update<T>, Gu, kBlock, 0, s, n, x, r, p, ap, pa, PA, st, it & 1, pb,
                 mir);
@@ -711,6 +755,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
                 mir);
       CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
       ++issued;
+      ++it;
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
         if (ws.mir->done) break;
@@ -930,6 +975,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
   cs.m = m;
   cs.fp32 = fp32;
   cs.profile = opt.profile != 0;
+  cs.persistent = opt.iteration_kernel == 0;
   cp_config_default(&cs.cur);
   if (opt.force) cs.cur = *opt.force;
   ensure_format(ctx, m, cs.cur, ctx->main);
@@ -987,6 +1033,8 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     info->t_total_ms = t_total;
     info->t_spmv_ms = cs.spmv_ms();
     info->n_spmv = cs.n_spmv;
+    info->t_persist_ms = cs.t_persist_ms;
+    info->persist_iters = cs.persist_iters;
     info->n_launches = (int32_t)(ctx->launches.load() - launches0);
     info->status = res.status;
   }

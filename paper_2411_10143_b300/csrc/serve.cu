@@ -103,6 +103,9 @@ static void run_job(cp_server* S, int lane, cp_server::Job& job) {
     } else {
       const cp_request& r = job.reqs[0];
       o.mode = S->opts.mode;
+      // lanes run concurrently: cooperative grids sized for the whole device
+      // must not share it, so every lane uses one launch per step
+      o.iteration_kernel = 1;
       cp_solve_info info;
       std::memset(&info, 0, sizeof(info));
       cp_status st = CP_OK;

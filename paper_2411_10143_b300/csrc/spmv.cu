@@ -11,20 +11,9 @@
 // FMA, far below any tensor-core shape's arithmetic intensity.
 #include "common.cuh"
 #include "internal.cuh"
+#include "spmv_rows.cuh"
 
 namespace cp {
-
-// y_i <- s (solver form) or alpha s + beta y_i (general form; y not read when beta = 0)
-template <typename T, bool GEN>
-__device__ __forceinline__ void store_row(T* y, int64_t i, T s, T alpha, T beta) {
-  if (GEN) {
-    T r = alpha * s;
-    if (beta != T(0)) r = fma(beta, y[i], r);
-    y[i] = r;
-  } else {
-    y[i] = s;
-  }
-}
 
 template <bool DOT>
 __device__ __forceinline__ void write_partial(double acc, double* partials) {
@@ -35,75 +24,29 @@ __device__ __forceinline__ void write_partial(double acc, double* partials) {
   }
 }
 
-// ------------------------------------------------------------------ CSR scalar
+// The row-parallel SpMV kernels: grid-stride wrappers around the row loops of
+// spmv_rows.cuh (which the persistent CG kernel runs as its SpMV phase).
 template <typename T, bool GEN, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_csr_scalar(
     int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
     const T* __restrict__ dotv, double* __restrict__ partials, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  T acc = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int s = rp[i], e = rp[i + 1];
-    T sum = 0;
-    // chunks of 4 entries: the 8 index/value loads are independent, then 4 gathers
-    for (int k0 = s; k0 < e; k0 += 4) {
-      int32_t c[4];
-      T w[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool in = k0 + u < e;
-        c[u] = in ? ld_stream(ci + k0 + u) : 0;
-        w[u] = in ? ld_stream(v + k0 + u) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (k0 + u < e) sum = fma(w[u], ld_ro(x + c[u]), sum);
-    }
-    store_row<T, GEN>(y, i, sum, alpha, beta);
-    if (DOT) acc = fma(sum, dotv[i], acc);
-  }
+  const T acc = csr_scalar_rows<T, GEN, DOT>(n, rp, ci, v, x, y, alpha, beta, dotv,
+                                             blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                             (int64_t)gridDim.x * blockDim.x);
   write_partial<DOT>((double)acc, partials);
 }
 
-// ------------------------------------------------------------------ CSR vector
-// TPV lanes per row; the warp walks its rows in lock step so the shuffles of
-// the row reduction always see the full warp.
 template <typename T, int TPV, bool GEN, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_csr_vector(
     int64_t n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
     const T* __restrict__ dotv, double* __restrict__ partials, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  constexpr int RPW = 32 / TPV;  // rows per warp step
-  const int lane = threadIdx.x & 31;
-  const int sub = lane % TPV;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  T acc = 0;
-  for (int64_t r0 = warp * RPW; r0 < n; r0 += nwarps * RPW) {
-    const int64_t i = r0 + lane / TPV;
-    T sum = 0;
-    if (i < n) {
-      const int s = rp[i], e = rp[i + 1];
-      for (int k = s + sub; k < e; k += 2 * TPV) {
-        const bool in2 = k + TPV < e;
-        const int32_t c0 = ld_stream(ci + k);
-        const int32_t c1 = in2 ? ld_stream(ci + k + TPV) : 0;
-        const T w0 = ld_stream(v + k);
-        const T w1 = in2 ? ld_stream(v + k + TPV) : T(0);
-        sum = fma(w0, ld_ro(x + c0), sum);
-        if (in2) sum = fma(w1, ld_ro(x + c1), sum);
-      }
-    }
-#pragma unroll
-    for (int o = TPV / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (sub == 0 && i < n) {
-      store_row<T, GEN>(y, i, sum, alpha, beta);
-      if (DOT) acc = fma(sum, dotv[i], acc);
-    }
-  }
+  const T acc = csr_vector_rows<T, TPV, GEN, DOT>(
+      n, rp, ci, v, x, y, alpha, beta, dotv, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+      ((int64_t)gridDim.x * blockDim.x) >> 5);
   write_partial<DOT>((double)acc, partials);
 }
 
@@ -222,42 +165,18 @@ __global__ void k_merge_fixup(int64_t ntiles, const int32_t* __restrict__ carry_
   }
 }
 
-// ------------------------------------------------------------------ ELL
 template <typename T, bool GEN, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_ell(
     int64_t n, int64_t K, int64_t ld, const int32_t* __restrict__ ec, const T* __restrict__ ev,
     const T* __restrict__ x, T* __restrict__ y, T alpha, T beta, const T* __restrict__ dotv,
     double* __restrict__ partials, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  T acc = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    T sum = 0;
-    // chunks of 4 slots: 8 independent coalesced loads, then the gathers;
-    // padding (col -1) only follows a row's entries, so a padded chunk ends the row
-    for (int64_t k0 = 0; k0 < K; k0 += 4) {
-      int32_t c[4];
-      T w[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool in = k0 + u < K;
-        c[u] = in ? ld_stream(ec + (k0 + u) * ld + i) : -1;
-        w[u] = in ? ld_stream(ev + (k0 + u) * ld + i) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (c[u] >= 0) sum = fma(w[u], ld_ro(x + c[u]), sum);
-      if (c[3] < 0) break;
-    }
-    store_row<T, GEN>(y, i, sum, alpha, beta);
-    if (DOT) acc = fma(sum, dotv[i], acc);
-  }
+  const T acc = ell_rows<T, GEN, DOT>(n, K, ld, ec, ev, x, y, alpha, beta, dotv,
+                                      blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                      (int64_t)gridDim.x * blockDim.x);
   write_partial<DOT>((double)acc, partials);
 }
 
-// ------------------------------------------------------------------ SELL-C-sigma (C = 32)
-// One warp per chunk, lane r on slot r: every load of the chunk is one
-// contiguous 128-byte (col) and 256-byte (FP64 val) transaction.
 template <typename T, bool GEN, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_sell(
     int64_t n, int64_t nchunks, const int32_t* __restrict__ perm,
@@ -266,40 +185,12 @@ __global__ void __launch_bounds__(kBlock) k_sell(
     T* __restrict__ y, T alpha, T beta, const T* __restrict__ dotv,
     double* __restrict__ partials, const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  T acc = 0;
-  for (int64_t c = warp; c < nchunks; c += nwarps) {
-    const int64_t base = cptr[c] + lane;
-    const int w = clen[c];
-    T sum = 0;
-    for (int k0 = 0; k0 < w; k0 += 4) {
-      int32_t cc[4];
-      T vv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool in = k0 + u < w;
-        cc[u] = in ? ld_stream(sc + base + (int64_t)(k0 + u) * 32) : -1;
-        vv[u] = in ? ld_stream(sv + base + (int64_t)(k0 + u) * 32) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (cc[u] >= 0) sum = fma(vv[u], ld_ro(x + cc[u]), sum);
-    }
-    const int64_t s = c * 32 + lane;
-    if (s < n) {
-      const int64_t row = perm ? perm[s] : s;
-      store_row<T, GEN>(y, row, sum, alpha, beta);
-      if (DOT) acc = fma(sum, dotv[row], acc);
-    }
-  }
+  const T acc = sell_chunks<T, GEN, DOT>(n, nchunks, perm, clen, cptr, sc, sv, x, y, alpha, beta,
+                                         dotv, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+                                         ((int64_t)gridDim.x * blockDim.x) >> 5);
   write_partial<DOT>((double)acc, partials);
 }
 
-// ------------------------------------------------------------------ DIA
-// Thread per row; the offsets sit in shared memory; values and x are read
-// contiguously across the warp (no index arrays, no gather).
 template <typename T, bool GEN, bool DOT>
 __global__ void __launch_bounds__(kBlock) k_dia(
     int64_t n, int64_t ncols, int ndiag, const int32_t* __restrict__ offs,
@@ -309,25 +200,9 @@ __global__ void __launch_bounds__(kBlock) k_dia(
   __shared__ int32_t so[kDiaMax];
   for (int d = threadIdx.x; d < ndiag; d += blockDim.x) so[d] = offs[d];
   __syncthreads();
-  T acc = 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
-    T sum = 0;
-    for (int d0 = 0; d0 < ndiag; d0 += 4) {
-      T w[4], xv[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t c = i + (d0 + u < ndiag ? so[d0 + u] : 0);
-        const bool in = d0 + u < ndiag && c >= 0 && c < ncols;
-        w[u] = in ? ld_stream(dv + (int64_t)(d0 + u) * n + i) : T(0);
-        xv[u] = in ? ld_ro(x + c) : T(0);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) sum = fma(w[u], xv[u], sum);
-    }
-    store_row<T, GEN>(y, i, sum, alpha, beta);
-    if (DOT) acc = fma(sum, dotv[i], acc);
-  }
+  const T acc = dia_rows<T, GEN, DOT>(n, ncols, ndiag, so, dv, x, y, alpha, beta, dotv,
+                                      blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
+                                      (int64_t)gridDim.x * blockDim.x);
   write_partial<DOT>((double)acc, partials);
 }
 

@@ -224,3 +224,24 @@ def test_predict_sequential_api():
     cfg, ms = M.predict()
     assert cfg.fmt == C.FMT_ELL
     c.close()
+
+
+@pytest.mark.parametrize("cfg", [C.config("CSR"), C.config("CSR", C.ALGO_VECTOR, tpv=8),
+                                 C.config("ELL"), C.config("SELL", sigma=1024), C.config("DIA"),
+                                 C.config("HYB")])
+@pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
+def test_persistent_cg_matches_per_step_launches(ctx, cfg, precision):
+    """The persistent cooperative CG kernel and the one-launch-per-step path run the
+    same iteration; both reach the tolerance and agree with the oracle."""
+    A = W.poisson3d(20)
+    b = rhs(A, 12)
+    ref = oracle.cg(A, b, tol=1e-10)
+    out = {}
+    for mode in (0, 1):
+        x, info = gpu_solve(ctx, A, b, tol=1e-10, force=cfg, precision=precision,
+                            iteration_kernel=mode)
+        assert true_relres(A, x, b) <= 1e-10, (repr(cfg), mode)
+        assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+        out[mode] = (x, info)
+    assert out[0][1].persist_iters > 0 and out[1][1].persist_iters == 0
+    assert abs(out[0][1].iters - out[1][1].iters) <= 2
