@@ -305,6 +305,8 @@ typedef struct {
   float t_spmv_ms;         /* summed SpMV kernel time when profile = 1                    */
   float t_persist_ms;      /* summed duration of the persistent CG launches               */
   int32_t persist_iters;   /* iterations those launches ran                               */
+  float t_persist_last_ms; /* duration of the last persistent launch (final configuration) */
+  int32_t persist_last_iters; /* iterations it ran                                        */
 } cp_solve_info;
 
 void cp_solve_opts_default(cp_solve_opts* opts);

@@ -82,7 +82,8 @@ class SolveInfo(Structure):
                 ("relres_true", c_double), ("final_cfg", Config), ("t_features_ms", c_float),
                 ("t_predict_ms", c_float * 3), ("t_convert_ms", c_float),
                 ("t_total_ms", c_float), ("t_spmv_ms", c_float), ("t_persist_ms", c_float),
-                ("persist_iters", c_int32)]
+                ("persist_iters", c_int32), ("t_persist_last_ms", c_float),
+                ("persist_last_iters", c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, outer_iters=self.outer_iters,
@@ -92,7 +93,8 @@ class SolveInfo(Structure):
                     t_features_ms=self.t_features_ms, t_predict_ms=list(self.t_predict_ms),
                     t_convert_ms=self.t_convert_ms, t_total_ms=self.t_total_ms,
                     t_spmv_ms=self.t_spmv_ms, t_persist_ms=self.t_persist_ms,
-                    persist_iters=self.persist_iters)
+                    persist_iters=self.persist_iters, t_persist_last_ms=self.t_persist_last_ms,
+                    persist_last_iters=self.persist_last_iters)
 
 
 class ServerOpts(Structure):
@@ -213,25 +215,53 @@ def default_opts(**kw) -> SolveOpts:
     return o
 
 
+class _Ordered:
+    """Orders the library's main stream after torch's current stream on entry and
+    torch's current stream after the library's main stream on exit (event waits),
+    so tensors filled before a call are complete when the library reads them and
+    the library's results are complete before later torch work reads them."""
+
+    def __init__(self, ctx):
+        self.ctx = ctx
+
+    def __enter__(self):
+        import torch
+        cur = torch.cuda.current_stream(self.ctx.device)
+        if cur != self.ctx.stream:
+            self.ctx.stream.wait_stream(cur)
+        return self
+
+    def __exit__(self, *exc):
+        import torch
+        cur = torch.cuda.current_stream(self.ctx.device)
+        if cur != self.ctx.stream:
+            cur.wait_stream(self.ctx.stream)
+        return False
+
+
 class Context:
     """cp_create / cp_destroy.  ``main_stream`` / ``side_stream`` are torch CUDA
-    streams (or None for library-owned streams)."""
+    streams (or None)."""
 
     def __init__(self, device: int = 0, main_stream=None, side_stream=None):
-        """main_stream defaults to torch's current stream on ``device``, so the
-        library's work is ordered with the torch operations that fill its inputs
-        and read its outputs.  The side stream defaults to a library-owned
-        non-blocking stream."""
+        """Without ``main_stream`` the library gets a torch stream of its own (never
+        the legacy default stream, which serialises with other streams' allocations
+        and copies) and every call is ordered against torch's current stream by
+        event waits.  The side stream defaults to a library-owned non-blocking
+        stream."""
         import torch
         self._h = c_void_p()
         self.device = device
-        if main_stream is None:
-            main_stream = torch.cuda.current_stream(device)
+        if main_stream is None or main_stream.cuda_stream == 0:
+            main_stream = torch.cuda.Stream(device)
+        self.stream = main_stream
         self._streams = (main_stream, side_stream)  # keep them alive
-        # handle 0 is the legacy default stream: pass it as cudaStreamLegacy (1)
-        ms = c_void_p(main_stream.cuda_stream or 1)
-        ss = c_void_p(side_stream.cuda_stream or 1) if side_stream is not None else None
+        ms = c_void_p(main_stream.cuda_stream)
+        ss = c_void_p(side_stream.cuda_stream) if side_stream is not None else None
         _check(lib().cp_create(byref(self._h), device, ms, ss))
+
+    def ordered(self):
+        return _Ordered(self)
 
     @property
     def handle(self):
@@ -263,8 +293,9 @@ class Context:
             rowptr, col, val = _np(rowptr, np.int32), _np(col, np.int32), _np(val, np.float64)
         nnz = int(col.numel() if on_dev else col.size)
         h = c_void_p()
-        _check(lib().cp_csr_load(self._h, int(nrows), int(ncols), nnz, _ptr(rowptr), _ptr(col),
-                                 _ptr(val), 1 if on_dev else 0, byref(h)))
+        with self.ordered():
+            _check(lib().cp_csr_load(self._h, int(nrows), int(ncols), nnz, _ptr(rowptr),
+                                     _ptr(col), _ptr(val), 1 if on_dev else 0, byref(h)))
         return Matrix(self, h, int(nrows), int(ncols), nnz)
 
     def load(self, A) -> "Matrix":
@@ -296,17 +327,21 @@ class Context:
 
     def mlp_forward(self, dims, params, X, logits, scratch):
         d, h1, h2, k = dims
-        _check(lib().cp_mlp_forward(self._h, X.shape[0], d, h1, h2, k, _ptr(params), _ptr(X),
-                                    _ptr(logits), _ptr(scratch)))
+        with self.ordered():
+            _check(lib().cp_mlp_forward(self._h, X.shape[0], d, h1, h2, k, _ptr(params),
+                                        _ptr(X), _ptr(logits), _ptr(scratch)))
 
     def mlp_loss_grad(self, dims, params, X, labels, loss, grad, scratch):
         d, h1, h2, k = dims
-        _check(lib().cp_mlp_loss_grad(self._h, X.shape[0], d, h1, h2, k, _ptr(params), _ptr(X),
-                                      _ptr(labels), _ptr(loss), _ptr(grad), _ptr(scratch)))
+        with self.ordered():
+            _check(lib().cp_mlp_loss_grad(self._h, X.shape[0], d, h1, h2, k, _ptr(params),
+                                          _ptr(X), _ptr(labels), _ptr(loss), _ptr(grad),
+                                          _ptr(scratch)))
 
     def adam_step(self, params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
-        _check(lib().cp_adam_step(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m),
-                                  _ptr(v), t, lr, b1, b2, eps))
+        with self.ordered():
+            _check(lib().cp_adam_step(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m),
+                                      _ptr(v), t, lr, b1, b2, eps))
 
     def batch_solve(self, mats, solvers, bs, xs, opts=None, threads=0, raise_on_error=True):
         """cp_batch_solve: many small systems in one persistent launch.  mats:
@@ -319,7 +354,8 @@ class Context:
         hx = (c_void_p * n)(*[t.data_ptr() for t in xs])
         infos = (SolveInfo * n)()
         o = opts if opts is not None else default_opts(precision=PREC_FP32_IR)
-        st = lib().cp_batch_solve(self._h, n, hm, _ptr(hs), hb, hx, byref(o), threads, infos)
+        with self.ordered():
+            st = lib().cp_batch_solve(self._h, n, hm, _ptr(hs), hb, hx, byref(o), threads, infos)
         if raise_on_error:
             _check(st)
         return list(infos)
@@ -386,8 +422,10 @@ class Matrix:
         import torch
         dtype = DTYPE_F64 if x.dtype == torch.float64 else DTYPE_F32
         assert y.dtype == x.dtype and x.is_cuda and y.is_cuda
-        _check(lib().cp_spmv(self.ctx.handle, self._h, byref(cfg) if cfg is not None else None,
-                             dtype, alpha, _ptr(x), beta, _ptr(y)))
+        with self.ctx.ordered():
+            _check(lib().cp_spmv(self.ctx.handle, self._h,
+                                 byref(cfg) if cfg is not None else None, dtype, alpha, _ptr(x),
+                                 beta, _ptr(y)))
 
     def predict(self):
         cfg = Config()
@@ -400,7 +438,8 @@ class Matrix:
         if force is not None:
             o.force = ctypes.pointer(force)
         info = SolveInfo()
-        st = fn(self.ctx.handle, self._h, _ptr(b), _ptr(x), byref(o), byref(info))
+        with self.ctx.ordered():
+            st = fn(self.ctx.handle, self._h, _ptr(b), _ptr(x), byref(o), byref(info))
         if raise_on_error:
             _check(st)
         return info
@@ -429,6 +468,11 @@ class Server:
         self._keep = {}
 
     def submit(self, rid, mat: Matrix, solver, b, x):
+        """Queue a solve; b and x (torch CUDA float64) must stay alive until polled.
+        The lanes run on their own streams, so torch work that filled b and x is
+        waited for here."""
+        import torch
+        torch.cuda.current_stream(self.ctx.device).synchronize()
         r = Request(rid, mat._h.value, solver, 0, b.data_ptr(), x.data_ptr())
         self._keep[rid] = (mat, b, x)
         _check(lib().cp_server_submit(self._h, byref(r)))

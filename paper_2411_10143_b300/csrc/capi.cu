@@ -2,7 +2,10 @@
 // error capture and dispatch into the runtime.  No entry point lets a C++
 // exception or a CUDA error escape; each returns a cp_status and records a
 // message for cp_last_error().
+#include <chrono>
 #include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -18,6 +21,23 @@ void set_error(const char* fmt, ...) {
   va_start(ap, fmt);
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
+}
+
+void trace(const char* fmt, ...) {
+  static const bool on = [] {
+    const char* e = std::getenv("CASCADE_TRACE");
+    return e && e[0] == '1';
+  }();
+  if (!on) return;
+  static const auto t0 = std::chrono::steady_clock::now();
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::fprintf(stderr, "[cascade %10.3f ms] %s\n", ms, buf);
 }
 
 template <typename F>
@@ -102,7 +122,24 @@ cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_
         CP_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
         c->own_side = true;
       }
+      CP_CUDA(cudaHostAlloc(&c->pin_main, 4096, cudaHostAllocDefault));
+      CP_CUDA(cudaHostAlloc(&c->pin_side, 4096, cudaHostAllocDefault));
+      // keep memory freed by stream-ordered frees in this process's pool, so a
+      // conversion on the side stream reuses it instead of growing the pool
+      // (growth can wait for work already running on the device)
+      cudaMemPool_t pool;
+      CP_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
+      uint64_t keep = UINT64_MAX;
+      CP_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+      // the pool's first allocation is slow and can wait for running work: make it
+      // here, before any solve, and keep 64 MiB reserved for side-stream temporaries
+      void* warm = nullptr;
+      CP_CUDA(cudaMallocAsync(&warm, size_t(64) << 20, c->side));
+      CP_CUDA(cudaFreeAsync(warm, c->side));
+      CP_CUDA(cudaStreamSynchronize(c->side));
     } catch (...) {
+      if (c->pin_main) cudaFreeHost(c->pin_main);
+      if (c->pin_side) cudaFreeHost(c->pin_side);
       if (c->own_main && c->main) cudaStreamDestroy(c->main);
       if (c->own_side && c->side) cudaStreamDestroy(c->side);
       delete c;
@@ -125,6 +162,8 @@ cp_status cp_destroy(cp_ctx* ctx) {
     }
     if (ctx->own_main) cudaStreamDestroy(ctx->main);
     if (ctx->own_side) cudaStreamDestroy(ctx->side);
+    if (ctx->pin_main) cudaFreeHost(ctx->pin_main);
+    if (ctx->pin_side) cudaFreeHost(ctx->pin_side);
     delete ctx;
   });
 }

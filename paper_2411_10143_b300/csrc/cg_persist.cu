@@ -54,7 +54,7 @@ __device__ __forceinline__ bool grid_barrier(CgState* st, long long timeout_ns) 
           good = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(8);
       }
     }
     __threadfence();
@@ -86,7 +86,7 @@ __device__ __forceinline__ T spmv_phase(const PersistArgs<T>& a, const int32_t* 
 }
 
 template <typename T, int F, int TPV>
-__global__ void __launch_bounds__(kBlock) k_cg_persist(PersistArgs<T> a) {
+__global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> a) {
   // already converged (by iterations queued before this launch): nothing to do
   if (ld_cg(&a.st->done)) return;
   __shared__ double red[40];
@@ -101,6 +101,14 @@ __global__ void __launch_bounds__(kBlock) k_cg_persist(PersistArgs<T> a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   CgState* st = a.st;
+  unsigned long long tmark = lead ? global_ns() : 0;
+  auto lap = [&](int k) {  // block 0's step timer
+    if (lead) {
+      const unsigned long long now = global_ns();
+      st->t_ns[k] += now - tmark;
+      tmark = now;
+    }
+  };
   for (int it = a.it0; it < a.itmax; ++it) {
     const int slot = it & 1;
     // ---- phase 1: Ap = A p, partials of (p, Ap)
@@ -109,7 +117,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_persist(PersistArgs<T> a) {
       const double s = block_sum((double)acc, red);
       if (threadIdx.x == 0) a.pa[blockIdx.x] = s;
     }
+    lap(0);
     if (!grid_barrier(st, a.barrier_timeout_ns)) break;
+    lap(1);
     // ---- phase 2: alpha; x += alpha p; r -= alpha Ap; partials of (r, r)
     const double pap = reduce_partials_cg(a.pa, gridDim.x, red);
     const double rr = ld_cg(&st->rr[slot]);
@@ -156,7 +166,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_persist(PersistArgs<T> a) {
       st->alpha = rr / pap;
       st->stop = *a.yield;  // the host's request, published to all blocks by the barrier
     }
+    lap(2);
     if (!grid_barrier(st, a.barrier_timeout_ns)) break;
+    lap(3);
     // ---- phase 3: beta; convergence; p = r + beta p
     const double rr_new = reduce_partials_cg(a.pb, gridDim.x, red);
     const bool bad = !isfinite(rr_new);
@@ -191,7 +203,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_persist(PersistArgs<T> a) {
     }
     const int stop = *(volatile int*)&st->stop;
     if (stop) break;  // every block read the same value after the last barrier
+    lap(4);
     if (!grid_barrier(st, a.barrier_timeout_ns)) break;
+    lap(5);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int*)&st->bar_err) {
     st->status = CP_ERR_TIMEOUT;
@@ -203,16 +217,18 @@ __global__ void __launch_bounds__(kBlock) k_cg_persist(PersistArgs<T> a) {
 
 // ------------------------------------------------------------------ host
 template <typename T, int F, int TPV>
-static void launch_one(cp_ctx* ctx, PersistArgs<T>& a, cudaStream_t s) {
+static void launch_one(cp_ctx* ctx, PersistArgs<T>& a, cudaStream_t s, int share) {
   auto kern = k_cg_persist<T, F, TPV>;
   int per_sm = 0;
-  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, 0));
+  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistBlock, 0));
   CP_REQUIRE(per_sm >= 1, CP_ERR_CUDA, "persistent CG kernel does not fit an SM");
+  // share = 2: leave half of every SM to concurrent side-stream work
+  if (share == 2) per_sm = per_sm > 1 ? per_sm / 2 : 1;
   int grid = ctx->num_sms * per_sm;
   if (grid > kMaxPartials) grid = kMaxPartials;
   void* args[] = {&a};
   CP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid),
-                                      dim3(kBlock), args, 0, s));
+                                      dim3(kPersistBlock), args, 0, s));
   ctx->launches.fetch_add(1, std::memory_order_relaxed);
 }
 
@@ -225,7 +241,7 @@ bool persist_supported(const cp_mat* m, const cp_config& c) {
 
 template <typename T>
 void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a,
-                    cudaStream_t s) {
+                    cudaStream_t s, int share) {
   a.n = m->nrows;
   switch (c.fmt) {
     case CP_FMT_CSR:
@@ -233,14 +249,14 @@ void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a
       a.ci = m->col;
       a.v = PersistVals<T>::csr(m);
       if (c.algo == CP_ALGO_SCALAR) {
-        launch_one<T, kPersistCsrScalar, 1>(ctx, a, s);
+        launch_one<T, kPersistCsrScalar, 1>(ctx, a, s, share);
       } else {
         switch (c.tpv) {
-          case 2: launch_one<T, kPersistCsrVector, 2>(ctx, a, s); break;
-          case 4: launch_one<T, kPersistCsrVector, 4>(ctx, a, s); break;
-          case 8: launch_one<T, kPersistCsrVector, 8>(ctx, a, s); break;
-          case 16: launch_one<T, kPersistCsrVector, 16>(ctx, a, s); break;
-          default: launch_one<T, kPersistCsrVector, 32>(ctx, a, s); break;
+          case 2: launch_one<T, kPersistCsrVector, 2>(ctx, a, s, share); break;
+          case 4: launch_one<T, kPersistCsrVector, 4>(ctx, a, s, share); break;
+          case 8: launch_one<T, kPersistCsrVector, 8>(ctx, a, s, share); break;
+          case 16: launch_one<T, kPersistCsrVector, 16>(ctx, a, s, share); break;
+          default: launch_one<T, kPersistCsrVector, 32>(ctx, a, s, share); break;
         }
       }
       break;
@@ -251,7 +267,7 @@ void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a
       a.ld = e.ld;
       a.ec = e.col;
       a.ev = PersistVals<T>::ell(e);
-      launch_one<T, kPersistEll, 1>(ctx, a, s);
+      launch_one<T, kPersistEll, 1>(ctx, a, s, share);
       break;
     }
     case CP_FMT_SELL:
@@ -261,13 +277,13 @@ void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a
       a.cptr = m->sell.chunk_ptr;
       a.sc = m->sell.col;
       a.sv = PersistVals<T>::sell(m->sell);
-      launch_one<T, kPersistSell, 1>(ctx, a, s);
+      launch_one<T, kPersistSell, 1>(ctx, a, s, share);
       break;
     case CP_FMT_DIA:
       a.ndiag = (int)m->dia.ndiag;
       a.offs = m->dia.offs;
       a.dv = PersistVals<T>::dia(m->dia);
-      launch_one<T, kPersistDia, 1>(ctx, a, s);
+      launch_one<T, kPersistDia, 1>(ctx, a, s, share);
       break;
     default:
       CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent CG kernel for format %d", c.fmt);
@@ -277,8 +293,8 @@ void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a
 template bool persist_supported<double>(const cp_mat*, const cp_config&);
 template bool persist_supported<float>(const cp_mat*, const cp_config&);
 template void persist_launch<double>(cp_ctx*, cp_mat*, const cp_config&, PersistArgs<double>,
-                                     cudaStream_t);
+                                     cudaStream_t, int);
 template void persist_launch<float>(cp_ctx*, cp_mat*, const cp_config&, PersistArgs<float>,
-                                    cudaStream_t);
+                                    cudaStream_t, int);
 
 }  // namespace cp

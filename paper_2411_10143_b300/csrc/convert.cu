@@ -11,6 +11,14 @@
 
 namespace cp {
 
+void d2h_small(cp_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t s) {
+  CP_REQUIRE(bytes <= 4096, CP_ERR_INVALID, "staged copy too large");
+  void* pin = (s == ctx->side) ? ctx->pin_side : ctx->pin_main;
+  CP_CUDA(cudaMemcpyAsync(pin, src, bytes, cudaMemcpyDeviceToHost, s));
+  CP_CUDA(cudaStreamSynchronize(s));
+  std::memcpy(dst, pin, bytes);
+}
+
 static int grid_cap(cp_ctx* ctx, int64_t items, int block = kBlock) {
   int64_t g = (items + block - 1) / block;
   if (g > ctx->grid_stream) g = ctx->grid_stream;
@@ -285,7 +293,9 @@ void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15) {
   const int64_t words = (n + m->ncols - 1 + 31) / 32;
   void* scratch = nullptr;
   const size_t bytes = sizeof(FeatAcc) + 15 * sizeof(double) + words * sizeof(unsigned);
+  trace("features: start n=%lld", (long long)n);
   CP_CUDA(cudaMallocAsync(&scratch, bytes, s));
+  trace("features: scratch allocated");
   FeatAcc* acc = static_cast<FeatAcc*>(scratch);
   double* f = reinterpret_cast<double*>(static_cast<char*>(scratch) + sizeof(FeatAcc));
   unsigned* bm = reinterpret_cast<unsigned*>(f + 15);
@@ -297,9 +307,10 @@ void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15) {
     CP_LAUNCH(ctx, k_features_long, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, bm, acc);
     CP_LAUNCH(ctx, k_popcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, acc);
     CP_LAUNCH(ctx, k_features_final, 1, 1, 0, s, n, m->ncols, m->nnz, acc, f);
-    CP_CUDA(cudaMemcpyAsync(m->features, f, 15 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    trace("features: kernels queued");
+    d2h_small(ctx, m->features, f, 15 * sizeof(double), s);
+    trace("features: done");
     CP_CUDA(cudaFreeAsync(scratch, s));
-    CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     cudaFreeAsync(scratch, s);
     throw;
@@ -686,8 +697,8 @@ static void convert_ell(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   e.ld = (m->nrows + 31) / 32 * 32;
   check_budget(ctx, e.K * e.ld * 12, "ELL");
   try {
-    e.col = dalloc<int32_t>(e.K * e.ld);
-    e.val = dalloc<double>(e.K * e.ld);
+    e.col = dalloc_async<int32_t>(e.K * e.ld, s);
+    e.val = dalloc_async<double>(e.K * e.ld, s);
     CP_LAUNCH(ctx, k_ell_fill, grid_cap(ctx, e.ld), kBlock, 0, s, m->nrows, e.ld, e.K, m->rowptr,
               m->col, m->val, e.col, e.val);
     CP_CUDA(cudaStreamSynchronize(s));
@@ -706,7 +717,7 @@ static void convert_coo(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   c.val = m->val;
   c.owns_colval = false;
   try {
-    c.row = dalloc<int32_t>(m->nnz);
+    c.row = dalloc_async<int32_t>(m->nnz, s);
     CP_LAUNCH(ctx, k_coo_rows, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, m->rowptr, c.row);
     CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
@@ -724,10 +735,10 @@ static void convert_sell(cp_ctx* ctx, cp_mat* m, int64_t sigma, cudaStream_t s) 
   p.nchunks = (m->nrows + 31) / 32;
   int64_t* cnt = nullptr;
   try {
-    p.perm = dalloc<int32_t>(m->nrows);
-    p.chunk_len = dalloc<int32_t>(p.nchunks);
-    p.chunk_ptr = dalloc<int64_t>(p.nchunks + 1);
-    cnt = dalloc<int64_t>(p.nchunks);
+    p.perm = dalloc_async<int32_t>(m->nrows, s);
+    p.chunk_len = dalloc_async<int32_t>(p.nchunks, s);
+    p.chunk_ptr = dalloc_async<int64_t>(p.nchunks + 1, s);
+    cnt = dalloc_async<int64_t>(p.nchunks, s);
     if (sigma == 1) {
       CP_LAUNCH(ctx, k_iota, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, p.perm);
     } else {
@@ -742,19 +753,17 @@ static void convert_sell(cp_ctx* ctx, cp_mat* m, int64_t sigma, cudaStream_t s) 
     CP_LAUNCH(ctx, k_sell_widths, grid_cap(ctx, p.nchunks * 32), kBlock, 0, s, m->nrows,
               p.nchunks, m->rowptr, p.perm, p.chunk_len, cnt);
     exclusive_scan_i64(ctx, cnt, p.chunk_ptr, p.nchunks, s);
-    CP_CUDA(cudaMemcpyAsync(&p.slots, p.chunk_ptr + p.nchunks, sizeof(int64_t),
-                            cudaMemcpyDeviceToHost, s));
-    CP_CUDA(cudaStreamSynchronize(s));
-    dfree(cnt);
+    dfree_async(cnt, s);
     cnt = nullptr;
+    d2h_small(ctx, &p.slots, p.chunk_ptr + p.nchunks, sizeof(int64_t), s);
     check_budget(ctx, p.slots * 12, "SELL-C-sigma");
-    p.col = dalloc<int32_t>(p.slots);
-    p.val = dalloc<double>(p.slots);
+    p.col = dalloc_async<int32_t>(p.slots, s);
+    p.val = dalloc_async<double>(p.slots, s);
     CP_LAUNCH(ctx, k_sell_fill, grid_cap(ctx, p.nchunks * 32), kBlock, 0, s, m->nrows, p.nchunks,
               m->rowptr, m->col, m->val, p.perm, p.chunk_len, p.chunk_ptr, p.col, p.val);
     CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
-    dfree(cnt);
+    dfree_async(cnt, s);
     free_sell(p);
     throw;
   }
@@ -772,34 +781,33 @@ static void convert_hyb(cp_ctx* ctx, cp_mat* m, int64_t K, cudaStream_t s) {
   e.ld = (m->nrows + 31) / 32 * 32;
   check_budget(ctx, e.K * e.ld * 12, "HYB ELL part");
   try {
-    e.col = dalloc<int32_t>(e.K * e.ld);
-    e.val = dalloc<double>(e.K * e.ld);
+    e.col = dalloc_async<int32_t>(e.K * e.ld, s);
+    e.val = dalloc_async<double>(e.K * e.ld, s);
     CP_LAUNCH(ctx, k_ell_fill, grid_cap(ctx, e.ld), kBlock, 0, s, m->nrows, e.ld, e.K, m->rowptr,
               m->col, m->val, e.col, e.val);
-    cnt = dalloc<int64_t>(m->nrows);
-    off = dalloc<int64_t>(m->nrows + 1);
+    cnt = dalloc_async<int64_t>(m->nrows, s);
+    off = dalloc_async<int64_t>(m->nrows + 1, s);
     CP_LAUNCH(ctx, k_hyb_counts, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, K, m->rowptr,
               cnt);
     exclusive_scan_i64(ctx, cnt, off, m->nrows, s);
-    CP_CUDA(cudaMemcpyAsync(&c.n, off + m->nrows, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CP_CUDA(cudaStreamSynchronize(s));
+    d2h_small(ctx, &c.n, off + m->nrows, sizeof(int64_t), s);
     c.owns_colval = true;
-    c.row = dalloc<int32_t>(c.n);
-    c.col = dalloc<int32_t>(c.n);
-    c.val = dalloc<double>(c.n);
+    c.row = dalloc_async<int32_t>(c.n, s);
+    c.col = dalloc_async<int32_t>(c.n, s);
+    c.val = dalloc_async<double>(c.n, s);
     if (c.n > 0)
       CP_LAUNCH(ctx, k_hyb_coo_fill, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows, K,
                 m->rowptr, m->col, m->val, off, c.row, c.col, c.val);
     CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
-    dfree(cnt);
-    dfree(off);
+    dfree_async(cnt, s);
+    dfree_async(off, s);
     free_ell(e);
     free_coo(c);
     throw;
   }
-  dfree(cnt);
-  dfree(off);
+  dfree_async(cnt, s);
+  dfree_async(off, s);
   free_ell(m->hyb_ell);
   free_coo(m->hyb_coo);
   m->hyb_ell = e;
@@ -823,52 +831,52 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   int64_t *cnt = nullptr, *pos = nullptr;
   int32_t* lut = nullptr;
   try {
-    bm = dalloc<unsigned>(words);
-    cnt = dalloc<int64_t>(words);
-    pos = dalloc<int64_t>(words + 1);
-    lut = dalloc<int32_t>(span);
-    d.offs = dalloc<int32_t>(kDiaMax);
+    bm = dalloc_async<unsigned>(words, s);
+    cnt = dalloc_async<int64_t>(words, s);
+    pos = dalloc_async<int64_t>(words + 1, s);
+    lut = dalloc_async<int32_t>(span, s);
+    d.offs = dalloc_async<int32_t>(kDiaMax, s);
     CP_CUDA(cudaMemsetAsync(bm, 0, words * sizeof(unsigned), s));
     CP_LAUNCH(ctx, k_dia_mark, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, bm);
     CP_LAUNCH(ctx, k_dia_wordcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, cnt);
     exclusive_scan_i64(ctx, cnt, pos, words, s);
     CP_LAUNCH(ctx, k_dia_compact, grid_cap(ctx, words), kBlock, 0, s, n, words, bm, pos, d.offs,
               lut, (int64_t)kDiaMax);
-    CP_CUDA(cudaMemcpyAsync(&d.ndiag, pos + words, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    CP_CUDA(cudaStreamSynchronize(s));
+    d2h_small(ctx, &d.ndiag, pos + words, sizeof(int64_t), s);
     CP_REQUIRE(d.ndiag <= kDiaMax, CP_ERR_FOOTPRINT,
                "DIA needs %lld diagonals, more than the %d it accepts", (long long)d.ndiag,
                kDiaMax);
     check_budget(ctx, d.ndiag * n * 8, "DIA");
-    d.val = dalloc<double>(d.ndiag * n);
+    d.val = dalloc_async<double>(d.ndiag * n, s);
     CP_CUDA(cudaMemsetAsync(d.val, 0, d.ndiag * n * sizeof(double), s));
     CP_LAUNCH(ctx, k_dia_fill, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, m->val, lut,
               d.val);
     CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
-    dfree(bm);
-    dfree(cnt);
-    dfree(pos);
-    dfree(lut);
+    dfree_async(bm, s);
+    dfree_async(cnt, s);
+    dfree_async(pos, s);
+    dfree_async(lut, s);
     free_dia(d);
     throw;
   }
-  dfree(bm);
-  dfree(cnt);
-  dfree(pos);
-  dfree(lut);
+  dfree_async(bm, s);
+  dfree_async(cnt, s);
+  dfree_async(pos, s);
+  dfree_async(lut, s);
   m->dia = d;
   m->has_dia = true;
 }
 
-static void prepare_merge(cp_ctx* ctx, cp_mat* m) {
+static void prepare_merge(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   (void)ctx;
   const int64_t tiles = (m->nrows + m->nnz + kBlock * 7 - 1) / (kBlock * 7);
   if (m->merge_tiles == tiles && m->merge_carry_row) return;
   dfree(m->merge_carry_row);
   dfree(m->merge_carry_val);
-  m->merge_carry_row = dalloc<int32_t>(tiles);
-  m->merge_carry_val = dalloc<double>(tiles);
+  m->merge_carry_row = dalloc_async<int32_t>(tiles, s);
+  m->merge_carry_val = dalloc_async<double>(tiles, s);
+  CP_CUDA(cudaStreamSynchronize(s));
   m->merge_tiles = tiles;
 }
 
@@ -877,7 +885,7 @@ void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s)
   std::lock_guard<std::mutex> lock(m->mu);
   switch (cfg.fmt) {
     case CP_FMT_CSR:
-      if (cfg.algo == CP_ALGO_MERGE) prepare_merge(ctx, m);
+      if (cfg.algo == CP_ALGO_MERGE) prepare_merge(ctx, m, s);
       break;
     case CP_FMT_COO:
       if (!m->has_coo) convert_coo(ctx, m, s);
@@ -900,7 +908,7 @@ void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s)
 }
 
 static float* cast_copy(cp_ctx* ctx, const double* src, int64_t n, cudaStream_t s) {
-  float* d = dalloc<float>(n);
+  float* d = dalloc_async<float>(n, s);
   if (n > 0) CP_LAUNCH(ctx, k_cast_f32, grid_cap(ctx, n), kBlock, 0, s, n, src, d);
   return d;
 }

@@ -15,6 +15,9 @@ namespace cp {
 
 // ---------------------------------------------------------------- errors
 void set_error(const char* fmt, ...);
+// Timestamped trace line on stderr when the environment sets CASCADE_TRACE=1
+// (prediction / conversion / solve-loop steps; off by default).
+void trace(const char* fmt, ...);
 
 struct Error {
   cp_status status;
@@ -57,6 +60,20 @@ T* dalloc(size_t count) {
 }
 inline void dfree(void* p) {
   if (p) cudaFree(p);
+}
+
+// Stream-ordered temporaries: unlike cudaFree, cudaFreeAsync does not wait for
+// the whole device, so conversions on the side stream never stall behind the
+// solve running on the main stream.
+template <typename T>
+T* dalloc_async(size_t count, cudaStream_t s) {
+  void* p = nullptr;
+  if (count == 0) count = 1;
+  CP_CUDA(cudaMallocAsync(&p, count * sizeof(T), s));
+  return static_cast<T*>(p);
+}
+inline void dfree_async(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
 }
 
 constexpr int kBlock = 256;         // threads per block of the streaming kernels
@@ -114,6 +131,11 @@ struct cp_ctx {
   int grid_stream = 0;  // resident blocks of kBlock threads for streaming kernels
   cp::ModelSlot models[CP_NUM_STAGES];
   std::mutex model_mu;
+  // pinned staging for small device-to-host reads, one per stream: a copy into
+  // pageable memory can serialise behind the legacy default stream, which
+  // would stall the side stream's prediction behind a running solve
+  void* pin_main = nullptr;
+  void* pin_side = nullptr;
 };
 
 struct cp_mat {
@@ -172,6 +194,10 @@ template <typename T>
 void spmv_general(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, const T* x, T beta,
                   T* y, cudaStream_t s);
 
+// Copy `bytes` (<= 4096) of device memory to host `dst` through the stream's
+// pinned staging buffer and wait for the stream.
+void d2h_small(cp_ctx* ctx, void* dst, const void* src, size_t bytes, cudaStream_t s);
+
 // Exclusive scan of int64 counts in[0..n) into out[0..n] (out[n] = total).
 void exclusive_scan_i64(cp_ctx* ctx, const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 
@@ -190,6 +216,7 @@ struct Channel {
   std::vector<std::pair<int, cp_config>> published;  // (stage, configuration) in order
   std::atomic<int> count{0};
   std::atomic<bool> cancel{false};
+  std::atomic<bool> finished{false};  // the side work has ended (all stages, cancel or error)
   bool need_fp32 = false;  // the solve also needs FP32 values of every published format
   float t_features_ms = 0.f, t_predict_ms[3] = {0.f, 0.f, 0.f}, t_convert_ms = 0.f;
   cp_status status = CP_OK;  // first error of the side thread, if any

@@ -600,6 +600,8 @@ struct ConfigSource {
   bool persistent = true;     // run CG iterations in the persistent kernel when it supports cfg
   float t_persist_ms = 0.f;   // summed duration of the persistent launches
   int persist_iters = 0;      // iterations they ran
+  float t_persist_last_ms = 0.f;
+  int persist_last_iters = 0;
 
   void poll(int iter) {
     if (!ch) return;
@@ -705,11 +707,17 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
     int issued = 0;
     while (it < maxit) {
       cs.poll(it);
-      if (cs.persistent && persist_supported<T>(m, cs.cur)) {
+      // The persistent kernel runs only while no prediction work is pending on the
+      // side stream: a cooperative grid holds the device, so the side stream's
+      // kernels would wait for it.  Until the cascade has finished, iterations
+      // go one launch per step, interleaving with the side kernels.
+      const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire);
+      if (cs.persistent && side_idle && persist_supported<T>(m, cs.cur)) {
         // one cooperative launch runs iterations [it, maxit) until convergence, a
         // breakdown, or the host asks it to return at an iteration boundary
         // because the cascade published a new configuration
-        *ws.yield_h = 0;
+        int* yield_d = ws.yield();  // allocates the host-mapped flag on first use
+        *(volatile int*)ws.yield_h = 0;
         PersistArgs<T> pa_args;
         pa_args.x = x;
         pa_args.r = r;
@@ -719,7 +727,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         pa_args.pb = pb;
         pa_args.st = st;
         pa_args.mir = mir;
-        pa_args.yield = ws.yield();
+        pa_args.yield = yield_d;
         pa_args.it0 = it;
         pa_args.itmax = maxit;
         pa_args.tol2 = tol2;
@@ -727,14 +735,14 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         CP_CUDA(cudaEventCreate(&e0));
         CP_CUDA(cudaEventCreate(&e1));
         CP_CUDA(cudaEventRecord(e0, s));
-        persist_launch<T>(ctx, m, cs.cur, pa_args, s);
+        trace("solve: persistent launch at iteration %d (format %d)", it, cs.cur.fmt);
+        persist_launch<T>(ctx, m, cs.cur, pa_args, s, 1);
         CP_CUDA(cudaEventRecord(e1, s));
         for (;;) {
           const cudaError_t q = cudaEventQuery(e1);
           if (q == cudaSuccess) break;
           if (q != cudaErrorNotReady) CP_CUDA(q);
-          if (cs.ch && !*ws.yield_h &&
-              cs.ch->count.load(std::memory_order_acquire) > cs.applied)
+          if (cs.ch && !*ws.yield_h && cs.ch->count.load(std::memory_order_acquire) > cs.applied)
             *(volatile int*)ws.yield_h = 1;
           std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
@@ -744,7 +752,10 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         cudaEventDestroy(e1);
         cs.t_persist_ms += t;
         cs.persist_iters += ws.mir->iters - it;
+        cs.t_persist_last_ms = t;
+        cs.persist_last_iters = ws.mir->iters - it;
         it = ws.mir->iters;
+        trace("solve: persistent launch returned at iteration %d (%.3f ms)", it, t);
         if (ws.mir->done || ws.mir->status != CP_OK) break;
         continue;  // returned on request: the poll above applies the new configuration
       }
@@ -760,6 +771,8 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
         if (ws.mir->done) break;
       }
+      // the loop head hands the remaining iterations to the persistent kernel
+      // once the side work is over (the queued steps finish first, in stream order)
     }
     CP_CUDA(cudaStreamSynchronize(s));
     res.iters = ws.mir->iters;
@@ -791,6 +804,14 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
   }
   CP_CUDA(cudaMemcpyAsync(x_user, xw, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CP_CUDA(cudaStreamSynchronize(s));
+  if (cs.persist_iters > 0) {
+    unsigned long long tn[6];
+    CP_CUDA(cudaMemcpy(tn, st->t_ns, sizeof(tn), cudaMemcpyDeviceToHost));
+    const double k = 1e-3 / (cs.persist_iters > 0 ? cs.persist_iters : 1);
+    trace("persistent CG per iteration (us): spmv %.2f bar %.2f update %.2f bar %.2f "
+          "direction %.2f bar %.2f", tn[0] * k, tn[1] * k, tn[2] * k, tn[3] * k, tn[4] * k,
+          tn[5] * k);
+  }
   return res;
 }
 
@@ -985,6 +1006,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
   ch.need_fp32 = fp32;
   std::thread side;
   const bool predict = !opt.force && opt.mode != CP_MODE_PLAIN;
+  trace("solve: start n=%lld mode=%d precision=%d", (long long)m->nrows, opt.mode, opt.precision);
   if (predict) {
     cs.ch = &ch;
     if (opt.mode == CP_MODE_SEQUENTIAL) {
@@ -1035,6 +1057,8 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     info->n_spmv = cs.n_spmv;
     info->t_persist_ms = cs.t_persist_ms;
     info->persist_iters = cs.persist_iters;
+    info->t_persist_last_ms = cs.t_persist_last_ms;
+    info->persist_last_iters = cs.persist_last_iters;
     info->n_launches = (int32_t)(ctx->launches.load() - launches0);
     info->status = res.status;
   }

@@ -15,7 +15,12 @@ struct CgState {
   int stop;      // persistent kernel: return at the end of this iteration
   unsigned bar_count, bar_gen;  // grid barrier of the persistent kernel
   int bar_err;                  // a barrier wait gave up
+  // block 0's time in the persistent kernel's steps (ns): SpMV, barrier, update,
+  // barrier, direction, barrier
+  unsigned long long t_ns[6];
 };
+
+constexpr int kPersistBlock = 1024;  // one block per SM: 148 barrier arrivals, 148 partials
 
 // Host-mapped mirror written by the kernels that finish an iteration.
 struct Mirror {
@@ -80,8 +85,10 @@ struct PersistVals<float> {
 
 template <typename T>
 bool persist_supported(const cp_mat* m, const cp_config& c);
+// share = 1: the whole device; 2: half of every SM, leaving room for the
+// side stream's feature / prediction / conversion kernels while they run.
 template <typename T>
 void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a,
-                    cudaStream_t s);
+                    cudaStream_t s, int share);
 
 }  // namespace cp

@@ -333,9 +333,8 @@ int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s) {
   int h_out = -1;
   CP_LAUNCH(ctx, k_mlp_infer, 1, 64, 0, s, F, D, slot.d_params, slot.d_mu, slot.d_sd, d_out,
             (float*)nullptr);
-  CP_CUDA(cudaMemcpyAsync(&h_out, d_out, sizeof(int), cudaMemcpyDeviceToHost, s));
+  d2h_small(ctx, &h_out, d_out, sizeof(int), s);
   CP_CUDA(cudaFreeAsync(d_out, s));
-  CP_CUDA(cudaStreamSynchronize(s));
   return h_out;
 }
 
@@ -422,12 +421,17 @@ static int tpv_heuristic(const double* f) {
 }
 
 void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
+  struct Finish {  // tell the solve loop the side work has ended, however it ends
+    Channel* c;
+    ~Finish() { c->finished.store(true, std::memory_order_release); }
+  } finish{ch};
   using Clock = std::chrono::steady_clock;
   auto ms = [](Clock::time_point a) {
     return (float)std::chrono::duration<double, std::milli>(Clock::now() - a).count();
   };
   try {
     CP_CUDA(cudaSetDevice(ctx->device));  // the side thread's CUDA calls target ctx's GPU
+    trace("cascade: side thread started");
     auto t = Clock::now();
     double f[kFeat];
     compute_features(ctx, m, s, f);  // Table IV, on the side stream
@@ -448,6 +452,7 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
       }
     }
     ch->t_predict_ms[0] = ms(t);
+    trace("cascade: FORMAT -> %d", next.fmt);
     if (ch->cancel.load()) return;
     if (next.fmt != cfg.fmt) {
       t = Clock::now();
@@ -460,6 +465,7 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
         if (e.status != CP_ERR_FOOTPRINT) throw;
       }
       ch->t_convert_ms = ms(t);
+      trace("cascade: converted, publishing format %d", cfg.fmt);
       if (cfg.fmt != CP_FMT_CSR) ch->publish(0, cfg);
     }
     if (ch->cancel.load() || cfg.fmt != CP_FMT_CSR) return;

@@ -99,33 +99,43 @@ __device__ __forceinline__ T csr_vector_rows(int64_t n, const int32_t* __restric
 }
 
 // ------------------------------------------------------------------ ELL
-// Thread per row; chunks of 4 slots give 8 independent coalesced loads before
-// the gathers; padding (col -1) only follows a row's entries, so a padded
-// chunk ends the row.
+// Thread per row pair (i and i + stride); chunks of 4 slots give 16 independent
+// coalesced loads before the gathers; padding (col -1) only follows a row's
+// entries, so once both rows show padding the pair is done.
 template <typename T, bool GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T ell_rows(int64_t n, int64_t K, int64_t ld,
                                       const int32_t* __restrict__ ec, const T* __restrict__ ev,
                                       const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
                                       const T* __restrict__ dotv, int64_t tid, int64_t stride) {
   T acc = 0;
-  for (int64_t i = tid; i < n; i += stride) {
-    T sum = 0;
+  for (int64_t i0 = tid; i0 < n; i0 += 2 * stride) {
+    const int64_t i1 = i0 + stride;
+    const bool has1 = i1 < n;
+    T s0 = 0, s1 = 0;
     for (int64_t k0 = 0; k0 < K; k0 += 4) {
-      int32_t c[4];
-      T w[4];
+      int32_t c0[4], c1[4];
+      T w0[4], w1[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const bool in = k0 + u < K;
-        c[u] = in ? ld_stream(ec + (k0 + u) * ld + i) : -1;
-        w[u] = in ? ld_stream(ev + (k0 + u) * ld + i) : T(0);
+        c0[u] = in ? ld_stream(ec + (k0 + u) * ld + i0) : -1;
+        w0[u] = in ? ld_stream(ev + (k0 + u) * ld + i0) : T(0);
+        c1[u] = (in && has1) ? ld_stream(ec + (k0 + u) * ld + i1) : -1;
+        w1[u] = (in && has1) ? ld_stream(ev + (k0 + u) * ld + i1) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (c[u] >= 0) sum = fma(w[u], ld_x<COH>(x + c[u]), sum);
-      if (c[3] < 0) break;
+      for (int u = 0; u < 4; ++u) {
+        if (c0[u] >= 0) s0 = fma(w0[u], ld_x<COH>(x + c0[u]), s0);
+        if (c1[u] >= 0) s1 = fma(w1[u], ld_x<COH>(x + c1[u]), s1);
+      }
+      if (c0[3] < 0 && c1[3] < 0) break;
     }
-    store_row<T, GEN>(y, i, sum, alpha, beta);
-    if (DOT) acc = fma(sum, COH ? ld_cg(dotv + i) : dotv[i], acc);
+    store_row<T, GEN>(y, i0, s0, alpha, beta);
+    if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
+    if (has1) {
+      store_row<T, GEN>(y, i1, s1, alpha, beta);
+      if (DOT) acc = fma(s1, COH ? ld_cg(dotv + i1) : dotv[i1], acc);
+    }
   }
   return acc;
 }
@@ -173,30 +183,49 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
 }
 
 // ------------------------------------------------------------------ DIA
-// Thread per row; so[] holds the offsets (in shared memory); values and x are
-// read contiguously across the warp (no index arrays, no gather).
+// Thread per row pair (i and i + stride, so twice the loads in flight); so[]
+// holds the offsets (in shared memory); values and x are read contiguously
+// across the warp (no index arrays, no gather).  An FMA runs only for a real
+// diagonal (a warp-uniform test), since FP64 FMAs are as scarce as bytes here.
 template <typename T, bool GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const int32_t* so,
                                       const T* __restrict__ dv, const T* __restrict__ x,
                                       T* __restrict__ y, T alpha, T beta,
                                       const T* __restrict__ dotv, int64_t tid, int64_t stride) {
   T acc = 0;
-  for (int64_t i = tid; i < n; i += stride) {
-    T sum = 0;
+  for (int64_t i0 = tid; i0 < n; i0 += 2 * stride) {
+    const int64_t i1 = i0 + stride;
+    const bool has1 = i1 < n;
+    T s0 = 0, s1 = 0;
     for (int d0 = 0; d0 < ndiag; d0 += 4) {
-      T w[4], xv[4];
+      T w0[4], x0[4], w1[4], x1[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int64_t c = i + (d0 + u < ndiag ? so[d0 + u] : 0);
-        const bool in = d0 + u < ndiag && c >= 0 && c < ncols;
-        w[u] = in ? ld_stream(dv + (int64_t)(d0 + u) * n + i) : T(0);
-        xv[u] = in ? ld_x<COH>(x + c) : T(0);
+        const bool real = d0 + u < ndiag;
+        const int64_t off = real ? so[d0 + u] : 0;
+        const int64_t c0 = i0 + off, c1 = i1 + off;
+        const bool in0 = real && c0 >= 0 && c0 < ncols;
+        const bool in1 = real && has1 && c1 >= 0 && c1 < ncols;
+        const int64_t base = (int64_t)(d0 + u) * n;
+        w0[u] = in0 ? ld_stream(dv + base + i0) : T(0);
+        x0[u] = in0 ? ld_x<COH>(x + c0) : T(0);
+        w1[u] = in1 ? ld_stream(dv + base + i1) : T(0);
+        x1[u] = in1 ? ld_x<COH>(x + c1) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) sum = fma(w[u], xv[u], sum);
+      for (int u = 0; u < 4; ++u) {
+        if (d0 + u < ndiag) {
+          s0 = fma(w0[u], x0[u], s0);
+          s1 = fma(w1[u], x1[u], s1);
+        }
+      }
     }
-    store_row<T, GEN>(y, i, sum, alpha, beta);
-    if (DOT) acc = fma(sum, COH ? ld_cg(dotv + i) : dotv[i], acc);
+    store_row<T, GEN>(y, i0, s0, alpha, beta);
+    if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
+    if (has1) {
+      store_row<T, GEN>(y, i1, s1, alpha, beta);
+      if (DOT) acc = fma(s1, COH ? ld_cg(dotv + i1) : dotv[i1], acc);
+    }
   }
   return acc;
 }
