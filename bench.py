@@ -149,6 +149,35 @@ def cg_iteration_bytes(A, fmt):
     return spmv_bytes(A, fmt) + 9 * 8 * A.nrows
 
 
+# DRAM traffic of the persistent CG kernel from one ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum over a launch that ran a known number of iterations:
+# forced DIA, FP64, 3D Poisson 128^3, 429 iterations), per iteration.  Valid only
+# for the kernel sources it was taken on: the bench reports null traffic once
+# any of them changes (their SHA-256 differs).  The capture's summary is
+# profiles/k_cg_persist_dia_poisson3d_128.md.
+PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
+PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
+                   "sha256": "4fb4b57d665d2028600fcf32e33e71f8b65bbffbe3a8cc3304b6d951a2136b5c",
+                   "dram_bytes_per_iteration": 160370736.3}
+
+
+def persist_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for name in PERSIST_KERNEL_SOURCES:
+        h.update((ROOT / "paper_2411_10143_b300" / "csrc" / name).read_bytes())
+    return h.hexdigest()
+
+
+def persist_traffic(A, fmt, iters_per_launch):
+    """DRAM bytes of one persistent launch from the recorded capture, or None."""
+    t = PERSIST_TRAFFIC
+    if (fmt != t["format"] or A.nrows != t["n"] or not t["sha256"]
+            or persist_sources_sha256() != t["sha256"]):
+        return None
+    return t["dram_bytes_per_iteration"] * iters_per_launch
+
+
 def measured_peaks():
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -275,7 +304,7 @@ def run_ours(args, world, rank, local):
         torch.cuda.synchronize()
         barrier(world)
         region = time.perf_counter() - t0
-    launches = ctx.launch_count() - launches0
+    gpu_launches = ctx.launch_count() - launches0
     value = max_over_ranks(float(np.mean(tts)), world, "cuda")
     region = max_over_ranks(region, world, "cuda")
     last = infos[-1]
@@ -296,12 +325,14 @@ def run_ours(args, world, rank, local):
         launches = len(infos)
         avg_us = t_last / len(infos) * 1e3
         achieved = cg_iteration_bytes(A, fmt) * it_last / (t_last * 1e-3) / 1e9
+        traffic = persist_traffic(A, fmt, it_last / len(infos))
     else:
         kernel = f"spmv ({fmt})"
         per_launch = spmv_bytes(A, fmt)
         launches = n_spmv
         avg_us = t_spmv / max(n_spmv, 1) * 1e3
         achieved = spmv_bytes(A, fmt) * n_spmv / (t_spmv * 1e-3) / 1e9 if t_spmv > 0 else None
+        traffic = None
     extra = {}
     if rank == 0 and not args.no_compare:
         extra = comparisons(args, ctx, M, A, b, x, xs_d, stream, C)
@@ -312,10 +343,10 @@ def run_ours(args, world, rank, local):
         "data": "synthetic", "config": bench_config(A),
         "roofline": {"bound": "hbm", "kernel": kernel,
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None,
+                     "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_launch": per_launch,
                      "launches": launches, "avg_launch_us": avg_us},
-        "gpu_launches": int(launches),
+        "gpu_launches": int(gpu_launches),
         "clocks": clk.summary(),
         "solve": {"iters": last.iters, "final_cfg": repr(last.final_cfg),
                   "persist_iters": last.persist_iters, "t_persist_ms": last.t_persist_ms,
@@ -475,6 +506,39 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
             "resident_matrices": len(buckets), "failures": fails}
 
 
+def run_profile_cg(args):
+    """One configuration, no prediction: plain-mode CG on the bench workload with
+    the SpMV configuration forced, so the persistent kernel runs every iteration
+    in one launch (the case the profiles under profiles/ capture).  Prints one
+    JSON line per solve; not a bench line."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+
+    ctx = C.Context(0)
+    A, xs = workload()
+    M = ctx.load(A)
+    xs_d = torch.as_tensor(xs, device="cuda")
+    b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    M.spmv(xs_d, b)
+    cfg = C.config(args.profile_cg)
+    M.convert(cfg)
+    opts = C.default_opts(tol=TOL, mode=C.MODE_PLAIN, precision=args.profile_precision, profile=1)
+    for k in range(args.steps):
+        x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        info = M.solve_cg(b, x, opts, force=cfg)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        print(json.dumps({"solve": k, "config": repr(cfg), "precision": args.profile_precision,
+                          "ms": e0.elapsed_time(e1), "iters": info.iters,
+                          "persist_iters": info.persist_iters, "t_persist_ms": info.t_persist_ms,
+                          "us_per_iteration": info.t_persist_ms * 1e3 / max(info.persist_iters, 1),
+                          "relres_true": info.relres_true}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -486,7 +550,14 @@ def main():
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain / sequential / FP32-IR / end-to-end / CPU legs")
+    ap.add_argument("--profile-cg", default=None, metavar="FMT",
+                    help="profiling aid: forced-configuration CG solves (e.g. DIA), no bench line")
+    ap.add_argument("--profile-precision", type=int, default=0,
+                    help="with --profile-cg: 0 FP64, 1 FP32 inner solves in FP64 refinement")
     args = ap.parse_args()
+    if args.profile_cg:
+        run_profile_cg(args)
+        return
     if args.impl == "reference":
         world, rank, _ = dist_init("gloo")
         run_reference(args, world, rank)

@@ -64,6 +64,28 @@ __device__ __forceinline__ double bsum(double v, double* red) {
   return red[32];
 }
 
+// Block sum; thread 0 also forms g(total) (a quotient: FP64 divisions are
+// instruction sequences on the FP64 pipe, so one thread forms them); both go
+// to every thread.
+template <int BT, typename G>
+__device__ __forceinline__ double2 bsum_g(double v, double* red, G g) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (warp == 0) {
+    double s = lane < BT / 32 ? red[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) {
+      red[32] = s;
+      red[33] = g(s);
+    }
+  }
+  __syncthreads();
+  return make_double2(red[32], red[33]);
+}
+
 // FP64 residual r = b - A x (FP64 values) and ||r||^2
 template <int BT>
 __device__ double resid64(const BatchSys& S, double* red) {
@@ -107,25 +129,30 @@ __device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, dou
   rr = bsum<BT>(rr, red);
   const double stop = P.inner_tol * P.inner_tol * rr;
   int it = 0;
+  // Each thread accumulates its share of a dot product in FP32 (a few dozen
+  // terms at most: the inner solve is FP32 throughout); the block adds the
+  // shares in FP64.
   while (it < budget && rr > stop) {
     __syncthreads();
     spmv32<BT>(S, p, ap);
     __syncthreads();
-    double pap = 0.0;
-    for (int64_t i = threadIdx.x; i < n; i += BT) pap += (double)p[i] * (double)ap[i];
-    pap = bsum<BT>(pap, red);
-    if (!(pap > 0.0)) return -1 - it;  // breakdown: not SPD
-    const float alpha = (float)(rr / pap);
-    double rn = 0.0;
+    float pap_t = 0.f;
+    for (int64_t i = threadIdx.x; i < n; i += BT) pap_t = fmaf(p[i], ap[i], pap_t);
+    // alpha = rr / (p, Ap); -1 flags a breakdown (A not SPD)
+    const double alpha_d =
+        bsum_g<BT>((double)pap_t, red, [rr](double pap) { return pap > 0.0 ? rr / pap : -1.0; }).y;
+    if (alpha_d < 0.0) return -1 - it;
+    const float alpha = (float)alpha_d;
+    float rn_t = 0.f;
     for (int64_t i = threadIdx.x; i < n; i += BT) {
       d[i] = fmaf(alpha, p[i], d[i]);
       const float ri = fmaf(-alpha, ap[i], r[i]);
       r[i] = ri;
-      rn = fma((double)ri, (double)ri, rn);
+      rn_t = fmaf(ri, ri, rn_t);
     }
-    rn = bsum<BT>(rn, red);
-    const float beta = (float)(rn / rr);
-    rr = rn;
+    const double2 rb = bsum_g<BT>((double)rn_t, red, [rr](double rn) { return rn / rr; });
+    const float beta = (float)rb.y;
+    rr = rb.x;
     for (int64_t i = threadIdx.x; i < n; i += BT) p[i] = fmaf(beta, p[i], r[i]);
     ++it;
   }
@@ -209,14 +236,14 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
           hv[threadIdx.x] += s;
         }
         __syncthreads();
-        double wn = 0.0;
+        float wn_t = 0.f;
         for (int64_t i = threadIdx.x; i < n; i += BT) {
           float wi = w[i];
           for (int c = 0; c <= j; ++c) wi = fmaf(-(float)red[64 + c], V[(int64_t)c * n + i], wi);
           w[i] = wi;
-          wn = fma((double)wi, (double)wi, wn);
+          wn_t = fmaf(wi, wi, wn_t);
         }
-        wn = bsum<BT>(wn, red);
+        const double wn = bsum<BT>((double)wn_t, red);
         if (pass == 1 && threadIdx.x == 0) red[40] = wn;
       }
       // Givens rotation in FP64 (thread 0)
@@ -237,6 +264,7 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
         gs[j] = cs[j] * gs[j];
         red[41] = hn;
         red[42] = fabs(gs[j + 1]);
+        red[43] = hn > 0.0 ? 1.0 / hn : 0.0;
       }
       __syncthreads();
       const double hn = red[41];
@@ -246,7 +274,7 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
         conv = red[42] <= stop;
         break;
       }
-      const float inv2 = (float)(1.0 / hn);
+      const float inv2 = (float)red[43];
       for (int64_t i = threadIdx.x; i < n; i += BT) w[i] *= inv2;
     }
     // y = R^{-1} g, d += V y

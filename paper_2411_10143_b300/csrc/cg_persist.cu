@@ -3,16 +3,22 @@
 // phases per iteration are separated by grid-wide barriers instead of kernel
 // boundaries:
 //   1. Ap = A p with the format's row loop, and the block partials of (p, Ap)
-//   2. alpha = (r, r)/(Ap, p) (every block sums the partials in the same order);
-//      x += alpha p, r -= alpha Ap, block partials of (r, r)
-//   3. beta = (r+, r+)/(r, r); stop if ||r+|| <= tol ||b||; else p = r + beta p
+//   2. alpha = (r, r)/(Ap, p); r -= alpha Ap, block partials of (r, r)
+//   3. beta = (r+, r+)/(r, r); stop if ||r+|| <= tol ||b||; x += alpha p and,
+//      unless stopping, p = r + beta p
+// x is updated in phase 3 rather than phase 2 so that p is read once for both
+// of its uses; the values are the same as with the textbook order.  Every
+// block sums the previous phase's partials in the same fixed order, and one
+// thread per block forms alpha and beta (FP64 divisions are sequences on the
+// FP64 pipe, the unit that bounds this kernel on parts with a reduced FP64 rate).
 // The host asks the kernel to return at the next iteration boundary (to switch
 // to a newly predicted SpMV configuration) through a host-mapped flag that
 // block 0 reads in phase 2 and publishes to every block through the state.
 // The launch is cooperative, so every block is resident.  The grid barrier is
-// the library's own (an arrival counter and a generation word) with a time
-// limit: a wait that exceeds it records CP_ERR_TIMEOUT, and every block leaves
-// the loop at its next barrier; the iteration loop is bounded by itmax.
+// the library's own (a monotone arrival counter, zeroed by the host before the
+// launch) with a time limit: a wait that exceeds it records CP_ERR_TIMEOUT,
+// and every block leaves the loop at its next barrier; the iteration loop is
+// bounded by itmax.
 #include "common.cuh"
 #include "internal.cuh"
 #include "persist.cuh"
@@ -26,25 +32,23 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier with a time limit.  Returns false (in every thread of the
-// block) when the wait gave up or another block already did.
-__device__ __forceinline__ bool grid_barrier(CgState* st, long long timeout_ns) {
+// Grid-wide barrier with a time limit.  target: the arrival count that ends
+// this barrier (the block's running count of barriers times the grid size).
+// Returns false (in every thread of the block) when the wait gave up or
+// another block already did.
+__device__ __forceinline__ bool grid_barrier(CgState* st, unsigned target,
+                                             long long timeout_ns) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = &st->bar_gen;
+    volatile unsigned* cnt = &st->bar_count;
     volatile int* err = &st->bar_err;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&st->bar_count, 1u) + 1u;
+    __threadfence();  // this block's writes before its arrival
+    atomicAdd(&st->bar_count, 1u);
     int good = 1;
-    if (arrived == gridDim.x) {
-      st->bar_count = 0;
-      __threadfence();
-      atomicAdd(&st->bar_gen, 1u);
-    } else {
+    if ((int)(*cnt - target) < 0) {
       const unsigned long long t0 = global_ns();
-      while (*gen == g) {
+      while ((int)(*cnt - target) < 0) {
         if (*err) {
           good = 0;
           break;
@@ -54,10 +58,9 @@ __device__ __forceinline__ bool grid_barrier(CgState* st, long long timeout_ns) 
           good = 0;
           break;
         }
-        __nanosleep(8);
       }
     }
-    __threadfence();
+    __threadfence();  // the other blocks' writes before this block's reads
     ok = good && !*err;
   }
   __syncthreads();
@@ -85,22 +88,30 @@ __device__ __forceinline__ T spmv_phase(const PersistArgs<T>& a, const int32_t* 
                                     stride);
 }
 
+// Pairs handled per thread per trip of the vector loops: all of a trip's
+// loads are issued before its stores.
+constexpr int kPersistU = 1;
+
 template <typename T, int F, int TPV>
 __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> a) {
   // already converged (by iterations queued before this launch): nothing to do
   if (ld_cg(&a.st->done)) return;
-  __shared__ double red[40];
+  __shared__ double red[kPersistBlock + 4];
+  __shared__ double sc_val;  // alpha (phase 2) or beta (phase 3), formed by thread 0
+  __shared__ int sc_flag;    // breakdown (phase 2) or stop (phase 3)
   __shared__ int32_t so[F == kPersistDia ? kDiaMax : 1];
   if constexpr (F == kPersistDia) {
     for (int d = threadIdx.x; d < a.ndiag; d += blockDim.x) so[d] = a.offs[d];  // immutable
     __syncthreads();
   }
   using V = typename Vec2<T>::type;
+  constexpr int U = kPersistU;
   const int64_t n2 = a.n >> 1;
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
   CgState* st = a.st;
+  unsigned bar_target = 0;
   unsigned long long tmark = lead ? global_ns() : 0;
   auto lap = [&](int k) {  // block 0's step timer
     if (lead) {
@@ -109,102 +120,176 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
       tmark = now;
     }
   };
+  V* x2 = reinterpret_cast<V*>(a.x);
+  V* r2 = reinterpret_cast<V*>(a.r);
+  V* p2 = reinterpret_cast<V*>(a.p);
+  const V* q2 = reinterpret_cast<const V*>(a.ap);
   for (int it = a.it0; it < a.itmax; ++it) {
     const int slot = it & 1;
     // ---- phase 1: Ap = A p, partials of (p, Ap)
     {
       const T acc = spmv_phase<T, F, TPV>(a, so);
-      const double s = block_sum((double)acc, red);
+      const double s = block_sum_lean((double)acc, red);
       if (threadIdx.x == 0) a.pa[blockIdx.x] = s;
     }
     lap(0);
-    if (!grid_barrier(st, a.barrier_timeout_ns)) break;
+    bar_target += gridDim.x;
+    if (!grid_barrier(st, bar_target, a.barrier_timeout_ns)) break;
     lap(1);
-    // ---- phase 2: alpha; x += alpha p; r -= alpha Ap; partials of (r, r)
-    const double pap = reduce_partials_cg(a.pa, gridDim.x, red);
-    const double rr = ld_cg(&st->rr[slot]);
-    if (!(pap > 0.0) || !isfinite(pap)) {  // A not SPD, or overflow / NaN: every block stops
-      if (lead) {
-        st->status = CP_ERR_BREAKDOWN;
-        st->done = 1;
-        a.mir->status = CP_ERR_BREAKDOWN;
-        a.mir->done = 1;
+    // ---- phase 2: alpha; r -= alpha Ap; partials of (r, r)
+    if (threadIdx.x < 32) {
+      const double pap = warp_partials_cg(a.pa, gridDim.x);
+      if (threadIdx.x == 0) {
+        const bool bad = !(pap > 0.0) || !isfinite(pap);  // A not SPD, or overflow / NaN
+        const double alpha_d = bad ? 0.0 : ld_cg(&st->rr[slot]) / pap;
+        sc_val = alpha_d;
+        sc_flag = bad;
+        if (lead) {
+          if (bad) {
+            st->status = CP_ERR_BREAKDOWN;
+            st->done = 1;
+            a.mir->status = CP_ERR_BREAKDOWN;
+            a.mir->done = 1;
+          } else {
+            st->pap = pap;
+            st->alpha = alpha_d;
+          }
+          st->stop = *a.yield;  // the host's request, published to all blocks by the barrier
+        }
       }
-      break;
     }
-    const T alpha = (T)(rr / pap);
+    __syncthreads();
+    if (sc_flag) break;  // every block saw the same partials
+    const double alpha_d = sc_val;
+    const T alpha = (T)alpha_d;
     {
-      V* x2 = reinterpret_cast<V*>(a.x);
-      V* r2 = reinterpret_cast<V*>(a.r);
-      const V* p2 = reinterpret_cast<const V*>(a.p);
-      const V* q2 = reinterpret_cast<const V*>(a.ap);
       T acc = 0;
-      for (int64_t i = tid; i < n2; i += stride) {
-        const V xv = ld_cg(x2 + i), rv = ld_cg(r2 + i), pv = ld_cg(p2 + i), qv = ld_cg(q2 + i);
-        V xn, rn;
-        xn.x = fma(alpha, pv.x, xv.x);
-        xn.y = fma(alpha, pv.y, xv.y);
-        rn.x = fma(-alpha, qv.x, rv.x);
-        rn.y = fma(-alpha, qv.y, rv.y);
-        x2[i] = xn;
-        r2[i] = rn;
-        acc = fma(rn.x, rn.x, acc);
-        acc = fma(rn.y, rn.y, acc);
+      for (int64_t i0 = tid; i0 < n2; i0 += U * stride) {
+        V rv[U], qv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t i = i0 + u * stride;
+          if (i < n2) {
+            rv[u] = ld_cg(r2 + i);
+            qv[u] = ld_cg(q2 + i);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t i = i0 + u * stride;
+          if (i < n2) {
+            V rn;
+            rn.x = fma(-alpha, qv[u].x, rv[u].x);
+            rn.y = fma(-alpha, qv[u].y, rv[u].y);
+            r2[i] = rn;
+            acc = fma(rn.x, rn.x, acc);
+            acc = fma(rn.y, rn.y, acc);
+          }
+        }
       }
       if ((a.n & 1) && tid == 0) {
         const int64_t i = a.n - 1;
-        a.x[i] = fma(alpha, ld_cg(a.p + i), ld_cg(a.x + i));
         const T ri = fma(-alpha, ld_cg(a.ap + i), ld_cg(a.r + i));
         a.r[i] = ri;
         acc = fma(ri, ri, acc);
       }
-      const double s = block_sum((double)acc, red);
+      const double s = block_sum_lean((double)acc, red);
       if (threadIdx.x == 0) a.pb[blockIdx.x] = s;
     }
-    if (lead) {
-      st->pap = pap;
-      st->alpha = rr / pap;
-      st->stop = *a.yield;  // the host's request, published to all blocks by the barrier
-    }
     lap(2);
-    if (!grid_barrier(st, a.barrier_timeout_ns)) break;
+    bar_target += gridDim.x;
+    if (!grid_barrier(st, bar_target, a.barrier_timeout_ns)) break;
     lap(3);
-    // ---- phase 3: beta; convergence; p = r + beta p
-    const double rr_new = reduce_partials_cg(a.pb, gridDim.x, red);
-    const bool bad = !isfinite(rr_new);
-    const bool conv = rr_new <= a.tol2 * ld_cg(&st->bb);
-    if (lead) {
-      st->rr[slot ^ 1] = rr_new;
-      st->iters += 1;
-      a.mir->res = sqrt(rr_new);
-      a.mir->iters = st->iters;
-      if (bad) {
-        st->status = CP_ERR_BREAKDOWN;
-        a.mir->status = CP_ERR_BREAKDOWN;
-      }
-      if (conv || bad) {
-        st->done = 1;
-        a.mir->done = 1;
+    // ---- phase 3: beta; convergence; x += alpha p; p = r + beta p
+    if (threadIdx.x < 32) {
+      const double rr_new = warp_partials_cg(a.pb, gridDim.x);
+      if (threadIdx.x == 0) {
+        const bool bad = !isfinite(rr_new);
+        const bool conv = rr_new <= a.tol2 * ld_cg(&st->bb);
+        const double beta_d = rr_new / ld_cg(&st->rr[slot]);
+        sc_val = beta_d;
+        sc_flag = conv || bad;
+        if (lead) {
+          st->rr[slot ^ 1] = rr_new;
+          st->beta = beta_d;
+          st->iters += 1;
+          a.mir->res = sqrt(rr_new);
+          a.mir->iters = st->iters;
+          if (bad) {
+            st->status = CP_ERR_BREAKDOWN;
+            a.mir->status = CP_ERR_BREAKDOWN;
+          }
+          if (conv || bad) {
+            st->done = 1;
+            a.mir->done = 1;
+          }
+        }
       }
     }
-    if (conv || bad) break;
-    const T beta = (T)(rr_new / rr);
-    {
-      const V* r2 = reinterpret_cast<const V*>(a.r);
-      V* p2 = reinterpret_cast<V*>(a.p);
-      for (int64_t i = tid; i < n2; i += stride) {
-        const V rv = ld_cg(r2 + i), pv = ld_cg(p2 + i);
-        V pn;
-        pn.x = fma(beta, pv.x, rv.x);
-        pn.y = fma(beta, pv.y, rv.y);
-        p2[i] = pn;
+    __syncthreads();
+    const int fin = sc_flag;
+    const T beta = (T)sc_val;
+    if (fin) {  // last iteration: x only
+      for (int64_t i0 = tid; i0 < n2; i0 += U * stride) {
+        V xv[U], pv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t i = i0 + u * stride;
+          if (i < n2) {
+            xv[u] = ld_cg(x2 + i);
+            pv[u] = ld_cg(p2 + i);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t i = i0 + u * stride;
+          if (i < n2) {
+            V xn;
+            xn.x = fma(alpha, pv[u].x, xv[u].x);
+            xn.y = fma(alpha, pv[u].y, xv[u].y);
+            x2[i] = xn;
+          }
+        }
       }
-      if ((a.n & 1) && tid == 0) a.p[a.n - 1] = fma(beta, ld_cg(a.p + a.n - 1), ld_cg(a.r + a.n - 1));
+      if ((a.n & 1) && tid == 0) a.x[a.n - 1] = fma(alpha, ld_cg(a.p + a.n - 1), ld_cg(a.x + a.n - 1));
+      break;
+    }
+    for (int64_t i0 = tid; i0 < n2; i0 += U * stride) {
+      V xv[U], rv[U], pv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < n2) {
+          xv[u] = ld_cg(x2 + i);
+          rv[u] = ld_cg(r2 + i);
+          pv[u] = ld_cg(p2 + i);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t i = i0 + u * stride;
+        if (i < n2) {
+          V xn, pn;
+          xn.x = fma(alpha, pv[u].x, xv[u].x);
+          xn.y = fma(alpha, pv[u].y, xv[u].y);
+          pn.x = fma(beta, pv[u].x, rv[u].x);
+          pn.y = fma(beta, pv[u].y, rv[u].y);
+          x2[i] = xn;
+          p2[i] = pn;
+        }
+      }
+    }
+    if ((a.n & 1) && tid == 0) {
+      const int64_t i = a.n - 1;
+      const T pi = ld_cg(a.p + i);
+      a.x[i] = fma(alpha, pi, ld_cg(a.x + i));
+      a.p[i] = fma(beta, pi, ld_cg(a.r + i));
     }
     const int stop = *(volatile int*)&st->stop;
     if (stop) break;  // every block read the same value after the last barrier
     lap(4);
-    if (!grid_barrier(st, a.barrier_timeout_ns)) break;
+    bar_target += gridDim.x;
+    if (!grid_barrier(st, bar_target, a.barrier_timeout_ns)) break;
     lap(5);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int*)&st->bar_err) {
@@ -227,6 +312,8 @@ static void launch_one(cp_ctx* ctx, PersistArgs<T>& a, cudaStream_t s, int share
   int grid = ctx->num_sms * per_sm;
   if (grid > kMaxPartials) grid = kMaxPartials;
   void* args[] = {&a};
+  // the barrier's arrival counter counts up from zero in every launch
+  CP_CUDA(cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned), s));
   CP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid),
                                       dim3(kPersistBlock), args, 0, s));
   ctx->launches.fetch_add(1, std::memory_order_relaxed);

@@ -56,6 +56,30 @@ __device__ __forceinline__ double block_sum(double v, double* smem) {
   return s;
 }
 
+// Sum over the block with few FP64 additions, for blocks of a multiple of 128
+// threads: the values go to shared memory, 128 threads (one warp per
+// scheduler) each add blockDim.x / 128 of them in a fixed order, then a
+// shuffle tree and the 4 warp sums.  About 55 warp-wide FP64 adds for 1024
+// threads instead of the 165 of a shuffle tree in every warp, which matters
+// where the FP64 pipe is the bound.  buf holds blockDim.x + 4 doubles; the
+// result is valid in thread 0; every thread must call it.
+__device__ __forceinline__ double block_sum_lean(double v, double* buf) {
+  const int nt = blockDim.x;
+  __syncthreads();  // buf may still be read by a previous call
+  buf[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 128) {
+    s = buf[threadIdx.x];
+    for (int k = threadIdx.x + 128; k < nt; k += 128) s += buf[k];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) buf[nt + (threadIdx.x >> 5)] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) s = (buf[nt] + buf[nt + 1]) + (buf[nt + 2] + buf[nt + 3]);
+  return s;
+}
+
 // The same for G values at once (G small): out[g] valid in thread 0.
 template <int G>
 __device__ __forceinline__ void block_sum_multi(double (&v)[G], double* smem /*G*32*/) {
@@ -93,18 +117,25 @@ __device__ __forceinline__ double reduce_partials(const double* __restrict__ par
   return s;
 }
 
-// reduce_partials for partials written by other blocks of the same kernel
-__device__ __forceinline__ double reduce_partials_cg(const double* __restrict__ partials, int P,
-                                                     double* smem) {
+// Sum of P block partials in fixed order, valid in thread 0 only.  Scalars
+// derived from it (alpha, beta) are then formed once by thread 0 and handed to
+// the block through shared memory: an FP64 division is a multi-instruction
+// sequence on the FP64 pipe, which CG keeps saturated on parts with a reduced
+// FP64 rate, so every thread dividing would cost several microseconds a step.
+__device__ __forceinline__ double partials_sum0(const double* __restrict__ partials, int P,
+                                                double* smem) {
   double s = 0.0;
-  for (int i = threadIdx.x; i < P; i += blockDim.x) s += __ldcg(partials + i);
-  s = block_sum(s, smem);
-  const int last = blockDim.x >> 5;
-  if (threadIdx.x == 0) smem[last] = s;
-  __syncthreads();
-  s = smem[last];
-  __syncthreads();
-  return s;
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s += partials[i];
+  return block_sum(s, smem);
+}
+
+// Sum of P block partials written by other blocks of the same kernel, by one
+// warp (lane l adds partials l, l + 32, ... in order, then a fixed shuffle
+// tree): every lane holds the same value, and every block gets the same bits.
+__device__ __forceinline__ double warp_partials_cg(const double* __restrict__ partials, int P) {
+  double s = 0.0;
+  for (int i = threadIdx.x & 31; i < P; i += 32) s += __ldcg(partials + i);
+  return warp_sum(s);
 }
 
 template <typename T>

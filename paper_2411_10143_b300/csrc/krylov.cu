@@ -121,23 +121,29 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int64_t n, T* __restrict__
   };
   if (t < ntiles) load(t);
   __shared__ double red[40];
-  const double pap = reduce_partials(pa, PA, red);
-  const double rr = st->rr[slot];
-  if (!(pap > 0.0) || !isfinite(pap)) {  // A not SPD, or overflow / NaN
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      st->status = CP_ERR_BREAKDOWN;
-      st->done = 1;
-      mir->status = CP_ERR_BREAKDOWN;
-      mir->done = 1;
+  __shared__ double sc_alpha;
+  __shared__ int sc_bad;
+  const double pap = partials_sum0(pa, PA, red);
+  if (threadIdx.x == 0) {  // alpha formed once per block
+    const bool bad = !(pap > 0.0) || !isfinite(pap);  // A not SPD, or overflow / NaN
+    const double alpha_d = bad ? 0.0 : st->rr[slot] / pap;
+    sc_alpha = alpha_d;
+    sc_bad = bad;
+    if (blockIdx.x == 0) {
+      if (bad) {
+        st->status = CP_ERR_BREAKDOWN;
+        st->done = 1;
+        mir->status = CP_ERR_BREAKDOWN;
+        mir->done = 1;
+      } else {
+        st->pap = pap;
+        st->alpha = alpha_d;
+      }
     }
-    return;
   }
-  const double alpha_d = rr / pap;
-  const T alpha = (T)alpha_d;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->pap = pap;
-    st->alpha = alpha_d;
-  }
+  __syncthreads();
+  if (sc_bad) return;
+  const T alpha = (T)sc_alpha;
   T acc = 0;
   for (; t < ntiles; t += gridDim.x) {
     if (t != blockIdx.x) load(t);
@@ -197,27 +203,35 @@ __global__ void __launch_bounds__(kBlock) k_cg_direction(int64_t n, const T* __r
   };
   if (t < ntiles) load(t);
   __shared__ double red[40];
-  const double rr_new = reduce_partials(pb, PB, red);
-  const double rr = st->rr[slot];
-  const bool bad = !isfinite(rr_new);
-  const bool conv = rr_new <= tol2 * st->bb;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    st->rr[slot ^ 1] = rr_new;
-    st->iters += 1;
-    mir->res = sqrt(rr_new);
-    mir->iters = st->iters;
-    if (bad) {
-      st->status = CP_ERR_BREAKDOWN;
-      mir->status = CP_ERR_BREAKDOWN;
-    }
-    if (conv || bad) {
-      st->done = 1;
-      mir->done = 1;
+  __shared__ double sc_beta;
+  __shared__ int sc_stop;
+  const double rr_new = partials_sum0(pb, PB, red);
+  if (threadIdx.x == 0) {  // beta and the stopping test, once per block
+    const bool bad = !isfinite(rr_new);
+    const bool conv = rr_new <= tol2 * st->bb;
+    const double beta_d = rr_new / st->rr[slot];
+    sc_beta = beta_d;
+    sc_stop = conv || bad;
+    if (blockIdx.x == 0) {
+      st->rr[slot ^ 1] = rr_new;
+      st->iters += 1;
+      mir->res = sqrt(rr_new);
+      mir->iters = st->iters;
+      if (bad) {
+        st->status = CP_ERR_BREAKDOWN;
+        mir->status = CP_ERR_BREAKDOWN;
+      }
+      if (conv || bad) {
+        st->done = 1;
+        mir->done = 1;
+      } else {
+        st->beta = beta_d;
+      }
     }
   }
-  if (conv || bad) return;
-  const T beta = (T)(rr_new / rr);
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->beta = rr_new / rr;
+  __syncthreads();
+  if (sc_stop) return;
+  const T beta = (T)sc_beta;
   for (; t < ntiles; t += gridDim.x) {
     if (t != blockIdx.x) load(t);
 #pragma unroll

@@ -13,14 +13,15 @@ struct CgState {
   int status;    // CP_OK / CP_ERR_BREAKDOWN / CP_ERR_TIMEOUT
   int iters;     // completed iterations
   int stop;      // persistent kernel: return at the end of this iteration
-  unsigned bar_count, bar_gen;  // grid barrier of the persistent kernel
+  unsigned bar_count;  // arrivals at the persistent kernel's grid barriers (this launch)
   int bar_err;                  // a barrier wait gave up
   // block 0's time in the persistent kernel's steps (ns): SpMV, barrier, update,
   // barrier, direction, barrier
   unsigned long long t_ns[6];
 };
 
-constexpr int kPersistBlock = 1024;  // one block per SM: 148 barrier arrivals, 148 partials
+constexpr int kPersistBlock = 1024;  // one block per SM: 148 barrier arrivals, 148 partials;
+                                     // a multiple of 128 (block_sum_lean)
 
 // Host-mapped mirror written by the kernels that finish an iteration.
 struct Mirror {
