@@ -97,6 +97,14 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_first(self, timeout=10.0):
+        """Block until the first sample arrives: nvidia-smi's start-up (driver
+        queries that can briefly hold up CUDA calls) then falls outside the
+        timed region."""
+        t0 = time.time()
+        while self.proc and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.02)
+
     def __exit__(self, *exc):
         if self.proc:
             self.proc.terminate()
@@ -287,13 +295,16 @@ def run_ours(args, world, rank, local):
         e1.synchronize()
         return e0.elapsed_time(e1), info
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    barrier(world)
-    launches0 = ctx.launch_count()
-    infos, tts = [], []
+    # the clock sampler runs from before the warm-up to the end of the timed
+    # region, started early so that its own start-up is not timed
     with ClockSampler(local) as clk:
+        clk.wait_first()
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        barrier(world)
+        launches0 = ctx.launch_count()
+        infos, tts = [], []
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
@@ -415,6 +426,8 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
                   "h2d_bytes_per_step": int(rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8
                                             + bh.numel() * 8),
                   "d2h_bytes_per_step": int(xh.numel() * 8)}
+    if not args.no_sweep:
+        res["spmv_sweep"] = spmv_sweep_bench(ctx, measured_peaks()[0])
     if args.serve_requests > 0:
         res["serve"] = serve_bench(ctx, args.serve_requests)
     if args.gpus == 1 and not args.no_cpu_baseline:
@@ -431,6 +444,94 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
 
 
 # ------------------------------------------------------------------ serving leg
+def sweep_configs(C):
+    """Every SpMV configuration of the format space (Sec. III-B-2, Table III)."""
+    cfgs = [C.config("CSR", algo=C.ALGO_SCALAR)]
+    cfgs += [C.config("CSR", algo=C.ALGO_VECTOR, tpv=t) for t in (2, 4, 8, 16, 32)]
+    cfgs += [C.config("CSR", algo=C.ALGO_MERGE), C.config("COO"), C.config("ELL")]
+    cfgs += [C.config("SELL", sigma=s) for s in (1, 32, 1024, 8192)]
+    cfgs += [C.config("HYB"), C.config("DIA")]
+    return cfgs
+
+
+def time_spmv(ctx, M, cfg, x, y, reps, warm):
+    """Median and mean of reps back-to-back launches (CUDA events around each,
+    on the library's stream), after warm launches.  The matrices are larger
+    than L2, so every launch streams them from HBM."""
+    import torch
+    for _ in range(warm):
+        M.spmv(x, y, cfg)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    torch.cuda.synchronize()
+    for e0, e1 in ev:
+        e0.record(ctx.stream)
+        M.spmv(x, y, cfg)
+        e1.record(ctx.stream)
+    torch.cuda.synchronize()
+    t = np.array([e0.elapsed_time(e1) for e0, e1 in ev])
+    return float(np.median(t)), float(np.mean(t))
+
+
+def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=log):
+    """SpMV format/kernel sweep with cascaded prediction on the four sweep
+    matrices (3D Poisson 128^3, power law, uniform, banded; FP64 values
+    U[-1,1]): per matrix the predicted configuration's GB/s and fraction of the
+    measured HBM peak, the best and the CSR-scalar configuration beside it, and
+    the cost of the prediction (features + three stages) and of the conversion.
+    GB/s counts algorithmic bytes (padding excluded, x once)."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import workloads as W
+    out = {}
+    for k, (name, gen) in enumerate(W.spmv_sweep().items()):
+        A = gen()
+        M = ctx.load(A)
+        x = torch.as_tensor(W.vector(A.ncols, W.RHS_SEED_BASE + 1), device="cuda")
+        y = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cfg_p, stage_ms = M.predict()
+        t_pred = (time.perf_counter() - t0) * 1e3
+        t0 = time.perf_counter()
+        M.convert(cfg_p)
+        torch.cuda.synchronize()
+        t_conv = (time.perf_counter() - t0) * 1e3
+        cfgs = [cfg_p] if only_predicted else sweep_configs(C)
+        if repr(cfg_p) not in [repr(c) for c in cfgs]:
+            cfgs.append(cfg_p)
+        rows = {}
+        for cfg in cfgs:
+            try:
+                M.convert(cfg)
+            except C.CascadeError as e:  # padded format over its memory budget, DIA > 1024 offsets
+                rows[repr(cfg)] = {"skipped": str(e)[:80]}
+                continue
+            med, mean = time_spmv(ctx, M, cfg, x, y, reps, warm)
+            gbs = spmv_bytes(A, repr(cfg)) / (med * 1e-3) / 1e9
+            rows[repr(cfg)] = {"median_us": med * 1e3, "mean_us": mean * 1e3, "gbs": gbs,
+                               "frac": gbs / peak}
+        timed = {c: r for c, r in rows.items() if "median_us" in r}
+        best = min(timed, key=lambda c: timed[c]["median_us"])
+        pr = rows[repr(cfg_p)]
+        res = {"n": A.nrows, "nnz": A.nnz, "predicted": repr(cfg_p), "predicted_gbs": pr["gbs"],
+               "predicted_frac": pr["frac"], "predict_ms": t_pred, "predict_stage_ms":
+               [float(v) for v in stage_ms], "convert_ms": t_conv}
+        if not only_predicted:
+            base = rows["CSR-scalar"]
+            res.update({"best": best, "best_gbs": timed[best]["gbs"], "best_frac": timed[best]["frac"],
+                        "csr_scalar_gbs": base["gbs"],
+                        "speedup_vs_csr_scalar": base["median_us"] / pr["median_us"],
+                        "regret": pr["median_us"] / timed[best]["median_us"], "configs": rows})
+        out[name] = res
+        log_fn(f"spmv sweep {name}: predicted {res['predicted']} {pr['gbs']:.0f} GB/s "
+               f"({pr['frac']:.2f} of peak)" + ("" if only_predicted else
+               f", best {best} {timed[best]['gbs']:.0f} GB/s"))
+        M.free()
+        del x, y
+    return out
+
+
 def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     """Continuous-batching server under Poisson arrivals: n log-uniform in
     [1e3, 1e6], 40 % 2D/3D Poisson (CG), 30 % SPD power law (CG), 30 %
@@ -550,6 +651,9 @@ def main():
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain / sequential / FP32-IR / end-to-end / CPU legs")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the SpMV sweep leg")
+    ap.add_argument("--profile-spmv", action="store_true",
+                    help="profiling aid: the predicted SpMV of each sweep matrix, 3 launches")
     ap.add_argument("--profile-cg", default=None, metavar="FMT",
                     help="profiling aid: forced-configuration CG solves (e.g. DIA), no bench line")
     ap.add_argument("--profile-precision", type=int, default=0,
@@ -557,6 +661,14 @@ def main():
     args = ap.parse_args()
     if args.profile_cg:
         run_profile_cg(args)
+        return
+    if args.profile_spmv:
+        from paper_2411_10143_b300 import cascade as C
+        from paper_2411_10143_b300 import models
+        ctx = C.Context(0)
+        models.load_default(ctx)
+        print(json.dumps(spmv_sweep_bench(ctx, measured_peaks()[0], reps=3, warm=1,
+                                          only_predicted=True)), flush=True)
         return
     if args.impl == "reference":
         world, rank, _ = dist_init("gloo")

@@ -110,6 +110,7 @@ cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_
       CP_CUDA(cudaDeviceGetAttribute(&max_threads, cudaDevAttrMaxThreadsPerMultiProcessor, device));
       c->grid_stream = c->num_sms * (max_threads / kBlock);
       if (c->grid_stream > kMaxPartials) c->grid_stream = kMaxPartials;
+      spmv_set_attributes();
       if (main_stream) {
         c->main = static_cast<cudaStream_t>(main_stream);
       } else {

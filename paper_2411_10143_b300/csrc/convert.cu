@@ -676,8 +676,10 @@ void free_formats(cp_mat* m) {
   m->has_coo = m->has_ell = m->has_sell = m->has_hyb = m->has_dia = false;
   dfree(m->merge_carry_row);
   dfree(m->merge_carry_val);
+  dfree(m->merge_start);
   m->merge_carry_row = nullptr;
   m->merge_carry_val = nullptr;
+  m->merge_start = nullptr;
   m->merge_tiles = 0;
   dfree(m->val32);
   m->val32 = nullptr;
@@ -868,16 +870,21 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   m->has_dia = true;
 }
 
+// Merge-path set-up, once per matrix: the per-tile carries and the tile start
+// points (the matrix is fixed, so the diagonal searches are not repeated in
+// every SpMV).
 static void prepare_merge(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
-  (void)ctx;
-  const int64_t tiles = (m->nrows + m->nnz + kBlock * 7 - 1) / (kBlock * 7);
+  const int64_t tiles = (m->nrows + m->nnz + kMergeTile - 1) / kMergeTile;
   if (m->merge_tiles == tiles && m->merge_carry_row) return;
   dfree(m->merge_carry_row);
   dfree(m->merge_carry_val);
+  dfree(m->merge_start);
   m->merge_carry_row = dalloc_async<int32_t>(tiles, s);
   m->merge_carry_val = dalloc_async<double>(tiles, s);
-  CP_CUDA(cudaStreamSynchronize(s));
+  m->merge_start = dalloc_async<int32_t>(tiles + 1, s);
   m->merge_tiles = tiles;
+  merge_partition(ctx, m, s);
+  CP_CUDA(cudaStreamSynchronize(s));
 }
 
 void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s) {

@@ -78,6 +78,8 @@ inline void dfree_async(void* p, cudaStream_t s) {
 
 constexpr int kBlock = 256;         // threads per block of the streaming kernels
 constexpr int kMaxPartials = 4096;  // capacity of one block-partials buffer
+constexpr int kMergeItems = 7;      // merge-path items per thread
+constexpr int kMergeTile = kBlock * kMergeItems;
 
 struct ModelSlot {
   bool loaded = false;
@@ -157,6 +159,7 @@ struct cp_mat {
   // merge-path scratch: one carry (row, value) per tile
   int32_t* merge_carry_row = nullptr;
   double* merge_carry_val = nullptr;
+  int32_t* merge_start = nullptr;  // row index where each tile's merge path starts (tiles + 1)
   int64_t merge_tiles = 0;
   std::mutex mu;       // serialises conversions issued by the side thread and the caller
   std::mutex feat_mu;  // serialises the feature computation
@@ -190,6 +193,11 @@ template <typename T>
 int dot_partials(cp_ctx* ctx, int64_t n, const T* a, const T* b, double* partials,
                  const int* skip, cudaStream_t s);
 // General y = alpha A x + beta y.
+// merge_start[t] for every tile boundary t = 0..tiles (one search per boundary)
+void merge_partition(cp_ctx* ctx, cp_mat* m, cudaStream_t s);
+// shared-memory carve-out of the kernels that stage tiles in shared memory
+void spmv_set_attributes();
+
 template <typename T>
 void spmv_general(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, const T* x, T beta,
                   T* y, cudaStream_t s);

@@ -54,13 +54,13 @@ __global__ void __launch_bounds__(kBlock) k_csr_vector(
 // The merge of the row-end offsets rowptr[1..n] with the non-zero indices
 // 0..nnz-1 is cut into tiles of equal length (n + nnz items in total), so a
 // 50k-entry row costs the same per item as a 3-entry row.  A tile's start is
-// found by a binary search along its diagonal; its row ends are staged in
+// found once per matrix by a binary search along its diagonal
+// (k_merge_partition; the allocation-free entry point searches in the kernel
+// instead, tile_start = null).  The block stages the tile's row ends in
 // shared memory; each thread walks kMergeItems items.  Rows that a thread
 // finishes are written directly; partial rows are combined inside the block,
 // and the partial of the row still open at the tile's end becomes the tile's
 // carry, added by k_merge_fixup.
-constexpr int kMergeItems = 7;
-constexpr int kMergeTile = kBlock * kMergeItems;
 
 // First split point (i = row ends consumed, k = non-zeros consumed) on diagonal
 // d of the merge path, with ties taking the row end after the non-zeros < it.
@@ -80,8 +80,8 @@ template <typename T, bool GEN>
 __global__ void __launch_bounds__(kBlock) k_csr_merge(
     int64_t n, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
-    int64_t ntiles, int32_t* __restrict__ carry_row, T* __restrict__ carry_val,
-    const int* __restrict__ skip) {
+    int64_t ntiles, const int32_t* __restrict__ tile_start, int32_t* __restrict__ carry_row,
+    T* __restrict__ carry_val, const int* __restrict__ skip) {
   if (skip && *skip) return;
   __shared__ int32_t s_end[kMergeTile + 1];
   __shared__ int64_t s_bounds[2];
@@ -92,11 +92,15 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t d0 = t * kMergeTile;
     const int64_t d1 = d0 + kMergeTile < total ? d0 + kMergeTile : total;
-    if (threadIdx.x == 0) s_bounds[0] = merge_search(d0, row_end, n, nnz);
-    if (threadIdx.x == 32) s_bounds[1] = merge_search(d1, row_end, n, nnz);
+    if (tile_start) {
+      if (threadIdx.x < 2) s_bounds[threadIdx.x] = tile_start[t + threadIdx.x];
+    } else {
+      if (threadIdx.x == 0) s_bounds[0] = merge_search(d0, row_end, n, nnz);
+      if (threadIdx.x == 32) s_bounds[1] = merge_search(d1, row_end, n, nnz);
+    }
     __syncthreads();
     const int64_t i0 = s_bounds[0], i1 = s_bounds[1];
-    const int64_t k0 = d0 - i0;
+    const int64_t k0 = d0 - i0, k1 = d1 - i1;
     // stage row_end[i0 .. min(i1, n-1)]
     const int64_t last = i1 < n ? i1 : n - 1;
     for (int64_t r = i0 + threadIdx.x; r <= last; r += blockDim.x) s_end[r - i0] = row_end[r];
@@ -105,8 +109,7 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
     int64_t dt = d0 + (int64_t)threadIdx.x * kMergeItems;
     if (dt > d1) dt = d1;
     // search rows i in [i0, i1] with i + k = dt and k in [k0, d1 - i1]
-    const int64_t kmax = d1 - i1;
-    int64_t a = dt - kmax > i0 ? dt - kmax : i0;
+    int64_t a = dt - k1 > i0 ? dt - k1 : i0;
     int64_t b = dt - k0 < i1 ? dt - k0 : i1;
     while (a < b) {
       const int64_t mid = (a + b) >> 1;
@@ -150,6 +153,17 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
       carry_val[t] = c;
     }
     __syncthreads();
+  }
+}
+
+// tile_start[t] = first split row of tile t's diagonal, t = 0..ntiles
+__global__ void k_merge_partition(int64_t n, int64_t nnz, const int32_t* __restrict__ rp,
+                                  int64_t ntiles, int32_t* __restrict__ tile_start) {
+  const int64_t total = n + nnz;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = t * kMergeTile < total ? t * kMergeTile : total;
+    tile_start[t] = (int32_t)merge_search(d, rp + 1, n, nnz);
   }
 }
 
@@ -206,42 +220,164 @@ __global__ void __launch_bounds__(kBlock) k_dia(
   write_partial<DOT>((double)acc, partials);
 }
 
-// ------------------------------------------------------------------ COO (segmented)
-// Each warp takes 32 * kCooPerLane consecutive entries; a segmented warp scan
-// by row sums each row's run and the run's last lane adds it to y atomically.
-// y must already hold the rest of the row (0, beta*y, or HYB's ELL part).
-constexpr int kCooPerLane = 8;
+// ------------------------------------------------------------------ COO (tiled segmented sums)
+// A block takes a tile of kCooTile consecutive entries (sorted by row); each
+// thread loads its kCooItems consecutive entries into registers (the lanes of
+// a warp read adjacent runs, so the seven loads share their cache lines),
+// gathers x for all of them, and sums them row by row in a fully unrolled walk
+// (one FMA per entry).  A row inside one thread's entries is written
+// directly.  A row that spans threads is completed by the thread that holds
+// its last entry, which adds the partials of the preceding threads' last
+// segments from shared memory.  A row that touches the tile's first or last
+// entry may have entries in another tile and is added with an atomic.  ADD: y
+// already holds the rest of the row (beta*y, or HYB's ELL part) and every
+// write adds to it; otherwise y is zero and a row completed in one place is
+// stored.
+constexpr int kCooItems = 7;
+constexpr int kCooTile = kBlock * kCooItems;
 
+constexpr int kCooChain = 4;  // threads walked back serially before the scan takes over
+
+// Segmented inclusive scan of the thread partials part[] in thread order, a
+// run (segment) starting at a thread whose last segment began inside it
+// (multi) or whose last row differs from the previous thread's: the result in
+// thread t is the sum of part[] from the start of t's run to t.  A shuffle scan
+// inside each warp, then the runs that cross warp boundaries take the carry of
+// the preceding warps (at most blockDim.x / 32 steps).  Every thread calls it.
 template <typename T>
+__device__ __forceinline__ T coo_run_scan(const int32_t* last, const T* part, const int8_t* multi,
+                                          T* wsum, int8_t* whead) {
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  T v = part[t];
+  bool f = t == 0 || multi[t] || last[t - 1] != last[t];  // a run starts here
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T up = __shfl_up_sync(0xffffffffu, v, o);
+    const bool fup = __shfl_up_sync(0xffffffffu, (int)f, o) != 0;
+    if (lane >= o) {
+      if (!f) v += up;
+      f = f || fup;
+    }
+  }
+  if (lane == 31) {
+    wsum[w] = v;
+    whead[w] = f;
+  }
+  __syncthreads();
+  if (!f) {  // the run began before this warp: add the preceding warps' tails
+    for (int q = w - 1; q >= 0; --q) {
+      v += wsum[q];
+      if (whead[q]) break;
+    }
+  }
+  return v;
+}
+
+template <typename T, bool ADD>
+__device__ __forceinline__ void coo_put(T* y, int32_t r, T alpha, T s) {
+  y[r] = ADD ? fma(alpha, s, y[r]) : alpha * s;
+}
+
+template <typename T, bool ADD>
 __global__ void __launch_bounds__(kBlock) k_coo(
     int64_t nnz, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
     const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, T alpha,
     const int* __restrict__ skip) {
   if (skip && *skip) return;
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t chunk = 32 * kCooPerLane;
-  for (int64_t base = warp * chunk; base < nnz; base += nwarps * chunk) {
-#pragma unroll 2
-    for (int j = 0; j < kCooPerLane; ++j) {
-      const int64_t idx = base + j * 32 + lane;
-      int32_t r = -1;
-      T p = 0;
-      if (idx < nnz) {
-        r = ld_stream(row + idx);
-        p = ld_stream(val + idx) * ld_ro(x + ld_stream(col + idx));
-      }
+  __shared__ int32_t s_first[kBlock + 1];  // row of each thread's first entry (-1: none)
+  __shared__ int32_t s_last[kBlock];       // row of each thread's last segment
+  __shared__ T s_part[kBlock];             // that segment's partial sum
+  __shared__ int8_t s_multi[kBlock];       // the thread's entries span more than one row
+  __shared__ T s_scan[kBlock];             // segmented scan of the partials (long runs)
+  __shared__ T s_wsum[kBlock / 32];
+  __shared__ int8_t s_whead[kBlock / 32];
+  const int64_t ntiles = (nnz + kCooTile - 1) / kCooTile;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t e0 = t * kCooTile;
+    const int cnt = (int)(nnz - e0 < kCooTile ? nnz - e0 : kCooTile);
+    const int j0 = threadIdx.x * kCooItems;
+    const int mine = cnt - j0 < 0 ? 0 : (cnt - j0 < kCooItems ? cnt - j0 : kCooItems);
+    const int64_t b = e0 + j0;
+    int32_t r[kCooItems], c[kCooItems];
+    T w[kCooItems], xv[kCooItems];
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const T up = __shfl_up_sync(0xffffffffu, p, o);
-        const int32_t rup = __shfl_up_sync(0xffffffffu, r, o);
-        if (lane >= o && rup == r) p += up;
-      }
-      const int32_t rnext = __shfl_down_sync(0xffffffffu, r, 1);
-      const bool tail = (lane == 31) || (rnext != r);
-      if (tail && r >= 0) atomicAdd(y + r, alpha * p);
+    for (int u = 0; u < kCooItems; ++u) {
+      const bool in = u < mine;
+      // cached loads: the seven loads of a warp read the same lines in turn
+      r[u] = in ? ld_ro(row + b + u) : -1;
+      c[u] = in ? ld_ro(col + b + u) : 0;
+      w[u] = in ? ld_ro(val + b + u) : T(0);
     }
+#pragma unroll
+    for (int u = 0; u < kCooItems; ++u) xv[u] = u < mine ? ld_ro(x + c[u]) : T(0);
+    const int32_t first = r[0];
+    int32_t cur = r[0];
+    T head = 0, sum = 0;
+    bool multi = false;
+#pragma unroll
+    for (int u = 0; u < kCooItems; ++u) {
+      if (u < mine) {
+        if (u > 0 && r[u] != cur) {
+          if (!multi) head = sum;  // the first segment closes
+          else coo_put<T, ADD>(y, cur, alpha, sum);  // a row inside this thread only
+          multi = true;
+          cur = r[u];
+          sum = 0;
+        }
+        sum = fma(w[u], xv[u], sum);
+      }
+    }
+    s_first[threadIdx.x] = first;
+    s_last[threadIdx.x] = cur;
+    s_part[threadIdx.x] = sum;
+    s_multi[threadIdx.x] = multi;
+    if (threadIdx.x == 0) s_first[kBlock] = -1;
+    __syncthreads();
+    const int32_t tile_row0 = s_first[0];
+    const bool last_in_tile = mine > 0 && j0 + mine == cnt;
+    const bool ends_here = mine > 0 && (last_in_tile || s_first[threadIdx.x + 1] != cur);
+    // Sums of the runs of thread partials that complete a row here: the first
+    // row's (for a thread whose entries span rows) and the last row's.  Short
+    // runs are walked (at most kCooChain threads back); if any run is longer
+    // (rows of hundreds of entries), the whole block takes a segmented scan.
+    T head_cs = head, tail_cs = 0;
+    bool long_run = false;
+    if (multi) {
+      int j = (int)threadIdx.x - 1, k = 0;
+      for (; j >= 0 && s_last[j] == first && k < kCooChain; --j, ++k) {
+        head_cs += s_part[j];
+        if (s_multi[j]) break;  // the row started in thread j
+      }
+      long_run |= j >= 0 && k == kCooChain && s_last[j] == first;
+    }
+    if (ends_here) {
+      int j = (int)threadIdx.x, k = 0;
+      for (; j >= 0 && s_last[j] == cur && k < kCooChain; --j, ++k) {
+        tail_cs += s_part[j];
+        if (s_multi[j]) break;
+      }
+      long_run |= j >= 0 && k == kCooChain && s_last[j] == cur;
+    }
+    if (__syncthreads_or(long_run)) {
+      const T scan = coo_run_scan(s_last, s_part, s_multi, s_wsum, s_whead);
+      s_scan[threadIdx.x] = scan;
+      __syncthreads();
+      if (multi)
+        head_cs = head + (threadIdx.x > 0 && s_last[threadIdx.x - 1] == first
+                              ? s_scan[threadIdx.x - 1] : T(0));
+      tail_cs = scan;
+    }
+    if (multi) {
+      if (tile_row0 == first) atomicAdd(y + first, alpha * head_cs);  // may continue from the last tile
+      else coo_put<T, ADD>(y, first, alpha, head_cs);
+    }
+    if (ends_here) {
+      // atomically if the row touches the tile's first or last entry (other
+      // tiles may hold entries of it)
+      if (last_in_tile || tile_row0 == cur) atomicAdd(y + cur, alpha * tail_cs);
+      else coo_put<T, ADD>(y, cur, alpha, tail_cs);
+    }
+    __syncthreads();
   }
 }
 
@@ -315,6 +451,38 @@ static int grid_for(cp_ctx* ctx, int64_t work_items) {
   return (int)(g < 1 ? 1 : g);
 }
 
+void merge_partition(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
+  CP_LAUNCH(ctx, k_merge_partition, grid_for(ctx, m->merge_tiles + 1), kBlock, 0, s, m->nrows,
+            m->nnz, m->rowptr, m->merge_tiles, m->merge_start);
+}
+
+// The merge-path and COO kernels stage ~25-40 KB of a tile in shared memory:
+// prefer the largest shared-memory carve-out so that several blocks share an SM.
+void spmv_set_attributes() {
+  const int carve = cudaSharedmemCarveoutMaxShared;
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<double, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<double, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<float, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<float, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_coo<double, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_coo<double, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_coo<float, false>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_coo<float, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+}
+
+static int coo_grid(cp_ctx* ctx, int64_t nnz) {
+  const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
+  return (int)(tiles < 1 ? 1 : tiles < ctx->grid_stream ? tiles : ctx->grid_stream);
+}
+
 // One routine for both forms: GEN = general alpha/beta, DOT = fused partials.
 // skip (device flag, may be null): when set at launch time the kernels return
 // at once, so a converged solve's queued iterations cost only their launch.
@@ -335,8 +503,8 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
       if (cfg.algo == CP_ALGO_MERGE) {
         const int g = (int)(m->merge_tiles < ctx->grid_stream ? m->merge_tiles : ctx->grid_stream);
         CP_LAUNCH(ctx, (k_csr_merge<T, GEN>), g > 0 ? g : 1, kBlock, 0, s, n, m->nnz, m->rowptr,
-                  m->col, v, x, y, alpha, beta, m->merge_tiles, m->merge_carry_row,
-                  reinterpret_cast<T*>(m->merge_carry_val), skip);
+                  m->col, v, x, y, alpha, beta, m->merge_tiles, m->merge_start,
+                  m->merge_carry_row, reinterpret_cast<T*>(m->merge_carry_val), skip);
         CP_LAUNCH(ctx, k_merge_fixup<T>, grid_for(ctx, m->merge_tiles), kBlock, 0, s,
                   m->merge_tiles, m->merge_carry_row,
                   reinterpret_cast<const T*>(m->merge_carry_val), y, GEN ? alpha : T(1), skip);
@@ -372,7 +540,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
                 m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, nullptr, nullptr,
                 skip);
       if (m->hyb_coo.n > 0)
-        CP_LAUNCH(ctx, k_coo<T>, grid_for(ctx, (m->hyb_coo.n + kCooPerLane - 1) / kCooPerLane),
+        CP_LAUNCH(ctx, (k_coo<T, true>), coo_grid(ctx, m->hyb_coo.n),
                   kBlock, 0, s, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
                   Vals<T>::coo(m->hyb_coo), x, y, GEN ? alpha : T(1), skip);
       break;
@@ -385,10 +553,12 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
     }
     case CP_FMT_COO: {
       CP_LAUNCH(ctx, k_scale<T>, grid_for(ctx, n), kBlock, 0, s, n, y, GEN ? beta : T(0), skip);
-      if (m->nnz > 0)
-        CP_LAUNCH(ctx, k_coo<T>, grid_for(ctx, (m->nnz + kCooPerLane - 1) / kCooPerLane), kBlock,
-                  0, s, m->nnz, m->coo.row, m->col, Vals<T>::csr(m), x, y, GEN ? alpha : T(1),
-                  skip);
+      if (m->nnz > 0 && GEN && beta != T(0))
+        CP_LAUNCH(ctx, (k_coo<T, true>), coo_grid(ctx, m->nnz), kBlock, 0, s, m->nnz, m->coo.row,
+                  m->col, Vals<T>::csr(m), x, y, alpha, skip);
+      else if (m->nnz > 0)
+        CP_LAUNCH(ctx, (k_coo<T, false>), coo_grid(ctx, m->nnz), kBlock, 0, s, m->nnz,
+                  m->coo.row, m->col, Vals<T>::csr(m), x, y, GEN ? alpha : T(1), skip);
       break;
     }
     default:
@@ -414,7 +584,13 @@ int spmv_solver(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, const T* x, T* y, 
 template <typename T>
 void spmv_general(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, const T* x, T beta,
                   T* y, cudaStream_t s) {
-  spmv_dispatch<T, true, false>(ctx, m, cfg, alpha, x, beta, y, nullptr, nullptr, nullptr, s);
+  // y = A x is the plain form bit for bit (1 * s = s, and beta = 0 never reads
+  // y); it saves the scaling and the test of beta, two FP64-pipe operations a
+  // row, in kernels the FP64 pipe bounds
+  if (alpha == T(1) && beta == T(0))
+    spmv_dispatch<T, false, false>(ctx, m, cfg, T(1), x, T(0), y, nullptr, nullptr, nullptr, s);
+  else
+    spmv_dispatch<T, true, false>(ctx, m, cfg, alpha, x, beta, y, nullptr, nullptr, nullptr, s);
 }
 
 template <typename T>
@@ -470,6 +646,7 @@ static const NoAllocDevice& noalloc_setup(int dev) {
     CP_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&d.carry_row), g_noalloc_carry_row));
     CP_CUDA(cudaGetSymbolAddress(reinterpret_cast<void**>(&d.carry_val), g_noalloc_carry_val));
     CP_CUDA(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    spmv_set_attributes();  // function attributes only: allocates nothing
     d.ready = true;
   }
   return d;
@@ -501,8 +678,8 @@ extern "C" cp_status cp_spmv_csr_merge_noalloc(int64_t nrows, int64_t ncols, int
     const int64_t cap = (int64_t)d.num_sms * 8;
     const int grid = (int)(tiles < cap ? tiles : cap);
     k_csr_merge<double, false><<<grid, kBlock, 0, s>>>(nrows, nnz, rowptr, col, val, x, y, 1.0,
-                                                        0.0, tiles, d.carry_row, d.carry_val,
-                                                        nullptr);
+                                                        0.0, tiles, nullptr, d.carry_row,
+                                                        d.carry_val, nullptr);
     CP_CUDA(cudaGetLastError());
     const int64_t fg = (tiles + kBlock - 1) / kBlock;
     k_merge_fixup<double><<<(int)(fg < cap ? fg : cap), kBlock, 0, s>>>(

@@ -98,6 +98,31 @@ __device__ __forceinline__ T csr_vector_rows(int64_t n, const int32_t* __restric
   return acc;
 }
 
+// Compile-time slot count for the unrolled loops below.
+template <int R>
+struct Slots {
+  static constexpr int value = R;
+};
+
+// Runs f(k0, Slots<4>) over the full chunks of 4 slots in [0, w), then once
+// with the exact remainder (1 to 3 slots).  w is the same in every lane of the
+// warp (ELL width, a SELL chunk's width, the DIA diagonal count), so the
+// remainder branch is uniform and no padding slot issues a predicated-off FMA:
+// where the FP64 pipe bounds the kernel, a slot with no work costs as much as
+// one with work.  f returns true to stop early.
+template <typename F>
+__device__ __forceinline__ void for_slots(int64_t w, F&& f) {
+  int64_t k0 = 0;
+  for (; k0 + 4 <= w; k0 += 4)
+    if (f(k0, Slots<4>{})) return;
+  switch (w - k0) {
+    case 3: f(k0, Slots<3>{}); break;
+    case 2: f(k0, Slots<2>{}); break;
+    case 1: f(k0, Slots<1>{}); break;
+    default: break;
+  }
+}
+
 // ------------------------------------------------------------------ ELL
 // Thread per row pair (i and i + stride); chunks of 4 slots give 16 independent
 // coalesced loads before the gathers; padding (col -1) only follows a row's
@@ -112,24 +137,24 @@ __device__ __forceinline__ T ell_rows(int64_t n, int64_t K, int64_t ld,
     const int64_t i1 = i0 + stride;
     const bool has1 = i1 < n;
     T s0 = 0, s1 = 0;
-    for (int64_t k0 = 0; k0 < K; k0 += 4) {
-      int32_t c0[4], c1[4];
-      T w0[4], w1[4];
+    for_slots(K, [&](int64_t k0, auto R) {
+      constexpr int r = decltype(R)::value;
+      int32_t c0[r], c1[r];
+      T w0[r], w1[r];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool in = k0 + u < K;
-        c0[u] = in ? ld_stream(ec + (k0 + u) * ld + i0) : -1;
-        w0[u] = in ? ld_stream(ev + (k0 + u) * ld + i0) : T(0);
-        c1[u] = (in && has1) ? ld_stream(ec + (k0 + u) * ld + i1) : -1;
-        w1[u] = (in && has1) ? ld_stream(ev + (k0 + u) * ld + i1) : T(0);
+      for (int u = 0; u < r; ++u) {
+        c0[u] = ld_stream(ec + (k0 + u) * ld + i0);
+        w0[u] = ld_stream(ev + (k0 + u) * ld + i0);
+        c1[u] = has1 ? ld_stream(ec + (k0 + u) * ld + i1) : -1;
+        w1[u] = has1 ? ld_stream(ev + (k0 + u) * ld + i1) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < r; ++u) {
         if (c0[u] >= 0) s0 = fma(w0[u], ld_x<COH>(x + c0[u]), s0);
         if (c1[u] >= 0) s1 = fma(w1[u], ld_x<COH>(x + c1[u]), s1);
       }
-      if (c0[3] < 0 && c1[3] < 0) break;
-    }
+      return c0[r - 1] < 0 && c1[r - 1] < 0;
+    });
     store_row<T, GEN>(y, i0, s0, alpha, beta);
     if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
     if (has1) {
@@ -157,21 +182,21 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
   T acc = 0;
   for (int64_t c = warp; c < nchunks; c += nwarps) {
     const int64_t base = cptr[c] + lane;
-    const int w = clen[c];
     T sum = 0;
-    for (int k0 = 0; k0 < w; k0 += 4) {
-      int32_t cc[4];
-      T vv[4];
+    for_slots(clen[c], [&](int64_t k0, auto R) {
+      constexpr int r = decltype(R)::value;
+      int32_t cc[r];
+      T vv[r];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool in = k0 + u < w;
-        cc[u] = in ? ld_stream(sc + base + (int64_t)(k0 + u) * 32) : -1;
-        vv[u] = in ? ld_stream(sv + base + (int64_t)(k0 + u) * 32) : T(0);
+      for (int u = 0; u < r; ++u) {
+        cc[u] = ld_stream(sc + base + (k0 + u) * 32);
+        vv[u] = ld_stream(sv + base + (k0 + u) * 32);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < r; ++u)
         if (cc[u] >= 0) sum = fma(vv[u], ld_x<COH>(x + cc[u]), sum);
-    }
+      return false;
+    });
     const int64_t s = c * 32 + lane;
     if (s < n) {
       const int64_t row = perm ? perm[s] : s;
@@ -185,8 +210,8 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
 // ------------------------------------------------------------------ DIA
 // Thread per row pair (i and i + stride, so twice the loads in flight); so[]
 // holds the offsets (in shared memory); values and x are read contiguously
-// across the warp (no index arrays, no gather).  An FMA runs only for a real
-// diagonal (a warp-uniform test), since FP64 FMAs are as scarce as bytes here.
+// across the warp (no index arrays, no gather).  Every diagonal slot is real
+// (exact remainder chunk), since FP64 FMAs are as scarce as bytes here.
 template <typename T, bool GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const int32_t* so,
                                       const T* __restrict__ dv, const T* __restrict__ x,
@@ -197,29 +222,28 @@ __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const
     const int64_t i1 = i0 + stride;
     const bool has1 = i1 < n;
     T s0 = 0, s1 = 0;
-    for (int d0 = 0; d0 < ndiag; d0 += 4) {
-      T w0[4], x0[4], w1[4], x1[4];
+    for_slots(ndiag, [&](int64_t d0, auto R) {
+      constexpr int r = decltype(R)::value;
+      T w0[r], x0[r], w1[r], x1[r];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const bool real = d0 + u < ndiag;
-        const int64_t off = real ? so[d0 + u] : 0;
+      for (int u = 0; u < r; ++u) {
+        const int64_t off = so[d0 + u];
         const int64_t c0 = i0 + off, c1 = i1 + off;
-        const bool in0 = real && c0 >= 0 && c0 < ncols;
-        const bool in1 = real && has1 && c1 >= 0 && c1 < ncols;
-        const int64_t base = (int64_t)(d0 + u) * n;
+        const bool in0 = c0 >= 0 && c0 < ncols;
+        const bool in1 = has1 && c1 >= 0 && c1 < ncols;
+        const int64_t base = (d0 + u) * n;
         w0[u] = in0 ? ld_stream(dv + base + i0) : T(0);
         x0[u] = in0 ? ld_x<COH>(x + c0) : T(0);
         w1[u] = in1 ? ld_stream(dv + base + i1) : T(0);
         x1[u] = in1 ? ld_x<COH>(x + c1) : T(0);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (d0 + u < ndiag) {
-          s0 = fma(w0[u], x0[u], s0);
-          s1 = fma(w1[u], x1[u], s1);
-        }
+      for (int u = 0; u < r; ++u) {
+        s0 = fma(w0[u], x0[u], s0);
+        s1 = fma(w1[u], x1[u], s1);
       }
-    }
+      return false;
+    });
     store_row<T, GEN>(y, i0, s0, alpha, beta);
     if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
     if (has1) {
