@@ -445,6 +445,18 @@ static void launch_csr_vector(cp_ctx* ctx, int tpv, int grid, cudaStream_t s, in
 #undef CP_VEC_CASE
 }
 
+// Grid for a grid-stride loop over `units` one-thread work units in which
+// every thread runs the same number of trips: the resident grid needs
+// trips = ceil(units / (grid_stream * kBlock)) of them, and the grid is shrunk
+// to the fewest blocks that cover the units in that many trips.  (3.5 trips on
+// the full grid would leave half of the threads idle in the last one.)
+static int balanced_grid(cp_ctx* ctx, int64_t units) {
+  const int64_t per = (int64_t)ctx->grid_stream * kBlock;
+  const int64_t trips = units > 0 ? (units + per - 1) / per : 1;
+  const int64_t g = (units + trips * kBlock - 1) / (trips * kBlock);
+  return (int)(g < 1 ? 1 : g > ctx->grid_stream ? ctx->grid_stream : g);
+}
+
 static int grid_for(cp_ctx* ctx, int64_t work_items) {
   const int64_t need = (work_items + kBlock - 1) / kBlock;
   int64_t g = need < ctx->grid_stream ? need : ctx->grid_stream;
@@ -495,7 +507,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
     case CP_FMT_CSR: {
       const T* v = Vals<T>::csr(m);
       if (cfg.algo == CP_ALGO_VECTOR) {
-        const int g = grid_for(ctx, n * cfg.tpv);
+        const int g = balanced_grid(ctx, n * cfg.tpv);
         launch_csr_vector<T, GEN, DOT>(ctx, cfg.tpv, g, s, n, m->rowptr, m->col, v, x, y, alpha,
                                        beta, dotv, partials, skip);
         return DOT ? g : 0;
@@ -510,26 +522,26 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
                   reinterpret_cast<const T*>(m->merge_carry_val), y, GEN ? alpha : T(1), skip);
         break;
       }
-      const int g = grid_for(ctx, n);
+      const int g = balanced_grid(ctx, n);
       CP_LAUNCH(ctx, (k_csr_scalar<T, GEN, DOT>), g, kBlock, 0, s, n, m->rowptr, m->col, v, x, y,
                 alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;
     }
     case CP_FMT_ELL: {
-      const int g = grid_for(ctx, n);
+      const int g = balanced_grid(ctx, (n + 1) / 2);  // a thread per row pair
       CP_LAUNCH(ctx, (k_ell<T, GEN, DOT>), g, kBlock, 0, s, n, m->ell.K, m->ell.ld, m->ell.col,
                 Vals<T>::ell(m->ell), x, y, alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;
     }
     case CP_FMT_SELL: {
-      const int g = grid_for(ctx, m->sell.nchunks * 32);
+      const int g = balanced_grid(ctx, m->sell.nchunks * 32);  // a warp per chunk
       CP_LAUNCH(ctx, (k_sell<T, GEN, DOT>), g, kBlock, 0, s, n, m->sell.nchunks,
                 m->sell.sigma > 1 ? m->sell.perm : nullptr, m->sell.chunk_len, m->sell.chunk_ptr,
                 m->sell.col, Vals<T>::sell(m->sell), x, y, alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;
     }
     case CP_FMT_HYB: {
-      const int g = grid_for(ctx, n);
+      const int g = balanced_grid(ctx, (n + 1) / 2);
       if (m->hyb_coo.n == 0) {  // every row fits the ELL part: the fused ELL kernel suffices
         CP_LAUNCH(ctx, (k_ell<T, GEN, DOT>), g, kBlock, 0, s, n, m->hyb_ell.K, m->hyb_ell.ld,
                   m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, dotv, partials,
@@ -546,7 +558,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
       break;
     }
     case CP_FMT_DIA: {
-      const int g = grid_for(ctx, n);
+      const int g = balanced_grid(ctx, (n + 1) / 2);
       CP_LAUNCH(ctx, (k_dia<T, GEN, DOT>), g, kBlock, 0, s, n, m->ncols, (int)m->dia.ndiag,
                 m->dia.offs, Vals<T>::dia(m->dia), x, y, alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;
