@@ -165,8 +165,8 @@ def cg_iteration_bytes(A, fmt):
 # profiles/k_cg_persist_dia_poisson3d_128.md.
 PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
 PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
-                   "sha256": "4fb4b57d665d2028600fcf32e33e71f8b65bbffbe3a8cc3304b6d951a2136b5c",
-                   "dram_bytes_per_iteration": 160370736.3}
+                   "sha256": "6df0ca3c14935047f0c135fa62eb1ec562c4c145caa9cfe68c8d45d2b65b513e",
+                   "dram_bytes_per_iteration": 158165489.1}
 
 
 def persist_sources_sha256():
