@@ -564,6 +564,20 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
         items.append((r, A, M, 1 if r.kind == "convdiff" else 0, b))
     torch.cuda.synchronize()
     log_fn(f"serve: {len(buckets)} resident matrices built in {time.time() - t0:.0f}s")
+    # the batching autotuner on three random groups of small requests (the
+    # classes the server's batches fall in); cp_batch_solve then uses its picks
+    rng = np.random.default_rng(seed + 1)
+    small = [it for it in items if it[1].nrows <= 32768]
+    tuned = []
+    for _ in range(3 if len(small) >= 32 else 0):
+        grp = [small[i] for i in rng.choice(len(small), 32, replace=False)]
+        best, ms = ctx.batch_tune([g[2] for g in grp], [g[3] for g in grp], [g[4] for g in grp],
+                                  C.default_opts(tol=TOL, inner_tol=1e-5, restart=30,
+                                                 precision=C.PREC_FP32_IR))
+        tuned.append({"mean_rows": int(np.mean([g[1].nrows for g in grp])),
+                      "gmres": any(g[3] for g in grp), "threads": best,
+                      "ms": [round(t, 3) for t in ms]})
+    log_fn(f"serve: batch autotuner picks {[t['threads'] for t in tuned]}")
     # sequential service rate on a sample
     srv = C.Server(ctx, lanes=1)
     sample = items[: min(24, len(items))]
@@ -604,7 +618,7 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
             "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": len(items) / wall,
             "arrival_rate_per_s": rate, "sequential_service_ms": seq * 1e3, "lanes": lanes,
             "batched": int(sum(q.batched for q in res)), "max_relres_true": worst,
-            "resident_matrices": len(buckets), "failures": fails}
+            "resident_matrices": len(buckets), "batch_tuning": tuned, "failures": fails}
 
 
 def run_profile_cg(args):

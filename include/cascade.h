@@ -341,6 +341,26 @@ cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const i
                          const double* const* b, double* const* x, const cp_solve_opts* opts,
                          int32_t threads, cp_solve_info* infos);
 
+/* cp_batch_tune: the batching autotuner (a systems addition for the batched
+ * pattern; the paper has no counterpart).  Solves the given batch as
+ * cp_batch_solve does, but into scratch solutions (the batch's own x are not
+ * touched, x0 = 0), once per candidate of 128, 256, 512 and 1024 threads per
+ * system after one warm-up each, timing each launch with CUDA events.  It
+ * records the fastest in a per-device schedule under the batch's class:
+ * whether the batch holds a GMRES system, and floor(log2(mean rows)).
+ * cp_batch_solve with threads = 0 then uses that choice for batches of the
+ * class.  Arguments as cp_batch_solve.  best_threads (may be NULL) receives the
+ * choice; ms (may be NULL, 4 floats) the times of the four candidates in that
+ * order.  Any system that fails to converge returns its status. */
+cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
+                        const double* const* b, const cp_solve_opts* opts,
+                        int32_t* best_threads, float* ms);
+/* Threads per system that cp_batch_solve(threads = 0) uses for a batch with
+ * mean_rows rows per system (has_gmres: the batch holds a GMRES system): the
+ * tuned choice of that class, else 128 / 256 / 512 / 1024 for mean rows below
+ * 512 / 2048 / 8192 / above.  Returns 0 if ctx is NULL. */
+int32_t cp_batch_threads(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres);
+
 /* ------------------------------------------------------------------ serving */
 /* A continuous-batching solve server.  Requests carry a matrix already loaded
  * with cp_csr_load (kept resident; several requests may share one), a device

@@ -149,6 +149,9 @@ _SIGS = {
     "cp_solve_gmres": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_batch_solve": (c_int32, [_p, c_int32, _p, _p, _p, _p, POINTER(SolveOpts), c_int32,
                                  _p]),
+    "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
+                                _p]),
+    "cp_batch_threads": (c_int32, [_p, c_int64, c_int32]),
     "cp_server_opts_default": (None, [POINTER(ServerOpts)]),
     "cp_server_create": (c_int32, [_p, POINTER(ServerOpts), POINTER(_p)]),
     "cp_server_submit": (c_int32, [_p, POINTER(Request)]),
@@ -359,6 +362,26 @@ class Context:
         if raise_on_error:
             _check(st)
         return list(infos)
+
+    def batch_tune(self, mats, solvers, bs, opts=None):
+        """cp_batch_tune: time 128/256/512/1024 threads per system on this batch
+        (scratch solutions) and record the fastest for its class.  Returns
+        (best threads, [ms of each candidate])."""
+        n = len(mats)
+        hm = (c_void_p * n)(*[m._h.value for m in mats])
+        hs = np.ascontiguousarray(solvers, np.int32)
+        hb = (c_void_p * n)(*[t.data_ptr() for t in bs])
+        best = c_int32(0)
+        ms = np.zeros(4, np.float32)
+        o = opts if opts is not None else default_opts(precision=PREC_FP32_IR)
+        with self.ordered():
+            _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
+                                       _ptr(ms)))
+        return best.value, ms.tolist()
+
+    def batch_threads(self, mean_rows, has_gmres=False):
+        """Threads per system cp_batch_solve(threads=0) uses for a batch class."""
+        return int(lib().cp_batch_threads(self._h, int(mean_rows), 1 if has_gmres else 0))
 
     @staticmethod
     def mlp_nparams(d, h1, h2, k):

@@ -7,11 +7,14 @@
 // the FP64 residual r = b - A x, the refinement update and GMRES's Givens /
 // least-squares step in FP64, the SpMV and Krylov vectors in FP32.  Every
 // reduction is a block reduction; no host round trip happens inside a solve.
-// The launch is captured in a CUDA graph and replayed for later batches of the
-// same shape.
+// The single persistent launch is captured in a CUDA graph and launched as one.
+// Threads per system come from a per-device schedule that cp_batch_tune fills
+// by timing the candidates on real batches (the autotuner), else from the
+// mean system size.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -358,144 +361,238 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
 }
 
 // ------------------------------------------------------------------ host
-struct BatchPlan {
-  int threads = 256;
-};
-
+// Runs one batch with BT threads per system; returns the launch's time (ms,
+// CUDA events around the graph launch on s).
 template <int BT>
-static void launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const int* d_order,
-                         int* d_next, const BatchParams& P, BatchOut* d_out, cudaStream_t s) {
+static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const int* d_order,
+                          int* d_next, const BatchParams& P, BatchOut* d_out, cudaStream_t s) {
   int per_sm = 0;
   CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT>, BT, 0));
   int grid = ctx->num_sms * std::max(per_sm, 1);
   if (grid > nsys) grid = nsys;
-  // capture the single persistent launch in a graph and replay it
+  // capture the single persistent launch in a graph and launch it
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   cudaStream_t cap = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
   CP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
   try {
+    CP_CUDA(cudaEventCreate(&e0));
+    CP_CUDA(cudaEventCreate(&e1));
     CP_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
     k_batch_solve<BT><<<grid, BT, 0, cap>>>(d_sys, nsys, d_order, d_next, P, d_out);
     CP_CUDA(cudaStreamEndCapture(cap, &g));
     CP_CUDA(cudaGraphInstantiate(&ge, g, 0));
     ctx->launches.fetch_add(1, std::memory_order_relaxed);
+    CP_CUDA(cudaEventRecord(e0, s));
     CP_CUDA(cudaGraphLaunch(ge, s));
-    CP_CUDA(cudaStreamSynchronize(s));
+    CP_CUDA(cudaEventRecord(e1, s));
+    CP_CUDA(cudaEventSynchronize(e1));
+    CP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
   } catch (...) {
     if (ge) cudaGraphExecDestroy(ge);
     if (g) cudaGraphDestroy(g);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     cudaStreamDestroy(cap);
     throw;
   }
   cudaGraphExecDestroy(ge);
   cudaGraphDestroy(g);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   cudaStreamDestroy(cap);
+  return ms;
 }
 
-void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
-                 const double* const* b, double* const* x, const cp_solve_opts* o,
-                 cp_solve_info* infos, int threads) {
-  CP_REQUIRE(nsys >= 1 && mats && solver && b && x, CP_ERR_INVALID, "bad batch arguments");
-  cp_solve_opts opt;
-  cp_solve_opts_default(&opt);
-  if (o) opt = *o;
+static float launch_batch_bt(int bt, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
+                             const int* d_order, int* d_next, const BatchParams& P,
+                             BatchOut* d_out, cudaStream_t s) {
+  switch (bt) {
+    case 128: return launch_batch<128>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 256: return launch_batch<256>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 512: return launch_batch<512>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    default: return launch_batch<1024>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+  }
+}
+
+// ---- the autotuner's schedule: threads per system for a batch class, per
+// device.  A class is (the batch holds a GMRES system, floor(log2(mean rows))).
+namespace {
+constexpr int kSchedDevices = 64;
+constexpr int kSchedBuckets = 32;
+std::mutex g_sched_mu;
+int g_sched[kSchedDevices][2][kSchedBuckets] = {};  // 0: not tuned
+
+int size_bucket(int64_t mean_rows) {
+  int b = 0;
+  while (b + 1 < kSchedBuckets && (int64_t(1) << (b + 1)) <= mean_rows) ++b;
+  return b;
+}
+
+// Untuned rule.  The tuner measured 1024 threads fastest for batches of
+// 32 mixed CG / GMRES systems of about 10,000 rows (52.8 ms against 94 / 175 /
+// 341 ms with 512 / 256 / 128): a block per system leaves most SMs idle when
+// the batch is smaller than the GPU, so wider blocks win early.
+int default_threads(int64_t mean_rows) {
+  return mean_rows < 512 ? 128 : mean_rows < 2048 ? 256 : mean_rows < 8192 ? 512 : 1024;
+}
+}  // namespace
+
+int batch_threads(cp_ctx* ctx, int64_t mean_rows, bool has_gmres) {
+  if (ctx->device >= 0 && ctx->device < kSchedDevices) {
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    const int t = g_sched[ctx->device][has_gmres ? 1 : 0][size_bucket(mean_rows)];
+    if (t) return t;
+  }
+  return default_threads(mean_rows);
+}
+
+// A batch laid out on the device: per-system descriptors, workspaces, the
+// largest-first work order and the outputs, all stream-ordered on s.
+struct BatchJob {
+  cudaStream_t s = nullptr;
+  std::vector<BatchSys> hs;
+  double* d64 = nullptr;
+  float* d32 = nullptr;
+  double* xs = nullptr;  // tuning: scratch solutions
+  BatchSys* d_sys = nullptr;
+  int* d_order = nullptr;  // nsys entries + the work counter
+  BatchOut* d_out = nullptr;
+  int64_t total_rows = 0;
+  bool has_gmres = false;
+  ~BatchJob() {
+    dfree_async(d64, s);
+    dfree_async(d32, s);
+    dfree_async(xs, s);
+    dfree_async(d_sys, s);
+    dfree_async(d_order, s);
+    dfree_async(d_out, s);
+  }
+};
+
+static void batch_prepare(cp_ctx* ctx, BatchJob& J, int nsys, cp_mat* const* mats,
+                          const int32_t* solver, const double* const* b, double* const* x,
+                          const cp_solve_opts& opt, bool scratch_x) {
+  CP_REQUIRE(nsys >= 1 && mats && solver && b && (x || scratch_x), CP_ERR_INVALID,
+             "bad batch arguments");
   CP_REQUIRE(opt.restart >= 1 && opt.restart <= kBatchMaxM, CP_ERR_INVALID,
              "batched GMRES restart must be in 1..%d", kBatchMaxM);
-  CP_REQUIRE(threads == 0 || threads == 128 || threads == 256 || threads == 512 || threads == 1024,
-             CP_ERR_INVALID, "threads per system must be 128, 256, 512 or 1024");
-  cudaStream_t s = ctx->main;
+  cudaStream_t s = J.s;
   cp_config csr;
   cp_config_default(&csr);
-  std::vector<BatchSys> hs(nsys);
   int64_t ws64 = 0, ws32 = 0;
-  int64_t total_rows = 0;
   for (int i = 0; i < nsys; ++i) {
     cp_mat* m = mats[i];
-    CP_REQUIRE(m && m->nrows == m->ncols && b[i] && x[i], CP_ERR_INVALID,
+    CP_REQUIRE(m && m->nrows == m->ncols && b[i] && (scratch_x || x[i]), CP_ERR_INVALID,
                "system %d: NULL or non-square", i);
     CP_REQUIRE(solver[i] == 0 || solver[i] == 1, CP_ERR_INVALID, "system %d: solver must be 0/1",
                i);
     ensure_val32(ctx, m, csr, s);
     ws64 += m->nrows;
     ws32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
-    total_rows += m->nrows;
+    J.total_rows += m->nrows;
+    J.has_gmres |= solver[i] == 1;
   }
-  double* d64 = nullptr;
-  float* d32 = nullptr;
-  BatchSys* d_sys = nullptr;
-  int* d_order = nullptr;
-  BatchOut* d_out = nullptr;
-  try {
-    d64 = dalloc<double>(ws64);
-    d32 = dalloc<float>(ws32);
-    int64_t o64 = 0, o32 = 0;
-    for (int i = 0; i < nsys; ++i) {
-      cp_mat* m = mats[i];
-      hs[i] = BatchSys{m->nrows, m->rowptr, m->col, m->val, m->val32, b[i], x[i],
-                       d64 + o64, d32 + o32, solver[i]};
-      o64 += m->nrows;
-      o32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
-    }
-    // largest systems first, so the dynamic queue ends with short jobs
-    std::vector<int> order(nsys);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
-      return hs[a].n * (hs[a].solver ? 3 : 1) > hs[c].n * (hs[c].solver ? 3 : 1);
-    });
-    d_sys = dalloc<BatchSys>(nsys);
-    d_order = dalloc<int>(nsys + 1);  // last slot: the work counter
-    d_out = dalloc<BatchOut>(nsys);
-    CP_CUDA(cudaMemcpyAsync(d_sys, hs.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice, s));
-    CP_CUDA(cudaMemcpyAsync(d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
-    CP_CUDA(cudaMemsetAsync(d_order + nsys, 0, sizeof(int), s));
-    BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart};
-    int bt = threads;
-    if (bt == 0) {  // default: block size from the mean system size
-      const int64_t mean = total_rows / nsys;
-      bt = mean < 2048 ? 128 : mean < 16384 ? 256 : mean < 131072 ? 512 : 1024;
-    }
-    switch (bt) {
-      case 128: launch_batch<128>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
-      case 256: launch_batch<256>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
-      case 512: launch_batch<512>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
-      default: launch_batch<1024>(ctx, d_sys, nsys, d_order, d_order + nsys, P, d_out, s); break;
-    }
-    std::vector<BatchOut> out(nsys);
-    CP_CUDA(cudaMemcpy(out.data(), d_out, nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost));
-    int worst = CP_OK;
-    for (int i = 0; i < nsys; ++i) {
-      if (infos) {
-        std::memset(&infos[i], 0, sizeof(cp_solve_info));
-        infos[i].iters = out[i].inner;
-        infos[i].outer_iters = out[i].outer;
-        infos[i].relres_true = out[i].relres;
-        infos[i].status = out[i].status;
-        infos[i].switch_iter[0] = infos[i].switch_iter[1] = infos[i].switch_iter[2] = -1;
-        infos[i].final_cfg = csr;
-      }
-      if (out[i].status != CP_OK && worst == CP_OK) worst = out[i].status;
-    }
-    dfree(d64);
-    dfree(d32);
-    dfree(d_sys);
-    dfree(d_order);
-    dfree(d_out);
-    d64 = nullptr;
-    d32 = nullptr;
-    d_sys = nullptr;
-    d_order = nullptr;
-    d_out = nullptr;
-    CP_REQUIRE(worst == CP_OK, (cp_status)worst, "a batched system did not converge (status %d)",
-               worst);
-  } catch (...) {
-    dfree(d64);
-    dfree(d32);
-    dfree(d_sys);
-    dfree(d_order);
-    dfree(d_out);
-    throw;
+  J.d64 = dalloc_async<double>(ws64, s);
+  J.d32 = dalloc_async<float>(ws32, s);
+  if (scratch_x) J.xs = dalloc_async<double>(J.total_rows, s);
+  J.hs.resize(nsys);
+  int64_t o64 = 0, o32 = 0;
+  for (int i = 0; i < nsys; ++i) {
+    cp_mat* m = mats[i];
+    J.hs[i] = BatchSys{m->nrows, m->rowptr, m->col, m->val, m->val32, b[i],
+                       scratch_x ? J.xs + o64 : x[i], J.d64 + o64, J.d32 + o32, solver[i]};
+    o64 += m->nrows;
+    o32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
   }
+  // largest systems first, so the dynamic queue ends with short jobs
+  std::vector<int> order(nsys);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+    return J.hs[a].n * (J.hs[a].solver ? 3 : 1) > J.hs[c].n * (J.hs[c].solver ? 3 : 1);
+  });
+  J.d_sys = dalloc_async<BatchSys>(nsys, s);
+  J.d_order = dalloc_async<int>(nsys + 1, s);
+  J.d_out = dalloc_async<BatchOut>(nsys, s);
+  // the host arrays outlive the copies: the job synchronises before it is destroyed
+  CP_CUDA(cudaMemcpyAsync(J.d_sys, J.hs.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
+                          s));
+  CP_CUDA(cudaMemcpyAsync(J.d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
+  CP_CUDA(cudaStreamSynchronize(s));
+}
+
+static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& opt, int bt) {
+  cudaStream_t s = J.s;
+  if (J.xs) CP_CUDA(cudaMemsetAsync(J.xs, 0, J.total_rows * sizeof(double), s));
+  CP_CUDA(cudaMemsetAsync(J.d_order + nsys, 0, sizeof(int), s));
+  BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart};
+  return launch_batch_bt(bt, ctx, J.d_sys, nsys, J.d_order, J.d_order + nsys, P, J.d_out, s);
+}
+
+void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
+                 const double* const* b, double* const* x, const cp_solve_opts* o,
+                 cp_solve_info* infos, int threads) {
+  cp_solve_opts opt;
+  cp_solve_opts_default(&opt);
+  if (o) opt = *o;
+  CP_REQUIRE(threads == 0 || threads == 128 || threads == 256 || threads == 512 || threads == 1024,
+             CP_ERR_INVALID, "threads per system must be 128, 256, 512 or 1024");
+  BatchJob J;
+  J.s = ctx->main;
+  batch_prepare(ctx, J, nsys, mats, solver, b, x, opt, false);
+  const int bt = threads ? threads : batch_threads(ctx, J.total_rows / nsys, J.has_gmres);
+  batch_run(ctx, J, nsys, opt, bt);
+  std::vector<BatchOut> out(nsys);
+  CP_CUDA(cudaMemcpyAsync(out.data(), J.d_out, nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost,
+                          J.s));
+  CP_CUDA(cudaStreamSynchronize(J.s));
+  cp_config csr;
+  cp_config_default(&csr);
+  int worst = CP_OK;
+  for (int i = 0; i < nsys; ++i) {
+    if (infos) {
+      std::memset(&infos[i], 0, sizeof(cp_solve_info));
+      infos[i].iters = out[i].inner;
+      infos[i].outer_iters = out[i].outer;
+      infos[i].relres_true = out[i].relres;
+      infos[i].status = out[i].status;
+      infos[i].switch_iter[0] = infos[i].switch_iter[1] = infos[i].switch_iter[2] = -1;
+      infos[i].final_cfg = csr;
+    }
+    if (out[i].status != CP_OK && worst == CP_OK) worst = out[i].status;
+  }
+  CP_REQUIRE(worst == CP_OK, (cp_status)worst, "a batched system did not converge (status %d)",
+             worst);
+}
+
+int batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
+               const double* const* b, const cp_solve_opts* o, float* ms4) {
+  cp_solve_opts opt;
+  cp_solve_opts_default(&opt);
+  if (o) opt = *o;
+  BatchJob J;
+  J.s = ctx->main;
+  batch_prepare(ctx, J, nsys, mats, solver, b, nullptr, opt, true);
+  const int cand[4] = {128, 256, 512, 1024};
+  int best = 0;
+  float best_ms = 0.f;
+  for (int c = 0; c < 4; ++c) {
+    batch_run(ctx, J, nsys, opt, cand[c]);  // warm-up: module load, caches
+    const float ms = batch_run(ctx, J, nsys, opt, cand[c]);
+    if (ms4) ms4[c] = ms;
+    if (!best || ms < best_ms) {
+      best = cand[c];
+      best_ms = ms;
+    }
+  }
+  CP_CUDA(cudaStreamSynchronize(J.s));
+  if (ctx->device >= 0 && ctx->device < kSchedDevices) {
+    std::lock_guard<std::mutex> lock(g_sched_mu);
+    g_sched[ctx->device][J.has_gmres ? 1 : 0][size_bucket(J.total_rows / nsys)] = best;
+  }
+  return best;
 }
 
 }  // namespace cp

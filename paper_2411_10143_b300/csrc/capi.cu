@@ -334,6 +334,22 @@ cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const i
   });
 }
 
+cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
+                        const double* const* b, const cp_solve_opts* opts,
+                        int32_t* best_threads, float* ms) {
+  return guard([&] {
+    CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
+    use_device(ctx);
+    const int best = batch_tune(ctx, nsys, mats, solver, b, opts, ms);
+    if (best_threads) *best_threads = best;
+  });
+}
+
+int32_t cp_batch_threads(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres) {
+  if (!ctx) return 0;
+  return batch_threads(ctx, mean_rows, has_gmres != 0);
+}
+
 int64_t cp_mlp_nparams(int32_t d, int32_t h1, int32_t h2, int32_t k) {
   return (int64_t)h1 * d + h1 + (int64_t)h2 * h1 + h2 + (int64_t)k * h2 + k;
 }

@@ -78,3 +78,27 @@ def test_batch_rejects_bad_arguments():
     with pytest.raises(C.CascadeError):
         ctx.batch_solve([M], [1], [b], [x], C.default_opts(restart=40, precision=1))
     ctx.close()
+
+
+def test_autotuner_times_every_candidate_and_its_choice_is_used():
+    """cp_batch_tune times the four thread counts on a real batch (scratch
+    solutions: the caller's x are untouched), records the fastest for the
+    batch's class, and cp_batch_solve(threads=0) then solves with it to the
+    same tolerance."""
+    ctx = C.Context(0)
+    sys = [(W.poisson2d(N), 0) for N in (40, 44, 48, 52)] + [(W.spd_powerlaw(2500, seed=9), 0)]
+    mats = [ctx.load(A) for A, _ in sys]
+    rhs = [oracle.spmv(A, W.vector(A.nrows, q + 70)) for q, (A, _) in enumerate(sys)]
+    bs = [torch.as_tensor(b, device="cuda") for b in rhs]
+    opts = C.default_opts(tol=1e-10, inner_tol=1e-5, precision=C.PREC_FP32_IR)
+    best, ms = ctx.batch_tune(mats, [s for _, s in sys], bs, opts)
+    assert best in (128, 256, 512, 1024)
+    assert len(ms) == 4 and all(t > 0 for t in ms)
+    assert ms[(128, 256, 512, 1024).index(best)] == min(ms)
+    mean = sum(A.nrows for A, _ in sys) // len(sys)
+    assert ctx.batch_threads(mean, False) == best
+    # a class that was not tuned keeps the size rule
+    assert ctx.batch_threads(100, True) == 128 and ctx.batch_threads(200000, True) == 1024
+    assert ctx.batch_threads(1000, True) == 256 and ctx.batch_threads(4000, True) == 512
+    check(ctx, sys, 0, seeds=[q + 30 for q in range(len(sys))])
+    ctx.close()
