@@ -334,7 +334,8 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
  * least-squares step.  mats[i] (square, CSR; the kernel is the CSR scalar one),
  * b[i], x[i] (device FP64, x read as x0) are host arrays of nsys entries;
  * opts->maxit bounds the inner steps of each system; threads per block: 128,
- * 256, 512, 1024 or 0 (chosen from the mean system size).  infos (host array of
+ * 256, 512, 1024 or 0 (the autotuner's choice for the batch's class, see
+ * cp_batch_tune, else a rule on the mean system size).  infos (host array of
  * nsys, may be NULL) receives per-system iterations, relres_true, status.
  * Returns the first non-OK system status, else CP_OK. */
 cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
