@@ -307,9 +307,49 @@ typedef struct {
   int32_t persist_iters;   /* iterations those launches ran                               */
   float t_persist_last_ms; /* duration of the last persistent launch (final configuration) */
   int32_t persist_last_iters; /* iterations it ran                                        */
+  int32_t gate_declined;   /* the cost-aware gate kept the default format (cp_gate)       */
+  float gate_remaining;    /* its estimate of the iterations left when it decided (-1: none) */
+  float gate_cost_spmvs;   /* its estimate of the conversion cost, in default-kernel SpMVs */
 } cp_solve_info;
 
 void cp_solve_opts_default(cp_solve_opts* opts);
+
+/* ------------------------------------------------------------------ cost-aware switching
+ * An extension of Sec. III-C-2's switch.  The paper converts whenever a
+ * prediction lands.  Sec. II-B quotes conversion costs of 9 to 270 CSR SpMVs; in
+ * Sec. IV-B the conversion outweighs the gain on a small matrix; Sec. V-C
+ * describes selecting a format only when the iteration count, estimated from
+ * the first iterations' residuals, is large enough.  Here, before converting to
+ * the predicted format f, the side thread asks whether the
+ * expected saving over the rest of the solve exceeds the conversion cost, in
+ * units of one SpMV of the default kernel:
+ *     remaining x (1 - 1/speedup[f])  >  cost_f(nnz)
+ * remaining: iterations left, extrapolated from the residual decay the solve
+ * has shown so far (geometric rate over the iterations done; a verdict to keep
+ * the default is confirmed on the rate of the next 8 iterations, since Krylov
+ * residuals often fall fast at first);
+ * speedup[f]: typical SpMV speedup of format f over the default kernel where
+ * the classifier picks f; cost_f(nnz) = (conv_a_ms[f] + conv_b_ms[f] nnz/1e6) /
+ * (spmv_a_ms + spmv_b_ms nnz/1e6), linear fits of conversion and default-SpMV
+ * times.  All figures are measured on this GPU when the cascade is trained.
+ * Indices of the arrays: CP_FMT_*. */
+typedef struct {
+  double speedup[6];
+  double conv_a_ms[6], conv_b_ms[6];  /* conversion time = a + b * nnz / 1e6 (ms)       */
+  double spmv_a_ms, spmv_b_ms;        /* default-kernel SpMV time = a + b * nnz / 1e6    */
+  int32_t enabled;                    /* 0: always switch (the paper's behaviour)        */
+} cp_gate;
+
+/* Install (or, with enabled = 0, disable) the gate for solves in ctx. */
+cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate);
+/* The gate's rule, on the host: 1 to convert and switch to format fmt, 0 to
+ * keep the default.  iters, res0, res: iterations done, the initial and the
+ * latest residual norms; target: the residual norm that ends the solve
+ * (tol * ||b||).  Too little history (iters < 2) or no decay yet counts as a
+ * long solve (switch).  remaining and cost_spmvs (may be NULL) receive the
+ * estimates (-1: unknown). */
+int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t iters, double res0,
+                       double res, double target, double* remaining, double* cost_spmvs);
 
 /* cp_solve_cg: CG (Sec. I) for SPD A.  b, x: device FP64 arrays of nrows
  * entries; x is read as x0 and overwritten with the solution.  info (host) may

@@ -83,7 +83,8 @@ class SolveInfo(Structure):
                 ("t_predict_ms", c_float * 3), ("t_convert_ms", c_float),
                 ("t_total_ms", c_float), ("t_spmv_ms", c_float), ("t_persist_ms", c_float),
                 ("persist_iters", c_int32), ("t_persist_last_ms", c_float),
-                ("persist_last_iters", c_int32)]
+                ("persist_last_iters", c_int32), ("gate_declined", c_int32),
+                ("gate_remaining", c_float), ("gate_cost_spmvs", c_float)]
 
     def as_dict(self):
         return dict(iters=self.iters, outer_iters=self.outer_iters,
@@ -94,7 +95,36 @@ class SolveInfo(Structure):
                     t_convert_ms=self.t_convert_ms, t_total_ms=self.t_total_ms,
                     t_spmv_ms=self.t_spmv_ms, t_persist_ms=self.t_persist_ms,
                     persist_iters=self.persist_iters, t_persist_last_ms=self.t_persist_last_ms,
-                    persist_last_iters=self.persist_last_iters)
+                    persist_last_iters=self.persist_last_iters,
+                    gate_declined=self.gate_declined, gate_remaining=self.gate_remaining,
+                    gate_cost_spmvs=self.gate_cost_spmvs)
+
+
+class Gate(Structure):
+    """cp_gate: the cost-aware switching figures (arrays indexed by FORMATS)."""
+    _fields_ = [("speedup", c_double * 6), ("conv_a_ms", c_double * 6),
+                ("conv_b_ms", c_double * 6), ("spmv_a_ms", c_double), ("spmv_b_ms", c_double),
+                ("enabled", c_int32)]
+
+    @classmethod
+    def from_dict(cls, d, enabled=True):
+        g = cls()
+        for i in range(6):
+            g.speedup[i] = float(d["speedup"][i])
+            g.conv_a_ms[i] = float(d["conv_a_ms"][i])
+            g.conv_b_ms[i] = float(d["conv_b_ms"][i])
+        g.spmv_a_ms = float(d["spmv_a_ms"])
+        g.spmv_b_ms = float(d["spmv_b_ms"])
+        g.enabled = 1 if enabled else 0
+        return g
+
+
+def gate_decide(gate: Gate, fmt, nnz, iters, res0, res, target):
+    """cp_gate_decide (host only): (switch?, remaining iterations, cost in SpMVs)."""
+    rem, cost = c_double(0.0), c_double(0.0)
+    go = lib().cp_gate_decide(byref(gate), int(fmt), int(nnz), int(iters), float(res0),
+                              float(res), float(target), byref(rem), byref(cost))
+    return bool(go), rem.value, cost.value
 
 
 class ServerOpts(Structure):
@@ -149,6 +179,9 @@ _SIGS = {
     "cp_solve_gmres": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_batch_solve": (c_int32, [_p, c_int32, _p, _p, _p, _p, POINTER(SolveOpts), c_int32,
                                  _p]),
+    "cp_gate_set": (c_int32, [_p, _p]),
+    "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
+                                 POINTER(c_double), POINTER(c_double)]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
                                 _p]),
     "cp_batch_threads": (c_int32, [_p, c_int64, c_int32]),
@@ -378,6 +411,10 @@ class Context:
             _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
                                        _ptr(ms)))
         return best.value, ms.tolist()
+
+    def gate_set(self, gate: "Gate"):
+        """cp_gate_set: install (gate.enabled = 1) or disable the cost-aware switch."""
+        _check(lib().cp_gate_set(self._h, byref(gate)))
 
     def batch_threads(self, mean_rows, has_gmres=False):
         """Threads per system cp_batch_solve(threads=0) uses for a batch class."""

@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -332,6 +333,26 @@ cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const i
     use_device(ctx);
     batch_solve(ctx, nsys, mats, solver, b, x, opts, infos, threads);
   });
+}
+
+cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate) {
+  return guard([&] {
+    CP_REQUIRE(ctx && gate, CP_ERR_INVALID, "NULL argument");
+    for (int f = 0; f < CP_NUM_FMT; ++f)
+      CP_REQUIRE(std::isfinite(gate->speedup[f]) && std::isfinite(gate->conv_a_ms[f]) &&
+                     std::isfinite(gate->conv_b_ms[f]),
+                 CP_ERR_INVALID, "gate figures must be finite");
+    CP_REQUIRE(gate->spmv_a_ms >= 0.0 && gate->spmv_b_ms >= 0.0 &&
+                   gate->spmv_a_ms + gate->spmv_b_ms > 0.0,
+               CP_ERR_INVALID, "the default SpMV time fit must be positive");
+    ctx->gate = *gate;
+  });
+}
+
+int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t iters, double res0,
+                       double res, double target, double* remaining, double* cost_spmvs) {
+  if (!gate) return 1;
+  return gate_decide(*gate, fmt, nnz, iters, res0, res, target, remaining, cost_spmvs);
 }
 
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,

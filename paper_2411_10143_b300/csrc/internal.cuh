@@ -138,6 +138,7 @@ struct cp_ctx {
   // would stall the side stream's prediction behind a running solve
   void* pin_main = nullptr;
   void* pin_side = nullptr;
+  cp_gate gate{};  // cost-aware switching (disabled until installed)
 };
 
 struct cp_mat {
@@ -229,6 +230,14 @@ struct Channel {
   float t_features_ms = 0.f, t_predict_ms[3] = {0.f, 0.f, 0.f}, t_convert_ms = 0.f;
   cp_status status = CP_OK;  // first error of the side thread, if any
   std::string error;
+  // the solve's progress for the cost-aware gate (FP64 solves): iterations
+  // done, the latest and the initial residual norm, ||b||; iters < 0: none yet
+  std::atomic<int> prog_iters{-1};
+  std::atomic<double> prog_res{0.0}, prog_res0{0.0}, prog_bnorm{0.0};
+  std::atomic<bool> solve_done{false};
+  double tol = 0.0;
+  bool gate_declined = false;
+  float gate_remaining = -1.f, gate_cost = -1.f;
 
   void publish(int stage, const cp_config& c) {
     std::lock_guard<std::mutex> lock(mu);
@@ -241,6 +250,9 @@ struct Channel {
 // stream s; publishes into ch after every stage that changes the
 // configuration.  Runs until done or ch->cancel is set.
 void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch);
+// the cost-aware gate's rule (see cp_gate_decide)
+int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, double res,
+                double target, double* remaining, double* cost);
 // One cascade stage's classifier on the features: returns the arg-max class,
 // or -1 when the stage has no model.
 int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s);

@@ -75,6 +75,8 @@ __global__ void k_cg_init_final(const double* __restrict__ pr, const double* __r
     st->done = done;
     st->status = CP_OK;
     mir->res = sqrt(rr);
+    mir->res0 = sqrt(rr);
+    mir->bnorm = sqrt(bb);
     mir->done = done;
     mir->status = CP_OK;
     mir->iters = st->iters;
@@ -432,6 +434,10 @@ __global__ void k_gm_start(const double* __restrict__ part, int P, GmState* st, 
   st->done = (conv || !isfinite(rr)) ? 1 : 0;
   st->halt = st->done;
   mir->res = beta;
+  if (first) {
+    mir->res0 = beta;
+    mir->bnorm = sqrt(st->bb);
+  }
   mir->done = st->done;
   mir->halt = st->halt;
   mir->jdone = 0;
@@ -617,6 +623,14 @@ struct ConfigSource {
   float t_persist_last_ms = 0.f;
   int persist_last_iters = 0;
 
+  // the solve's progress, for the side thread's cost-aware gate
+  void progress(const Mirror* mir) {
+    if (!ch) return;
+    ch->prog_res0.store(mir->res0, std::memory_order_relaxed);
+    ch->prog_bnorm.store(mir->bnorm, std::memory_order_relaxed);
+    ch->prog_res.store(mir->res, std::memory_order_relaxed);
+    ch->prog_iters.store(mir->iters, std::memory_order_release);
+  }
   void poll(int iter) {
     if (!ch) return;
     const int c = ch->count.load(std::memory_order_acquire);
@@ -783,6 +797,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       ++it;
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
+        cs.progress(ws.mir);
         if (ws.mir->done) break;
       }
       // the loop head hands the remaining iterations to the persistent kernel
@@ -894,6 +909,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       ++issued;
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));
+        cs.progress(ws.mir);
         if (ws.mir->halt) break;
       }
     }
@@ -1018,6 +1034,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
 
   Channel ch;
   ch.need_fp32 = fp32;
+  ch.tol = fp32 ? 0.0 : opt.tol;  // the gate follows FP64 solves' residuals
   std::thread side;
   const bool predict = !opt.force && opt.mode != CP_MODE_PLAIN;
   trace("solve: start n=%lld mode=%d precision=%d", (long long)m->nrows, opt.mode, opt.precision);
@@ -1031,6 +1048,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     }
   }
   auto stop_side = [&]() {
+    ch.solve_done.store(true);
     ch.cancel.store(true);
     if (side.joinable()) side.join();
   };
@@ -1073,6 +1091,9 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     info->persist_iters = cs.persist_iters;
     info->t_persist_last_ms = cs.t_persist_last_ms;
     info->persist_last_iters = cs.persist_last_iters;
+    info->gate_declined = ch.gate_declined ? 1 : 0;
+    info->gate_remaining = ch.gate_remaining;
+    info->gate_cost_spmvs = ch.gate_cost;
     info->n_launches = (int32_t)(ctx->launches.load() - launches0);
     info->status = res.status;
   }

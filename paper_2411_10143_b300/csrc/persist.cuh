@@ -25,7 +25,9 @@ constexpr int kPersistBlock = 1024;  // one block per SM: 148 barrier arrivals, 
 
 // Host-mapped mirror written by the kernels that finish an iteration.
 struct Mirror {
-  volatile double res;  // latest residual norm (recursive / estimated / true)
+  volatile double res;    // latest residual norm (recursive / estimated / true)
+  volatile double res0;   // residual norm at the (re)start
+  volatile double bnorm;  // ||b||
   volatile int done, halt, status, iters, jdone, conv_est;
 };
 

@@ -8,6 +8,7 @@
 // forward / backward / Adam kernels below.
 #include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstring>
 #include <vector>
 
@@ -420,6 +421,51 @@ static int tpv_heuristic(const double* f) {
   return t;
 }
 
+int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, double res,
+                double target, double* remaining, double* cost) {
+  double rem = -1.0, kappa = -1.0;
+  int go = 1;
+  if (g.enabled && fmt > 0 && fmt < CP_NUM_FMT) {
+    const double mnnz = (double)nnz * 1e-6;
+    const double t_spmv = g.spmv_a_ms + g.spmv_b_ms * mnnz;
+    const double t_conv = g.conv_a_ms[fmt] + g.conv_b_ms[fmt] * mnnz;
+    kappa = t_spmv > 0.0 ? t_conv / t_spmv : 1e300;
+    const double s = g.speedup[fmt];
+    if (!(s > 1.0)) {
+      go = 0;  // no gain expected from the format
+    } else if (iters >= 2 && res0 > 0.0 && res > 0.0 && target > 0.0) {
+      if (res <= target) {
+        rem = 0.0;
+        go = 0;
+      } else {
+        const double rate = std::log(res / res0) / iters;  // < 0 while the residual decays
+        if (rate < 0.0) {
+          rem = std::log(target / res) / rate;
+          go = rem * (1.0 - 1.0 / s) > kappa ? 1 : 0;
+        }  // no decay yet: a long solve ahead, switch
+      }
+    }
+  }
+  if (remaining) *remaining = rem;
+  if (cost) *cost = kappa;
+  return go;
+}
+
+constexpr int kGateWindow = 8;  // iterations over which a "keep" verdict is confirmed
+
+// Waits (bounded) until the solve has reported at least `iters` iterations,
+// finished, or the side work was cancelled.
+static void wait_progress(Channel* ch, int iters, double max_ms) {
+  const auto t0 = std::chrono::steady_clock::now();
+  while (ch->prog_iters.load(std::memory_order_acquire) < iters &&
+         !ch->solve_done.load(std::memory_order_acquire) && !ch->cancel.load()) {
+    if (std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() >
+        max_ms)
+      return;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
 void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
   struct Finish {  // tell the solve loop the side work has ended, however it ends
     Channel* c;
@@ -454,6 +500,40 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
     ch->t_predict_ms[0] = ms(t);
     trace("cascade: FORMAT -> %d", next.fmt);
     if (ch->cancel.load()) return;
+    if (next.fmt != cfg.fmt && ctx->gate.enabled && ch->tol > 0.0) {
+      // cost-aware switching: convert only if the saving over the iterations
+      // left pays for the conversion.  A solve that has not reported two
+      // iterations by now (a large matrix) counts as long: no waiting here.
+      double rem = -1.0, cost = -1.0;
+      const double target = ch->tol * ch->prog_bnorm.load();
+      int go = gate_decide(ctx->gate, next.fmt, m->nnz, ch->prog_iters.load(),
+                           ch->prog_res0.load(), ch->prog_res.load(), target, &rem, &cost);
+      ch->gate_remaining = (float)rem;
+      ch->gate_cost = (float)cost;
+      trace("cascade: gate for format %d: %d iterations left, conversion %.1f SpMVs -> %s",
+            next.fmt, (int)rem, cost, go ? "switch" : "keep (to be confirmed)");
+      if (!go) {
+        // Krylov residuals often drop fast in the first iterations, so a "keep"
+        // is confirmed on the decay over the next kGateWindow iterations; the
+        // solve stays on the default kernel meanwhile
+        ch->gate_declined = true;
+        const int k1 = ch->prog_iters.load(std::memory_order_acquire);
+        const double r1 = ch->prog_res.load();
+        wait_progress(ch, k1 + kGateWindow, 50.0);
+        if (ch->cancel.load()) return;
+        const int k2 = ch->prog_iters.load(std::memory_order_acquire);
+        if (k2 > k1) {
+          go = gate_decide(ctx->gate, next.fmt, m->nnz, k2 - k1, r1, ch->prog_res.load(), target,
+                           &rem, &cost);
+          ch->gate_remaining = (float)rem;
+          ch->gate_cost = (float)cost;
+          trace("cascade: gate window %d..%d: %d iterations left -> %s", k1, k2, (int)rem,
+                go ? "switch" : "keep");
+        }
+        if (!go) return;
+        ch->gate_declined = false;
+      }
+    }
     if (next.fmt != cfg.fmt) {
       t = Clock::now();
       try {

@@ -34,7 +34,11 @@ def load(path: Path = WEIGHTS) -> dict:
     if not path.exists():
         return {}
     data = json.loads(path.read_text())
-    return data.get("stages", {})
+    out = dict(data.get("stages", {}))
+    gate = data.get("meta", {}).get("gate")
+    if gate:
+        out["_gate"] = gate
+    return out
 
 
 def install(ctx, models: dict) -> list:
@@ -55,6 +59,9 @@ def install(ctx, models: dict) -> list:
         ctx.model_load(i, h1, h2, k, np.asarray(m["params"], np.float32),
                        np.asarray(m["mu"], np.float32), np.asarray(m["sd"], np.float32))
         done.append(name)
+    if models.get("_gate"):  # the cost-aware switch's figures, measured with the labels
+        ctx.gate_set(C.Gate.from_dict(models["_gate"]))
+        done.append("GATE")
     return done
 
 

@@ -43,27 +43,57 @@ def config_space():
 
 
 def time_spmv(M, cfg, reps=100, warm=5):
-    """Mean time (ms) of one SpMV with ``cfg``, CUDA events on the context's stream."""
+    """Median time (ms) of one SpMV with ``cfg``: CUDA events around every call on
+    the library's stream, so the host's time between calls is not counted (a
+    configuration of several kernels still pays its own launch gaps)."""
     import torch
     x = torch.ones(M.ncols, dtype=torch.float64, device="cuda")
     y = torch.empty(M.nrows, dtype=torch.float64, device="cuda")
     M.convert(cfg)
     for _ in range(warm):
         M.spmv(x, y, cfg)
-    s = torch.cuda.current_stream()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(reps):
+    s = M.ctx.stream
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    torch.cuda.synchronize()
+    for e0, e1 in ev:
+        e0.record(s)
         M.spmv(x, y, cfg)
-    e1.record(s)
-    e1.synchronize()
-    return e0.elapsed_time(e1) / reps
+        e1.record(s)
+    torch.cuda.synchronize()
+    return float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+
+
+# one configuration per format whose conversion the cost-aware switch weighs
+CONVERSIONS = [(C.FMT_COO, C.config("COO")), (C.FMT_ELL, C.config("ELL")),
+               (C.FMT_SELL, C.config("SELL", sigma=32)), (C.FMT_HYB, C.config("HYB")),
+               (C.FMT_DIA, C.config("DIA"))]
+
+
+def conversion_times(M):
+    """{format index: ms} of converting the CSR matrix to each format from
+    scratch (cached formats dropped first), host clock around the call."""
+    import torch
+    out = {}
+    for f, cfg in CONVERSIONS:
+        M.reset()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            M.convert(cfg)
+        except C.CascadeError as e:
+            if e.status not in (C.ERR_FOOTPRINT, C.ERR_UNSUPPORTED):
+                raise
+            continue
+        torch.cuda.synchronize()
+        out[f] = (time.perf_counter() - t0) * 1e3
+    M.reset()
+    return out
 
 
 def sweep(ctx, A, reps=100):
-    """{config name: ms} for one matrix (configurations over the format budget
-    are absent)."""
+    """Features, {config name: SpMV ms} (configurations over the format budget
+    are absent) and {format: conversion ms} for one matrix."""
     M = ctx.load(A)
     times = {}
     for name, cfg in config_space():
@@ -72,9 +102,63 @@ def sweep(ctx, A, reps=100):
         except C.CascadeError as e:
             if e.status != C.ERR_FOOTPRINT:
                 raise
+    conv = conversion_times(M)
     feats = M.features()
     M.free()
-    return feats, times
+    return feats, times, conv
+
+
+def format_best(times):
+    """Fastest SpMV time of each format (CP_FMT_* index -> ms; inf if absent)."""
+    inf = float("inf")
+    return {
+        C.FMT_CSR: min([times.get("CSR-scalar", inf), times.get("CSR-merge", inf)]
+                       + [times.get(f"CSR-vector{t}", inf) for t in C.TPV_CLASSES]),
+        C.FMT_COO: times.get("COO", inf),
+        C.FMT_ELL: times.get("ELL", inf),
+        C.FMT_SELL: min(times.get(f"SELL-{s}", inf) for s in C.SIGMA_CLASSES),
+        C.FMT_HYB: times.get("HYB", inf),
+        C.FMT_DIA: times.get("DIA", inf),
+    }
+
+
+def fit_line(x, y):
+    """y = a + b x with a, b >= 0, least squares in relative error (weights
+    1/y), so the small matrices' launch-bound times and the large ones'
+    per-non-zero cost both fit."""
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
+    if len(x) < 2:
+        return (float(y.mean()) if len(y) else 0.0), 0.0
+    w = 1.0 / np.maximum(y, 1e-9)
+    b, a = np.polyfit(x, y, 1, w=w)
+    if a < 0:
+        a, b = 0.0, float(np.sum(w * w * x * y) / max(np.sum(w * w * x * x), 1e-300))
+    if b < 0:
+        a, b = float(np.average(y, weights=w * w)), 0.0
+    return float(a), float(b)
+
+
+def gate_figures(T, CV, NNZ, L):
+    """The cost-aware switch's figures (cp_gate): per format the median SpMV
+    speedup over CSR-scalar where the FORMAT label is that format, and linear
+    fits (in millions of non-zeros) of the conversion times and of the
+    CSR-scalar SpMV time."""
+    mnnz = np.asarray(NNZ, np.float64) * 1e-6
+    spmv_a, spmv_b = fit_line(mnnz, [t["CSR-scalar"] for t in T])
+    speedup, conv_a, conv_b = [1.0] * 6, [0.0] * 6, [0.0] * 6
+    for f in range(1, 6):
+        ratio = [t["CSR-scalar"] / format_best(t)[f] for t, lab in zip(T, L)
+                 if lab[0] == f and np.isfinite(format_best(t)[f])]
+        if not ratio:  # never the label: its typical ratio where it runs
+            ratio = [t["CSR-scalar"] / format_best(t)[f] for t in T
+                     if np.isfinite(format_best(t)[f])]
+        speedup[f] = float(np.median(ratio)) if ratio else 1.0
+        xs = [x for x, c in zip(mnnz, CV) if f in c]
+        ys = [c[f] for c in CV if f in c]
+        conv_a[f], conv_b[f] = fit_line(xs, ys)
+    return dict(speedup=speedup, conv_a_ms=conv_a, conv_b_ms=conv_b, spmv_a_ms=spmv_a,
+                spmv_b_ms=spmv_b)
 
 
 def _argmin_tie(cands):
@@ -120,19 +204,21 @@ def cascade_pick_time(times, pred):
 
 
 def build_dataset(ctx, suite, reps=100, log=print):
-    F, L, T, names = [], [], [], []
+    F, L, T, CV, NNZ, names = [], [], [], [], [], []
     t0 = time.time()
     for i, (name, make) in enumerate(suite):
         A = make()
-        f, times = sweep(ctx, A, reps)
+        f, times, conv = sweep(ctx, A, reps)
         F.append(f)
         L.append(labels_from_times(times))
         T.append(times)
+        CV.append(conv)
+        NNZ.append(A.nnz)
         names.append(name)
         if log and i % 20 == 0:
             log(f"[{i}/{len(suite)}] {name} n={A.nrows} nnz={A.nnz} "
                 f"best={min(times, key=times.get)} ({time.time() - t0:.0f}s)")
-    return np.array(F), np.array(L, np.int32), T, names
+    return np.array(F), np.array(L, np.int32), T, CV, NNZ, names
 
 
 def train_all(ctx, F, L, h=32, epochs=3000, lr=3e-3, seed=7):
@@ -194,7 +280,7 @@ def main():
     args = ap.parse_args()
     ctx = C.Context(0)
     suite = W.training_suite(seed=77, count=args.count)
-    F, L, T, names = build_dataset(ctx, suite, args.reps)
+    F, L, T, CV, NNZ, names = build_dataset(ctx, suite, args.reps)
     rng = np.random.default_rng(0)
     test = rng.random(len(F)) < 0.2
     mdl = train_all(ctx, F[~test], L[~test], epochs=args.epochs)
@@ -205,11 +291,16 @@ def main():
     import torch
     meta = dict(gpu=torch.cuda.get_device_name(0), matrices=len(F), test=int(test.sum()),
                 reps=args.reps, epochs=args.epochs, test_accuracy=acc, eval_test=ev_test,
-                eval_train=ev_train, losses={k: v["loss"] for k, v in mdl.items()})
+                eval_train=ev_train, losses={k: v["loss"] for k, v in mdl.items()},
+                gate=gate_figures([T[i] for i in np.flatnonzero(~test)],
+                                  [CV[i] for i in np.flatnonzero(~test)],
+                                  [NNZ[i] for i in np.flatnonzero(~test)], L[~test]))
     models.save(mdl, Path(args.out), meta)
     np.savez_compressed(Path(args.out).with_name("dataset.npz"), features=F, labels=L,
-                        names=np.array(names), test=test,
-                        times=np.array([json.dumps(t) for t in T]))
+                        names=np.array(names), test=test, nnz=np.array(NNZ),
+                        times=np.array([json.dumps(t) for t in T]),
+                        conversions=np.array([json.dumps({str(k): v for k, v in c.items()})
+                                              for c in CV]))
     print(json.dumps(meta, indent=1))
 
 

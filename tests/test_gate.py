@@ -1,0 +1,66 @@
+"""The cost-aware switch's rule (cp_gate_decide), host only: convert to the
+predicted format when (iterations left) x (1 - 1/speedup) exceeds the conversion
+cost in default-kernel SpMVs; iterations left extrapolate the residual decay seen
+so far.  Cases with a known answer, worked by hand."""
+import math
+
+import pytest
+
+from paper_2411_10143_b300 import cascade as C
+
+
+def gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05, enabled=True):
+    return C.Gate.from_dict({"speedup": [1.0] + [speedup] * 5, "conv_a_ms": [0.0] + [conv_ms] * 5,
+                             "conv_b_ms": [0.0] * 6, "spmv_a_ms": spmv_ms, "spmv_b_ms": 0.0},
+                            enabled=enabled)
+
+
+def test_disabled_gate_always_switches():
+    go, rem, cost = C.gate_decide(gate(enabled=False), C.FMT_ELL, 10**6, 10, 1.0, 0.5, 1e-10)
+    assert go and rem == -1.0 and cost == -1.0
+
+
+def test_fast_decay_does_not_pay_for_the_conversion():
+    # residual falls 10x per iteration: from 1e-2 after 2 iterations to 1e-10
+    # takes 8 more; the saving 8 * (1 - 1/2) = 4 SpMVs is below the cost 5 / 0.05 = 100
+    go, rem, cost = C.gate_decide(gate(), C.FMT_ELL, 10**6, 2, 1.0, 1e-2, 1e-10)
+    assert not go
+    assert rem == pytest.approx(8.0, rel=1e-12) and cost == pytest.approx(100.0, rel=1e-12)
+
+
+def test_slow_decay_pays_for_it():
+    # 0.999 per iteration: about 23,000 iterations left, saving ~11,500 SpMVs > 100
+    r = 0.999 ** 20
+    go, rem, _ = C.gate_decide(gate(), C.FMT_DIA, 10**6, 20, 1.0, r, 1e-10)
+    assert go and rem == pytest.approx(math.log(1e-10 / r) / math.log(0.999), rel=1e-9)
+
+
+def test_break_even_is_the_cost():
+    # at speedup 1.5 an iteration saves 1/3 SpMV: 299 iterations left save 99.7
+    # SpMVs (below the cost of 100), 301 save 100.3 (above it)
+    rate = 0.9
+    r = rate ** 10
+    g = gate(speedup=1.5)
+    assert not C.gate_decide(g, C.FMT_HYB, 10**6, 10, 1.0, r, r * rate ** 299)[0]
+    assert C.gate_decide(g, C.FMT_HYB, 10**6, 10, 1.0, r, r * rate ** 301)[0]
+
+
+def test_no_history_or_no_decay_counts_as_a_long_solve():
+    assert C.gate_decide(gate(), C.FMT_ELL, 10**6, 1, 1.0, 0.1, 1e-10)[0]
+    go, rem, _ = C.gate_decide(gate(), C.FMT_ELL, 10**6, 10, 1.0, 1.2, 1e-10)
+    assert go and rem == -1.0
+
+
+def test_no_expected_gain_or_converged_keeps_the_default():
+    assert not C.gate_decide(gate(speedup=1.0), C.FMT_ELL, 10**6, 10, 1.0, 0.5, 1e-10)[0]
+    go, rem, _ = C.gate_decide(gate(), C.FMT_ELL, 10**6, 10, 1.0, 1e-11, 1e-10)
+    assert not go and rem == 0.0
+
+
+def test_cost_scales_with_the_fits():
+    g = C.Gate.from_dict({"speedup": [1.0] * 6, "conv_a_ms": [0.0, 0.1, 0.2, 0.3, 0.4, 0.5],
+                          "conv_b_ms": [0.0, 1.0, 2.0, 3.0, 4.0, 5.0], "spmv_a_ms": 0.01,
+                          "spmv_b_ms": 0.1})
+    # DIA on 2M non-zeros: (0.5 + 5 * 2) / (0.01 + 0.1 * 2) = 50 SpMVs
+    _, _, cost = C.gate_decide(g, C.FMT_DIA, 2 * 10**6, 10, 1.0, 0.5, 1e-10)
+    assert cost == pytest.approx(10.5 / 0.21, rel=1e-12)

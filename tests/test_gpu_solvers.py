@@ -248,3 +248,40 @@ def test_persistent_cg_matches_per_step_launches(ctx, cfg, precision):
         out[mode] = (x, info)
     assert out[0][1].persist_iters > 0 and out[1][1].persist_iters == 0
     assert abs(out[0][1].iters - out[1][1].iters) <= 2
+
+
+def fixed_gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05):
+    return C.Gate.from_dict({"speedup": [1.0] + [speedup] * 5, "conv_a_ms": [0.0] + [conv_ms] * 5,
+                             "conv_b_ms": [0.0] * 6, "spmv_a_ms": spmv_ms, "spmv_b_ms": 0.0})
+
+
+def test_cost_aware_gate_keeps_the_default_on_a_short_solve():
+    """A well-conditioned system converges in a few dozen iterations: with a
+    conversion worth 100 default SpMVs and a 2x predicted speedup the gate keeps
+    CSR-scalar (no conversion, no switch), and the solve is unaffected."""
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    c.gate_set(fixed_gate())
+    A = W.diagonally_dominant(W.poisson2d(256), margin=4.0)
+    b = rhs(A, 31)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert true_relres(A, x, b) <= 1e-10
+    assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR
+    assert max(info.switch_iter) == -1 and info.t_convert_ms == 0.0
+    assert 0.0 <= info.gate_remaining < 200.0 and info.gate_cost_spmvs == pytest.approx(100.0)
+    c.close()
+
+
+def test_cost_aware_gate_switches_on_a_long_solve():
+    """2D Poisson on a 512^2 grid needs about two thousand CG iterations: the
+    same gate converts to the predicted format and switches mid-run."""
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    c.gate_set(fixed_gate())
+    A = W.poisson2d(512)
+    b = rhs(A, 32)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert true_relres(A, x, b) <= 1e-10
+    assert info.gate_declined == 0 and info.final_cfg.fmt == C.FMT_ELL
+    assert info.switch_iter[0] >= 0 and info.gate_remaining > 200.0
+    c.close()
