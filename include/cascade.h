@@ -307,7 +307,8 @@ typedef struct {
   int32_t persist_iters;   /* iterations those launches ran                               */
   float t_persist_last_ms; /* duration of the last persistent launch (final configuration) */
   int32_t persist_last_iters; /* iterations it ran                                        */
-  int32_t gate_declined;   /* the cost-aware gate kept the default format (cp_gate)       */
+  int32_t gate_declined;   /* the cost-aware gate kept the default format (cp_gate): 1 after
+                              the FORMAT stage, 2 before the feature pass (two-tier)      */
   float gate_remaining;    /* its estimate of the iterations left when it decided (-1: none) */
   float gate_cost_spmvs;   /* its estimate of the conversion cost, in default-kernel SpMVs */
 } cp_solve_info;
@@ -325,9 +326,10 @@ void cp_solve_opts_default(cp_solve_opts* opts);
  * units of one SpMV of the default kernel:
  *     remaining x (1 - 1/speedup[f])  >  cost_f(nnz)
  * remaining: iterations left, extrapolated from the residual decay the solve
- * has shown so far (geometric rate over the iterations done; a verdict to keep
- * the default is confirmed on the rate of the next 8 iterations, since Krylov
- * residuals often fall fast at first);
+ * has shown so far (geometric rate over the iterations done).  Krylov
+ * residuals often fall fast at first, so a verdict to keep the default is
+ * re-examined on later windows of 8, 16, ... iterations (at most 6) while the
+ * estimate keeps growing by more than a quarter; a steady estimate is final;
  * speedup[f]: typical SpMV speedup of format f over the default kernel where
  * the classifier picks f; cost_f(nnz) = (conv_a_ms[f] + conv_b_ms[f] nnz/1e6) /
  * (spmv_a_ms + spmv_b_ms nnz/1e6), linear fits of conversion and default-SpMV
@@ -337,13 +339,24 @@ typedef struct {
   double speedup[6];
   double conv_a_ms[6], conv_b_ms[6];  /* conversion time = a + b * nnz / 1e6 (ms)       */
   double spmv_a_ms, spmv_b_ms;        /* default-kernel SpMV time = a + b * nnz / 1e6    */
+  double feat_a_ms, feat_b_ms;        /* Table IV feature extraction time, same form     */
+  int64_t small_rows;                 /* two-tier features below this many rows          */
   int32_t enabled;                    /* 0: always switch (the paper's behaviour)        */
 } cp_gate;
 
-/* Install (or, with enabled = 0, disable) the gate for solves in ctx. */
+/* Two-tier features (also an extension; Sec. II-B quotes Swann et al.: below
+ * 100,000 rows, extracting the features costs more than one SpMV).  For a
+ * matrix with fewer than small_rows rows, the side thread first applies the
+ * rule with what costs O(1): the iterations left (from the residual decay),
+ * the best speedup over all formats, and the cost of the O(nnz) feature pass
+ * plus the cheapest conversion.  It computes the features (and runs the
+ * cascade) only if even that best case pays.
+ * Install (or, with enabled = 0, disable) the gate for solves in ctx. */
 cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate);
 /* The gate's rule, on the host: 1 to convert and switch to format fmt, 0 to
- * keep the default.  iters, res0, res: iterations done, the initial and the
+ * keep the default.  fmt < 0: the first tier's rule (compute the features or
+ * not), with the largest speedup[] and the feature pass plus the cheapest
+ * conversion as the cost.  iters, res0, res: iterations done, the initial and the
  * latest residual norms; target: the residual norm that ends the solve
  * (tol * ||b||).  Too little history (iters < 2) or no decay yet counts as a
  * long solve (switch).  remaining and cost_spmvs (may be NULL) receive the

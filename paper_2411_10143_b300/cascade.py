@@ -104,6 +104,7 @@ class Gate(Structure):
     """cp_gate: the cost-aware switching figures (arrays indexed by FORMATS)."""
     _fields_ = [("speedup", c_double * 6), ("conv_a_ms", c_double * 6),
                 ("conv_b_ms", c_double * 6), ("spmv_a_ms", c_double), ("spmv_b_ms", c_double),
+                ("feat_a_ms", c_double), ("feat_b_ms", c_double), ("small_rows", c_int64),
                 ("enabled", c_int32)]
 
     @classmethod
@@ -115,6 +116,9 @@ class Gate(Structure):
             g.conv_b_ms[i] = float(d["conv_b_ms"][i])
         g.spmv_a_ms = float(d["spmv_a_ms"])
         g.spmv_b_ms = float(d["spmv_b_ms"])
+        g.feat_a_ms = float(d.get("feat_a_ms", 0.0))
+        g.feat_b_ms = float(d.get("feat_b_ms", 0.0))
+        g.small_rows = int(d.get("small_rows", 100_000))
         g.enabled = 1 if enabled else 0
         return g
 

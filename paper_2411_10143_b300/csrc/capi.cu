@@ -112,6 +112,7 @@ cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_
       c->grid_stream = c->num_sms * (max_threads / kBlock);
       if (c->grid_stream > kMaxPartials) c->grid_stream = kMaxPartials;
       spmv_set_attributes();
+      c->side_worker = new cp::SideWorker(device);
       if (main_stream) {
         c->main = static_cast<cudaStream_t>(main_stream);
       } else {
@@ -140,6 +141,7 @@ cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_
       CP_CUDA(cudaFreeAsync(warm, c->side));
       CP_CUDA(cudaStreamSynchronize(c->side));
     } catch (...) {
+      delete c->side_worker;
       if (c->pin_main) cudaFreeHost(c->pin_main);
       if (c->pin_side) cudaFreeHost(c->pin_side);
       if (c->own_main && c->main) cudaStreamDestroy(c->main);
@@ -151,10 +153,54 @@ cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_
   });
 }
 
+namespace cp {
+SideWorker::SideWorker(int device) : th_([this, device] { loop(device); }) {}
+
+SideWorker::~SideWorker() {
+  {
+    std::lock_guard<std::mutex> lock(mu_);
+    stop_ = true;
+  }
+  cv_.notify_all();
+  th_.join();
+}
+
+void SideWorker::post(std::function<void()> job) {
+  std::lock_guard<std::mutex> lock(mu_);
+  job_ = std::move(job);
+  busy_ = true;
+  cv_.notify_all();
+}
+
+void SideWorker::wait() {
+  std::unique_lock<std::mutex> lock(mu_);
+  cv_.wait(lock, [this] { return !busy_; });
+}
+
+void SideWorker::loop(int device) {
+  cudaSetDevice(device);
+  std::unique_lock<std::mutex> lock(mu_);
+  for (;;) {
+    cv_.wait(lock, [this] { return stop_ || busy_; });
+    if (busy_) {
+      std::function<void()> job = std::move(job_);
+      lock.unlock();
+      job();  // run_cascade catches its own errors
+      lock.lock();
+      busy_ = false;
+      cv_.notify_all();
+    }
+    if (stop_ && !busy_) return;
+  }
+}
+}  // namespace cp
+
 cp_status cp_destroy(cp_ctx* ctx) {
   return guard([&] {
     if (!ctx) return;
     use_device(ctx);
+    delete ctx->side_worker;  // joins the side thread (idle between solves)
+    ctx->side_worker = nullptr;
     cudaStreamSynchronize(ctx->main);
     cudaStreamSynchronize(ctx->side);
     for (auto& mslot : ctx->models) {
@@ -345,6 +391,9 @@ cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate) {
     CP_REQUIRE(gate->spmv_a_ms >= 0.0 && gate->spmv_b_ms >= 0.0 &&
                    gate->spmv_a_ms + gate->spmv_b_ms > 0.0,
                CP_ERR_INVALID, "the default SpMV time fit must be positive");
+    CP_REQUIRE(std::isfinite(gate->feat_a_ms) && std::isfinite(gate->feat_b_ms) &&
+                   gate->small_rows >= 0,
+               CP_ERR_INVALID, "feature-cost figures must be finite, small_rows >= 0");
     ctx->gate = *gate;
   });
 }

@@ -4,10 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <condition_variable>
+#include <functional>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
 #include <string>
+#include <thread>
 
 #include "cascade.h"
 
@@ -123,6 +126,29 @@ constexpr int kDiaMax = 1024;  // most diagonals a DIA conversion accepts
 
 }  // namespace cp
 
+namespace cp {
+// The side thread of the asynchronous mode ("thread 2" of Sec. III-C-2), kept
+// alive for the context's lifetime and bound to its GPU, so that starting the
+// cascade costs a wake-up (tens of microseconds), not a thread creation and a
+// device binding (up to a millisecond, longer than a small solve).  One job at
+// a time: post() hands it over, wait() returns when it has finished.
+class SideWorker {
+ public:
+  explicit SideWorker(int device);
+  ~SideWorker();
+  void post(std::function<void()> job);
+  void wait();
+
+ private:
+  void loop(int device);
+  std::mutex mu_;
+  std::condition_variable cv_;
+  std::function<void()> job_;
+  bool busy_ = false, stop_ = false;
+  std::thread th_;
+};
+}  // namespace cp
+
 struct cp_ctx {
   int device = 0;
   int num_sms = 0;
@@ -139,6 +165,7 @@ struct cp_ctx {
   void* pin_main = nullptr;
   void* pin_side = nullptr;
   cp_gate gate{};  // cost-aware switching (disabled until installed)
+  cp::SideWorker* side_worker = nullptr;
 };
 
 struct cp_mat {
@@ -220,23 +247,29 @@ namespace cp {
 // conversions on the side stream, driven by a host thread) to the solve loop.
 // A configuration is published only after the conversion it needs has
 // completed on the side stream, so the solve loop may use it at once.
+struct Mirror;  // persist.cuh
+
 struct Channel {
   std::mutex mu;
   std::vector<std::pair<int, cp_config>> published;  // (stage, configuration) in order
   std::atomic<int> count{0};
   std::atomic<bool> cancel{false};
   std::atomic<bool> finished{false};  // the side work has ended (all stages, cancel or error)
+  // the side thread is only waiting on the host (the cost-aware gate's
+  // windows): the solve may run its persistent kernel meanwhile, and asks it
+  // to return as soon as this goes false (the side stream needs the GPU)
+  std::atomic<bool> side_gpu_idle{false};
   bool need_fp32 = false;  // the solve also needs FP32 values of every published format
   float t_features_ms = 0.f, t_predict_ms[3] = {0.f, 0.f, 0.f}, t_convert_ms = 0.f;
   cp_status status = CP_OK;  // first error of the side thread, if any
   std::string error;
-  // the solve's progress for the cost-aware gate (FP64 solves): iterations
-  // done, the latest and the initial residual norm, ||b||; iters < 0: none yet
-  std::atomic<int> prog_iters{-1};
-  std::atomic<double> prog_res{0.0}, prog_res0{0.0}, prog_bnorm{0.0};
+  // the solve's progress for the cost-aware gate (FP64 solves): the solve's
+  // host-mapped mirror, which the GPU updates as iterations complete (null
+  // until the solve has set it up)
+  std::atomic<const Mirror*> live{nullptr};
   std::atomic<bool> solve_done{false};
   double tol = 0.0;
-  bool gate_declined = false;
+  int gate_declined = 0;  // 1: kept the default after FORMAT; 2: skipped the feature pass
   float gate_remaining = -1.f, gate_cost = -1.f;
 
   void publish(int stage, const cp_config& c) {

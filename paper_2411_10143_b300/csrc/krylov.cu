@@ -623,13 +623,9 @@ struct ConfigSource {
   float t_persist_last_ms = 0.f;
   int persist_last_iters = 0;
 
-  // the solve's progress, for the side thread's cost-aware gate
-  void progress(const Mirror* mir) {
-    if (!ch) return;
-    ch->prog_res0.store(mir->res0, std::memory_order_relaxed);
-    ch->prog_bnorm.store(mir->bnorm, std::memory_order_relaxed);
-    ch->prog_res.store(mir->res, std::memory_order_relaxed);
-    ch->prog_iters.store(mir->iters, std::memory_order_release);
+  // hands the solve's live mirror to the side thread's cost-aware gate
+  void expose(const Mirror* mir) {
+    if (ch) ch->live.store(mir, std::memory_order_release);
   }
   void poll(int iter) {
     if (!ch) return;
@@ -708,6 +704,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
   double *pa = B.pa, *pb = B.pb, *pc = B.pc;
   CgState* st = B.st;
   Mirror* mir = ws.mirror();
+  cs.expose(ws.mir);
   CP_CUDA(cudaMemsetAsync(st, 0, sizeof(CgState), s));
   const double tol2 = tol * tol;
   const int G = grid_n(ctx, n);
@@ -737,9 +734,11 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       cs.poll(it);
       // The persistent kernel runs only while no prediction work is pending on the
       // side stream: a cooperative grid holds the device, so the side stream's
-      // kernels would wait for it.  Until the cascade has finished, iterations
-      // go one launch per step, interleaving with the side kernels.
-      const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire);
+      // kernels would wait for it.  Until the cascade has finished (or while it
+      // only waits on the host), iterations go one launch per step,
+      // interleaving with the side kernels.
+      const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire) ||
+                             cs.ch->side_gpu_idle.load(std::memory_order_acquire);
       if (cs.persistent && side_idle && persist_supported<T>(m, cs.cur)) {
         // one cooperative launch runs iterations [it, maxit) until convergence, a
         // breakdown, or the host asks it to return at an iteration boundary
@@ -770,7 +769,12 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
           const cudaError_t q = cudaEventQuery(e1);
           if (q == cudaSuccess) break;
           if (q != cudaErrorNotReady) CP_CUDA(q);
-          if (cs.ch && !*ws.yield_h && cs.ch->count.load(std::memory_order_acquire) > cs.applied)
+          // return at the next iteration boundary when a configuration was
+          // published, or when the side thread needs the GPU again
+          if (cs.ch && !*ws.yield_h &&
+              (cs.ch->count.load(std::memory_order_acquire) > cs.applied ||
+               (!cs.ch->finished.load(std::memory_order_acquire) &&
+                !cs.ch->side_gpu_idle.load(std::memory_order_acquire))))
             *(volatile int*)ws.yield_h = 1;
           std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
@@ -797,7 +801,6 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       ++it;
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
-        cs.progress(ws.mir);
         if (ws.mir->done) break;
       }
       // the loop head hands the remaining iterations to the persistent kernel
@@ -858,6 +861,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
   double *part = B.part, *pn = B.pn;
   GmState* st = B.st;
   Mirror* mir = ws.mirror();
+  cs.expose(ws.mir);
   CP_CUDA(cudaMemsetAsync(st, 0, sizeof(GmState), s));
   const double tol2 = tol * tol;
   const int G = grid_n(ctx, n);
@@ -909,7 +913,6 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       ++issued;
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));
-        cs.progress(ws.mir);
         if (ws.mir->halt) break;
       }
     }
@@ -1034,8 +1037,10 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
 
   Channel ch;
   ch.need_fp32 = fp32;
-  ch.tol = fp32 ? 0.0 : opt.tol;  // the gate follows FP64 solves' residuals
-  std::thread side;
+  // the gate follows an FP64 solve's residuals while it runs (asynchronous
+  // mode); the sequential mode predicts before there is any
+  ch.tol = (!fp32 && opt.mode == CP_MODE_ASYNC) ? opt.tol : 0.0;
+  bool side_posted = false;
   const bool predict = !opt.force && opt.mode != CP_MODE_PLAIN;
   trace("solve: start n=%lld mode=%d precision=%d", (long long)m->nrows, opt.mode, opt.precision);
   if (predict) {
@@ -1044,13 +1049,15 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
       run_cascade(ctx, m, ctx->side, &ch);  // predict first, then solve (SerGMRES)
       cs.poll(0);
     } else {
-      side = std::thread([ctx, m, &ch]() { run_cascade(ctx, m, ctx->side, &ch); });
+      ctx->side_worker->post([ctx, m, &ch]() { run_cascade(ctx, m, ctx->side, &ch); });
+      side_posted = true;
     }
   }
   auto stop_side = [&]() {
     ch.solve_done.store(true);
     ch.cancel.store(true);
-    if (side.joinable()) side.join();
+    if (side_posted) ctx->side_worker->wait();
+    side_posted = false;
   };
 
   LoopResult res;
@@ -1091,7 +1098,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     info->persist_iters = cs.persist_iters;
     info->t_persist_last_ms = cs.t_persist_last_ms;
     info->persist_last_iters = cs.persist_last_iters;
-    info->gate_declined = ch.gate_declined ? 1 : 0;
+    info->gate_declined = ch.gate_declined;
     info->gate_remaining = ch.gate_remaining;
     info->gate_cost_spmvs = ch.gate_cost;
     info->n_launches = (int32_t)(ctx->launches.load() - launches0);

@@ -6,6 +6,7 @@
 // that inference costs microseconds (Sec. III-C-2, Table V); here inference is
 // one GPU block on the side stream, and training runs on the GPU with the
 // forward / backward / Adam kernels below.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <thread>
@@ -14,6 +15,7 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "persist.cuh"
 
 namespace cp {
 
@@ -425,12 +427,23 @@ int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, 
                 double target, double* remaining, double* cost) {
   double rem = -1.0, kappa = -1.0;
   int go = 1;
-  if (g.enabled && fmt > 0 && fmt < CP_NUM_FMT) {
+  if (g.enabled && fmt < CP_NUM_FMT && fmt != 0) {
     const double mnnz = (double)nnz * 1e-6;
     const double t_spmv = g.spmv_a_ms + g.spmv_b_ms * mnnz;
-    const double t_conv = g.conv_a_ms[fmt] + g.conv_b_ms[fmt] * mnnz;
+    double t_conv, s;
+    if (fmt > 0) {
+      t_conv = g.conv_a_ms[fmt] + g.conv_b_ms[fmt] * mnnz;
+      s = g.speedup[fmt];
+    } else {  // first tier: the best case over the formats, features included
+      t_conv = 1e300;
+      s = 1.0;
+      for (int f = 1; f < CP_NUM_FMT; ++f) {
+        t_conv = std::min(t_conv, g.conv_a_ms[f] + g.conv_b_ms[f] * mnnz);
+        s = std::max(s, g.speedup[f]);
+      }
+      t_conv += g.feat_a_ms + g.feat_b_ms * mnnz;
+    }
     kappa = t_spmv > 0.0 ? t_conv / t_spmv : 1e300;
-    const double s = g.speedup[fmt];
     if (!(s > 1.0)) {
       go = 0;  // no gain expected from the format
     } else if (iters >= 2 && res0 > 0.0 && res > 0.0 && target > 0.0) {
@@ -451,19 +464,89 @@ int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, 
   return go;
 }
 
-constexpr int kGateWindow = 8;  // iterations over which a "keep" verdict is confirmed
+constexpr int kGateWindow = 8;  // first window over which a "keep" verdict is re-examined
+constexpr int kGateRounds = 6;  // windows at most (8, 16, ... iterations)
 
-// Waits (bounded) until the solve has reported at least `iters` iterations,
+// The solve's progress as its GPU has written it: iterations done (-1: not
+// started), latest and initial residual norm, ||b||.
+struct Progress {
+  int iters = -1;
+  double res = 0.0, res0 = 0.0, bnorm = 0.0;
+};
+static Progress progress(const Channel* ch) {
+  Progress p;
+  const Mirror* mir = ch->live.load(std::memory_order_acquire);
+  if (!mir) return p;
+  p.res0 = mir->res0;
+  p.bnorm = mir->bnorm;
+  p.res = mir->res;
+  p.iters = p.res0 > 0.0 ? mir->iters : -1;  // res0 is written when the solve starts
+  return p;
+}
+
+// Waits (bounded) until the solve has done at least `iters` iterations,
 // finished, or the side work was cancelled.
 static void wait_progress(Channel* ch, int iters, double max_ms) {
   const auto t0 = std::chrono::steady_clock::now();
-  while (ch->prog_iters.load(std::memory_order_acquire) < iters &&
-         !ch->solve_done.load(std::memory_order_acquire) && !ch->cancel.load()) {
+  while (progress(ch).iters < iters && !ch->solve_done.load(std::memory_order_acquire) &&
+         !ch->cancel.load()) {
     if (std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() >
         max_ms)
       return;
     std::this_thread::sleep_for(std::chrono::microseconds(20));
   }
+}
+
+// The gate: decides on the decay since the start; a "keep" is re-examined on
+// later windows (the solve stays on the default kernel meanwhile).  Returns
+// true to go on; records the estimates in ch; sets ch->gate_declined to `tier`
+// while keeping.
+static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
+  // only host waits follow until the verdict: the solve may use the whole GPU
+  struct Idle {
+    Channel* c;
+    explicit Idle(Channel* ch) : c(ch) { c->side_gpu_idle.store(true, std::memory_order_release); }
+    ~Idle() { c->side_gpu_idle.store(false, std::memory_order_release); }
+  } idle(ch);
+  double rem = -1.0, cost = -1.0;
+  wait_progress(ch, 2, 5.0);  // two iterations of history (the GPU's own count)
+  if (ch->cancel.load()) return false;
+  const Progress p = progress(ch);
+  const double target = ch->tol * p.bnorm;
+  int go = gate_decide(ctx->gate, fmt, m->nnz, p.iters, p.res0, p.res, target, &rem, &cost);
+  ch->gate_remaining = (float)rem;
+  ch->gate_cost = (float)cost;
+  trace("cascade: gate (tier %d, format %d): %d iterations left, cost %.1f SpMVs -> %s", tier,
+        fmt, (int)rem, cost, go ? "go" : "keep (to be confirmed)");
+  if (go) return true;
+  // Krylov residuals often drop fast in the first iterations and slow down
+  // later, so a "keep" is re-examined on later windows of doubling length
+  // while the estimate of the iterations left keeps growing (by more than a
+  // quarter per window); a steady estimate makes it final
+  ch->gate_declined = tier;
+  int k1 = p.iters;
+  double r1 = p.res, est = rem;
+  int w = std::max(kGateWindow, k1);
+  for (int round = 0; round < kGateRounds; ++round, w *= 2) {
+    wait_progress(ch, k1 + w, 50.0);
+    if (ch->cancel.load()) return false;
+    const Progress q = progress(ch);
+    if (q.iters <= k1) return false;
+    go = gate_decide(ctx->gate, fmt, m->nnz, q.iters - k1, r1, q.res, target, &rem, &cost);
+    ch->gate_remaining = (float)rem;
+    ch->gate_cost = (float)cost;
+    trace("cascade: gate window %d..%d: %d iterations left -> %s", k1, q.iters, (int)rem,
+          go ? "go" : "keep");
+    if (go) {
+      ch->gate_declined = 0;
+      return true;
+    }
+    if (!(rem > 1.25 * est)) return false;  // the estimate has settled
+    est = rem;
+    k1 = q.iters;
+    r1 = q.res;
+  }
+  return false;
 }
 
 void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
@@ -478,6 +561,11 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
   try {
     CP_CUDA(cudaSetDevice(ctx->device));  // the side thread's CUDA calls target ctx's GPU
     trace("cascade: side thread started");
+    if (ctx->gate.enabled && ch->tol > 0.0 && m->nrows < ctx->gate.small_rows) {
+      // two-tier features: on a small matrix the O(nnz) feature pass is run
+      // only if the best case over the formats can pay for it
+      if (!gate_pass(ctx, m, ch, -1, 2)) return;
+    }
     auto t = Clock::now();
     double f[kFeat];
     compute_features(ctx, m, s, f);  // Table IV, on the side stream
@@ -502,37 +590,9 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
     if (ch->cancel.load()) return;
     if (next.fmt != cfg.fmt && ctx->gate.enabled && ch->tol > 0.0) {
       // cost-aware switching: convert only if the saving over the iterations
-      // left pays for the conversion.  A solve that has not reported two
-      // iterations by now (a large matrix) counts as long: no waiting here.
-      double rem = -1.0, cost = -1.0;
-      const double target = ch->tol * ch->prog_bnorm.load();
-      int go = gate_decide(ctx->gate, next.fmt, m->nnz, ch->prog_iters.load(),
-                           ch->prog_res0.load(), ch->prog_res.load(), target, &rem, &cost);
-      ch->gate_remaining = (float)rem;
-      ch->gate_cost = (float)cost;
-      trace("cascade: gate for format %d: %d iterations left, conversion %.1f SpMVs -> %s",
-            next.fmt, (int)rem, cost, go ? "switch" : "keep (to be confirmed)");
-      if (!go) {
-        // Krylov residuals often drop fast in the first iterations, so a "keep"
-        // is confirmed on the decay over the next kGateWindow iterations; the
-        // solve stays on the default kernel meanwhile
-        ch->gate_declined = true;
-        const int k1 = ch->prog_iters.load(std::memory_order_acquire);
-        const double r1 = ch->prog_res.load();
-        wait_progress(ch, k1 + kGateWindow, 50.0);
-        if (ch->cancel.load()) return;
-        const int k2 = ch->prog_iters.load(std::memory_order_acquire);
-        if (k2 > k1) {
-          go = gate_decide(ctx->gate, next.fmt, m->nnz, k2 - k1, r1, ch->prog_res.load(), target,
-                           &rem, &cost);
-          ch->gate_remaining = (float)rem;
-          ch->gate_cost = (float)cost;
-          trace("cascade: gate window %d..%d: %d iterations left -> %s", k1, k2, (int)rem,
-                go ? "switch" : "keep");
-        }
-        if (!go) return;
-        ch->gate_declined = false;
-      }
+      // left pays for the conversion.  The gate waits at most 5 ms for two
+      // iterations of history; without it the solve counts as long.
+      if (!gate_pass(ctx, m, ch, next.fmt, 1)) return;
     }
     if (next.fmt != cfg.fmt) {
       t = Clock::now();

@@ -43,25 +43,32 @@ def config_space():
 
 
 def time_spmv(M, cfg, reps=100, warm=5):
-    """Median time (ms) of one SpMV with ``cfg``: CUDA events around every call on
-    the library's stream, so the host's time between calls is not counted (a
-    configuration of several kernels still pays its own launch gaps)."""
+    """Device time (ms) of one SpMV with ``cfg``: `reps` calls captured in one
+    CUDA graph on the library's stream and replayed between two events, so the
+    host's launch latency (larger than a small matrix's kernel) is not timed; a
+    configuration of several kernels still pays its own launches."""
     import torch
     x = torch.ones(M.ncols, dtype=torch.float64, device="cuda")
     y = torch.empty(M.nrows, dtype=torch.float64, device="cuda")
     M.convert(cfg)
     for _ in range(warm):
         M.spmv(x, y, cfg)
+    torch.cuda.synchronize()
     s = M.ctx.stream
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(reps)]
-    torch.cuda.synchronize()
-    for e0, e1 in ev:
-        e0.record(s)
-        M.spmv(x, y, cfg)
-        e1.record(s)
-    torch.cuda.synchronize()
-    return float(np.median([e0.elapsed_time(e1) for e0, e1 in ev]))
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+        for _ in range(reps):
+            M.spmv(x, y, cfg)
+    g.replay()  # warm
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record()
+        g.replay()
+        e1.record()
+    e1.synchronize()
+    del g
+    return e0.elapsed_time(e1) / reps
 
 
 # one configuration per format whose conversion the cost-aware switch weighs
@@ -72,7 +79,8 @@ CONVERSIONS = [(C.FMT_COO, C.config("COO")), (C.FMT_ELL, C.config("ELL")),
 
 def conversion_times(M):
     """{format index: ms} of converting the CSR matrix to each format from
-    scratch (cached formats dropped first), host clock around the call."""
+    scratch (cached formats dropped first), host clock around the call; the
+    sweep adds "features": ms of the feature pass."""
     import torch
     out = {}
     for f, cfg in CONVERSIONS:
@@ -103,7 +111,12 @@ def sweep(ctx, A, reps=100):
             if e.status != C.ERR_FOOTPRINT:
                 raise
     conv = conversion_times(M)
-    feats = M.features()
+    import torch
+    M.reset()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    feats = M.features()  # the O(nnz) Table IV pass, timed for the two-tier rule
+    conv["features"] = (time.perf_counter() - t0) * 1e3
     M.free()
     return feats, times, conv
 
@@ -157,8 +170,9 @@ def gate_figures(T, CV, NNZ, L):
         xs = [x for x, c in zip(mnnz, CV) if f in c]
         ys = [c[f] for c in CV if f in c]
         conv_a[f], conv_b[f] = fit_line(xs, ys)
+    feat_a, feat_b = fit_line(mnnz, [c["features"] for c in CV])
     return dict(speedup=speedup, conv_a_ms=conv_a, conv_b_ms=conv_b, spmv_a_ms=spmv_a,
-                spmv_b_ms=spmv_b)
+                spmv_b_ms=spmv_b, feat_a_ms=feat_a, feat_b_ms=feat_b, small_rows=100_000)
 
 
 def _argmin_tie(cands):

@@ -64,3 +64,19 @@ def test_cost_scales_with_the_fits():
     # DIA on 2M non-zeros: (0.5 + 5 * 2) / (0.01 + 0.1 * 2) = 50 SpMVs
     _, _, cost = C.gate_decide(g, C.FMT_DIA, 2 * 10**6, 10, 1.0, 0.5, 1e-10)
     assert cost == pytest.approx(10.5 / 0.21, rel=1e-12)
+
+
+def test_first_tier_uses_the_best_case_and_the_feature_cost():
+    # fmt < 0 (before the feature pass): the largest speedup (4) and the cost
+    # of the features plus the cheapest conversion, (0.5 + 0.25) / 0.05 = 15 SpMVs
+    g = C.Gate.from_dict({"speedup": [1.0, 1.5, 4.0, 2.0, 1.2, 3.0],
+                          "conv_a_ms": [0.0, 1.0, 0.25, 2.0, 0.5, 3.0], "conv_b_ms": [0.0] * 6,
+                          "spmv_a_ms": 0.05, "spmv_b_ms": 0.0, "feat_a_ms": 0.5,
+                          "feat_b_ms": 0.0})
+    rate = 0.8
+    r = rate ** 4
+    # 19 iterations left save 19 * 0.75 = 14.25 SpMVs < 15; 21 save 15.75 > 15
+    go, rem, cost = C.gate_decide(g, -1, 10**4, 4, 1.0, r, r * rate ** 19)
+    assert not go and cost == pytest.approx(15.0, rel=1e-12)
+    assert rem == pytest.approx(19.0, rel=1e-9)
+    assert C.gate_decide(g, -1, 10**4, 4, 1.0, r, r * rate ** 21)[0]

@@ -250,9 +250,10 @@ def test_persistent_cg_matches_per_step_launches(ctx, cfg, precision):
     assert abs(out[0][1].iters - out[1][1].iters) <= 2
 
 
-def fixed_gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05):
+def fixed_gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05, feat_ms=0.0, small_rows=0):
     return C.Gate.from_dict({"speedup": [1.0] + [speedup] * 5, "conv_a_ms": [0.0] + [conv_ms] * 5,
-                             "conv_b_ms": [0.0] * 6, "spmv_a_ms": spmv_ms, "spmv_b_ms": 0.0})
+                             "conv_b_ms": [0.0] * 6, "spmv_a_ms": spmv_ms, "spmv_b_ms": 0.0,
+                             "feat_a_ms": feat_ms, "feat_b_ms": 0.0, "small_rows": small_rows})
 
 
 def test_cost_aware_gate_keeps_the_default_on_a_short_solve():
@@ -262,11 +263,12 @@ def test_cost_aware_gate_keeps_the_default_on_a_short_solve():
     c = C.Context(0)
     one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
     c.gate_set(fixed_gate())
-    A = W.diagonally_dominant(W.poisson2d(256), margin=4.0)
+    A = W.diagonally_dominant(W.poisson2d(256), margin=0.5)  # a few dozen iterations
     b = rhs(A, 31)
     x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
     assert true_relres(A, x, b) <= 1e-10
-    assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR
+    diag = (info.gate_declined, info.gate_remaining, info.gate_cost_spmvs, info.iters)
+    assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR, diag
     assert max(info.switch_iter) == -1 and info.t_convert_ms == 0.0
     assert 0.0 <= info.gate_remaining < 200.0 and info.gate_cost_spmvs == pytest.approx(100.0)
     c.close()
@@ -284,4 +286,23 @@ def test_cost_aware_gate_switches_on_a_long_solve():
     assert true_relres(A, x, b) <= 1e-10
     assert info.gate_declined == 0 and info.final_cfg.fmt == C.FMT_ELL
     assert info.switch_iter[0] >= 0 and info.gate_remaining > 200.0
+    c.close()
+
+
+def test_two_tier_features_skip_the_feature_pass_on_a_short_small_solve():
+    """Below small_rows rows the side thread first asks whether even the best
+    format could pay for the O(nnz) feature pass plus a conversion; on a
+    well-conditioned small system it cannot, so no feature is computed and the
+    solve stays on CSR-scalar."""
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    c.gate_set(fixed_gate(feat_ms=20.0, small_rows=100_000))
+    A = W.diagonally_dominant(W.poisson2d(300), margin=0.5)  # n 90,000: tens of iterations
+    b = rhs(A, 33)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert true_relres(A, x, b) <= 1e-10
+    diag = (info.gate_declined, info.gate_remaining, info.gate_cost_spmvs, info.iters)
+    assert info.gate_declined == 2 and info.t_features_ms == 0.0, diag
+    assert info.final_cfg.fmt == C.FMT_CSR and max(info.switch_iter) == -1
+    assert info.gate_cost_spmvs == pytest.approx((20.0 + 5.0) / 0.05)
     c.close()
