@@ -14,11 +14,13 @@
 #include <cmath>
 #include <cstring>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
 #include "internal.cuh"
 #include "persist.cuh"
+#include "spmv_rows.cuh"
 
 namespace cp {
 
@@ -36,6 +38,8 @@ struct GmState {
   int jdone;             // steps completed in this cycle
   int status;
   int iters;             // steps completed in total
+  int skip2;             // this step's second Gram-Schmidt pass is not needed
+  int reorths;           // steps that took the second pass
 };
 
 // ================================================================== CG kernels
@@ -297,54 +301,94 @@ __global__ void k_add_f32(int64_t n, double* __restrict__ x, const float* __rest
 }
 
 // ================================================================== GMRES kernels
-// Multi-dot of w with columns V[0..nc): partials[c * P + block]; columns in
-// groups of 8 so each thread keeps 8 accumulators.
+// Multi-dot of w with columns V[c0 .. c0+R) (and, with NORM, (w, w) as one
+// more column): partials[(c0 + g) * P + block].  R is exact (no padding
+// columns: an idle FMA slot costs the FP64 pipe as much as a used one).
+template <typename T, int R, bool NORM>
+__device__ __forceinline__ void gm_dots_group(int64_t n, const T* __restrict__ V, int64_t ldv,
+                                              int c0, int nc, const T* __restrict__ w,
+                                              double* __restrict__ part, double* red) {
+  constexpr int G = R + (NORM ? 1 : 0);
+  T acc[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) acc[g] = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const T wi = w[i];
+    T v[R];
+#pragma unroll
+    for (int g = 0; g < R; ++g) v[g] = V[(int64_t)(c0 + g) * ldv + i];
+#pragma unroll
+    for (int g = 0; g < R; ++g) acc[g] = fma(v[g], wi, acc[g]);
+    if (NORM) acc[R] = fma(wi, wi, acc[R]);
+  }
+  double accd[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) accd[g] = (double)acc[g];
+  block_sum_multi_lean<G>(accd, red);
+  if (threadIdx.x == 0) {
+    const int P = gridDim.x;
+#pragma unroll
+    for (int g = 0; g < R; ++g) part[(int64_t)(c0 + g) * P + blockIdx.x] = accd[g];
+    if (NORM) part[(int64_t)nc * P + blockIdx.x] = accd[R];
+  }
+  __syncthreads();
+}
+
+template <typename T, bool NORM>
+__device__ __forceinline__ void gm_dots_rest(int r, int64_t n, const T* V, int64_t ldv, int c0,
+                                             int nc, const T* w, double* part, double* red) {
+  switch (r) {
+    case 1: gm_dots_group<T, 1, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    case 2: gm_dots_group<T, 2, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    case 3: gm_dots_group<T, 3, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    case 4: gm_dots_group<T, 4, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    case 5: gm_dots_group<T, 5, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    case 6: gm_dots_group<T, 6, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    case 7: gm_dots_group<T, 7, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    default: gm_dots_group<T, 8, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+  }
+}
+
+// Multi-dot of w with columns V[0..nc): partials[c * P + block], columns in
+// groups of 8 (eight accumulators a thread) with an exact last group; the
+// first pass (with_norm) also gives (w, w) in column nc.  The second pass
+// returns at once when the first left w orthogonal enough (skip2).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gm_dots(int64_t n, const T* __restrict__ V,
                                                     int64_t ldv, int nc, const T* __restrict__ w,
-                                                    double* __restrict__ part, GmState* st) {
+                                                    double* __restrict__ part, GmState* st,
+                                                    int with_norm) {
   if (*(volatile int*)&st->halt) return;
-  __shared__ double red[8 * 32];
-  const int P = gridDim.x;
+  if (!with_norm && *(volatile int*)&st->skip2) return;
+  __shared__ double red[9 * kBlock + 9];
   for (int c0 = 0; c0 < nc; c0 += 8) {
-    T acc[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) acc[g] = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-      const T wi = w[i];
-#pragma unroll
-      for (int g = 0; g < 8; ++g)
-        if (c0 + g < nc) acc[g] = fma(V[(int64_t)(c0 + g) * ldv + i], wi, acc[g]);
-    }
-    double accd[8];
-#pragma unroll
-    for (int g = 0; g < 8; ++g) accd[g] = (double)acc[g];
-    block_sum_multi<8>(accd, red);
-    if (threadIdx.x == 0) {
-#pragma unroll
-      for (int g = 0; g < 8; ++g)
-        if (c0 + g < nc) part[(int64_t)(c0 + g) * P + blockIdx.x] = accd[g];
-    }
-    __syncthreads();
+    const int r = nc - c0 < 8 ? nc - c0 : 8;
+    if (with_norm && c0 == 0) gm_dots_rest<T, true>(r, n, V, ldv, c0, nc, w, part, red);
+    else gm_dots_rest<T, false>(r, n, V, ldv, c0, nc, w, part, red);
   }
 }
 
 // nc blocks: out[c] = sum of column c's partials (fixed order)
-__global__ void k_gm_reduce(const double* __restrict__ part, int P, double* out, GmState* st) {
+__global__ void k_gm_reduce(const double* __restrict__ part, int P, double* out, GmState* st,
+                            int pass2) {
   if (*(volatile int*)&st->halt) return;
+  if (pass2 && *(volatile int*)&st->skip2) return;
   __shared__ double red[40];
   const double s = reduce_partials(part + (int64_t)blockIdx.x * P, P, red);
   if (threadIdx.x == 0) out[blockIdx.x] = s;
 }
 
-// w -= V[:, 0..nc) h; partials of ||w||^2
+// w -= V[:, 0..nc) h; partials of ||w||^2.  The columns go four at a time with
+// their loads issued together (an exact last chunk).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_gm_sub(int64_t n, const T* __restrict__ V,
                                                    int64_t ldv, int nc, T* __restrict__ w,
                                                    const double* __restrict__ h,
-                                                   double* __restrict__ part, GmState* st) {
+                                                   double* __restrict__ part, GmState* st,
+                                                   int pass2) {
   if (*(volatile int*)&st->halt) return;
+  if (pass2 && *(volatile int*)&st->skip2) return;
   __shared__ T hs[kMaxRestart + 1];
   for (int c = threadIdx.x; c < nc; c += blockDim.x) hs[c] = (T)h[c];
   __syncthreads();
@@ -352,13 +396,43 @@ __global__ void __launch_bounds__(kBlock) k_gm_sub(int64_t n, const T* __restric
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     T wi = w[i];
-    for (int c = 0; c < nc; ++c) wi = fma(-hs[c], V[(int64_t)c * ldv + i], wi);
+    for_slots(nc, [&](int64_t c0, auto R) {
+      constexpr int r = decltype(R)::value;
+      T v[r];
+#pragma unroll
+      for (int u = 0; u < r; ++u) v[u] = V[(c0 + u) * ldv + i];
+#pragma unroll
+      for (int u = 0; u < r; ++u) wi = fma(-hs[c0 + u], v[u], wi);
+      return false;
+    });
     w[i] = wi;
     acc = fma(wi, wi, acc);
   }
-  __shared__ double red[33];
-  const double s = block_sum((double)acc, red);
+  __shared__ double red[kBlock + 4];
+  const double s = block_sum_lean((double)acc, red);
   if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+// One thread after the first Gram-Schmidt pass: the second pass is needed only
+// if the first removed most of w, ||w'|| < ||w|| / sqrt(2) (the criterion of
+// Daniel, Gragg, Kaufman and Stewart, 1976); otherwise its coefficients are 0.
+// (w, w) before the pass is h1[nc]; ||w'||^2 comes from the partials.
+// FP32 solves (the inner solves of the refinement) always take the second
+// pass: single precision loses orthogonality too fast for the test to pay.
+__global__ void k_gm_reorth_test(const double* __restrict__ part, int P, GmState* st, int nc,
+                                 int always) {
+  if (*(volatile int*)&st->halt) return;
+  __shared__ double red[40];
+  const double w2 = reduce_partials(part, P, red);
+  if (threadIdx.x != 0) return;
+  const double ww = st->h1[nc];
+  const int skip = (!always && w2 >= 0.5 * ww) ? 1 : 0;
+  st->skip2 = skip;
+  if (skip) {
+    for (int c = 0; c < nc; ++c) st->h2[c] = 0.0;
+  } else {
+    st->reorths += 1;
+  }
 }
 
 // One thread: column j of H from h1 + h2 and ||w||, previous rotations, the new
@@ -865,6 +939,15 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
   CP_CUDA(cudaMemsetAsync(st, 0, sizeof(GmState), s));
   const double tol2 = tol * tol;
   const int G = grid_n(ctx, n);
+  // the multi-dot kernel keeps up to nine accumulators a thread: its grid is
+  // what stays resident (more blocks would only queue in waves)
+  int Gd = G;
+  {
+    int per_sm = 0;
+    CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_gm_dots<T>, kBlock, 0));
+    const int res = ctx->num_sms * (per_sm > 0 ? per_sm : 1);
+    if (Gd > res) Gd = res;
+  }
   // ||b||^2 into h1[0] for the first cycle start
   {
     const int P = dot_partials<T>(ctx, n, b, b, pn, nullptr, s);
@@ -901,11 +984,18 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       T* vj = V + (int64_t)j * ldv;
       T* w = V + (int64_t)(j + 1) * ldv;
       spmv_cur<T>(cs, vj, w, nullptr, nullptr, &st->halt, s);
-      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+      // classical Gram-Schmidt, and a second time only where the first pass
+      // removed most of w (k_gm_reorth_test)
+      for (int pass = 0; pass < 2; ++pass) {
         double* h = pass == 0 ? st->h1 : st->h2;
-        CP_LAUNCH(ctx, k_gm_dots<T>, G, kBlock, 0, s, n, V, ldv, j + 1, w, part, st);
-        CP_LAUNCH(ctx, k_gm_reduce, j + 1, kBlock, 0, s, part, G, h, st);
-        CP_LAUNCH(ctx, k_gm_sub<T>, G, kBlock, 0, s, n, V, ldv, j + 1, w, h, pn, st);
+        CP_LAUNCH(ctx, k_gm_dots<T>, Gd, kBlock, 0, s, n, V, ldv, j + 1, w, part, st,
+                  pass == 0 ? 1 : 0);
+        CP_LAUNCH(ctx, k_gm_reduce, pass == 0 ? j + 2 : j + 1, kBlock, 0, s, part, Gd, h, st,
+                  pass);
+        CP_LAUNCH(ctx, k_gm_sub<T>, G, kBlock, 0, s, n, V, ldv, j + 1, w, h, pn, st, pass);
+        if (pass == 0)
+          CP_LAUNCH(ctx, k_gm_reorth_test, 1, kBlock, 0, s, pn, G, st, j + 1,
+                    std::is_same<T, float>::value ? 1 : 0);
       }
       CP_LAUNCH(ctx, k_gm_givens, 1, kBlock, 0, s, pn, G, st, j, steps, tol2, mir);
       CP_LAUNCH(ctx, k_gm_scale<T>, G, kBlock, 0, s, n, w, st, 1);
