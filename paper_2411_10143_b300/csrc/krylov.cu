@@ -335,6 +335,8 @@ __device__ __forceinline__ void gm_dots_group(int64_t n, const T* __restrict__ V
   __syncthreads();
 }
 
+constexpr int kGmGroup = 4;  // columns a thread accumulates at once
+
 template <typename T, bool NORM>
 __device__ __forceinline__ void gm_dots_rest(int r, int64_t n, const T* V, int64_t ldv, int c0,
                                              int nc, const T* w, double* part, double* red) {
@@ -342,28 +344,26 @@ __device__ __forceinline__ void gm_dots_rest(int r, int64_t n, const T* V, int64
     case 1: gm_dots_group<T, 1, NORM>(n, V, ldv, c0, nc, w, part, red); break;
     case 2: gm_dots_group<T, 2, NORM>(n, V, ldv, c0, nc, w, part, red); break;
     case 3: gm_dots_group<T, 3, NORM>(n, V, ldv, c0, nc, w, part, red); break;
-    case 4: gm_dots_group<T, 4, NORM>(n, V, ldv, c0, nc, w, part, red); break;
-    case 5: gm_dots_group<T, 5, NORM>(n, V, ldv, c0, nc, w, part, red); break;
-    case 6: gm_dots_group<T, 6, NORM>(n, V, ldv, c0, nc, w, part, red); break;
-    case 7: gm_dots_group<T, 7, NORM>(n, V, ldv, c0, nc, w, part, red); break;
-    default: gm_dots_group<T, 8, NORM>(n, V, ldv, c0, nc, w, part, red); break;
+    default: gm_dots_group<T, kGmGroup, NORM>(n, V, ldv, c0, nc, w, part, red); break;
   }
 }
 
 // Multi-dot of w with columns V[0..nc): partials[c * P + block], columns in
-// groups of 8 (eight accumulators a thread) with an exact last group; the
-// first pass (with_norm) also gives (w, w) in column nc.  The second pass
-// returns at once when the first left w orthogonal enough (skip2).
+// groups of kGmGroup (that many accumulators a thread, registers for four
+// resident blocks an SM) with an exact last group; the first pass (with_norm)
+// also gives (w, w) in column nc.  The second pass returns at once when the
+// first left w orthogonal enough (skip2).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_gm_dots(int64_t n, const T* __restrict__ V,
-                                                    int64_t ldv, int nc, const T* __restrict__ w,
-                                                    double* __restrict__ part, GmState* st,
-                                                    int with_norm) {
+__global__ void __launch_bounds__(kBlock, 4) k_gm_dots(int64_t n, const T* __restrict__ V,
+                                                       int64_t ldv, int nc,
+                                                       const T* __restrict__ w,
+                                                       double* __restrict__ part, GmState* st,
+                                                       int with_norm) {
   if (*(volatile int*)&st->halt) return;
   if (!with_norm && *(volatile int*)&st->skip2) return;
-  __shared__ double red[9 * kBlock + 9];
-  for (int c0 = 0; c0 < nc; c0 += 8) {
-    const int r = nc - c0 < 8 ? nc - c0 : 8;
+  __shared__ double red[(kGmGroup + 1) * kBlock + kGmGroup + 1];
+  for (int c0 = 0; c0 < nc; c0 += kGmGroup) {
+    const int r = nc - c0 < kGmGroup ? nc - c0 : kGmGroup;
     if (with_norm && c0 == 0) gm_dots_rest<T, true>(r, n, V, ldv, c0, nc, w, part, red);
     else gm_dots_rest<T, false>(r, n, V, ldv, c0, nc, w, part, red);
   }
@@ -939,7 +939,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
   CP_CUDA(cudaMemsetAsync(st, 0, sizeof(GmState), s));
   const double tol2 = tol * tol;
   const int G = grid_n(ctx, n);
-  // the multi-dot kernel keeps up to nine accumulators a thread: its grid is
+  // the multi-dot kernel keeps several accumulators a thread: its grid is
   // what stays resident (more blocks would only queue in waves)
   int Gd = G;
   {
