@@ -32,6 +32,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Arrival and polling with release / acquire semantics at GPU scope: the
+// block's writes (ordered before thread 0 by the preceding __syncthreads) are
+// published by the release; the acquire makes the other blocks' writes visible
+// before the block's next reads (which go through L2).
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 // Grid-wide barrier with a time limit.  target: the arrival count that ends
 // this barrier (the block's running count of barriers times the grid size).
 // Returns false (in every thread of the block) when the wait gave up or
@@ -41,14 +54,12 @@ __device__ __forceinline__ bool grid_barrier(CgState* st, unsigned target,
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* cnt = &st->bar_count;
     volatile int* err = &st->bar_err;
-    __threadfence();  // this block's writes before its arrival
-    atomicAdd(&st->bar_count, 1u);
+    red_add_release(&st->bar_count, 1u);
     int good = 1;
-    if ((int)(*cnt - target) < 0) {
+    if ((int)(ld_acquire(&st->bar_count) - target) < 0) {
       const unsigned long long t0 = global_ns();
-      while ((int)(*cnt - target) < 0) {
+      while ((int)(ld_acquire(&st->bar_count) - target) < 0) {
         if (*err) {
           good = 0;
           break;
@@ -60,7 +71,6 @@ __device__ __forceinline__ bool grid_barrier(CgState* st, unsigned target,
         }
       }
     }
-    __threadfence();  // the other blocks' writes before this block's reads
     ok = good && !*err;
   }
   __syncthreads();
