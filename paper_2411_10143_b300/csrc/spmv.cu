@@ -220,58 +220,21 @@ __global__ void __launch_bounds__(kBlock) k_dia(
   write_partial<DOT>((double)acc, partials);
 }
 
-// ------------------------------------------------------------------ COO (tiled segmented sums)
-// A block takes a tile of kCooTile consecutive entries (sorted by row); each
-// thread loads its kCooItems consecutive entries into registers (the lanes of
-// a warp read adjacent runs, so the seven loads share their cache lines),
-// gathers x for all of them, and sums them row by row in a fully unrolled walk
-// (one FMA per entry).  A row inside one thread's entries is written
-// directly.  A row that spans threads is completed by the thread that holds
-// its last entry, which adds the partials of the preceding threads' last
-// segments from shared memory.  A row that touches the tile's first or last
-// entry may have entries in another tile and is added with an atomic.  ADD: y
-// already holds the rest of the row (beta*y, or HYB's ELL part) and every
-// write adds to it; otherwise y is zero and a row completed in one place is
-// stored.
+// ------------------------------------------------------------------ COO (warp-tiled segmented sums)
+// Each warp takes kCooWarpTile consecutive entries (sorted by row), loads them
+// coalesced into its slice of shared memory, and each lane takes its kCooItems
+// consecutive entries into registers, gathers x for all of them and sums them
+// row by row in a fully unrolled walk (one FMA per entry).
+// A row inside one lane's entries is written directly.  Rows that span lanes
+// are combined with a segmented shuffle scan over the lanes' last segments;
+// the lane that holds a row's last entry in the warp writes it, with an atomic
+// if the row touches the warp's first or last entry (other warps may hold
+// entries of it).  No shared memory and no block barrier: long rows cost the
+// same per entry as short ones.  ADD: y already holds the rest of the row
+// (beta*y, or HYB's ELL part) and every write adds to it; otherwise y is zero
+// and a row completed in one place is stored.
 constexpr int kCooItems = 7;
-constexpr int kCooTile = kBlock * kCooItems;
-
-constexpr int kCooChain = 4;  // threads walked back serially before the scan takes over
-
-// Segmented inclusive scan of the thread partials part[] in thread order, a
-// run (segment) starting at a thread whose last segment began inside it
-// (multi) or whose last row differs from the previous thread's: the result in
-// thread t is the sum of part[] from the start of t's run to t.  A shuffle scan
-// inside each warp, then the runs that cross warp boundaries take the carry of
-// the preceding warps (at most blockDim.x / 32 steps).  Every thread calls it.
-template <typename T>
-__device__ __forceinline__ T coo_run_scan(const int32_t* last, const T* part, const int8_t* multi,
-                                          T* wsum, int8_t* whead) {
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  T v = part[t];
-  bool f = t == 0 || multi[t] || last[t - 1] != last[t];  // a run starts here
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const T up = __shfl_up_sync(0xffffffffu, v, o);
-    const bool fup = __shfl_up_sync(0xffffffffu, (int)f, o) != 0;
-    if (lane >= o) {
-      if (!f) v += up;
-      f = f || fup;
-    }
-  }
-  if (lane == 31) {
-    wsum[w] = v;
-    whead[w] = f;
-  }
-  __syncthreads();
-  if (!f) {  // the run began before this warp: add the preceding warps' tails
-    for (int q = w - 1; q >= 0; --q) {
-      v += wsum[q];
-      if (whead[q]) break;
-    }
-  }
-  return v;
-}
+constexpr int kCooWarpTile = 32 * kCooItems;
 
 template <typename T, bool ADD>
 __device__ __forceinline__ void coo_put(T* y, int32_t r, T alpha, T s) {
@@ -284,29 +247,40 @@ __global__ void __launch_bounds__(kBlock) k_coo(
     const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, T alpha,
     const int* __restrict__ skip) {
   if (skip && *skip) return;
-  __shared__ int32_t s_first[kBlock + 1];  // row of each thread's first entry (-1: none)
-  __shared__ int32_t s_last[kBlock];       // row of each thread's last segment
-  __shared__ T s_part[kBlock];             // that segment's partial sum
-  __shared__ int8_t s_multi[kBlock];       // the thread's entries span more than one row
-  __shared__ T s_scan[kBlock];             // segmented scan of the partials (long runs)
-  __shared__ T s_wsum[kBlock / 32];
-  __shared__ int8_t s_whead[kBlock / 32];
-  const int64_t ntiles = (nnz + kCooTile - 1) / kCooTile;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t e0 = t * kCooTile;
-    const int cnt = (int)(nnz - e0 < kCooTile ? nnz - e0 : kCooTile);
-    const int j0 = threadIdx.x * kCooItems;
+  // the warp's tile passes through shared memory: coalesced loads in, then each
+  // lane reads its consecutive entries (a stride of 7 words, or 14 for FP64,
+  // maps every 16-lane phase onto distinct banks)
+  __shared__ int32_t s_r[kBlock / 32][kCooWarpTile];
+  __shared__ int32_t s_c[kBlock / 32][kCooWarpTile];
+  __shared__ T s_v[kBlock / 32][kCooWarpTile];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t ntiles = (nnz + kCooWarpTile - 1) / kCooWarpTile;
+  for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles;
+       t += nwarps) {
+    const int64_t e0 = t * kCooWarpTile;
+    const int cnt = (int)(nnz - e0 < kCooWarpTile ? nnz - e0 : kCooWarpTile);
+    const int j0 = lane * kCooItems;
     const int mine = cnt - j0 < 0 ? 0 : (cnt - j0 < kCooItems ? cnt - j0 : kCooItems);
-    const int64_t b = e0 + j0;
+    __syncwarp();  // the previous tile's reads of the slice are done
+#pragma unroll
+    for (int u = 0; u < kCooItems; ++u) {
+      const int k = u * 32 + lane;
+      if (k < cnt) {
+        s_r[wib][k] = ld_stream(row + e0 + k);
+        s_c[wib][k] = ld_stream(col + e0 + k);
+        s_v[wib][k] = ld_stream(val + e0 + k);
+      }
+    }
+    __syncwarp();
     int32_t r[kCooItems], c[kCooItems];
     T w[kCooItems], xv[kCooItems];
 #pragma unroll
     for (int u = 0; u < kCooItems; ++u) {
       const bool in = u < mine;
-      // cached loads: the seven loads of a warp read the same lines in turn
-      r[u] = in ? ld_ro(row + b + u) : -1;
-      c[u] = in ? ld_ro(col + b + u) : 0;
-      w[u] = in ? ld_ro(val + b + u) : T(0);
+      r[u] = in ? s_r[wib][j0 + u] : -1;
+      c[u] = in ? s_c[wib][j0 + u] : 0;
+      w[u] = in ? s_v[wib][j0 + u] : T(0);
     }
 #pragma unroll
     for (int u = 0; u < kCooItems; ++u) xv[u] = u < mine ? ld_ro(x + c[u]) : T(0);
@@ -319,7 +293,7 @@ __global__ void __launch_bounds__(kBlock) k_coo(
       if (u < mine) {
         if (u > 0 && r[u] != cur) {
           if (!multi) head = sum;  // the first segment closes
-          else coo_put<T, ADD>(y, cur, alpha, sum);  // a row inside this thread only
+          else coo_put<T, ADD>(y, cur, alpha, sum);  // a row inside this lane only
           multi = true;
           cur = r[u];
           sum = 0;
@@ -327,57 +301,37 @@ __global__ void __launch_bounds__(kBlock) k_coo(
         sum = fma(w[u], xv[u], sum);
       }
     }
-    s_first[threadIdx.x] = first;
-    s_last[threadIdx.x] = cur;
-    s_part[threadIdx.x] = sum;
-    s_multi[threadIdx.x] = multi;
-    if (threadIdx.x == 0) s_first[kBlock] = -1;
-    __syncthreads();
-    const int32_t tile_row0 = s_first[0];
-    const bool last_in_tile = mine > 0 && j0 + mine == cnt;
-    const bool ends_here = mine > 0 && (last_in_tile || s_first[threadIdx.x + 1] != cur);
-    // Sums of the runs of thread partials that complete a row here: the first
-    // row's (for a thread whose entries span rows) and the last row's.  Short
-    // runs are walked (at most kCooChain threads back); if any run is longer
-    // (rows of hundreds of entries), the whole block takes a segmented scan.
-    T head_cs = head, tail_cs = 0;
-    bool long_run = false;
-    if (multi) {
-      int j = (int)threadIdx.x - 1, k = 0;
-      for (; j >= 0 && s_last[j] == first && k < kCooChain; --j, ++k) {
-        head_cs += s_part[j];
-        if (s_multi[j]) break;  // the row started in thread j
+    // segmented inclusive scan of the lanes' last segments: a run starts at a
+    // lane whose last segment began inside it (multi), or whose last row
+    // differs from the previous lane's
+    const int32_t prev_cur = __shfl_up_sync(0xffffffffu, cur, 1);
+    T v = sum;
+    bool f = lane == 0 || multi || prev_cur != cur;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T up = __shfl_up_sync(0xffffffffu, v, o);
+      const bool fup = __shfl_up_sync(0xffffffffu, (int)f, o) != 0;
+      if (lane >= o) {
+        if (!f) v += up;
+        f = f || fup;
       }
-      long_run |= j >= 0 && k == kCooChain && s_last[j] == first;
     }
-    if (ends_here) {
-      int j = (int)threadIdx.x, k = 0;
-      for (; j >= 0 && s_last[j] == cur && k < kCooChain; --j, ++k) {
-        tail_cs += s_part[j];
-        if (s_multi[j]) break;
-      }
-      long_run |= j >= 0 && k == kCooChain && s_last[j] == cur;
-    }
-    if (__syncthreads_or(long_run)) {
-      const T scan = coo_run_scan(s_last, s_part, s_multi, s_wsum, s_whead);
-      s_scan[threadIdx.x] = scan;
-      __syncthreads();
-      if (multi)
-        head_cs = head + (threadIdx.x > 0 && s_last[threadIdx.x - 1] == first
-                              ? s_scan[threadIdx.x - 1] : T(0));
-      tail_cs = scan;
-    }
+    const T v_prev = __shfl_up_sync(0xffffffffu, v, 1);
+    const int32_t next_first = __shfl_down_sync(0xffffffffu, first, 1);
+    const int32_t warp_row0 = __shfl_sync(0xffffffffu, first, 0);
+    const bool last_in_warp = mine > 0 && j0 + mine == cnt;
     if (multi) {
-      if (tile_row0 == first) atomicAdd(y + first, alpha * head_cs);  // may continue from the last tile
-      else coo_put<T, ADD>(y, first, alpha, head_cs);
+      // the first row ends in this lane: add the run of preceding lanes' last
+      // segments with that row (the scan value of the previous lane)
+      const T cs = head + (lane > 0 && prev_cur == first ? v_prev : T(0));
+      if (warp_row0 == first) atomicAdd(y + first, alpha * cs);  // may start in an earlier warp
+      else coo_put<T, ADD>(y, first, alpha, cs);
     }
-    if (ends_here) {
-      // atomically if the row touches the tile's first or last entry (other
-      // tiles may hold entries of it)
-      if (last_in_tile || tile_row0 == cur) atomicAdd(y + cur, alpha * tail_cs);
-      else coo_put<T, ADD>(y, cur, alpha, tail_cs);
+    if (mine > 0 && (last_in_warp || next_first != cur)) {
+      // this lane holds the last entry in the warp of its last row
+      if (last_in_warp || warp_row0 == cur) atomicAdd(y + cur, alpha * v);
+      else coo_put<T, ADD>(y, cur, alpha, v);
     }
-    __syncthreads();
   }
 }
 
@@ -491,7 +445,7 @@ void spmv_set_attributes() {
 }
 
 static int coo_grid(cp_ctx* ctx, int64_t nnz) {
-  const int64_t tiles = (nnz + kCooTile - 1) / kCooTile;
+  const int64_t tiles = (nnz + kCooWarpTile * (kBlock / 32) - 1) / (kCooWarpTile * (kBlock / 32));
   return (int)(tiles < 1 ? 1 : tiles < ctx->grid_stream ? tiles : ctx->grid_stream);
 }
 
