@@ -165,8 +165,8 @@ def cg_iteration_bytes(A, fmt):
 # profiles/k_cg_persist_dia_poisson3d_128.md.
 PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
 PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
-                   "sha256": "6df0ca3c14935047f0c135fa62eb1ec562c4c145caa9cfe68c8d45d2b65b513e",
-                   "dram_bytes_per_iteration": 158165489.1}
+                   "sha256": "bdda7387bcf823443d79014d5ea40143fd28684efb5fced4a7e7f077eb17a30d",
+                   "dram_bytes_per_iteration": 158400446.4}
 
 
 def persist_sources_sha256():

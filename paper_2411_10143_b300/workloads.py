@@ -328,13 +328,15 @@ def training_suite(seed: int = 77, count: int = 240):
 
     Families: 2D/3D stencils, power law with several exponents and means,
     uniform random, banded with several widths and fills, block-dense rows;
-    sizes log-uniform between 2^12 and 2^21 rows.  Yields (name, builder).
+    sizes log-uniform between 2^12 and 2^22 rows, so that the sizes the solver
+    meets (up to about 2^21) lie inside the range rather than at its edge.
+    Yields (name, builder).
     """
     rng = np.random.default_rng(seed)
     out = []
     for i in range(count):
         fam = i % 6
-        n = int(2 ** rng.uniform(12, 21))
+        n = int(2 ** rng.uniform(12, 22))
         s = int(rng.integers(0, 2**31 - 1))
         if fam == 0:
             N = max(8, int(round(n ** 0.5)))
