@@ -288,6 +288,9 @@ typedef struct {
                             falling back to one launch per step otherwise; 1 = always
                             one launch per step                                       */
   const cp_config* force;/* non-NULL: use this configuration from the first iteration    */
+  double wait_limit_ms;  /* bound of every device-side wait of the persistent kernel (its
+                            grid barriers); a wait that exceeds it ends the solve with
+                            CP_ERR_TIMEOUT and the context stays usable.  0: 2000 ms    */
 } cp_solve_opts;
 
 typedef struct {
@@ -311,6 +314,9 @@ typedef struct {
                               the FORMAT stage, 2 before the feature pass (two-tier)      */
   float gate_remaining;    /* its estimate of the iterations left when it decided (-1: none) */
   float gate_cost_spmvs;   /* its estimate of the conversion cost, in default-kernel SpMVs */
+  int32_t side_status;     /* the prediction side's first error (CP_OK if none): the solve
+                              carries on with the configuration it has (the default CSR
+                              kernel at worst) and still returns its own status          */
 } cp_solve_info;
 
 void cp_solve_opts_default(cp_solve_opts* opts);
@@ -343,6 +349,14 @@ typedef struct {
   int64_t small_rows;                 /* two-tier features below this many rows          */
   int32_t enabled;                    /* 0: always switch (the paper's behaviour)        */
 } cp_gate;
+
+/* Fault injection on the host, for tests of the asynchronous mode's recovery:
+ * the next solve's prediction side thread raises an error at `point` (0: before
+ * the feature pass, 1: after it, 2: after the FORMAT stage, before any
+ * conversion; -1 cancels a pending injection).  One-shot.  Nothing runs on or
+ * waits for the GPU differently; the solve must finish on the default kernel
+ * and report the error in cp_solve_info.side_status. */
+cp_status cp_inject_side_failure(cp_ctx* ctx, int32_t point);
 
 /* Two-tier features (also an extension; Sec. II-B quotes Swann et al.: below
  * 100,000 rows, extracting the features costs more than one SpMV).  For a

@@ -73,7 +73,7 @@ class SolveOpts(Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("restart", c_int32), ("mode", c_int32),
                 ("precision", c_int32), ("inner_tol", c_double), ("max_outer", c_int32),
                 ("check_every", c_int32), ("profile", c_int32), ("iteration_kernel", c_int32),
-                ("force", POINTER(Config))]
+                ("force", POINTER(Config)), ("wait_limit_ms", c_double)]
 
 
 class SolveInfo(Structure):
@@ -84,7 +84,8 @@ class SolveInfo(Structure):
                 ("t_total_ms", c_float), ("t_spmv_ms", c_float), ("t_persist_ms", c_float),
                 ("persist_iters", c_int32), ("t_persist_last_ms", c_float),
                 ("persist_last_iters", c_int32), ("gate_declined", c_int32),
-                ("gate_remaining", c_float), ("gate_cost_spmvs", c_float)]
+                ("gate_remaining", c_float), ("gate_cost_spmvs", c_float),
+                ("side_status", c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, outer_iters=self.outer_iters,
@@ -97,7 +98,7 @@ class SolveInfo(Structure):
                     persist_iters=self.persist_iters, t_persist_last_ms=self.t_persist_last_ms,
                     persist_last_iters=self.persist_last_iters,
                     gate_declined=self.gate_declined, gate_remaining=self.gate_remaining,
-                    gate_cost_spmvs=self.gate_cost_spmvs)
+                    gate_cost_spmvs=self.gate_cost_spmvs, side_status=self.side_status)
 
 
 class Gate(Structure):
@@ -184,6 +185,7 @@ _SIGS = {
     "cp_batch_solve": (c_int32, [_p, c_int32, _p, _p, _p, _p, POINTER(SolveOpts), c_int32,
                                  _p]),
     "cp_gate_set": (c_int32, [_p, _p]),
+    "cp_inject_side_failure": (c_int32, [_p, c_int32]),
     "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
                                  POINTER(c_double), POINTER(c_double)]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
@@ -415,6 +417,10 @@ class Context:
             _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
                                        _ptr(ms)))
         return best.value, ms.tolist()
+
+    def inject_side_failure(self, point):
+        """cp_inject_side_failure (tests): the next solve's side thread fails at point."""
+        _check(lib().cp_inject_side_failure(self._h, int(point)))
 
     def gate_set(self, gate: "Gate"):
         """cp_gate_set: install (gate.enabled = 1) or disable the cost-aware switch."""

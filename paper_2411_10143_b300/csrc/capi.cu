@@ -90,6 +90,7 @@ void cp_solve_opts_default(cp_solve_opts* o) {
   o->check_every = 8;
   o->profile = 0;
   o->force = nullptr;
+  o->wait_limit_ms = 0.0;
 }
 
 const char* cp_last_error(void) { return g_err; }
@@ -378,6 +379,13 @@ cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const i
     CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
     use_device(ctx);
     batch_solve(ctx, nsys, mats, solver, b, x, opts, infos, threads);
+  });
+}
+
+cp_status cp_inject_side_failure(cp_ctx* ctx, int32_t point) {
+  return guard([&] {
+    CP_REQUIRE(ctx && point >= -1 && point <= 2, CP_ERR_INVALID, "bad injection point %d", point);
+    ctx->inject_side_fail.store(point);
   });
 }
 

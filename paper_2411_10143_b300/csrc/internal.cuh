@@ -165,6 +165,7 @@ struct cp_ctx {
   void* pin_main = nullptr;
   void* pin_side = nullptr;
   cp_gate gate{};  // cost-aware switching (disabled until installed)
+  std::atomic<int> inject_side_fail{-1};  // host fault injection point (tests), -1: none
   cp::SideWorker* side_worker = nullptr;
 };
 

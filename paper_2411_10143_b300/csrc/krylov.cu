@@ -692,6 +692,7 @@ struct ConfigSource {
   std::vector<cudaEvent_t> ev;
   int n_spmv = 0;
   bool persistent = true;     // run CG iterations in the persistent kernel when it supports cfg
+  double wait_limit_ms = 0.0; // bound of the persistent kernel's device waits (0: default)
   float t_persist_ms = 0.f;   // summed duration of the persistent launches
   int persist_iters = 0;      // iterations they ran
   float t_persist_last_ms = 0.f;
@@ -832,6 +833,8 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         pa_args.it0 = it;
         pa_args.itmax = maxit;
         pa_args.tol2 = tol2;
+        if (cs.wait_limit_ms > 0.0)
+          pa_args.barrier_timeout_ns = (long long)(cs.wait_limit_ms * 1e6);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
         CP_CUDA(cudaEventCreate(&e0));
         CP_CUDA(cudaEventCreate(&e1));
@@ -1120,6 +1123,8 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
   cs.fp32 = fp32;
   cs.profile = opt.profile != 0;
   cs.persistent = opt.iteration_kernel == 0;
+  CP_REQUIRE(opt.wait_limit_ms >= 0.0, CP_ERR_INVALID, "wait_limit_ms must be >= 0");
+  cs.wait_limit_ms = opt.wait_limit_ms;
   cp_config_default(&cs.cur);
   if (opt.force) cs.cur = *opt.force;
   ensure_format(ctx, m, cs.cur, ctx->main);
@@ -1191,6 +1196,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     info->gate_declined = ch.gate_declined;
     info->gate_remaining = ch.gate_remaining;
     info->gate_cost_spmvs = ch.gate_cost;
+    info->side_status = ch.status;
     info->n_launches = (int32_t)(ctx->launches.load() - launches0);
     info->status = res.status;
   }

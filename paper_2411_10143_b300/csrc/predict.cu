@@ -549,6 +549,13 @@ static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
   return false;
 }
 
+// Host fault injection (cp_inject_side_failure): one-shot, at `point`.
+static void maybe_fail(cp_ctx* ctx, int point) {
+  int want = point;
+  if (ctx->inject_side_fail.compare_exchange_strong(want, -1))
+    throw Error{CP_ERR_CUDA};  // as a failing CUDA call would
+}
+
 void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
   struct Finish {  // tell the solve loop the side work has ended, however it ends
     Channel* c;
@@ -566,11 +573,13 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
       // only if the best case over the formats can pay for it
       if (!gate_pass(ctx, m, ch, -1, 2)) return;
     }
+    maybe_fail(ctx, 0);
     auto t = Clock::now();
     double f[kFeat];
     compute_features(ctx, m, s, f);  // Table IV, on the side stream
     ch->t_features_ms = ms(t);
     if (ch->cancel.load()) return;
+    maybe_fail(ctx, 1);
 
     cp_config cfg;
     cp_config_default(&cfg);
@@ -588,6 +597,7 @@ void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch) {
     ch->t_predict_ms[0] = ms(t);
     trace("cascade: FORMAT -> %d", next.fmt);
     if (ch->cancel.load()) return;
+    maybe_fail(ctx, 2);
     if (next.fmt != cfg.fmt && ctx->gate.enabled && ch->tol > 0.0) {
       // cost-aware switching: convert only if the saving over the iterations
       // left pays for the conversion.  The gate waits at most 5 ms for two

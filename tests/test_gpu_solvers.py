@@ -306,3 +306,39 @@ def test_two_tier_features_skip_the_feature_pass_on_a_short_small_solve():
     assert info.final_cfg.fmt == C.FMT_CSR and max(info.switch_iter) == -1
     assert info.gate_cost_spmvs == pytest.approx((20.0 + 5.0) / 0.05)
     c.close()
+
+
+def test_bounded_device_wait_times_out_cleanly():
+    """The persistent kernel's grid barrier gives up after wait_limit_ms.  With a
+    limit of one nanosecond its first wait runs out: every block leaves at its
+    next barrier, the solve ends with CP_ERR_TIMEOUT (no fault, no hang), and the
+    same context then solves normally."""
+    c = C.Context(0)
+    A = W.poisson3d(24)
+    b = rhs(A, 44)
+    x, info = gpu_solve(c, A, b, tol=1e-10, force=C.config("DIA"), raise_on_error=False,
+                        wait_limit_ms=1e-6)
+    assert info.status == C.ERR_TIMEOUT and info.persist_iters == 0
+    x, info = gpu_solve(c, A, b, tol=1e-10, force=C.config("DIA"))
+    assert info.status == 0 and true_relres(A, x, b) <= 1e-10
+    c.close()
+
+
+@pytest.mark.parametrize("point", [0, 1, 2])
+def test_prediction_side_failure_leaves_the_solve_on_the_default_kernel(point):
+    """Fault injected on the host: the side thread fails before the feature pass,
+    after it, or after the FORMAT stage.  The asynchronous solve carries on with
+    CSR-scalar, converges, and reports the side's error."""
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    A = W.poisson2d(256)
+    b = rhs(A, 45 + point)
+    c.inject_side_failure(point)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert info.status == 0 and true_relres(A, x, b) <= 1e-10
+    assert info.side_status == C.ERR_CUDA
+    assert info.final_cfg.fmt == C.FMT_CSR and max(info.switch_iter) == -1
+    # one-shot: the next solve predicts and switches as usual
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert info.side_status == 0 and info.final_cfg.fmt == C.FMT_ELL
+    c.close()
