@@ -282,15 +282,19 @@ typedef struct {
   int32_t max_outer;     /* FP32_IR: refinement steps limit                               */
   int32_t check_every;   /* iterations between host convergence checks (0: default 8)   */
   int32_t profile;       /* 1: time every SpMV launch with CUDA events (t_spmv_ms)        */
-  int32_t iteration_kernel; /* CG: 0 = one persistent cooperative launch runs the
-                            iterations while the format has a row-parallel kernel (CSR
-                            scalar / vector, ELL, SELL, DIA, HYB without COO part),
+  int32_t iteration_kernel; /* CG and GMRES: 0 = one persistent cooperative launch runs
+                            the iterations while the format has a row-parallel kernel
+                            (CSR scalar / vector, ELL, SELL, DIA, HYB without COO part)
+                            and no prediction work is pending on the side stream,
                             falling back to one launch per step otherwise; 1 = always
                             one launch per step                                       */
   const cp_config* force;/* non-NULL: use this configuration from the first iteration    */
   double wait_limit_ms;  /* bound of every device-side wait of the persistent kernel (its
                             grid barriers); a wait that exceeds it ends the solve with
                             CP_ERR_TIMEOUT and the context stays usable.  0: 2000 ms    */
+  int32_t persist_chunk; /* > 0: a persistent launch returns to the host after this many
+                            iterations (the host launches again to go on), e.g. to poll
+                            for cancellation; 0: it runs to the end of the solve      */
 } cp_solve_opts;
 
 typedef struct {
@@ -306,7 +310,7 @@ typedef struct {
   float t_features_ms, t_predict_ms[3], t_convert_ms; /* side-stream step times           */
   float t_total_ms;        /* wall time from entry to x ready                             */
   float t_spmv_ms;         /* summed SpMV kernel time when profile = 1                    */
-  float t_persist_ms;      /* summed duration of the persistent CG launches               */
+  float t_persist_ms;      /* summed duration of the persistent (CG or GMRES) launches    */
   int32_t persist_iters;   /* iterations those launches ran                               */
   float t_persist_last_ms; /* duration of the last persistent launch (final configuration) */
   int32_t persist_last_iters; /* iterations it ran                                        */
@@ -317,6 +321,7 @@ typedef struct {
   int32_t side_status;     /* the prediction side's first error (CP_OK if none): the solve
                               carries on with the configuration it has (the default CSR
                               kernel at worst) and still returns its own status          */
+  int32_t persist_launches; /* persistent launches the solve made                           */
 } cp_solve_info;
 
 void cp_solve_opts_default(cp_solve_opts* opts);

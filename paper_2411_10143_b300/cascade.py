@@ -73,7 +73,8 @@ class SolveOpts(Structure):
     _fields_ = [("tol", c_double), ("maxit", c_int32), ("restart", c_int32), ("mode", c_int32),
                 ("precision", c_int32), ("inner_tol", c_double), ("max_outer", c_int32),
                 ("check_every", c_int32), ("profile", c_int32), ("iteration_kernel", c_int32),
-                ("force", POINTER(Config)), ("wait_limit_ms", c_double)]
+                ("force", POINTER(Config)), ("wait_limit_ms", c_double),
+                ("persist_chunk", c_int32)]
 
 
 class SolveInfo(Structure):
@@ -85,7 +86,7 @@ class SolveInfo(Structure):
                 ("persist_iters", c_int32), ("t_persist_last_ms", c_float),
                 ("persist_last_iters", c_int32), ("gate_declined", c_int32),
                 ("gate_remaining", c_float), ("gate_cost_spmvs", c_float),
-                ("side_status", c_int32)]
+                ("side_status", c_int32), ("persist_launches", c_int32)]
 
     def as_dict(self):
         return dict(iters=self.iters, outer_iters=self.outer_iters,
@@ -98,7 +99,8 @@ class SolveInfo(Structure):
                     persist_iters=self.persist_iters, t_persist_last_ms=self.t_persist_last_ms,
                     persist_last_iters=self.persist_last_iters,
                     gate_declined=self.gate_declined, gate_remaining=self.gate_remaining,
-                    gate_cost_spmvs=self.gate_cost_spmvs, side_status=self.side_status)
+                    gate_cost_spmvs=self.gate_cost_spmvs, side_status=self.side_status,
+                    persist_launches=self.persist_launches)
 
 
 class Gate(Structure):

@@ -24,12 +24,16 @@ void set_error(const char* fmt, ...) {
   va_end(ap);
 }
 
-void trace(const char* fmt, ...) {
+bool trace_on() {
   static const bool on = [] {
     const char* e = std::getenv("CASCADE_TRACE");
     return e && e[0] == '1';
   }();
-  if (!on) return;
+  return on;
+}
+
+void trace(const char* fmt, ...) {
+  if (!trace_on()) return;
   static const auto t0 = std::chrono::steady_clock::now();
   const double ms =
       std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -91,6 +95,7 @@ void cp_solve_opts_default(cp_solve_opts* o) {
   o->profile = 0;
   o->force = nullptr;
   o->wait_limit_ms = 0.0;
+  o->persist_chunk = 0;
 }
 
 const char* cp_last_error(void) { return g_err; }

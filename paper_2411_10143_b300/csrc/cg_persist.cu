@@ -26,78 +26,6 @@
 
 namespace cp {
 
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Arrival and polling with release / acquire semantics at GPU scope: the
-// block's writes (ordered before thread 0 by the preceding __syncthreads) are
-// published by the release; the acquire makes the other blocks' writes visible
-// before the block's next reads (which go through L2).
-__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid-wide barrier with a time limit.  target: the arrival count that ends
-// this barrier (the block's running count of barriers times the grid size).
-// Returns false (in every thread of the block) when the wait gave up or
-// another block already did.
-__device__ __forceinline__ bool grid_barrier(CgState* st, unsigned target,
-                                             long long timeout_ns) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile int* err = &st->bar_err;
-    red_add_release(&st->bar_count, 1u);
-    int good = 1;
-    if ((int)(ld_acquire(&st->bar_count) - target) < 0) {
-      const unsigned long long t0 = global_ns();
-      while ((int)(ld_acquire(&st->bar_count) - target) < 0) {
-        if (*err) {
-          good = 0;
-          break;
-        }
-        if ((long long)(global_ns() - t0) > timeout_ns) {
-          atomicExch(&st->bar_err, 1);
-          good = 0;
-          break;
-        }
-      }
-    }
-    ok = good && !*err;
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-template <typename T, int F, int TPV>
-__device__ __forceinline__ T spmv_phase(const PersistArgs<T>& a, const int32_t* so) {
-  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  if constexpr (F == kPersistCsrScalar)
-    return csr_scalar_rows<T, false, true, true>(a.n, a.rp, a.ci, a.v, a.p, a.ap, T(1), T(0), a.p, tid,
-                                           stride);
-  else if constexpr (F == kPersistCsrVector)
-    return csr_vector_rows<T, TPV, false, true, true>(a.n, a.rp, a.ci, a.v, a.p, a.ap, T(1), T(0), a.p,
-                                                tid >> 5, stride >> 5);
-  else if constexpr (F == kPersistEll)
-    return ell_rows<T, false, true, true>(a.n, a.K, a.ld, a.ec, a.ev, a.p, a.ap, T(1), T(0), a.p, tid,
-                                    stride);
-  else if constexpr (F == kPersistSell)
-    return sell_chunks<T, false, true, true>(a.n, a.nchunks, a.perm, a.clen, a.cptr, a.sc, a.sv, a.p,
-                                       a.ap, T(1), T(0), a.p, tid >> 5, stride >> 5);
-  else
-    return dia_rows<T, false, true, true>(a.n, a.n, a.ndiag, so, a.dv, a.p, a.ap, T(1), T(0), a.p, tid,
-                                    stride);
-}
-
 // Pairs handled per thread per trip of the vector loops: all of a trip's
 // loads are issued before its stores.
 constexpr int kPersistU = 1;
@@ -138,13 +66,13 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
     const int slot = it & 1;
     // ---- phase 1: Ap = A p, partials of (p, Ap)
     {
-      const T acc = spmv_phase<T, F, TPV>(a, so);
+      const T acc = persist_spmv<T, F, TPV, false, true>(a, so, a.p, a.ap, T(1), T(0), a.p);
       const double s = block_sum_lean((double)acc, red);
       if (threadIdx.x == 0) a.pa[blockIdx.x] = s;
     }
     lap(0);
     bar_target += gridDim.x;
-    if (!grid_barrier(st, bar_target, a.barrier_timeout_ns)) break;
+    if (!grid_barrier(&st->bar_count, &st->bar_err, bar_target, a.barrier_timeout_ns)) break;
     lap(1);
     // ---- phase 2: alpha; r -= alpha Ap; partials of (r, r)
     if (threadIdx.x < 32) {
@@ -208,7 +136,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
     }
     lap(2);
     bar_target += gridDim.x;
-    if (!grid_barrier(st, bar_target, a.barrier_timeout_ns)) break;
+    if (!grid_barrier(&st->bar_count, &st->bar_err, bar_target, a.barrier_timeout_ns)) break;
     lap(3);
     // ---- phase 3: beta; convergence; x += alpha p; p = r + beta p
     if (threadIdx.x < 32) {
@@ -299,7 +227,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
     if (stop) break;  // every block read the same value after the last barrier
     lap(4);
     bar_target += gridDim.x;
-    if (!grid_barrier(st, bar_target, a.barrier_timeout_ns)) break;
+    if (!grid_barrier(&st->bar_count, &st->bar_err, bar_target, a.barrier_timeout_ns)) break;
     lap(5);
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && *(volatile int*)&st->bar_err) {
@@ -331,60 +259,15 @@ static void launch_one(cp_ctx* ctx, PersistArgs<T>& a, cudaStream_t s, int share
 
 template <typename T>
 bool persist_supported(const cp_mat* m, const cp_config& c) {
-  if (c.fmt == CP_FMT_CSR) return c.algo == CP_ALGO_SCALAR || c.algo == CP_ALGO_VECTOR;
-  if (c.fmt == CP_FMT_HYB) return m->hyb_coo.n == 0;  // HYB without a COO part is ELL
-  return c.fmt == CP_FMT_ELL || c.fmt == CP_FMT_SELL || c.fmt == CP_FMT_DIA;
+  return persist_format_ok(m, c);
 }
 
 template <typename T>
 void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a,
                     cudaStream_t s, int share) {
-  a.n = m->nrows;
-  switch (c.fmt) {
-    case CP_FMT_CSR:
-      a.rp = m->rowptr;
-      a.ci = m->col;
-      a.v = PersistVals<T>::csr(m);
-      if (c.algo == CP_ALGO_SCALAR) {
-        launch_one<T, kPersistCsrScalar, 1>(ctx, a, s, share);
-      } else {
-        switch (c.tpv) {
-          case 2: launch_one<T, kPersistCsrVector, 2>(ctx, a, s, share); break;
-          case 4: launch_one<T, kPersistCsrVector, 4>(ctx, a, s, share); break;
-          case 8: launch_one<T, kPersistCsrVector, 8>(ctx, a, s, share); break;
-          case 16: launch_one<T, kPersistCsrVector, 16>(ctx, a, s, share); break;
-          default: launch_one<T, kPersistCsrVector, 32>(ctx, a, s, share); break;
-        }
-      }
-      break;
-    case CP_FMT_ELL:
-    case CP_FMT_HYB: {
-      const EllPart& e = c.fmt == CP_FMT_ELL ? m->ell : m->hyb_ell;
-      a.K = e.K;
-      a.ld = e.ld;
-      a.ec = e.col;
-      a.ev = PersistVals<T>::ell(e);
-      launch_one<T, kPersistEll, 1>(ctx, a, s, share);
-      break;
-    }
-    case CP_FMT_SELL:
-      a.nchunks = m->sell.nchunks;
-      a.perm = m->sell.sigma > 1 ? m->sell.perm : nullptr;
-      a.clen = m->sell.chunk_len;
-      a.cptr = m->sell.chunk_ptr;
-      a.sc = m->sell.col;
-      a.sv = PersistVals<T>::sell(m->sell);
-      launch_one<T, kPersistSell, 1>(ctx, a, s, share);
-      break;
-    case CP_FMT_DIA:
-      a.ndiag = (int)m->dia.ndiag;
-      a.offs = m->dia.offs;
-      a.dv = PersistVals<T>::dia(m->dia);
-      launch_one<T, kPersistDia, 1>(ctx, a, s, share);
-      break;
-    default:
-      CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent CG kernel for format %d", c.fmt);
-  }
+  persist_dispatch<T>(m, c, a, [&](auto f, auto tpv) {
+    launch_one<T, decltype(f)::value, decltype(tpv)::value>(ctx, a, s, share);
+  });
 }
 
 template bool persist_supported<double>(const cp_mat*, const cp_config&);

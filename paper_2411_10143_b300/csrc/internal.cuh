@@ -21,6 +21,7 @@ void set_error(const char* fmt, ...);
 // Timestamped trace line on stderr when the environment sets CASCADE_TRACE=1
 // (prediction / conversion / solve-loop steps; off by default).
 void trace(const char* fmt, ...);
+bool trace_on();
 
 struct Error {
   cp_status status;

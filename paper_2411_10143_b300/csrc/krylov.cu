@@ -24,24 +24,6 @@
 
 namespace cp {
 
-constexpr int kMaxRestart = 64;
-
-// ================================================================== device state
-struct GmState {
-  double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
-  double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
-  double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
-  double bb, beta, inv;  // ||b||^2, cycle start ||r||, 1 / current norm
-  int done;              // converged (true residual of a cycle start)
-  int halt;              // no further steps in this cycle
-  int conv_est;          // the cycle's residual estimate reached tol
-  int jdone;             // steps completed in this cycle
-  int status;
-  int iters;             // steps completed in total
-  int skip2;             // this step's second Gram-Schmidt pass is not needed
-  int reorths;           // steps that took the second pass
-};
-
 // ================================================================== CG kernels
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_init(int64_t n, const T* __restrict__ b,
@@ -579,7 +561,7 @@ struct CgBufs {
 template <typename T>
 struct GmBufs {
   T *V = nullptr, *tmp = nullptr;
-  double *part = nullptr, *pn = nullptr;
+  double *part = nullptr, *part2 = nullptr, *pn = nullptr;
   GmState* st = nullptr;
   int mrest = 0;
 };
@@ -623,6 +605,7 @@ struct Workspace {
       B.V = get<T>(ldv * (mrest + 1));
       B.tmp = get<T>(n);
       B.part = get<double>((int64_t)kMaxPartials * (kMaxRestart + 2));
+      B.part2 = get<double>((int64_t)kMaxPartials * (kMaxRestart + 2));
       B.pn = get<double>(kMaxPartials);
       B.st = get<GmState>(1);
       B.mrest = mrest;
@@ -693,6 +676,8 @@ struct ConfigSource {
   int n_spmv = 0;
   bool persistent = true;     // run CG iterations in the persistent kernel when it supports cfg
   double wait_limit_ms = 0.0; // bound of the persistent kernel's device waits (0: default)
+  int persist_chunk = 0;      // iterations a persistent launch runs before returning (0: all)
+  int persist_launches = 0;   // persistent launches made
   float t_persist_ms = 0.f;   // summed duration of the persistent launches
   int persist_iters = 0;      // iterations they ran
   float t_persist_last_ms = 0.f;
@@ -831,7 +816,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         pa_args.mir = mir;
         pa_args.yield = yield_d;
         pa_args.it0 = it;
-        pa_args.itmax = maxit;
+        pa_args.itmax = cs.persist_chunk > 0 ? std::min(maxit, it + cs.persist_chunk) : maxit;
         pa_args.tol2 = tol2;
         if (cs.wait_limit_ms > 0.0)
           pa_args.barrier_timeout_ns = (long long)(cs.wait_limit_ms * 1e6);
@@ -841,6 +826,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         CP_CUDA(cudaEventRecord(e0, s));
         trace("solve: persistent launch at iteration %d (format %d)", it, cs.cur.fmt);
         persist_launch<T>(ctx, m, cs.cur, pa_args, s, 1);
+        ++cs.persist_launches;
         CP_CUDA(cudaEventRecord(e1, s));
         for (;;) {
           const cudaError_t q = cudaEventQuery(e1);
@@ -958,6 +944,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
   }
   LoopResult res;
   int first = 1;
+  bool finished = false;  // the persistent kernel ended the solve (converged or failed)
   for (;;) {
     // cycle start: V0 = b - A x, beta = ||V0||, V0 /= beta
     int P0 = G;
@@ -980,10 +967,90 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       res.status = CP_ERR_NOT_CONVERGED;
       break;
     }
-    const int steps = std::min(mrest, maxit - res.iters);
+    int steps = std::min(mrest, maxit - res.iters);  // this cycle's length
     int issued = 0;
-    for (int j = 0; j < steps; ++j) {
+    bool x_updated = false;  // the persistent kernel ended the cycle and updated x
+    int j = 0;
+    while (j < steps) {
       cs.poll(res.iters + j);
+      // Once no prediction work is pending on the side stream, one cooperative
+      // launch takes over the steps (across cycles) until the solve ends, the
+      // budget is spent, or the host asks it to return at a step boundary
+      // because a new configuration was published or the side needs the GPU.
+      const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire) ||
+                             cs.ch->side_gpu_idle.load(std::memory_order_acquire);
+      if (cs.persistent && side_idle && gm_persist_supported<T>(m, cs.cur, mrest)) {
+        int* yield_d = ws.yield();
+        *(volatile int*)ws.yield_h = 0;
+        ws.mir->exit_kind = 0;
+        GmPersistArgs<T> ga;
+        ga.V = V;
+        ga.ldv = ldv;
+        ga.x = x;
+        ga.b = b;
+        ga.part = part;
+        ga.part2 = B.part2;
+        ga.pn = pn;
+        ga.st = st;
+        ga.mir = mir;
+        ga.yield = yield_d;
+        ga.itmax = maxit;
+        ga.mrest = mrest;
+        ga.mcyc = steps;
+        ga.chunk = cs.persist_chunk;
+        ga.true_check = true_check ? 1 : 0;
+        ga.always_reorth = std::is_same<T, float>::value ? 1 : 0;
+        ga.tol2 = tol2;
+        if (cs.wait_limit_ms > 0.0)
+          ga.barrier_timeout_ns = (long long)(cs.wait_limit_ms * 1e6);
+        const int it_before = res.iters + j;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        CP_CUDA(cudaEventCreate(&e0));
+        CP_CUDA(cudaEventCreate(&e1));
+        CP_CUDA(cudaEventRecord(e0, s));
+        trace("solve: persistent GMRES launch at step %d of the cycle (format %d)", j,
+              cs.cur.fmt);
+        gm_persist_launch<T>(ctx, m, cs.cur, ga, s);
+        ++cs.persist_launches;
+        CP_CUDA(cudaEventRecord(e1, s));
+        for (;;) {
+          const cudaError_t q = cudaEventQuery(e1);
+          if (q == cudaSuccess) break;
+          if (q != cudaErrorNotReady) CP_CUDA(q);
+          if (cs.ch && !*ws.yield_h &&
+              (cs.ch->count.load(std::memory_order_acquire) > cs.applied ||
+               (!cs.ch->finished.load(std::memory_order_acquire) &&
+                !cs.ch->side_gpu_idle.load(std::memory_order_acquire))))
+            *(volatile int*)ws.yield_h = 1;
+          std::this_thread::sleep_for(std::chrono::microseconds(20));
+        }
+        float t = 0.f;
+        CP_CUDA(cudaEventElapsedTime(&t, e0, e1));
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        const int kind = ws.mir->exit_kind;
+        const int ran = ws.mir->iters - it_before;
+        cs.t_persist_ms += t;
+        cs.persist_iters += ran;
+        cs.t_persist_last_ms = t;
+        cs.persist_last_iters = ran;
+        trace("solve: persistent GMRES returned (kind %d) after %d steps (%.3f ms)", kind, ran, t);
+        if (ws.mir->done || ws.mir->status != CP_OK) {
+          finished = true;
+          break;
+        }
+        if (kind == 2) {  // at the end of a cycle, x updated
+          x_updated = true;
+          break;
+        }
+        if (kind == 0) break;  // the cycle had ended in a step queued before the launch
+        // inside a cycle (possibly a later one): the per-step kernels carry on
+        res.iters = ws.mir->iters - ws.mir->jdone;
+        steps = ws.mir->mcyc;
+        j = ws.mir->jdone;
+        issued = 0;
+        continue;
+      }
       T* vj = V + (int64_t)j * ldv;
       T* w = V + (int64_t)(j + 1) * ldv;
       spmv_cur<T>(cs, vj, w, nullptr, nullptr, &st->halt, s);
@@ -1004,18 +1071,36 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       CP_LAUNCH(ctx, k_gm_scale<T>, G, kBlock, 0, s, n, w, st, 1);
       CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
       ++issued;
+      ++j;
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));
         if (ws.mir->halt) break;
       }
     }
-    CP_LAUNCH(ctx, k_gm_backsub, 1, 1, 0, s, st);
-    CP_LAUNCH(ctx, k_gm_update_x<T>, G, kBlock, 0, s, n, V, ldv, x, st);
+    if (finished) {
+      res.iters = ws.mir->iters;
+      res.status = ws.mir->status;
+      res.res = ws.mir->res;
+      break;
+    }
+    if (!x_updated) {
+      CP_LAUNCH(ctx, k_gm_backsub, 1, 1, 0, s, st);
+      CP_LAUNCH(ctx, k_gm_update_x<T>, G, kBlock, 0, s, n, V, ldv, x, st);
+    }
     CP_CUDA(cudaStreamSynchronize(s));
     res.iters = ws.mir->iters;
     res.status = ws.mir->status;
     if (res.status != CP_OK) break;
     if (!true_check && ws.mir->conv_est) break;
+  }
+  if (cs.persist_iters > 0 && trace_on()) {
+    unsigned long long tn[6];
+    CP_CUDA(cudaStreamSynchronize(s));
+    CP_CUDA(cudaMemcpy(tn, st->t_ns, sizeof(tn), cudaMemcpyDeviceToHost));
+    const double k = 1e-3 / cs.persist_iters;
+    trace("persistent GMRES per step (us): spmv+dots %.2f bar %.2f sub %.2f bar %.2f "
+          "second pass %.2f cycle ends %.2f", tn[0] * k, tn[1] * k, tn[2] * k, tn[3] * k,
+          tn[4] * k, tn[5] * k);
   }
   if (true_check) {
     // FP64 true residual of the returned x
@@ -1125,6 +1210,8 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
   cs.persistent = opt.iteration_kernel == 0;
   CP_REQUIRE(opt.wait_limit_ms >= 0.0, CP_ERR_INVALID, "wait_limit_ms must be >= 0");
   cs.wait_limit_ms = opt.wait_limit_ms;
+  CP_REQUIRE(opt.persist_chunk >= 0, CP_ERR_INVALID, "persist_chunk must be >= 0");
+  cs.persist_chunk = opt.persist_chunk;
   cp_config_default(&cs.cur);
   if (opt.force) cs.cur = *opt.force;
   ensure_format(ctx, m, cs.cur, ctx->main);
@@ -1197,6 +1284,7 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
     info->gate_remaining = ch.gate_remaining;
     info->gate_cost_spmvs = ch.gate_cost;
     info->side_status = ch.status;
+    info->persist_launches = cs.persist_launches;
     info->n_launches = (int32_t)(ctx->launches.load() - launches0);
     info->status = res.status;
   }

@@ -1,8 +1,14 @@
-// Shared declarations of the persistent CG kernel (cg_persist.cu) and its host
-// driver (krylov.cu).
+// Shared declarations of the persistent Krylov kernels (cg_persist.cu,
+// gm_persist.cu) and their host drivers (krylov.cu): solver state, the
+// host-mapped mirror, the grid barrier and the SpMV phase over the formats a
+// persistent kernel runs.
 #pragma once
 
+#include <type_traits>
+
+#include "common.cuh"
 #include "internal.cuh"
+#include "spmv_rows.cuh"
 
 namespace cp {
 
@@ -20,6 +26,33 @@ struct CgState {
   unsigned long long t_ns[6];
 };
 
+constexpr int kMaxRestart = 64;  // largest GMRES restart length
+
+// GMRES(m) state of one solve (Sec. I; Saad, Alg. 6.9): the rotated Hessenberg
+// matrix, the Givens rotations and the rotated right-hand side g of the current
+// cycle, written by the per-step kernels and by the persistent kernel's block 0.
+struct GmState {
+  double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
+  double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
+  double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+  double bb, beta, inv;  // ||b||^2, cycle start ||r||, 1 / current norm
+  int done;              // converged (true residual of a cycle start)
+  int halt;              // no further steps in this cycle
+  int conv_est;          // the cycle's residual estimate reached tol
+  int jdone;             // steps completed in this cycle
+  int status;
+  int iters;             // steps completed in total
+  int skip2;             // this step's second Gram-Schmidt pass is not needed
+  int reorths;           // steps that took the second pass
+  int mcyc;              // length of the current cycle (min(m, iterations left at its start))
+  int stop;              // persistent kernel: return at the next step boundary
+  unsigned bar_count;    // persistent kernel: barrier arrivals (this launch)
+  int bar_err;           // persistent kernel: a barrier wait gave up
+  // block 0's time in the persistent kernel (ns): SpMV + first dots, barrier,
+  // subtraction, barrier, second pass, end of cycle
+  unsigned long long t_ns[6];
+};
+
 constexpr int kPersistBlock = 1024;  // one block per SM: 148 barrier arrivals, 148 partials;
                                      // a multiple of 128 (block_sum_lean)
 
@@ -29,6 +62,9 @@ struct Mirror {
   volatile double res0;   // residual norm at the (re)start
   volatile double bnorm;  // ||b||
   volatile int done, halt, status, iters, jdone, conv_est;
+  volatile int mcyc;       // GMRES: length of the current cycle
+  volatile int exit_kind;  // persistent GMRES: 1 = returned inside a cycle (columns
+                           // normalised), 2 = returned at a cycle end (x updated)
 };
 
 enum {
@@ -39,17 +75,63 @@ enum {
   kPersistDia = 4
 };
 
+// ------------------------------------------------------------------ grid barrier
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Arrival and polling with release / acquire semantics at GPU scope: the
+// block's writes (ordered before thread 0 by the preceding __syncthreads) are
+// published by the release; the acquire makes the other blocks' writes visible
+// before the block's next reads (which go through L2).
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier with a time limit over a monotone arrival counter (zeroed
+// by the host before the launch).  target: the arrival count that ends this
+// barrier (the block's running count of barriers times the grid size).
+// Returns false (in every thread of the block) when the wait gave up or
+// another block already did (err set).
+__device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned target,
+                                             long long timeout_ns) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile int* e = err;
+    red_add_release(count, 1u);
+    int good = 1;
+    if ((int)(ld_acquire(count) - target) < 0) {
+      const unsigned long long t0 = global_ns();
+      while ((int)(ld_acquire(count) - target) < 0) {
+        if (*e) {
+          good = 0;
+          break;
+        }
+        if ((long long)(global_ns() - t0) > timeout_ns) {
+          atomicExch(err, 1);
+          good = 0;
+          break;
+        }
+      }
+    }
+    ok = good && !*e;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// ------------------------------------------------------------------ matrix of a persistent kernel
 template <typename T>
-struct PersistArgs {
+struct PersistMat {
   int64_t n = 0;
-  T *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr;
-  double *pa = nullptr, *pb = nullptr;  // block partials, capacity >= grid
-  CgState* st = nullptr;
-  Mirror* mir = nullptr;
-  const volatile int* yield = nullptr;  // host-mapped: return at the next iteration boundary
-  int it0 = 0, itmax = 0;
-  double tol2 = 0.0;
-  long long barrier_timeout_ns = 2000000000ll;
   // CSR
   const int32_t *rp = nullptr, *ci = nullptr;
   const T* v = nullptr;
@@ -69,6 +151,31 @@ struct PersistArgs {
   const T* dv = nullptr;
 };
 
+// y = alpha A x + beta y (GEN) or y = A x over the rows of the format's
+// grid-stride mapping; returns the thread's share of (y, dotv) when DOT.  x is
+// read through L2 (the persistent kernels rewrite it between phases).
+template <typename T, int F, int TPV, bool GEN, bool DOT>
+__device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t* so,
+                                          const T* x, T* y, T alpha, T beta, const T* dotv) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  if constexpr (F == kPersistCsrScalar)
+    return csr_scalar_rows<T, GEN, DOT, true>(a.n, a.rp, a.ci, a.v, x, y, alpha, beta, dotv,
+                                              tid, stride);
+  else if constexpr (F == kPersistCsrVector)
+    return csr_vector_rows<T, TPV, GEN, DOT, true>(a.n, a.rp, a.ci, a.v, x, y, alpha, beta,
+                                                   dotv, tid >> 5, stride >> 5);
+  else if constexpr (F == kPersistEll)
+    return ell_rows<T, GEN, DOT, true>(a.n, a.K, a.ld, a.ec, a.ev, x, y, alpha, beta, dotv, tid,
+                                       stride);
+  else if constexpr (F == kPersistSell)
+    return sell_chunks<T, GEN, DOT, true>(a.n, a.nchunks, a.perm, a.clen, a.cptr, a.sc, a.sv, x,
+                                          y, alpha, beta, dotv, tid >> 5, stride >> 5);
+  else
+    return dia_rows<T, GEN, DOT, true>(a.n, a.n, a.ndiag, so, a.dv, x, y, alpha, beta, dotv,
+                                       tid, stride);
+}
+
 template <typename T>
 struct PersistVals;
 template <>
@@ -86,6 +193,82 @@ struct PersistVals<float> {
   static const float* dia(const DiaPart& d) { return d.val32; }
 };
 
+// Formats a persistent kernel runs: CSR (scalar or vector), ELL, HYB without a
+// COO part (which is ELL), SELL and DIA.
+inline bool persist_format_ok(const cp_mat* m, const cp_config& c) {
+  if (c.fmt == CP_FMT_CSR) return c.algo == CP_ALGO_SCALAR || c.algo == CP_ALGO_VECTOR;
+  if (c.fmt == CP_FMT_HYB) return m->hyb_coo.n == 0;
+  return c.fmt == CP_FMT_ELL || c.fmt == CP_FMT_SELL || c.fmt == CP_FMT_DIA;
+}
+
+template <int V>
+using IntC = std::integral_constant<int, V>;
+
+// Fills a's format fields from m's data for configuration c and calls
+// launch(IntC<F>{}, IntC<TPV>{}) with the matching kernel variant.
+template <typename T, typename L>
+void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launch) {
+  a.n = m->nrows;
+  switch (c.fmt) {
+    case CP_FMT_CSR:
+      a.rp = m->rowptr;
+      a.ci = m->col;
+      a.v = PersistVals<T>::csr(m);
+      if (c.algo == CP_ALGO_SCALAR) {
+        launch(IntC<kPersistCsrScalar>{}, IntC<1>{});
+      } else {
+        switch (c.tpv) {
+          case 2: launch(IntC<kPersistCsrVector>{}, IntC<2>{}); break;
+          case 4: launch(IntC<kPersistCsrVector>{}, IntC<4>{}); break;
+          case 8: launch(IntC<kPersistCsrVector>{}, IntC<8>{}); break;
+          case 16: launch(IntC<kPersistCsrVector>{}, IntC<16>{}); break;
+          default: launch(IntC<kPersistCsrVector>{}, IntC<32>{}); break;
+        }
+      }
+      break;
+    case CP_FMT_ELL:
+    case CP_FMT_HYB: {
+      const EllPart& e = c.fmt == CP_FMT_ELL ? m->ell : m->hyb_ell;
+      a.K = e.K;
+      a.ld = e.ld;
+      a.ec = e.col;
+      a.ev = PersistVals<T>::ell(e);
+      launch(IntC<kPersistEll>{}, IntC<1>{});
+      break;
+    }
+    case CP_FMT_SELL:
+      a.nchunks = m->sell.nchunks;
+      a.perm = m->sell.sigma > 1 ? m->sell.perm : nullptr;
+      a.clen = m->sell.chunk_len;
+      a.cptr = m->sell.chunk_ptr;
+      a.sc = m->sell.col;
+      a.sv = PersistVals<T>::sell(m->sell);
+      launch(IntC<kPersistSell>{}, IntC<1>{});
+      break;
+    case CP_FMT_DIA:
+      a.ndiag = (int)m->dia.ndiag;
+      a.offs = m->dia.offs;
+      a.dv = PersistVals<T>::dia(m->dia);
+      launch(IntC<kPersistDia>{}, IntC<1>{});
+      break;
+    default:
+      CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent kernel for format %d", c.fmt);
+  }
+}
+
+// ------------------------------------------------------------------ CG
+template <typename T>
+struct PersistArgs : PersistMat<T> {
+  T *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr;
+  double *pa = nullptr, *pb = nullptr;  // block partials, capacity >= grid
+  CgState* st = nullptr;
+  Mirror* mir = nullptr;
+  const volatile int* yield = nullptr;  // host-mapped: return at the next iteration boundary
+  int it0 = 0, itmax = 0;
+  double tol2 = 0.0;
+  long long barrier_timeout_ns = 2000000000ll;
+};
+
 template <typename T>
 bool persist_supported(const cp_mat* m, const cp_config& c);
 // share = 1: the whole device; 2: half of every SM, leaving room for the
@@ -93,5 +276,33 @@ bool persist_supported(const cp_mat* m, const cp_config& c);
 template <typename T>
 void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a,
                     cudaStream_t s, int share);
+
+// ------------------------------------------------------------------ GMRES
+template <typename T>
+struct GmPersistArgs : PersistMat<T> {
+  T* V = nullptr;  // basis, column c at V + c * ldv; column jdone holds the next vector
+  int64_t ldv = 0;
+  T* x = nullptr;
+  const T* b = nullptr;
+  double *part = nullptr, *part2 = nullptr;  // (m + 2) x grid block partials each
+  double* pn = nullptr;                      // grid block partials
+  GmState* st = nullptr;
+  Mirror* mir = nullptr;
+  const volatile int* yield = nullptr;  // host-mapped: return at the next step boundary
+  int itmax = 0;         // iteration budget (total steps)
+  int mrest = 0;         // restart length m
+  int mcyc = 0;          // length of the cycle the launch enters
+  int chunk = 0;         // > 0: return at the step boundary after this many steps
+  int true_check = 1;    // 0: a cycle whose estimate reached tol ends the solve (FP32 inner solves)
+  int always_reorth = 0; // second Gram-Schmidt pass in every step (FP32)
+  double tol2 = 0.0;
+  long long barrier_timeout_ns = 2000000000ll;
+};
+
+template <typename T>
+bool gm_persist_supported(const cp_mat* m, const cp_config& c, int mrest);
+template <typename T>
+void gm_persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, GmPersistArgs<T> a,
+                       cudaStream_t s);
 
 }  // namespace cp

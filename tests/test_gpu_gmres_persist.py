@@ -1,0 +1,199 @@
+"""The persistent GMRES(m) kernel (one cooperative launch across Arnoldi steps,
+cycle ends and restarts) against the one-launch-per-step path and the oracle.
+
+Acceptance as for every solver test: the true relative residual of the GPU
+solution, recomputed by the oracle's SpMV, is <= 1e-10 and the solution is
+within 1e-7 (relative) of the oracle's GMRES(m) solution at the same
+tolerance.  The two GPU paths orthogonalise with classical Gram-Schmidt in a
+different summation order, so their iteration counts may differ by a few."""
+import functools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2411_10143_b300 import cascade as C
+from paper_2411_10143_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+# Row-parallel configurations the persistent kernel runs.  SELL with sigma > 1
+# permutes rows inside its sorting windows, so its SpMV rows are not the
+# block's own rows and the kernel takes a grid barrier after the SpMV.
+CFGS = [C.config("CSR"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
+        C.config("CSR", C.ALGO_VECTOR, tpv=32), C.config("ELL"), C.config("SELL", sigma=1),
+        C.config("SELL", sigma=1024), C.config("DIA"), C.config("HYB")]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = C.Context(0)
+    yield c
+    c.close()
+
+
+def true_relres(A, x, b):
+    return np.linalg.norm(b - oracle.spmv(A, x)) / np.linalg.norm(b)
+
+
+def solve(ctx, A, b, **kw):
+    M = ctx.load(A)
+    force = kw.pop("force", None)
+    raise_on_error = kw.pop("raise_on_error", True)
+    bd = torch.as_tensor(b, device="cuda")
+    xd = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+    info = M.solve_gmres(bd, xd, C.default_opts(**kw), force=force,
+                         raise_on_error=raise_on_error)
+    return xd.cpu().numpy(), info
+
+
+@functools.lru_cache(maxsize=None)
+def system(k, seed):
+    """Convection-diffusion on a k^3 grid with b = A x*, and the oracle's
+    GMRES(m) solutions by m."""
+    A = W.convdiff3d(k)
+    b = oracle.spmv(A, W.vector(A.ncols, seed))
+    return A, b
+
+
+@functools.lru_cache(maxsize=None)
+def reference(k, seed, m):
+    A, b = system(k, seed)
+    return oracle.gmres(A, b, m=m, tol=1e-10)
+
+
+def check(A, b, x, ref):
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+def close_iters(a, b):
+    return abs(a - b) <= max(3, 0.05 * b)
+
+
+@pytest.mark.parametrize("cfg", CFGS, ids=repr)
+@pytest.mark.parametrize("m", [5, 30])
+def test_persistent_gmres_matches_per_step_launches(ctx, cfg, m):
+    """n = 2,744: three of the 148 blocks own rows (the last one a ragged
+    segment), the others none; m = 5 restarts inside the kernel many times."""
+    A, b = system(14, 21)
+    ref = reference(14, 21, m)
+    out = {}
+    for kernel in (0, 1):
+        x, info = solve(ctx, A, b, restart=m, tol=1e-10, force=cfg, iteration_kernel=kernel)
+        assert info.status == 0, (repr(cfg), kernel)
+        check(A, b, x, ref)
+        out[kernel] = info
+    if cfg.fmt != C.FMT_HYB:  # HYB runs persistently only without a COO part
+        assert out[0].persist_iters == out[0].iters and out[0].persist_launches >= 1
+    assert out[1].persist_iters == 0 and out[1].persist_launches == 0
+    assert close_iters(out[0].iters, out[1].iters), (out[0].iters, out[1].iters)
+
+
+@pytest.mark.parametrize("cfg", [C.config("DIA"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
+                                 C.config("SELL", sigma=1024)], ids=repr)
+def test_persistent_gmres_rows_in_several_segments(ctx, cfg):
+    """n = 175,616 is more than one row per thread of the grid, so every block
+    owns several row segments (CSR-vector with 4 lanes a row: segments of 256
+    rows)."""
+    A, b = system(56, 22)
+    ref = reference(56, 22, 30)
+    x, info = solve(ctx, A, b, restart=30, tol=1e-10, force=cfg)
+    assert info.status == 0 and info.persist_iters == info.iters
+    check(A, b, x, ref)
+    assert close_iters(info.iters, ref.iters), (info.iters, ref.iters)
+
+
+@pytest.mark.parametrize("cfg", [C.config("DIA"), C.config("CSR")], ids=repr)
+def test_persistent_gmres_largest_restart(ctx, cfg):
+    """m = 64, the largest restart: the kernel's shared memory (the cycle's
+    Hessenberg matrix in every block) exceeds the 48 KB default and is opted in."""
+    A, b = system(14, 23)
+    ref = reference(14, 23, 64)
+    x, info = solve(ctx, A, b, restart=64, tol=1e-10, force=cfg)
+    assert info.status == 0 and info.persist_iters == info.iters
+    check(A, b, x, ref)
+
+
+def test_persistent_gmres_tiny_system(ctx):
+    """n = 27: one block owns every row, one warp has the only chunk of dot work."""
+    A, b = system(3, 24)
+    ref = reference(3, 24, 30)
+    x, info = solve(ctx, A, b, restart=30, tol=1e-10, force=C.config("CSR"))
+    assert info.status == 0
+    check(A, b, x, ref)
+
+
+@pytest.mark.parametrize("cfg", [C.config("DIA"), C.config("CSR"),
+                                 C.config("SELL", sigma=1024)], ids=repr)
+def test_persistent_gmres_fp32_inner_solves(ctx, cfg):
+    """FP64 refinement around FP32 GMRES(30) inner solves, every inner step in
+    the persistent kernel (second Gram-Schmidt pass in every step)."""
+    A, b = system(20, 25)
+    ref64 = reference(20, 25, 30)
+    out = {}
+    for kernel in (0, 1):
+        x, info = solve(ctx, A, b, restart=30, tol=1e-10, force=cfg, iteration_kernel=kernel,
+                        precision=C.PREC_FP32_IR, inner_tol=1e-5)
+        assert info.status == 0 and info.outer_iters >= 2
+        check(A, b, x, ref64)
+        out[kernel] = info
+    assert out[0].persist_iters == out[0].iters and out[1].persist_iters == 0
+
+
+@pytest.mark.parametrize("chunk", [1, 7])
+def test_persistent_gmres_returns_and_resumes(ctx, chunk):
+    """persist_chunk makes every launch return after `chunk` steps: with m = 5
+    and 7 steps a launch it returns inside cycles (columns normalised, the state
+    handed back) and at their ends (x updated); the next launch resumes there.
+    The solution is the same as with one launch."""
+    A, b = system(14, 26)
+    ref = reference(14, 26, 5)
+    x1, one = solve(ctx, A, b, restart=5, tol=1e-10, force=C.config("DIA"))
+    x, info = solve(ctx, A, b, restart=5, tol=1e-10, force=C.config("DIA"),
+                    persist_chunk=chunk)
+    assert info.status == 0 and one.persist_launches == 1
+    assert info.persist_iters == info.iters
+    assert info.persist_launches >= info.iters // chunk
+    check(A, b, x, ref)
+    assert close_iters(info.iters, one.iters)
+
+
+def test_persistent_cg_returns_and_resumes(ctx):
+    A = W.poisson3d(20)
+    b = oracle.spmv(A, W.vector(A.ncols, 27))
+    ref = oracle.cg(A, b, tol=1e-10)
+    M = ctx.load(A)
+    bd = torch.as_tensor(b, device="cuda")
+    xd = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+    info = M.solve_cg(bd, xd, C.default_opts(tol=1e-10, persist_chunk=10),
+                      force=C.config("DIA"))
+    x = xd.cpu().numpy()
+    assert info.status == 0 and info.persist_launches >= info.iters // 10
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+def test_persistent_gmres_iteration_budget(ctx):
+    """maxit = 13 with m = 5: the kernel ends the third cycle after 3 steps and
+    returns; the solve reports CP_ERR_NOT_CONVERGED after exactly 13 steps."""
+    A, b = system(14, 28)
+    x, info = solve(ctx, A, b, restart=5, tol=1e-10, maxit=13, force=C.config("DIA"),
+                    raise_on_error=False)
+    assert info.status == C.ERR_NOT_CONVERGED and info.iters == 13
+    assert info.persist_iters == 13
+
+
+def test_persistent_gmres_bounded_wait_times_out_cleanly():
+    """A barrier wait limit of one nanosecond: the first grid barrier gives up,
+    every block leaves at its next barrier, the solve returns CP_ERR_TIMEOUT, and
+    the context then solves normally."""
+    c = C.Context(0)
+    A, b = system(14, 29)
+    x, info = solve(c, A, b, restart=30, tol=1e-10, force=C.config("DIA"),
+                    raise_on_error=False, wait_limit_ms=1e-6)
+    assert info.status == C.ERR_TIMEOUT
+    x, info = solve(c, A, b, restart=30, tol=1e-10, force=C.config("DIA"))
+    assert info.status == 0 and true_relres(A, x, b) <= 1e-10
+    c.close()
