@@ -206,11 +206,115 @@ __device__ __forceinline__ T block_sub(const BlockRows& br, T* V, int64_t ldv, i
   return acc;
 }
 
+// Modified Gram-Schmidt in groups of four columns.  For unit vectors v_c the
+// product of the projections (I - v_{c+3} v_{c+3}^T) ... (I - v_c v_c^T) equals
+// I - V T V^T with V = [v_c .. v_{c+3}] and T = (I + L)^{-1}, L the strictly
+// lower part of V^T V (the compact WY form, exact for any unit vectors).  So
+// h = T V^T w, a forward substitution with the group's inner products (v_q,
+// v_c), gives the coefficients modified Gram-Schmidt computes one column at a
+// time, and the group costs one grid reduction instead of four.  A pass over
+// the block's rows subtracts one group and forms the dot products of the next
+// (or, after the last group, ||w||^2 and the new column's inner products with
+// the columns of its own group, the entries of L its group will need).
+constexpr int kMgsThreads = 512;  // threads of a block that run the passes: half the
+                                  // FP64 partials to reduce of 1024, and still
+                                  // enough loads in flight (512 measured fastest of
+                                  // 256 / 512 / 1024 on 884,736 rows)
+
+template <typename T, int RS, int RD, bool FIRST, bool LAST>
+__device__ __forceinline__ void mgs_pass(const BlockRows& br, const T* V, int64_t ldv, int cs0,
+                                         int cd0, const T* kc, T* ws, T* wg, double (&out)[4]) {
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  T k[RS > 0 ? RS : 1];
+#pragma unroll
+  for (int u = 0; u < RS; ++u) k[u] = kc[u];
+  for (int64_t f = threadIdx.x; f < br.count; f += kMgsThreads) {
+    const int64_t i = br.row(f);
+    T wv = FIRST ? ld_cg(wg + i) : ws[f];
+    T a[RS > 0 ? RS : 1], d[RD > 0 ? RD : 1];
+#pragma unroll
+    for (int u = 0; u < RS; ++u) a[u] = ld_cg(V + (int64_t)(cs0 + u) * ldv + i);
+#pragma unroll
+    for (int u = 0; u < RD; ++u) d[u] = ld_cg(V + (int64_t)(cd0 + u) * ldv + i);
+#pragma unroll
+    for (int u = 0; u < RS; ++u) wv = fma(-k[u], a[u], wv);
+    if (LAST) {
+      wg[i] = wv;  // the next step's SpMV gathers it
+      acc[0] = fma(wv, wv, acc[0]);
+      if (RS < 4) {
+#pragma unroll
+        for (int u = 0; u < RS; ++u) acc[1 + u] = fma(a[u], wv, acc[1 + u]);
+      }
+    } else {
+      ws[f] = wv;
+#pragma unroll
+      for (int u = 0; u < RD; ++u) acc[u] = fma(d[u], wv, acc[u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) out[u] = (double)acc[u];
+}
+
+template <typename T>
+__device__ __forceinline__ void mgs_first(int rd, const BlockRows& br, const T* V, int64_t ldv,
+                                          T* ws, T* wg, double (&out)[4]) {
+  switch (rd) {
+    case 1: mgs_pass<T, 0, 1, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
+    case 2: mgs_pass<T, 0, 2, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
+    case 3: mgs_pass<T, 0, 3, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
+    default: mgs_pass<T, 0, 4, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void mgs_mid(int rd, const BlockRows& br, const T* V, int64_t ldv,
+                                        int cs0, const T* kc, T* ws, T* wg, double (&out)[4]) {
+  switch (rd) {
+    case 1: mgs_pass<T, 4, 1, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
+    case 2: mgs_pass<T, 4, 2, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
+    case 3: mgs_pass<T, 4, 3, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
+    default: mgs_pass<T, 4, 4, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
+  }
+}
+template <typename T>
+__device__ __forceinline__ void mgs_last(int rs, const BlockRows& br, const T* V, int64_t ldv,
+                                         int cs0, const T* kc, T* ws, T* wg, double (&out)[4]) {
+  switch (rs) {
+    case 1: mgs_pass<T, 1, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
+    case 2: mgs_pass<T, 2, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
+    case 3: mgs_pass<T, 3, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
+    default: mgs_pass<T, 4, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
+  }
+}
+
+static_assert(4 * (kMgsThreads / 32) <= 32 * 3, "warp-sum table too small for kMgsThreads");
+
+// Block sums of four values held by the first kMgsThreads threads: each warp
+// folds its four with warp_sum4, four threads add the warps' results in order
+// and write the block's partials part[q * grid + block].  wp: 4 * kMgsThreads / 32
+// doubles (the kernel's warp-sum table holds at least 96).
+__device__ __forceinline__ void mgs_block_partials(const double (&v)[4], double* wp,
+                                                   double* part) {
+  constexpr int nw = kMgsThreads / 32;
+  if (threadIdx.x < kMgsThreads) {
+    const double s = warp_sum4(v[0], v[1], v[2], v[3]);
+    const int lane = threadIdx.x & 31;
+    if ((lane & 7) == 0) wp[((lane >> 3) & 3) * nw + (threadIdx.x >> 5)] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double t = 0.0;
+#pragma unroll
+    for (int k = 0; k < nw; ++k) t += wp[threadIdx.x * nw + k];
+    part[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  }
+}
+
 // Layout of the kernel's dynamic shared memory for restart length M, in
 // doubles: the one description both the kernel's carving and the host's size use.
 struct GmSmem {
-  int64_t H, cs, sn, g, y, sc, h, h2, coef, wp, red, total;
-  __host__ __device__ constexpr explicit GmSmem(int M)
+  int64_t H, cs, sn, g, y, sc, h, h2, coef, wp, red, G, w, total;
+  // wrows: rows of w a block keeps in shared memory (modified Gram-Schmidt), or 0
+  __host__ __device__ constexpr GmSmem(int M, int64_t wrows)
       : H(0),
         cs(H + (int64_t)(M + 1) * M),  // H: (M + 1) x M, H[i * M + j]
         sn(cs + M),
@@ -222,7 +326,9 @@ struct GmSmem {
         coef(h2 + M + 2),
         wp(coef + M + 2),  // coef: M + 2 values of T (at most a double each)
         red(wp + 32 * (int64_t)(M + 2)),
-        total(red + kPersistBlock + 4) {}
+        G(red + kPersistBlock + 4),  // G: (M + 1) x 4 group inner products
+        w(G + 4 * (int64_t)(M + 1)),
+        total(w + wrows) {}
 };
 
 template <typename T, int F, int TPV>
@@ -233,7 +339,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
   if (ld_cg(&st->done) || ld_cg(&st->halt)) return;
   extern __shared__ double dsm[];
   const int M = a.mrest;
-  const GmSmem L(M);
+  const GmSmem L(M, a.wrows);
   double* H = dsm + L.H;    // rotated Hessenberg matrix of the cycle, H[i * M + j]
   double* cs = dsm + L.cs;  // Givens rotations
   double* sn = dsm + L.sn;
@@ -245,8 +351,11 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
   T* coef = reinterpret_cast<T*>(dsm + L.coef);
   double* wp = dsm + L.wp;  // (M + 2) x 32 warp sums of block_dots
   double* red = dsm + L.red;
+  double* G = dsm + L.G;    // (v_q, v_c) within groups of four columns, G[q * 4 + c % 4]
+  T* ws = reinterpret_cast<T*>(dsm + L.w);  // the block's rows of w (modified Gram-Schmidt)
   __shared__ int32_t so[F == kPersistDia ? kDiaMax : 1];
   __shared__ double sh_w2;
+  __shared__ double rsum[4];  // a grouped Gram-Schmidt round's four sums
   __shared__ int sh_flag, sh_halt, sh_stop, sh_bad, sh_conv, sh_fin, sh_mcyc;
 
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -270,6 +379,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
     g[k] = ld_cg(&st->g[k]);
     sc[k] = 1.0;
   }
+  for (int k = threadIdx.x; k < 4 * (M + 1); k += blockDim.x) G[k] = ld_cg(&st->G[k]);
   if (lead) {
     st->mcyc = a.mcyc;
     a.mir->mcyc = a.mcyc;
@@ -295,72 +405,143 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
     }
   };
   int exit_kind = 0;
+  unsigned rounds = 0;  // grid reductions of the modified Gram-Schmidt loop so far
   for (;;) {
     T* w = V + (int64_t)(j + 1) * ldv;
-    // ---- 1. w = A v_j, first-pass dots
-    persist_spmv<T, F, TPV, true, false>(a, so, V + (int64_t)j * ldv, w, (T)sc[j], T(0),
-                                         nullptr);
-    if (!fused && !barrier()) break;
-    block_dots<T>(br, V, ldv, j + 2, j + 1, a.part, wp);
-    lap(0);
-    if (!barrier()) break;
-    lap(1);
-    // ---- 2. first subtraction
-    // the host's request (or the end of the launch's chunk of steps), published
-    // to every block by the next barrier
-    if (lead) st->stop = *a.yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
-    sum_items(a.part, j + 2, h);
-    for (int c = threadIdx.x; c <= j; c += blockDim.x) {
-      const double hc = h[c] * sc[c];  // (v_c, w)
-      h[c] = hc;
-      coef[c] = (T)(hc * sc[c]);
-    }
-    __syncthreads();
-    const double ww = h[j + 1];
-    {
-      const T acc = block_sub<T>(br, V, ldv, j + 1, j + 1, coef);
-      if (a.always_reorth) {
-        block_dots<T>(br, V, ldv, j + 1, j + 1, a.part2, wp);
+    int second = 0;
+    if (a.mgs) {
+      // ---- 1-3 (modified Gram-Schmidt in groups of four): w = A v_j; per group
+      // B_k = [4k, 4k + R_k) one grid reduction of (v_c, w), then h_B = T_k (V_B^T w)
+      // and w -= V_B h_B in the pass that forms the next group's dot products.
+      // The block's rows of w stay in shared memory.
+      persist_spmv<T, F, TPV, true, false>(a, so, V + (int64_t)j * ldv, w, (T)sc[j], T(0),
+                                           nullptr);
+      if (!fused) {
+        if (!barrier()) break;
       } else {
-        const double s = block_sum_lean((double)acc, red);
-        if (threadIdx.x == 0) a.pn[blockIdx.x] = s;
+        __syncthreads();  // the block reads back the rows its threads wrote
       }
-    }
-    lap(2);
-    if (!barrier()) break;
-    lap(3);
-    // ---- 3. second pass where needed
-    int second = a.always_reorth;
-    if (!second) {
-      if (threadIdx.x < 32) {
-        const double w2 = warp_partials_cg(a.pn, gridDim.x);
-        if (threadIdx.x == 0) {
-          sh_w2 = w2;
-          sh_flag = !(w2 >= 0.5 * ww);
+      const int nb = (j + 4) >> 2;  // groups of the columns 0 .. j
+      double part4[4] = {0.0, 0.0, 0.0, 0.0};
+      if (threadIdx.x < kMgsThreads)
+        mgs_first<T>(j + 1 < 4 ? j + 1 : 4, br, V, ldv, ws, w, part4);
+      lap(0);
+      bool ok = true;
+      for (int k = 0;; ++k) {
+        // partials alternate between two buffers over consecutive rounds, so a
+        // round's writes never meet a slower block's reads of the round before
+        double* pr = a.part + (int64_t)(rounds++ & 1) * 4 * gridDim.x;
+        mgs_block_partials(part4, wp, pr);
+        if (!barrier()) {
+          ok = false;
+          break;
+        }
+        if (k == 0 && lead) st->stop = *a.yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
+        if (threadIdx.x < 128) {
+          const double t = warp_partials_cg(pr + (int64_t)(threadIdx.x >> 5) * gridDim.x,
+                                            gridDim.x);
+          if ((threadIdx.x & 31) == 0) rsum[threadIdx.x >> 5] = t;
+        }
+        __syncthreads();
+        if (k == nb) break;  // rsum[0] = ||w||^2, rsum[1 ..] its group's raw inner products
+        const int c0 = 4 * k, R = j + 1 - c0 < 4 ? j + 1 - c0 : 4;
+        if (threadIdx.x == 0) {  // h_B = T_k r by forward substitution
+          for (int i = 0; i < R; ++i) {
+            const int c = c0 + i;
+            double r = rsum[i] * sc[c];
+            for (int l = 0; l < i; ++l) r -= G[c * 4 + l] * h[c0 + l];
+            h[c] = r;
+            coef[i] = (T)(r * sc[c]);
+          }
+        }
+        __syncthreads();
+        if (threadIdx.x < kMgsThreads) {
+          if (k + 1 < nb) {
+            const int rn = j + 1 - (c0 + 4) < 4 ? j + 1 - (c0 + 4) : 4;
+            mgs_mid<T>(rn, br, V, ldv, c0, coef, ws, w, part4);
+          } else {
+            mgs_last<T>(R, br, V, ldv, c0, coef, ws, w, part4);
+          }
         }
       }
-      __syncthreads();
-      second = sh_flag;
-      if (second) {
-        block_dots<T>(br, V, ldv, j + 1, j + 1, a.part2, wp);
-        if (!barrier()) break;
+      if (!ok) break;
+      if (threadIdx.x == 0) {  // the new column's inner products within its group
+        sh_w2 = rsum[0];
+        const int q = j + 1, r = q & 3;
+        const double sq = rsum[0] > 0.0 ? 1.0 / sqrt(rsum[0]) : 0.0;
+        for (int l = 0; l < 4; ++l) {
+          const double gv = l < r ? rsum[1 + l] * sc[q - r + l] * sq : 0.0;
+          G[q * 4 + l] = gv;
+          if (lead) st->G[q * 4 + l] = gv;
+        }
       }
-    }
-    if (second) {
-      sum_items(a.part2, j + 1, h2);
+      lap(2);
+    } else {
+      // ---- 1. w = A v_j, first-pass dots
+      persist_spmv<T, F, TPV, true, false>(a, so, V + (int64_t)j * ldv, w, (T)sc[j], T(0),
+                                           nullptr);
+      if (!fused && !barrier()) break;
+      block_dots<T>(br, V, ldv, j + 2, j + 1, a.part, wp);
+      lap(0);
+      if (!barrier()) break;
+      lap(1);
+      // ---- 2. first subtraction
+      // the host's request (or the end of the launch's chunk of steps), published
+      // to every block by the next barrier
+      if (lead) st->stop = *a.yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
+      sum_items(a.part, j + 2, h);
       for (int c = threadIdx.x; c <= j; c += blockDim.x) {
-        const double hc = h2[c] * sc[c];
-        h2[c] = hc;
+        const double hc = h[c] * sc[c];  // (v_c, w)
+        h[c] = hc;
         coef[c] = (T)(hc * sc[c]);
       }
       __syncthreads();
-      const T acc = block_sub<T>(br, V, ldv, j + 1, j + 1, coef);
-      const double s = block_sum_lean((double)acc, red);
-      if (threadIdx.x == 0) a.pn[blockIdx.x] = s;
+      const double ww = h[j + 1];
+      {
+        const T acc = block_sub<T>(br, V, ldv, j + 1, j + 1, coef);
+        if (a.always_reorth) {
+          block_dots<T>(br, V, ldv, j + 1, j + 1, a.part2, wp);
+        } else {
+          const double s = block_sum_lean((double)acc, red);
+          if (threadIdx.x == 0) a.pn[blockIdx.x] = s;
+        }
+      }
+      lap(2);
       if (!barrier()) break;
-      if (threadIdx.x < 32) {
-        const double w2 = warp_partials_cg(a.pn, gridDim.x);
-        if (threadIdx.x == 0) sh_w2 = w2;
+      lap(3);
+      // ---- 3. second pass where needed
+      second = a.always_reorth;
+      if (!second) {
+        if (threadIdx.x < 32) {
+          const double w2 = warp_partials_cg(a.pn, gridDim.x);
+          if (threadIdx.x == 0) {
+            sh_w2 = w2;
+            sh_flag = !(w2 >= 0.5 * ww);
+          }
+        }
+        __syncthreads();
+        second = sh_flag;
+        if (second) {
+          block_dots<T>(br, V, ldv, j + 1, j + 1, a.part2, wp);
+          if (!barrier()) break;
+        }
+      }
+      if (second) {
+        sum_items(a.part2, j + 1, h2);
+        for (int c = threadIdx.x; c <= j; c += blockDim.x) {
+          const double hc = h2[c] * sc[c];
+          h2[c] = hc;
+          coef[c] = (T)(hc * sc[c]);
+        }
+        __syncthreads();
+        const T acc = block_sub<T>(br, V, ldv, j + 1, j + 1, coef);
+        const double s = block_sum_lean((double)acc, red);
+        if (threadIdx.x == 0) a.pn[blockIdx.x] = s;
+        if (!barrier()) break;
+        if (threadIdx.x < 32) {
+          const double w2 = warp_partials_cg(a.pn, gridDim.x);
+          if (threadIdx.x == 0) sh_w2 = w2;
+        }
       }
     }
     lap(4);
@@ -415,6 +596,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       }
     }
     __syncthreads();
+    if (a.mgs) lap(1);
     ++iters;
     ++j;
     if (sh_bad) break;  // breakdown: the status is recorded
@@ -493,10 +675,12 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
         sc[0] = beta > 0.0 ? 1.0 / beta : 0.0;
         g[0] = beta;
         for (int k = 1; k <= M; ++k) g[k] = 0.0;
+        for (int k = 0; k < 4 * (M + 1); ++k) G[k] = 0.0;
         if (lead) {
           st->beta = beta;
           st->g[0] = beta;
           for (int k = 1; k <= kMaxRestart; ++k) st->g[k] = 0.0;
+          for (int k = 0; k < 4 * (kMaxRestart + 1); ++k) st->G[k] = 0.0;
           st->inv = sc[0];
           st->jdone = 0;
           st->conv_est = 0;
@@ -532,24 +716,46 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
 }
 
 // ------------------------------------------------------------------ host
-static size_t gm_smem_bytes(int M) { return (size_t)GmSmem(M).total * sizeof(double); }
-
+// The launch: one 1024-thread block per SM.  FP64 solves orthogonalise with
+// modified Gram-Schmidt when a block's rows of w fit in shared memory next to
+// the cycle's small matrices (n up to about three million rows at m = 30):
+// half the FP64 FMAs of classical Gram-Schmidt applied twice, for one grid
+// reduction per column.  Otherwise (and in FP32, where the kernel is bound by
+// memory and synchronisation rather than by FMAs) classical Gram-Schmidt with
+// the conditional second pass.
 template <typename T, int F, int TPV>
 static void gm_launch_one(cp_ctx* ctx, GmPersistArgs<T>& a, cudaStream_t s) {
   auto kern = k_gm_persist<T, F, TPV>;
-  const size_t smem = gm_smem_bytes(a.mrest);
+  const int grid = ctx->num_sms < kMaxPartials ? ctx->num_sms : kMaxPartials;
+  constexpr int lshift = F == kPersistCsrVector ? 10 - ilog2(TPV) : 10;
+  const int64_t L = 1ll << lshift, S = (int64_t)grid * L;
+  const int64_t wrows = (a.n + S - 1) / S * L;  // most rows a block owns
+  cudaFuncAttributes fa{};
+  CP_CUDA(cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(kern)));
+  int optin = 0;
+  CP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+  const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  a.mgs = 0;
+  a.wrows = 0;
+  if (std::is_same<T, double>::value &&
+      (size_t)GmSmem(a.mrest, wrows).total * sizeof(double) <= room) {
+    a.mgs = 1;
+    a.wrows = wrows;
+  }
+  const size_t smem = (size_t)GmSmem(a.mrest, a.wrows).total * sizeof(double);
+  CP_REQUIRE(smem <= room, CP_ERR_UNSUPPORTED, "persistent GMRES: restart too long for shared memory");
   CP_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPersistBlock, smem));
   CP_REQUIRE(per_sm >= 1, CP_ERR_CUDA, "persistent GMRES kernel does not fit an SM");
-  int grid = ctx->num_sms * per_sm;
-  if (grid > kMaxPartials) grid = kMaxPartials;
   void* args[] = {&a};
   CP_CUDA(cudaMemsetAsync(&a.st->bar_count, 0, sizeof(unsigned), s));
   CP_CUDA(cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid),
                                       dim3(kPersistBlock), args, smem, s));
   ctx->launches.fetch_add(1, std::memory_order_relaxed);
+  trace("persistent GMRES: %s, %d blocks, %zu bytes of shared memory",
+        a.mgs ? "modified Gram-Schmidt" : "classical Gram-Schmidt", grid, smem);
 }
 
 template <typename T>

@@ -35,6 +35,12 @@ struct GmState {
   double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
   double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
   double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+  // inner products (v_q, v_c) of column q with the columns c before it in its
+  // aligned group of four, G[q * 4 + (c - 4 floor(q / 4))]: the persistent kernel's
+  // modified Gram-Schmidt applies a group's four projections in one pass with
+  // them.  Zero for columns made by the per-step kernels (orthogonal to working
+  // precision by the second Gram-Schmidt pass).
+  double G[(kMaxRestart + 1) * 4];
   double bb, beta, inv;  // ||b||^2, cycle start ||r||, 1 / current norm
   int done;              // converged (true residual of a cycle start)
   int halt;              // no further steps in this cycle
@@ -293,6 +299,8 @@ struct GmPersistArgs : PersistMat<T> {
   int mrest = 0;         // restart length m
   int mcyc = 0;          // length of the cycle the launch enters
   int chunk = 0;         // > 0: return at the step boundary after this many steps
+  int mgs = 0;           // orthogonalise with modified Gram-Schmidt (w in shared memory)
+  int64_t wrows = 0;     // with mgs: shared-memory capacity for a block's rows of w
   int true_check = 1;    // 0: a cycle whose estimate reached tol ends the solve (FP32 inner solves)
   int always_reorth = 0; // second Gram-Schmidt pass in every step (FP32)
   double tol2 = 0.0;

@@ -4,8 +4,10 @@ cycle ends and restarts) against the one-launch-per-step path and the oracle.
 Acceptance as for every solver test: the true relative residual of the GPU
 solution, recomputed by the oracle's SpMV, is <= 1e-10 and the solution is
 within 1e-7 (relative) of the oracle's GMRES(m) solution at the same
-tolerance.  The two GPU paths orthogonalise with classical Gram-Schmidt in a
-different summation order, so their iteration counts may differ by a few."""
+tolerance.  In FP64 the persistent kernel orthogonalises with modified
+Gram-Schmidt (in groups of four columns, one grid reduction per group), the
+per-step launches with classical Gram-Schmidt and a conditional second pass,
+so their iteration counts may differ by a few."""
 import functools
 
 import numpy as np
@@ -100,6 +102,19 @@ def test_persistent_gmres_rows_in_several_segments(ctx, cfg):
     A, b = system(56, 22)
     ref = reference(56, 22, 30)
     x, info = solve(ctx, A, b, restart=30, tol=1e-10, force=cfg)
+    assert info.status == 0 and info.persist_iters == info.iters
+    check(A, b, x, ref)
+    assert close_iters(info.iters, ref.iters), (info.iters, ref.iters)
+
+
+@pytest.mark.parametrize("m", [1, 3, 4, 9])
+def test_persistent_gmres_short_restarts(ctx, m):
+    """Restart lengths around the groups of four columns that the FP64 kernel's
+    modified Gram-Schmidt handles per grid reduction: one column (GMRES(1)), a
+    partial group, exactly one group, two full groups and a one-column group."""
+    A, b = system(10, 30)
+    ref = reference(10, 30, m)
+    x, info = solve(ctx, A, b, restart=m, tol=1e-10, force=C.config("DIA"), maxit=20000)
     assert info.status == 0 and info.persist_iters == info.iters
     check(A, b, x, ref)
     assert close_iters(info.iters, ref.iters), (info.iters, ref.iters)
