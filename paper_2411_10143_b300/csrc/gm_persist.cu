@@ -286,7 +286,8 @@ __device__ __forceinline__ void mgs_last(int rs, const BlockRows& br, const T* V
   }
 }
 
-static_assert(4 * (kMgsThreads / 32) <= 32 * 3, "warp-sum table too small for kMgsThreads");
+// min(max(v, 0), 4): columns of a group that exist
+__device__ __forceinline__ int clamp4(int v) { return v < 0 ? 0 : (v > 4 ? 4 : v); }
 
 // Block sums of four values held by the first kMgsThreads threads: each warp
 // folds its four with warp_sum4, four threads add the warps' results in order
@@ -301,11 +302,14 @@ __device__ __forceinline__ void mgs_block_partials(const double (&v)[4], double*
     if ((lane & 7) == 0) wp[((lane >> 3) & 3) * nw + (threadIdx.x >> 5)] = s;
   }
   __syncthreads();
-  if (threadIdx.x < 4) {
-    double t = 0.0;
-#pragma unroll
-    for (int k = 0; k < nw; ++k) t += wp[threadIdx.x * nw + k];
-    part[(int64_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
+  static_assert(nw == 16, "the tree below adds 16 warp sums per value");
+  if (threadIdx.x < 32) {  // lane l: value l / 8, warp sums l % 8 and l % 8 + 8, then a tree
+    const int q = threadIdx.x >> 3, m = threadIdx.x & 7;
+    double t = wp[q * nw + m] + wp[q * nw + m + 8];
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    if (m == 0) part[(int64_t)q * gridDim.x + blockIdx.x] = t;
   }
 }
 
@@ -422,15 +426,17 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
         __syncthreads();  // the block reads back the rows its threads wrote
       }
       const int nb = (j + 4) >> 2;  // groups of the columns 0 .. j
+      int rot = 0;                  // rotations applied to column j (helper thread)
       double part4[4] = {0.0, 0.0, 0.0, 0.0};
       if (threadIdx.x < kMgsThreads)
-        mgs_first<T>(j + 1 < 4 ? j + 1 : 4, br, V, ldv, ws, w, part4);
+        mgs_first<T>(clamp4(j + 1), br, V, ldv, ws, w, part4);
       lap(0);
       bool ok = true;
       for (int k = 0;; ++k) {
         // partials alternate between two buffers over consecutive rounds, so a
         // round's writes never meet a slower block's reads of the round before
         double* pr = a.part + (int64_t)(rounds++ & 1) * 4 * gridDim.x;
+        if (k > 0) lap(2);  // passes
         mgs_block_partials(part4, wp, pr);
         if (!barrier()) {
           ok = false;
@@ -445,26 +451,42 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
         __syncthreads();
         if (k == nb) break;  // rsum[0] = ||w||^2, rsum[1 ..] its group's raw inner products
         const int c0 = 4 * k, R = j + 1 - c0 < 4 ? j + 1 - c0 : 4;
-        if (threadIdx.x == 0) {  // h_B = T_k r by forward substitution
-          for (int i = 0; i < R; ++i) {
-            const int c = c0 + i;
-            double r = rsum[i] * sc[c];
-            for (int l = 0; l < i; ++l) r -= G[c * 4 + l] * h[c0 + l];
-            h[c] = r;
-            coef[i] = (T)(r * sc[c]);
+        if (threadIdx.x < 32) {  // h_B = T_k r: forward substitution, lane i on h_{c0+i}
+          const int i = threadIdx.x;
+          double r = i < R ? rsum[i] * sc[c0 + i] : 0.0;
+          for (int l = 0; l + 1 < R; ++l) {
+            const double hl = __shfl_sync(0xffffffffu, r, l);
+            if (i > l && i < R) r = fma(-G[(c0 + i) * 4 + l], hl, r);
+          }
+          if (i < R) {
+            h[c0 + i] = r;
+            coef[i] = (T)(r * sc[c0 + i]);
           }
         }
         __syncthreads();
+        lap(3);  // reductions, barriers, substitutions
+        if (threadIdx.x == kMgsThreads) {
+          // a thread outside the passes puts the group's coefficients into column j
+          // of the Hessenberg matrix and applies the earlier Givens rotations as far
+          // as the known entries allow, while the passes run
+          for (int i = 0; i < R; ++i) H[(c0 + i) * M + j] = h[c0 + i];
+          const int upto = c0 + R - 1 < j ? c0 + R - 1 : j;
+          for (; rot < upto; ++rot) {
+            const double p = H[rot * M + j], q = H[(rot + 1) * M + j];
+            H[rot * M + j] = cs[rot] * p + sn[rot] * q;
+            H[(rot + 1) * M + j] = -sn[rot] * p + cs[rot] * q;
+          }
+        }
         if (threadIdx.x < kMgsThreads) {
           if (k + 1 < nb) {
-            const int rn = j + 1 - (c0 + 4) < 4 ? j + 1 - (c0 + 4) : 4;
-            mgs_mid<T>(rn, br, V, ldv, c0, coef, ws, w, part4);
+            mgs_mid<T>(clamp4(j + 1 - (c0 + 4)), br, V, ldv, c0, coef, ws, w, part4);
           } else {
             mgs_last<T>(R, br, V, ldv, c0, coef, ws, w, part4);
           }
         }
       }
       if (!ok) break;
+      lap(3);
       if (threadIdx.x == 0) {  // the new column's inner products within its group
         sh_w2 = rsum[0];
         const int q = j + 1, r = q & 3;
@@ -549,11 +571,13 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
     if (threadIdx.x == 0) {
       const double hn2 = sh_w2;
       const double hn = sqrt(hn2);
-      for (int i = 0; i <= j; ++i) H[i * M + j] = h[i] + (second ? h2[i] : 0.0);
-      for (int i = 0; i < j; ++i) {
-        const double p = H[i * M + j], q = H[(i + 1) * M + j];
-        H[i * M + j] = cs[i] * p + sn[i] * q;
-        H[(i + 1) * M + j] = -sn[i] * p + cs[i] * q;
+      if (!a.mgs) {  // (the modified Gram-Schmidt branch has filled and rotated column j)
+        for (int i = 0; i <= j; ++i) H[i * M + j] = h[i] + (second ? h2[i] : 0.0);
+        for (int i = 0; i < j; ++i) {
+          const double p = H[i * M + j], q = H[(i + 1) * M + j];
+          H[i * M + j] = cs[i] * p + sn[i] * q;
+          H[(i + 1) * M + j] = -sn[i] * p + cs[i] * q;
+        }
       }
       const double p = H[j * M + j];
       const double den = sqrt(p * p + hn2);
