@@ -295,6 +295,12 @@ typedef struct {
   int32_t persist_chunk; /* > 0: a persistent launch returns to the host after this many
                             iterations (the host launches again to go on), e.g. to poll
                             for cancellation; 0: it runs to the end of the solve      */
+  int32_t gmres_orth;    /* persistent GMRES orthogonalisation: 0 = modified Gram-Schmidt
+                            in groups of four columns where a block's rows of the new
+                            vector fit in shared memory (n up to about 3 million rows
+                            in FP64 at m = 30), else 1; 1 = classical Gram-Schmidt
+                            with a second pass (conditional in FP64, always in FP32),
+                            as the one-launch-per-step kernels use               */
 } cp_solve_opts;
 
 typedef struct {

@@ -74,7 +74,7 @@ class SolveOpts(Structure):
                 ("precision", c_int32), ("inner_tol", c_double), ("max_outer", c_int32),
                 ("check_every", c_int32), ("profile", c_int32), ("iteration_kernel", c_int32),
                 ("force", POINTER(Config)), ("wait_limit_ms", c_double),
-                ("persist_chunk", c_int32)]
+                ("persist_chunk", c_int32), ("gmres_orth", c_int32)]
 
 
 class SolveInfo(Structure):

@@ -80,16 +80,17 @@ struct BlockRows {
 // Sums four values over the warp with six shuffles (halving the values held
 // per lane at each of the first two exchanges).  Lane l returns the warp
 // total of value q = (l >> 3) & 3.
-__device__ __forceinline__ double warp_sum4(double v0, double v1, double v2, double v3) {
+template <typename A>
+__device__ __forceinline__ A warp_sum4(A v0, A v1, A v2, A v3) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const bool h16 = lane & 16, h8 = lane & 8;
-  double k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
-  const double s0 = h16 ? v0 : v2, s1 = h16 ? v1 : v3;
+  A k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
+  const A s0 = h16 ? v0 : v2, s1 = h16 ? v1 : v3;
   k0 += __shfl_xor_sync(full, s0, 16);
   k1 += __shfl_xor_sync(full, s1, 16);
-  double k = h8 ? k1 : k0;
-  const double s = h8 ? k0 : k1;
+  A k = h8 ? k1 : k0;
+  const A s = h8 ? k0 : k1;
   k += __shfl_xor_sync(full, s, 8);
   k += __shfl_xor_sync(full, k, 4);
   k += __shfl_xor_sync(full, k, 2);
@@ -123,7 +124,7 @@ __device__ __forceinline__ void dot_units(const BlockRows& br, const T* V, int64
   double d[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int q = 0; q < R; ++q) d[q] = (double)acc[q];
-  const double s = warp_sum4(d[0], d[1], d[2], d[3]);
+  const double s = warp_sum4<double>(d[0], d[1], d[2], d[3]);
   const int q = (lane >> 3) & 3;
   if ((lane & 7) == 0 && q < R) wp[(c0 + q) * 32 + warp] = s;
 }
@@ -223,7 +224,7 @@ constexpr int kMgsThreads = 512;  // threads of a block that run the passes: hal
 
 template <typename T, int RS, int RD, bool FIRST, bool LAST>
 __device__ __forceinline__ void mgs_pass(const BlockRows& br, const T* V, int64_t ldv, int cs0,
-                                         int cd0, const T* kc, T* ws, T* wg, double (&out)[4]) {
+                                         int cd0, const T* kc, T* ws, T* wg, T (&out)[4]) {
   T acc[4] = {T(0), T(0), T(0), T(0)};
   T k[RS > 0 ? RS : 1];
 #pragma unroll
@@ -252,12 +253,12 @@ __device__ __forceinline__ void mgs_pass(const BlockRows& br, const T* V, int64_
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] = (double)acc[u];
+  for (int u = 0; u < 4; ++u) out[u] = acc[u];
 }
 
 template <typename T>
 __device__ __forceinline__ void mgs_first(int rd, const BlockRows& br, const T* V, int64_t ldv,
-                                          T* ws, T* wg, double (&out)[4]) {
+                                          T* ws, T* wg, T (&out)[4]) {
   switch (rd) {
     case 1: mgs_pass<T, 0, 1, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
     case 2: mgs_pass<T, 0, 2, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
@@ -267,7 +268,7 @@ __device__ __forceinline__ void mgs_first(int rd, const BlockRows& br, const T* 
 }
 template <typename T>
 __device__ __forceinline__ void mgs_mid(int rd, const BlockRows& br, const T* V, int64_t ldv,
-                                        int cs0, const T* kc, T* ws, T* wg, double (&out)[4]) {
+                                        int cs0, const T* kc, T* ws, T* wg, T (&out)[4]) {
   switch (rd) {
     case 1: mgs_pass<T, 4, 1, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
     case 2: mgs_pass<T, 4, 2, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
@@ -277,7 +278,7 @@ __device__ __forceinline__ void mgs_mid(int rd, const BlockRows& br, const T* V,
 }
 template <typename T>
 __device__ __forceinline__ void mgs_last(int rs, const BlockRows& br, const T* V, int64_t ldv,
-                                         int cs0, const T* kc, T* ws, T* wg, double (&out)[4]) {
+                                         int cs0, const T* kc, T* ws, T* wg, T (&out)[4]) {
   switch (rs) {
     case 1: mgs_pass<T, 1, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
     case 2: mgs_pass<T, 2, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
@@ -293,11 +294,12 @@ __device__ __forceinline__ int clamp4(int v) { return v < 0 ? 0 : (v > 4 ? 4 : v
 // folds its four with warp_sum4, four threads add the warps' results in order
 // and write the block's partials part[q * grid + block].  wp: 4 * kMgsThreads / 32
 // doubles (the kernel's warp-sum table holds at least 96).
-__device__ __forceinline__ void mgs_block_partials(const double (&v)[4], double* wp,
+template <typename T>
+__device__ __forceinline__ void mgs_block_partials(const T (&v)[4], double* wp,
                                                    double* part) {
   constexpr int nw = kMgsThreads / 32;
   if (threadIdx.x < kMgsThreads) {
-    const double s = warp_sum4(v[0], v[1], v[2], v[3]);
+    const double s = (double)warp_sum4<T>(v[0], v[1], v[2], v[3]);
     const int lane = threadIdx.x & 31;
     if ((lane & 7) == 0) wp[((lane >> 3) & 3) * nw + (threadIdx.x >> 5)] = s;
   }
@@ -317,8 +319,8 @@ __device__ __forceinline__ void mgs_block_partials(const double (&v)[4], double*
 // doubles: the one description both the kernel's carving and the host's size use.
 struct GmSmem {
   int64_t H, cs, sn, g, y, sc, h, h2, coef, wp, red, G, w, total;
-  // wrows: rows of w a block keeps in shared memory (modified Gram-Schmidt), or 0
-  __host__ __device__ constexpr GmSmem(int M, int64_t wrows)
+  // wdoubles: doubles that hold a block's rows of w (modified Gram-Schmidt), or 0
+  __host__ __device__ constexpr GmSmem(int M, int64_t wdoubles)
       : H(0),
         cs(H + (int64_t)(M + 1) * M),  // H: (M + 1) x M, H[i * M + j]
         sn(cs + M),
@@ -332,7 +334,7 @@ struct GmSmem {
         red(wp + 32 * (int64_t)(M + 2)),
         G(red + kPersistBlock + 4),  // G: (M + 1) x 4 group inner products
         w(G + 4 * (int64_t)(M + 1)),
-        total(w + wrows) {}
+        total(w + wdoubles) {}
 };
 
 template <typename T, int F, int TPV>
@@ -343,7 +345,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
   if (ld_cg(&st->done) || ld_cg(&st->halt)) return;
   extern __shared__ double dsm[];
   const int M = a.mrest;
-  const GmSmem L(M, a.wrows);
+  const GmSmem L(M, a.wdoubles);
   double* H = dsm + L.H;    // rotated Hessenberg matrix of the cycle, H[i * M + j]
   double* cs = dsm + L.cs;  // Givens rotations
   double* sn = dsm + L.sn;
@@ -427,7 +429,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       }
       const int nb = (j + 4) >> 2;  // groups of the columns 0 .. j
       int rot = 0;                  // rotations applied to column j (helper thread)
-      double part4[4] = {0.0, 0.0, 0.0, 0.0};
+      T part4[4] = {T(0), T(0), T(0), T(0)};
       if (threadIdx.x < kMgsThreads)
         mgs_first<T>(clamp4(j + 1), br, V, ldv, ws, w, part4);
       lap(0);
@@ -437,7 +439,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
         // round's writes never meet a slower block's reads of the round before
         double* pr = a.part + (int64_t)(rounds++ & 1) * 4 * gridDim.x;
         if (k > 0) lap(2);  // passes
-        mgs_block_partials(part4, wp, pr);
+        mgs_block_partials<T>(part4, wp, pr);
         if (!barrier()) {
           ok = false;
           break;
@@ -740,13 +742,13 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
 }
 
 // ------------------------------------------------------------------ host
-// The launch: one 1024-thread block per SM.  FP64 solves orthogonalise with
-// modified Gram-Schmidt when a block's rows of w fit in shared memory next to
-// the cycle's small matrices (n up to about three million rows at m = 30):
-// half the FP64 FMAs of classical Gram-Schmidt applied twice, for one grid
-// reduction per column.  Otherwise (and in FP32, where the kernel is bound by
-// memory and synchronisation rather than by FMAs) classical Gram-Schmidt with
-// the conditional second pass.
+// The launch: one 1024-thread block per SM.  The kernel orthogonalises with
+// modified Gram-Schmidt in groups of four when a block's rows of w fit in shared
+// memory next to the cycle's small matrices (FP64: n up to about three million
+// rows at m = 30, FP32 twice that): half the FMAs and passes of classical
+// Gram-Schmidt applied twice, for one grid reduction per group.  Larger systems
+// take classical Gram-Schmidt with the second pass (conditional in FP64, in
+// every step in FP32).
 template <typename T, int F, int TPV>
 static void gm_launch_one(cp_ctx* ctx, GmPersistArgs<T>& a, cudaStream_t s) {
   auto kern = k_gm_persist<T, F, TPV>;
@@ -759,14 +761,15 @@ static void gm_launch_one(cp_ctx* ctx, GmPersistArgs<T>& a, cudaStream_t s) {
   int optin = 0;
   CP_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
   const size_t room = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+  const bool want_mgs = a.mgs != 0;
   a.mgs = 0;
-  a.wrows = 0;
-  if (std::is_same<T, double>::value &&
-      (size_t)GmSmem(a.mrest, wrows).total * sizeof(double) <= room) {
+  a.wdoubles = 0;
+  const int64_t wdoubles = (wrows * (int64_t)sizeof(T) + 7) / 8;  // w region, in doubles
+  if (want_mgs && (size_t)GmSmem(a.mrest, wdoubles).total * sizeof(double) <= room) {
     a.mgs = 1;
-    a.wrows = wrows;
+    a.wdoubles = wdoubles;
   }
-  const size_t smem = (size_t)GmSmem(a.mrest, a.wrows).total * sizeof(double);
+  const size_t smem = (size_t)GmSmem(a.mrest, a.wdoubles).total * sizeof(double);
   CP_REQUIRE(smem <= room, CP_ERR_UNSUPPORTED, "persistent GMRES: restart too long for shared memory");
   CP_CUDA(cudaFuncSetAttribute(reinterpret_cast<const void*>(kern),
                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

@@ -678,6 +678,7 @@ struct ConfigSource {
   bool persistent = true;     // run CG iterations in the persistent kernel when it supports cfg
   double wait_limit_ms = 0.0; // bound of the persistent kernel's device waits (0: default)
   int persist_chunk = 0;      // iterations a persistent launch runs before returning (0: all)
+  int gmres_orth = 0;         // persistent GMRES: 0 modified Gram-Schmidt where it fits, 1 classical
   int persist_launches = 0;   // persistent launches made
   float t_persist_ms = 0.f;   // summed duration of the persistent launches
   int persist_iters = 0;      // iterations they ran
@@ -1000,6 +1001,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
         ga.mrest = mrest;
         ga.mcyc = steps;
         ga.chunk = cs.persist_chunk;
+        ga.mgs = cs.gmres_orth == 0 ? 1 : 0;  // a request; the launch checks that it fits
         ga.true_check = true_check ? 1 : 0;
         ga.always_reorth = std::is_same<T, float>::value ? 1 : 0;
         ga.tol2 = tol2;
@@ -1215,6 +1217,9 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
   cs.wait_limit_ms = opt.wait_limit_ms;
   CP_REQUIRE(opt.persist_chunk >= 0, CP_ERR_INVALID, "persist_chunk must be >= 0");
   cs.persist_chunk = opt.persist_chunk;
+  CP_REQUIRE(opt.gmres_orth == 0 || opt.gmres_orth == 1, CP_ERR_INVALID,
+             "gmres_orth must be 0 or 1");
+  cs.gmres_orth = opt.gmres_orth;
   cp_config_default(&cs.cur);
   if (opt.force) cs.cur = *opt.force;
   ensure_format(ctx, m, cs.cur, ctx->main);

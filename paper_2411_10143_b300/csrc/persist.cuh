@@ -299,8 +299,8 @@ struct GmPersistArgs : PersistMat<T> {
   int mrest = 0;         // restart length m
   int mcyc = 0;          // length of the cycle the launch enters
   int chunk = 0;         // > 0: return at the step boundary after this many steps
-  int mgs = 0;           // orthogonalise with modified Gram-Schmidt (w in shared memory)
-  int64_t wrows = 0;     // with mgs: shared-memory capacity for a block's rows of w
+  int mgs = 0;           // host: modified Gram-Schmidt wanted; kernel: in use (w in shared memory)
+  int64_t wdoubles = 0;  // with mgs: shared-memory doubles that hold a block's rows of w
   int true_check = 1;    // 0: a cycle whose estimate reached tol ends the solve (FP32 inner solves)
   int always_reorth = 0; // second Gram-Schmidt pass in every step (FP32)
   double tol2 = 0.0;

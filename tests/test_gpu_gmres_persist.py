@@ -4,10 +4,11 @@ cycle ends and restarts) against the one-launch-per-step path and the oracle.
 Acceptance as for every solver test: the true relative residual of the GPU
 solution, recomputed by the oracle's SpMV, is <= 1e-10 and the solution is
 within 1e-7 (relative) of the oracle's GMRES(m) solution at the same
-tolerance.  In FP64 the persistent kernel orthogonalises with modified
-Gram-Schmidt (in groups of four columns, one grid reduction per group), the
-per-step launches with classical Gram-Schmidt and a conditional second pass,
-so their iteration counts may differ by a few."""
+tolerance.  The persistent kernel orthogonalises with modified Gram-Schmidt
+(in groups of four columns, one grid reduction per group) unless gmres_orth = 1
+asks for classical Gram-Schmidt with a second pass, which is also what the
+per-step launches and the persistent kernel on systems too large for the
+shared-memory path use; iteration counts may differ by a few between them."""
 import functools
 
 import numpy as np
@@ -93,6 +94,21 @@ def test_persistent_gmres_matches_per_step_launches(ctx, cfg, m):
     assert close_iters(out[0].iters, out[1].iters), (out[0].iters, out[1].iters)
 
 
+@pytest.mark.parametrize("cfg", [C.config("CSR"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
+                                 C.config("SELL", sigma=1024), C.config("DIA")], ids=repr)
+@pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
+@pytest.mark.parametrize("m", [4, 30])
+def test_persistent_gmres_classical_orthogonalisation(ctx, cfg, precision, m):
+    """gmres_orth = 1: the persistent kernel's classical Gram-Schmidt with the
+    second pass (the path of systems whose rows do not fit in shared memory)."""
+    A, b = system(14, 31)
+    ref = reference(14, 31, m)
+    x, info = solve(ctx, A, b, restart=m, tol=1e-10, force=cfg, gmres_orth=1,
+                    precision=precision, inner_tol=1e-5)
+    assert info.status == 0 and info.persist_iters == info.iters
+    check(A, b, x, ref)
+
+
 @pytest.mark.parametrize("cfg", [C.config("DIA"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
                                  C.config("SELL", sigma=1024)], ids=repr)
 def test_persistent_gmres_rows_in_several_segments(ctx, cfg):
@@ -144,7 +160,7 @@ def test_persistent_gmres_tiny_system(ctx):
                                  C.config("SELL", sigma=1024)], ids=repr)
 def test_persistent_gmres_fp32_inner_solves(ctx, cfg):
     """FP64 refinement around FP32 GMRES(30) inner solves, every inner step in
-    the persistent kernel (second Gram-Schmidt pass in every step)."""
+    the persistent kernel."""
     A, b = system(20, 25)
     ref64 = reference(20, 25, 30)
     out = {}
