@@ -14,7 +14,9 @@ Printed JSON line: value = mean time-to-solution (ms, CUDA events around each
 solve on the main stream); plus the plain CSR-scalar CG and the sequential
 (predict-then-solve) and FP32-inner refinement variants, the SpMV roofline,
 the CPU oracle baseline, the end-to-end time through host buffers, clocks and
-kernel counts.
+kernel counts, and a GMRES(30) leg on convection-diffusion 96^3 (asynchronous
+cascade, FP32 inner solves, per-step launches, the persistent kernel's FP64
+FMA rate).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -165,8 +167,8 @@ def cg_iteration_bytes(A, fmt):
 # profiles/k_cg_persist_dia_poisson3d_128.md.
 PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
 PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
-                   "sha256": "bdda7387bcf823443d79014d5ea40143fd28684efb5fced4a7e7f077eb17a30d",
-                   "dram_bytes_per_iteration": 158400446.4}
+                   "sha256": "96fed50fa86fe4b682fd77e4d38bf96632764bd8a73130129f5c11db3284d30e",
+                   "dram_bytes_per_iteration": 158546926.7}
 
 
 def persist_sources_sha256():
@@ -426,6 +428,8 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
                   "h2d_bytes_per_step": int(rp.numel() * 4 + ci.numel() * 4 + va.numel() * 8
                                             + bh.numel() * 8),
                   "d2h_bytes_per_step": int(xh.numel() * 8)}
+    if not args.no_gmres:
+        res["gmres"] = gmres_bench(ctx)
     if not args.no_sweep:
         res["spmv_sweep"] = spmv_sweep_bench(ctx, measured_peaks()[0])
     if args.serve_requests > 0:
@@ -441,6 +445,84 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
                                "sample": f"{sample} single-threaded oracle CG iterations, "
                                          f"scaled to the {full} iterations of the full solve"}
     return res
+
+
+# ------------------------------------------------------------------ GMRES leg
+GMRES_GRID = 96
+GMRES_M = 30
+# FP64 FMA lanes per second of the B300: 2 per SM per clock (148 SMs, 2,032 MHz)
+FP64_DFMA_PEAK = 2 * 148 * 2.032e9
+
+
+def gmres_dfma(n, nnz, iters, m):
+    """Algorithmic FP64 FMAs of GMRES(m) with modified Gram-Schmidt over `iters`
+    Arnoldi steps: step j of a cycle costs nnz (SpMV) + (j + 1) n dot products +
+    (j + 1) n updates + n for the norm; a cycle of L steps adds L n for x += V y
+    and nnz + n for the restart residual and its norm."""
+    total, left = 0, iters
+    while left > 0:
+        L = min(m, left)
+        total += L * nnz + n * (L * L + 2 * L) + L * n + nnz + n
+        left -= L
+    return total
+
+
+def gmres_bench(ctx, reps=2):
+    """GMRES(30) on convection-diffusion 96^3 (n = 884,736): the asynchronous
+    cascade in FP64 and with FP32 inner solves, the one-launch-per-step CSR
+    iteration, and the persistent kernel with DIA forced, whose FP64 FMA rate
+    gives the roofline (the kernel is bound by the FP64 pipe)."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import workloads as W
+
+    A = W.convdiff3d(GMRES_GRID)
+    M = ctx.load(A)
+    xs = torch.as_tensor(W.vector(A.ncols, 2004), device="cuda")
+    b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    M.spmv(xs, b)
+    x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+
+    def timed(opts, force=None, reset=True):
+        ts, info = [], None
+        for _ in range(reps):
+            if reset:
+                M.reset()
+            x.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            info = M.solve_gmres(b, x, opts, force=force)
+            e1.record(ctx.stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts)), info
+
+    base = dict(tol=TOL, restart=GMRES_M)
+    async_ms, a = timed(C.default_opts(mode=C.MODE_ASYNC, **base))
+    ir_ms, ir = timed(C.default_opts(mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
+                                     inner_tol=1e-5, **base))
+    step_ms, st = timed(C.default_opts(mode=C.MODE_PLAIN, iteration_kernel=1, **base))
+    dia = C.config("DIA")
+    M.convert(dia)
+    dia_ms, d = timed(C.default_opts(mode=C.MODE_PLAIN, **base), force=dia, reset=False)
+    flops = gmres_dfma(A.nrows, A.nnz, d.persist_iters, GMRES_M)
+    rate = flops / (d.t_persist_ms * 1e-3)
+    return {
+        "workload": f"GMRES({GMRES_M}), convection-diffusion {GMRES_GRID}^3 (n={A.nrows:,}, "
+                    f"nnz={A.nnz:,}), FP64, rel. residual {TOL:g}, b = A x*, x0 = 0",
+        "async_ms": async_ms, "iters": a.iters, "final_cfg": repr(a.final_cfg),
+        "relres_true": a.relres_true, "persist_iters": a.persist_iters,
+        "fp32_ir_async_ms": ir_ms, "fp32_ir": {"outer": ir.outer_iters, "inner": ir.iters,
+                                               "relres_true": ir.relres_true},
+        "per_step_launches_csr_ms": step_ms, "per_step_launches": st.n_launches,
+        "persistent_dia_ms": dia_ms,
+        "roofline": {"kernel": "k_gm_persist (DIA, FP64, modified Gram-Schmidt)", "bound": "alu",
+                     "achieved": rate / 1e9, "peak": FP64_DFMA_PEAK / 1e9,
+                     "unit": "G FP64 FMA/s", "frac": rate / FP64_DFMA_PEAK,
+                     "fma_per_solve": flops,
+                     "peak_note": "2 FP64 FMA per SM per clock x 148 SMs x 2,032 MHz"},
+    }
 
 
 # ------------------------------------------------------------------ serving leg
@@ -654,6 +736,41 @@ def run_profile_cg(args):
                           "relres_true": info.relres_true}), flush=True)
 
 
+def run_profile_gmres(args):
+    """Forced-configuration GMRES(30) solves on the GMRES leg's workload
+    (convection-diffusion 96^3), plain mode, so one persistent launch runs the
+    whole solve (the case the GMRES profile under profiles/ captures).  Prints
+    one JSON line per solve; not a bench line."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import workloads as W
+
+    ctx = C.Context(0)
+    A = W.convdiff3d(GMRES_GRID)
+    M = ctx.load(A)
+    xs = torch.as_tensor(W.vector(A.ncols, 2004), device="cuda")
+    b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    M.spmv(xs, b)
+    cfg = C.config(args.profile_gmres)
+    M.convert(cfg)
+    opts = C.default_opts(tol=TOL, mode=C.MODE_PLAIN, restart=GMRES_M,
+                          precision=args.profile_precision, inner_tol=1e-5)
+    for k in range(args.steps):
+        x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        info = M.solve_gmres(b, x, opts, force=cfg)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        print(json.dumps({"solve": k, "config": repr(cfg), "precision": args.profile_precision,
+                          "ms": e0.elapsed_time(e1), "iters": info.iters,
+                          "persist_iters": info.persist_iters, "t_persist_ms": info.t_persist_ms,
+                          "us_per_step": info.t_persist_ms * 1e3 / max(info.persist_iters, 1),
+                          "relres_true": info.relres_true}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -666,15 +783,22 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain / sequential / FP32-IR / end-to-end / CPU legs")
     ap.add_argument("--no-sweep", action="store_true", help="skip the SpMV sweep leg")
+    ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES leg")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="profiling aid: the predicted SpMV of each sweep matrix, 3 launches")
     ap.add_argument("--profile-cg", default=None, metavar="FMT",
                     help="profiling aid: forced-configuration CG solves (e.g. DIA), no bench line")
     ap.add_argument("--profile-precision", type=int, default=0,
                     help="with --profile-cg: 0 FP64, 1 FP32 inner solves in FP64 refinement")
+    ap.add_argument("--profile-gmres", default=None, metavar="FMT",
+                    help="profiling aid: forced-configuration GMRES(30) solves on "
+                         "convection-diffusion 96^3, no bench line")
     args = ap.parse_args()
     if args.profile_cg:
         run_profile_cg(args)
+        return
+    if args.profile_gmres:
+        run_profile_gmres(args)
         return
     if args.profile_spmv:
         from paper_2411_10143_b300 import cascade as C

@@ -46,6 +46,7 @@
 
 #include "common.cuh"
 #include "internal.cuh"
+#include "gm_state.cuh"
 #include "persist.cuh"
 #include "spmv_rows.cuh"
 
