@@ -219,6 +219,8 @@ cp_status cp_destroy(cp_ctx* ctx) {
     if (ctx->own_side) cudaStreamDestroy(ctx->side);
     if (ctx->pin_main) cudaFreeHost(ctx->pin_main);
     if (ctx->pin_side) cudaFreeHost(ctx->pin_side);
+    ctx->mapped.release();
+    ctx->events.release();
     delete ctx;
   });
 }

@@ -8,9 +8,11 @@
 #include <functional>
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 #include <string>
 #include <thread>
+#include <vector>
 
 #include "cascade.h"
 
@@ -130,6 +132,78 @@ constexpr int kDiaMax = 1024;  // most diagonals a DIA conversion accepts
 namespace cp {
 // The side thread of the asynchronous mode ("thread 2" of Sec. III-C-2), kept
 // alive for the context's lifetime and bound to its GPU, so that starting the
+// Host-mapped pages a context reuses across solves (each solve's mirror and
+// yield flag).  cudaHostAlloc takes hundreds of microseconds and cudaFreeHost
+// waits for the device, both inside a solve's time, so the pages are kept.
+class MappedPool {
+ public:
+  static constexpr size_t kPage = 4096;
+  void* take() {  // a zeroed page; its device view is cudaHostGetDevicePointer's
+    void* p = nullptr;
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      if (!free_.empty()) {
+        p = free_.back();
+        free_.pop_back();
+      }
+    }
+    if (!p) {
+      CP_CUDA(cudaHostAlloc(&p, kPage, cudaHostAllocMapped));
+      std::lock_guard<std::mutex> lock(mu_);
+      all_.push_back(p);
+    }
+    std::memset(p, 0, kPage);
+    return p;
+  }
+  void give(void* p) {
+    std::lock_guard<std::mutex> lock(mu_);
+    free_.push_back(p);
+  }
+  void release() {  // at context destruction, with no solve running
+    for (void* p : all_) cudaFreeHost(p);
+    all_.clear();
+    free_.clear();
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<void*> free_, all_;
+};
+
+// CUDA events a context reuses across solves (the profiling pairs around SpMV
+// launches, the host's look-ahead ring, the persistent launches' timers).
+class EventPool {
+ public:
+  cudaEvent_t take(bool timing) {
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      auto& v = timing ? timing_ : plain_;
+      if (!v.empty()) {
+        cudaEvent_t e = v.back();
+        v.pop_back();
+        return e;
+      }
+    }
+    cudaEvent_t e = nullptr;
+    CP_CUDA(cudaEventCreateWithFlags(&e, timing ? cudaEventDefault : cudaEventDisableTiming));
+    return e;
+  }
+  void give(cudaEvent_t e, bool timing) {
+    std::lock_guard<std::mutex> lock(mu_);
+    (timing ? timing_ : plain_).push_back(e);
+  }
+  void release() {
+    for (auto e : timing_) cudaEventDestroy(e);
+    for (auto e : plain_) cudaEventDestroy(e);
+    timing_.clear();
+    plain_.clear();
+  }
+
+ private:
+  std::mutex mu_;
+  std::vector<cudaEvent_t> timing_, plain_;
+};
+
 // cascade costs a wake-up (tens of microseconds), not a thread creation and a
 // device binding (up to a millisecond, longer than a small solve).  One job at
 // a time: post() hands it over, wait() returns when it has finished.
@@ -168,6 +242,8 @@ struct cp_ctx {
   cp_gate gate{};  // cost-aware switching (disabled until installed)
   std::atomic<int> inject_side_fail{-1};  // host fault injection point (tests), -1: none
   cp::SideWorker* side_worker = nullptr;
+  cp::MappedPool mapped;  // host-mapped pages reused by the solves
+  cp::EventPool events;   // CUDA events reused by the solves
 };
 
 struct cp_mat {

@@ -569,7 +569,12 @@ struct GmBufs {
 };
 
 // Device and host-mapped work areas of one solve (buffers are made once and
-// reused by every inner solve of an iterative refinement).
+// reused by every inner solve of an iterative refinement).  Device buffers come
+// from the stream-ordered pool on the solve's stream (the context keeps the
+// pool's memory, so an allocation is a pool hit) and go back to it in stream
+// order; the host-mapped page and the events come from the context's pools.  A
+// solve then spends no time in cudaMalloc / cudaFree / cudaHostAlloc, whose
+// frees wait for the whole device.
 struct Workspace {
   cp_ctx* ctx;
   std::vector<void*> dev;
@@ -616,41 +621,42 @@ struct Workspace {
   }
   template <typename U>
   U* get(size_t count) {
-    U* p = dalloc<U>(count);
+    U* p = dalloc_async<U>(count, ctx->main);
     dev.push_back(p);
     return p;
+  }
+  // one host-mapped page: the mirror at its start, the yield flag after it
+  void* page = nullptr;
+  char* page_d = nullptr;
+  static constexpr size_t kYieldOffset = 1024;
+  static_assert(sizeof(Mirror) <= kYieldOffset, "mirror overlaps the yield flag");
+  void map_page() {
+    if (page) return;
+    page = ctx->mapped.take();
+    CP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&page_d), page, 0));
+    mir = static_cast<Mirror*>(page);
+    mir_d = reinterpret_cast<Mirror*>(page_d);
+    yield_h = reinterpret_cast<int*>(static_cast<char*>(page) + kYieldOffset);
+    yield_d = reinterpret_cast<int*>(page_d + kYieldOffset);
   }
   int* yield_h = nullptr;  // host-mapped flag asking the persistent kernel to return
   int* yield_d = nullptr;
   int* yield() {
-    if (!yield_h) {
-      CP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&yield_h), sizeof(int), cudaHostAllocMapped));
-      *yield_h = 0;
-      CP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&yield_d), yield_h, 0));
-    }
+    map_page();
     return yield_d;
   }
   Mirror* mirror() {
-    if (!mir) {
-      CP_CUDA(cudaHostAlloc(reinterpret_cast<void**>(&mir), sizeof(Mirror), cudaHostAllocMapped));
-      std::memset((void*)mir, 0, sizeof(Mirror));
-      CP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&mir_d), mir, 0));
-    }
+    map_page();
     return mir_d;
   }
   cudaEvent_t event(int i, int depth) {
-    while ((int)ring.size() < depth) {
-      cudaEvent_t e;
-      CP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-      ring.push_back(e);
-    }
+    while ((int)ring.size() < depth) ring.push_back(ctx->events.take(false));
     return ring[i % depth];
   }
   ~Workspace() {
-    for (void* p : dev) cudaFree(p);
-    for (auto e : ring) cudaEventDestroy(e);
-    if (mir) cudaFreeHost((void*)mir);
-    if (yield_h) cudaFreeHost(yield_h);
+    for (void* p : dev) dfree_async(p, ctx->main);
+    for (auto e : ring) ctx->events.give(e, false);
+    if (page) ctx->mapped.give(page);
   }
 };
 
@@ -708,11 +714,7 @@ struct ConfigSource {
     if (!profile) return;
     const size_t need = 2 * (size_t)(n_spmv + 1);
     while (ev.size() < need) {
-      for (int q = 0; q < 256; ++q) {
-        cudaEvent_t e;
-        CP_CUDA(cudaEventCreate(&e));
-        ev.push_back(e);
-      }
+      for (int q = 0; q < 256; ++q) ev.push_back(ctx->events.take(true));
     }
     CP_CUDA(cudaEventRecord(ev[2 * n_spmv], s));
   }
@@ -730,7 +732,7 @@ struct ConfigSource {
     return tot;
   }
   ~ConfigSource() {
-    for (auto e : ev) cudaEventDestroy(e);
+    for (auto e : ev) ctx->events.give(e, true);
   }
 };
 
@@ -823,9 +825,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         pa_args.tol2 = tol2;
         if (cs.wait_limit_ms > 0.0)
           pa_args.barrier_timeout_ns = (long long)(cs.wait_limit_ms * 1e6);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        CP_CUDA(cudaEventCreate(&e0));
-        CP_CUDA(cudaEventCreate(&e1));
+        cudaEvent_t e0 = ctx->events.take(true), e1 = ctx->events.take(true);
         CP_CUDA(cudaEventRecord(e0, s));
         trace("solve: persistent launch at iteration %d (format %d)", it, cs.cur.fmt);
         persist_launch<T>(ctx, m, cs.cur, pa_args, s, 1);
@@ -846,8 +846,8 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         }
         float t = 0.f;
         CP_CUDA(cudaEventElapsedTime(&t, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        ctx->events.give(e0, true);
+        ctx->events.give(e1, true);
         cs.t_persist_ms += t;
         cs.persist_iters += ws.mir->iters - it;
         cs.t_persist_last_ms = t;
@@ -1009,9 +1009,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
         if (cs.wait_limit_ms > 0.0)
           ga.barrier_timeout_ns = (long long)(cs.wait_limit_ms * 1e6);
         const int it_before = res.iters + j;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        CP_CUDA(cudaEventCreate(&e0));
-        CP_CUDA(cudaEventCreate(&e1));
+        cudaEvent_t e0 = ctx->events.take(true), e1 = ctx->events.take(true);
         CP_CUDA(cudaEventRecord(e0, s));
         trace("solve: persistent GMRES launch at step %d of the cycle (format %d)", j,
               cs.cur.fmt);
@@ -1031,8 +1029,8 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
         }
         float t = 0.f;
         CP_CUDA(cudaEventElapsedTime(&t, e0, e1));
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
+        ctx->events.give(e0, true);
+        ctx->events.give(e1, true);
         const int kind = ws.mir->exit_kind;
         const int ran = ws.mir->iters - it_before;
         cs.t_persist_ms += t;
