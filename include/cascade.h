@@ -361,6 +361,18 @@ typedef struct {
   int32_t enabled;                    /* 0: always switch (the paper's behaviour)        */
 } cp_gate;
 
+/* cp_warmup: runs, once, every kernel a solve can launch -- features, the
+ * cascade's inference when models are installed, each format's conversion and
+ * SpMV in FP64 and FP32, CG and GMRES in both precisions on the persistent and
+ * the per-step paths, and an asynchronous solve of each -- on a small internal
+ * system (3D Poisson 10^3), so that no later solve pays the one-time cost of a
+ * kernel's first launch in the process (the CUDA runtime loads kernels lazily;
+ * measured: a first asynchronous GMRES(30) solve of 86 ms against 59 ms for the
+ * next).  Takes about 0.1-0.3 s; the solves' time-to-solution (Sec. IV) assumes
+ * it was made.  cp_server_create calls it.  Blocking; uses ctx's streams.
+ * Errors: CP_ERR_CUDA, CP_ERR_OOM. */
+cp_status cp_warmup(cp_ctx* ctx);
+
 /* Fault injection on the host, for tests of the asynchronous mode's recovery:
  * the next solve's prediction side thread raises an error at `point` (0: before
  * the feature pass, 1: after it, 2: after the FORMAT stage, before any

@@ -188,6 +188,7 @@ _SIGS = {
                                  _p]),
     "cp_gate_set": (c_int32, [_p, _p]),
     "cp_inject_side_failure": (c_int32, [_p, c_int32]),
+    "cp_warmup": (c_int32, [_p]),
     "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
                                  POINTER(c_double), POINTER(c_double)]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
@@ -419,6 +420,12 @@ class Context:
             _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
                                        _ptr(ms)))
         return best.value, ms.tolist()
+
+    def warmup(self):
+        """cp_warmup: launch every solve-path kernel once on a small system, so that
+        no timed solve pays a kernel's one-time first-launch cost."""
+        with self.ordered():
+            _check(lib().cp_warmup(self._h))
 
     def inject_side_failure(self, point):
         """cp_inject_side_failure (tests): the next solve's side thread fails at point."""

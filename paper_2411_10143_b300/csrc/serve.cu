@@ -257,6 +257,15 @@ cp_status cp_server_create(cp_ctx* ctx, const cp_server_opts* opts, cp_server** 
                    S->opts.restart >= 1 && S->opts.restart <= 32 && S->opts.mem_budget > 0,
                CP_ERR_INVALID, "bad server options");
     S->parent = ctx;
+    // the lanes share this process's loaded kernels: load them once, before the
+    // first request's time starts
+    {
+      const cp_status ws = cp_warmup(ctx);
+      if (ws != CP_OK) {
+        delete S;
+        return ws;
+      }
+    }
     S->t0 = std::chrono::steady_clock::now();
     const int L = S->opts.lanes;
     S->lane_jobs.resize(L);

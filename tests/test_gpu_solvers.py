@@ -342,3 +342,38 @@ def test_prediction_side_failure_leaves_the_solve_on_the_default_kernel(point):
     x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
     assert info.side_status == 0 and info.final_cfg.fmt == C.FMT_ELL
     c.close()
+
+
+def test_warmup_makes_the_first_solve_as_fast_as_the_next():
+    """cp_warmup launches every solve-path kernel once on its own small system
+    (with and without installed models).  After it, the process's first
+    asynchronous GMRES(30) solve of a mid-size system takes about what the
+    second does: no kernel's first-launch cost lands inside a solve."""
+    import time
+    from paper_2411_10143_b300 import models
+    bare = C.Context(0)
+    bare.warmup()  # no models installed: the cascade's inference is skipped
+    bare.close()
+    c = C.Context(0)
+    models.load_default(c)
+    t0 = time.perf_counter()
+    c.warmup()
+    assert time.perf_counter() - t0 < 10.0
+    A = W.convdiff3d(48)
+    b = rhs(A, 46)
+    M = c.load(A)
+    bd = torch.as_tensor(b, device="cuda")
+    times = []
+    for _ in range(2):
+        M.reset()
+        xd = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        info = M.solve_gmres(bd, xd, C.default_opts(tol=1e-10, restart=30, mode=C.MODE_ASYNC))
+        e1.record(c.stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+        assert info.status == 0 and true_relres(A, xd.cpu().numpy(), b) <= 1e-10
+    assert times[0] <= 1.5 * times[1] + 3.0, times
+    c.close()
