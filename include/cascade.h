@@ -475,6 +475,12 @@ typedef struct {
   int32_t lanes;        /* concurrent jobs on the device, 1..32                 */
   int32_t mode;         /* CP_MODE_* of the full-GPU solver for large requests  */
   int64_t mem_budget;   /* bytes of solver workspace admitted at once           */
+  int32_t small_max_n_gmres; /* GMRES requests are batched only up to this many rows
+                           (<= small_max_n; default 8192): a batched system's
+                           Krylov basis is streamed from HBM every step while
+                           the batch's other systems share the bandwidth, so a
+                           mid-size GMRES request is served faster by the
+                           full-GPU persistent solver                          */
 } cp_server_opts;
 typedef struct {
   int64_t id;           /* caller's tag, returned in the result                 */

@@ -137,7 +137,8 @@ def gate_decide(gate: Gate, fmt, nnz, iters, res0, res, target):
 class ServerOpts(Structure):
     _fields_ = [("tol", c_double), ("inner_tol", c_double), ("restart", c_int32),
                 ("maxit", c_int32), ("small_max_n", c_int32), ("max_batch", c_int32),
-                ("lanes", c_int32), ("mode", c_int32), ("mem_budget", c_int64)]
+                ("lanes", c_int32), ("mode", c_int32), ("mem_budget", c_int64),
+                ("small_max_n_gmres", c_int32)]
 
 
 class Request(Structure):

@@ -4,13 +4,15 @@
 // any time.  A scheduler thread admits them while their Krylov workspace fits
 // the HBM budget and hands work to `lanes` worker threads, each with its own
 // context and streams, so several solves run on the device at once:
-//  - a request with n <= small_max_n joins the next batch: a free lane takes
+//  - a request with n <= small_max_n (GMRES: small_max_n_gmres) joins the next
+//    batch: a free lane takes
 //    every admitted small request (up to max_batch) into one persistent,
 //    graph-captured batched launch (cp_batch_solve's kernel);
 //  - a larger request gets a lane of its own and runs the asynchronous
 //    cascaded solver with FP32 inner solves inside FP64 refinement.
 // Requests that arrive while others run are admitted as soon as a lane and
 // memory free up.  Every completion records submit / start / done times.
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -53,11 +55,17 @@ struct cp_server {
 
 namespace cp {
 
+// Whether a request joins a batch (else it gets a lane of its own).
+static bool batched(const cp_request& r, const cp_server_opts& o) {
+  const int64_t lim = r.solver == 1 ? std::min(o.small_max_n, o.small_max_n_gmres) : o.small_max_n;
+  return r.mat->nrows <= lim;
+}
+
 // Device workspace a request needs while it runs (its matrix is already resident).
 static int64_t request_bytes(const cp_request& r, const cp_server_opts& o) {
   const int64_t n = r.mat->nrows;
   const int64_t m = o.restart > 0 ? o.restart : 30;
-  if (n <= o.small_max_n) return n * 8 + (r.solver == 0 ? 4 : m + 2) * n * 4;
+  if (batched(r, o)) return n * 8 + (r.solver == 0 ? 4 : m + 2) * n * 4;
   // full-GPU solver: FP64 refinement vectors + FP32 inner (CG 3n, GMRES (m+2)n)
   return 4 * n * 8 + (r.solver == 0 ? 3 : m + 2) * n * 4 + n * 4 + r.mat->nnz * 4;
 }
@@ -175,7 +183,7 @@ static void scheduler_loop(cp_server* S) {
     cp_server::Job job;
     job.t_admit = S->now_ms();
     const cp_request& head = S->pending.front();
-    if (head.mat->nrows > o.small_max_n) {
+    if (!batched(head, o)) {
       const int64_t need = request_bytes(head, o);
       if (S->in_use_bytes + need > o.mem_budget && S->in_use_bytes > 0) {
         // wait for memory to free up (a running job will notify)
@@ -201,7 +209,7 @@ static void scheduler_loop(cp_server* S) {
         S->pending.pop_front();
         S->pending_submit.pop_front();
         const int64_t need = request_bytes(r, o);
-        if (r.mat->nrows <= o.small_max_n && (int)job.reqs.size() < o.max_batch &&
+        if (batched(r, o) && (int)job.reqs.size() < o.max_batch &&
             S->in_use_bytes + job.bytes + need <= o.mem_budget) {
           job.reqs.push_back(r);
           job.t_submit.push_back(ts);
@@ -240,6 +248,7 @@ void cp_server_opts_default(cp_server_opts* o) {
   o->restart = 30;
   o->maxit = 100000;
   o->small_max_n = 32768;
+  o->small_max_n_gmres = 8192;
   o->max_batch = 256;
   o->lanes = 4;
   o->mem_budget = int64_t(16) << 30;
