@@ -78,24 +78,27 @@ struct BlockRows {
   }
 };
 
-// Sums four values over the warp with six shuffles (halving the values held
-// per lane at each of the first two exchanges).  Lane l returns the warp
-// total of value q = (l >> 3) & 3.
-template <typename A>
-__device__ __forceinline__ A warp_sum4(A v0, A v1, A v2, A v3) {
+// Sums G values (G = 2, 4, 8 or 16) over the warp: at each of the first log2(G)
+// exchanges a lane keeps half of its values and adds its partner's copies of
+// them, then plain butterfly levels follow.  Lane l returns the warp total of
+// value q = l / (32 / G).
+template <int G, typename A>
+__device__ __forceinline__ A warp_sum_group(A (&v)[G]) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const bool h16 = lane & 16, h8 = lane & 8;
-  A k0 = h16 ? v2 : v0, k1 = h16 ? v3 : v1;
-  const A s0 = h16 ? v0 : v2, s1 = h16 ? v1 : v3;
-  k0 += __shfl_xor_sync(full, s0, 16);
-  k1 += __shfl_xor_sync(full, s1, 16);
-  A k = h8 ? k1 : k0;
-  const A s = h8 ? k0 : k1;
-  k += __shfl_xor_sync(full, s, 8);
-  k += __shfl_xor_sync(full, k, 4);
-  k += __shfl_xor_sync(full, k, 2);
-  k += __shfl_xor_sync(full, k, 1);
+#pragma unroll
+  for (int n = G, sp = 16; n > 1; n >>= 1, sp >>= 1) {
+    const bool hi = lane & sp;
+#pragma unroll
+    for (int u = 0; u < n / 2; ++u) {
+      const A keep = hi ? v[u + n / 2] : v[u];
+      const A send = hi ? v[u] : v[u + n / 2];
+      v[u] = keep + __shfl_xor_sync(full, send, sp);
+    }
+  }
+  A k = v[0];
+#pragma unroll
+  for (int sp = 16 / G; sp >= 1; sp >>= 1) k += __shfl_xor_sync(full, k, sp);
   return k;
 }
 
@@ -125,7 +128,7 @@ __device__ __forceinline__ void dot_units(const BlockRows& br, const T* V, int64
   double d[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
   for (int q = 0; q < R; ++q) d[q] = (double)acc[q];
-  const double s = warp_sum4<double>(d[0], d[1], d[2], d[3]);
+  const double s = warp_sum_group<4, double>(d);
   const int q = (lane >> 3) & 3;
   if ((lane & 7) == 0 && q < R) wp[(c0 + q) * 32 + warp] = s;
 }
@@ -208,25 +211,48 @@ __device__ __forceinline__ T block_sub(const BlockRows& br, T* V, int64_t ldv, i
   return acc;
 }
 
-// Modified Gram-Schmidt in groups of four columns.  For unit vectors v_c the
-// product of the projections (I - v_{c+3} v_{c+3}^T) ... (I - v_c v_c^T) equals
-// I - V T V^T with V = [v_c .. v_{c+3}] and T = (I + L)^{-1}, L the strictly
-// lower part of V^T V (the compact WY form, exact for any unit vectors).  So
-// h = T V^T w, a forward substitution with the group's inner products (v_q,
-// v_c), gives the coefficients modified Gram-Schmidt computes one column at a
-// time, and the group costs one grid reduction instead of four.  A pass over
-// the block's rows subtracts one group and forms the dot products of the next
-// (or, after the last group, ||w||^2 and the new column's inner products with
-// the columns of its own group, the entries of L its group will need).
+// Modified Gram-Schmidt in groups of G columns.  For unit vectors v_c the
+// product of the projections (I - v_{c+G-1} v_{c+G-1}^T) ... (I - v_c v_c^T)
+// equals I - V T V^T with V = [v_c .. v_{c+G-1}] and T = (I + L)^{-1}, L the
+// strictly lower part of V^T V (the compact WY form, exact for any unit
+// vectors).  So h = T V^T w, a forward substitution with the group's inner
+// products (v_q, v_c), gives the coefficients modified Gram-Schmidt computes one
+// column at a time, and the group costs one grid reduction instead of G.  A
+// pass over the block's rows subtracts one group and forms the dot products of
+// the next (or, after the last group, ||w||^2 and the new column's inner
+// products with the columns of its own group, the entries of L its group will
+// need).  G = 4 in FP64 (a pass holds 2G values a row in registers, and FP64
+// halves what fits) and 8 in FP32, where the rounds' synchronisation, not the
+// passes, is the larger cost.
 constexpr int kMgsThreads = 512;  // threads of a block that run the passes: half the
                                   // FP64 partials to reduce of 1024, and still
                                   // enough loads in flight (512 measured fastest of
                                   // 256 / 512 / 1024 on 884,736 rows)
+constexpr int kMgsGroupMax = 8;   // the Gram entries' stride in the solver state
 
-template <typename T, int RS, int RD, bool FIRST, bool LAST>
+template <typename T>
+struct MgsGroup {
+  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
+};
+
+// Calls f(IntC<r>) for the runtime r in [R, MAX] (group sizes: exact register
+// counts, no padding lanes of FP64 work).
+template <int R, int MAX, typename F>
+__device__ __forceinline__ void dispatch_r(int r, F&& f) {
+  if constexpr (R >= MAX) {
+    f(IntC<MAX>{});
+  } else {
+    if (r == R) f(IntC<R>{});
+    else dispatch_r<R + 1, MAX>(r, f);
+  }
+}
+
+template <typename T, int G, int RS, int RD, bool FIRST, bool LAST>
 __device__ __forceinline__ void mgs_pass(const BlockRows& br, const T* V, int64_t ldv, int cs0,
-                                         int cd0, const T* kc, T* ws, T* wg, T (&out)[4]) {
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+                                         int cd0, const T* kc, T* ws, T* wg, T (&out)[G]) {
+  T acc[G];
+#pragma unroll
+  for (int u = 0; u < G; ++u) acc[u] = T(0);
   T k[RS > 0 ? RS : 1];
 #pragma unroll
   for (int u = 0; u < RS; ++u) k[u] = kc[u];
@@ -243,7 +269,7 @@ __device__ __forceinline__ void mgs_pass(const BlockRows& br, const T* V, int64_
     if (LAST) {
       wg[i] = wv;  // the next step's SpMV gathers it
       acc[0] = fma(wv, wv, acc[0]);
-      if (RS < 4) {
+      if (RS < G) {
 #pragma unroll
         for (int u = 0; u < RS; ++u) acc[1 + u] = fma(a[u], wv, acc[1 + u]);
       }
@@ -254,64 +280,60 @@ __device__ __forceinline__ void mgs_pass(const BlockRows& br, const T* V, int64_
     }
   }
 #pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] = acc[u];
+  for (int u = 0; u < G; ++u) out[u] = acc[u];
 }
 
-template <typename T>
+// The three kinds of pass: the first (w from global memory, dots of group 0),
+// the middle ones (subtract a full group, dots of the next), the last
+// (subtract the last group, ||w||^2 and the new column's group inner products).
+template <typename T, int G>
 __device__ __forceinline__ void mgs_first(int rd, const BlockRows& br, const T* V, int64_t ldv,
-                                          T* ws, T* wg, T (&out)[4]) {
-  switch (rd) {
-    case 1: mgs_pass<T, 0, 1, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
-    case 2: mgs_pass<T, 0, 2, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
-    case 3: mgs_pass<T, 0, 3, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
-    default: mgs_pass<T, 0, 4, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out); break;
-  }
+                                          T* ws, T* wg, T (&out)[G]) {
+  dispatch_r<1, G>(rd, [&](auto R) {
+    mgs_pass<T, G, 0, decltype(R)::value, true, false>(br, V, ldv, 0, 0, nullptr, ws, wg, out);
+  });
 }
-template <typename T>
+template <typename T, int G>
 __device__ __forceinline__ void mgs_mid(int rd, const BlockRows& br, const T* V, int64_t ldv,
-                                        int cs0, const T* kc, T* ws, T* wg, T (&out)[4]) {
-  switch (rd) {
-    case 1: mgs_pass<T, 4, 1, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
-    case 2: mgs_pass<T, 4, 2, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
-    case 3: mgs_pass<T, 4, 3, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
-    default: mgs_pass<T, 4, 4, false, false>(br, V, ldv, cs0, cs0 + 4, kc, ws, wg, out); break;
-  }
+                                        int cs0, const T* kc, T* ws, T* wg, T (&out)[G]) {
+  dispatch_r<1, G>(rd, [&](auto R) {
+    mgs_pass<T, G, G, decltype(R)::value, false, false>(br, V, ldv, cs0, cs0 + G, kc, ws, wg,
+                                                        out);
+  });
 }
-template <typename T>
+template <typename T, int G>
 __device__ __forceinline__ void mgs_last(int rs, const BlockRows& br, const T* V, int64_t ldv,
-                                         int cs0, const T* kc, T* ws, T* wg, T (&out)[4]) {
-  switch (rs) {
-    case 1: mgs_pass<T, 1, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
-    case 2: mgs_pass<T, 2, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
-    case 3: mgs_pass<T, 3, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
-    default: mgs_pass<T, 4, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out); break;
-  }
+                                         int cs0, const T* kc, T* ws, T* wg, T (&out)[G]) {
+  dispatch_r<1, G>(rs, [&](auto R) {
+    mgs_pass<T, G, decltype(R)::value, 0, false, true>(br, V, ldv, cs0, 0, kc, ws, wg, out);
+  });
 }
 
-// min(max(v, 0), 4): columns of a group that exist
-__device__ __forceinline__ int clamp4(int v) { return v < 0 ? 0 : (v > 4 ? 4 : v); }
+// min(max(v, 0), G): columns of a group that exist
+template <int G>
+__device__ __forceinline__ int clamp_group(int v) { return v < 0 ? 0 : (v > G ? G : v); }
 
-// Block sums of four values held by the first kMgsThreads threads: each warp
-// folds its four with warp_sum4, four threads add the warps' results in order
-// and write the block's partials part[q * grid + block].  wp: 4 * kMgsThreads / 32
-// doubles (the kernel's warp-sum table holds at least 96).
-template <typename T>
-__device__ __forceinline__ void mgs_block_partials(const T (&v)[4], double* wp,
-                                                   double* part) {
-  constexpr int nw = kMgsThreads / 32;
+// Block sums of G values held by the first kMgsThreads threads: each warp folds
+// its G with warp_sum_group, then warp 0 adds the 16 warps' results of each value
+// (32 / G lanes per value, a fixed tree) and writes the block's partials
+// part[q * grid + block].  wp: G * 16 doubles.
+template <typename T, int G>
+__device__ __forceinline__ void mgs_block_partials(T (&v)[G], double* wp, double* part) {
+  constexpr int nw = kMgsThreads / 32, LP = 32 / G;
+  static_assert(nw == 16 && nw % LP == 0, "the tree below assumes 16 pass warps");
   if (threadIdx.x < kMgsThreads) {
-    const double s = (double)warp_sum4<T>(v[0], v[1], v[2], v[3]);
+    const double s = (double)warp_sum_group<G, T>(v);
     const int lane = threadIdx.x & 31;
-    if ((lane & 7) == 0) wp[((lane >> 3) & 3) * nw + (threadIdx.x >> 5)] = s;
+    if ((lane & (LP - 1)) == 0) wp[(lane / LP) * nw + (threadIdx.x >> 5)] = s;
   }
   __syncthreads();
-  static_assert(nw == 16, "the tree below adds 16 warp sums per value");
-  if (threadIdx.x < 32) {  // lane l: value l / 8, warp sums l % 8 and l % 8 + 8, then a tree
-    const int q = threadIdx.x >> 3, m = threadIdx.x & 7;
-    double t = wp[q * nw + m] + wp[q * nw + m + 8];
-    t += __shfl_xor_sync(0xffffffffu, t, 4);
-    t += __shfl_xor_sync(0xffffffffu, t, 2);
-    t += __shfl_xor_sync(0xffffffffu, t, 1);
+  if (threadIdx.x < 32) {  // lane l: value l / LP; warp sums l % LP, l % LP + LP, ...
+    const int q = threadIdx.x / LP, m = threadIdx.x & (LP - 1);
+    double t = wp[q * nw + m];
+#pragma unroll
+    for (int k = m + LP; k < nw; k += LP) t += wp[q * nw + k];
+#pragma unroll
+    for (int sp = LP / 2; sp >= 1; sp >>= 1) t += __shfl_xor_sync(0xffffffffu, t, sp);
     if (m == 0) part[(int64_t)q * gridDim.x + blockIdx.x] = t;
   }
 }
@@ -332,9 +354,9 @@ struct GmSmem {
         h2(h + M + 2),
         coef(h2 + M + 2),
         wp(coef + M + 2),  // coef: M + 2 values of T (at most a double each)
-        red(wp + 32 * (int64_t)(M + 2)),
-        G(red + kPersistBlock + 4),  // G: (M + 1) x 4 group inner products
-        w(G + 4 * (int64_t)(M + 1)),
+        red(wp + 32 * (int64_t)(M + 2 > 4 ? M + 2 : 4)),  // wp: at least 128
+        G(red + kPersistBlock + 4),  // G: (M + 1) x 8 group inner products
+        w(G + 8 * (int64_t)(M + 1)),
         total(w + wdoubles) {}
 };
 
@@ -358,11 +380,12 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
   T* coef = reinterpret_cast<T*>(dsm + L.coef);
   double* wp = dsm + L.wp;  // (M + 2) x 32 warp sums of block_dots
   double* red = dsm + L.red;
-  double* G = dsm + L.G;    // (v_q, v_c) within groups of four columns, G[q * 4 + c % 4]
+  constexpr int GS = MgsGroup<T>::value;  // columns per grid reduction
+  double* G = dsm + L.G;    // (v_q, v_c) within groups of GS columns, G[q * GS + c % GS]
   T* ws = reinterpret_cast<T*>(dsm + L.w);  // the block's rows of w (modified Gram-Schmidt)
   __shared__ int32_t so[F == kPersistDia ? kDiaMax : 1];
   __shared__ double sh_w2;
-  __shared__ double rsum[4];  // a grouped Gram-Schmidt round's four sums
+  __shared__ double rsum[kMgsGroupMax];  // a grouped Gram-Schmidt round's sums
   __shared__ int sh_flag, sh_halt, sh_stop, sh_bad, sh_conv, sh_fin, sh_mcyc;
 
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -386,7 +409,8 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
     g[k] = ld_cg(&st->g[k]);
     sc[k] = 1.0;
   }
-  for (int k = threadIdx.x; k < 4 * (M + 1); k += blockDim.x) G[k] = ld_cg(&st->G[k]);
+  for (int k = threadIdx.x; k < GS * (M + 1); k += blockDim.x)
+    G[k] = ld_cg(&st->G[(k / GS) * kMgsGroupMax + k % GS]);
   if (lead) {
     st->mcyc = a.mcyc;
     a.mir->mcyc = a.mcyc;
@@ -417,8 +441,8 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
     T* w = V + (int64_t)(j + 1) * ldv;
     int second = 0;
     if (a.mgs) {
-      // ---- 1-3 (modified Gram-Schmidt in groups of four): w = A v_j; per group
-      // B_k = [4k, 4k + R_k) one grid reduction of (v_c, w), then h_B = T_k (V_B^T w)
+      // ---- 1-3 (modified Gram-Schmidt in groups of GS): w = A v_j; per group
+      // B_k = [GS k, GS k + R_k) one grid reduction of (v_c, w), then h_B = T_k (V_B^T w)
       // and w -= V_B h_B in the pass that forms the next group's dot products.
       // The block's rows of w stay in shared memory.
       persist_spmv<T, F, TPV, true, false>(a, so, V + (int64_t)j * ldv, w, (T)sc[j], T(0),
@@ -428,38 +452,40 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       } else {
         __syncthreads();  // the block reads back the rows its threads wrote
       }
-      const int nb = (j + 4) >> 2;  // groups of the columns 0 .. j
-      int rot = 0;                  // rotations applied to column j (helper thread)
-      T part4[4] = {T(0), T(0), T(0), T(0)};
+      const int nb = (j + GS) / GS;  // groups of the columns 0 .. j
+      int rot = 0;                   // rotations applied to column j (helper thread)
+      T part[GS];
+#pragma unroll
+      for (int u = 0; u < GS; ++u) part[u] = T(0);
       if (threadIdx.x < kMgsThreads)
-        mgs_first<T>(clamp4(j + 1), br, V, ldv, ws, w, part4);
+        mgs_first<T, GS>(clamp_group<GS>(j + 1), br, V, ldv, ws, w, part);
       lap(0);
       bool ok = true;
       for (int k = 0;; ++k) {
         // partials alternate between two buffers over consecutive rounds, so a
         // round's writes never meet a slower block's reads of the round before
-        double* pr = a.part + (int64_t)(rounds++ & 1) * 4 * gridDim.x;
+        double* pr = a.part + (int64_t)(rounds++ & 1) * GS * gridDim.x;
         if (k > 0) lap(2);  // passes
-        mgs_block_partials<T>(part4, wp, pr);
+        mgs_block_partials<T, GS>(part, wp, pr);
         if (!barrier()) {
           ok = false;
           break;
         }
         if (k == 0 && lead) st->stop = *a.yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
-        if (threadIdx.x < 128) {
+        if (threadIdx.x < 32 * GS) {  // one warp per value
           const double t = warp_partials_cg(pr + (int64_t)(threadIdx.x >> 5) * gridDim.x,
                                             gridDim.x);
           if ((threadIdx.x & 31) == 0) rsum[threadIdx.x >> 5] = t;
         }
         __syncthreads();
         if (k == nb) break;  // rsum[0] = ||w||^2, rsum[1 ..] its group's raw inner products
-        const int c0 = 4 * k, R = j + 1 - c0 < 4 ? j + 1 - c0 : 4;
+        const int c0 = GS * k, R = j + 1 - c0 < GS ? j + 1 - c0 : GS;
         if (threadIdx.x < 32) {  // h_B = T_k r: forward substitution, lane i on h_{c0+i}
           const int i = threadIdx.x;
           double r = i < R ? rsum[i] * sc[c0 + i] : 0.0;
           for (int l = 0; l + 1 < R; ++l) {
             const double hl = __shfl_sync(0xffffffffu, r, l);
-            if (i > l && i < R) r = fma(-G[(c0 + i) * 4 + l], hl, r);
+            if (i > l && i < R) r = fma(-G[(c0 + i) * GS + l], hl, r);
           }
           if (i < R) {
             h[c0 + i] = r;
@@ -482,9 +508,10 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
         }
         if (threadIdx.x < kMgsThreads) {
           if (k + 1 < nb) {
-            mgs_mid<T>(clamp4(j + 1 - (c0 + 4)), br, V, ldv, c0, coef, ws, w, part4);
+            mgs_mid<T, GS>(clamp_group<GS>(j + 1 - (c0 + GS)), br, V, ldv, c0, coef, ws, w,
+                           part);
           } else {
-            mgs_last<T>(R, br, V, ldv, c0, coef, ws, w, part4);
+            mgs_last<T, GS>(R, br, V, ldv, c0, coef, ws, w, part);
           }
         }
       }
@@ -492,12 +519,12 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       lap(3);
       if (threadIdx.x == 0) {  // the new column's inner products within its group
         sh_w2 = rsum[0];
-        const int q = j + 1, r = q & 3;
+        const int q = j + 1, r = q % GS;
         const double sq = rsum[0] > 0.0 ? 1.0 / sqrt(rsum[0]) : 0.0;
-        for (int l = 0; l < 4; ++l) {
+        for (int l = 0; l < GS; ++l) {
           const double gv = l < r ? rsum[1 + l] * sc[q - r + l] * sq : 0.0;
-          G[q * 4 + l] = gv;
-          if (lead) st->G[q * 4 + l] = gv;
+          G[q * GS + l] = gv;
+          if (lead) st->G[q * kMgsGroupMax + l] = gv;
         }
       }
       lap(2);
@@ -702,12 +729,12 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
         sc[0] = beta > 0.0 ? 1.0 / beta : 0.0;
         g[0] = beta;
         for (int k = 1; k <= M; ++k) g[k] = 0.0;
-        for (int k = 0; k < 4 * (M + 1); ++k) G[k] = 0.0;
+        for (int k = 0; k < GS * (M + 1); ++k) G[k] = 0.0;
         if (lead) {
           st->beta = beta;
           st->g[0] = beta;
           for (int k = 1; k <= kMaxRestart; ++k) st->g[k] = 0.0;
-          for (int k = 0; k < 4 * (kMaxRestart + 1); ++k) st->G[k] = 0.0;
+          for (int k = 0; k < kMgsGroupMax * (kMaxRestart + 1); ++k) st->G[k] = 0.0;
           st->inv = sc[0];
           st->jdone = 0;
           st->conv_est = 0;

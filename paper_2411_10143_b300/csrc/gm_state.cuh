@@ -16,11 +16,12 @@ struct GmState {
   double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
   double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
   // inner products (v_q, v_c) of column q with the columns c before it in its
-  // aligned group of four, G[q * 4 + (c - 4 floor(q / 4))]: the persistent kernel's
-  // modified Gram-Schmidt applies a group's four projections in one pass with
-  // them.  Zero for columns made by the per-step kernels (orthogonal to working
-  // precision by the second Gram-Schmidt pass).
-  double G[(kMaxRestart + 1) * 4];
+  // aligned group of g columns (g = 4 in FP64, 8 in FP32), G[q * 8 + (c - g
+  // floor(q / g))]: the persistent kernel's modified Gram-Schmidt applies a
+  // group's projections in one pass with them.  Zero for columns made by the
+  // per-step kernels (orthogonal to working precision by the second
+  // Gram-Schmidt pass).
+  double G[(kMaxRestart + 1) * 8];
   double bb, beta, inv;  // ||b||^2, cycle start ||r||, 1 / current norm
   int done;              // converged (true residual of a cycle start)
   int halt;              // no further steps in this cycle
