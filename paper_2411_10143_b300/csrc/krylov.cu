@@ -771,6 +771,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
   Mirror* mir = ws.mirror();
   cs.expose(ws.mir);
   CP_CUDA(cudaMemsetAsync(st, 0, sizeof(CgState), s));
+  const int persist_iters0 = cs.persist_iters;
   const double tol2 = tol * tol;
   const int G = grid_n(ctx, n);
   // the vector kernels work on pairs in tiles of kBlock * kVecU (update) and
@@ -902,10 +903,12 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
   }
   CP_CUDA(cudaMemcpyAsync(x_user, xw, n * sizeof(T), cudaMemcpyDeviceToDevice, s));
   CP_CUDA(cudaStreamSynchronize(s));
-  if (cs.persist_iters > 0) {
+  if (cs.persist_iters > persist_iters0 && trace_on()) {
+    // the state (with its timers) is zeroed by every call; the iteration count
+    // of the solve accumulates over the inner solves of a refinement
     unsigned long long tn[6];
     CP_CUDA(cudaMemcpy(tn, st->t_ns, sizeof(tn), cudaMemcpyDeviceToHost));
-    const double k = 1e-3 / (cs.persist_iters > 0 ? cs.persist_iters : 1);
+    const double k = 1e-3 / (cs.persist_iters - persist_iters0);
     trace("persistent CG per iteration (us): spmv %.2f bar %.2f update %.2f bar %.2f "
           "direction %.2f bar %.2f", tn[0] * k, tn[1] * k, tn[2] * k, tn[3] * k, tn[4] * k,
           tn[5] * k);
