@@ -167,8 +167,8 @@ def cg_iteration_bytes(A, fmt):
 # profiles/k_cg_persist_dia_poisson3d_128.md.
 PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
 PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
-                   "sha256": "96fed50fa86fe4b682fd77e4d38bf96632764bd8a73130129f5c11db3284d30e",
-                   "dram_bytes_per_iteration": 158546926.7}
+                   "sha256": "0f2a4dd0fb03733f993dd47a8f37da7110e6a9e74dc473d4660b9aabfb9182f7",
+                   "dram_bytes_per_iteration": 163620083.5}
 
 
 def persist_sources_sha256():

@@ -123,6 +123,34 @@ __device__ __forceinline__ void for_slots(int64_t w, F&& f) {
   }
 }
 
+// The same with chunks of 8 slots (remainder 1 to 7): twice the loads in flight
+// per chunk, for loops whose values take one register each (FP32), where the
+// row loop is bound by memory latency rather than by the FMA pipe.
+template <typename F>
+__device__ __forceinline__ void for_slots8(int64_t w, F&& f) {
+  int64_t k0 = 0;
+  for (; k0 + 8 <= w; k0 += 8)
+    if (f(k0, Slots<8>{})) return;
+  switch (w - k0) {
+    case 7: f(k0, Slots<7>{}); break;
+    case 6: f(k0, Slots<6>{}); break;
+    case 5: f(k0, Slots<5>{}); break;
+    case 4: f(k0, Slots<4>{}); break;
+    case 3: f(k0, Slots<3>{}); break;
+    case 2: f(k0, Slots<2>{}); break;
+    case 1: f(k0, Slots<1>{}); break;
+    default: break;
+  }
+}
+
+// Chunks of 8 for FP32 values, 4 for FP64 (whose loops the FP64 pipe bounds,
+// and whose registers are twice as scarce).
+template <typename T, typename F>
+__device__ __forceinline__ void for_slots_t(int64_t w, F&& f) {
+  if constexpr (sizeof(T) == 4) for_slots8(w, f);
+  else for_slots(w, f);
+}
+
 // ------------------------------------------------------------------ ELL
 // Thread per row pair (i and i + stride); chunks of 4 slots give 16 independent
 // coalesced loads before the gathers; padding (col -1) only follows a row's
@@ -137,7 +165,7 @@ __device__ __forceinline__ T ell_rows(int64_t n, int64_t K, int64_t ld,
     const int64_t i1 = i0 + stride;
     const bool has1 = i1 < n;
     T s0 = 0, s1 = 0;
-    for_slots(K, [&](int64_t k0, auto R) {
+    for_slots_t<T>(K, [&](int64_t k0, auto R) {
       constexpr int r = decltype(R)::value;
       int32_t c0[r], c1[r];
       T w0[r], w1[r];
@@ -183,7 +211,7 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
   for (int64_t c = warp; c < nchunks; c += nwarps) {
     const int64_t base = cptr[c] + lane;
     T sum = 0;
-    for_slots(clen[c], [&](int64_t k0, auto R) {
+    for_slots_t<T>(clen[c], [&](int64_t k0, auto R) {
       constexpr int r = decltype(R)::value;
       int32_t cc[r];
       T vv[r];
@@ -218,32 +246,63 @@ __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const
                                       T* __restrict__ y, T alpha, T beta,
                                       const T* __restrict__ dotv, int64_t tid, int64_t stride) {
   T acc = 0;
+  // rows i with every i + offset inside [0, ncols) (all but a band at each end
+  // for a stencil) take a loop without per-slot bounds checks
+  int32_t omin = 0, omax = 0;
+  for (int d = 0; d < ndiag; ++d) {
+    const int32_t o = so[d];
+    omin = o < omin ? o : omin;
+    omax = o > omax ? o : omax;
+  }
+  const int64_t lo = -(int64_t)omin, hi = ncols - (int64_t)omax;
   for (int64_t i0 = tid; i0 < n; i0 += 2 * stride) {
     const int64_t i1 = i0 + stride;
     const bool has1 = i1 < n;
     T s0 = 0, s1 = 0;
-    for_slots(ndiag, [&](int64_t d0, auto R) {
-      constexpr int r = decltype(R)::value;
-      T w0[r], x0[r], w1[r], x1[r];
+    if (has1 && i0 >= lo && i1 < hi) {
+      for_slots_t<T>(ndiag, [&](int64_t d0, auto R) {
+        constexpr int r = decltype(R)::value;
+        T w0[r], x0[r], w1[r], x1[r];
 #pragma unroll
-      for (int u = 0; u < r; ++u) {
-        const int64_t off = so[d0 + u];
-        const int64_t c0 = i0 + off, c1 = i1 + off;
-        const bool in0 = c0 >= 0 && c0 < ncols;
-        const bool in1 = has1 && c1 >= 0 && c1 < ncols;
-        const int64_t base = (d0 + u) * n;
-        w0[u] = in0 ? ld_stream(dv + base + i0) : T(0);
-        x0[u] = in0 ? ld_x<COH>(x + c0) : T(0);
-        w1[u] = in1 ? ld_stream(dv + base + i1) : T(0);
-        x1[u] = in1 ? ld_x<COH>(x + c1) : T(0);
-      }
+        for (int u = 0; u < r; ++u) {
+          const int64_t off = so[d0 + u];
+          const int64_t base = (d0 + u) * n;
+          w0[u] = ld_stream(dv + base + i0);
+          x0[u] = ld_x<COH>(x + i0 + off);
+          w1[u] = ld_stream(dv + base + i1);
+          x1[u] = ld_x<COH>(x + i1 + off);
+        }
 #pragma unroll
-      for (int u = 0; u < r; ++u) {
-        s0 = fma(w0[u], x0[u], s0);
-        s1 = fma(w1[u], x1[u], s1);
-      }
-      return false;
-    });
+        for (int u = 0; u < r; ++u) {
+          s0 = fma(w0[u], x0[u], s0);
+          s1 = fma(w1[u], x1[u], s1);
+        }
+        return false;
+      });
+    } else {
+      for_slots_t<T>(ndiag, [&](int64_t d0, auto R) {
+        constexpr int r = decltype(R)::value;
+        T w0[r], x0[r], w1[r], x1[r];
+#pragma unroll
+        for (int u = 0; u < r; ++u) {
+          const int64_t off = so[d0 + u];
+          const int64_t c0 = i0 + off, c1 = i1 + off;
+          const bool in0 = c0 >= 0 && c0 < ncols;
+          const bool in1 = has1 && c1 >= 0 && c1 < ncols;
+          const int64_t base = (d0 + u) * n;
+          w0[u] = in0 ? ld_stream(dv + base + i0) : T(0);
+          x0[u] = in0 ? ld_x<COH>(x + c0) : T(0);
+          w1[u] = in1 ? ld_stream(dv + base + i1) : T(0);
+          x1[u] = in1 ? ld_x<COH>(x + c1) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < r; ++u) {
+          s0 = fma(w0[u], x0[u], s0);
+          s1 = fma(w1[u], x1[u], s1);
+        }
+        return false;
+      });
+    }
     store_row<T, GEN>(y, i0, s0, alpha, beta);
     if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
     if (has1) {
