@@ -10,21 +10,33 @@
 // first Gram-Schmidt pass needs no grid barrier after the SpMV.  (SELL with a
 // row permutation is the exception and takes one.)
 //
-// Step j of a cycle, w = column j + 1 of V:
+// Step j of a cycle, w = column j + 1 of V, orthogonalised by modified
+// Gram-Schmidt in groups of g columns (g = 4 in FP64, 8 in FP32; see the
+// grouped passes below) while the block's rows of w fit in shared memory:
+//   1. w = A v_j; the block keeps its rows of w in shared memory and forms the
+//      partials of (v_c, w) for the first group
+//   2. per group: a grid reduction (every block sums the partials in the same
+//      order, so every block gets the same bits), the group's coefficients by a
+//      forward substitution with its inner products, then one pass that
+//      subtracts the group and forms the next group's partials (after the last
+//      group: ||w||^2 and the new column's inner products within its group)
+//   3. thread 0 of every block forms the next Givens rotation and the residual
+//      estimate |g_{j+1}| (a thread outside the passes has applied the earlier
+//      rotations to the new Hessenberg column meanwhile); every block holds the
+//      cycle's small matrices in shared memory and takes the same decisions
+//      without further synchronisation.
+// Systems whose rows of w do not fit (or gmres_orth = 1) take classical
+// Gram-Schmidt instead:
 //   1. w = A v_j; block partials of (v_c, w) for c <= j and of (w, w)
 //   -- grid barrier
-//   2. every block sums the partials (same order, same bits everywhere);
-//      w -= sum_c h_c v_c; partials of ||w||^2, or (FP32) at once the block
+//   2. w -= sum_c h_c v_c; partials of ||w||^2, or (FP32) at once the block
 //      partials of the second pass (v_c, w)
 //   -- grid barrier
 //   3. FP64: the second pass only when the first removed most of w,
 //      ||w'||^2 < ||w||^2 / 2 (Daniel, Gragg, Kaufman and Stewart, 1976):
 //      dots, barrier, subtraction, partials of ||w''||^2, barrier.  FP32 runs
 //      the subtraction of its second pass here, then a barrier.
-//   4. thread 0 of every block applies the previous rotations to the new
-//      Hessenberg column, forms the next rotation and the residual estimate
-//      |g_{j+1}|; every block holds the cycle's small matrices in shared memory
-//      and takes the same decisions without further synchronisation.
+//   4. the Givens rotation as above.
 // Columns are never normalised in place: column c of V holds v_c / s_c with
 // the scale s_c kept in shared memory (1 / ||w|| of the step that made it), and
 // the scales are folded into the SpMV's alpha, the dot products, the
