@@ -287,7 +287,10 @@ typedef struct {
                             (CSR scalar / vector, ELL, SELL, DIA, HYB without COO part)
                             and no prediction work is pending on the side stream,
                             falling back to one launch per step otherwise; 1 = always
-                            one launch per step                                       */
+                            one launch per step; 2 = alternate persistent launches of
+                            persist_chunk iterations with as many one-launch-per-step
+                            iterations (hands the iteration over between the two paths,
+                            as a switch does, at every chunk; for tests)          */
   const cp_config* force;/* non-NULL: use this configuration from the first iteration    */
   double wait_limit_ms;  /* bound of every device-side wait of the persistent kernel (its
                             grid barriers); a wait that exceeds it ends the solve with

@@ -687,6 +687,15 @@ struct ConfigSource {
   int persist_chunk = 0;      // iterations a persistent launch runs before returning (0: all)
   int gmres_orth = 0;         // persistent GMRES: 0 modified Gram-Schmidt where it fits, 1 classical
   int persist_launches = 0;   // persistent launches made
+  bool alternate = false;     // after each persistent launch, persist_chunk per-step iterations
+  int per_step_left = 0;      // per-step iterations still due before the next persistent launch
+  bool persistent_now() const { return persistent && per_step_left == 0; }
+  void after_persist() {
+    if (alternate) per_step_left = persist_chunk;
+  }
+  void after_step() {
+    if (per_step_left > 0) --per_step_left;
+  }
   float t_persist_ms = 0.f;   // summed duration of the persistent launches
   int persist_iters = 0;      // iterations they ran
   float t_persist_last_ms = 0.f;
@@ -805,7 +814,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       // interleaving with the side kernels.
       const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire) ||
                              cs.ch->side_gpu_idle.load(std::memory_order_acquire);
-      if (cs.persistent && side_idle && persist_supported<T>(m, cs.cur)) {
+      if (cs.persistent_now() && side_idle && persist_supported<T>(m, cs.cur)) {
         // one cooperative launch runs iterations [it, maxit) until convergence, a
         // breakdown, or the host asks it to return at an iteration boundary
         // because the cascade published a new configuration
@@ -856,6 +865,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         it = ws.mir->iters;
         trace("solve: persistent launch returned at iteration %d (%.3f ms)", it, t);
         if (ws.mir->done || ws.mir->status != CP_OK) break;
+        cs.after_persist();
         continue;  // returned on request: the poll above applies the new configuration
       }
       const int PA = spmv_cur<T>(cs, p, ap, p, pa, done, s);
@@ -866,6 +876,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
       ++issued;
       ++it;
+      cs.after_step();
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
         if (ws.mir->done) break;
@@ -986,7 +997,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       // because a new configuration was published or the side needs the GPU.
       const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire) ||
                              cs.ch->side_gpu_idle.load(std::memory_order_acquire);
-      if (cs.persistent && side_idle && gm_persist_supported<T>(m, cs.cur, mrest)) {
+      if (cs.persistent_now() && side_idle && gm_persist_supported<T>(m, cs.cur, mrest)) {
         int* yield_d = ws.yield();
         *(volatile int*)ws.yield_h = 0;
         ws.mir->exit_kind = 0;
@@ -1045,6 +1056,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
           finished = true;
           break;
         }
+        cs.after_persist();
         if (kind == 2) {  // at the end of a cycle, x updated
           x_updated = true;
           break;
@@ -1078,6 +1090,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       CP_CUDA(cudaEventRecord(ws.event(issued, depth), s));
       ++issued;
       ++j;
+      cs.after_step();
       if (issued >= depth) {
         CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));
         if (ws.mir->halt) break;
@@ -1214,7 +1227,12 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
   cs.m = m;
   cs.fp32 = fp32;
   cs.profile = opt.profile != 0;
-  cs.persistent = opt.iteration_kernel == 0;
+  CP_REQUIRE(opt.iteration_kernel >= 0 && opt.iteration_kernel <= 2, CP_ERR_INVALID,
+             "iteration_kernel must be 0, 1 or 2");
+  CP_REQUIRE(opt.iteration_kernel != 2 || opt.persist_chunk > 0, CP_ERR_INVALID,
+             "iteration_kernel 2 needs persist_chunk > 0");
+  cs.persistent = opt.iteration_kernel != 1;
+  cs.alternate = opt.iteration_kernel == 2;
   CP_REQUIRE(opt.wait_limit_ms >= 0.0, CP_ERR_INVALID, "wait_limit_ms must be >= 0");
   cs.wait_limit_ms = opt.wait_limit_ms;
   CP_REQUIRE(opt.persist_chunk >= 0, CP_ERR_INVALID, "persist_chunk must be >= 0");

@@ -232,3 +232,45 @@ def test_persistent_gmres_bounded_wait_times_out_cleanly():
     x, info = solve(c, A, b, restart=30, tol=1e-10, force=C.config("DIA"))
     assert info.status == 0 and true_relres(A, x, b) <= 1e-10
     c.close()
+
+
+@pytest.mark.parametrize("m,chunk", [(30, 7), (5, 3)])
+@pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
+def test_gmres_hand_over_between_persistent_and_per_step(ctx, m, chunk, precision):
+    """iteration_kernel = 2 alternates persistent launches of `chunk` steps with
+    as many one-launch-per-step steps, inside cycles and across their ends: the
+    persistent kernel normalises its columns and hands the cycle's state back,
+    the per-step kernels extend the cycle with classical Gram-Schmidt, and the
+    persistent kernel takes the cycle up again (its group inner products of the
+    per-step columns being zero).  The solution is the oracle's."""
+    A, b = system(14, 32)
+    ref = reference(14, 32, m)
+    x, info = solve(ctx, A, b, restart=m, tol=1e-10, force=C.config("DIA"), iteration_kernel=2,
+                    persist_chunk=chunk, precision=precision, inner_tol=1e-5)
+    assert info.status == 0
+    assert 0 < info.persist_iters < info.iters and info.persist_launches >= 2
+    check(A, b, x, ref)
+
+
+@pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
+def test_cg_hand_over_between_persistent_and_per_step(ctx, precision):
+    A = W.poisson3d(20)
+    b = oracle.spmv(A, W.vector(A.ncols, 33))
+    ref = oracle.cg(A, b, tol=1e-10)
+    M = ctx.load(A)
+    bd = torch.as_tensor(b, device="cuda")
+    xd = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+    info = M.solve_cg(bd, xd, C.default_opts(tol=1e-10, iteration_kernel=2, persist_chunk=9,
+                                             precision=precision, inner_tol=1e-5),
+                      force=C.config("DIA"))
+    x = xd.cpu().numpy()
+    assert info.status == 0 and 0 < info.persist_iters < info.iters
+    assert info.persist_launches >= 2
+    assert true_relres(A, x, b) <= 1e-10
+    assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+
+
+def test_alternating_mode_needs_a_chunk(ctx):
+    A, b = system(3, 34)
+    with pytest.raises(Exception):
+        solve(ctx, A, b, iteration_kernel=2, persist_chunk=0)
