@@ -386,6 +386,7 @@ def run_ours(args, world, rank, local):
 def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
     """Plain / sequential / FP32-IR variants, the end-to-end number, the CPU baseline."""
     import torch
+    from paper_2411_10143_b300 import workloads as W
 
     def timed(opts, reps=2):
         out = []
@@ -437,7 +438,10 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
     if not args.no_gmres:
         res["gmres"] = gmres_bench(ctx)
     if not args.no_sweep:
-        res["spmv_sweep"] = spmv_sweep_bench(ctx, measured_peaks()[0])
+        res["spmv_sweep"] = spmv_sweep_bench(ctx, measured_peaks()[0], solves=True)
+    if not args.no_gmres:
+        # the random SPD power-law system of the asynchronous solves (n = 500k)
+        res["spd_powerlaw_cg"] = variant_solves(ctx, W.spd_powerlaw(), W.RHS_SEED_BASE + 3, "cg")
     if args.serve_requests > 0:
         res["serve"] = serve_bench(ctx, args.serve_requests)
     if args.gpus == 1 and not args.no_cpu_baseline:
@@ -561,7 +565,57 @@ def time_spmv(ctx, M, cfg, x, y, reps, warm):
     return float(np.median(t)), float(np.mean(t))
 
 
-def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=log):
+def timed_solve(ctx, M, b, xstar, kind, opts, force=None, reps=2):
+    """Mean time (CUDA events on the library's stream) of `reps` solves from x0 = 0,
+    every one from the freshly loaded CSR (converted formats and features dropped),
+    with the last solve's info and its error against x*."""
+    import torch
+    ts, info, x = [], None, None
+    for _ in range(reps):
+        M.reset()
+        x = torch.zeros(M.nrows, dtype=torch.float64, device="cuda")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        info = (M.solve_cg if kind == "cg" else M.solve_gmres)(b, x, opts, force=force)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    err = float(torch.linalg.norm(x - xstar) / torch.linalg.norm(xstar))
+    return float(np.mean(ts)), info, err
+
+
+def variant_solves(ctx, A, seed, kind, restart=30):
+    """A solve on a matrix: plain FP64 with the default CSR-scalar kernel against
+    the asynchronous cascade with FP32 inner solves in FP64 refinement (and in
+    FP64 for CG), to relative residual 1e-10; b = A x*."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import workloads as W
+    M = ctx.load(A)
+    xs = torch.as_tensor(W.vector(A.ncols, seed), device="cuda")
+    b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    M.spmv(xs, b)
+    base = dict(tol=TOL, restart=restart)
+    out = {"n": A.nrows, "nnz": A.nnz}
+    legs = [("plain_fp64", C.default_opts(mode=C.MODE_PLAIN, **base))]
+    if kind == "cg":
+        legs.append(("async_fp64", C.default_opts(mode=C.MODE_ASYNC, **base)))
+    legs.append(("async_fp32_ir", C.default_opts(mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
+                                                 inner_tol=1e-5, **base)))
+    for name, opts in legs:
+        # the plain leg once: on the power-law variant CSR-scalar takes tens of seconds
+        ms, info, err = timed_solve(ctx, M, b, xs, kind, opts, reps=1 if name == "plain_fp64" else 2)
+        out[name] = {"ms": ms, "iters": info.iters, "outer": info.outer_iters,
+                     "final_cfg": repr(info.final_cfg), "relres_true": info.relres_true,
+                     "err_vs_xstar": err}
+    out["speedup_vs_plain"] = out["plain_fp64"]["ms"] / out["async_fp32_ir"]["ms"]
+    M.free()
+    return out
+
+
+def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=log,
+                     solves=False):
     """SpMV format/kernel sweep with cascaded prediction on the four sweep
     matrices (3D Poisson 128^3, power law, uniform, banded; FP64 values
     U[-1,1]): per matrix the predicted configuration's GB/s and fraction of the
@@ -611,6 +665,11 @@ def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=
                         "csr_scalar_gbs": base["gbs"],
                         "speedup_vs_csr_scalar": base["median_us"] / pr["median_us"],
                         "regret": pr["median_us"] / timed[best]["median_us"], "configs": rows})
+        if solves and name != "poisson3d":
+            # the mixed-precision solve on this matrix's nonsymmetric solve variant
+            # (the same pattern, diagonally dominant), GMRES(30)
+            res["gmres_variant"] = variant_solves(ctx, W.diagonally_dominant(A),
+                                                  W.RHS_SEED_BASE + 4, "gmres")
         out[name] = res
         log_fn(f"spmv sweep {name}: predicted {res['predicted']} {pr['gbs']:.0f} GB/s "
                f"({pr['frac']:.2f} of peak)" + ("" if only_predicted else
@@ -784,7 +843,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=1000,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving leg (0 skips it)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the plain / sequential / FP32-IR / end-to-end / CPU legs")

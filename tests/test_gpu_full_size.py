@@ -15,7 +15,10 @@ they are checked through properties that hold at any size:
   oracle) obeys ||x - x*|| <= ||b - A x|| / lambda_min where a lower bound of
   lambda_min is known in closed form (3D Poisson: 6 - 6 cos(pi / (N + 1));
   the SPD power-law matrix: 1, by Gershgorin, since every diagonal exceeds its
-  row's off-diagonal sum by 1), and is <= 1e-7 relative for 3D Poisson.
+  row's off-diagonal sum by 1), and is <= 1e-7 relative for 3D Poisson;
+* for the nonsymmetric, strictly diagonally dominant solve variants of the
+  sweep matrices, ||x - x*||_inf <= ||b - A x||_inf, since ||A^-1||_inf <= 1
+  (Varah's bound with dominance margin 1).
 """
 import json
 from pathlib import Path
@@ -130,6 +133,22 @@ def test_async_gmres30_convdiff_96(ctx, precision):
                           precision=precision, inner_tol=1e-5)
     assert info.status == 0 and r <= 1e-10 * np.linalg.norm(b)
     assert np.linalg.norm(x - xs) <= 1e-6 * np.linalg.norm(xs)
+
+
+@pytest.mark.parametrize("name", ["powerlaw", "uniform", "banded"])
+def test_fp32_refinement_on_the_sweep_matrices_solve_variants(ctx, name):
+    """Mixed precision on the SpMV-sweep matrices (power law n = 1M, uniform
+    n = 2M, banded n = 1M): their nonsymmetric solve variants (the same pattern,
+    diagonal = off-diagonal row sum + 1), GMRES(30) with FP32 inner solves in
+    FP64 refinement, asynchronous cascade.  Strict diagonal dominance by 1 bounds
+    ||A^-1||_inf <= 1 (Varah, 1975), so ||x - x*||_inf <= ||b - A x||_inf."""
+    A = W.diagonally_dominant(W.spmv_sweep()[name]())
+    xs = W.vector(A.nrows, 2005)
+    x, b, r, info = solve(ctx, A, xs, "gmres", mode=C.MODE_ASYNC, restart=30,
+                          precision=C.PREC_FP32_IR, inner_tol=1e-5)
+    assert info.status == 0 and r <= 1e-10 * np.linalg.norm(b)
+    r_inf = np.max(np.abs(b - oracle.spmv(A, x)))
+    assert np.max(np.abs(x - xs)) <= r_inf * (1 + 1e-9)
 
 
 def median_us(ctx, M, cfg, x, y, reps=40):
