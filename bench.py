@@ -167,8 +167,8 @@ def cg_iteration_bytes(A, fmt):
 # profiles/k_cg_persist_dia_poisson3d_128.md.
 PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
 PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
-                   "sha256": "0f2a4dd0fb03733f993dd47a8f37da7110e6a9e74dc473d4660b9aabfb9182f7",
-                   "dram_bytes_per_iteration": 163620083.5}
+                   "sha256": "aa0b8b13feccb2d1381954fad83418ad6917eaf5740920cdc9b254b9fb99da32",
+                   "dram_bytes_per_iteration": 163332529.8}
 
 
 def persist_sources_sha256():
@@ -608,7 +608,12 @@ def variant_solves(ctx, A, seed, kind, restart=30):
         ms, info, err = timed_solve(ctx, M, b, xs, kind, opts, reps=1 if name == "plain_fp64" else 2)
         out[name] = {"ms": ms, "iters": info.iters, "outer": info.outer_iters,
                      "final_cfg": repr(info.final_cfg), "relres_true": info.relres_true,
-                     "err_vs_xstar": err}
+                     "err_vs_xstar": err, "switch_iter": list(info.switch_iter),
+                     "persist_iters": info.persist_iters,
+                     "t_persist_ms": round(float(info.t_persist_ms), 3),
+                     "t_features_ms": round(float(info.t_features_ms), 3),
+                     "t_predict_ms": round(float(sum(info.t_predict_ms)), 3),
+                     "t_convert_ms": round(float(info.t_convert_ms), 3)}
     out["speedup_vs_plain"] = out["plain_fp64"]["ms"] / out["async_fp32_ir"]["ms"]
     M.free()
     return out

@@ -62,11 +62,13 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
   V* r2 = reinterpret_cast<V*>(a.r);
   V* p2 = reinterpret_cast<V*>(a.p);
   const V* q2 = reinterpret_cast<const V*>(a.ap);
+  V* qc2 = reinterpret_cast<V*>(a.apc);
   for (int it = a.it0; it < a.itmax; ++it) {
     const int slot = it & 1;
     // ---- phase 1: Ap = A p, partials of (p, Ap)
     {
-      const T acc = persist_spmv<T, F, TPV, false, true>(a, so, a.p, a.ap, T(1), T(0), a.p);
+      T acc = persist_spmv<T, F, TPV, false, true>(a, so, a.p, a.ap, T(1), T(0), a.p);
+      if constexpr (F == kPersistHyb) acc += coo_tail_atomic(a, a.p, a.apc);
       const double s = block_sum_lean((double)acc, red);
       if (threadIdx.x == 0) a.pa[blockIdx.x] = s;
     }
@@ -74,7 +76,8 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
     bar_target += gridDim.x;
     if (!grid_barrier(&st->bar_count, &st->bar_err, bar_target, a.barrier_timeout_ns)) break;
     lap(1);
-    // ---- phase 2: alpha; r -= alpha Ap; partials of (r, r)
+    // ---- phase 2: alpha; r -= alpha Ap (HYB: Ap = ap + apc, apc zeroed for
+    // the next iteration); partials of (r, r)
     if (threadIdx.x < 32) {
       const double pap = warp_partials_cg(a.pa, gridDim.x);
       if (threadIdx.x == 0) {
@@ -110,6 +113,12 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
           if (i < n2) {
             rv[u] = ld_cg(r2 + i);
             qv[u] = ld_cg(q2 + i);
+            if constexpr (F == kPersistHyb) {
+              const V c = ld_cg(qc2 + i);
+              qv[u].x += c.x;
+              qv[u].y += c.y;
+              qc2[i] = V{T(0), T(0)};
+            }
           }
         }
 #pragma unroll
@@ -127,7 +136,12 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
       }
       if ((a.n & 1) && tid == 0) {
         const int64_t i = a.n - 1;
-        const T ri = fma(-alpha, ld_cg(a.ap + i), ld_cg(a.r + i));
+        T qi = ld_cg(a.ap + i);
+        if constexpr (F == kPersistHyb) {
+          qi += ld_cg(a.apc + i);
+          a.apc[i] = T(0);
+        }
+        const T ri = fma(-alpha, qi, ld_cg(a.r + i));
         a.r[i] = ri;
         acc = fma(ri, ri, acc);
       }
@@ -259,13 +273,13 @@ static void launch_one(cp_ctx* ctx, PersistArgs<T>& a, cudaStream_t s, int share
 
 template <typename T>
 bool persist_supported(const cp_mat* m, const cp_config& c) {
-  return persist_format_ok(m, c);
+  return persist_format_ok(m, c, true);
 }
 
 template <typename T>
 void persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, PersistArgs<T> a,
                     cudaStream_t s, int share) {
-  persist_dispatch<T>(m, c, a, [&](auto f, auto tpv) {
+  persist_dispatch<T, true>(m, c, a, [&](auto f, auto tpv) {
     launch_one<T, decltype(f)::value, decltype(tpv)::value>(ctx, a, s, share);
   });
 }

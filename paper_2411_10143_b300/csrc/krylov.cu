@@ -557,6 +557,7 @@ static int grid_n(cp_ctx* ctx, int64_t n) {
 template <typename T>
 struct CgBufs {
   T *r = nullptr, *p = nullptr, *ap = nullptr, *xw = nullptr;
+  T* apc = nullptr;  // HYB's COO part of A p in the persistent kernel (zeroed on allocation)
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   CgState* st = nullptr;
 };
@@ -825,6 +826,13 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         pa_args.r = r;
         pa_args.p = p;
         pa_args.ap = ap;
+        if (cs.cur.fmt == CP_FMT_HYB && m->hyb_coo.n > 0) {
+          if (!B.apc) {  // the kernel leaves it zero after every iteration
+            B.apc = ws.get<T>(n);
+            CP_CUDA(cudaMemsetAsync(B.apc, 0, n * sizeof(T), s));
+          }
+          pa_args.apc = B.apc;
+        }
         pa_args.pa = pa;
         pa_args.pb = pb;
         pa_args.st = st;

@@ -45,7 +45,8 @@ enum {
   kPersistCsrVector = 1,
   kPersistEll = 2,
   kPersistSell = 3,
-  kPersistDia = 4
+  kPersistDia = 4,
+  kPersistHyb = 5  // HYB with a COO part: ELL rows plus the COO tail (CG only)
 };
 
 // ------------------------------------------------------------------ grid barrier
@@ -122,6 +123,10 @@ struct PersistMat {
   int ndiag = 0;
   const int32_t* offs = nullptr;
   const T* dv = nullptr;
+  // HYB's COO part (entries beyond the ELL width, in row order)
+  int64_t coo_n = 0;
+  const int32_t *coo_row = nullptr, *coo_col = nullptr;
+  const T* coo_val = nullptr;
 };
 
 // y = alpha A x + beta y (GEN) or y = A x over the rows of the format's
@@ -138,7 +143,7 @@ __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t*
   else if constexpr (F == kPersistCsrVector)
     return csr_vector_rows<T, TPV, GEN, DOT, true>(a.n, a.rp, a.ci, a.v, x, y, alpha, beta,
                                                    dotv, tid >> 5, stride >> 5);
-  else if constexpr (F == kPersistEll)
+  else if constexpr (F == kPersistEll || F == kPersistHyb)  // (HYB: the ELL rows here)
     return ell_rows<T, GEN, DOT, true>(a.n, a.K, a.ld, a.ec, a.ev, x, y, alpha, beta, dotv, tid,
                                        stride);
   else if constexpr (F == kPersistSell)
@@ -149,6 +154,40 @@ __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t*
                                        tid, stride);
 }
 
+// HYB's COO tail in a persistent SpMV phase: yc[row] += val * x[col] for every
+// tail entry, through FP64 (FP32) atomics, one per row segment of a warp's 32
+// consecutive entries (a segmented scan over the lanes: the entries are in row
+// order).  Returns the thread's share of sum_e x[row_e] val_e x[col_e], the
+// tail's part of (x, A x).  yc must not be the ELL part's output (other blocks
+// add to any row while the ELL rows are stored).
+template <typename T>
+__device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x, T* yc) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  T dot = 0;
+  for (int64_t e0 = gw * 32; e0 < a.coo_n; e0 += nw * 32) {
+    const int64_t e = e0 + lane;
+    const bool in = e < a.coo_n;
+    const int32_t r = in ? ld_stream(a.coo_row + e) : -1 - lane;  // padding: distinct rows
+    T v = 0;
+    if (in) {
+      v = ld_stream(a.coo_val + e) * ld_x<true>(x + ld_stream(a.coo_col + e));
+      dot = fma(ld_cg(x + r), v, dot);
+    }
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T up = __shfl_up_sync(full, v, o);
+      const int32_t ru = __shfl_up_sync(full, r, o);
+      if (lane >= o && ru == r) v += up;  // sorted rows: equal ends mean one segment
+    }
+    const int32_t rn = __shfl_down_sync(full, r, 1);
+    if (in && (lane == 31 || rn != r)) atomicAdd(yc + r, v);
+  }
+  return dot;
+}
+
 template <typename T>
 struct PersistVals;
 template <>
@@ -157,6 +196,7 @@ struct PersistVals<double> {
   static const double* ell(const EllPart& e) { return e.val; }
   static const double* sell(const SellPart& s) { return s.val; }
   static const double* dia(const DiaPart& d) { return d.val; }
+  static const double* coo(const CooPart& c) { return c.val; }
 };
 template <>
 struct PersistVals<float> {
@@ -164,13 +204,14 @@ struct PersistVals<float> {
   static const float* ell(const EllPart& e) { return e.val32; }
   static const float* sell(const SellPart& s) { return s.val32; }
   static const float* dia(const DiaPart& d) { return d.val32; }
+  static const float* coo(const CooPart& c) { return c.val32; }
 };
 
 // Formats a persistent kernel runs: CSR (scalar or vector), ELL, HYB without a
-// COO part (which is ELL), SELL and DIA.
-inline bool persist_format_ok(const cp_mat* m, const cp_config& c) {
+// COO part (which is ELL), SELL and DIA; with coo_tail, HYB with a COO part too.
+inline bool persist_format_ok(const cp_mat* m, const cp_config& c, bool coo_tail = false) {
   if (c.fmt == CP_FMT_CSR) return c.algo == CP_ALGO_SCALAR || c.algo == CP_ALGO_VECTOR;
-  if (c.fmt == CP_FMT_HYB) return m->hyb_coo.n == 0;
+  if (c.fmt == CP_FMT_HYB) return m->hyb_coo.n == 0 || coo_tail;
   return c.fmt == CP_FMT_ELL || c.fmt == CP_FMT_SELL || c.fmt == CP_FMT_DIA;
 }
 
@@ -178,8 +219,9 @@ template <int V>
 using IntC = std::integral_constant<int, V>;
 
 // Fills a's format fields from m's data for configuration c and calls
-// launch(IntC<F>{}, IntC<TPV>{}) with the matching kernel variant.
-template <typename T, typename L>
+// launch(IntC<F>{}, IntC<TPV>{}) with the matching kernel variant.  TAIL: the
+// caller's kernel handles HYB's COO part (kPersistHyb).
+template <typename T, bool TAIL = false, typename L>
 void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launch) {
   a.n = m->nrows;
   switch (c.fmt) {
@@ -206,7 +248,19 @@ void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launc
       a.ld = e.ld;
       a.ec = e.col;
       a.ev = PersistVals<T>::ell(e);
-      launch(IntC<kPersistEll>{}, IntC<1>{});
+      if (c.fmt == CP_FMT_HYB && m->hyb_coo.n > 0) {
+        if constexpr (TAIL) {
+          a.coo_n = m->hyb_coo.n;
+          a.coo_row = m->hyb_coo.row;
+          a.coo_col = m->hyb_coo.col;
+          a.coo_val = PersistVals<T>::coo(m->hyb_coo);
+          launch(IntC<kPersistHyb>{}, IntC<1>{});
+        } else {
+          CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent kernel for HYB with a COO part");
+        }
+      } else {
+        launch(IntC<kPersistEll>{}, IntC<1>{});
+      }
       break;
     }
     case CP_FMT_SELL:
@@ -233,6 +287,7 @@ void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launc
 template <typename T>
 struct PersistArgs : PersistMat<T> {
   T *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr;
+  T* apc = nullptr;  // HYB: the COO tail's part of Ap, zero between iterations
   double *pa = nullptr, *pb = nullptr;  // block partials, capacity >= grid
   CgState* st = nullptr;
   Mirror* mir = nullptr;

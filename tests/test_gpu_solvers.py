@@ -250,6 +250,34 @@ def test_persistent_cg_matches_per_step_launches(ctx, cfg, precision):
     assert abs(out[0][1].iters - out[1][1].iters) <= 2
 
 
+@pytest.mark.parametrize("make,hyb_k", [(lambda: W.spd_powerlaw(8000, seed=2), 0),
+                                         (lambda: W.spd_powerlaw(8000, seed=2), 2),
+                                         (lambda: W.poisson3d(21), 3)])
+@pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
+def test_persistent_cg_hyb_with_a_coo_part(ctx, make, hyb_k, precision):
+    """HYB whose rows overflow the ELL width keeps the persistent CG kernel: the
+    COO tail is added by warp-segmented sums and atomics into a second buffer.
+    Power-law rows (segments longer than a warp) and a 3D Poisson grid of odd
+    order (n = 9261, an odd last element) against the one-launch-per-step path,
+    the oracle, and chunked launches that alternate with per-step launches."""
+    A = make()
+    b = rhs(A, 13)
+    ref = oracle.cg(A, b, tol=1e-10)
+    cfg = C.config("HYB", hyb_k=hyb_k)
+    runs = {}
+    for mode, chunk in ((0, 0), (1, 0), (2, 7)):
+        x, info = gpu_solve(ctx, A, b, tol=1e-10, force=cfg, precision=precision,
+                            iteration_kernel=mode, persist_chunk=chunk)
+        assert info.status == 0 and true_relres(A, x, b) <= 1e-10, (hyb_k, mode)
+        assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+        assert info.final_cfg.fmt == C.FMT_HYB
+        runs[mode] = info
+    assert runs[0].persist_iters > 0 and runs[0].persist_launches >= 1
+    assert runs[1].persist_iters == 0
+    assert runs[2].persist_iters > 0 and runs[2].persist_launches >= 2
+    assert abs(runs[0].iters - runs[1].iters) <= 2
+
+
 def fixed_gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05, feat_ms=0.0, small_rows=0):
     return C.Gate.from_dict({"speedup": [1.0] + [speedup] * 5, "conv_a_ms": [0.0] + [conv_ms] * 5,
                              "conv_b_ms": [0.0] * 6, "spmv_a_ms": spmv_ms, "spmv_b_ms": 0.0,
