@@ -782,7 +782,12 @@ def run_profile_cg(args):
     from paper_2411_10143_b300 import cascade as C
 
     ctx = C.Context(0)
-    A, xs = workload()
+    if args.profile_matrix == "spd_powerlaw":
+        from paper_2411_10143_b300 import workloads as W
+        A = W.spd_powerlaw()
+        xs = W.vector(A.ncols, W.RHS_SEED_BASE + 3)
+    else:
+        A, xs = workload()
     M = ctx.load(A)
     xs_d = torch.as_tensor(xs, device="cuda")
     b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
@@ -858,6 +863,9 @@ def main():
                     help="profiling aid: the predicted SpMV of each sweep matrix, 3 launches")
     ap.add_argument("--profile-cg", default=None, metavar="FMT",
                     help="profiling aid: forced-configuration CG solves (e.g. DIA), no bench line")
+    ap.add_argument("--profile-matrix", default="poisson3d", choices=["poisson3d", "spd_powerlaw"],
+                    help="--profile-cg's system: the bench's 3D Poisson, or the SPD power law "
+                         "(n 500k) of the spd_powerlaw_cg leg")
     ap.add_argument("--profile-precision", type=int, default=0,
                     help="with --profile-cg: 0 FP64, 1 FP32 inner solves in FP64 refinement")
     ap.add_argument("--profile-gmres", default=None, metavar="FMT",

@@ -127,6 +127,7 @@ struct PersistMat {
   int64_t coo_n = 0;
   const int32_t *coo_row = nullptr, *coo_col = nullptr;
   const T* coo_val = nullptr;
+  int coo_vec = 0;  // all three 16-byte aligned: vector loads of 8 entries
 };
 
 // y = alpha A x + beta y (GEN) or y = A x over the rows of the format's
@@ -155,35 +156,117 @@ __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t*
 }
 
 // HYB's COO tail in a persistent SpMV phase: yc[row] += val * x[col] for every
-// tail entry, through FP64 (FP32) atomics, one per row segment of a warp's 32
-// consecutive entries (a segmented scan over the lanes: the entries are in row
-// order).  Returns the thread's share of sum_e x[row_e] val_e x[col_e], the
-// tail's part of (x, A x).  yc must not be the ELL part's output (other blocks
-// add to any row while the ELL rows are stored).
+// tail entry, through FP64 (FP32) atomics.  The entries are in row order.  A
+// warp takes a tile of 32 * kCooTailE consecutive entries, each lane
+// kCooTailE consecutive ones: a lane sums its entries row by row with one FMA
+// each and adds a row that starts and ends inside it at once; the rows that
+// cross lanes are combined by a segmented scan of the lanes' last partial sums
+// and added once per row and tile.  On parts with a reduced FP64 rate the FP64
+// instructions bound this loop, and a lane per entry (a product, a scan of five
+// additions and a dot-product FMA for every 32 entries) spent about three times
+// as many as this.  Returns the thread's share of sum_e x[row_e] val_e x[col_e],
+// the tail's part of (x, A x).  yc must not be the ELL part's output (other
+// blocks add to any row while the ELL rows are stored).
+constexpr int kCooTailE = 8;
+
+__device__ __forceinline__ void ld8_ro(const int32_t* p, int32_t (&o)[8]) {
+  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+  const int4 b = __ldg(reinterpret_cast<const int4*>(p) + 1);
+  o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w, o[4] = b.x, o[5] = b.y, o[6] = b.z, o[7] = b.w;
+}
+__device__ __forceinline__ void ld8_ro(const double* p, double (&o)[8]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldg(reinterpret_cast<const double2*>(p) + k);
+    o[2 * k] = a.x, o[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void ld8_ro(const float* p, float (&o)[8]) {
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p) + k);
+    o[4 * k] = a.x, o[4 * k + 1] = a.y, o[4 * k + 2] = a.z, o[4 * k + 3] = a.w;
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x, T* yc) {
+  constexpr int E = kCooTailE;
+  static_assert(E == 8, "the vector loads take 8 entries");
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   T dot = 0;
-  for (int64_t e0 = gw * 32; e0 < a.coo_n; e0 += nw * 32) {
-    const int64_t e = e0 + lane;
-    const bool in = e < a.coo_n;
-    const int32_t r = in ? ld_stream(a.coo_row + e) : -1 - lane;  // padding: distinct rows
-    T v = 0;
-    if (in) {
-      v = ld_stream(a.coo_val + e) * ld_x<true>(x + ld_stream(a.coo_col + e));
-      dot = fma(ld_cg(x + r), v, dot);
+  for (int64_t e0 = gw * 32 * E; e0 < a.coo_n; e0 += nw * 32 * E) {
+    const int64_t el = e0 + (int64_t)lane * E;  // this lane's first entry
+    const int64_t left = a.coo_n - el;
+    const int mine = left <= 0 ? 0 : (left < E ? (int)left : E);
+    int32_t r[E], c[E];
+    T v[E];
+    if (mine == E && a.coo_vec) {
+      ld8_ro(a.coo_row + el, r);
+      ld8_ro(a.coo_col + el, c);
+      ld8_ro(a.coo_val + el, v);
+    } else {
+      // a lane's missing entries repeat its last row with a zero value, and a
+      // lane without entries has a negative row of its own, never flushed
+#pragma unroll
+      for (int u = 0; u < E; ++u) {
+        const bool in = u < mine;
+        r[u] = in ? __ldg(a.coo_row + el + u) : (u > 0 ? r[u - 1] : -1 - lane);
+        c[u] = in ? __ldg(a.coo_col + el + u) : -1;
+        v[u] = in ? __ldg(a.coo_val + el + u) : T(0);
+      }
     }
+    T xg[E];
+#pragma unroll
+    for (int u = 0; u < E; ++u) xg[u] = c[u] >= 0 ? ld_x<true>(x + c[u]) : T(0);
+    const int32_t first = r[0];
+    int32_t cur = first;
+    T run = 0, head = 0;
+    bool split = false;  // a row ended inside this lane
+#pragma unroll
+    for (int u = 0; u < E; ++u) {
+      if (u > 0 && r[u] != cur) {
+        if (split) {  // the row lies inside this lane: its whole tail part
+          atomicAdd(yc + cur, run);
+          dot = fma(ld_cg(x + cur), run, dot);
+        } else {
+          head = run;  // the lane's first row, which may continue from the left
+        }
+        split = true;
+        cur = r[u];
+        run = 0;
+      }
+      run = fma(v[u], xg[u], run);
+    }
+    // segmented inclusive scan of the lanes' last partial sums: a run of lanes
+    // starts at a lane whose last row began inside it or differs from the
+    // previous lane's last row
+    const int32_t prev_cur = __shfl_up_sync(full, cur, 1);
+    T sv = run;
+    bool f = lane == 0 || split || prev_cur != cur;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const T up = __shfl_up_sync(full, v, o);
-      const int32_t ru = __shfl_up_sync(full, r, o);
-      if (lane >= o && ru == r) v += up;  // sorted rows: equal ends mean one segment
+      const T up = __shfl_up_sync(full, sv, o);
+      const bool fup = __shfl_up_sync(full, (int)f, o) != 0;
+      if (lane >= o) {
+        if (!f) sv += up;
+        f = f || fup;
+      }
     }
-    const int32_t rn = __shfl_down_sync(full, r, 1);
-    if (in && (lane == 31 || rn != r)) atomicAdd(yc + r, v);
+    const T sv_prev = __shfl_up_sync(full, sv, 1);
+    const int32_t next_first = __shfl_down_sync(full, first, 1);
+    if (split && first >= 0) {  // the first row ends here: add the lanes before with that row
+      const T cs = head + (lane > 0 && prev_cur == first ? sv_prev : T(0));
+      atomicAdd(yc + first, cs);
+      dot = fma(ld_cg(x + first), cs, dot);
+    }
+    if (cur >= 0 && (lane == 31 || next_first != cur)) {  // the last lane of a run
+      atomicAdd(yc + cur, sv);
+      dot = fma(ld_cg(x + cur), sv, dot);
+    }
   }
   return dot;
 }
@@ -254,6 +337,8 @@ void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launc
           a.coo_row = m->hyb_coo.row;
           a.coo_col = m->hyb_coo.col;
           a.coo_val = PersistVals<T>::coo(m->hyb_coo);
+          auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+          a.coo_vec = al16(a.coo_row) && al16(a.coo_col) && al16(a.coo_val);
           launch(IntC<kPersistHyb>{}, IntC<1>{});
         } else {
           CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent kernel for HYB with a COO part");
