@@ -169,26 +169,6 @@ __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t*
 // blocks add to any row while the ELL rows are stored).
 constexpr int kCooTailE = 8;
 
-__device__ __forceinline__ void ld8_ro(const int32_t* p, int32_t (&o)[8]) {
-  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
-  const int4 b = __ldg(reinterpret_cast<const int4*>(p) + 1);
-  o[0] = a.x, o[1] = a.y, o[2] = a.z, o[3] = a.w, o[4] = b.x, o[5] = b.y, o[6] = b.z, o[7] = b.w;
-}
-__device__ __forceinline__ void ld8_ro(const double* p, double (&o)[8]) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const double2 a = __ldg(reinterpret_cast<const double2*>(p) + k);
-    o[2 * k] = a.x, o[2 * k + 1] = a.y;
-  }
-}
-__device__ __forceinline__ void ld8_ro(const float* p, float (&o)[8]) {
-#pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    const float4 a = __ldg(reinterpret_cast<const float4*>(p) + k);
-    o[4 * k] = a.x, o[4 * k + 1] = a.y, o[4 * k + 2] = a.z, o[4 * k + 3] = a.w;
-  }
-}
-
 template <typename T>
 __device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x, T* yc) {
   constexpr int E = kCooTailE;

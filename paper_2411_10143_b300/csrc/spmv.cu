@@ -221,10 +221,12 @@ __global__ void __launch_bounds__(kBlock) k_dia(
 }
 
 // ------------------------------------------------------------------ COO (warp-tiled segmented sums)
-// Each warp takes kCooWarpTile consecutive entries (sorted by row), loads them
-// coalesced into its slice of shared memory, and each lane takes its kCooItems
-// consecutive entries into registers, gathers x for all of them and sums them
-// row by row in a fully unrolled walk (one FMA per entry).
+// Each warp takes kCooWarpTile consecutive entries (sorted by row); each lane
+// loads its kCooItems consecutive entries straight into registers (16-byte
+// vector loads through L1, which serves the second half of every sector),
+// gathers x for all of them and sums them row by row in a fully unrolled walk
+// (one FMA per entry).  (Staging the tile through shared memory for coalesced
+// loads left the kernel throttled on the shared-memory pipe.)
 // A row inside one lane's entries is written directly.  Rows that span lanes
 // are combined with a segmented shuffle scan over the lanes' last segments;
 // the lane that holds a row's last entry in the warp writes it, with an atomic
@@ -233,7 +235,7 @@ __global__ void __launch_bounds__(kBlock) k_dia(
 // same per entry as short ones.  ADD: y already holds the rest of the row
 // (beta*y, or HYB's ELL part) and every write adds to it; otherwise y is zero
 // and a row completed in one place is stored.
-constexpr int kCooItems = 7;
+constexpr int kCooItems = 8;
 constexpr int kCooWarpTile = 32 * kCooItems;
 
 template <typename T, bool ADD>
@@ -247,40 +249,32 @@ __global__ void __launch_bounds__(kBlock) k_coo(
     const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, T alpha,
     const int* __restrict__ skip) {
   if (skip && *skip) return;
-  // the warp's tile passes through shared memory: coalesced loads in, then each
-  // lane reads its consecutive entries (a stride of 7 words, or 14 for FP64,
-  // maps every 16-lane phase onto distinct banks)
-  __shared__ int32_t s_r[kBlock / 32][kCooWarpTile];
-  __shared__ int32_t s_c[kBlock / 32][kCooWarpTile];
-  __shared__ T s_v[kBlock / 32][kCooWarpTile];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  static_assert(kCooItems == 8, "the vector loads take 8 entries");
+  const int lane = threadIdx.x & 31;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t ntiles = (nnz + kCooWarpTile - 1) / kCooWarpTile;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const bool vec = al16(row) && al16(col) && al16(val);
   for (int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; t < ntiles;
        t += nwarps) {
     const int64_t e0 = t * kCooWarpTile;
     const int cnt = (int)(nnz - e0 < kCooWarpTile ? nnz - e0 : kCooWarpTile);
     const int j0 = lane * kCooItems;
     const int mine = cnt - j0 < 0 ? 0 : (cnt - j0 < kCooItems ? cnt - j0 : kCooItems);
-    __syncwarp();  // the previous tile's reads of the slice are done
-#pragma unroll
-    for (int u = 0; u < kCooItems; ++u) {
-      const int k = u * 32 + lane;
-      if (k < cnt) {
-        s_r[wib][k] = ld_stream(row + e0 + k);
-        s_c[wib][k] = ld_stream(col + e0 + k);
-        s_v[wib][k] = ld_stream(val + e0 + k);
-      }
-    }
-    __syncwarp();
     int32_t r[kCooItems], c[kCooItems];
     T w[kCooItems], xv[kCooItems];
+    if (vec && mine == kCooItems) {
+      ld8_ro(row + e0 + j0, r);
+      ld8_ro(col + e0 + j0, c);
+      ld8_ro(val + e0 + j0, w);
+    } else {
 #pragma unroll
-    for (int u = 0; u < kCooItems; ++u) {
-      const bool in = u < mine;
-      r[u] = in ? s_r[wib][j0 + u] : -1;
-      c[u] = in ? s_c[wib][j0 + u] : 0;
-      w[u] = in ? s_v[wib][j0 + u] : T(0);
+      for (int u = 0; u < kCooItems; ++u) {
+        const bool in = u < mine;
+        r[u] = in ? __ldg(row + e0 + j0 + u) : -1;
+        c[u] = in ? __ldg(col + e0 + j0 + u) : 0;
+        w[u] = in ? __ldg(val + e0 + j0 + u) : T(0);
+      }
     }
 #pragma unroll
     for (int u = 0; u < kCooItems; ++u) xv[u] = u < mine ? ld_ro(x + c[u]) : T(0);
@@ -422,7 +416,7 @@ void merge_partition(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
             m->nnz, m->rowptr, m->merge_tiles, m->merge_start);
 }
 
-// The merge-path and COO kernels stage ~25-40 KB of a tile in shared memory:
+// The merge-path kernel stages ~25-40 KB of a tile in shared memory:
 // prefer the largest shared-memory carve-out so that several blocks share an SM.
 void spmv_set_attributes() {
   const int carve = cudaSharedmemCarveoutMaxShared;
@@ -434,19 +428,22 @@ void spmv_set_attributes() {
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
   CP_CUDA(cudaFuncSetAttribute(k_csr_merge<float, true>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_coo<double, false>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_coo<double, true>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_coo<float, false>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_coo<float, true>,
-                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
 }
 
+// One wave of the COO kernel: its registers (not the thread limit) bound the
+// blocks an SM holds, and a second wave would only queue behind the first.
+template <typename T, bool ADD>
 static int coo_grid(cp_ctx* ctx, int64_t nnz) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_coo<T, ADD>, kBlock, 0) != cudaSuccess)
+      b = 1;
+    return b > 0 ? b : 1;
+  }();
+  int64_t cap = (int64_t)ctx->num_sms * per_sm;
+  if (cap > ctx->grid_stream) cap = ctx->grid_stream;
   const int64_t tiles = (nnz + kCooWarpTile * (kBlock / 32) - 1) / (kCooWarpTile * (kBlock / 32));
-  return (int)(tiles < 1 ? 1 : tiles < ctx->grid_stream ? tiles : ctx->grid_stream);
+  return (int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap);
 }
 
 // One routine for both forms: GEN = general alpha/beta, DOT = fused partials.
@@ -506,7 +503,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
                 m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, nullptr, nullptr,
                 skip);
       if (m->hyb_coo.n > 0)
-        CP_LAUNCH(ctx, (k_coo<T, true>), coo_grid(ctx, m->hyb_coo.n),
+        CP_LAUNCH(ctx, (k_coo<T, true>), (coo_grid<T, true>(ctx, m->hyb_coo.n)),
                   kBlock, 0, s, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
                   Vals<T>::coo(m->hyb_coo), x, y, GEN ? alpha : T(1), skip);
       break;
@@ -520,10 +517,10 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
     case CP_FMT_COO: {
       CP_LAUNCH(ctx, k_scale<T>, grid_for(ctx, n), kBlock, 0, s, n, y, GEN ? beta : T(0), skip);
       if (m->nnz > 0 && GEN && beta != T(0))
-        CP_LAUNCH(ctx, (k_coo<T, true>), coo_grid(ctx, m->nnz), kBlock, 0, s, m->nnz, m->coo.row,
+        CP_LAUNCH(ctx, (k_coo<T, true>), (coo_grid<T, true>(ctx, m->nnz)), kBlock, 0, s, m->nnz, m->coo.row,
                   m->col, Vals<T>::csr(m), x, y, alpha, skip);
       else if (m->nnz > 0)
-        CP_LAUNCH(ctx, (k_coo<T, false>), coo_grid(ctx, m->nnz), kBlock, 0, s, m->nnz,
+        CP_LAUNCH(ctx, (k_coo<T, false>), (coo_grid<T, false>(ctx, m->nnz)), kBlock, 0, s, m->nnz,
                   m->coo.row, m->col, Vals<T>::csr(m), x, y, GEN ? alpha : T(1), skip);
       break;
     }
