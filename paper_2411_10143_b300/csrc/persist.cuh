@@ -229,6 +229,7 @@ __device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x,
     bool f = lane == 0 || split || prev_cur != cur;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+      if (__all_sync(full, f)) break;  // every run is complete
       const T up = __shfl_up_sync(full, sv, o);
       const bool fup = __shfl_up_sync(full, (int)f, o) != 0;
       if (lane >= o) {

@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(kBlock) k_coo(
     bool f = lane == 0 || multi || prev_cur != cur;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
+      if (__all_sync(0xffffffffu, f)) break;  // every run is complete (short rows)
       const T up = __shfl_up_sync(0xffffffffu, v, o);
       const bool fup = __shfl_up_sync(0xffffffffu, (int)f, o) != 0;
       if (lane >= o) {
