@@ -238,12 +238,20 @@ __global__ void __launch_bounds__(kBlock) k_dia(
 constexpr int kCooItems = 8;
 constexpr int kCooWarpTile = 32 * kCooItems;
 
-template <typename T, bool ADD>
+// ONE: alpha is 1, and a write spends no FP64 instruction (a store, or an
+// atomic add, which the L2 performs): on B300 the FP64 pipe, not DRAM, bounds
+// this kernel on matrices with short rows.
+template <typename T, bool ADD, bool ONE>
 __device__ __forceinline__ void coo_put(T* y, int32_t r, T alpha, T s) {
-  y[r] = ADD ? fma(alpha, s, y[r]) : alpha * s;
+  if constexpr (ONE) {
+    if constexpr (ADD) atomicAdd(y + r, s);  // the row is this warp's alone: the same sum
+    else y[r] = s;
+  } else {
+    y[r] = ADD ? fma(alpha, s, y[r]) : alpha * s;
+  }
 }
 
-template <typename T, bool ADD>
+template <typename T, bool ADD, bool ONE>
 __global__ void __launch_bounds__(kBlock) k_coo(
     int64_t nnz, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
     const T* __restrict__ val, const T* __restrict__ x, T* __restrict__ y, T alpha,
@@ -287,7 +295,7 @@ __global__ void __launch_bounds__(kBlock) k_coo(
       if (u < mine) {
         if (u > 0 && r[u] != cur) {
           if (!multi) head = sum;  // the first segment closes
-          else coo_put<T, ADD>(y, cur, alpha, sum);  // a row inside this lane only
+          else coo_put<T, ADD, ONE>(y, cur, alpha, sum);  // a row inside this lane only
           multi = true;
           cur = r[u];
           sum = 0;
@@ -319,13 +327,13 @@ __global__ void __launch_bounds__(kBlock) k_coo(
       // the first row ends in this lane: add the run of preceding lanes' last
       // segments with that row (the scan value of the previous lane)
       const T cs = head + (lane > 0 && prev_cur == first ? v_prev : T(0));
-      if (warp_row0 == first) atomicAdd(y + first, alpha * cs);  // may start in an earlier warp
-      else coo_put<T, ADD>(y, first, alpha, cs);
+      if (warp_row0 == first) atomicAdd(y + first, ONE ? cs : alpha * cs);  // may start earlier
+      else coo_put<T, ADD, ONE>(y, first, alpha, cs);
     }
     if (mine > 0 && (last_in_warp || next_first != cur)) {
       // this lane holds the last entry in the warp of its last row
-      if (last_in_warp || warp_row0 == cur) atomicAdd(y + cur, alpha * v);
-      else coo_put<T, ADD>(y, cur, alpha, v);
+      if (last_in_warp || warp_row0 == cur) atomicAdd(y + cur, ONE ? v : alpha * v);
+      else coo_put<T, ADD, ONE>(y, cur, alpha, v);
     }
   }
 }
@@ -433,11 +441,12 @@ void spmv_set_attributes() {
 
 // One wave of the COO kernel: its registers (not the thread limit) bound the
 // blocks an SM holds, and a second wave would only queue behind the first.
-template <typename T, bool ADD>
+template <typename T, bool ADD, bool ONE>
 static int coo_grid(cp_ctx* ctx, int64_t nnz) {
   static const int per_sm = [] {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_coo<T, ADD>, kBlock, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_coo<T, ADD, ONE>, kBlock, 0) !=
+        cudaSuccess)
       b = 1;
     return b > 0 ? b : 1;
   }();
@@ -445,6 +454,19 @@ static int coo_grid(cp_ctx* ctx, int64_t nnz) {
   if (cap > ctx->grid_stream) cap = ctx->grid_stream;
   const int64_t tiles = (nnz + kCooWarpTile * (kBlock / 32) - 1) / (kCooWarpTile * (kBlock / 32));
   return (int)(tiles < 1 ? 1 : tiles < cap ? tiles : cap);
+}
+
+// y (+)= alpha A x over COO entries (row-sorted), with the alpha == 1 variant
+// when it applies.
+template <typename T, bool ADD>
+static void launch_coo(cp_ctx* ctx, int64_t nnz, const int32_t* row, const int32_t* col,
+                       const T* val, const T* x, T* y, T alpha, const int* skip, cudaStream_t s) {
+  if (alpha == T(1))
+    CP_LAUNCH(ctx, (k_coo<T, ADD, true>), (coo_grid<T, ADD, true>(ctx, nnz)), kBlock, 0, s, nnz,
+              row, col, val, x, y, alpha, skip);
+  else
+    CP_LAUNCH(ctx, (k_coo<T, ADD, false>), (coo_grid<T, ADD, false>(ctx, nnz)), kBlock, 0, s, nnz,
+              row, col, val, x, y, alpha, skip);
 }
 
 // One routine for both forms: GEN = general alpha/beta, DOT = fused partials.
@@ -504,9 +526,8 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
                 m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, nullptr, nullptr,
                 skip);
       if (m->hyb_coo.n > 0)
-        CP_LAUNCH(ctx, (k_coo<T, true>), (coo_grid<T, true>(ctx, m->hyb_coo.n)),
-                  kBlock, 0, s, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
-                  Vals<T>::coo(m->hyb_coo), x, y, GEN ? alpha : T(1), skip);
+        launch_coo<T, true>(ctx, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
+                            Vals<T>::coo(m->hyb_coo), x, y, GEN ? alpha : T(1), skip, s);
       break;
     }
     case CP_FMT_DIA: {
@@ -518,11 +539,11 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
     case CP_FMT_COO: {
       CP_LAUNCH(ctx, k_scale<T>, grid_for(ctx, n), kBlock, 0, s, n, y, GEN ? beta : T(0), skip);
       if (m->nnz > 0 && GEN && beta != T(0))
-        CP_LAUNCH(ctx, (k_coo<T, true>), (coo_grid<T, true>(ctx, m->nnz)), kBlock, 0, s, m->nnz, m->coo.row,
-                  m->col, Vals<T>::csr(m), x, y, alpha, skip);
+        launch_coo<T, true>(ctx, m->nnz, m->coo.row, m->col, Vals<T>::csr(m), x, y, alpha, skip,
+                            s);
       else if (m->nnz > 0)
-        CP_LAUNCH(ctx, (k_coo<T, false>), (coo_grid<T, false>(ctx, m->nnz)), kBlock, 0, s, m->nnz,
-                  m->coo.row, m->col, Vals<T>::csr(m), x, y, GEN ? alpha : T(1), skip);
+        launch_coo<T, false>(ctx, m->nnz, m->coo.row, m->col, Vals<T>::csr(m), x, y,
+                             GEN ? alpha : T(1), skip, s);
       break;
     }
     default:

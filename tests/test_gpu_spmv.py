@@ -67,14 +67,18 @@ def test_spmv_random_fp64_and_fp32(ctx, mi):
         assert np.linalg.norm(y32 - ref32) <= 1e-5 * max(np.linalg.norm(ref32), 1e-30), repr(cfg)
 
 
-def test_spmv_general_alpha_beta(ctx):
+@pytest.mark.parametrize("alpha,beta", [(0.5, -2.0), (0.5, 0.0), (1.0, 3.0)])
+def test_spmv_general_alpha_beta(ctx, alpha, beta):
+    """y = alpha A x + beta y0 in every configuration: the general form, a scaled
+    product over a zero y, and alpha = 1 over a nonzero y (the COO kernel's
+    alpha = 1 variants add with atomics)."""
     A = ragged_matrices(False)[2]
     M = ctx.load(A)
     x = W.vector(A.ncols, 1)
     y0 = W.vector(A.nrows, 2)
-    ref = 0.5 * oracle.spmv(A, x) - 2.0 * y0
+    ref = alpha * oracle.spmv(A, x) + beta * y0
     for cfg in usable(A, all_configs()):
-        y = run(M, cfg, x, alpha=0.5, beta=-2.0, y0=y0)
+        y = run(M, cfg, x, alpha=alpha, beta=beta, y0=y0)
         assert np.linalg.norm(y - ref) <= 1e-12 * np.linalg.norm(ref), repr(cfg)
 
 
