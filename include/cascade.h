@@ -283,9 +283,9 @@ typedef struct {
   int32_t check_every;   /* iterations between host convergence checks (0: default 8)   */
   int32_t profile;       /* 1: time every SpMV launch with CUDA events (t_spmv_ms)        */
   int32_t iteration_kernel; /* CG and GMRES: 0 = one persistent cooperative launch runs
-                            the iterations while the format has a row-parallel kernel
-                            (CSR scalar / vector, ELL, SELL, DIA, HYB without COO part)
-                            and no prediction work is pending on the side stream,
+                            the iterations while the format has a persistent kernel
+                            (CSR scalar / vector, ELL, SELL, DIA, HYB, COO; not
+                            CSR-merge) and no prediction work is pending on the side stream,
                             falling back to one launch per step otherwise; 1 = always
                             one launch per step; 2 = alternate persistent launches of
                             persist_chunk iterations with as many one-launch-per-step

@@ -8,7 +8,9 @@
 // Gram-Schmidt subtraction, the update of x) runs over those same rows, so what
 // a block's SpMV wrote is read back by the block after a __syncthreads: the
 // first Gram-Schmidt pass needs no grid barrier after the SpMV.  (SELL with a
-// row permutation is the exception and takes one.)
+// row permutation is the exception and takes one; so do HYB with a COO part and
+// COO, whose COO entries every block adds by atomics into a zeroed vector that
+// each block then folds into its own rows.)
 //
 // Step j of a cycle, w = column j + 1 of V, orthogonalised by modified
 // Gram-Schmidt in groups of g columns (g = 4 in FP64, 8 in FP32; see the
@@ -89,6 +91,19 @@ struct BlockRows {
     return (f >> lshift) * S + base + (f & ((1ll << lshift) - 1));
   }
 };
+
+// HYB with a COO part, and COO: the product's COO entries went to wc through
+// atomics from every block; after a grid barrier each block adds its own rows
+// into y (scaled like the rest of the product) and leaves wc zero again.
+template <typename T>
+__device__ __forceinline__ void fold_tail(const BlockRows& br, T* y, T* wc, T alpha) {
+  for (int64_t f = threadIdx.x; f < br.count; f += blockDim.x) {
+    const int64_t i = br.row(f);
+    y[i] = fma(alpha, ld_cg(wc + i), ld_cg(y + i));
+    wc[i] = T(0);
+  }
+  __syncthreads();
+}
 
 // Sums G values (G = 2, 4, 8 or 16) over the warp: at each of the first log2(G)
 // exchanges a lane keeps half of its values and adds its partner's copies of
@@ -459,7 +474,11 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       // The block's rows of w stay in shared memory.
       persist_spmv<T, F, TPV, true, false>(a, so, V + (int64_t)j * ldv, w, (T)sc[j], T(0),
                                            nullptr);
-      if (!fused) {
+      if constexpr (F == kPersistHyb) {
+        coo_tail_atomic<T, false>(a, V + (int64_t)j * ldv, a.wc);
+        if (!barrier()) break;
+        fold_tail(br, w, a.wc, (T)sc[j]);
+      } else if (!fused) {
         if (!barrier()) break;
       } else {
         __syncthreads();  // the block reads back the rows its threads wrote
@@ -544,6 +563,11 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       // ---- 1. w = A v_j, first-pass dots
       persist_spmv<T, F, TPV, true, false>(a, so, V + (int64_t)j * ldv, w, (T)sc[j], T(0),
                                            nullptr);
+      if constexpr (F == kPersistHyb) {
+        coo_tail_atomic<T, false>(a, V + (int64_t)j * ldv, a.wc);
+        if (!barrier()) break;
+        fold_tail(br, w, a.wc, (T)sc[j]);
+      }
       if (!fused && !barrier()) break;
       block_dots<T>(br, V, ldv, j + 2, j + 1, a.part, wp);
       lap(0);
@@ -712,7 +736,11 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
     if (!barrier()) break;
     // ---- restart: r = b - A x into column 0, the true-residual test
     persist_spmv<T, F, TPV, false, false>(a, so, a.x, V, T(1), T(0), nullptr);
-    if (!fused) {
+    if constexpr (F == kPersistHyb) {
+      coo_tail_atomic<T, false>(a, a.x, a.wc);
+      if (!barrier()) break;
+      fold_tail(br, V, a.wc, T(1));
+    } else if (!fused) {
       if (!barrier()) break;
     } else {
       __syncthreads();
@@ -827,13 +855,13 @@ static void gm_launch_one(cp_ctx* ctx, GmPersistArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 bool gm_persist_supported(const cp_mat* m, const cp_config& c, int mrest) {
-  return persist_format_ok(m, c) && mrest >= 1 && mrest <= kMaxRestart;
+  return persist_format_ok(m, c, true) && mrest >= 1 && mrest <= kMaxRestart;
 }
 
 template <typename T>
 void gm_persist_launch(cp_ctx* ctx, cp_mat* m, const cp_config& c, GmPersistArgs<T> a,
                        cudaStream_t s) {
-  persist_dispatch<T>(m, c, a, [&](auto f, auto tpv) {
+  persist_dispatch<T, true>(m, c, a, [&](auto f, auto tpv) {
     gm_launch_one<T, decltype(f)::value, decltype(tpv)::value>(ctx, a, s);
   });
 }

@@ -48,6 +48,7 @@ struct GmPersistArgs : PersistMat<T> {
   int64_t ldv = 0;
   T* x = nullptr;
   const T* b = nullptr;
+  T* wc = nullptr;  // HYB / COO: the COO entries' part of a product, zero between products
   double *part = nullptr, *part2 = nullptr;  // (m + 2) x grid block partials each
   double* pn = nullptr;                      // grid block partials
   GmState* st = nullptr;

@@ -557,13 +557,14 @@ static int grid_n(cp_ctx* ctx, int64_t n) {
 template <typename T>
 struct CgBufs {
   T *r = nullptr, *p = nullptr, *ap = nullptr, *xw = nullptr;
-  T* apc = nullptr;  // HYB's COO part of A p in the persistent kernel (zeroed on allocation)
+  T* apc = nullptr;  // the COO entries' part of A p in the persistent kernel (HYB, COO)
   double *pa = nullptr, *pb = nullptr, *pc = nullptr;
   CgState* st = nullptr;
 };
 template <typename T>
 struct GmBufs {
   T *V = nullptr, *tmp = nullptr;
+  T* wc = nullptr;  // the COO entries' part of A v in the persistent kernel (HYB, COO)
   double *part = nullptr, *part2 = nullptr, *pn = nullptr;
   GmState* st = nullptr;
   int mrest = 0;
@@ -826,7 +827,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
         pa_args.r = r;
         pa_args.p = p;
         pa_args.ap = ap;
-        if (cs.cur.fmt == CP_FMT_HYB && m->hyb_coo.n > 0) {
+        if ((cs.cur.fmt == CP_FMT_HYB && m->hyb_coo.n > 0) || cs.cur.fmt == CP_FMT_COO) {
           if (!B.apc) {  // the kernel leaves it zero after every iteration
             B.apc = ws.get<T>(n);
             CP_CUDA(cudaMemsetAsync(B.apc, 0, n * sizeof(T), s));
@@ -1030,6 +1031,13 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
         ga.tol2 = tol2;
         if (cs.wait_limit_ms > 0.0)
           ga.barrier_timeout_ns = (long long)(cs.wait_limit_ms * 1e6);
+        if ((cs.cur.fmt == CP_FMT_HYB && m->hyb_coo.n > 0) || cs.cur.fmt == CP_FMT_COO) {
+          if (!B.wc) {  // the kernel leaves it zero after every product
+            B.wc = ws.get<T>(n);
+            CP_CUDA(cudaMemsetAsync(B.wc, 0, n * sizeof(T), s));
+          }
+          ga.wc = B.wc;
+        }
         const int it_before = res.iters + j;
         cudaEvent_t e0 = ctx->events.take(true), e1 = ctx->events.take(true);
         CP_CUDA(cudaEventRecord(e0, s));

@@ -46,7 +46,7 @@ enum {
   kPersistEll = 2,
   kPersistSell = 3,
   kPersistDia = 4,
-  kPersistHyb = 5  // HYB with a COO part: ELL rows plus the COO tail (CG only)
+  kPersistHyb = 5  // HYB with a COO part (ELL rows plus the COO tail), or COO (no ELL part)
 };
 
 // ------------------------------------------------------------------ grid barrier
@@ -109,7 +109,7 @@ struct PersistMat {
   // CSR
   const int32_t *rp = nullptr, *ci = nullptr;
   const T* v = nullptr;
-  // ELL (or HYB without a COO part)
+  // ELL, or HYB's ELL part (K = 0 for COO)
   int64_t K = 0, ld = 0;
   const int32_t* ec = nullptr;
   const T* ev = nullptr;
@@ -164,12 +164,13 @@ __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t*
 // and added once per row and tile.  On parts with a reduced FP64 rate the FP64
 // instructions bound this loop, and a lane per entry (a product, a scan of five
 // additions and a dot-product FMA for every 32 entries) spent about three times
-// as many as this.  Returns the thread's share of sum_e x[row_e] val_e x[col_e],
-// the tail's part of (x, A x).  yc must not be the ELL part's output (other
-// blocks add to any row while the ELL rows are stored).
+// as many as this.  DOT: returns the thread's share of
+// sum_e x[row_e] val_e x[col_e], the tail's part of (x, A x).  yc must not be
+// the ELL part's output (other blocks add to any row while the ELL rows are
+// stored).
 constexpr int kCooTailE = 8;
 
-template <typename T>
+template <typename T, bool DOT = true>
 __device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x, T* yc) {
   constexpr int E = kCooTailE;
   static_assert(E == 8, "the vector loads take 8 entries");
@@ -211,7 +212,7 @@ __device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x,
       if (u > 0 && r[u] != cur) {
         if (split) {  // the row lies inside this lane: its whole tail part
           atomicAdd(yc + cur, run);
-          dot = fma(ld_cg(x + cur), run, dot);
+          if (DOT) dot = fma(ld_cg(x + cur), run, dot);
         } else {
           head = run;  // the lane's first row, which may continue from the left
         }
@@ -242,11 +243,11 @@ __device__ __forceinline__ T coo_tail_atomic(const PersistMat<T>& a, const T* x,
     if (split && first >= 0) {  // the first row ends here: add the lanes before with that row
       const T cs = head + (lane > 0 && prev_cur == first ? sv_prev : T(0));
       atomicAdd(yc + first, cs);
-      dot = fma(ld_cg(x + first), cs, dot);
+      if (DOT) dot = fma(ld_cg(x + first), cs, dot);
     }
     if (cur >= 0 && (lane == 31 || next_first != cur)) {  // the last lane of a run
       atomicAdd(yc + cur, sv);
-      dot = fma(ld_cg(x + cur), sv, dot);
+      if (DOT) dot = fma(ld_cg(x + cur), sv, dot);
     }
   }
   return dot;
@@ -272,15 +273,29 @@ struct PersistVals<float> {
 };
 
 // Formats a persistent kernel runs: CSR (scalar or vector), ELL, HYB without a
-// COO part (which is ELL), SELL and DIA; with coo_tail, HYB with a COO part too.
+// COO part (which is ELL), SELL and DIA; with coo_tail, HYB with a COO part and
+// COO too (kPersistHyb: the caller's kernel adds the entries by atomics).
 inline bool persist_format_ok(const cp_mat* m, const cp_config& c, bool coo_tail = false) {
   if (c.fmt == CP_FMT_CSR) return c.algo == CP_ALGO_SCALAR || c.algo == CP_ALGO_VECTOR;
   if (c.fmt == CP_FMT_HYB) return m->hyb_coo.n == 0 || coo_tail;
+  if (c.fmt == CP_FMT_COO) return coo_tail;
   return c.fmt == CP_FMT_ELL || c.fmt == CP_FMT_SELL || c.fmt == CP_FMT_DIA;
 }
 
 template <int V>
 using IntC = std::integral_constant<int, V>;
+
+// The COO entries a kPersistHyb kernel adds by atomics (row order).
+template <typename T>
+void persist_tail(PersistMat<T>& a, int64_t n, const int32_t* row, const int32_t* col,
+                  const T* val) {
+  a.coo_n = n;
+  a.coo_row = row;
+  a.coo_col = col;
+  a.coo_val = val;
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  a.coo_vec = al16(row) && al16(col) && al16(val);
+}
 
 // Fills a's format fields from m's data for configuration c and calls
 // launch(IntC<F>{}, IntC<TPV>{}) with the matching kernel variant.  TAIL: the
@@ -314,12 +329,8 @@ void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launc
       a.ev = PersistVals<T>::ell(e);
       if (c.fmt == CP_FMT_HYB && m->hyb_coo.n > 0) {
         if constexpr (TAIL) {
-          a.coo_n = m->hyb_coo.n;
-          a.coo_row = m->hyb_coo.row;
-          a.coo_col = m->hyb_coo.col;
-          a.coo_val = PersistVals<T>::coo(m->hyb_coo);
-          auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-          a.coo_vec = al16(a.coo_row) && al16(a.coo_col) && al16(a.coo_val);
+          persist_tail(a, m->hyb_coo.n, m->hyb_coo.row, m->hyb_coo.col,
+                       PersistVals<T>::coo(m->hyb_coo));
           launch(IntC<kPersistHyb>{}, IntC<1>{});
         } else {
           CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent kernel for HYB with a COO part");
@@ -329,6 +340,17 @@ void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launc
       }
       break;
     }
+    case CP_FMT_COO:
+      // HYB with an empty ELL part: every entry is in the tail
+      if constexpr (TAIL) {
+        a.K = 0;
+        a.ld = m->nrows;
+        persist_tail(a, m->nnz, m->coo.row, m->col, PersistVals<T>::csr(m));
+        launch(IntC<kPersistHyb>{}, IntC<1>{});
+      } else {
+        CP_REQUIRE(false, CP_ERR_UNSUPPORTED, "no persistent kernel for COO");
+      }
+      break;
     case CP_FMT_SELL:
       a.nchunks = m->sell.nchunks;
       a.perm = m->sell.sigma > 1 ? m->sell.perm : nullptr;
@@ -353,7 +375,7 @@ void persist_dispatch(cp_mat* m, const cp_config& c, PersistMat<T>& a, L&& launc
 template <typename T>
 struct PersistArgs : PersistMat<T> {
   T *x = nullptr, *r = nullptr, *p = nullptr, *ap = nullptr;
-  T* apc = nullptr;  // HYB: the COO tail's part of Ap, zero between iterations
+  T* apc = nullptr;  // HYB / COO: the COO entries' part of Ap, zero between iterations
   double *pa = nullptr, *pb = nullptr;  // block partials, capacity >= grid
   CgState* st = nullptr;
   Mirror* mir = nullptr;

@@ -84,6 +84,8 @@ extern "C" cp_status cp_warmup(cp_ctx* ctx) {
     add(CP_FMT_ELL, CP_ALGO_SCALAR, 8, 1);
     for (int sigma : {1, 32, 1024, 8192}) add(CP_FMT_SELL, CP_ALGO_SCALAR, 8, sigma);
     add(CP_FMT_HYB, CP_ALGO_SCALAR, 8, 1);
+    add(CP_FMT_HYB, CP_ALGO_SCALAR, 8, 1);
+    cfgs.back().hyb_k = 3;  // rows longer than 3: a COO part (the persistent tail variants)
     add(CP_FMT_DIA, CP_ALGO_SCALAR, 8, 1);
 
     cp_solve_opts o;

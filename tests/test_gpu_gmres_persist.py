@@ -21,12 +21,15 @@ from paper_2411_10143_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-# Row-parallel configurations the persistent kernel runs.  SELL with sigma > 1
-# permutes rows inside its sorting windows, so its SpMV rows are not the
-# block's own rows and the kernel takes a grid barrier after the SpMV.
+# Configurations the persistent kernel runs.  SELL with sigma > 1 permutes rows
+# inside its sorting windows, so its SpMV rows are not the block's own rows and
+# the kernel takes a grid barrier after the SpMV.  HYB with K = 3 has a COO part
+# on the 7-point stencil, and COO is all COO part: their COO entries go through
+# atomics into a zeroed vector, a grid barrier, then each block's own rows.
 CFGS = [C.config("CSR"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
         C.config("CSR", C.ALGO_VECTOR, tpv=32), C.config("ELL"), C.config("SELL", sigma=1),
-        C.config("SELL", sigma=1024), C.config("DIA"), C.config("HYB")]
+        C.config("SELL", sigma=1024), C.config("DIA"), C.config("HYB"),
+        C.config("HYB", hyb_k=3), C.config("COO")]
 
 
 @pytest.fixture(scope="module")
@@ -88,14 +91,14 @@ def test_persistent_gmres_matches_per_step_launches(ctx, cfg, m):
         assert info.status == 0, (repr(cfg), kernel)
         check(A, b, x, ref)
         out[kernel] = info
-    if cfg.fmt != C.FMT_HYB:  # HYB runs persistently only without a COO part
-        assert out[0].persist_iters == out[0].iters and out[0].persist_launches >= 1
+    assert out[0].persist_iters == out[0].iters and out[0].persist_launches >= 1
     assert out[1].persist_iters == 0 and out[1].persist_launches == 0
     assert close_iters(out[0].iters, out[1].iters), (out[0].iters, out[1].iters)
 
 
 @pytest.mark.parametrize("cfg", [C.config("CSR"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
-                                 C.config("SELL", sigma=1024), C.config("DIA")], ids=repr)
+                                 C.config("SELL", sigma=1024), C.config("DIA"),
+                                 C.config("HYB", hyb_k=3), C.config("COO")], ids=repr)
 @pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
 @pytest.mark.parametrize("m", [4, 30])
 def test_persistent_gmres_classical_orthogonalisation(ctx, cfg, precision, m):
@@ -110,7 +113,8 @@ def test_persistent_gmres_classical_orthogonalisation(ctx, cfg, precision, m):
 
 
 @pytest.mark.parametrize("cfg", [C.config("DIA"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
-                                 C.config("SELL", sigma=1024)], ids=repr)
+                                 C.config("SELL", sigma=1024), C.config("HYB", hyb_k=3),
+                                 C.config("COO")], ids=repr)
 def test_persistent_gmres_rows_in_several_segments(ctx, cfg):
     """n = 175,616 is more than one row per thread of the grid, so every block
     owns several row segments (CSR-vector with 4 lanes a row: segments of 256
@@ -121,6 +125,34 @@ def test_persistent_gmres_rows_in_several_segments(ctx, cfg):
     assert info.status == 0 and info.persist_iters == info.iters
     check(A, b, x, ref)
     assert close_iters(info.iters, ref.iters), (info.iters, ref.iters)
+
+
+@functools.lru_cache(maxsize=None)
+def powerlaw_system():
+    """A diagonally dominant nonsymmetric power-law matrix (n = 6,000, rows up to
+    400 entries) with b = A x*, and the oracle's GMRES(30) solution."""
+    A = W.diagonally_dominant(W.powerlaw(6000, lmax=400, seed=8))
+    b = oracle.spmv(A, W.vector(A.ncols, 23))
+    return A, b, oracle.gmres(A, b, m=30, tol=1e-10)
+
+
+@pytest.mark.parametrize("cfg", [C.config("HYB"), C.config("HYB", hyb_k=1), C.config("COO")],
+                         ids=repr)
+@pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
+def test_persistent_gmres_power_law_coo_entries(ctx, cfg, precision):
+    """Power-law rows (COO runs of several hundred entries across lanes, warps
+    and blocks) through the persistent kernel's atomic COO path, in both
+    precisions, against the per-step launches and the oracle."""
+    A, b, ref = powerlaw_system()
+    out = {}
+    for kernel in (0, 1):
+        x, info = solve(ctx, A, b, restart=30, tol=1e-10, force=cfg, iteration_kernel=kernel,
+                        precision=precision, inner_tol=1e-5)
+        assert info.status == 0, (repr(cfg), kernel)
+        check(A, b, x, ref)
+        out[kernel] = info
+    assert out[0].persist_iters == out[0].iters and out[0].persist_launches >= 1
+    assert out[1].persist_iters == 0
 
 
 @pytest.mark.parametrize("m", [1, 3, 4, 8, 9, 17])

@@ -250,27 +250,30 @@ def test_persistent_cg_matches_per_step_launches(ctx, cfg, precision):
     assert abs(out[0][1].iters - out[1][1].iters) <= 2
 
 
-@pytest.mark.parametrize("make,hyb_k", [(lambda: W.spd_powerlaw(8000, seed=2), 0),
-                                         (lambda: W.spd_powerlaw(8000, seed=2), 2),
-                                         (lambda: W.poisson3d(21), 3)])
+@pytest.mark.parametrize("make,fmt,hyb_k", [(lambda: W.spd_powerlaw(8000, seed=2), "HYB", 0),
+                                             (lambda: W.spd_powerlaw(8000, seed=2), "HYB", 2),
+                                             (lambda: W.spd_powerlaw(8000, seed=2), "COO", 0),
+                                             (lambda: W.poisson3d(21), "HYB", 3),
+                                             (lambda: W.poisson3d(21), "COO", 0)])
 @pytest.mark.parametrize("precision", [C.PREC_FP64, C.PREC_FP32_IR])
-def test_persistent_cg_hyb_with_a_coo_part(ctx, make, hyb_k, precision):
-    """HYB whose rows overflow the ELL width keeps the persistent CG kernel: the
-    COO tail is added by warp-segmented sums and atomics into a second buffer.
-    Power-law rows (segments longer than a warp) and a 3D Poisson grid of odd
-    order (n = 9261, an odd last element) against the one-launch-per-step path,
-    the oracle, and chunked launches that alternate with per-step launches."""
+def test_persistent_cg_hyb_with_a_coo_part(ctx, make, fmt, hyb_k, precision):
+    """HYB whose rows overflow the ELL width, and COO, keep the persistent CG
+    kernel: the COO entries are added by lane sums, a segmented scan across
+    lanes and atomics into a second buffer.  Power-law rows (runs longer than a
+    warp's tile) and a 3D Poisson grid of odd order (n = 9261, an odd last
+    element) against the one-launch-per-step path, the oracle, and chunked
+    launches that alternate with per-step launches."""
     A = make()
     b = rhs(A, 13)
     ref = oracle.cg(A, b, tol=1e-10)
-    cfg = C.config("HYB", hyb_k=hyb_k)
+    cfg = C.config(fmt, hyb_k=hyb_k)
     runs = {}
     for mode, chunk in ((0, 0), (1, 0), (2, 7)):
         x, info = gpu_solve(ctx, A, b, tol=1e-10, force=cfg, precision=precision,
                             iteration_kernel=mode, persist_chunk=chunk)
         assert info.status == 0 and true_relres(A, x, b) <= 1e-10, (hyb_k, mode)
         assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
-        assert info.final_cfg.fmt == C.FMT_HYB
+        assert info.final_cfg.fmt == cfg.fmt
         runs[mode] = info
     assert runs[0].persist_iters > 0 and runs[0].persist_launches >= 1
     assert runs[1].persist_iters == 0
