@@ -281,6 +281,43 @@ def test_persistent_cg_hyb_with_a_coo_part(ctx, make, fmt, hyb_k, precision):
     assert abs(runs[0].iters - runs[1].iters) <= 2
 
 
+def arrow_spd(n, seed):
+    """Row 0 and column 0 dense, a diagonal elsewhere: A[0, j] = A[j, 0] = a_j
+    ~ U[-1, 1], A[j, j] = 1 + |a_j|, A[0, 0] = 1 + sum |a_j| (strictly diagonally
+    dominant, so SPD).  Row 0 holds n entries: in HYB's COO part and in COO it
+    spans tiles of many warps and blocks, all adding into one row."""
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(-1.0, 1.0, n - 1)
+    rowptr = np.zeros(n + 1, np.int32)
+    rowptr[1] = n
+    rowptr[2:] = n + 2 * np.arange(1, n)
+    col = np.empty(n + 2 * (n - 1), np.int32)
+    val = np.empty(col.size)
+    col[:n] = np.arange(n)
+    val[0] = 1.0 + np.abs(a).sum()
+    val[1:n] = a
+    col[n::2] = 0
+    col[n + 1::2] = np.arange(1, n)
+    val[n::2] = a
+    val[n + 1::2] = 1.0 + np.abs(a)
+    return W.Matrix(n, n, rowptr, col, val)
+
+
+@pytest.mark.parametrize("cfg", [C.config("HYB"), C.config("COO")], ids=repr)
+@pytest.mark.parametrize("kind", ["cg", "gmres"])
+def test_persistent_solvers_one_dense_row(ctx, cfg, kind):
+    """An arrow matrix (n = 20,001: one row of 20,001 entries) in the persistent
+    kernels' COO path against the per-step launches and the oracle."""
+    A = arrow_spd(20001, 5)
+    b = rhs(A, 14)
+    ref = oracle.cg(A, b, tol=1e-10) if kind == "cg" else oracle.gmres(A, b, m=30, tol=1e-10)
+    for mode in (0, 1):
+        x, info = gpu_solve(ctx, A, b, kind=kind, tol=1e-10, force=cfg, iteration_kernel=mode)
+        assert info.status == 0 and true_relres(A, x, b) <= 1e-10, (kind, mode)
+        assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+        assert (info.persist_iters > 0) == (mode == 0)
+
+
 def fixed_gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05, feat_ms=0.0, small_rows=0):
     return C.Gate.from_dict({"speedup": [1.0] + [speedup] * 5, "conv_a_ms": [0.0] + [conv_ms] * 5,
                              "conv_b_ms": [0.0] * 6, "spmv_a_ms": spmv_ms, "spmv_b_ms": 0.0,
