@@ -257,9 +257,11 @@ cp_status cp_csr_load(cp_ctx* ctx, int64_t nrows, int64_t ncols, int64_t nnz,
     m->ncols = ncols;
     m->nnz = nnz;
     try {
-      m->rowptr = dalloc<int32_t>(nrows + 1);
-      m->col = dalloc<int32_t>(nnz);
-      m->val = dalloc<double>(nnz);
+      // from the context's stream-ordered pool, which keeps its memory: a load
+      // after the first spends no time mapping fresh device memory
+      m->rowptr = dalloc_async<int32_t>(nrows + 1, ctx->main);
+      m->col = dalloc_async<int32_t>(nnz, ctx->main);
+      m->val = dalloc_async<double>(nnz, ctx->main);
       const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
       CP_CUDA(cudaMemcpyAsync(m->rowptr, rowptr, (nrows + 1) * 4, kind, ctx->main));
       if (nnz > 0) {
@@ -268,9 +270,10 @@ cp_status cp_csr_load(cp_ctx* ctx, int64_t nrows, int64_t ncols, int64_t nnz,
       }
       csr_validate(ctx, m);  // synchronises the main stream
     } catch (...) {
-      dfree(m->rowptr);
-      dfree(m->col);
-      dfree(m->val);
+      dfree_async(m->rowptr, ctx->main);
+      dfree_async(m->col, ctx->main);
+      dfree_async(m->val, ctx->main);
+      cudaStreamSynchronize(ctx->main);
       delete m;
       throw;
     }
@@ -285,9 +288,10 @@ cp_status cp_mat_free(cp_mat* m) {
     cudaStreamSynchronize(m->ctx->main);
     cudaStreamSynchronize(m->ctx->side);
     free_formats(m);
-    dfree(m->rowptr);
-    dfree(m->col);
-    dfree(m->val);
+    dfree_async(m->rowptr, m->ctx->main);
+    dfree_async(m->col, m->ctx->main);
+    dfree_async(m->val, m->ctx->main);
+    cudaStreamSynchronize(m->ctx->main);
     delete m;
   });
 }
