@@ -747,6 +747,40 @@ struct ConfigSource {
   }
 };
 
+// How many one-launch-per-step iterations the host keeps queued.  A newly
+// published configuration applies only to iterations not yet queued, so while
+// the cascade may still publish, the queue holds about kQueueAheadUs of device
+// time (at least two iterations, at most depth), from the host's pace while it
+// waits for the device (about one iteration's device time per loop).  Slow
+// default-kernel iterations (CSR-scalar on power-law rows: hundreds of us)
+// then switch within a few iterations instead of depth; otherwise the queue
+// is depth deep.
+struct QueueLimit {
+  static constexpr double kQueueAheadUs = 300.0;
+  int depth, lim;
+  bool adapt;
+  double ema_us = 0.0;
+  std::chrono::steady_clock::time_point last;
+  bool have_last = false;
+  QueueLimit(int d, bool cascade) : depth(d), lim(cascade ? std::min(2, d) : d), adapt(cascade) {}
+  int limit(bool pending) {
+    if (!adapt || !pending) return depth;
+    return lim;
+  }
+  void waited() {
+    if (!adapt) return;
+    const auto now = std::chrono::steady_clock::now();
+    if (have_last) {
+      const double dt = std::chrono::duration<double, std::micro>(now - last).count();
+      ema_us = ema_us > 0.0 ? 0.5 * ema_us + 0.5 * dt : dt;
+      const int want = (int)std::ceil(kQueueAheadUs / std::max(ema_us, 1.0));
+      lim = std::max(std::min(2, depth), std::min(depth, want));
+    }
+    last = now;
+    have_last = true;
+  }
+};
+
 // SpMV of the configuration in force (T selects FP64 or FP32 values).
 template <typename T>
 static int spmv_cur(ConfigSource& cs, const T* x, T* y, const T* dotv, double* part,
@@ -807,6 +841,7 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
               keep_bb ? 1 : 0);
     keep_bb = true;
     int issued = 0;
+    QueueLimit ql(depth, cs.ch != nullptr);
     while (it < maxit) {
       cs.poll(it);
       // The persistent kernel runs only while no prediction work is pending on the
@@ -886,8 +921,11 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       ++issued;
       ++it;
       cs.after_step();
-      if (issued >= depth) {
-        CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));  // the one issued depth ago
+      const int lim = ql.limit(cs.ch && !cs.ch->finished.load(std::memory_order_acquire));
+      if (issued >= lim) {
+        // the one issued lim ago (lim <= depth: its ring slot is not reused yet)
+        CP_CUDA(cudaEventSynchronize(ws.event(issued - lim, depth)));
+        ql.waited();
         if (ws.mir->done) break;
       }
       // the loop head hands the remaining iterations to the persistent kernel
