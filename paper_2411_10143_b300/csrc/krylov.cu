@@ -1034,6 +1034,7 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
     }
     int steps = std::min(mrest, maxit - res.iters);  // this cycle's length
     int issued = 0;
+    QueueLimit ql(depth, cs.ch != nullptr);
     bool x_updated = false;  // the persistent kernel ended the cycle and updated x
     int j = 0;
     while (j < steps) {
@@ -1145,8 +1146,10 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       ++issued;
       ++j;
       cs.after_step();
-      if (issued >= depth) {
-        CP_CUDA(cudaEventSynchronize(ws.event(issued, depth)));
+      const int lim = ql.limit(cs.ch && !cs.ch->finished.load(std::memory_order_acquire));
+      if (issued >= lim) {
+        CP_CUDA(cudaEventSynchronize(ws.event(issued - lim, depth)));
+        ql.waited();
         if (ws.mir->halt) break;
       }
     }
