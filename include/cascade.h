@@ -71,7 +71,8 @@ typedef struct {
   int32_t tpv;        /* CSR-vector threads per row: 2, 4, 8, 16 or 32                */
   int32_t sell_c;     /* SELL chunk height; only 32 is supported (one warp per chunk) */
   int32_t sell_sigma; /* SELL sort window: 1 (no sort) or a multiple of 32, <= 8192   */
-  int32_t hyb_k;      /* HYB ELL width; 0 = ceil(mean row length)                     */
+  int32_t hyb_k;      /* HYB ELL width; 0 = the 75th percentile of the row lengths (at
+                          least 1; ceil(mean row length) if that is 1,023 or more)      */
 } cp_config;
 
 /* The default configuration every solve starts from: CSR, scalar kernel (one

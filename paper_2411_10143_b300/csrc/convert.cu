@@ -6,6 +6,8 @@
 #include <climits>
 #include <cstring>
 
+#include <vector>
+
 #include "common.cuh"
 #include "internal.cuh"
 
@@ -632,11 +634,60 @@ bool config_equal(const cp_config& a, const cp_config& b) {
   }
 }
 
-int64_t hyb_width(const cp_mat* m, const cp_config& c) {
+// Rows by length for HYB's width rule: lengths 0 .. kLenBins - 2, longer rows
+// in the last bin.
+constexpr int kLenBins = 1024;
+__global__ void k_row_length_hist(int64_t n, const int32_t* __restrict__ rp,
+                                  unsigned* __restrict__ hist) {
+  __shared__ unsigned h[kLenBins];
+  for (int i = threadIdx.x; i < kLenBins; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int64_t len = (int64_t)rp[i + 1] - rp[i];
+    atomicAdd(&h[len < kLenBins - 1 ? len : kLenBins - 1], 1u);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kLenBins; i += blockDim.x)
+    if (h[i]) atomicAdd(&hist[i], h[i]);
+}
+
+// HYB's ELL width K (Sec. III-B-2 lists it among the format's parameters; the
+// paper fixes no default).  hyb_k > 0 gives it.  Otherwise K is the smallest
+// width (at least 1) that at most a quarter of the rows exceed, the 75th
+// percentile of the row lengths: one more slot a row costs n ELL slots and
+// saves one COO entry per longer row, and on this GPU a COO entry costs about
+// four ELL slots (a fit of HYB SpMV times over K on a power-law matrix), so the
+// total stops falling where a quarter of the rows are longer.  If that
+// percentile is past the histogram (rows of 1,023 entries or more),
+// ceil(mean row length).  Found once per matrix.
+int64_t hyb_width(cp_ctx* ctx, cp_mat* m, const cp_config& c, cudaStream_t s) {
   if (c.hyb_k > 0) return c.hyb_k;
-  // ceil(mean row length), at least 1
-  const int64_t k = (m->nnz + m->nrows - 1) / m->nrows;
-  return k < 1 ? 1 : k;
+  if (m->hyb_auto_k > 0) return m->hyb_auto_k;
+  unsigned* d = dalloc_async<unsigned>(kLenBins, s);
+  std::vector<unsigned> h(kLenBins);
+  try {
+    CP_CUDA(cudaMemsetAsync(d, 0, kLenBins * sizeof(unsigned), s));
+    CP_LAUNCH(ctx, k_row_length_hist, grid_cap(ctx, m->nrows), kBlock, 0, s, m->nrows,
+              m->rowptr, d);
+    static_assert(kLenBins * sizeof(unsigned) <= 4096, "one staged copy");
+    d2h_small(ctx, h.data(), d, kLenBins * sizeof(unsigned), s);
+  } catch (...) {
+    dfree_async(d, s);
+    throw;
+  }
+  dfree_async(d, s);
+  int64_t K = 0, over = m->nrows - (int64_t)h[0];  // rows longer than K
+  while (K < kLenBins - 2 && (K < 1 || 4 * over > m->nrows)) {
+    ++K;
+    over -= h[K];
+  }
+  if (4 * over > m->nrows) {  // the percentile is in the last bin
+    K = (m->nnz + m->nrows - 1) / m->nrows;
+    if (K < 1) K = 1;
+  }
+  m->hyb_auto_k = K;
+  return K;
 }
 
 static void free_ell(EllPart& e) {
@@ -904,7 +955,7 @@ void ensure_format(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, cudaStream_t s)
       if (!m->has_sell || m->sell.sigma != cfg.sell_sigma) convert_sell(ctx, m, cfg.sell_sigma, s);
       break;
     case CP_FMT_HYB: {
-      const int64_t K = hyb_width(m, cfg);
+      const int64_t K = hyb_width(ctx, m, cfg, s);
       if (!m->has_hyb || m->hyb_ell.K != K) convert_hyb(ctx, m, K, s);
       break;
     }

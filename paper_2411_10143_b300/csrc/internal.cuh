@@ -259,6 +259,7 @@ struct cp_mat {
   cp::SellPart sell;
   cp::EllPart hyb_ell;
   cp::CooPart hyb_coo;
+  int64_t hyb_auto_k = 0;  // HYB's width for hyb_k = 0, found on first use
   cp::DiaPart dia;
   bool has_features = false;
   double features[15] = {0};
@@ -284,7 +285,7 @@ void format_export(cp_mat* m, const cp_config& cfg, int array_id, void* dst, int
 void free_formats(cp_mat* m);
 void config_check(const cp_config& c);  // throws CP_ERR_UNSUPPORTED
 bool config_equal(const cp_config& a, const cp_config& b);
-int64_t hyb_width(const cp_mat* m, const cp_config& c);
+int64_t hyb_width(cp_ctx* ctx, cp_mat* m, const cp_config& c, cudaStream_t s);
 
 // SpMV for the solvers: y = A x and, when dotv is non-null, block partial sums
 // of y .* dotv written to partials[0..P); returns P (0 without dotv).

@@ -15,6 +15,17 @@ from gpu_helpers import ragged_matrices
 pytestmark = pytest.mark.gpu
 
 
+def hyb_auto_width(A):
+    """HYB's width for hyb_k = 0 as the header defines it: the smallest K >= 1 that
+    at most a quarter of the rows exceed, else ceil(mean row length) when that
+    is 1,023 or more."""
+    lens = np.diff(A.rowptr)
+    for K in range(1, 1023):
+        if 4 * np.count_nonzero(lens > K) <= A.nrows:
+            return K
+    return max(1, -(-A.nnz // A.nrows))
+
+
 @pytest.fixture(scope="module")
 def ctx():
     c = C.Context(0)
@@ -47,7 +58,7 @@ def test_conversions_bit_exact(ctx, mi):
         assert np.array_equal(M.format_export(cfg, "SELL_COL", np.int32), scol), sigma
         assert np.array_equal(bits(M.format_export(cfg, "SELL_VAL", np.float64)), bits(sval))
     for hk in (0, 1, 3):
-        Kh = hk if hk > 0 else max(1, -(-A.nnz // A.nrows))
+        Kh = hk if hk > 0 else hyb_auto_width(A)
         ld, ec, ev, cr, cc, cv = oracle.to_hyb(A, Kh)
         cfg = C.config("HYB", hyb_k=hk)
         assert M.format_dims(cfg)[:3] == [Kh, ld, len(cr)]
