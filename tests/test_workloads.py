@@ -101,3 +101,28 @@ def test_uniform_rows():
     valid_csr(A)
     lens = np.diff(A.rowptr)
     assert lens.max() == 8 and lens.mean() > 7.99  # rare duplicate draws merged
+
+
+def test_request_stream_mix_sizes_and_arrivals():
+    """Serving requests: Poisson arrivals at the given rate, n log-uniform in
+    [1e3, 1e6], 40 % Poisson (2D and 3D half each), 30 % SPD power law, 30 %
+    convection-diffusion; a request's system has about n rows."""
+    reqs = W.request_stream(4000, rate_per_s=50.0, seed=3000)
+    kinds = np.array([r.kind for r in reqs])
+    share = {k: np.mean(kinds == k) for k in ("poisson2d", "poisson3d", "spd_powerlaw", "convdiff")}
+    assert abs(share["poisson2d"] + share["poisson3d"] - 0.4) < 0.03
+    assert abs(share["poisson2d"] - share["poisson3d"]) < 0.04
+    assert abs(share["spd_powerlaw"] - 0.3) < 0.03 and abs(share["convdiff"] - 0.3) < 0.03
+    n = np.array([r.n for r in reqs])
+    assert n.min() >= 1000 and n.max() <= 1_000_000
+    logn = np.log10(n)
+    assert abs(np.median(logn) - 4.5) < 0.1  # the middle of [3, 6] on a log scale
+    assert abs(np.mean((logn >= 3.0) & (logn < 4.0)) - 1 / 3) < 0.03
+    t = np.array([r.arrival_s for r in reqs])
+    gaps = np.diff(t)
+    assert np.all(gaps > 0) and abs(gaps.mean() * 50.0 - 1.0) < 0.05
+    assert abs(np.std(gaps) / np.mean(gaps) - 1.0) < 0.1  # exponential gaps
+    for r in reqs[:12]:
+        A = W.request_matrix(r) if r.n < 30000 else None
+        if A is not None:
+            assert 0.5 * r.n <= A.nrows <= 2.0 * r.n, (r.kind, r.n, A.nrows)
