@@ -5,8 +5,9 @@
 // Every kernel is a persistent grid-stride kernel launched with the resident
 // grid of the device (a multiple of the SM count), so a fused reduction leaves
 // one partial per block and the consumer can sum them in a fixed order.
-// Matrix arrays are read with evict-first loads; x is gathered through the
-// read-only path.  T is the value type (double, or float for the FP32 inner
+// Matrix arrays are read with evict-first loads (COO's through the read-only
+// path, whose L1 serves the second half of each sector its vector loads touch);
+// x is gathered through the read-only path.  T is the value type (double, or float for the FP32 inner
 // solves).  No tensor cores: SpMV moves 12 bytes per FP64 non-zero for one
 // FMA, far below any tensor-core shape's arithmetic intensity.
 #include "common.cuh"
