@@ -6,6 +6,7 @@ the FP64 derived ones agree to 1e-12 (the GPU takes sd from exact integer
 sums, the oracle sums (mean - r_i)^2 row by row)."""
 import numpy as np
 import pytest
+import torch
 
 import oracle
 from paper_2411_10143_b300 import cascade as C
@@ -102,3 +103,29 @@ def test_features_long_rows_and_structures(ctx):
             W.uniform_random(5000, 8, seed=3, ncols=7000)]
     for A in mats:
         check_features(ctx.load(A).features(), oracle.features(A))
+
+
+@pytest.mark.parametrize("k,lens", [(1100, None), (4000, "skewed")])
+def test_hyb_default_width_rule(ctx, k, lens):
+    """hyb_k = 0: the 75th percentile of the row lengths, and ceil(mean) when that
+    lies past the 1,023-entry histogram (a dense 1,100 x 1,100 matrix); the
+    layout equals the oracle's at that width and the SpMV agrees."""
+    if lens is None:
+        A = W.dense_matrix(k, seed=3)
+    else:
+        A = W.random_csr(k, k, [1, 2, 2, 3, 40] * (k // 5), seed=6)
+    K = hyb_auto_width(A)
+    assert K == (k if lens is None else 3)
+    M = ctx.load(A)
+    cfg = C.config("HYB")
+    ld, ec, ev, cr, cc, cv = oracle.to_hyb(A, K)
+    assert M.format_dims(cfg)[:3] == [K, ld, len(cr)]
+    assert np.array_equal(M.format_export(cfg, "HYB_ELL_COL", np.int32), ec)
+    assert np.array_equal(M.format_export(cfg, "HYB_COO_ROW", np.int32), cr)
+    x = W.vector(A.ncols, 2)
+    ref = oracle.spmv(A, x)
+    xd = torch.as_tensor(x, device="cuda")
+    yd = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+    M.spmv(xd, yd, cfg)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(yd.cpu().numpy() - ref) <= 1e-12 * np.linalg.norm(ref)
