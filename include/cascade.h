@@ -90,6 +90,11 @@ void cp_config_default(cp_config* cfg);
  * (Sec. III-C-2).
  * Errors: CP_ERR_INVALID (bad device), CP_ERR_CUDA, CP_ERR_OOM. */
 cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_stream);
+/* cp_destroy: waits for the context's streams, stops its prediction side
+ * thread (the second thread of Sec. III-C-2's asynchronous model), releases
+ * its device memory pool, pinned buffers and the streams it created (streams
+ * the caller passed stay the caller's).  Every cp_mat of the context must be
+ * freed first.  NULL is accepted (no-op).  Errors: CP_ERR_CUDA. */
 cp_status cp_destroy(cp_ctx* ctx);
 
 /* Message describing the last error of the calling thread ("" if none). */
@@ -99,7 +104,10 @@ const char* cp_last_error(void);
 cp_status cp_ctx_launch_count(cp_ctx* ctx, int64_t* count);
 
 /* ------------------------------------------------------------------ matrices */
-/* cp_csr_load: copies a CSR matrix into library-owned device memory and
+/* cp_csr_load: the online stage starts from a given iterative solver, sparse
+ * matrix and default SpMV configuration (Sec. III-A, Fig. 3); this call hands
+ * the matrix, in CSR (the default configuration's format), to the library.
+ * It copies a CSR matrix into library-owned device memory and
  * validates it on the device (rowptr[0] = 0, rowptr non-decreasing,
  * rowptr[nrows] = nnz, 0 <= col < ncols, columns strictly increasing within
  * each row).  rowptr[nrows+1], col[nnz], val[nnz] are host pointers when
@@ -110,6 +118,10 @@ cp_status cp_ctx_launch_count(cp_ctx* ctx, int64_t* count);
 cp_status cp_csr_load(cp_ctx* ctx, int64_t nrows, int64_t ncols, int64_t nnz,
                       const int32_t* rowptr, const int32_t* col, const double* val,
                       int32_t on_device, cp_mat** out);
+/* cp_mat_free: releases the CSR copy and every converted format and cached
+ * feature vector of `mat` (the storage a format change costs, Sec. III-C-1),
+ * after the context's streams have finished with them.  NULL is accepted.
+ * Errors: CP_ERR_CUDA. */
 cp_status cp_mat_free(cp_mat* mat);
 
 /* cp_mat_reset: drop every converted format and the cached features of `mat`,
@@ -195,8 +207,11 @@ cp_status cp_spmv(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32_t dtype,
  *    768 KiB file-scope device array that every GPU loading the library keeps
  *    until the process exits; nrows + nnz may be at most 117,440,512
  *    (65,536 tiles), larger inputs return CP_ERR_INVALID.
- *  - The first call on a device looks up that array's device address
- *    (cudaGetSymbolAddress); make it before any stream capture.
+ *  - The first call on a device, with that device current, does a one-time
+ *    set-up: it looks up that array's device address (cudaGetSymbolAddress),
+ *    reads the SM count and sets the kernel's function attributes.  Make that
+ *    first call before any stream capture; a call on a 1-row matrix with
+ *    nnz = 0 (rowptr = {0, 0}, col and val may be NULL) is enough.
  *  - Work is queued on `stream` (a cudaStream_t, NULL = the default stream) of
  *    the current device; the call does not synchronise.  Every call shares the
  *    one scratch array, so calls that overlap on the GPU (other streams or
@@ -259,6 +274,21 @@ cp_status cp_adam_step(cp_ctx* ctx, int64_t nparams, float* params, const float*
 cp_status cp_model_train(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
                          const int32_t* labels, int32_t h1, int32_t h2, int32_t k,
                          int32_t epochs, float lr, uint64_t seed, float* final_loss);
+
+/* cp_predict_stage: one cascade stage's classifier (Sec. III-B-3: one trained
+ * model per stage of Fig. 5's cascade) applied to a given feature vector, with
+ * the kernel and the installed weights the cascade itself uses.
+ *  - features15: host double[15], the Table IV features in cp_features order.
+ *  - logits: host float[k] (k = the stage's classes, see the stage list above)
+ *    or NULL; receives the stage's FP32 logits.
+ *  - pick: host, may be NULL; receives the arg-max class (the first on ties),
+ *    the choice the cascade takes at that stage.
+ * Runs on the side stream and waits for it.  Exposed so that the inference
+ * can be checked against a reference implementation of the classifier.
+ * Errors: CP_ERR_INVALID (NULL features, bad stage, no model installed in the
+ * stage), CP_ERR_CUDA. */
+cp_status cp_predict_stage(cp_ctx* ctx, int32_t stage, const double* features15, float* logits,
+                           int32_t* pick);
 
 /* cp_predict: the sequential cascaded prediction (SerGMRES-style, Sec. IV-C):
  * features, then FORMAT, then the algorithm / parameter stage that applies,

@@ -183,6 +183,7 @@ _SIGS = {
     "cp_model_train": (c_int32, [_p, c_int32, c_int64, _p, _p, c_int32, c_int32, c_int32,
                                  c_int32, c_float, c_uint64, POINTER(c_float)]),
     "cp_predict": (c_int32, [_p, _p, POINTER(Config), _p]),
+    "cp_predict_stage": (c_int32, [_p, c_int32, _p, _p, POINTER(c_int32)]),
     "cp_solve_cg": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_solve_gmres": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_batch_solve": (c_int32, [_p, c_int32, _p, _p, _p, _p, POINTER(SolveOpts), c_int32,
@@ -240,15 +241,38 @@ def _np(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
 
 
-def spmv_csr_merge_noalloc(nrows, ncols, rowptr, col, val, x, y, stream=None):
+def spmv_csr_merge_noalloc(nrows, ncols, rowptr, col, val, x, y, stream=None, nnz=None):
     """cp_spmv_csr_merge_noalloc on torch CUDA tensors: y = A x with no device
     allocation (fixed library scratch; see cascade.h for its limit and for why
-    overlapping calls must be serialised)."""
+    overlapping calls must be serialised).
+
+    The C entry point does not validate the CSR, so the arrays' types, device,
+    layout and lengths are checked here before any pointer reaches a kernel:
+    int32 rowptr / col, float64 val / x / y, contiguous, on the current CUDA
+    device, rowptr of nrows + 1 entries, col and val of at least nnz entries,
+    x of at least ncols and y of at least nrows.  ``nnz`` defaults to
+    ``col.numel()``; pass it when col / val are slices of a larger arena buffer.
+    """
     import torch
+    nrows, ncols = int(nrows), int(ncols)
+    nnz = int(col.numel()) if nnz is None else int(nnz)
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("rowptr", rowptr, torch.int32), ("col", col, torch.int32),
+                        ("val", val, torch.float64), ("x", x, torch.float64),
+                        ("y", y, torch.float64)):
+        if not isinstance(t, torch.Tensor) or t.dtype != dt or not t.is_cuda or \
+                t.device.index != dev or not t.is_contiguous():
+            raise CascadeError(ERR_INVALID, f"spmv_csr_merge_noalloc: {name} must be a "
+                               f"contiguous {dt} tensor on cuda:{dev}")
+    if nrows < 1 or ncols < 1 or nnz < 0:
+        raise CascadeError(ERR_INVALID, "spmv_csr_merge_noalloc: sizes out of range")
+    if rowptr.numel() != nrows + 1 or col.numel() < nnz or val.numel() < nnz or \
+            x.numel() < ncols or y.numel() < nrows:
+        raise CascadeError(ERR_INVALID, "spmv_csr_merge_noalloc: an array is shorter than "
+                           "its size argument (rowptr nrows+1, col/val nnz, x ncols, y nrows)")
     s = (stream or torch.cuda.current_stream()).cuda_stream
-    _check(lib().cp_spmv_csr_merge_noalloc(int(nrows), int(ncols), int(col.numel()), _ptr(rowptr),
-                                           _ptr(col), _ptr(val), _ptr(x), _ptr(y),
-                                           c_void_p(s) if s else None))
+    _check(lib().cp_spmv_csr_merge_noalloc(nrows, ncols, nnz, _ptr(rowptr), _ptr(col), _ptr(val),
+                                           _ptr(x), _ptr(y), c_void_p(s) if s else None))
 
 
 def default_opts(**kw) -> SolveOpts:
@@ -362,6 +386,15 @@ class Context:
         sd = np.zeros(15, np.float32)
         _check(lib().cp_model_get(self._h, stage, _ptr(dims), _ptr(params), n, _ptr(mu), _ptr(sd)))
         return dict(dims=dims.tolist(), params=params, mu=mu, sd=sd)
+
+    def predict_stage(self, stage, features):
+        """cp_predict_stage: (logits, pick) of one installed cascade stage on a
+        15-feature host vector."""
+        f = _np(features, np.float64).reshape(15)
+        logits = np.zeros(STAGE_CLASSES[stage], np.float32)
+        pick = c_int32()
+        _check(lib().cp_predict_stage(self._h, stage, _ptr(f), _ptr(logits), byref(pick)))
+        return logits, pick.value
 
     def model_train(self, stage, F, labels, h1=32, h2=32, epochs=2000, lr=3e-3, seed=1):
         F = _np(F, np.float64).reshape(-1, 15)

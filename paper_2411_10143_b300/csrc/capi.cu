@@ -519,6 +519,18 @@ cp_status cp_model_train(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
   });
 }
 
+cp_status cp_predict_stage(cp_ctx* ctx, int32_t stage, const double* features15,
+                           float* logits, int32_t* pick) {
+  return guard([&] {
+    CP_REQUIRE(ctx && features15, CP_ERR_INVALID, "NULL argument");
+    CP_REQUIRE(stage >= 0 && stage < CP_NUM_STAGES, CP_ERR_INVALID, "bad stage %d", stage);
+    CP_REQUIRE(stage_classes(ctx, stage) > 0, CP_ERR_INVALID, "stage %d has no model", stage);
+    use_device(ctx);
+    const int p = infer_stage(ctx, stage, features15, ctx->side, logits);
+    if (pick) *pick = p;
+  });
+}
+
 cp_status cp_predict(cp_ctx* ctx, cp_mat* m, cp_config* out, float* stage_ms) {
   return guard([&] {
     CP_REQUIRE(ctx && m && out, CP_ERR_INVALID, "NULL argument");

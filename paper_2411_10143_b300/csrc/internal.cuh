@@ -367,7 +367,13 @@ int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, 
                 double target, double* remaining, double* cost);
 // One cascade stage's classifier on the features: returns the arg-max class,
 // or -1 when the stage has no model.
-int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s);
+// One cascade stage's classifier (k_mlp_infer) on a feature vector: returns the
+// arg-max class (-1 without a model); logits (host, k floats, may be NULL)
+// receives the stage's logits.
+int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s,
+                float* logits = nullptr);
+// Classes of the stage's installed model (0 if none).
+int stage_classes(cp_ctx* ctx, int stage);
 
 // ---------------------------------------------------------------- predictor MLP
 struct MlpDims {

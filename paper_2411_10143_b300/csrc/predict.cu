@@ -321,7 +321,7 @@ void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* p
   old = fresh;
 }
 
-int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s) {
+int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s, float* logits) {
   ModelSlot slot;
   {
     std::lock_guard<std::mutex> lock(ctx->model_mu);
@@ -330,15 +330,22 @@ int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s) {
   if (!slot.loaded) return -1;
   Feat15 F;
   std::memcpy(F.f, f15, sizeof(F.f));
+  // one staging word for the pick, then the k logits (one copy back)
   int* d_out = nullptr;
-  CP_CUDA(cudaMallocAsync(&d_out, sizeof(int), s));
+  CP_CUDA(cudaMallocAsync(&d_out, sizeof(int) * (1 + kMaxClass), s));
   const MlpDims D{kFeat, slot.h1, slot.h2, slot.k};
-  int h_out = -1;
+  int h_out[1 + kMaxClass] = {-1};
   CP_LAUNCH(ctx, k_mlp_infer, 1, 64, 0, s, F, D, slot.d_params, slot.d_mu, slot.d_sd, d_out,
-            (float*)nullptr);
-  d2h_small(ctx, &h_out, d_out, sizeof(int), s);
+            reinterpret_cast<float*>(d_out + 1));
+  d2h_small(ctx, h_out, d_out, sizeof(int) * (1 + slot.k), s);
   CP_CUDA(cudaFreeAsync(d_out, s));
-  return h_out;
+  if (logits) std::memcpy(logits, h_out + 1, sizeof(float) * slot.k);
+  return h_out[0];
+}
+
+int stage_classes(cp_ctx* ctx, int stage) {
+  std::lock_guard<std::mutex> lock(ctx->model_mu);
+  return ctx->models[stage].loaded ? ctx->models[stage].k : 0;
 }
 
 void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host, const int32_t* lab_host,

@@ -1,0 +1,155 @@
+"""Parity of the cascade's inference with the oracle (Sec. III-C-1, Fig. 5; one
+classifier per stage, Sec. III-B-3).
+
+The hot path classifies a matrix with ``k_mlp_infer``: the Table IV features go
+through z = (log(1 + f) - mu) / sd in FP64, are rounded to FP32, and pass
+through three FP32 layers; the stage's pick is the arg-max.  Here that kernel
+runs on the shipped trained weights and its logits are compared with the
+oracle's FP64 forward pass of the same weights, ``oracle.mlp_forward(P,
+oracle.mlp_input(f, mu, sd))``:
+
+* logits: norm-wise relative error <= 1e-4 (FP32 arithmetic against FP64; the
+  inputs' rounding to FP32 alone contributes about 6e-8 relative per entry);
+* picks: equal to the oracle's arg-max wherever the oracle's top-two logit
+  margin exceeds 1e-3 (below it the FP32 rounding may legitimately flip the
+  order, and either class is a correct result of the classifier).
+
+Inputs: the 240 feature vectors of the training set stored beside the weights,
+and features the GPU computes (``cp_features``) on the four full-size sweep
+matrices and on held-out training-suite matrices, for which the whole
+cascade (``cp_predict``) is also compared with ``oracle.cascade`` applied to
+the oracle's logits.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2411_10143_b300 import cascade as C
+from paper_2411_10143_b300 import models
+from paper_2411_10143_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LOGIT_RTOL = 1e-4
+MARGIN = 1e-3
+WEIGHTS = models.load()
+DATASET = models.WEIGHTS.parent / "dataset.npz"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = C.Context(0)
+    installed = models.load_default(c)
+    assert all(s in installed for s in models.STAGE_NAMES), installed
+    yield c
+    c.close()
+
+
+def oracle_logits(stage, f):
+    m = WEIGHTS[models.STAGE_NAMES[stage]]
+    P = np.asarray(m["params"], np.float32).astype(np.float64)
+    z = oracle.mlp_input(f, np.asarray(m["mu"], np.float32), np.asarray(m["sd"], np.float32))
+    return oracle.mlp_forward(P, z.reshape(1, -1), tuple(m["dims"]))[0]
+
+
+def margin(lg):
+    top = np.sort(lg)[::-1]
+    return top[0] - top[1]
+
+
+def check_stage(ctx, stage, f):
+    """GPU logits and pick of one stage against the oracle; returns the oracle's
+    logits and whether its pick is decided (margin above MARGIN)."""
+    lg, pick = ctx.predict_stage(stage, f)
+    ref = oracle_logits(stage, f)
+    err = np.linalg.norm(lg.astype(np.float64) - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert err <= LOGIT_RTOL, (stage, err, lg, ref)
+    decided = margin(ref) > MARGIN
+    if decided:
+        assert pick == int(np.argmax(ref)), (stage, pick, lg, ref)
+    # the kernel's pick is always the arg-max of its own logits (first on ties)
+    assert pick == int(np.argmax(lg)), (stage, pick, lg)
+    return ref, decided
+
+
+def test_every_stage_on_the_training_features(ctx):
+    F = np.load(DATASET)["features"]
+    assert F.shape == (240, 15)
+    decided = 0
+    for f in F:
+        for stage in range(C.STAGE_FORMAT, C.STAGE_SELL_SIGMA + 1):
+            decided += check_stage(ctx, stage, f)[1]
+    # nearly every pick is decided by a clear margin; the comparison is not vacuous
+    assert decided >= 0.9 * 4 * len(F)
+
+
+def test_stage_rejects_a_stage_without_model():
+    c = C.Context(0)
+    with pytest.raises(C.CascadeError) as e:
+        c.predict_stage(C.STAGE_FORMAT, np.ones(15))
+    assert e.value.status == C.ERR_INVALID
+    c.close()
+
+
+def expected_config(ctx, M, f):
+    """The cascade's configuration by oracle.cascade on the oracle's logits, or
+    None where a decision is within the margin.  A padded format refused for its
+    memory budget leaves the cascade on CSR, which then takes its ALGO stage."""
+    lf, ok = check_stage(ctx, C.STAGE_FORMAT, f)
+    if not ok:
+        return None
+    la, oka = check_stage(ctx, C.STAGE_CSR_ALGO, f)
+    lt, okt = check_stage(ctx, C.STAGE_CSR_TPV, f)
+    ls, oks = check_stage(ctx, C.STAGE_SELL_SIGMA, f)
+    fmt, _, _ = oracle.cascade(lf)
+    if fmt != C.FMT_CSR:
+        try:
+            M.convert(C.config(fmt, sigma=32))
+        except C.CascadeError as e:
+            assert e.status in (C.ERR_FOOTPRINT, C.ERR_UNSUPPORTED), e
+            lf = np.eye(len(lf))[C.FMT_CSR]  # the plain fallback
+        M.reset()
+    fmt, algo, param = oracle.cascade(lf, la, lt, ls)
+    if (fmt == C.FMT_CSR and not oka) or (algo == C.ALGO_VECTOR and not okt) or \
+            (fmt == C.FMT_SELL and not oks):
+        return None
+    return fmt, algo, param
+
+
+def config_matches(cfg, want):
+    fmt, algo, param = want
+    if cfg.fmt != fmt:
+        return False
+    if fmt == C.FMT_SELL:
+        return cfg.sell_sigma == C.SIGMA_CLASSES[param]
+    if fmt == C.FMT_CSR:
+        if cfg.algo != algo:
+            return False
+        if algo == C.ALGO_VECTOR:
+            return cfg.tpv == C.TPV_CLASSES[param]
+    return True
+
+
+def heldout_matrices(limit=16, max_nnz=4_000_000):
+    d = np.load(DATASET)
+    names = [str(n) for n, t, z in zip(d["names"], d["test"], d["nnz"]) if t and z <= max_nnz]
+    suite = dict(W.training_suite())
+    return [(n, suite[n]) for n in names[:limit] if n in suite]
+
+
+CASES = [(f"sweep_{k}", v) for k, v in W.spmv_sweep().items()] + heldout_matrices()
+
+
+@pytest.mark.parametrize("name,build", CASES, ids=[c[0] for c in CASES])
+def test_cascade_on_gpu_features(ctx, name, build):
+    A = build()
+    M = ctx.load(A)
+    f = M.features()
+    # the features the cascade sees match the oracle's Table IV features
+    fo = oracle.features(A)
+    assert np.allclose(f, fo, rtol=1e-12, atol=0), (f, fo)
+    want = expected_config(ctx, M, f)
+    cfg, _ = M.predict()
+    if want is not None:
+        assert config_matches(cfg, want), (name, repr(cfg), want)
+    M.free()

@@ -1,6 +1,8 @@
 """Pins of the oracle's predictor MLP: finite differences, an independent NumPy forward
 pass, the uniform-logit loss and the closed form of Adam's first step."""
+import json
 import math
+from pathlib import Path
 
 import numpy as np
 import pytest
@@ -8,6 +10,7 @@ import pytest
 import oracle
 
 DIMS = (15, 8, 6, 5)
+GOLDEN = Path(__file__).resolve().parent / "golden"
 
 
 def params(seed, dims=DIMS, scale=0.5):
@@ -97,7 +100,21 @@ def test_cascade_control_flow():
     assert oracle.cascade([0, 0, 5, 0, 0], [9, 0, 0], [1, 0, 0, 0, 0], [1, 0, 0, 0]) == (2, -1, -1)
 
 
-def test_mlp_input_transform():
-    f = np.arange(15, dtype=float)
-    z = oracle.mlp_input(f, np.zeros(15), np.ones(15))
-    assert np.allclose(z, np.log1p(f))
+def test_mlp_input_worked_example():
+    """Hand-derived fixture: log(1 + f) is an exact multiple of log 2, log 3 or
+    log 10 and mu, sd are short binary fractions, so every z is a closed form.
+    A log in place of log1p, swapped mu and sd, or a sign error fails it."""
+    g = json.loads((GOLDEN / "mlp_input_worked.json").read_text())
+    z = oracle.mlp_input(g["f"], g["mu"], g["sd"])
+    assert np.allclose(z, g["z"], rtol=2e-15, atol=2e-15), z - np.asarray(g["z"])
+
+
+def test_mlp_input_is_increasing_in_each_feature():
+    """The input map is strictly increasing in f_j (sd > 0): a larger feature can
+    never give a smaller classifier input."""
+    rng = np.random.default_rng(6)
+    mu, sd = rng.normal(size=15), rng.uniform(0.1, 3, 15)
+    f = rng.uniform(0, 1e6, (50, 15))
+    f.sort(axis=0)
+    z = np.stack([oracle.mlp_input(r, mu, sd) for r in f])
+    assert np.all(np.diff(z, axis=0) >= 0)

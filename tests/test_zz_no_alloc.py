@@ -8,11 +8,13 @@ scratch in a fixed library array.  The test checks it, through the C ABI,
 against the existing cp_spmv with the same merge-path configuration, within the
 FP64 SpMV tolerance of the other tests (1e-12 relative), on two calls in a row
 with different matrices, so a stale carry left by the first call would show.
+Both calls are also compared with the oracle's CSR SpMV on the same inputs.
 It sits in a file pytest collects last."""
 import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2411_10143_b300 import cascade as C
 from paper_2411_10143_b300 import workloads as W
 
@@ -42,7 +44,39 @@ def test_noalloc_matches_cp_spmv_on_two_calls_in_a_row():
     for A, seed in ((first, 1), (second, 2)):
         ref, got = reference_and_noalloc(ctx, A, seed)
         assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
+        exact = oracle.spmv(A, W.vector(A.ncols, seed))
+        assert np.linalg.norm(got - exact) <= 1e-12 * np.linalg.norm(exact)
     ctx.close()
+
+
+def test_noalloc_setup_call_on_an_empty_row():
+    """The one-time set-up can be done by a 1-row, nnz = 0 call (y = 0)."""
+    rp = torch.zeros(2, dtype=torch.int32, device="cuda")
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    v = torch.empty(0, dtype=torch.float64, device="cuda")
+    x = torch.ones(1, dtype=torch.float64, device="cuda")
+    y = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
+    C.spmv_csr_merge_noalloc(1, 1, rp, e, v, x, y)
+    torch.cuda.synchronize()
+    assert y.item() == 0.0
+
+
+def test_noalloc_binding_checks_arrays_before_the_call():
+    """Wrong dtypes or arrays shorter than their sizes never reach the kernel."""
+    A = W.random_csr(40, 30, np.full(40, 3), seed=3)
+    rp = torch.as_tensor(A.rowptr, device="cuda")
+    ci = torch.as_tensor(A.col, device="cuda")
+    va = torch.as_tensor(A.val, device="cuda")
+    x = torch.zeros(A.ncols, dtype=torch.float64, device="cuda")
+    y = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+    bad = [dict(rowptr=rp.long()), dict(col=ci.long()), dict(x=x.float()), dict(val=va.cpu()),
+           dict(x=x[:-1]), dict(y=y[:-1]), dict(rowptr=rp[:-1]), dict(nnz=A.nnz + 1)]
+    for b in bad:
+        args = dict(rowptr=rp, col=ci, val=va, x=x, y=y)
+        args.update(b)
+        with pytest.raises(C.CascadeError) as e:
+            C.spmv_csr_merge_noalloc(A.nrows, A.ncols, **args)
+        assert e.value.status == C.ERR_INVALID
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
