@@ -142,21 +142,33 @@ def workload():
     return A, xs
 
 
-def spmv_bytes(A, fmt="CSR"):
-    """Algorithmic bytes of one FP64 SpMV (padding excluded, x read once): index
-    formats move 12 nnz + 4 (n+1) + 8 ncols + 8 n; DIA stores no indices and
-    moves 8 nnz + 8 ncols + 8 n; COO adds a row index, 16 nnz + 8 ncols + 8 n."""
+def spmv_bytes(A):
+    """Algorithmic bytes of one FP64 SpMV with int32 indices, one definition for
+    every configuration: the CSR matrix (val, col, rowptr), x read once and y
+    written once, 12 nnz + 4 (n+1) + 8 ncols + 8 n.  Padding and repeated x
+    gathers are not counted, so every format is measured against the same
+    work and the fractions rank as the times do."""
+    return 12 * A.nnz + 4 * (A.nrows + 1) + 8 * A.ncols + 8 * A.nrows
+
+
+def format_bytes(A, fmt):
+    """The bytes a format must move by its own layout (padding excluded, x once),
+    reported beside spmv_bytes: DIA stores no indices, 8 nnz + 8 ncols + 8 n;
+    COO adds a row index per entry, 16 nnz + 8 ncols + 8 n; the other formats
+    move what CSR moves."""
     if fmt.startswith("DIA"):
         return 8 * A.nnz + 8 * A.ncols + 8 * A.nrows
     if fmt.startswith("COO"):
         return 16 * A.nnz + 8 * A.ncols + 8 * A.nrows
-    return 12 * A.nnz + 4 * (A.nrows + 1) + 8 * A.ncols + 8 * A.nrows
+    return spmv_bytes(A)
 
 
-def cg_iteration_bytes(A, fmt):
+def cg_iteration_bytes(A, fmt=None):
     """Algorithmic bytes of one CG iteration: the SpMV plus 9 n-vector passes
-    (read x, r, p, Ap and write x, r; read r, p and write p)."""
-    return spmv_bytes(A, fmt) + 9 * 8 * A.nrows
+    (read x, r, p, Ap and write x, r; read r, p and write p).  With ``fmt``, the
+    SpMV counts the format's own bytes instead."""
+    spmv = spmv_bytes(A) if fmt is None else format_bytes(A, fmt)
+    return spmv + 9 * 8 * A.nrows
 
 
 # DRAM traffic of the persistent CG kernel from one ncu capture (dram__bytes_read.sum
@@ -197,67 +209,58 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ CPU oracle arms
-def oracle_sample(A, b, iters_budget):
-    """Single-threaded oracle CG bounded to ``iters_budget`` iterations; returns
-    seconds per iteration."""
+REF_MAX_STEPS = 3  # full oracle solves the reference arm times (about 17 s each)
+
+
+def host_cores():
+    """Cores this process may run on (the host's nproc under its affinity mask)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_solve_ms(A, b, all_cores=False):
+    """One full oracle CG solve of the benchmark system to 1e-10 from x0 = 0:
+    (milliseconds, iterations, true relative residual, threads)."""
     import oracle
     t0 = time.perf_counter()
-    r = oracle.cg(A, b, tol=1e-300, maxit=iters_budget)
-    dt = time.perf_counter() - t0
-    return dt / max(r.iters, 1), r.iters
+    r = oracle.cg_all_cores(A, b, tol=TOL) if all_cores else oracle.cg(A, b, tol=TOL)
+    ms = (time.perf_counter() - t0) * 1e3
+    return ms, r.iters, r.relres_true, (r.threads if all_cores else 1)
 
 
 def run_reference(args, world, rank):
-    """The CPU oracle as the reference arm (bounded samples, extrapolated)."""
+    """The CPU oracle as the reference arm: each timed step is one full
+    single-threaded oracle CG solve of the benchmark system (no extrapolation).
+    At most REF_MAX_STEPS steps are timed so that the arm ends within about a
+    minute; the line's ``steps`` is the number actually run."""
     if rank != 0:
         return
     import oracle
     A, xs = workload()
     b = oracle.spmv(A, xs)
-    # iterations of the full solve: one full oracle run would take minutes, so
-    # the count comes from the convergence rate of a bounded run
-    sample_iters = 40
-    per_iter, _ = oracle_sample(A, b, 5)  # warm caches
-    times = []
-    for _ in range(args.warmup):
-        oracle_sample(A, b, 5)
-    full_iters = oracle_iteration_estimate(A, b)
-    for _ in range(args.steps):
-        per_iter, n = oracle_sample(A, b, sample_iters)
-        times.append(per_iter * full_iters * 1e3)
-    value = float(np.mean(times))
+    for _ in range(args.warmup):  # warm the caches and the page tables: 5 iterations
+        oracle.cg(A, b, tol=1e-300, maxit=5)
+    steps = max(1, min(args.steps, REF_MAX_STEPS))
+    t0 = time.perf_counter()
+    runs = [oracle_solve_ms(A, b) for _ in range(steps)]
+    region = time.perf_counter() - t0
+    value = float(np.mean([r[0] for r in runs]))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "ms",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": value, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": bench_config(A),
+        "n_gpus": args.gpus, "steps": steps, "steps_requested": args.steps,
+        "warmup": args.warmup, "ms_per_step": region * 1e3 / steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": bench_config(A),
         "cpu_baseline": {"value": value, "unit": "ms", "cores": 1, "kind": "oracle",
-                         "sample": f"{sample_iters} CG iterations per step, scaled to the "
-                                   f"{full_iters} iterations of the full solve"},
+                         "host_cores": host_cores(),
+                         "sample": f"{steps} full single-threaded oracle CG solves to "
+                                   f"{TOL:g} ({runs[-1][1]} iterations, true relative "
+                                   f"residual {runs[-1][2]:.2e}), no extrapolation"},
         "e2e": {"value": value, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-_ITER_CACHE = ROOT / "oracle" / "cg_iterations_poisson3d_128.json"
-
-
-def oracle_iteration_estimate(A, b):
-    """CG iteration count of the oracle on this workload.  It is measured once by
-    running the oracle to convergence (oracle/cg_iterations.py, several minutes on
-    one core); without that file a shorter run's residual decay is extrapolated."""
-    if _ITER_CACHE.exists():
-        d = json.loads(_ITER_CACHE.read_text())
-        if d.get("grid") == GRID and d.get("tol") == TOL:
-            return int(d["iters"])
-    import oracle
-    r = oracle.cg(A, b, tol=1e-300, maxit=60, hist_cap=60)
-    # residual decay from the recursive (r,r) = rr_0 * prod(beta)
-    lb = np.cumsum(np.log(r.betas))
-    rate = (lb[-1] - lb[len(lb) // 2]) / (len(lb) - 1 - len(lb) // 2)
-    need = 2 * np.log(TOL)
-    return int(len(lb) + max(0.0, (need - lb[-1]) / rate))
 
 
 def bench_config(A):
@@ -338,19 +341,21 @@ def run_ours(args, world, rank, local):
     it_last = sum(i.persist_last_iters for i in infos)
     n_spmv = sum(i.n_spmv for i in infos)
     t_spmv = sum(i.t_spmv_ms for i in infos)
+    own = None
     if t_last > 0:
         kernel = f"k_cg_persist ({fmt}): one launch runs the CG iterations after the switch"
-        per_launch = cg_iteration_bytes(A, fmt) * it_last / len(infos)
+        per_launch = cg_iteration_bytes(A) * it_last / len(infos)
         launches = len(infos)
         avg_us = t_last / len(infos) * 1e3
-        achieved = cg_iteration_bytes(A, fmt) * it_last / (t_last * 1e-3) / 1e9
+        achieved = cg_iteration_bytes(A) * it_last / (t_last * 1e-3) / 1e9
+        own = cg_iteration_bytes(A, fmt) * it_last / (t_last * 1e-3) / 1e9
         traffic = persist_traffic(A, fmt, it_last / len(infos))
     else:
         kernel = f"spmv ({fmt})"
-        per_launch = spmv_bytes(A, fmt)
+        per_launch = spmv_bytes(A)
         launches = n_spmv
         avg_us = t_spmv / max(n_spmv, 1) * 1e3
-        achieved = spmv_bytes(A, fmt) * n_spmv / (t_spmv * 1e-3) / 1e9 if t_spmv > 0 else None
+        achieved = spmv_bytes(A) * n_spmv / (t_spmv * 1e-3) / 1e9 if t_spmv > 0 else None
         traffic = None
     extra = {}
     if rank == 0 and not args.no_compare:
@@ -364,7 +369,11 @@ def run_ours(args, world, rank, local):
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if achieved else None, "traffic": traffic,
                      "peak_kind": peak_kind, "bytes_per_launch": per_launch,
-                     "launches": launches, "avg_launch_us": avg_us},
+                     "bytes": "12 nnz + 4 (n+1) + 16 n per SpMV (CSR matrix, x once, y once) "
+                              "+ 9 x 8 n vector passes per CG iteration",
+                     "launches": launches, "avg_launch_us": avg_us,
+                     "achieved_own_format_bytes": own,
+                     "frac_own_format_bytes": own / peak if own else None},
         "gpu_launches": int(gpu_launches),
         "clocks": clk.summary(),
         "solve": {"iters": last.iters, "final_cfg": repr(last.final_cfg),
@@ -446,15 +455,19 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
     if args.serve_requests > 0:
         res["serve"] = serve_bench(ctx, args.serve_requests)
     if args.gpus == 1 and not args.no_cpu_baseline:
+        # the oracle as it stands, one full solve, then its all-core build
         import oracle
         bn = b.cpu().numpy()
-        sample = 150
-        per_iter, _ = oracle_sample(A, bn, sample)
-        full = oracle_iteration_estimate(A, bn)
-        res["cpu_baseline"] = {"value": per_iter * full * 1e3, "unit": "ms", "cores": 1,
-                               "kind": "oracle",
-                               "sample": f"{sample} single-threaded oracle CG iterations, "
-                                         f"scaled to the {full} iterations of the full solve"}
+        ms1, it1, rel1, _ = oracle_solve_ms(A, bn)
+        msn, itn, reln, thr = oracle_solve_ms(A, bn, all_cores=True)
+        res["cpu_baseline"] = {
+            "value": ms1, "unit": "ms", "cores": 1, "kind": "oracle", "host_cores": host_cores(),
+            "sample": f"one full single-threaded oracle CG solve to {TOL:g} ({it1} iterations, "
+                      f"true relative residual {rel1:.2e}), no extrapolation",
+            "all_cores": {"value": msn, "unit": "ms", "threads": thr, "iters": itn,
+                          "relres_true": reln,
+                          "build": "the same oracle.c compiled with -fopenmp: row-parallel "
+                                   "SpMV and CG vector loops, static-chunk reductions"}}
     return res
 
 
@@ -510,6 +523,9 @@ def gmres_bench(ctx, reps=2):
         return float(np.mean(ts)), info
 
     base = dict(tol=TOL, restart=GMRES_M)
+    # the metric's denominator: plain FP64 GMRES on the default CSR-scalar
+    # kernel, on the library's default iteration path (the persistent kernel)
+    plain_ms, pl = timed(C.default_opts(mode=C.MODE_PLAIN, **base))
     async_ms, a = timed(C.default_opts(mode=C.MODE_ASYNC, **base))
     ir_ms, ir = timed(C.default_opts(mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
                                      inner_tol=1e-5, **base))
@@ -519,20 +535,28 @@ def gmres_bench(ctx, reps=2):
     dia_ms, d = timed(C.default_opts(mode=C.MODE_PLAIN, **base), force=dia, reset=False)
     flops = gmres_dfma(A.nrows, A.nnz, d.persist_iters, GMRES_M)
     rate = flops / (d.t_persist_ms * 1e-3)
+    peak = ctx.fp64_fma_rate()
     return {
         "workload": f"GMRES({GMRES_M}), convection-diffusion {GMRES_GRID}^3 (n={A.nrows:,}, "
                     f"nnz={A.nnz:,}), FP64, rel. residual {TOL:g}, b = A x*, x0 = 0",
+        "plain_csr_gmres_ms": plain_ms, "plain_iters": pl.iters,
+        "plain_relres_true": pl.relres_true,
         "async_ms": async_ms, "iters": a.iters, "final_cfg": repr(a.final_cfg),
         "relres_true": a.relres_true, "persist_iters": a.persist_iters,
         "fp32_ir_async_ms": ir_ms, "fp32_ir": {"outer": ir.outer_iters, "inner": ir.iters,
                                                "relres_true": ir.relres_true},
-        "per_step_launches_csr_ms": step_ms, "per_step_launches": st.n_launches,
+        "csr_scalar_one_launch_per_step_ms": step_ms, "one_launch_per_step_launches":
+            st.n_launches,
         "persistent_dia_ms": dia_ms,
+        "speedup_vs_plain": {"async": plain_ms / async_ms, "fp32_ir_async": plain_ms / ir_ms,
+                             "dia_forced": plain_ms / dia_ms},
         "roofline": {"kernel": "k_gm_persist (DIA, FP64, modified Gram-Schmidt)", "bound": "alu",
-                     "achieved": rate / 1e9, "peak": FP64_DFMA_PEAK / 1e9,
-                     "unit": "G FP64 FMA/s", "frac": rate / FP64_DFMA_PEAK,
-                     "fma_per_solve": flops,
-                     "peak_note": "2 FP64 FMA per SM per clock x 148 SMs x 2,032 MHz"},
+                     "achieved": rate / 1e9, "peak": peak / 1e9,
+                     "unit": "G FP64 FMA/s", "frac": rate / peak,
+                     "fma_per_solve": flops, "peak_kind": "measured",
+                     "peak_note": "cp_fp64_fma_rate: independent FMA chains on every SM, best "
+                                  "of five launches; nominal 2 per SM per clock x 148 SMs x "
+                                  f"2,032 MHz = {FP64_DFMA_PEAK / 1e9:.1f}"},
     }
 
 
@@ -656,9 +680,11 @@ def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=
                 rows[repr(cfg)] = {"skipped": str(e)[:80]}
                 continue
             med, mean = time_spmv(ctx, M, cfg, x, y, reps, warm)
-            gbs = spmv_bytes(A, repr(cfg)) / (med * 1e-3) / 1e9
+            gbs = spmv_bytes(A) / (med * 1e-3) / 1e9
+            own = format_bytes(A, repr(cfg)) / (med * 1e-3) / 1e9
             rows[repr(cfg)] = {"median_us": med * 1e3, "mean_us": mean * 1e3, "gbs": gbs,
-                               "frac": gbs / peak}
+                               "frac": gbs / peak, "gbs_own_format_bytes": own,
+                               "frac_own_format_bytes": own / peak}
         timed = {c: r for c, r in rows.items() if "median_us" in r}
         best = min(timed, key=lambda c: timed[c]["median_us"])
         pr = rows[repr(cfg_p)]
@@ -689,10 +715,13 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     """Continuous-batching server under Poisson arrivals: n log-uniform in
     [1e3, 1e6], 40 % 2D/3D Poisson (CG), 30 % SPD power law (CG), 30 %
     convection-diffusion (GMRES(30)), FP32 inner solves in FP64 refinement to
-    1e-10.  The arrival rate is 0.8 x the sequential service rate measured on a
-    sample of the same requests.  Matrices are generated once per size bucket
-    (6 per decade and kind) and stay resident; every request has its own
-    right-hand side."""
+    1e-10.  The stream is replayed at 0.5, 0.8, 1.0 and 1.2 x the sequential
+    service rate measured on a sample of the same requests (0.8 x gives the
+    headline p50 / p99), once with every request submitted at once (the
+    saturation throughput), and once served one request at a time by plain FP64
+    CSR-scalar solves at 0.8 x (the baseline).  Matrices are generated once per
+    size bucket (6 per decade and kind) and stay resident; every request has its
+    own right-hand side."""
     import torch
     from paper_2411_10143_b300 import cascade as C
     from paper_2411_10143_b300 import workloads as W
@@ -742,18 +771,48 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     seq = (time.perf_counter() - t1) / len(sample)
     srv.poll()
     srv.close()
-    rate = 0.8 / seq
-    # replay the arrivals at that rate
+    out = {"requests": len(items), "sequential_service_ms": seq * 1e3, "lanes": lanes,
+           "resident_matrices": len(buckets), "batch_tuning": tuned, "loads": {}}
+    for load in SERVE_LOADS:
+        res = serve_replay(ctx, items, load / seq, lanes, C)
+        res["load"] = load
+        out["loads"][f"{load:g}"] = res
+        log_fn(f"serve at {load:g}x: p50 {res['p50_ms']:.1f} ms, p99 {res['p99_ms']:.1f} ms, "
+               f"{res['solves_per_s']:.1f} solves/s (offered {res['arrival_rate_per_s']:.1f})")
+    sat = serve_replay(ctx, items, None, lanes, C)
+    out["saturation"] = sat
+    log_fn(f"serve, every request at once: {sat['solves_per_s']:.1f} solves/s")
+    plain = serve_plain(ctx, items, 0.8 / seq, C)
+    out["plain_one_at_a_time"] = plain
+    log_fn(f"serve, plain FP64 CSR-scalar one at a time at 0.8x: p50 {plain['p50_ms']:.1f} ms, "
+           f"p99 {plain['p99_ms']:.1f} ms")
+    # the headline figures: the 0.8x load
+    main = out["loads"]["0.8"]
+    for k in ("p50_ms", "p99_ms", "solves_per_s", "arrival_rate_per_s", "completed_ok",
+              "batched", "max_relres_true", "failures"):
+        out[k] = main[k]
+    out["saturation_solves_per_s"] = sat["solves_per_s"]
+    return out
+
+
+SERVE_LOADS = (0.5, 0.8, 1.0, 1.2)  # arrival rate / sequential service rate
+
+
+def serve_replay(ctx, items, rate, lanes, C):
+    """Replay the requests' arrivals at ``rate`` per second (None: all at once)
+    into a server with ``lanes`` lanes; latency is arrival to completion."""
+    import torch
     srv = C.Server(ctx, lanes=lanes)
     xs_keep = []
     start = time.perf_counter()
     for k, (r, A, M, s, b) in enumerate(items):
-        due = start + r.arrival_s / rate
-        while True:
-            now = time.perf_counter()
-            if now >= due:
-                break
-            time.sleep(min(due - now, 0.002))
+        if rate is not None:
+            due = start + r.arrival_s / rate
+            while True:
+                now = time.perf_counter()
+                if now >= due:
+                    break
+                time.sleep(min(due - now, 0.002))
         x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
         xs_keep.append(x)
         srv.submit(k, M, s, b, x)
@@ -762,16 +821,46 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     res = srv.poll(capacity=len(items) + 8)
     srv.close()
     lat = np.array([q.t_done_ms - q.t_submit_ms for q in res])
-    ok = sum(1 for q in res if q.status == 0)
-    worst = max(q.relres_true for q in res) if res else None
     fails = [{"id": int(q.id), "kind": items[q.id][0].kind, "n": int(items[q.id][1].nrows),
               "status": int(q.status), "relres": q.relres_true, "batched": int(q.batched)}
              for q in res if q.status != 0][:10]
-    return {"requests": len(items), "completed_ok": ok, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": len(items) / wall,
-            "arrival_rate_per_s": rate, "sequential_service_ms": seq * 1e3, "lanes": lanes,
-            "batched": int(sum(q.batched for q in res)), "max_relres_true": worst,
-            "resident_matrices": len(buckets), "batch_tuning": tuned, "failures": fails}
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": len(res) / wall,
+            "arrival_rate_per_s": rate if rate is not None else None,
+            "completed_ok": sum(1 for q in res if q.status == 0),
+            "batched": int(sum(q.batched for q in res)),
+            "max_relres_true": max(q.relres_true for q in res) if res else None,
+            "failures": fails}
+
+
+def serve_plain(ctx, items, rate, C):
+    """The same arrivals served one request at a time by plain FP64 solves on
+    the default CSR-scalar kernel (the library's default iteration path, no
+    prediction, no batching): the baseline the served solve is compared with.
+    Latency is arrival to completion; a request waits while the one before it
+    runs."""
+    import torch
+    opts = C.default_opts(tol=TOL, mode=C.MODE_PLAIN, restart=30)
+    lat, worst, ok = [], 0.0, 0
+    start = time.perf_counter()
+    for r, A, M, s, b in items:
+        due = start + r.arrival_s / rate
+        while True:
+            now = time.perf_counter()
+            if now >= due:
+                break
+            time.sleep(min(due - now, 0.002))
+        x = torch.zeros(A.nrows, dtype=torch.float64, device="cuda")
+        info = (M.solve_gmres if s else M.solve_cg)(b, x, opts, raise_on_error=False)
+        torch.cuda.current_stream().synchronize()
+        lat.append((time.perf_counter() - due) * 1e3)
+        ok += info.status == 0
+        worst = max(worst, info.relres_true)
+    wall = time.perf_counter() - start
+    lat = np.array(lat)
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "solves_per_s": len(items) / wall, "arrival_rate_per_s": rate, "completed_ok": ok,
+            "max_relres_true": worst}
 
 
 def run_profile_cg(args):

@@ -407,6 +407,14 @@ typedef struct {
  * Errors: CP_ERR_CUDA, CP_ERR_OOM. */
 cp_status cp_warmup(cp_ctx* ctx);
 
+/* cp_fp64_fma_rate: measures this GPU's FP64 fused multiply-add rate (FMAs per
+ * second, host double) with a kernel of independent FMA chains on every SM,
+ * the best of five timed launches (CUDA events on the main stream).  The paper
+ * has no counterpart: it is the denominator of the roofline of the kernels
+ * bound by the FP64 pipe (persistent GMRES), measured rather than taken from a
+ * data sheet.  Blocking; about 0.1 s.  Errors: CP_ERR_INVALID, CP_ERR_CUDA. */
+cp_status cp_fp64_fma_rate(cp_ctx* ctx, double* fma_per_s);
+
 /* Fault injection on the host, for tests of the asynchronous mode's recovery:
  * the next solve's prediction side thread raises an error at `point` (0: before
  * the feature pass, 1: after it, 2: after the FORMAT stage, before any

@@ -54,7 +54,24 @@ def build(force: bool = False) -> Path:
     return _LIB
 
 
+_LIB_OMP = _HERE / "liboracle_omp.so"
+
+
+def build_omp(force: bool = False) -> Path:
+    """Compile the same ``oracle.c`` a second time with ``-fopenmp`` into
+    ``liboracle_omp.so``: its SpMV rows and CG vector loops run on every host
+    core.  Used only as an all-core timing baseline; parity is the serial build's."""
+    if force or not _LIB_OMP.exists() or _LIB_OMP.stat().st_mtime < _SRC.stat().st_mtime:
+        tmp = _LIB_OMP.with_suffix(f".so.{os.getpid()}")
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+             "-fopenmp", "-shared", "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
 _lib = None
+_lib_omp = None
 
 
 def lib() -> ctypes.CDLL:
@@ -162,6 +179,29 @@ def cg(A, b, x0=None, tol=1e-10, maxit=100000, hist_cap=0) -> SolveResult:
     k = min(it, hist_cap)
     return SolveResult(x=x, iters=int(it), relres_true=float(rel[0]), status=int(st[0]),
                        alphas=ah[:k].copy(), betas=bh[:k].copy())
+
+
+def cg_all_cores(A, b, tol=1e-10, maxit=100000) -> SolveResult:
+    """``cg`` run by the all-core build (``build_omp``) with x0 = 0; ``threads``
+    is the OpenMP thread count it used.  A timing baseline only: its reductions
+    sum in per-thread chunks, so its rounding differs from the serial oracle's."""
+    global _lib_omp
+    if _lib_omp is None:
+        build_omp()
+        L = ctypes.CDLL(str(_LIB_OMP))
+        L.or_cg.restype = _i64
+        L.or_cg.argtypes = [_i64, _p, _p, _p, _p, _p, _f64, _i64, _p, _p, _i64, _p, _p]
+        _lib_omp = L
+    A = _as_csr(A)
+    b = _c(b, np.float64)
+    x = np.zeros(A.nrows)
+    rel = np.zeros(1)
+    st = np.zeros(1, np.int32)
+    it = _lib_omp.or_cg(A.nrows, _ptr(A.rowptr), _ptr(A.col), _ptr(A.val), _ptr(b), _ptr(x),
+                        tol, maxit, None, None, 0, _ptr(rel), _ptr(st))
+    threads = int(os.environ.get("OMP_NUM_THREADS", "0")) or len(os.sched_getaffinity(0))
+    return SolveResult(x=x, iters=int(it), relres_true=float(rel[0]), status=int(st[0]),
+                       threads=threads)
 
 
 def gmres(A, b, x0=None, tol=1e-10, m=30, maxit=100000, hist_cap=0) -> SolveResult:

@@ -33,11 +33,16 @@
 typedef int32_t i32;
 typedef int64_t i64;
 
+/* The pragmas below mark the row-parallel SpMV and the vector loops of CG for
+ * the second, all-core build of this same file (gcc -fopenmp, used only as a
+ * timing baseline).  The oracle itself is built without -fopenmp: the pragmas
+ * are then ignored and every loop runs serially in the order written.        */
 /* ------------------------------------------------------------------------- */
 /* SpMV (definition).  Pinned: brute-force dense matvec, exact integer data.  */
 /* ------------------------------------------------------------------------- */
 void or_spmv(i64 n, const i32* rowptr, const i32* col, const double* val,
              const double* x, double* y) {
+#pragma omp parallel for schedule(static)
   for (i64 i = 0; i < n; ++i) {
     double s = 0.0;
     for (i64 k = rowptr[i]; k < rowptr[i + 1]; ++k) s += val[k] * x[col[k]];
@@ -58,6 +63,7 @@ void or_spmv_f32(i64 n, const i32* rowptr, const i32* col, const float* val,
 
 static double dot(i64 n, const double* a, const double* b) {
   double s = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : s)
   for (i64 i = 0; i < n; ++i) s += a[i] * b[i];
   return s;
 }
@@ -67,6 +73,7 @@ static double nrm2(i64 n, const double* a) { return sqrt(dot(n, a, a)); }
 static void residual(i64 n, const i32* rp, const i32* ci, const double* v,
                      const double* b, const double* x, double* r) {
   or_spmv(n, rp, ci, v, x, r);
+#pragma omp parallel for schedule(static)
   for (i64 i = 0; i < n; ++i) r[i] = b[i] - r[i];
 }
 
@@ -112,7 +119,9 @@ i64 or_cg(i64 n, const i32* rp, const i32* ci, const double* v,
       const double pap = dot(n, ap, p);
       if (!(pap > 0.0)) { *status = 5; break; }
       const double alpha = rr / pap;
+#pragma omp parallel for schedule(static)
       for (i64 i = 0; i < n; ++i) x[i] += alpha * p[i];
+#pragma omp parallel for schedule(static)
       for (i64 i = 0; i < n; ++i) r[i] -= alpha * ap[i];
       const double rr_new = dot(n, r, r);
       const double beta = rr_new / rr;
@@ -121,6 +130,7 @@ i64 or_cg(i64 n, const i32* rp, const i32* ci, const double* v,
       ++it;
       rr = rr_new;
       if (sqrt(rr) <= tol * bnorm) { check = 1; break; }
+#pragma omp parallel for schedule(static)
       for (i64 i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
     }
     if (*status == 5) break;

@@ -191,6 +191,7 @@ _SIGS = {
     "cp_gate_set": (c_int32, [_p, _p]),
     "cp_inject_side_failure": (c_int32, [_p, c_int32]),
     "cp_warmup": (c_int32, [_p]),
+    "cp_fp64_fma_rate": (c_int32, [_p, POINTER(c_double)]),
     "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
                                  POINTER(c_double), POINTER(c_double)]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
@@ -454,6 +455,13 @@ class Context:
             _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
                                        _ptr(ms)))
         return best.value, ms.tolist()
+
+    def fp64_fma_rate(self):
+        """cp_fp64_fma_rate: measured FP64 FMAs per second of this GPU."""
+        r = c_double()
+        with self.ordered():
+            _check(lib().cp_fp64_fma_rate(self._h, byref(r)))
+        return r.value
 
     def warmup(self):
         """cp_warmup: launch every solve-path kernel once on a small system, so that

@@ -136,3 +136,65 @@ extern "C" cp_status cp_warmup(cp_ctx* ctx) {
     return CP_ERR_CUDA;
   }
 }
+
+// ------------------------------------------------------------------ FP64 FMA rate
+// The denominator of the FP64-pipe roofline: independent FMA chains, eight per
+// thread, on every SM at full occupancy.  The multiplier and addend are kernel
+// arguments, so the compiler can neither fold nor shorten a chain; the final
+// values are stored only if a condition no finite input meets holds.
+namespace {
+
+constexpr int kRateChains = 8;
+
+__global__ void __launch_bounds__(256) k_dfma_rate(int iters, double mul, double add,
+                                                   double* sink) {
+  double a[kRateChains];
+#pragma unroll
+  for (int c = 0; c < kRateChains; ++c) a[c] = 1.0 + 1e-3 * c + 1e-9 * threadIdx.x;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kRateChains; ++c) a[c] = fma(a[c], mul, add);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int c = 0; c < kRateChains; ++c) s += a[c];
+  if (s == -1.0) sink[blockIdx.x] = s;  // never true for the inputs used
+}
+
+}  // namespace
+
+extern "C" cp_status cp_fp64_fma_rate(cp_ctx* ctx, double* fma_per_s) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double* sink = nullptr;
+  try {
+    CP_REQUIRE(ctx && fma_per_s, CP_ERR_INVALID, "NULL argument");
+    CP_CUDA(cudaSetDevice(ctx->device));
+    int sms = 0;
+    CP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int block = 256, grid = sms * 8, iters = 4096;  // 2,048 threads per SM
+    CP_CUDA(cudaMalloc(&sink, sizeof(double) * grid));
+    CP_CUDA(cudaEventCreate(&e0));
+    CP_CUDA(cudaEventCreate(&e1));
+    cudaStream_t s = ctx->main;
+    float best = 1e30f;
+    for (int rep = 0; rep < 6; ++rep) {  // the first launch loads the kernel: not kept
+      CP_CUDA(cudaEventRecord(e0, s));
+      CP_LAUNCH(ctx, k_dfma_rate, grid, block, 0, s, iters, 0.9999999, 1e-7, sink);
+      CP_CUDA(cudaEventRecord(e1, s));
+      CP_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0 && ms < best) best = ms;
+    }
+    *fma_per_s = (double)grid * block * iters * kRateChains / (best * 1e-3);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sink);
+    return CP_OK;
+  } catch (const cp::Error& e) {
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (sink) cudaFree(sink);
+    return e.status;
+  }
+}

@@ -9,16 +9,20 @@ from paper_2411_10143_b300 import workloads as W
 
 
 def test_spmv_bytes_count_every_array_once():
-    """Index formats: values (8 B) and column indices (4 B) per non-zero, the row
-    pointer, x read once and y written once.  DIA drops the indices and the row
-    pointer; COO carries a row index per non-zero instead of the row pointer."""
+    """One definition for every configuration: values (8 B) and column indices
+    (4 B) per non-zero, the row pointer, x read once and y written once.  The
+    formats' own layouts are reported beside it: DIA drops the indices and the
+    row pointer; COO carries a row index per non-zero instead of the row
+    pointer; the others move what CSR moves."""
     A = W.random_csr(37, 41, [3, 0, 5, 1] * 9 + [2], seed=4)
     n, nc, nnz = A.nrows, A.ncols, A.nnz
     vals, cols, rowptr, x, y = 8 * nnz, 4 * nnz, 4 * (n + 1), 8 * nc, 8 * n
-    assert bench.spmv_bytes(A, "CSR") == vals + cols + rowptr + x + y
-    assert bench.spmv_bytes(A, "ELL") == bench.spmv_bytes(A, "CSR")
-    assert bench.spmv_bytes(A, "DIA") == vals + x + y
-    assert bench.spmv_bytes(A, "COO") == vals + cols + 4 * nnz + x + y
+    assert bench.spmv_bytes(A) == vals + cols + rowptr + x + y
+    assert bench.format_bytes(A, "ELL") == bench.spmv_bytes(A)
+    assert bench.format_bytes(A, "HYB-K0") == bench.spmv_bytes(A)
+    assert bench.format_bytes(A, "DIA") == vals + x + y
+    assert bench.format_bytes(A, "COO") == vals + cols + 4 * nnz + x + y
+    assert bench.cg_iteration_bytes(A) == vals + cols + rowptr + x + y + 9 * 8 * n
     assert bench.cg_iteration_bytes(A, "DIA") == vals + x + y + 9 * 8 * n
 
 

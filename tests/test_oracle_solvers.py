@@ -79,6 +79,19 @@ def test_cg_matches_dense_solve_spd():
     assert np.linalg.norm(r.x - ref) <= 1e-9 * np.linalg.norm(ref)
 
 
+def test_cg_all_core_build_solves_the_same_system():
+    """The all-core timing build (the same source with -fopenmp) reaches the
+    tolerance and the dense solution; only its reductions' rounding differs."""
+    A = W.poisson3d(12)
+    xs = W.vector(A.nrows, 7)
+    b = oracle.spmv(A, xs)
+    r1 = oracle.cg(A, b, tol=1e-10)
+    rn = oracle.cg_all_cores(A, b, tol=1e-10)
+    assert rn.status == 0 and rn.relres_true <= 1e-10 and rn.threads >= 1
+    assert abs(rn.iters - r1.iters) <= 2
+    assert np.linalg.norm(rn.x - xs) <= 1e-7 * np.linalg.norm(xs)
+
+
 def test_cg_edge_cases():
     A = W.poisson2d(6)
     r = oracle.cg(A, np.zeros(36))
