@@ -57,11 +57,15 @@ __global__ void __launch_bounds__(kBlock) k_csr_vector(
 // 50k-entry row costs the same per item as a 3-entry row.  A tile's start is
 // found once per matrix by a binary search along its diagonal
 // (k_merge_partition; the allocation-free entry point searches in the kernel
-// instead, tile_start = null).  The block stages the tile's row ends in
-// shared memory; each thread walks kMergeItems items.  Rows that a thread
-// finishes are written directly; partial rows are combined inside the block,
-// and the partial of the row still open at the tile's end becomes the tile's
-// carry, added by k_merge_fixup.
+// instead, tile_start = null).  The block first stages the whole tile in
+// shared memory with coalesced loads: the row ends, and for every non-zero of
+// the tile its value and the x entry its column selects (the gather of x is
+// issued here, all of a thread's loads back to back).  Each thread then walks
+// kMergeItems consecutive items out of shared memory (an odd item count keeps
+// a half-warp's FP64 reads on distinct banks), one FMA per non-zero.  Rows
+// that a thread finishes are written directly; partial rows are combined
+// inside the block, and the partial of the row still open at the tile's end
+// becomes the tile's carry, added by k_merge_fixup.
 
 // First split point (i = row ends consumed, k = non-zeros consumed) on diagonal
 // d of the merge path, with ties taking the row end after the non-zeros < it.
@@ -83,8 +87,11 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
     const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
     int64_t ntiles, const int32_t* __restrict__ tile_start, int32_t* __restrict__ carry_row,
     T* __restrict__ carry_val, const int* __restrict__ skip) {
+  static_assert(kMergeItems % 2 == 1, "an odd item count keeps the walk's reads conflict-free");
   if (skip && *skip) return;
   __shared__ int32_t s_end[kMergeTile + 1];
+  __shared__ T s_val[kMergeTile];   // the tile's values
+  __shared__ T s_x[kMergeTile];     // x[col] of each of the tile's non-zeros
   __shared__ int64_t s_bounds[2];
   __shared__ int32_t s_row[kBlock];  // row each thread ends in (its carry row)
   __shared__ T s_carry[kBlock];      // that row's partial in the thread
@@ -102,9 +109,31 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
     __syncthreads();
     const int64_t i0 = s_bounds[0], i1 = s_bounds[1];
     const int64_t k0 = d0 - i0, k1 = d1 - i1;
-    // stage row_end[i0 .. min(i1, n-1)]
+    // stage row_end[i0 .. min(i1, n-1)] and the tile's k1 - k0 non-zeros
+    // (at most kMergeTile of each: (i1 - i0) + (k1 - k0) = d1 - d0)
     const int64_t last = i1 < n ? i1 : n - 1;
     for (int64_t r = i0 + threadIdx.x; r <= last; r += blockDim.x) s_end[r - i0] = row_end[r];
+    {
+      const int cnt = (int)(k1 - k0);
+      int32_t c[kMergeItems];
+      T a[kMergeItems];
+#pragma unroll
+      for (int q = 0; q < kMergeItems; ++q) {
+        const int j = threadIdx.x + q * kBlock;
+        if (j < cnt) {
+          c[q] = ld_stream(ci + k0 + j);
+          a[q] = ld_stream(v + k0 + j);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kMergeItems; ++q) {
+        const int j = threadIdx.x + q * kBlock;
+        if (j < cnt) {
+          s_val[j] = a[q];
+          s_x[j] = ld_ro(x + c[q]);
+        }
+      }
+    }
     __syncthreads();
     // this thread's split inside the tile
     int64_t dt = d0 + (int64_t)threadIdx.x * kMergeItems;
@@ -117,31 +146,37 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
       if ((int64_t)s_end[mid - i0] <= dt - mid - 1) a = mid + 1;
       else b = mid;
     }
-    int64_t i = a, k = dt - a;
-    const int64_t start_row = i;
+    // walk with tile-relative indices: row ri = i - i0, non-zero kk = k - k0
+    int ri = (int)(a - i0), kk = (int)(dt - a - k0);
+    const int start_ri = ri;
+    const int nsteps = (int)((dt + kMergeItems < d1 ? dt + kMergeItems : d1) - dt);
+    const int32_t k0i = (int32_t)k0;
     T sum = 0, head = 0;
     bool has_head = false;
-    const int64_t dend = dt + kMergeItems < d1 ? dt + kMergeItems : d1;
-    for (int64_t d = dt; d < dend; ++d) {
-      if (k < (int64_t)s_end[i - i0]) {
-        sum = fma(ld_stream(v + k), ld_ro(x + ld_stream(ci + k)), sum);
-        ++k;
+    int row_limit = s_end[ri] - k0i;
+    for (int q = 0; q < nsteps; ++q) {
+      if (kk < row_limit) {
+        sum = fma(s_val[kk], s_x[kk], sum);
+        ++kk;
       } else {
-        if (i == start_row) {
+        if (ri == start_ri) {
           head = sum;
           has_head = true;
         } else {
-          store_row<T, GEN>(y, i, sum, alpha, beta);
+          store_row<T, GEN>(y, i0 + ri, sum, alpha, beta);
         }
         sum = 0;
-        ++i;
+        ++ri;
+        row_limit = s_end[ri] - k0i;
       }
     }
-    s_row[threadIdx.x] = (int32_t)(i < n ? i : n);
+    const int64_t end_row = i0 + ri;
+    s_row[threadIdx.x] = (int32_t)(end_row < n ? end_row : n);
     s_carry[threadIdx.x] = sum;
     __syncthreads();
     if (has_head) {
       // add the partials of the preceding threads that ended inside start_row
+      const int32_t start_row = (int32_t)(i0 + start_ri);
       T c = 0;
       for (int j = (int)threadIdx.x - 1; j >= 0 && s_row[j] == start_row; --j) c += s_carry[j];
       store_row<T, GEN>(y, start_row, head + c, alpha, beta);
@@ -440,6 +475,24 @@ void spmv_set_attributes() {
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
 }
 
+// One wave of the merge-path kernel: its staged tile (about 39 KB of shared
+// memory in FP64) bounds the blocks an SM holds; tiles are equal work, so each
+// block of the wave takes every gridDim-th tile.
+template <typename T, bool GEN>
+static int merge_grid(int num_sms, int64_t cap, int64_t tiles) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_merge<T, GEN>, kBlock, 0) !=
+        cudaSuccess)
+      b = 1;
+    return b > 0 ? b : 1;
+  }();
+  int64_t g = (int64_t)num_sms * per_sm;
+  if (g > cap) g = cap;
+  if (g > tiles) g = tiles;
+  return (int)(g < 1 ? 1 : g);
+}
+
 // One wave of the COO kernel: its registers (not the thread limit) bound the
 // blocks an SM holds, and a second wave would only queue behind the first.
 template <typename T, bool ADD, bool ONE>
@@ -488,8 +541,8 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
         return DOT ? g : 0;
       }
       if (cfg.algo == CP_ALGO_MERGE) {
-        const int g = (int)(m->merge_tiles < ctx->grid_stream ? m->merge_tiles : ctx->grid_stream);
-        CP_LAUNCH(ctx, (k_csr_merge<T, GEN>), g > 0 ? g : 1, kBlock, 0, s, n, m->nnz, m->rowptr,
+        const int g = merge_grid<T, GEN>(ctx->num_sms, ctx->grid_stream, m->merge_tiles);
+        CP_LAUNCH(ctx, (k_csr_merge<T, GEN>), g, kBlock, 0, s, n, m->nnz, m->rowptr,
                   m->col, v, x, y, alpha, beta, m->merge_tiles, m->merge_start,
                   m->merge_carry_row, reinterpret_cast<T*>(m->merge_carry_val), skip);
         CP_LAUNCH(ctx, k_merge_fixup<T>, grid_for(ctx, m->merge_tiles), kBlock, 0, s,
@@ -662,7 +715,7 @@ extern "C" cp_status cp_spmv_csr_merge_noalloc(int64_t nrows, int64_t ncols, int
     const NoAllocDevice& d = noalloc_setup(dev);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int64_t cap = (int64_t)d.num_sms * 8;
-    const int grid = (int)(tiles < cap ? tiles : cap);
+    const int grid = merge_grid<double, false>(d.num_sms, cap, tiles);
     k_csr_merge<double, false><<<grid, kBlock, 0, s>>>(nrows, nnz, rowptr, col, val, x, y, 1.0,
                                                         0.0, tiles, nullptr, d.carry_row,
                                                         d.carry_val, nullptr);
