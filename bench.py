@@ -645,18 +645,22 @@ def variant_solves(ctx, A, seed, kind, restart=30):
 
 
 def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=log,
-                     solves=False):
+                     solves=False, matrices=None, config=None):
     """SpMV format/kernel sweep with cascaded prediction on the four sweep
     matrices (3D Poisson 128^3, power law, uniform, banded; FP64 values
     U[-1,1]): per matrix the predicted configuration's GB/s and fraction of the
     measured HBM peak, the best and the CSR-scalar configuration beside it, and
     the cost of the prediction (features + three stages) and of the conversion.
-    GB/s counts algorithmic bytes (padding excluded, x once)."""
+    GB/s counts algorithmic bytes (padding excluded, x once).  ``matrices``
+    (names) and ``config`` (a configuration name such as "ELL" or "CSR-merge",
+    with only_predicted) narrow it for profiling."""
     import torch
     from paper_2411_10143_b300 import cascade as C
     from paper_2411_10143_b300 import workloads as W
     out = {}
     for k, (name, gen) in enumerate(W.spmv_sweep().items()):
+        if matrices and name not in matrices:
+            continue
         A = gen()
         M = ctx.load(A)
         x = torch.as_tensor(W.vector(A.ncols, W.RHS_SEED_BASE + 1), device="cuda")
@@ -669,6 +673,8 @@ def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=
         M.convert(cfg_p)
         torch.cuda.synchronize()
         t_conv = (time.perf_counter() - t0) * 1e3
+        if config:
+            cfg_p = next(c for c in sweep_configs(C) if repr(c) == config)
         cfgs = [cfg_p] if only_predicted else sweep_configs(C)
         if repr(cfg_p) not in [repr(c) for c in cfgs]:
             cfgs.append(cfg_p)
@@ -951,6 +957,11 @@ def main():
     ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES leg")
     ap.add_argument("--profile-spmv", action="store_true",
                     help="profiling aid: the predicted SpMV of each sweep matrix, 3 launches")
+    ap.add_argument("--spmv-matrix", default=None,
+                    help="with --profile-spmv: sweep matrices to run (comma-separated names)")
+    ap.add_argument("--spmv-config", default=None,
+                    help="with --profile-spmv: run this configuration (e.g. ELL, CSR-merge) "
+                         "instead of the predicted one")
     ap.add_argument("--profile-cg", default=None, metavar="FMT",
                     help="profiling aid: forced-configuration CG solves (e.g. DIA), no bench line")
     ap.add_argument("--profile-matrix", default="poisson3d", choices=["poisson3d", "spd_powerlaw"],
@@ -973,8 +984,10 @@ def main():
         from paper_2411_10143_b300 import models
         ctx = C.Context(0)
         models.load_default(ctx)
-        print(json.dumps(spmv_sweep_bench(ctx, measured_peaks()[0], reps=3, warm=1,
-                                          only_predicted=True)), flush=True)
+        print(json.dumps(spmv_sweep_bench(
+            ctx, measured_peaks()[0], reps=3, warm=1, only_predicted=True,
+            matrices=args.spmv_matrix.split(",") if args.spmv_matrix else None,
+            config=args.spmv_config)), flush=True)
         return
     if args.impl == "reference":
         world, rank, _ = dist_init("gloo")

@@ -925,7 +925,7 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
 // points (the matrix is fixed, so the diagonal searches are not repeated in
 // every SpMV).
 static void prepare_merge(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
-  const int64_t tiles = (m->nrows + m->nnz + kMergeTile - 1) / kMergeTile;
+  const int64_t tiles = (m->nrows + m->nnz + kMergeWarpTile - 1) / kMergeWarpTile;
   if (m->merge_tiles == tiles && m->merge_carry_row) return;
   dfree(m->merge_carry_row);
   dfree(m->merge_carry_val);

@@ -85,7 +85,8 @@ inline void dfree_async(void* p, cudaStream_t s) {
 constexpr int kBlock = 256;         // threads per block of the streaming kernels
 constexpr int kMaxPartials = 4096;  // capacity of one block-partials buffer
 constexpr int kMergeItems = 7;      // merge-path items per thread
-constexpr int kMergeTile = kBlock * kMergeItems;
+constexpr int kMergeTile = kBlock * kMergeItems;  // block tile (allocation-free kernel)
+constexpr int kMergeWarpTile = 32 * kMergeItems;  // warp tile (the matrix path's kernel)
 
 struct ModelSlot {
   bool loaded = false;

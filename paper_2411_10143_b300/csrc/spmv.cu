@@ -55,17 +55,22 @@ __global__ void __launch_bounds__(kBlock) k_csr_vector(
 // The merge of the row-end offsets rowptr[1..n] with the non-zero indices
 // 0..nnz-1 is cut into tiles of equal length (n + nnz items in total), so a
 // 50k-entry row costs the same per item as a 3-entry row.  A tile's start is
-// found once per matrix by a binary search along its diagonal
-// (k_merge_partition; the allocation-free entry point searches in the kernel
-// instead, tile_start = null).  The block first stages the whole tile in
+// the split point found by a binary search along its diagonal.
+//
+// Two kernels.  The matrix path (cp_spmv and the solvers) runs warp tiles
+// (k_csr_merge_warp below) whose start points k_merge_partition computes once
+// per matrix.  The allocation-free entry point has no per-matrix set-up and
+// searches in the kernel (tile_start = null), so it runs block tiles
+// (k_csr_merge), eight times larger, to spread each search over more
+// items.  The block first stages the whole tile in
 // shared memory with coalesced loads: the row ends, and for every non-zero of
 // the tile its value and the x entry its column selects (the gather of x is
 // issued here, all of a thread's loads back to back).  Each thread then walks
 // kMergeItems consecutive items out of shared memory (an odd item count keeps
 // a half-warp's FP64 reads on distinct banks), one FMA per non-zero.  Rows
 // that a thread finishes are written directly; partial rows are combined
-// inside the block, and the partial of the row still open at the tile's end
-// becomes the tile's carry, added by k_merge_fixup.
+// inside the block by a segmented scan, and the partial of the row still open
+// at the tile's end becomes the tile's carry, added by k_merge_fixup.
 
 // First split point (i = row ends consumed, k = non-zeros consumed) on diagonal
 // d of the merge path, with ties taking the row end after the non-zeros < it.
@@ -93,8 +98,10 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
   __shared__ T s_val[kMergeTile];   // the tile's values
   __shared__ T s_x[kMergeTile];     // x[col] of each of the tile's non-zeros
   __shared__ int64_t s_bounds[2];
-  __shared__ int32_t s_row[kBlock];  // row each thread ends in (its carry row)
-  __shared__ T s_carry[kBlock];      // that row's partial in the thread
+  __shared__ int32_t s_row[kBlock];  // row each thread ends in (its open row)
+  __shared__ T s_carry[kBlock];      // sum of that row's partials up to the thread
+  __shared__ int32_t s_wfirst[kBlock / 32], s_wlast[kBlock / 32];  // per warp: open rows
+  __shared__ T s_wval[kBlock / 32], s_cin[kBlock / 32];              // of lanes 0 and 31
   const int64_t total = n + nnz;
   const int32_t* row_end = rp + 1;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -170,35 +177,259 @@ __global__ void __launch_bounds__(kBlock) k_csr_merge(
         row_limit = s_end[ri] - k0i;
       }
     }
+    // Every thread leaves a partial of the row it ends in (its open row).  An
+    // inclusive segmented scan over the block's threads, segments = equal open
+    // rows (rows never decrease along the threads, so each segment is a run),
+    // gives each thread the sum of its run up to itself: a log-depth scan, where
+    // a tile inside one long row would otherwise add 256 partials in sequence.
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t end_row = i0 + ri;
-    s_row[threadIdx.x] = (int32_t)(end_row < n ? end_row : n);
-    s_carry[threadIdx.x] = sum;
+    const int32_t open_row = (int32_t)(end_row < n ? end_row : n);
+    T run = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const T up = __shfl_up_sync(0xffffffffu, run, off);
+      const int32_t up_row = __shfl_up_sync(0xffffffffu, open_row, off);
+      if (lane >= off && up_row == open_row) run += up;
+    }
+    const int32_t warp_first = __shfl_sync(0xffffffffu, open_row, 0);
+    if (lane == 31) {
+      s_wlast[wid] = open_row;
+      s_wval[wid] = run;
+    }
+    if (lane == 0) s_wfirst[wid] = open_row;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // carry into each warp's first run from the warps before it
+      s_cin[0] = 0;
+      for (int w = 1; w < kBlock / 32; ++w) {
+        const T upto = s_wval[w - 1] + (s_wfirst[w - 1] == s_wlast[w - 1] ? s_cin[w - 1] : T(0));
+        s_cin[w] = s_wlast[w - 1] == s_wfirst[w] ? upto : T(0);
+      }
+    }
+    __syncthreads();
+    if (open_row == warp_first) run += s_cin[wid];
+    s_row[threadIdx.x] = open_row;
+    s_carry[threadIdx.x] = run;
     __syncthreads();
     if (has_head) {
       // add the partials of the preceding threads that ended inside start_row
       const int32_t start_row = (int32_t)(i0 + start_ri);
-      T c = 0;
-      for (int j = (int)threadIdx.x - 1; j >= 0 && s_row[j] == start_row; --j) c += s_carry[j];
+      const T c = threadIdx.x > 0 && s_row[threadIdx.x - 1] == start_row
+                      ? s_carry[threadIdx.x - 1] : T(0);
       store_row<T, GEN>(y, start_row, head + c, alpha, beta);
     }
     if (threadIdx.x == blockDim.x - 1) {
-      const int32_t r = s_row[threadIdx.x];
-      T c = 0;
-      for (int j = (int)threadIdx.x; j >= 0 && s_row[j] == r; --j) c += s_carry[j];
-      carry_row[t] = r < n ? r : -1;
-      carry_val[t] = c;
+      carry_row[t] = open_row < n ? open_row : -1;
+      carry_val[t] = run;
     }
     __syncthreads();
   }
 }
 
-// tile_start[t] = first split row of tile t's diagonal, t = 0..ntiles
+// Asynchronous global -> shared copies (cp.async, 4 or 8 bytes): the data goes
+// to shared memory without passing through registers, and a thread waits for
+// its own copies by commit group.
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(
+                   (uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+template <typename T>
+__device__ __forceinline__ void cp_async_t(T* smem, const T* gmem) {
+  if constexpr (sizeof(T) == 8) cp_async_8(smem, gmem);
+  else cp_async_4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+// waits until at most one committed group of this thread is still in flight
+__device__ __forceinline__ void cp_async_wait_prev() {
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+}
+
+constexpr int kMergeWarps = 4;  // warps per block of the warp-tile kernel
+
+// The matrix path's merge-path kernel: warp tiles of kMergeWarpTile items,
+// each warp independent of the others (no block barrier), with the tile start
+// points computed once per matrix.  Each warp runs a two-stage pipeline over
+// its tiles: while it walks one tile out of shared memory, the copies of its
+// next tile's row ends, column indices and values (coalesced cp.async, no
+// registers) are in flight into the other half of its shared-memory slice.
+// Each lane finds its split by a search in the staged row ends and takes the
+// next lane's split as its end, so it knows the non-zeros it owns (at most
+// kMergeItems, contiguous) and gathers their x entries back to back before
+// walking its items.  A warp-wide segmented scan (shuffles) combines the rows
+// that cross lanes; the partial of the row open at the tile's end is the
+// tile's carry.
+template <typename T, bool GEN>
+__global__ void __launch_bounds__(32 * kMergeWarps) k_csr_merge_warp(
+    int64_t n, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
+    const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
+    int64_t ntiles, const int32_t* __restrict__ tile_start, int32_t* __restrict__ carry_row,
+    T* __restrict__ carry_val, const int* __restrict__ skip) {
+  constexpr int W = kMergeWarpTile;
+  if (skip && *skip) return;
+  __shared__ int32_t s_end[kMergeWarps][2][W + 1];
+  __shared__ int32_t s_col[kMergeWarps][2][W];
+  __shared__ T s_val[kMergeWarps][2][W];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t total = n + nnz;
+  const int32_t* row_end = rp + 1;
+  const int64_t stride = (int64_t)gridDim.x * kMergeWarps;
+  // issue the copies of tile tt (bounds a0, a1) into half `h` of this warp's slice
+  auto stage = [&](int64_t tt, int h, int32_t a0, int32_t a1) {
+    const int64_t d0 = tt * W;
+    const int len = (int)(d0 + W < total ? W : total - d0);
+    const int32_t k0 = (int32_t)(d0 - a0);
+    const int cnt = len - (a1 - a0);
+    const int32_t last = a1 < n ? a1 : (int32_t)(n - 1);
+    int32_t* e = s_end[wid][h];
+    int32_t* c = s_col[wid][h];
+    T* w = s_val[wid][h];
+    for (int32_t r = a0 + lane; r <= last; r += 32) cp_async_4(e + (r - a0), row_end + r);
+#pragma unroll
+    for (int q = 0; q < kMergeItems; ++q) {
+      const int j = lane + 32 * q;
+      if (j < cnt) {
+        cp_async_4(c + j, ci + k0 + j);
+        cp_async_t(w + j, v + k0 + j);
+      }
+    }
+  };
+  int64_t t = (int64_t)blockIdx.x * kMergeWarps + wid;
+  // bounds of the current tile (b0, b1) and of the next one (nb0, nb1)
+  int32_t b0 = 0, b1 = 0, nb0 = 0, nb1 = 0;
+  if (t < ntiles) {
+    b0 = tile_start[t];
+    b1 = tile_start[t + 1];
+    stage(t, 0, b0, b1);
+  }
+  cp_async_commit();
+  if (t + stride < ntiles) {
+    nb0 = tile_start[t + stride];
+    nb1 = tile_start[t + stride + 1];
+  }
+  int h = 0;
+  for (; t < ntiles; t += stride, h ^= 1) {
+    const int32_t i0 = b0, i1 = b1;
+    // the next tile's copies go out before this tile is walked
+    if (t + stride < ntiles) stage(t + stride, h ^ 1, nb0, nb1);
+    cp_async_commit();  // one group per iteration, possibly empty
+    b0 = nb0;
+    b1 = nb1;
+    if (t + 2 * stride < ntiles) {
+      nb0 = tile_start[t + 2 * stride];
+      nb1 = tile_start[t + 2 * stride + 1];
+    }
+    cp_async_wait_prev();  // this tile's group has landed (the next one may not)
+    __syncwarp();
+    const int32_t* e_w = s_end[wid][h];
+    const int32_t* c_w = s_col[wid][h];
+    const T* v_w = s_val[wid][h];
+    const int64_t d0 = t * W;
+    const int len = (int)(d0 + W < total ? W : total - d0);  // items in the tile
+    const int32_t k0 = (int32_t)(d0 - i0);
+    const int ni = i1 - i0;    // row ends in the tile
+    const int cnt = len - ni;  // non-zeros in the tile
+    // this lane's split on its diagonal dr (tile-relative): rows ri_s consumed,
+    // non-zeros kk_s consumed, ri_s + kk_s = dr
+    const int dr = lane * kMergeItems < len ? lane * kMergeItems : len;
+    int a = dr - cnt > 0 ? dr - cnt : 0;
+    int b = dr < ni ? dr : ni;
+    while (a < b) {
+      const int mid = (a + b) >> 1;
+      if (e_w[mid] - k0 <= dr - mid - 1) a = mid + 1;
+      else b = mid;
+    }
+    const int ri_s = a;
+    const int kk_s = dr - a;
+    // the lane's end is the next lane's start (the last lane's: the tile's end)
+    int ri_e = __shfl_down_sync(0xffffffffu, ri_s, 1);
+    int kk_e = __shfl_down_sync(0xffffffffu, kk_s, 1);
+    if (lane == 31) {
+      ri_e = ni;
+      kk_e = cnt;
+    }
+    // the lane's non-zeros kk_s .. kk_e - 1: their x gathers back to back
+    const int nz = kk_e - kk_s;
+    T xv[kMergeItems];
+#pragma unroll
+    for (int q = 0; q < kMergeItems; ++q)
+      if (q < nz) xv[q] = ld_ro(x + c_w[kk_s + q]);
+    // walk: before non-zero k, every row whose end is <= k closes
+    int ri = ri_s;
+    T sum = 0, head = 0;
+    bool has_head = false;
+#pragma unroll
+    for (int q = 0; q < kMergeItems; ++q) {
+      if (q < nz) {
+        const int32_t kabs = k0 + kk_s + q;
+        while (e_w[ri] <= kabs) {
+          if (ri == ri_s) {
+            head = sum;
+            has_head = true;
+          } else {
+            store_row<T, GEN>(y, i0 + ri, sum, alpha, beta);
+          }
+          sum = 0;
+          ++ri;
+        }
+        sum = fma(v_w[kk_s + q], xv[q], sum);
+      }
+    }
+    while (ri < ri_e) {  // row ends after the lane's last non-zero
+      if (ri == ri_s) {
+        head = sum;
+        has_head = true;
+      } else {
+        store_row<T, GEN>(y, i0 + ri, sum, alpha, beta);
+      }
+      sum = 0;
+      ++ri;
+    }
+    // segmented inclusive scan of the open rows' partials across the warp
+    // (FP64 adds cost as much as the walk's FMAs on this GPU, so the scan stops
+    // as soon as no run spans more lanes than the steps so far cover: one step
+    // when rows cross at most one lane boundary)
+    const int32_t open_row = i0 + ri;  // n when the tile ends the matrix
+    T run = sum;
+    for (int off = 1; off < 32; off <<= 1) {
+      const int32_t up_row = __shfl_up_sync(0xffffffffu, open_row, off);
+      const bool joins = lane >= off && up_row == open_row;
+      if (!__any_sync(0xffffffffu, joins)) break;
+      const T up = __shfl_up_sync(0xffffffffu, run, off);
+      if (joins) run += up;
+    }
+    const T prev_run = __shfl_up_sync(0xffffffffu, run, 1);
+    const int32_t prev_row = __shfl_up_sync(0xffffffffu, open_row, 1);
+    if (has_head) {
+      const int32_t start_row = i0 + ri_s;
+      const T c = lane > 0 && prev_row == start_row ? prev_run : T(0);
+      store_row<T, GEN>(y, start_row, head + c, alpha, beta);
+    }
+    if (lane == 31) {
+      carry_row[t] = open_row < n ? open_row : -1;
+      carry_val[t] = run;
+    }
+    __syncwarp();  // every lane is done with half h before it is restaged
+  }
+}
+
+// tile_start[t] = first split row of the diagonal t * tile, t = 0..ntiles
 __global__ void k_merge_partition(int64_t n, int64_t nnz, const int32_t* __restrict__ rp,
-                                  int64_t ntiles, int32_t* __restrict__ tile_start) {
+                                  int64_t ntiles, int64_t tile, int32_t* __restrict__ tile_start) {
   const int64_t total = n + nnz;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles;
        t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = t * kMergeTile < total ? t * kMergeTile : total;
+    const int64_t d = t * tile < total ? t * tile : total;
     tile_start[t] = (int32_t)merge_search(d, rp + 1, n, nnz);
   }
 }
@@ -458,21 +689,41 @@ static int grid_for(cp_ctx* ctx, int64_t work_items) {
 
 void merge_partition(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   CP_LAUNCH(ctx, k_merge_partition, grid_for(ctx, m->merge_tiles + 1), kBlock, 0, s, m->nrows,
-            m->nnz, m->rowptr, m->merge_tiles, m->merge_start);
+            m->nnz, m->rowptr, m->merge_tiles, (int64_t)kMergeWarpTile, m->merge_start);
 }
 
-// The merge-path kernel stages ~25-40 KB of a tile in shared memory:
+// The merge-path kernels stage ~20-40 KB of tiles in shared memory:
 // prefer the largest shared-memory carve-out so that several blocks share an SM.
 void spmv_set_attributes() {
   const int carve = cudaSharedmemCarveoutMaxShared;
   CP_CUDA(cudaFuncSetAttribute(k_csr_merge<double, false>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<double, true>,
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge_warp<double, false>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<float, false>,
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge_warp<double, true>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
-  CP_CUDA(cudaFuncSetAttribute(k_csr_merge<float, true>,
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge_warp<float, false>,
                                cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+  CP_CUDA(cudaFuncSetAttribute(k_csr_merge_warp<float, true>,
+                               cudaFuncAttributePreferredSharedMemoryCarveout, carve));
+}
+
+// One wave of the warp-tile merge-path kernel (its shared memory and
+// registers bound the blocks an SM holds); each warp takes every
+// (gridDim * kMergeWarps)-th warp tile.
+template <typename T, bool GEN>
+static int merge_warp_grid(int num_sms, int64_t tiles) {
+  static const int per_sm = [] {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_csr_merge_warp<T, GEN>,
+                                                      32 * kMergeWarps, 0) != cudaSuccess)
+      b = 1;
+    return b > 0 ? b : 1;
+  }();
+  int64_t g = (int64_t)num_sms * per_sm;
+  const int64_t need = (tiles + kMergeWarps - 1) / kMergeWarps;
+  if (g > need) g = need;
+  return (int)(g < 1 ? 1 : g);
 }
 
 // One wave of the merge-path kernel: its staged tile (about 39 KB of shared
@@ -541,8 +792,8 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
         return DOT ? g : 0;
       }
       if (cfg.algo == CP_ALGO_MERGE) {
-        const int g = merge_grid<T, GEN>(ctx->num_sms, ctx->grid_stream, m->merge_tiles);
-        CP_LAUNCH(ctx, (k_csr_merge<T, GEN>), g, kBlock, 0, s, n, m->nnz, m->rowptr,
+        const int g = merge_warp_grid<T, GEN>(ctx->num_sms, m->merge_tiles);
+        CP_LAUNCH(ctx, (k_csr_merge_warp<T, GEN>), g, 32 * kMergeWarps, 0, s, n, m->nnz, m->rowptr,
                   m->col, v, x, y, alpha, beta, m->merge_tiles, m->merge_start,
                   m->merge_carry_row, reinterpret_cast<T*>(m->merge_carry_val), skip);
         CP_LAUNCH(ctx, k_merge_fixup<T>, grid_for(ctx, m->merge_tiles), kBlock, 0, s,
