@@ -452,6 +452,7 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
     if not args.no_gmres:
         # the random SPD power-law system of the asynchronous solves (n = 500k)
         res["spd_powerlaw_cg"] = variant_solves(ctx, W.spd_powerlaw(), W.RHS_SEED_BASE + 3, "cg")
+        res["async_by_size"] = async_by_size(ctx)
     if args.serve_requests > 0:
         res["serve"] = serve_bench(ctx, args.serve_requests)
     if args.gpus == 1 and not args.no_cpu_baseline:
@@ -644,6 +645,47 @@ def variant_solves(ctx, A, seed, kind, restart=30):
     return out
 
 
+def async_by_size(ctx, grids=(24, 32, 48, 64, 96, 128), reps=5, log_fn=log):
+    """Where asynchrony pays (Sec. III-C-2, Table VII): FP64 CG to 1e-10 on 3D
+    Poisson systems of several sizes, plain (CSR-scalar throughout), sequential
+    (prediction and conversion first, then the predicted kernel) and
+    asynchronous (the solve starts at once on CSR-scalar and switches when the
+    prediction lands); medians of ``reps`` solves each, every one from the
+    freshly loaded CSR.  The cascade's side work costs about the same at every
+    size, so its share, and what overlapping it saves, grows as the solve
+    shortens."""
+    import torch
+    from paper_2411_10143_b300 import cascade as C
+    from paper_2411_10143_b300 import workloads as W
+    out = {}
+    for N in grids:
+        A = W.poisson3d(N)
+        M = ctx.load(A)
+        xs = torch.as_tensor(W.vector(A.ncols, XSTAR_SEED), device="cuda")
+        b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+        M.spmv(xs, b)
+        row = {"n": A.nrows}
+        for name, mode in (("plain", C.MODE_PLAIN), ("sequential", C.MODE_SEQUENTIAL),
+                           ("async", C.MODE_ASYNC)):
+            ts, info = [], None
+            for _ in range(reps):
+                ms, info, _ = timed_solve(ctx, M, b, xs, "cg", C.default_opts(tol=TOL, mode=mode),
+                                          reps=1)
+                ts.append(ms)
+            row[f"{name}_ms"] = float(np.median(ts))
+            if name == "async":
+                row["async_switch_iter"] = list(info.switch_iter)
+                row["iters"] = info.iters
+                row["final_cfg"] = repr(info.final_cfg)
+        row["async_vs_sequential"] = row["sequential_ms"] / row["async_ms"]
+        row["async_vs_plain"] = row["plain_ms"] / row["async_ms"]
+        out[f"poisson3d_{N}"] = row
+        log_fn(f"async by size: 3D Poisson {N}^3 plain {row['plain_ms']:.2f} ms, sequential "
+               f"{row['sequential_ms']:.2f} ms, async {row['async_ms']:.2f} ms")
+        M.free()
+    return out
+
+
 def spmv_sweep_bench(ctx, peak, reps=200, warm=10, only_predicted=False, log_fn=log,
                      solves=False, matrices=None, config=None):
     """SpMV format/kernel sweep with cascaded prediction on the four sweep
@@ -721,8 +763,8 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     """Continuous-batching server under Poisson arrivals: n log-uniform in
     [1e3, 1e6], 40 % 2D/3D Poisson (CG), 30 % SPD power law (CG), 30 %
     convection-diffusion (GMRES(30)), FP32 inner solves in FP64 refinement to
-    1e-10.  The stream is replayed at 0.5, 0.8, 1.0 and 1.2 x the sequential
-    service rate measured on a sample of the same requests (0.8 x gives the
+    1e-10.  The stream is replayed at 0.5, 0.8, 1.0, 1.2 and 2.0 x the sequential
+    (one-lane) service rate measured on a sample of the same requests (0.8 x gives the
     headline p50 / p99), once with every request submitted at once (the
     saturation throughput), and once served one request at a time by plain FP64
     CSR-scalar solves at 0.8 x (the baseline).  Matrices are generated once per
@@ -801,7 +843,7 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     return out
 
 
-SERVE_LOADS = (0.5, 0.8, 1.0, 1.2)  # arrival rate / sequential service rate
+SERVE_LOADS = (0.5, 0.8, 1.0, 1.2, 2.0)  # arrival rate / sequential service rate
 
 
 def serve_replay(ctx, items, rate, lanes, C):

@@ -361,6 +361,40 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
 }
 
 // ------------------------------------------------------------------ host
+// The batched solve is one persistent launch in a CUDA graph.  Each context
+// instantiates the graph of each block size once, on first use; later batches
+// only update the kernel node's grid and arguments in the instantiated graph
+// (cudaGraphExecKernelNodeSetParams) and launch it, with no capture or
+// instantiation on the path of a batch.
+}  // namespace cp
+
+struct cp::BatchGraphs {
+  struct One {
+    cudaGraph_t graph = nullptr;
+    cudaGraphNode_t node = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  One by_bt[4];  // 128, 256, 512, 1024 threads per system
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace cp {
+
+void batch_graphs_release(cp_ctx* ctx) {
+  BatchGraphs* G = ctx->batch_graphs;
+  if (!G) return;
+  for (auto& o : G->by_bt) {
+    if (o.exec) cudaGraphExecDestroy(o.exec);
+    if (o.graph) cudaGraphDestroy(o.graph);
+  }
+  if (G->e0) cudaEventDestroy(G->e0);
+  if (G->e1) cudaEventDestroy(G->e1);
+  delete G;
+  ctx->batch_graphs = nullptr;
+}
+
+static int bt_slot(int bt) { return bt == 128 ? 0 : bt == 256 ? 1 : bt == 512 ? 2 : 3; }
+
 // Runs one batch with BT threads per system; returns the launch's time (ms,
 // CUDA events around the graph launch on s).
 template <int BT>
@@ -370,39 +404,49 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
   CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT>, BT, 0));
   int grid = ctx->num_sms * std::max(per_sm, 1);
   if (grid > nsys) grid = nsys;
-  // capture the single persistent launch in a graph and launch it
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ge = nullptr;
-  cudaStream_t cap = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  float ms = 0.f;
-  CP_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-  try {
-    CP_CUDA(cudaEventCreate(&e0));
-    CP_CUDA(cudaEventCreate(&e1));
-    CP_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    k_batch_solve<BT><<<grid, BT, 0, cap>>>(d_sys, nsys, d_order, d_next, P, d_out);
-    CP_CUDA(cudaStreamEndCapture(cap, &g));
-    CP_CUDA(cudaGraphInstantiate(&ge, g, 0));
-    ctx->launches.fetch_add(1, std::memory_order_relaxed);
-    CP_CUDA(cudaEventRecord(e0, s));
-    CP_CUDA(cudaGraphLaunch(ge, s));
-    CP_CUDA(cudaEventRecord(e1, s));
-    CP_CUDA(cudaEventSynchronize(e1));
-    CP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-  } catch (...) {
-    if (ge) cudaGraphExecDestroy(ge);
-    if (g) cudaGraphDestroy(g);
-    if (e0) cudaEventDestroy(e0);
-    if (e1) cudaEventDestroy(e1);
-    cudaStreamDestroy(cap);
-    throw;
+  if (!ctx->batch_graphs) {
+    BatchGraphs* G = new BatchGraphs;
+    if (cudaEventCreate(&G->e0) != cudaSuccess || cudaEventCreate(&G->e1) != cudaSuccess) {
+      ctx->batch_graphs = G;
+      batch_graphs_release(ctx);
+      CP_CUDA(cudaGetLastError());
+      throw Error{CP_ERR_CUDA};
+    }
+    ctx->batch_graphs = G;
   }
-  cudaGraphExecDestroy(ge);
-  cudaGraphDestroy(g);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  cudaStreamDestroy(cap);
+  BatchGraphs::One& g = ctx->batch_graphs->by_bt[bt_slot(BT)];
+  BatchSys const* a_sys = d_sys;
+  int a_nsys = nsys;
+  const int* a_order = d_order;
+  int* a_next = d_next;
+  BatchParams a_p = P;
+  BatchOut* a_out = d_out;
+  void* args[] = {&a_sys, &a_nsys, &a_order, &a_next, &a_p, &a_out};
+  cudaKernelNodeParams kp{};
+  kp.func = reinterpret_cast<void*>(k_batch_solve<BT>);
+  kp.gridDim = dim3(grid);
+  kp.blockDim = dim3(BT);
+  kp.sharedMemBytes = 0;
+  kp.kernelParams = args;
+  if (g.exec && cudaGraphExecKernelNodeSetParams(g.exec, g.node, &kp) != cudaSuccess) {
+    // an update the instantiated graph does not take: build it again
+    (void)cudaGetLastError();
+    cudaGraphExecDestroy(g.exec);
+    cudaGraphDestroy(g.graph);
+    g = BatchGraphs::One{};
+  }
+  if (!g.exec) {
+    CP_CUDA(cudaGraphCreate(&g.graph, 0));
+    CP_CUDA(cudaGraphAddKernelNode(&g.node, g.graph, nullptr, 0, &kp));
+    CP_CUDA(cudaGraphInstantiate(&g.exec, g.graph, 0));
+  }
+  ctx->launches.fetch_add(1, std::memory_order_relaxed);
+  float ms = 0.f;
+  CP_CUDA(cudaEventRecord(ctx->batch_graphs->e0, s));
+  CP_CUDA(cudaGraphLaunch(g.exec, s));
+  CP_CUDA(cudaEventRecord(ctx->batch_graphs->e1, s));
+  CP_CUDA(cudaEventSynchronize(ctx->batch_graphs->e1));
+  CP_CUDA(cudaEventElapsedTime(&ms, ctx->batch_graphs->e0, ctx->batch_graphs->e1));
   return ms;
 }
 

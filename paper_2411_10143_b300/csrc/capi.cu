@@ -221,6 +221,7 @@ cp_status cp_destroy(cp_ctx* ctx) {
     if (ctx->pin_side) cudaFreeHost(ctx->pin_side);
     ctx->mapped.release();
     ctx->events.release();
+    batch_graphs_release(ctx);
     delete ctx;
   });
 }

@@ -225,6 +225,12 @@ class SideWorker {
 };
 }  // namespace cp
 
+namespace cp {
+struct BatchGraphs;
+// Releases the context's batched-solve graphs (cp_destroy).
+void batch_graphs_release(cp_ctx* ctx);
+}  // namespace cp
+
 struct cp_ctx {
   int device = 0;
   int num_sms = 0;
@@ -245,6 +251,7 @@ struct cp_ctx {
   cp::SideWorker* side_worker = nullptr;
   cp::MappedPool mapped;  // host-mapped pages reused by the solves
   cp::EventPool events;   // CUDA events reused by the solves
+  cp::BatchGraphs* batch_graphs = nullptr;  // instantiated batched-solve graphs (batch.cu)
 };
 
 struct cp_mat {
