@@ -681,6 +681,18 @@ static int balanced_grid(cp_ctx* ctx, int64_t units) {
   return (int)(g < 1 ? 1 : g > ctx->grid_stream ? ctx->grid_stream : g);
 }
 
+// ELL and HYB without a fused dot product: one trip per thread (a row pair
+// each), up to the block-partials capacity.  The extra blocks over the
+// resident grid keep more x gathers in flight from the start, which pays on
+// random-column matrices (uniform 8 per row, n 2M: 81.7 -> 72.5 us) and is
+// neutral on stencil and banded ones.  With a fused dot the resident grid
+// stays: every block of the next kernel sums one partial per SpMV block.
+static int wide_grid(int64_t units) {
+  int64_t g = (units + kBlock - 1) / kBlock;
+  if (g > kMaxPartials) g = kMaxPartials;
+  return (int)(g < 1 ? 1 : g);
+}
+
 static int grid_for(cp_ctx* ctx, int64_t work_items) {
   const int64_t need = (work_items + kBlock - 1) / kBlock;
   int64_t g = need < ctx->grid_stream ? need : ctx->grid_stream;
@@ -807,7 +819,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
       return DOT ? g : 0;
     }
     case CP_FMT_ELL: {
-      const int g = balanced_grid(ctx, (n + 1) / 2);  // a thread per row pair
+      const int g = DOT ? balanced_grid(ctx, (n + 1) / 2) : wide_grid((n + 1) / 2);
       CP_LAUNCH(ctx, (k_ell<T, GEN, DOT>), g, kBlock, 0, s, n, m->ell.K, m->ell.ld, m->ell.col,
                 Vals<T>::ell(m->ell), x, y, alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;
@@ -820,7 +832,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
       return DOT ? g : 0;
     }
     case CP_FMT_HYB: {
-      const int g = balanced_grid(ctx, (n + 1) / 2);
+      const int g = DOT ? balanced_grid(ctx, (n + 1) / 2) : wide_grid((n + 1) / 2);
       if (m->hyb_coo.n == 0) {  // every row fits the ELL part: the fused ELL kernel suffices
         CP_LAUNCH(ctx, (k_ell<T, GEN, DOT>), g, kBlock, 0, s, n, m->hyb_ell.K, m->hyb_ell.ld,
                   m->hyb_ell.col, Vals<T>::ell(m->hyb_ell), x, y, alpha, beta, dotv, partials,
