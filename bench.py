@@ -805,9 +805,10 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
                                   C.default_opts(tol=TOL, inner_tol=1e-5, restart=30,
                                                  precision=C.PREC_FP32_IR))
         tuned.append({"mean_rows": int(np.mean([g[1].nrows for g in grp])),
-                      "gmres": any(g[3] for g in grp), "threads": best,
-                      "ms": [round(t, 3) for t in ms]})
-    log_fn(f"serve: batch autotuner picks {[t['threads'] for t in tuned]}")
+                      "gmres": any(g[3] for g in grp), "threads": best[0],
+                      "threads_per_row": best[1],
+                      "ms": {f"{t}x{r}": round(v, 3) for (t, r), v in ms.items()}})
+    log_fn(f"serve: batch autotuner picks {[(t['threads'], t['threads_per_row']) for t in tuned]}")
     # sequential service rate on a sample
     srv = C.Server(ctx, lanes=1)
     sample = items[: min(24, len(items))]

@@ -457,42 +457,52 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
                          const cp_solve_opts* opts, cp_solve_info* info);
 
 /* ------------------------------------------------------------------ batching */
-/* cp_batch_solve: solve nsys small systems A_i x_i = b_i in one persistent,
- * graph-captured launch.  One thread block per system at a time, systems taken
- * largest first from a device work queue.  Every system runs FP64 iterative
- * refinement to opts->tol around FP32 inner solves to opts->inner_tol:
- * solver[i] = 0 for CG (SPD A_i), 1 for GMRES(opts->restart), restart <= 32.
- * FP64 is kept for the outer residual, the update of x and GMRES's Givens /
- * least-squares step.  mats[i] (square, CSR; the kernel is the CSR scalar one),
- * b[i], x[i] (device FP64, x read as x0) are host arrays of nsys entries;
- * opts->maxit bounds the inner steps of each system; threads per block: 128,
- * 256, 512, 1024 or 0 (the autotuner's choice for the batch's class, see
- * cp_batch_tune, else a rule on the mean system size).  infos (host array of
- * nsys, may be NULL) receives per-system iterations, relres_true, status.
- * Returns the first non-OK system status, else CP_OK. */
+/* cp_batch_solve: solve nsys small systems A_i x_i = b_i in one persistent
+ * launch held in a CUDA graph (each context instantiates the graph of each
+ * launch shape once and updates its kernel node per batch).  One thread block
+ * per system at a time, systems taken largest first from a device work queue.
+ * Every system runs FP64 iterative refinement to opts->tol around FP32 inner
+ * solves to opts->inner_tol: solver[i] = 0 for CG (SPD A_i), 1 for
+ * GMRES(opts->restart), restart <= 32.  FP64 is kept for the outer residual,
+ * the update of x and GMRES's Givens / least-squares step.  mats[i] (square,
+ * CSR), b[i], x[i] (device FP64, x read as x0) are host arrays of nsys entries;
+ * opts->maxit bounds the inner steps of each system.  The launch shape:
+ *  - threads: threads per system, 128, 256, 512 or 1024; 0 = the schedule of
+ *    the batch's class (the autotuner's choice, see cp_batch_tune, else a rule
+ *    on the mean system size with a thread per row);
+ *  - threads_per_row: 1 (CSR-scalar rows), 4 or 16 (groups of lanes share a
+ *    row and add with shuffles, for long rows); 0 = the class's schedule when
+ *    threads = 0, else 1.
+ * infos (host array of nsys, may be NULL) receives per-system iterations,
+ * relres_true, status.  Returns the first non-OK system status, else CP_OK.
+ * (The batching pattern; the paper's solver handles one system at a time.) */
 cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                          const double* const* b, double* const* x, const cp_solve_opts* opts,
-                         int32_t threads, cp_solve_info* infos);
+                         int32_t threads, int32_t threads_per_row, cp_solve_info* infos);
 
 /* cp_batch_tune: the batching autotuner (a systems addition for the batched
  * pattern; the paper has no counterpart).  Solves the given batch as
  * cp_batch_solve does, but into scratch solutions (the batch's own x are not
- * touched, x0 = 0), once per candidate of 128, 256, 512 and 1024 threads per
- * system after one warm-up each, timing each launch with CUDA events.  It
- * records the fastest in a per-device schedule under the batch's class:
- * whether the batch holds a GMRES system, and floor(log2(mean rows)).
- * cp_batch_solve with threads = 0 then uses that choice for batches of the
- * class.  Arguments as cp_batch_solve.  best_threads (may be NULL) receives the
- * choice; ms (may be NULL, 4 floats) the times of the four candidates in that
- * order.  Any system that fails to converge returns its status. */
+ * touched, x0 = 0), once per launch shape -- 128, 256, 512 and 1024 threads per
+ * system, each with 1, 4 and 16 threads per row -- after one warm-up each,
+ * timing each launch with CUDA events.  It records the fastest shape in a
+ * per-device schedule under the batch's class: whether the batch holds a GMRES
+ * system, and floor(log2(mean rows)).  cp_batch_solve with threads = 0 then
+ * uses that shape for batches of the class.  Arguments as cp_batch_solve.
+ * best_threads / best_threads_per_row (may be NULL) receive the choice; ms (may
+ * be NULL, 12 floats) the times of the shapes, ms[3 t + r] for threads index t
+ * (128, 256, 512, 1024) and threads-per-row index r (1, 4, 16).  Any system that
+ * fails to converge returns its status. */
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                         const double* const* b, const cp_solve_opts* opts,
-                        int32_t* best_threads, float* ms);
-/* Threads per system that cp_batch_solve(threads = 0) uses for a batch with
- * mean_rows rows per system (has_gmres: the batch holds a GMRES system): the
- * tuned choice of that class, else 128 / 256 / 512 / 1024 for mean rows below
- * 512 / 2048 / 8192 / above.  Returns 0 if ctx is NULL. */
-int32_t cp_batch_threads(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres);
+                        int32_t* best_threads, int32_t* best_threads_per_row, float* ms);
+/* The launch shape cp_batch_solve(threads = 0) uses for a batch with mean_rows
+ * rows per system (has_gmres: the batch holds a GMRES system): the tuned shape
+ * of that class, else 128 / 256 / 512 / 1024 threads for mean rows below
+ * 512 / 2048 / 8192 / above, with 1 thread per row.  threads, threads_per_row:
+ * host int32.  Errors: CP_ERR_INVALID (NULL argument). */
+cp_status cp_batch_schedule(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres, int32_t* threads,
+                            int32_t* threads_per_row);
 
 /* ------------------------------------------------------------------ serving */
 /* A continuous-batching solve server.  Requests carry a matrix already loaded

@@ -187,7 +187,7 @@ _SIGS = {
     "cp_solve_cg": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_solve_gmres": (c_int32, [_p, _p, _p, _p, POINTER(SolveOpts), POINTER(SolveInfo)]),
     "cp_batch_solve": (c_int32, [_p, c_int32, _p, _p, _p, _p, POINTER(SolveOpts), c_int32,
-                                 _p]),
+                                 c_int32, _p]),
     "cp_gate_set": (c_int32, [_p, _p]),
     "cp_inject_side_failure": (c_int32, [_p, c_int32]),
     "cp_warmup": (c_int32, [_p]),
@@ -195,8 +195,8 @@ _SIGS = {
     "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
                                  POINTER(c_double), POINTER(c_double)]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
-                                _p]),
-    "cp_batch_threads": (c_int32, [_p, c_int64, c_int32]),
+                                POINTER(c_int32), _p]),
+    "cp_batch_schedule": (c_int32, [_p, c_int64, c_int32, POINTER(c_int32), POINTER(c_int32)]),
     "cp_server_opts_default": (None, [POINTER(ServerOpts)]),
     "cp_server_create": (c_int32, [_p, POINTER(ServerOpts), POINTER(_p)]),
     "cp_server_submit": (c_int32, [_p, POINTER(Request)]),
@@ -423,10 +423,12 @@ class Context:
             _check(lib().cp_adam_step(self._h, params.numel(), _ptr(params), _ptr(grad), _ptr(m),
                                       _ptr(v), t, lr, b1, b2, eps))
 
-    def batch_solve(self, mats, solvers, bs, xs, opts=None, threads=0, raise_on_error=True):
+    def batch_solve(self, mats, solvers, bs, xs, opts=None, threads=0, threads_per_row=0,
+                    raise_on_error=True):
         """cp_batch_solve: many small systems in one persistent launch.  mats:
         Matrix list; solvers: 0 (CG) / 1 (GMRES) per system; bs, xs: torch CUDA
-        float64 tensors (xs: x0 in, solutions out).  Returns the SolveInfo list."""
+        float64 tensors (xs: x0 in, solutions out); threads / threads_per_row: the
+        launch shape (0: the class's schedule).  Returns the SolveInfo list."""
         n = len(mats)
         hm = (c_void_p * n)(*[m._h.value for m in mats])
         hs = np.ascontiguousarray(solvers, np.int32)
@@ -435,26 +437,33 @@ class Context:
         infos = (SolveInfo * n)()
         o = opts if opts is not None else default_opts(precision=PREC_FP32_IR)
         with self.ordered():
-            st = lib().cp_batch_solve(self._h, n, hm, _ptr(hs), hb, hx, byref(o), threads, infos)
+            st = lib().cp_batch_solve(self._h, n, hm, _ptr(hs), hb, hx, byref(o), threads,
+                                      threads_per_row, infos)
         if raise_on_error:
             _check(st)
         return list(infos)
 
+    BATCH_THREADS = (128, 256, 512, 1024)
+    BATCH_TPV = (1, 4, 16)
+
     def batch_tune(self, mats, solvers, bs, opts=None):
-        """cp_batch_tune: time 128/256/512/1024 threads per system on this batch
-        (scratch solutions) and record the fastest for its class.  Returns
-        (best threads, [ms of each candidate])."""
+        """cp_batch_tune: time every launch shape (128/256/512/1024 threads per
+        system x 1/4/16 threads per row) on this batch (scratch solutions) and
+        record the fastest for its class.  Returns ((threads, threads per row),
+        {(threads, threads per row): ms})."""
         n = len(mats)
         hm = (c_void_p * n)(*[m._h.value for m in mats])
         hs = np.ascontiguousarray(solvers, np.int32)
         hb = (c_void_p * n)(*[t.data_ptr() for t in bs])
-        best = c_int32(0)
-        ms = np.zeros(4, np.float32)
+        best, best_tpv = c_int32(0), c_int32(0)
+        ms = np.zeros(12, np.float32)
         o = opts if opts is not None else default_opts(precision=PREC_FP32_IR)
         with self.ordered():
             _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
-                                       _ptr(ms)))
-        return best.value, ms.tolist()
+                                       byref(best_tpv), _ptr(ms)))
+        times = {(t, r): float(ms[3 * i + j]) for i, t in enumerate(self.BATCH_THREADS)
+                 for j, r in enumerate(self.BATCH_TPV)}
+        return (best.value, best_tpv.value), times
 
     def fp64_fma_rate(self):
         """cp_fp64_fma_rate: measured FP64 FMAs per second of this GPU."""
@@ -477,9 +486,13 @@ class Context:
         """cp_gate_set: install (gate.enabled = 1) or disable the cost-aware switch."""
         _check(lib().cp_gate_set(self._h, byref(gate)))
 
-    def batch_threads(self, mean_rows, has_gmres=False):
-        """Threads per system cp_batch_solve(threads=0) uses for a batch class."""
-        return int(lib().cp_batch_threads(self._h, int(mean_rows), 1 if has_gmres else 0))
+    def batch_schedule(self, mean_rows, has_gmres=False):
+        """(threads per system, threads per row) cp_batch_solve(threads=0) uses for
+        a batch class."""
+        t, r = c_int32(0), c_int32(0)
+        _check(lib().cp_batch_schedule(self._h, int(mean_rows), 1 if has_gmres else 0, byref(t),
+                                       byref(r)))
+        return t.value, r.value
 
     @staticmethod
     def mlp_nparams(d, h1, h2, k):

@@ -89,32 +89,65 @@ __device__ __forceinline__ double2 bsum_g(double v, double* red, G g) {
   return make_double2(red[32], red[33]);
 }
 
+// Row loops of the batched kernel: TPV threads per row (1: a thread per row,
+// CSR-scalar; 4 or 16: groups of lanes share a row's entries and add their
+// partial sums with shuffles, for systems with long rows).  The loop over row
+// blocks runs the same number of trips in every thread, so whole warps reach
+// the shuffles.
+template <int BT, int TPV, typename F>
+__device__ __forceinline__ void for_rows(int64_t n, F&& f) {
+  if constexpr (TPV == 1) {
+    for (int64_t i = threadIdx.x; i < n; i += BT) f(i, 0, true);
+  } else {
+    constexpr int RPB = BT / TPV;
+    const int sub = threadIdx.x % TPV;
+    for (int64_t base = 0; base < n; base += RPB) {
+      const int64_t i = base + threadIdx.x / TPV;
+      f(i, sub, i < n);
+    }
+  }
+}
+template <int TPV, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+  for (int o = TPV / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // FP64 residual r = b - A x (FP64 values) and ||r||^2
-template <int BT>
+template <int BT, int TPV>
 __device__ double resid64(const BatchSys& S, double* red) {
   double acc = 0.0;
-  for (int64_t i = threadIdx.x; i < S.n; i += BT) {
+  for_rows<BT, TPV>(S.n, [&](int64_t i, int sub, bool in) {
     double s = 0.0;
-    for (int k = S.rowptr[i]; k < S.rowptr[i + 1]; ++k) s = fma(S.val[k], S.x[S.col[k]], s);
-    const double ri = S.b[i] - s;
-    S.r[i] = ri;
-    acc = fma(ri, ri, acc);
-  }
+    if (in)
+      for (int k = S.rowptr[i] + sub; k < S.rowptr[i + 1]; k += TPV)
+        s = fma(S.val[k], S.x[S.col[k]], s);
+    s = group_sum<TPV>(s);
+    if (in && sub == 0) {
+      const double ri = S.b[i] - s;
+      S.r[i] = ri;
+      acc = fma(ri, ri, acc);
+    }
+  });
   return bsum<BT>(acc, red);
 }
 
 // y = A32 v (FP32)
-template <int BT>
+template <int BT, int TPV>
 __device__ __forceinline__ void spmv32(const BatchSys& S, const float* v, float* y) {
-  for (int64_t i = threadIdx.x; i < S.n; i += BT) {
+  for_rows<BT, TPV>(S.n, [&](int64_t i, int sub, bool in) {
     float s = 0.f;
-    for (int k = S.rowptr[i]; k < S.rowptr[i + 1]; ++k) s = fmaf(S.val32[k], v[S.col[k]], s);
-    y[i] = s;
-  }
+    if (in)
+      for (int k = S.rowptr[i] + sub; k < S.rowptr[i + 1]; k += TPV)
+        s = fmaf(S.val32[k], v[S.col[k]], s);
+    s = group_sum<TPV>(s);
+    if (in && sub == 0) y[i] = s;
+  });
 }
 
 // ------------------------------------------------------------------ inner CG (FP32)
-template <int BT>
+template <int BT, int TPV>
 __device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, double* red) {
   const int64_t n = S.n;
   float* r = S.w32;
@@ -137,7 +170,7 @@ __device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, dou
   // shares in FP64.
   while (it < budget && rr > stop) {
     __syncthreads();
-    spmv32<BT>(S, p, ap);
+    spmv32<BT, TPV>(S, p, ap);
     __syncthreads();
     float pap_t = 0.f;
     for (int64_t i = threadIdx.x; i < n; i += BT) pap_t = fmaf(p[i], ap[i], pap_t);
@@ -165,7 +198,7 @@ __device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, dou
 }
 
 // ------------------------------------------------------------------ inner GMRES (FP32 basis)
-template <int BT>
+template <int BT, int TPV>
 __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, double* red,
                            double* Hs /*(m+1)*m*/, double* gs /*m+1*/, double* cs, double* sn,
                            double* hv /*m+1*/, float* acc_red /*32*(BT/32)*/) {
@@ -190,7 +223,7 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
   while (it < budget) {
     if (!first) {  // restart: V0 = r32 - A d
       __syncthreads();
-      spmv32<BT>(S, d, V + n);  // scratch column 1
+      spmv32<BT, TPV>(S, d, V + n);  // scratch column 1
       __syncthreads();
       double s = 0.0;
       for (int64_t i = threadIdx.x; i < n; i += BT) {
@@ -213,7 +246,7 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
     for (int j = 0; j < m && it < budget; ++j) {
       float* w = V + (int64_t)(j + 1) * n;
       __syncthreads();
-      spmv32<BT>(S, V + (int64_t)j * n, w);
+      spmv32<BT, TPV>(S, V + (int64_t)j * n, w);
       if (threadIdx.x <= j) hv[threadIdx.x] = 0.0;
       for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
         __syncthreads();
@@ -303,7 +336,7 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
 }
 
 // ------------------------------------------------------------------ the persistent kernel
-template <int BT>
+template <int BT, int TPV>
 __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__ sys, int nsys,
                                                     const int* __restrict__ order,
                                                     int* __restrict__ next, BatchParams P,
@@ -328,7 +361,7 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
     double rr = 0.0;
     for (;;) {
       __syncthreads();
-      rr = resid64<BT>(S, red);
+      rr = resid64<BT, TPV>(S, red);
       if (bb == 0.0 || rr <= P.tol * P.tol * bb) break;
       if (!isfinite(rr)) {
         status = CP_ERR_BREAKDOWN;
@@ -340,8 +373,9 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
       }
       __syncthreads();
       const int budget = P.max_inner - inner;
-      int got = S.solver == 0 ? inner_cg<BT>(S, P, budget, red)
-                              : inner_gmres<BT>(S, P, budget, red, Hs, gs, cs, sn, hv, acc_red);
+      int got = S.solver == 0
+                    ? inner_cg<BT, TPV>(S, P, budget, red)
+                    : inner_gmres<BT, TPV>(S, P, budget, red, Hs, gs, cs, sn, hv, acc_red);
       if (got < 0) {
         status = CP_ERR_BREAKDOWN;
         inner += -got - 1;
@@ -362,11 +396,16 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
 
 // ------------------------------------------------------------------ host
 // The batched solve is one persistent launch in a CUDA graph.  Each context
-// instantiates the graph of each block size once, on first use; later batches
-// only update the kernel node's grid and arguments in the instantiated graph
-// (cudaGraphExecKernelNodeSetParams) and launch it, with no capture or
-// instantiation on the path of a batch.
+// instantiates the graph of each (block size, threads per row) once, on first
+// use; later batches only update the kernel node's grid and arguments in the
+// instantiated graph (cudaGraphExecKernelNodeSetParams) and launch it, with no
+// capture or instantiation on the path of a batch.
 }  // namespace cp
+
+namespace {
+constexpr int kBatchThreads[4] = {128, 256, 512, 1024};
+constexpr int kBatchTpv[3] = {1, 4, 16};
+}  // namespace
 
 struct cp::BatchGraphs {
   struct One {
@@ -374,7 +413,7 @@ struct cp::BatchGraphs {
     cudaGraphNode_t node = nullptr;
     cudaGraphExec_t exec = nullptr;
   };
-  One by_bt[4];  // 128, 256, 512, 1024 threads per system
+  One by_cfg[4][3];  // [threads per system][threads per row]
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 
@@ -383,10 +422,11 @@ namespace cp {
 void batch_graphs_release(cp_ctx* ctx) {
   BatchGraphs* G = ctx->batch_graphs;
   if (!G) return;
-  for (auto& o : G->by_bt) {
-    if (o.exec) cudaGraphExecDestroy(o.exec);
-    if (o.graph) cudaGraphDestroy(o.graph);
-  }
+  for (auto& row : G->by_cfg)
+    for (auto& o : row) {
+      if (o.exec) cudaGraphExecDestroy(o.exec);
+      if (o.graph) cudaGraphDestroy(o.graph);
+    }
   if (G->e0) cudaEventDestroy(G->e0);
   if (G->e1) cudaEventDestroy(G->e1);
   delete G;
@@ -394,14 +434,15 @@ void batch_graphs_release(cp_ctx* ctx) {
 }
 
 static int bt_slot(int bt) { return bt == 128 ? 0 : bt == 256 ? 1 : bt == 512 ? 2 : 3; }
+static int tpv_slot(int tpv) { return tpv == 1 ? 0 : tpv == 4 ? 1 : 2; }
 
-// Runs one batch with BT threads per system; returns the launch's time (ms,
-// CUDA events around the graph launch on s).
-template <int BT>
+// Runs one batch with BT threads per system and TPV threads per row; returns
+// the launch's time (ms, CUDA events around the graph launch on s).
+template <int BT, int TPV>
 static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const int* d_order,
                           int* d_next, const BatchParams& P, BatchOut* d_out, cudaStream_t s) {
   int per_sm = 0;
-  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT>, BT, 0));
+  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT, TPV>, BT, 0));
   int grid = ctx->num_sms * std::max(per_sm, 1);
   if (grid > nsys) grid = nsys;
   if (!ctx->batch_graphs) {
@@ -414,7 +455,7 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
     }
     ctx->batch_graphs = G;
   }
-  BatchGraphs::One& g = ctx->batch_graphs->by_bt[bt_slot(BT)];
+  BatchGraphs::One& g = ctx->batch_graphs->by_cfg[bt_slot(BT)][tpv_slot(TPV)];
   BatchSys const* a_sys = d_sys;
   int a_nsys = nsys;
   const int* a_order = d_order;
@@ -423,7 +464,7 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
   BatchOut* a_out = d_out;
   void* args[] = {&a_sys, &a_nsys, &a_order, &a_next, &a_p, &a_out};
   cudaKernelNodeParams kp{};
-  kp.func = reinterpret_cast<void*>(k_batch_solve<BT>);
+  kp.func = reinterpret_cast<void*>(k_batch_solve<BT, TPV>);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(BT);
   kp.sharedMemBytes = 0;
@@ -450,24 +491,36 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
   return ms;
 }
 
-static float launch_batch_bt(int bt, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
-                             const int* d_order, int* d_next, const BatchParams& P,
-                             BatchOut* d_out, cudaStream_t s) {
-  switch (bt) {
-    case 128: return launch_batch<128>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    case 256: return launch_batch<256>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    case 512: return launch_batch<512>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    default: return launch_batch<1024>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+template <int BT>
+static float launch_batch_tpv(int tpv, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
+                              const int* d_order, int* d_next, const BatchParams& P,
+                              BatchOut* d_out, cudaStream_t s) {
+  switch (tpv) {
+    case 1: return launch_batch<BT, 1>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 4: return launch_batch<BT, 4>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    default: return launch_batch<BT, 16>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
   }
 }
 
-// ---- the autotuner's schedule: threads per system for a batch class, per
-// device.  A class is (the batch holds a GMRES system, floor(log2(mean rows))).
+static float launch_batch_cfg(int bt, int tpv, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
+                              const int* d_order, int* d_next, const BatchParams& P,
+                              BatchOut* d_out, cudaStream_t s) {
+  switch (bt) {
+    case 128: return launch_batch_tpv<128>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 256: return launch_batch_tpv<256>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 512: return launch_batch_tpv<512>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    default: return launch_batch_tpv<1024>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+  }
+}
+
+// ---- the autotuner's schedule: (threads per system, threads per row) for a
+// batch class, per device.  A class is (the batch holds a GMRES system,
+// floor(log2(mean rows))).
 namespace {
 constexpr int kSchedDevices = 64;
 constexpr int kSchedBuckets = 32;
 std::mutex g_sched_mu;
-int g_sched[kSchedDevices][2][kSchedBuckets] = {};  // 0: not tuned
+BatchSchedule g_sched[kSchedDevices][2][kSchedBuckets] = {};  // threads 0: not tuned
 
 int size_bucket(int64_t mean_rows) {
   int b = 0;
@@ -478,19 +531,21 @@ int size_bucket(int64_t mean_rows) {
 // Untuned rule.  The tuner measured 1024 threads fastest for batches of
 // 32 mixed CG / GMRES systems of about 10,000 rows (52.8 ms against 94 / 175 /
 // 341 ms with 512 / 256 / 128): a block per system leaves most SMs idle when
-// the batch is smaller than the GPU, so wider blocks win early.
-int default_threads(int64_t mean_rows) {
-  return mean_rows < 512 ? 128 : mean_rows < 2048 ? 256 : mean_rows < 8192 ? 512 : 1024;
+// the batch is smaller than the GPU, so wider blocks win early.  A thread per
+// row (CSR-scalar).
+BatchSchedule default_schedule(int64_t mean_rows) {
+  return BatchSchedule{
+      mean_rows < 512 ? 128 : mean_rows < 2048 ? 256 : mean_rows < 8192 ? 512 : 1024, 1};
 }
 }  // namespace
 
-int batch_threads(cp_ctx* ctx, int64_t mean_rows, bool has_gmres) {
+BatchSchedule batch_schedule(cp_ctx* ctx, int64_t mean_rows, bool has_gmres) {
   if (ctx->device >= 0 && ctx->device < kSchedDevices) {
     std::lock_guard<std::mutex> lock(g_sched_mu);
-    const int t = g_sched[ctx->device][has_gmres ? 1 : 0][size_bucket(mean_rows)];
-    if (t) return t;
+    const BatchSchedule t = g_sched[ctx->device][has_gmres ? 1 : 0][size_bucket(mean_rows)];
+    if (t.threads) return t;
   }
-  return default_threads(mean_rows);
+  return default_schedule(mean_rows);
 }
 
 // A batch laid out on the device: per-system descriptors, workspaces, the
@@ -567,27 +622,35 @@ static void batch_prepare(cp_ctx* ctx, BatchJob& J, int nsys, cp_mat* const* mat
   CP_CUDA(cudaStreamSynchronize(s));
 }
 
-static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& opt, int bt) {
+static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& opt,
+                       BatchSchedule sc) {
   cudaStream_t s = J.s;
   if (J.xs) CP_CUDA(cudaMemsetAsync(J.xs, 0, J.total_rows * sizeof(double), s));
   CP_CUDA(cudaMemsetAsync(J.d_order + nsys, 0, sizeof(int), s));
   BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart};
-  return launch_batch_bt(bt, ctx, J.d_sys, nsys, J.d_order, J.d_order + nsys, P, J.d_out, s);
+  return launch_batch_cfg(sc.threads, sc.tpv, ctx, J.d_sys, nsys, J.d_order, J.d_order + nsys, P,
+                          J.d_out, s);
 }
 
 void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
                  const double* const* b, double* const* x, const cp_solve_opts* o,
-                 cp_solve_info* infos, int threads) {
+                 cp_solve_info* infos, int threads, int tpv) {
   cp_solve_opts opt;
   cp_solve_opts_default(&opt);
   if (o) opt = *o;
   CP_REQUIRE(threads == 0 || threads == 128 || threads == 256 || threads == 512 || threads == 1024,
              CP_ERR_INVALID, "threads per system must be 128, 256, 512 or 1024");
+  CP_REQUIRE(tpv == 0 || tpv == 1 || tpv == 4 || tpv == 16, CP_ERR_INVALID,
+             "threads per row must be 1, 4 or 16");
   BatchJob J;
   J.s = ctx->main;
   batch_prepare(ctx, J, nsys, mats, solver, b, x, opt, false);
-  const int bt = threads ? threads : batch_threads(ctx, J.total_rows / nsys, J.has_gmres);
-  batch_run(ctx, J, nsys, opt, bt);
+  // threads = 0: the tuned (or default) schedule of the batch's class, whose
+  // threads per row apply unless tpv is given
+  BatchSchedule sc = batch_schedule(ctx, J.total_rows / nsys, J.has_gmres);
+  if (threads) sc = BatchSchedule{threads, 1};
+  if (tpv) sc.tpv = tpv;
+  batch_run(ctx, J, nsys, opt, sc);
   std::vector<BatchOut> out(nsys);
   CP_CUDA(cudaMemcpyAsync(out.data(), J.d_out, nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost,
                           J.s));
@@ -611,26 +674,27 @@ void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solv
              worst);
 }
 
-int batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
-               const double* const* b, const cp_solve_opts* o, float* ms4) {
+BatchSchedule batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
+                         const double* const* b, const cp_solve_opts* o, float* ms12) {
   cp_solve_opts opt;
   cp_solve_opts_default(&opt);
   if (o) opt = *o;
   BatchJob J;
   J.s = ctx->main;
   batch_prepare(ctx, J, nsys, mats, solver, b, nullptr, opt, true);
-  const int cand[4] = {128, 256, 512, 1024};
-  int best = 0;
+  BatchSchedule best{0, 1};
   float best_ms = 0.f;
-  for (int c = 0; c < 4; ++c) {
-    batch_run(ctx, J, nsys, opt, cand[c]);  // warm-up: module load, caches
-    const float ms = batch_run(ctx, J, nsys, opt, cand[c]);
-    if (ms4) ms4[c] = ms;
-    if (!best || ms < best_ms) {
-      best = cand[c];
-      best_ms = ms;
+  for (int c = 0; c < 4; ++c)
+    for (int v = 0; v < 3; ++v) {
+      const BatchSchedule sc{kBatchThreads[c], kBatchTpv[v]};
+      batch_run(ctx, J, nsys, opt, sc);  // warm-up: module load, caches
+      const float ms = batch_run(ctx, J, nsys, opt, sc);
+      if (ms12) ms12[c * 3 + v] = ms;
+      if (!best.threads || ms < best_ms) {
+        best = sc;
+        best_ms = ms;
+      }
     }
-  }
   CP_CUDA(cudaStreamSynchronize(J.s));
   if (ctx->device >= 0 && ctx->device < kSchedDevices) {
     std::lock_guard<std::mutex> lock(g_sched_mu);

@@ -387,11 +387,11 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* m, const double* b, double* x,
 
 cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                          const double* const* b, double* const* x, const cp_solve_opts* opts,
-                         int32_t threads, cp_solve_info* infos) {
+                         int32_t threads, int32_t threads_per_row, cp_solve_info* infos) {
   return guard([&] {
     CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
     use_device(ctx);
-    batch_solve(ctx, nsys, mats, solver, b, x, opts, infos, threads);
+    batch_solve(ctx, nsys, mats, solver, b, x, opts, infos, threads, threads_per_row);
   });
 }
 
@@ -427,18 +427,24 @@ int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t it
 
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                         const double* const* b, const cp_solve_opts* opts,
-                        int32_t* best_threads, float* ms) {
+                        int32_t* best_threads, int32_t* best_threads_per_row, float* ms) {
   return guard([&] {
     CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
     use_device(ctx);
-    const int best = batch_tune(ctx, nsys, mats, solver, b, opts, ms);
-    if (best_threads) *best_threads = best;
+    const BatchSchedule best = batch_tune(ctx, nsys, mats, solver, b, opts, ms);
+    if (best_threads) *best_threads = best.threads;
+    if (best_threads_per_row) *best_threads_per_row = best.tpv;
   });
 }
 
-int32_t cp_batch_threads(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres) {
-  if (!ctx) return 0;
-  return batch_threads(ctx, mean_rows, has_gmres != 0);
+cp_status cp_batch_schedule(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres, int32_t* threads,
+                            int32_t* threads_per_row) {
+  return guard([&] {
+    CP_REQUIRE(ctx && threads && threads_per_row, CP_ERR_INVALID, "NULL argument");
+    const BatchSchedule sc = batch_schedule(ctx, mean_rows, has_gmres != 0);
+    *threads = sc.threads;
+    *threads_per_row = sc.tpv;
+  });
 }
 
 int64_t cp_mlp_nparams(int32_t d, int32_t h1, int32_t h2, int32_t k) {

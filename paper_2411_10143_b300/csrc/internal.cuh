@@ -403,15 +403,22 @@ void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host,
                  uint64_t seed, float* final_loss);
 int64_t scratch_floats_api(int64_t N, int d, int h1, int h2, int k);
 
+// A batched launch's shape: threads per system and threads per row.
+struct BatchSchedule {
+  int threads;
+  int tpv;
+};
+// threads / tpv = 0: the schedule of the batch's class (tuned, else by size)
 void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
                  const double* const* b, double* const* x, const cp_solve_opts* o,
-                 cp_solve_info* infos, int threads);
-// the autotuner: times 128/256/512/1024 threads per system on this batch (scratch
-// solutions), records the fastest for the batch's class, returns it
-int batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
-               const double* const* b, const cp_solve_opts* o, float* ms4);
-// threads per system cp_batch_solve uses for a batch class (tuned, else by size)
-int batch_threads(cp_ctx* ctx, int64_t mean_rows, bool has_gmres);
+                 cp_solve_info* infos, int threads, int tpv);
+// the autotuner: times 128/256/512/1024 threads per system x 1/4/16 threads per
+// row on this batch (scratch solutions), records the fastest for the batch's
+// class, returns it; ms12[threads index * 3 + tpv index]
+BatchSchedule batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
+                         const double* const* b, const cp_solve_opts* o, float* ms12);
+// the schedule cp_batch_solve uses for a batch class (tuned, else by size)
+BatchSchedule batch_schedule(cp_ctx* ctx, int64_t mean_rows, bool has_gmres);
 
 // The solve entry (CG or GMRES; FP64 or FP32-inner refinement; plain,
 // sequential or asynchronous prediction).

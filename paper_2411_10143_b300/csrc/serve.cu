@@ -98,7 +98,8 @@ static void run_job(cp_server* S, int lane, cp_server::Job& job) {
       }
       cp_status st = CP_OK;
       try {
-        batch_solve(ctx, nb, mats.data(), solver.data(), b.data(), x.data(), &o, infos.data(), 0);
+        batch_solve(ctx, nb, mats.data(), solver.data(), b.data(), x.data(), &o, infos.data(), 0,
+                    0);
       } catch (const Error& e) {
         st = e.status;
       }

@@ -285,26 +285,45 @@ def evaluate(times_list, picks):
                 mean_regret=g(regret), picks_within_2pct=exact, n=len(picks))
 
 
+def load_dataset(path):
+    """A dataset written by an earlier run (features, labels, timings,
+    conversion times, sizes, names and its held-out split)."""
+    d = np.load(path)
+    T = [json.loads(t) for t in d["times"]]
+    CV = [{(int(k) if k.isdigit() else k): v for k, v in json.loads(c).items()}
+          for c in d["conversions"]]
+    return (d["features"], d["labels"], T, CV, d["nnz"].tolist(), d["names"].tolist(),
+            d["test"])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--count", type=int, default=240)
     ap.add_argument("--reps", type=int, default=100)
     ap.add_argument("--epochs", type=int, default=3000)
+    ap.add_argument("--hidden", type=int, default=32)
+    ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--dataset", default=None,
+                    help="train on a stored dataset.npz instead of timing the suite again")
     ap.add_argument("--out", default=str(models.WEIGHTS))
     args = ap.parse_args()
     ctx = C.Context(0)
-    suite = W.training_suite(seed=77, count=args.count)
-    F, L, T, CV, NNZ, names = build_dataset(ctx, suite, args.reps)
-    rng = np.random.default_rng(0)
-    test = rng.random(len(F)) < 0.2
-    mdl = train_all(ctx, F[~test], L[~test], epochs=args.epochs)
+    if args.dataset:
+        F, L, T, CV, NNZ, names, test = load_dataset(args.dataset)
+    else:
+        suite = W.training_suite(seed=77, count=args.count)
+        F, L, T, CV, NNZ, names = build_dataset(ctx, suite, args.reps)
+        rng = np.random.default_rng(0)
+        test = rng.random(len(F)) < 0.2
+    mdl = train_all(ctx, F[~test], L[~test], h=args.hidden, epochs=args.epochs, seed=args.seed)
     picks = predict_classes(ctx, mdl, F)
     acc = {n: float((picks[test, i] == L[test, i]).mean()) for i, n in enumerate(models.STAGE_NAMES)}
     ev_test = evaluate([T[i] for i in np.flatnonzero(test)], picks[test])
     ev_train = evaluate([T[i] for i in np.flatnonzero(~test)], picks[~test])
     import torch
     meta = dict(gpu=torch.cuda.get_device_name(0), matrices=len(F), test=int(test.sum()),
-                reps=args.reps, epochs=args.epochs, test_accuracy=acc, eval_test=ev_test,
+                reps=args.reps, epochs=args.epochs, hidden=args.hidden, seed=args.seed,
+                test_accuracy=acc, eval_test=ev_test,
                 eval_train=ev_train, losses={k: v["loss"] for k, v in mdl.items()},
                 gate=gate_figures([T[i] for i in np.flatnonzero(~test)],
                                   [CV[i] for i in np.flatnonzero(~test)],

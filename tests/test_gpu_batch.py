@@ -77,14 +77,16 @@ def test_batch_rejects_bad_arguments():
         ctx.batch_solve([M], [2], [b], [x])
     with pytest.raises(C.CascadeError):
         ctx.batch_solve([M], [1], [b], [x], C.default_opts(restart=40, precision=1))
+    with pytest.raises(C.CascadeError):
+        ctx.batch_solve([M], [0], [b], [x], threads=256, threads_per_row=3)
     ctx.close()
 
 
 def test_autotuner_times_every_candidate_and_its_choice_is_used():
-    """cp_batch_tune times the four thread counts on a real batch (scratch
-    solutions: the caller's x are untouched), records the fastest for the
-    batch's class, and cp_batch_solve(threads=0) then solves with it to the
-    same tolerance."""
+    """cp_batch_tune times every launch shape (threads per system x threads per
+    row) on a real batch (scratch solutions: the caller's x are untouched),
+    records the fastest for the batch's class, and cp_batch_solve(threads=0) then
+    solves with it to the same tolerance."""
     ctx = C.Context(0)
     sys = [(W.poisson2d(N), 0) for N in (40, 44, 48, 52)] + [(W.spd_powerlaw(2500, seed=9), 0)]
     mats = [ctx.load(A) for A, _ in sys]
@@ -92,13 +94,36 @@ def test_autotuner_times_every_candidate_and_its_choice_is_used():
     bs = [torch.as_tensor(b, device="cuda") for b in rhs]
     opts = C.default_opts(tol=1e-10, inner_tol=1e-5, precision=C.PREC_FP32_IR)
     best, ms = ctx.batch_tune(mats, [s for _, s in sys], bs, opts)
-    assert best in (128, 256, 512, 1024)
-    assert len(ms) == 4 and all(t > 0 for t in ms)
-    assert ms[(128, 256, 512, 1024).index(best)] == min(ms)
+    assert best[0] in (128, 256, 512, 1024) and best[1] in (1, 4, 16)
+    assert len(ms) == 12 and all(t > 0 for t in ms.values())
+    assert ms[best] == min(ms.values())
     mean = sum(A.nrows for A, _ in sys) // len(sys)
-    assert ctx.batch_threads(mean, False) == best
-    # a class that was not tuned keeps the size rule
-    assert ctx.batch_threads(100, True) == 128 and ctx.batch_threads(200000, True) == 1024
-    assert ctx.batch_threads(1000, True) == 256 and ctx.batch_threads(4000, True) == 512
+    assert ctx.batch_schedule(mean, False) == best
+    # a class that was not tuned keeps the size rule, a thread per row
+    assert ctx.batch_schedule(100, True) == (128, 1)
+    assert ctx.batch_schedule(200000, True) == (1024, 1)
+    assert ctx.batch_schedule(1000, True) == (256, 1) and ctx.batch_schedule(4000, True) == (512, 1)
     check(ctx, sys, 0, seeds=[q + 30 for q in range(len(sys))])
+    ctx.close()
+
+
+@pytest.mark.parametrize("tpv", [4, 16])
+def test_batch_threads_per_row_matches_oracle(tpv):
+    """Rows shared by groups of 4 or 16 lanes (shuffle sums) give the same
+    solutions, on stencils, power-law rows and GMRES systems."""
+    ctx = C.Context(0)
+    mats = [ctx.load(A) for A, _ in systems()]
+    sys = systems()
+    rhs = [oracle.spmv(A, W.vector(A.nrows, q + 40)) for q, (A, _) in enumerate(sys)]
+    bs = [torch.as_tensor(b, device="cuda") for b in rhs]
+    xs = [torch.zeros(A.nrows, dtype=torch.float64, device="cuda") for A, _ in sys]
+    infos = ctx.batch_solve(mats, [s for _, s in sys], bs, xs,
+                            C.default_opts(tol=1e-10, inner_tol=1e-5, restart=30,
+                                           precision=C.PREC_FP32_IR), 256, tpv)
+    for (A, s), b, x, info in zip(sys, rhs, xs, infos):
+        xh = x.cpu().numpy()
+        rel = np.linalg.norm(b - oracle.spmv(A, xh)) / np.linalg.norm(b)
+        ref = (oracle.cg if s == 0 else oracle.gmres)(A, b, tol=1e-10)
+        assert info.status == 0 and rel <= 1e-10, (A.name, rel)
+        assert np.linalg.norm(xh - ref.x) <= 1e-7 * np.linalg.norm(ref.x), A.name
     ctx.close()

@@ -14,7 +14,7 @@ oracle.mlp_input(f, mu, sd))``:
   margin exceeds 1e-3 (below it the FP32 rounding may legitimately flip the
   order, and either class is a correct result of the classifier).
 
-Inputs: the 240 feature vectors of the training set stored beside the weights,
+Inputs: the feature vectors of the training set stored beside the weights,
 and features the GPU computes (``cp_features``) on the four full-size sweep
 matrices and on held-out training-suite matrices, for which the whole
 cascade (``cp_predict``) is also compared with ``oracle.cascade`` applied to
@@ -74,7 +74,7 @@ def check_stage(ctx, stage, f):
 
 def test_every_stage_on_the_training_features(ctx):
     F = np.load(DATASET)["features"]
-    assert F.shape == (240, 15)
+    assert F.shape[1] == 15 and F.shape[0] >= 240
     decided = 0
     for f in F:
         for stage in range(C.STAGE_FORMAT, C.STAGE_SELL_SIGMA + 1):
@@ -133,7 +133,7 @@ def config_matches(cfg, want):
 def heldout_matrices(limit=16, max_nnz=4_000_000):
     d = np.load(DATASET)
     names = [str(n) for n, t, z in zip(d["names"], d["test"], d["nnz"]) if t and z <= max_nnz]
-    suite = dict(W.training_suite())
+    suite = dict(W.training_suite(count=len(d["names"])))
     return [(n, suite[n]) for n in names[:limit] if n in suite]
 
 
