@@ -264,6 +264,17 @@ cp_status cp_mlp_loss_grad(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_
                            float* loss, float* grad, float* scratch);
 cp_status cp_adam_step(cp_ctx* ctx, int64_t nparams, float* params, const float* grad, float* m,
                        float* v, int32_t t, float lr, float beta1, float beta2, float eps);
+/* cp_mlp_loss_grad_soft: as cp_mlp_loss_grad with a target distribution per
+ * sample instead of a class: targets[N][k] (device FP32, each row >= 0 and
+ * summing to 1); loss = mean over the batch of logsumexp(z) - sum_c t_c z_c,
+ * whose gradient in the logits is softmax(z) - t.  One-hot rows give
+ * cp_mlp_loss_grad.  The cascade's labels come from measured SpMV times
+ * (Sec. III-B-2); soft targets spread a sample's weight over the configurations
+ * within a few percent of its fastest, so near-ties are learned as near-ties
+ * and a costly mistake costs more than a cheap one. */
+cp_status cp_mlp_loss_grad_soft(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_t h2,
+                                int32_t k, const float* params, const float* X,
+                                const float* targets, float* loss, float* grad, float* scratch);
 
 /* cp_model_train: train one stage on the GPU with the kernels above.  Host
  * inputs: raw features F[N][15] and labels[N] in [0, k); the standardisation
@@ -274,6 +285,13 @@ cp_status cp_adam_step(cp_ctx* ctx, int64_t nparams, float* params, const float*
 cp_status cp_model_train(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
                          const int32_t* labels, int32_t h1, int32_t h2, int32_t k,
                          int32_t epochs, float lr, uint64_t seed, float* final_loss);
+/* cp_model_train_soft: cp_model_train with host target distributions
+ * targets[N][k] (FP32, rows >= 0 summing to 1 within 1e-4) in place of labels,
+ * trained with cp_mlp_loss_grad_soft's loss.
+ * Errors: CP_ERR_INVALID (a row that is not a distribution), CP_ERR_CUDA. */
+cp_status cp_model_train_soft(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
+                              const float* targets, int32_t h1, int32_t h2, int32_t k,
+                              int32_t epochs, float lr, uint64_t seed, float* final_loss);
 
 /* cp_predict_stage: one cascade stage's classifier (Sec. III-B-3: one trained
  * model per stage of Fig. 5's cascade) applied to a given feature vector, with

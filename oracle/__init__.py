@@ -101,6 +101,7 @@ def lib() -> ctypes.CDLL:
             "or_mlp_nparams": (_i64, [_i64, _i64, _i64, _i64]),
             "or_mlp_forward": (None, [_i64, _i64, _i64, _i64, _i64, _p, _p, _p]),
             "or_mlp_loss_grad": (_f64, [_i64, _i64, _i64, _i64, _i64, _p, _p, _p, _p]),
+            "or_mlp_loss_grad_soft": (_f64, [_i64, _i64, _i64, _i64, _i64, _p, _p, _p, _p]),
             "or_adam_step": (None, [_i64, _p, _p, _p, _p, _i64, _f64, _f64, _f64, _f64]),
         }
         for name, (res, args) in sig.items():
@@ -386,6 +387,18 @@ def mlp_loss_grad(P, X, labels, dims):
     lab = _c(labels, np.int32)
     dP = np.empty_like(P)
     loss = lib().or_mlp_loss_grad(X.shape[0], d, h1, h2, k, _ptr(P), _ptr(X), _ptr(lab), _ptr(dP))
+    return float(loss), dP
+
+
+def mlp_loss_grad_soft(P, X, targets, dims):
+    """(mean cross-entropy against target distributions, gradient), FP64."""
+    d, h1, h2, k = dims
+    P = _c(P, np.float64)
+    X = _c(X, np.float64).reshape(-1, d)
+    Q = _c(targets, np.float64).reshape(X.shape[0], k)
+    dP = np.empty_like(P)
+    loss = lib().or_mlp_loss_grad_soft(X.shape[0], d, h1, h2, k, _ptr(P), _ptr(X), _ptr(Q),
+                                       _ptr(dP))
     return float(loss), dP
 
 

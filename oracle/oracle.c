@@ -746,6 +746,70 @@ double or_mlp_loss_grad(i64 N, i64 d, i64 h1, i64 h2, i64 k, const double* P,
   return loss / (double)N;
 }
 
+/* Mean cross-entropy with soft targets: for sample s with logits z and target
+ * distribution q = Q[s][0..k) (rows >= 0 summing to 1), the loss is
+ * logsumexp(z) - sum_c q_c z_c, and its gradient in z is softmax(z) - q (the
+ * one-hot q of a label gives or_mlp_loss_grad).  Returns the mean loss and the
+ * gradient dP of that mean, in P's layout.  Pinned: central finite differences;
+ * one-hot targets reproduce or_mlp_loss_grad; log k at zero weights for any q. */
+double or_mlp_loss_grad_soft(i64 N, i64 d, i64 h1, i64 h2, i64 k, const double* P,
+                             const double* X, const double* Q, double* dP) {
+  const double *W1 = P, *b1 = W1 + h1 * d, *W2 = b1 + h1, *b2 = W2 + h2 * h1;
+  const double *W3 = b2 + h2, *b3 = W3 + k * h2;
+  const i64 np = or_mlp_nparams(d, h1, h2, k);
+  double *dW1 = dP, *db1 = dW1 + h1 * d, *dW2 = db1 + h1, *db2 = dW2 + h2 * h1;
+  double *dW3 = db2 + h2, *db3 = dW3 + k * h2;
+  for (i64 i = 0; i < np; ++i) dP[i] = 0.0;
+  double* a1 = (double*)malloc(sizeof(double) * h1);
+  double* a2 = (double*)malloc(sizeof(double) * h2);
+  double* z = (double*)malloc(sizeof(double) * k);
+  double* g3 = (double*)malloc(sizeof(double) * k);
+  double* g2 = (double*)malloc(sizeof(double) * h2);
+  double* g1 = (double*)malloc(sizeof(double) * h1);
+  double loss = 0.0;
+  for (i64 s = 0; s < N; ++s) {
+    const double* x = X + s * d;
+    const double* q = Q + s * k;
+    layer(d, h1, W1, b1, x, a1, 1);
+    layer(h1, h2, W2, b2, a1, a2, 1);
+    layer(h2, k, W3, b3, a2, z, 0);
+    double zmax = z[0];
+    for (i64 o = 1; o < k; ++o) if (z[o] > zmax) zmax = z[o];
+    double se = 0.0;
+    for (i64 o = 0; o < k; ++o) se += exp(z[o] - zmax);
+    const double lse = zmax + log(se);
+    double qz = 0.0;
+    for (i64 o = 0; o < k; ++o) qz += q[o] * z[o];
+    loss += lse - qz;
+    /* dL/dz = softmax(z) - q, scaled by 1/N */
+    for (i64 o = 0; o < k; ++o) g3[o] = (exp(z[o] - lse) - q[o]) / (double)N;
+    for (i64 o = 0; o < k; ++o) {
+      db3[o] += g3[o];
+      for (i64 i = 0; i < h2; ++i) dW3[o * h2 + i] += g3[o] * a2[i];
+    }
+    for (i64 i = 0; i < h2; ++i) {
+      double s2 = 0.0;
+      for (i64 o = 0; o < k; ++o) s2 += W3[o * h2 + i] * g3[o];
+      g2[i] = a2[i] > 0.0 ? s2 : 0.0;
+    }
+    for (i64 o = 0; o < h2; ++o) {
+      db2[o] += g2[o];
+      for (i64 i = 0; i < h1; ++i) dW2[o * h1 + i] += g2[o] * a1[i];
+    }
+    for (i64 i = 0; i < h1; ++i) {
+      double s1 = 0.0;
+      for (i64 o = 0; o < h2; ++o) s1 += W2[o * h1 + i] * g2[o];
+      g1[i] = a1[i] > 0.0 ? s1 : 0.0;
+    }
+    for (i64 o = 0; o < h1; ++o) {
+      db1[o] += g1[o];
+      for (i64 i = 0; i < d; ++i) dW1[o * d + i] += g1[o] * x[i];
+    }
+  }
+  free(a1); free(a2); free(z); free(g3); free(g2); free(g1);
+  return loss / (double)N;
+}
+
 /* One Adam step (Kingma and Ba), step count t >= 1:
  * m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
  * P -= lr * (m / (1-b1^t)) / (sqrt(v / (1-b2^t)) + eps). */

@@ -176,6 +176,10 @@ _SIGS = {
     "cp_mlp_forward": (c_int32, [_p, c_int64, c_int32, c_int32, c_int32, c_int32, _p, _p, _p, _p]),
     "cp_mlp_loss_grad": (c_int32, [_p, c_int64, c_int32, c_int32, c_int32, c_int32, _p, _p, _p,
                                    _p, _p, _p]),
+    "cp_mlp_loss_grad_soft": (c_int32, [_p, c_int64, c_int32, c_int32, c_int32, c_int32, _p, _p,
+                                        _p, _p, _p, _p]),
+    "cp_model_train_soft": (c_int32, [_p, c_int32, c_int64, _p, _p, c_int32, c_int32, c_int32,
+                                      c_int32, c_float, c_uint64, POINTER(c_float)]),
     "cp_adam_step": (c_int32, [_p, c_int64, _p, _p, _p, _p, c_int32, c_float, c_float, c_float,
                                c_float]),
     "cp_model_load": (c_int32, [_p, c_int32, c_int32, c_int32, c_int32, _p, _p, _p]),
@@ -405,6 +409,15 @@ class Context:
                                     STAGE_CLASSES[stage], epochs, lr, seed, byref(loss)))
         return loss.value
 
+    def model_train_soft(self, stage, F, targets, h1=32, h2=32, epochs=2000, lr=3e-3, seed=1):
+        """cp_model_train_soft: train a stage on target distributions targets[N][k]."""
+        F = _np(F, np.float64).reshape(-1, 15)
+        Q = _np(targets, np.float32).reshape(F.shape[0], STAGE_CLASSES[stage])
+        loss = c_float()
+        _check(lib().cp_model_train_soft(self._h, stage, F.shape[0], _ptr(F), _ptr(Q), h1, h2,
+                                         STAGE_CLASSES[stage], epochs, lr, seed, byref(loss)))
+        return loss.value
+
     def mlp_forward(self, dims, params, X, logits, scratch):
         d, h1, h2, k = dims
         with self.ordered():
@@ -417,6 +430,13 @@ class Context:
             _check(lib().cp_mlp_loss_grad(self._h, X.shape[0], d, h1, h2, k, _ptr(params),
                                           _ptr(X), _ptr(labels), _ptr(loss), _ptr(grad),
                                           _ptr(scratch)))
+
+    def mlp_loss_grad_soft(self, dims, params, X, targets, loss, grad, scratch):
+        d, h1, h2, k = dims
+        with self.ordered():
+            _check(lib().cp_mlp_loss_grad_soft(self._h, X.shape[0], d, h1, h2, k, _ptr(params),
+                                               _ptr(X), _ptr(targets), _ptr(loss), _ptr(grad),
+                                               _ptr(scratch)))
 
     def adam_step(self, params, grad, m, v, t, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
         with self.ordered():

@@ -471,8 +471,20 @@ cp_status cp_mlp_loss_grad(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_
     CP_REQUIRE(ctx && params && X && labels && loss && grad && scratch && N >= 1, CP_ERR_INVALID,
                "bad argument");
     use_device(ctx);
-    mlp_loss_grad(ctx, N, MlpDims{d, h1, h2, k}, params, X, labels, loss, grad, scratch,
-                  ctx->main);
+    mlp_loss_grad(ctx, N, MlpDims{d, h1, h2, k}, params, X, labels, nullptr, loss, grad,
+                  scratch, ctx->main);
+  });
+}
+
+cp_status cp_mlp_loss_grad_soft(cp_ctx* ctx, int64_t N, int32_t d, int32_t h1, int32_t h2,
+                                int32_t k, const float* params, const float* X,
+                                const float* targets, float* loss, float* grad, float* scratch) {
+  return guard([&] {
+    CP_REQUIRE(ctx && params && X && targets && loss && grad && scratch && N >= 1,
+               CP_ERR_INVALID, "bad argument");
+    use_device(ctx);
+    mlp_loss_grad(ctx, N, MlpDims{d, h1, h2, k}, params, X, nullptr, targets, loss, grad,
+                  scratch, ctx->main);
   });
 }
 
@@ -522,7 +534,17 @@ cp_status cp_model_train(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
   return guard([&] {
     CP_REQUIRE(ctx && F && labels && epochs >= 0, CP_ERR_INVALID, "bad argument");
     use_device(ctx);
-    model_train(ctx, stage, N, F, labels, h1, h2, k, epochs, lr, seed, final_loss);
+    model_train(ctx, stage, N, F, labels, nullptr, h1, h2, k, epochs, lr, seed, final_loss);
+  });
+}
+
+cp_status cp_model_train_soft(cp_ctx* ctx, int32_t stage, int64_t N, const double* F,
+                              const float* targets, int32_t h1, int32_t h2, int32_t k,
+                              int32_t epochs, float lr, uint64_t seed, float* final_loss) {
+  return guard([&] {
+    CP_REQUIRE(ctx && F && targets && epochs >= 0, CP_ERR_INVALID, "bad argument");
+    use_device(ctx);
+    model_train(ctx, stage, N, F, nullptr, targets, h1, h2, k, epochs, lr, seed, final_loss);
   });
 }
 

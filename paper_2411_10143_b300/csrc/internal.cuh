@@ -392,15 +392,17 @@ struct MlpDims {
 };
 void mlp_forward(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const float* X, float* Z,
                  float* scratch, cudaStream_t s);
+// targets: class labels lab[N], or target distributions Q[N][k] (one of the two)
 void mlp_loss_grad(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const float* X,
-                   const int32_t* lab, float* loss, float* grad, float* scratch, cudaStream_t s);
+                   const int32_t* lab, const float* Q, float* loss, float* grad, float* scratch,
+                   cudaStream_t s);
 void adam_step(cp_ctx* ctx, int64_t np, float* P, const float* G, float* m, float* v, int t,
                float lr, float b1, float b2, float eps, cudaStream_t s);
 void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* params,
                    const float* mu, const float* sd, cudaStream_t s);
 void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host,
-                 const int32_t* lab_host, int h1, int h2, int k, int epochs, float lr,
-                 uint64_t seed, float* final_loss);
+                 const int32_t* lab_host, const float* q_host, int h1, int h2, int k, int epochs,
+                 float lr, uint64_t seed, float* final_loss);
 int64_t scratch_floats_api(int64_t N, int d, int h1, int h2, int k);
 
 // A batched launch's shape: threads per system and threads per row.

@@ -64,12 +64,14 @@ __global__ void k_mlp_fwd(int64_t N, MlpDims D, const float* __restrict__ P,
 }
 
 // Thread per sample: loss and the output / hidden deltas of softmax
-// cross-entropy averaged over the batch.
+// cross-entropy averaged over the batch.  The target of sample s is the class
+// lab[s] (Q = NULL), or the distribution Q[s][0..k) (soft targets, rows summing
+// to 1): loss = logsumexp(z) - sum_c Q_c z_c, dloss/dz = softmax(z) - Q.
 __global__ void k_mlp_bwd(int64_t N, MlpDims D, const float* __restrict__ P,
-                          const int32_t* __restrict__ lab, const float* __restrict__ A1,
-                          const float* __restrict__ A2, const float* __restrict__ Z,
-                          float* __restrict__ G1, float* __restrict__ G2, float* __restrict__ G3,
-                          float* __restrict__ L) {
+                          const int32_t* __restrict__ lab, const float* __restrict__ Q,
+                          const float* __restrict__ A1, const float* __restrict__ A2,
+                          const float* __restrict__ Z, float* __restrict__ G1,
+                          float* __restrict__ G2, float* __restrict__ G3, float* __restrict__ L) {
   const float* W2 = P + D.h1 * D.d + D.h1;
   const float* W3 = W2 + D.h2 * D.h1 + D.h2;
   const float invN = 1.f / (float)N;
@@ -81,10 +83,18 @@ __global__ void k_mlp_bwd(int64_t N, MlpDims D, const float* __restrict__ P,
     float se = 0.f;
     for (int o = 0; o < D.k; ++o) se += expf(z[o] - zmax);
     const float lse = zmax + logf(se);
-    const int y = lab[s];
-    L[s] = lse - z[y];
     float* g3 = G3 + s * D.k;
-    for (int o = 0; o < D.k; ++o) g3[o] = (expf(z[o] - lse) - (o == y ? 1.f : 0.f)) * invN;
+    if (Q) {
+      const float* q = Q + s * D.k;
+      float qz = 0.f;
+      for (int o = 0; o < D.k; ++o) qz = fmaf(q[o], z[o], qz);
+      L[s] = lse - qz;
+      for (int o = 0; o < D.k; ++o) g3[o] = (expf(z[o] - lse) - q[o]) * invN;
+    } else {
+      const int y = lab[s];
+      L[s] = lse - z[y];
+      for (int o = 0; o < D.k; ++o) g3[o] = (expf(z[o] - lse) - (o == y ? 1.f : 0.f)) * invN;
+    }
     const float* a2 = A2 + s * D.h2;
     float* g2 = G2 + s * D.h2;
     for (int i = 0; i < D.h2; ++i) {
@@ -268,7 +278,8 @@ void mlp_forward(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const float*
 }
 
 void mlp_loss_grad(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const float* X,
-                   const int32_t* lab, float* loss, float* grad, float* scratch, cudaStream_t s) {
+                   const int32_t* lab, const float* Q, float* loss, float* grad, float* scratch,
+                   cudaStream_t s) {
   check_dims(D);
   float* A1 = scratch;
   float* A2 = A1 + N * D.h1;
@@ -278,7 +289,7 @@ void mlp_loss_grad(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const floa
   float* G3 = G2 + N * D.h2;
   float* L = G3 + N * D.k;
   CP_LAUNCH(ctx, k_mlp_fwd, grid_small(N), 128, 0, s, N, D, P, X, A1, A2, Z);
-  CP_LAUNCH(ctx, k_mlp_bwd, grid_small(N), 128, 0, s, N, D, P, lab, A1, A2, Z, G1, G2, G3, L);
+  CP_LAUNCH(ctx, k_mlp_bwd, grid_small(N), 128, 0, s, N, D, P, lab, Q, A1, A2, Z, G1, G2, G3, L);
   CP_LAUNCH(ctx, k_mlp_grad, grid_small(D.nparams()), 128, 0, s, N, D, X, A1, A2, G1, G2, G3,
             grad);
   CP_LAUNCH(ctx, k_mlp_loss, 1, 256, 0, s, N, L, loss);
@@ -349,13 +360,29 @@ int stage_classes(cp_ctx* ctx, int stage) {
 }
 
 void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host, const int32_t* lab_host,
-                 int h1, int h2, int k, int epochs, float lr, uint64_t seed, float* final_loss) {
+                 const float* q_host, int h1, int h2, int k, int epochs, float lr, uint64_t seed,
+                 float* final_loss) {
   CP_REQUIRE(N >= 1, CP_ERR_INVALID, "no training samples");
+  CP_REQUIRE((lab_host != nullptr) != (q_host != nullptr), CP_ERR_INVALID,
+             "give either labels or target distributions");
   const MlpDims D{kFeat, h1, h2, k};
   check_dims(D);
-  for (int64_t q = 0; q < N; ++q)
-    CP_REQUIRE(lab_host[q] >= 0 && lab_host[q] < k, CP_ERR_INVALID, "label %d out of range",
-               lab_host[q]);
+  if (lab_host)
+    for (int64_t q = 0; q < N; ++q)
+      CP_REQUIRE(lab_host[q] >= 0 && lab_host[q] < k, CP_ERR_INVALID, "label %d out of range",
+                 lab_host[q]);
+  if (q_host)
+    for (int64_t q = 0; q < N; ++q) {
+      double sum = 0.0;
+      for (int o = 0; o < k; ++o) {
+        const float v = q_host[q * k + o];
+        CP_REQUIRE(v >= 0.f && std::isfinite(v), CP_ERR_INVALID, "target of sample %lld is not a "
+                   "distribution", (long long)q);
+        sum += v;
+      }
+      CP_REQUIRE(std::fabs(sum - 1.0) <= 1e-4, CP_ERR_INVALID,
+                 "targets of sample %lld sum to %g, not 1", (long long)q, sum);
+    }
   cudaStream_t s = ctx->main;
   const int64_t np = D.nparams();
   // Glorot-uniform initial weights from a splitmix64 stream, zero biases
@@ -384,7 +411,8 @@ void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host, const 
   };
   try {
     double* dF = static_cast<double*>(get(N * kFeat * 8));
-    int32_t* dL = static_cast<int32_t*>(get(N * 4));
+    int32_t* dL = lab_host ? static_cast<int32_t*>(get(N * 4)) : nullptr;
+    float* dQ = q_host ? static_cast<float*>(get(N * k * 4)) : nullptr;
     float* X = static_cast<float*>(get(N * kFeat * 4));
     float* mu = static_cast<float*>(get(kFeat * 4));
     float* sd = static_cast<float*>(get(kFeat * 4));
@@ -395,17 +423,18 @@ void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host, const 
     float* loss = static_cast<float*>(get(4));
     float* scratch = static_cast<float*>(get(scratch_floats(N, D) * 4));
     CP_CUDA(cudaMemcpyAsync(dF, F_host, N * kFeat * 8, cudaMemcpyHostToDevice, s));
-    CP_CUDA(cudaMemcpyAsync(dL, lab_host, N * 4, cudaMemcpyHostToDevice, s));
+    if (dL) CP_CUDA(cudaMemcpyAsync(dL, lab_host, N * 4, cudaMemcpyHostToDevice, s));
+    if (dQ) CP_CUDA(cudaMemcpyAsync(dQ, q_host, N * k * 4, cudaMemcpyHostToDevice, s));
     CP_CUDA(cudaMemcpyAsync(P, P0.data(), np * 4, cudaMemcpyHostToDevice, s));
     CP_CUDA(cudaMemsetAsync(M, 0, np * 4, s));
     CP_CUDA(cudaMemsetAsync(Vv, 0, np * 4, s));
     CP_LAUNCH(ctx, k_feat_stats, kFeat, 256, 0, s, N, dF, mu, sd);
     CP_LAUNCH(ctx, k_feat_standardise, grid_small(N * kFeat), 128, 0, s, N, dF, mu, sd, X);
     for (int t = 1; t <= epochs; ++t) {
-      mlp_loss_grad(ctx, N, D, P, X, dL, loss, G, scratch, s);
+      mlp_loss_grad(ctx, N, D, P, X, dL, dQ, loss, G, scratch, s);
       adam_step(ctx, np, P, G, M, Vv, t, lr, 0.9f, 0.999f, 1e-8f, s);
     }
-    mlp_loss_grad(ctx, N, D, P, X, dL, loss, G, scratch, s);
+    mlp_loss_grad(ctx, N, D, P, X, dL, dQ, loss, G, scratch, s);
     float h_loss = 0.f;
     CP_CUDA(cudaMemcpyAsync(&h_loss, loss, 4, cudaMemcpyDeviceToHost, s));
     CP_CUDA(cudaStreamSynchronize(s));

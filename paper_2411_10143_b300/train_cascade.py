@@ -8,7 +8,11 @@ library's own GPU training kernels (cp_model_train).
 
 Labelling rule: the configuration with the smallest mean time; times within 2 %
 of the best count as ties, broken toward the cheaper conversion (CSR < COO <
-HYB < SELL < ELL < DIA), then the smaller parameter.
+HYB < SELL < ELL < DIA), then the smaller parameter.  By default the classifiers
+train on soft targets instead, a distribution over each stage's classes with
+weight exp(-(t / t_best - 1) / tau), tau = 0.02 (cp_model_train_soft): near-ties
+are learned as near-ties, and a choice that costs 40 % weighs more than one that
+costs 3 %.  The labels remain for the accuracy report.
 
 Usage: python -m paper_2411_10143_b300.train_cascade [--count N] [--reps R]
 writes weights/cascade.json (and weights/dataset.npz with features, times and
@@ -205,6 +209,37 @@ def labels_from_times(times):
     return [fmt, algo, tpv, sig]
 
 
+def stage_times(times):
+    """Per-stage candidate times (FORMAT, CSR_ALGO, CSR_TPV, SELL_SIGMA), in the
+    class order of each stage; inf where a configuration was not timed."""
+    inf = float("inf")
+    csr_vec = [times.get(f"CSR-vector{t}", inf) for t in C.TPV_CLASSES]
+    sell = [times.get(f"SELL-{s}", inf) for s in C.SIGMA_CLASSES]
+    fb = format_best(times)
+    return ([fb[f] for f in range(6)],
+            [times.get("CSR-scalar", inf), min(csr_vec), times.get("CSR-merge", inf)],
+            csr_vec, sell)
+
+
+def soft_targets(times, tau):
+    """Target distributions of the four stages from one sweep: class c gets
+    weight exp(-(t_c / t_best - 1) / tau), normalised; untimed classes get 0.
+    With tau = 0.02, configurations within a few percent of the fastest share
+    the weight and one 10 % slower keeps under 1 % of it."""
+    out = []
+    for ts in stage_times(times):
+        t = np.asarray(ts, np.float64)
+        ok = np.isfinite(t)
+        w = np.zeros(len(t))
+        if ok.any():
+            best = t[ok].min()
+            w[ok] = np.exp(-(t[ok] / best - 1.0) / tau)
+        else:
+            w[:] = 1.0
+        out.append(w / w.sum())
+    return out
+
+
 def cascade_pick_time(times, pred):
     """SpMV time of the configuration the cascade picks from per-stage classes."""
     fmt, algo, tpv, sig = pred
@@ -235,11 +270,17 @@ def build_dataset(ctx, suite, reps=100, log=print):
     return np.array(F), np.array(L, np.int32), T, CV, NNZ, names
 
 
-def train_all(ctx, F, L, h=32, epochs=3000, lr=3e-3, seed=7):
+def train_all(ctx, F, L, h=32, epochs=3000, lr=3e-3, seed=7, targets=None):
+    """One classifier per stage, on the labels L, or on soft targets (a list of
+    four [N][k] arrays) when given."""
     out = {}
     for stage, name in enumerate(models.STAGE_NAMES):
-        loss = ctx.model_train(stage, F, L[:, stage], h1=h, h2=h, epochs=epochs, lr=lr,
-                               seed=seed + stage)
+        if targets is not None:
+            loss = ctx.model_train_soft(stage, F, targets[stage], h1=h, h2=h, epochs=epochs,
+                                        lr=lr, seed=seed + stage)
+        else:
+            loss = ctx.model_train(stage, F, L[:, stage], h1=h, h2=h, epochs=epochs, lr=lr,
+                                   seed=seed + stage)
         m = ctx.model_get(stage)
         out[name] = dict(dims=m["dims"], params=m["params"], mu=m["mu"], sd=m["sd"],
                          loss=loss)
@@ -303,6 +344,9 @@ def main():
     ap.add_argument("--epochs", type=int, default=3000)
     ap.add_argument("--hidden", type=int, default=32)
     ap.add_argument("--seed", type=int, default=7)
+    ap.add_argument("--tau", type=float, default=0.02,
+                    help="> 0: train on soft targets exp(-(t / t_best - 1) / tau) from the "
+                         "measured times; 0: on the arg-min labels")
     ap.add_argument("--dataset", default=None,
                     help="train on a stored dataset.npz instead of timing the suite again")
     ap.add_argument("--out", default=str(models.WEIGHTS))
@@ -315,7 +359,13 @@ def main():
         F, L, T, CV, NNZ, names = build_dataset(ctx, suite, args.reps)
         rng = np.random.default_rng(0)
         test = rng.random(len(F)) < 0.2
-    mdl = train_all(ctx, F[~test], L[~test], h=args.hidden, epochs=args.epochs, seed=args.seed)
+    targets = None
+    if args.tau > 0:
+        idx = np.flatnonzero(~test)
+        per = [soft_targets(T[i], args.tau) for i in idx]
+        targets = [np.stack([q[st] for q in per]) for st in range(4)]
+    mdl = train_all(ctx, F[~test], L[~test], h=args.hidden, epochs=args.epochs, seed=args.seed,
+                    targets=targets)
     picks = predict_classes(ctx, mdl, F)
     acc = {n: float((picks[test, i] == L[test, i]).mean()) for i, n in enumerate(models.STAGE_NAMES)}
     ev_test = evaluate([T[i] for i in np.flatnonzero(test)], picks[test])
@@ -323,6 +373,7 @@ def main():
     import torch
     meta = dict(gpu=torch.cuda.get_device_name(0), matrices=len(F), test=int(test.sum()),
                 reps=args.reps, epochs=args.epochs, hidden=args.hidden, seed=args.seed,
+                soft_tau=args.tau,
                 test_accuracy=acc, eval_test=ev_test,
                 eval_train=ev_train, losses={k: v["loss"] for k, v in mdl.items()},
                 gate=gate_figures([T[i] for i in np.flatnonzero(~test)],

@@ -77,3 +77,42 @@ def test_train_stage_learns_separable_labels(ctx):
     z = oracle.mlp_input(F, m["mu"].astype(np.float64), m["sd"].astype(np.float64))
     pred = oracle.mlp_forward(m["params"].astype(np.float64), z, m["dims"]).argmax(1)
     assert (pred == lab).mean() > 0.95
+
+
+@pytest.mark.parametrize("N", [1, 7, 300])
+def test_soft_target_loss_and_gradient_vs_oracle(ctx, N):
+    """Cross-entropy against target distributions (the cascade's training on
+    measured times): loss and gradient against the FP64 oracle, 1e-4."""
+    P, X, _ = setup(N, N + 50)
+    rng = np.random.default_rng(N)
+    Q = rng.random((N, DIMS[3])) ** 3
+    Q = (Q / Q.sum(axis=1, keepdims=True)).astype(np.float32)
+    scratch = torch.zeros(C.Context.mlp_scratch_floats(N, *DIMS), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    grad = torch.zeros(len(P), device="cuda")
+    ctx.mlp_loss_grad_soft(DIMS, dev(P), dev(X), dev(Q), loss, grad, scratch)
+    torch.cuda.synchronize()
+    ref_loss, ref_grad = oracle.mlp_loss_grad_soft(P.astype(np.float64), X.astype(np.float64),
+                                                   Q.astype(np.float64), DIMS)
+    assert loss.item() == pytest.approx(ref_loss, rel=1e-4)
+    g = grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - ref_grad) <= 1e-4 * np.linalg.norm(ref_grad)
+
+
+def test_train_stage_on_soft_targets(ctx):
+    """Soft targets concentrated on the separable label train as the labels do;
+    rows that are not distributions are rejected."""
+    rng = np.random.default_rng(6)
+    N = 600
+    F = np.exp(rng.uniform(0, 12, size=(N, 15)))
+    lab = ((np.log(F[:, 2]) > 6).astype(int) + 2 * (np.log(F[:, 7]) > 6).astype(int))
+    Q = np.full((N, 6), 0.02)
+    Q[np.arange(N), lab] = 0.9
+    ctx.model_train_soft(C.STAGE_FORMAT, F, Q, h1=32, h2=32, epochs=1500, lr=3e-3, seed=3)
+    m = ctx.model_get(C.STAGE_FORMAT)
+    z = oracle.mlp_input(F, m["mu"].astype(np.float64), m["sd"].astype(np.float64))
+    pred = oracle.mlp_forward(m["params"].astype(np.float64), z, m["dims"]).argmax(1)
+    assert (pred == lab).mean() > 0.95
+    with pytest.raises(C.CascadeError) as e:
+        ctx.model_train_soft(C.STAGE_FORMAT, F[:4], np.full((4, 6), 0.5), epochs=1)
+    assert e.value.status == C.ERR_INVALID

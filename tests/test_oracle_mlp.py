@@ -118,3 +118,59 @@ def test_mlp_input_is_increasing_in_each_feature():
     f.sort(axis=0)
     z = np.stack([oracle.mlp_input(r, mu, sd) for r in f])
     assert np.all(np.diff(z, axis=0) >= 0)
+
+
+def soft_targets(n, k, seed):
+    rng = np.random.default_rng(seed)
+    Q = rng.random((n, k)) ** 3
+    return Q / Q.sum(axis=1, keepdims=True)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_soft_gradient_central_differences(seed):
+    P = params(seed)
+    rng = np.random.default_rng(seed + 20)
+    X = rng.normal(size=(6, 15))
+    Q = soft_targets(6, DIMS[3], seed)
+    _, g = oracle.mlp_loss_grad_soft(P, X, Q, DIMS)
+    h = 1e-6
+    num = np.empty_like(P)
+    for i in range(len(P)):
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        num[i] = (oracle.mlp_loss_grad_soft(Pp, X, Q, DIMS)[0]
+                  - oracle.mlp_loss_grad_soft(Pm, X, Q, DIMS)[0]) / (2 * h)
+    assert np.allclose(g, num, rtol=1e-5, atol=1e-8)
+
+
+def test_soft_targets_one_hot_reduce_to_labels():
+    P = params(3)
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(9, 15))
+    lab = rng.integers(0, DIMS[3], 9)
+    Q = np.eye(DIMS[3])[lab]
+    l1, g1 = oracle.mlp_loss_grad(P, X, lab, DIMS)
+    l2, g2 = oracle.mlp_loss_grad_soft(P, X, Q, DIMS)
+    assert l2 == pytest.approx(l1, rel=1e-14)
+    assert np.allclose(g1, g2, rtol=1e-13, atol=1e-16)
+
+
+def test_soft_loss_at_zero_weights_is_log_k_for_any_targets():
+    """Zero weights give equal logits: logsumexp = log k + z and sum_c q_c z = z."""
+    P = np.zeros(oracle.mlp_nparams(*DIMS))
+    X = np.random.default_rng(5).normal(size=(7, 15))
+    loss, _ = oracle.mlp_loss_grad_soft(P, X, soft_targets(7, DIMS[3], 6), DIMS)
+    assert loss == pytest.approx(math.log(DIMS[3]), rel=1e-15)
+
+
+def test_soft_loss_minimum_is_the_targets_entropy():
+    """With the last layer's bias alone set to log q (one sample), softmax(z) = q,
+    the gradient in z vanishes and the loss equals the entropy of q (Gibbs)."""
+    d, h1, h2, k = DIMS
+    q = soft_targets(1, k, 8)[0]
+    P = np.zeros(oracle.mlp_nparams(*DIMS))
+    P[-k:] = np.log(q)
+    loss, g = oracle.mlp_loss_grad_soft(P, np.ones((1, d)), q.reshape(1, k), DIMS)
+    assert loss == pytest.approx(-np.sum(q * np.log(q)), rel=1e-12)
+    assert np.allclose(g[-k:], 0.0, atol=1e-15)
