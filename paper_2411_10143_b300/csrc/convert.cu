@@ -732,6 +732,9 @@ void free_formats(cp_mat* m) {
   m->merge_carry_val = nullptr;
   m->merge_start = nullptr;
   m->merge_tiles = 0;
+  if (m->merge_err) m->ctx->mapped.give(m->merge_err);
+  m->merge_err = nullptr;
+  m->merge_err_dev = nullptr;
   dfree(m->val32);
   m->val32 = nullptr;
 }
@@ -934,6 +937,11 @@ static void prepare_merge(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   m->merge_carry_val = dalloc_async<double>(tiles, s);
   m->merge_start = dalloc_async<int32_t>(tiles + 1, s);
   m->merge_tiles = tiles;
+  if (!m->merge_err) {
+    m->merge_err = static_cast<int*>(ctx->mapped.take());
+    CP_CUDA(cudaHostGetDevicePointer(reinterpret_cast<void**>(&m->merge_err_dev), m->merge_err,
+                                     0));
+  }
   merge_partition(ctx, m, s);
   CP_CUDA(cudaStreamSynchronize(s));
 }

@@ -276,6 +276,10 @@ struct cp_mat {
   double* merge_carry_val = nullptr;
   int32_t* merge_start = nullptr;  // row index where each tile's merge path starts (tiles + 1)
   int64_t merge_tiles = 0;
+  // a host-mapped word the merge-path kernel sets when a bounded wait for its
+  // tile copies gives up (host view, device view; from the context's page pool)
+  int* merge_err = nullptr;
+  int* merge_err_dev = nullptr;
   std::mutex mu;       // serialises conversions issued by the side thread and the caller
   std::mutex feat_mu;  // serialises the feature computation
 };

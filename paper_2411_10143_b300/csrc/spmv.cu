@@ -255,14 +255,69 @@ __device__ __forceinline__ void cp_async_wait_prev() {
   asm volatile("cp.async.wait_group 1;\n" ::: "memory");
 }
 
+// Bulk asynchronous copies (cp.async.bulk, the TMA engine) into shared memory,
+// completed on an mbarrier.  Both addresses 16-byte aligned, size a multiple
+// of 16 bytes.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+// Waits (bounded) until the phase with the given parity of bar has completed;
+// false if the bound ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// orders this thread's earlier generic-proxy accesses to shared memory before
+// later async-proxy (bulk copy) writes
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
 constexpr int kMergeWarps = 4;  // warps per block of the warp-tile kernel
 
 // The matrix path's merge-path kernel: warp tiles of kMergeWarpTile items,
 // each warp independent of the others (no block barrier), with the tile start
 // points computed once per matrix.  Each warp runs a two-stage pipeline over
 // its tiles: while it walks one tile out of shared memory, the copies of its
-// next tile's row ends, column indices and values (coalesced cp.async, no
-// registers) are in flight into the other half of its shared-memory slice.
+// next tile's row ends, column indices and values are in flight into the
+// other half of its shared-memory slice.  The copies are bulk copies on the
+// TMA engine (one per array, issued by one lane, 16-byte aligned windows
+// around the tile's ranges, completed on the half's mbarrier); an array whose
+// rounded window would run past its end (the matrix's last tiles) is copied
+// entry by entry with cp.async instead.  Every wait for the copies is bounded:
+// one that gives up sets *err (reported as CP_ERR_TIMEOUT at the matrix's next
+// merge-path launch) and ends the warp's work.
 // Each lane finds its split by a search in the staged row ends and takes the
 // next lane's split as its end, so it knows the non-zeros it owns (at most
 // kMergeItems, contiguous) and gathers their x entries back to back before
@@ -274,36 +329,86 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_csr_merge_warp(
     int64_t n, int64_t nnz, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
     const T* __restrict__ v, const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
     int64_t ntiles, const int32_t* __restrict__ tile_start, int32_t* __restrict__ carry_row,
-    T* __restrict__ carry_val, const int* __restrict__ skip) {
+    T* __restrict__ carry_val, const int* __restrict__ skip, int* __restrict__ err) {
   constexpr int W = kMergeWarpTile;
+  constexpr int SLOTS = W + 8;  // a tile's 16-byte aligned window of any of the arrays
   if (skip && *skip) return;
-  __shared__ int32_t s_end[kMergeWarps][2][W + 1];
-  __shared__ int32_t s_col[kMergeWarps][2][W];
-  __shared__ T s_val[kMergeWarps][2][W];
+  __shared__ __align__(16) int32_t s_end[kMergeWarps][2][SLOTS];
+  __shared__ __align__(16) int32_t s_col[kMergeWarps][2][SLOTS];
+  __shared__ __align__(16) T s_val[kMergeWarps][2][SLOTS];
+  __shared__ __align__(8) uint64_t s_bar[kMergeWarps][2];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t total = n + nnz;
-  const int32_t* row_end = rp + 1;
   const int64_t stride = (int64_t)gridDim.x * kMergeWarps;
-  // issue the copies of tile tt (bounds a0, a1) into half `h` of this warp's slice
-  auto stage = [&](int64_t tt, int h, int32_t a0, int32_t a1) {
+  constexpr int64_t VE = 16 / sizeof(T);  // values per 16 bytes
+  if (lane == 0) {
+    mbar_init(&s_bar[wid][0], 1);
+    mbar_init(&s_bar[wid][1], 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
+  // A tile's window of each array: [lo, hi) rounded out to 16 bytes.  The
+  // row-end window covers rp[i0 + 1 .. last + 1]; the column and value windows
+  // the tile's non-zeros [k0, k0 + cnt).
+  struct Win {
+    int64_t e_lo, e_hi, c_lo, c_hi, v_lo, v_hi;
+  };
+  auto window = [&](int64_t tt, int32_t a0, int32_t a1, int& cnt, int32_t& k0, int32_t& last) {
     const int64_t d0 = tt * W;
     const int len = (int)(d0 + W < total ? W : total - d0);
-    const int32_t k0 = (int32_t)(d0 - a0);
-    const int cnt = len - (a1 - a0);
-    const int32_t last = a1 < n ? a1 : (int32_t)(n - 1);
+    k0 = (int32_t)(d0 - a0);
+    cnt = len - (a1 - a0);
+    last = a1 < n ? a1 : (int32_t)(n - 1);
+    Win wn;
+    wn.e_lo = ((int64_t)a0 + 1) & ~int64_t(3);
+    wn.e_hi = ((int64_t)last + 2 + 3) & ~int64_t(3);
+    wn.c_lo = (int64_t)k0 & ~int64_t(3);
+    wn.c_hi = ((int64_t)k0 + cnt + 3) & ~int64_t(3);
+    wn.v_lo = (int64_t)k0 & ~(VE - 1);
+    wn.v_hi = ((int64_t)k0 + cnt + VE - 1) & ~(VE - 1);
+    return wn;
+  };
+  // issue the copies of tile tt (bounds a0, a1) into half h: a bulk copy per
+  // array by lane 0, or, for an array whose rounded window would run past its
+  // end (the matrix's last tiles), cp.async copies of the needed entries
+  auto stage = [&](int64_t tt, int h, int32_t a0, int32_t a1) {
+    int cnt;
+    int32_t k0, last;
+    const Win wn = window(tt, a0, a1, cnt, k0, last);
     int32_t* e = s_end[wid][h];
     int32_t* c = s_col[wid][h];
     T* w = s_val[wid][h];
-    for (int32_t r = a0 + lane; r <= last; r += 32) cp_async_4(e + (r - a0), row_end + r);
+    const bool be = wn.e_hi <= n + 1;
+    const bool bc = cnt > 0 && wn.c_hi <= nnz;
+    const bool bv = cnt > 0 && wn.v_hi <= nnz;
+    if (lane == 0) {
+      const uint32_t bytes = (be ? (uint32_t)(wn.e_hi - wn.e_lo) * 4u : 0u) +
+                             (bc ? (uint32_t)(wn.c_hi - wn.c_lo) * 4u : 0u) +
+                             (bv ? (uint32_t)(wn.v_hi - wn.v_lo) * (uint32_t)sizeof(T) : 0u);
+      fence_proxy_async();
+      mbar_arrive_expect_tx(&s_bar[wid][h], bytes);
+      if (be) bulk_g2s(e, rp + wn.e_lo, (uint32_t)(wn.e_hi - wn.e_lo) * 4u, &s_bar[wid][h]);
+      if (bc) bulk_g2s(c, ci + wn.c_lo, (uint32_t)(wn.c_hi - wn.c_lo) * 4u, &s_bar[wid][h]);
+      if (bv)
+        bulk_g2s(w, v + wn.v_lo, (uint32_t)(wn.v_hi - wn.v_lo) * (uint32_t)sizeof(T),
+                 &s_bar[wid][h]);
+    }
+    if (!be)
+      for (int32_t r = a0 + lane; r <= last; r += 32)
+        cp_async_4(e + (r + 1 - wn.e_lo), rp + r + 1);
+    if (!bc || !bv) {
 #pragma unroll
-    for (int q = 0; q < kMergeItems; ++q) {
-      const int j = lane + 32 * q;
-      if (j < cnt) {
-        cp_async_4(c + j, ci + k0 + j);
-        cp_async_t(w + j, v + k0 + j);
+      for (int q = 0; q < kMergeItems; ++q) {
+        const int j = lane + 32 * q;
+        if (j < cnt) {
+          if (!bc) cp_async_4(c + (k0 + j - wn.c_lo), ci + k0 + j);
+          if (!bv) cp_async_t(w + (k0 + j - wn.v_lo), v + k0 + j);
+        }
       }
     }
   };
+  uint32_t ph0 = 0u, ph1 = 0u;  // phase parity of each half's mbarrier
+  bool ok = true;
   int64_t t = (int64_t)blockIdx.x * kMergeWarps + wid;
   // bounds of the current tile (b0, b1) and of the next one (nb0, nb1)
   int32_t b0 = 0, b1 = 0, nb0 = 0, nb1 = 0;
@@ -318,7 +423,7 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_csr_merge_warp(
     nb1 = tile_start[t + stride + 1];
   }
   int h = 0;
-  for (; t < ntiles; t += stride, h ^= 1) {
+  for (; t < ntiles && ok; t += stride, h ^= 1) {
     const int32_t i0 = b0, i1 = b1;
     // the next tile's copies go out before this tile is walked
     if (t + stride < ntiles) stage(t + stride, h ^ 1, nb0, nb1);
@@ -329,11 +434,24 @@ __global__ void __launch_bounds__(32 * kMergeWarps) k_csr_merge_warp(
       nb0 = tile_start[t + 2 * stride];
       nb1 = tile_start[t + 2 * stride + 1];
     }
-    cp_async_wait_prev();  // this tile's group has landed (the next one may not)
+    cp_async_wait_prev();  // this tile's element copies have landed (the next ones may not)
+    ok = mbar_wait(&s_bar[wid][h], h ? ph1 : ph0);  // and its bulk copies
+    if (h) ph1 ^= 1u;
+    else ph0 ^= 1u;
     __syncwarp();
-    const int32_t* e_w = s_end[wid][h];
-    const int32_t* c_w = s_col[wid][h];
-    const T* v_w = s_val[wid][h];
+    if (!ok) {
+      // the copies did not land within the bound: record it (the host reports
+      // CP_ERR_TIMEOUT), give the other half's copies a bounded wait, and stop
+      if (lane == 0) atomicExch(err, 1);
+      if (t + stride < ntiles) (void)mbar_wait(&s_bar[wid][h ^ 1], h ? ph0 : ph1);
+      break;
+    }
+    int cnt_w;
+    int32_t k0_w, last_w;
+    const Win wn = window(t, i0, i1, cnt_w, k0_w, last_w);
+    const int32_t* e_w = s_end[wid][h] + (i0 + 1 - wn.e_lo);
+    const int32_t* c_w = s_col[wid][h] + (k0_w - wn.c_lo);
+    const T* v_w = s_val[wid][h] + (k0_w - wn.v_lo);
     const int64_t d0 = t * W;
     const int len = (int)(d0 + W < total ? W : total - d0);  // items in the tile
     const int32_t k0 = (int32_t)(d0 - i0);
@@ -804,10 +922,19 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
         return DOT ? g : 0;
       }
       if (cfg.algo == CP_ALGO_MERGE) {
+        // an earlier launch on this matrix whose bounded wait for its tile copies
+        // gave up (its y is incomplete) is reported here, at the next launch
+        if (m->merge_err && *reinterpret_cast<volatile int*>(m->merge_err)) {
+          *reinterpret_cast<volatile int*>(m->merge_err) = 0;
+          CP_REQUIRE(false, CP_ERR_TIMEOUT,
+                     "an earlier merge-path SpMV on this matrix gave up waiting for its tile "
+                     "copies; its result was incomplete");
+        }
         const int g = merge_warp_grid<T, GEN>(ctx->num_sms, m->merge_tiles);
         CP_LAUNCH(ctx, (k_csr_merge_warp<T, GEN>), g, 32 * kMergeWarps, 0, s, n, m->nnz, m->rowptr,
                   m->col, v, x, y, alpha, beta, m->merge_tiles, m->merge_start,
-                  m->merge_carry_row, reinterpret_cast<T*>(m->merge_carry_val), skip);
+                  m->merge_carry_row, reinterpret_cast<T*>(m->merge_carry_val), skip,
+                  m->merge_err_dev);
         CP_LAUNCH(ctx, k_merge_fixup<T>, grid_for(ctx, m->merge_tiles), kBlock, 0, s,
                   m->merge_tiles, m->merge_carry_row,
                   reinterpret_cast<const T*>(m->merge_carry_val), y, GEN ? alpha : T(1), skip);
