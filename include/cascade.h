@@ -191,6 +191,10 @@ cp_status cp_format_export(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32
  * y has nrows.  When beta = 0, y is not read.  Ordered on the main stream; does
  * not synchronise.  SpMV dominates CG and GMRES time (Sec. I). */
 enum { CP_DTYPE_F64 = 0, CP_DTYPE_F32 = 1 };
+/* Errors: CP_ERR_INVALID, CP_ERR_FOOTPRINT, CP_ERR_UNSUPPORTED (conversion);
+ * CP_ERR_TIMEOUT when an earlier merge-path SpMV on this matrix gave up a
+ * bounded wait for its tile copies (that call's y was incomplete; the error is
+ * reported once, at the matrix's next merge-path call). */
 cp_status cp_spmv(cp_ctx* ctx, cp_mat* mat, const cp_config* cfg, int32_t dtype,
                   double alpha, const void* x, double beta, void* y);
 
