@@ -799,12 +799,15 @@ static int balanced_grid(cp_ctx* ctx, int64_t units) {
   return (int)(g < 1 ? 1 : g > ctx->grid_stream ? ctx->grid_stream : g);
 }
 
-// ELL and HYB without a fused dot product: one trip per thread (a row pair
-// each), up to the block-partials capacity.  The extra blocks over the
-// resident grid keep more x gathers in flight from the start, which pays on
-// random-column matrices (uniform 8 per row, n 2M: 81.7 -> 72.5 us) and is
-// neutral on stencil and banded ones.  With a fused dot the resident grid
-// stays: every block of the next kernel sums one partial per SpMV block.
+// The row-parallel SpMVs without a fused dot product (CSR-scalar, CSR-vector,
+// ELL, HYB's ELL part, DIA): one trip per thread (a row, a row pair, or TPV
+// lanes' share of rows), up to the block-partials capacity.  The blocks beyond
+// the resident grid keep more loads in flight from the start: uniform 8 per row
+// (n 2M) ELL 81.7 -> 72.5 us, CSR-vector4 82.7 -> 79.6 us; banded CSR-scalar
+// 234 -> 215 us, CSR-vector4 132 -> 116 us; neutral on the stencils.  (SELL
+// keeps the resident grid: one trip each was 5-8 % slower on 3D Poisson.)
+// With a fused dot the resident grid stays: every block of the next kernel sums
+// one partial per SpMV block.
 static int wide_grid(int64_t units) {
   int64_t g = (units + kBlock - 1) / kBlock;
   if (g > kMaxPartials) g = kMaxPartials;
@@ -916,7 +919,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
     case CP_FMT_CSR: {
       const T* v = Vals<T>::csr(m);
       if (cfg.algo == CP_ALGO_VECTOR) {
-        const int g = balanced_grid(ctx, n * cfg.tpv);
+        const int g = DOT ? balanced_grid(ctx, n * cfg.tpv) : wide_grid(n * cfg.tpv);
         launch_csr_vector<T, GEN, DOT>(ctx, cfg.tpv, g, s, n, m->rowptr, m->col, v, x, y, alpha,
                                        beta, dotv, partials, skip);
         return DOT ? g : 0;
@@ -940,7 +943,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
                   reinterpret_cast<const T*>(m->merge_carry_val), y, GEN ? alpha : T(1), skip);
         break;
       }
-      const int g = balanced_grid(ctx, n);
+      const int g = DOT ? balanced_grid(ctx, n) : wide_grid(n);
       CP_LAUNCH(ctx, (k_csr_scalar<T, GEN, DOT>), g, kBlock, 0, s, n, m->rowptr, m->col, v, x, y,
                 alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;
@@ -975,7 +978,7 @@ static int spmv_dispatch(cp_ctx* ctx, cp_mat* m, const cp_config& cfg, T alpha, 
       break;
     }
     case CP_FMT_DIA: {
-      const int g = balanced_grid(ctx, (n + 1) / 2);
+      const int g = DOT ? balanced_grid(ctx, (n + 1) / 2) : wide_grid((n + 1) / 2);
       CP_LAUNCH(ctx, (k_dia<T, GEN, DOT>), g, kBlock, 0, s, n, m->ncols, (int)m->dia.ndiag,
                 m->dia.offs, Vals<T>::dia(m->dia), x, y, alpha, beta, dotv, partials, skip);
       return DOT ? g : 0;

@@ -328,12 +328,13 @@ def test_cost_aware_gate_keeps_the_default_on_a_short_solve():
     """A well-conditioned system converges in a few dozen iterations: with a
     conversion worth 100 default SpMVs and a 2x predicted speedup the gate keeps
     CSR-scalar (no conversion, no switch), and the solve is unaffected.  (n =
-    262,144: the iteration count does not grow with n here, and iterations long
-    enough that the side thread reaches the gate before the solve ends.)"""
+    1,048,576: the iteration count does not grow with n here, and the iterations
+    are long enough that the side thread reaches the gate before the solve ends;
+    at n = 262,144 the 44 iterations could end first.)"""
     c = C.Context(0)
     one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
     c.gate_set(fixed_gate())
-    A = W.diagonally_dominant(W.poisson2d(512), margin=0.5)  # a few dozen iterations
+    A = W.diagonally_dominant(W.poisson2d(1024), margin=0.5)  # a few dozen iterations
     b = rhs(A, 31)
     x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
     assert true_relres(A, x, b) <= 1e-10
