@@ -40,6 +40,8 @@ METRIC = "time-to-solution (incl. prep) vs plain CSR-CG; SpMV % HBM BW; serve p5
 GRID = 128
 TOL = 1e-10
 XSTAR_SEED = 2002
+# FP32 refinement: each inner solve to relative max(1e-5, IR_THETA tol ||b|| / ||r||)
+IR_THETA = 0.5
 
 
 def log(*a):
@@ -414,12 +416,17 @@ def comparisons(args, ctx, M, A, b, x, xs_d, stream, C):
     plain_ms, plain = timed(C.default_opts(tol=TOL, mode=C.MODE_PLAIN))
     seq_ms, seq = timed(C.default_opts(tol=TOL, mode=C.MODE_SEQUENTIAL))
     ir_ms, ir = timed(C.default_opts(tol=TOL, mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
-                                     inner_tol=1e-5))
+                                     inner_tol=1e-5, ir_theta=IR_THETA))
+    irf_ms, irf = timed(C.default_opts(tol=TOL, mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
+                                       inner_tol=1e-5, ir_theta=0.0))
     res = {
         "plain_csr_cg_ms": plain_ms, "plain_iters": plain.iters,
         "sequential_ms": seq_ms, "fp32_ir_async_ms": ir_ms,
         "fp32_ir": {"outer": ir.outer_iters, "inner": ir.iters, "relres_true": ir.relres_true,
-                    "final_cfg": repr(ir.final_cfg)},
+                    "final_cfg": repr(ir.final_cfg), "inner_tol": 1e-5, "ir_theta": IR_THETA,
+                    "every_inner_to_inner_tol": {"ms": irf_ms, "outer": irf.outer_iters,
+                                                 "inner": irf.iters,
+                                                 "relres_true": irf.relres_true}},
     }
     # end to end through host buffers: pinned CSR + b in, x out, per step
     rp = torch.as_tensor(A.rowptr).pin_memory()
@@ -529,7 +536,9 @@ def gmres_bench(ctx, reps=2):
     plain_ms, pl = timed(C.default_opts(mode=C.MODE_PLAIN, **base))
     async_ms, a = timed(C.default_opts(mode=C.MODE_ASYNC, **base))
     ir_ms, ir = timed(C.default_opts(mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
-                                     inner_tol=1e-5, **base))
+                                     inner_tol=1e-5, ir_theta=IR_THETA, **base))
+    irf_ms, irf = timed(C.default_opts(mode=C.MODE_ASYNC, precision=C.PREC_FP32_IR,
+                                       inner_tol=1e-5, ir_theta=0.0, **base))
     step_ms, st = timed(C.default_opts(mode=C.MODE_PLAIN, iteration_kernel=1, **base))
     dia = C.config("DIA")
     M.convert(dia)
@@ -545,7 +554,12 @@ def gmres_bench(ctx, reps=2):
         "async_ms": async_ms, "iters": a.iters, "final_cfg": repr(a.final_cfg),
         "relres_true": a.relres_true, "persist_iters": a.persist_iters,
         "fp32_ir_async_ms": ir_ms, "fp32_ir": {"outer": ir.outer_iters, "inner": ir.iters,
-                                               "relres_true": ir.relres_true},
+                                               "relres_true": ir.relres_true,
+                                               "inner_tol": 1e-5, "ir_theta": IR_THETA,
+                                               "every_inner_to_inner_tol": {
+                                                   "ms": irf_ms, "outer": irf.outer_iters,
+                                                   "inner": irf.iters,
+                                                   "relres_true": irf.relres_true}},
         "csr_scalar_one_launch_per_step_ms": step_ms, "one_launch_per_step_launches":
             st.n_launches,
         "persistent_dia_ms": dia_ms,

@@ -357,6 +357,13 @@ typedef struct {
                             in FP64 at m = 30), else 1; 1 = classical Gram-Schmidt
                             with a second pass (conditional in FP64, always in FP32),
                             as the one-launch-per-step kernels use               */
+  double ir_theta;       /* FP32_IR: an inner solve stops at relative inner_tol or as soon
+                            as its residual is at most ir_theta * tol * ||b||, whichever
+                            comes first: the correction need not be more accurate than
+                            what the outer target asks.  In effect each inner solve runs
+                            to relative max(inner_tol, ir_theta tol ||b|| / ||r_k||)
+                            (r_k the outer residual).  0 = always to inner_tol; default
+                            0.5; must be in [0, 1)                                  */
 } cp_solve_opts;
 
 typedef struct {
@@ -484,7 +491,8 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
  * launch shape once and updates its kernel node per batch).  One thread block
  * per system at a time, systems taken largest first from a device work queue.
  * Every system runs FP64 iterative refinement to opts->tol around FP32 inner
- * solves to opts->inner_tol: solver[i] = 0 for CG (SPD A_i), 1 for
+ * solves to opts->inner_tol (stopping early as opts->ir_theta allows):
+ * solver[i] = 0 for CG (SPD A_i), 1 for
  * GMRES(opts->restart), restart <= 32.  FP64 is kept for the outer residual,
  * the update of x and GMRES's Givens / least-squares step.  mats[i] (square,
  * CSR), b[i], x[i] (device FP64, x read as x0) are host arrays of nsys entries;
@@ -555,6 +563,7 @@ typedef struct {
                            the batch's other systems share the bandwidth, so a
                            mid-size GMRES request is served faster by the
                            full-GPU persistent solver                          */
+  double ir_theta;      /* inner-solve stop as cp_solve_opts.ir_theta (default 0.5) */
 } cp_server_opts;
 typedef struct {
   int64_t id;           /* caller's tag, returned in the result                 */

@@ -84,8 +84,8 @@ def lib() -> ctypes.CDLL:
             "or_spmv_f32": (None, [_i64, _p, _p, _p, _p, _p]),
             "or_cg": (_i64, [_i64, _p, _p, _p, _p, _p, _f64, _i64, _p, _p, _i64, _p, _p]),
             "or_gmres": (_i64, [_i64, _p, _p, _p, _p, _p, _f64, _i64, _i64, _p, _i64, _p, _p]),
-            "or_ir_solve": (_i64, [_i64, _p, _p, _p, _p, _p, _i32, _i64, _f64, _f64, _i64, _i64,
-                                   _p, _p, _p]),
+            "or_ir_solve": (_i64, [_i64, _p, _p, _p, _p, _p, _i32, _i64, _f64, _f64, _f64, _i64,
+                                   _i64, _p, _p, _p]),
             "or_features": (None, [_i64, _i64, _p, _p, _p]),
             "or_csr_to_coo": (None, [_i64, _p, _p, _p, _p, _p, _p]),
             "or_coo_to_csr": (None, [_i64, _i64, _p, _p, _p, _p, _p, _p]),
@@ -221,8 +221,9 @@ def gmres(A, b, x0=None, tol=1e-10, m=30, maxit=100000, hist_cap=0) -> SolveResu
 
 
 def ir_solve(A, b, solver="cg", m=30, tol=1e-10, inner_tol=1e-5, max_outer=50,
-             max_inner=100000) -> SolveResult:
-    """FP64 iterative refinement with FP32 CG/GMRES(m) inner solves (x0 = 0)."""
+             max_inner=100000, theta=0.5) -> SolveResult:
+    """FP64 iterative refinement with FP32 CG/GMRES(m) inner solves (x0 = 0),
+    each to relative max(inner_tol, theta tol ||b|| / ||r||)."""
     A = _as_csr(A)
     b = _c(b, np.float64)
     x = np.zeros(A.nrows)
@@ -231,7 +232,7 @@ def ir_solve(A, b, solver="cg", m=30, tol=1e-10, inner_tol=1e-5, max_outer=50,
     st = np.zeros(1, np.int32)
     outer = lib().or_ir_solve(A.nrows, _ptr(A.rowptr), _ptr(A.col), _ptr(A.val), _ptr(b),
                               _ptr(x), 0 if solver == "cg" else 1, m, tol, inner_tol,
-                              max_outer, max_inner, _ptr(inner), _ptr(rel), _ptr(st))
+                              theta, max_outer, max_inner, _ptr(inner), _ptr(rel), _ptr(st))
     return SolveResult(x=x, outer=int(outer), inner_total=int(inner[0]),
                        relres_true=float(rel[0]), status=int(st[0]))
 

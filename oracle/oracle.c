@@ -335,13 +335,16 @@ static i64 gmres_f32(i64 n, const i32* rp, const i32* ci, const float* v,
 /* Mixed-precision iterative refinement.  x0 = 0.  Loop: r = b - A x in FP64;  */
 /* stop when ||r|| <= tol ||b||; otherwise round A and r to FP32 (RN-even),    */
 /* solve A d = r in FP32 with CG (solver = 0) or GMRES(m) (solver = 1) to     */
-/* relative inner_tol, then x += (double) d.                                   */
+/* relative max(inner_tol, theta tol ||b|| / ||r||), then x += (double) d.     */
+/* (theta = 0: every inner solve to inner_tol.  theta > 0: an inner solve     */
+/* stops once its residual is theta tol ||b||, which is all the outer target  */
+/* needs of the correction.)                                                   */
 /* Returns outer iterations; *inner_total = inner steps summed.                */
 /* Pinned: the final FP64 true residual, recomputed by the definition SpMV.    */
 /* ------------------------------------------------------------------------- */
 i64 or_ir_solve(i64 n, const i32* rp, const i32* ci, const double* v,
                 const double* b, double* x, i32 solver, i64 m, double tol,
-                double inner_tol, i64 max_outer, i64 max_inner,
+                double inner_tol, double theta, i64 max_outer, i64 max_inner,
                 i64* inner_total, double* relres_true, i32* status) {
   i64 nnz = rp[n];
   float* v32 = (float*)malloc(sizeof(float) * (nnz > 0 ? nnz : 1));
@@ -362,9 +365,11 @@ i64 or_ir_solve(i64 n, const i32* rp, const i32* ci, const double* v,
     if (rn <= tol * bnorm) break;
     if (outer >= max_outer) { *status = 4; break; }
     for (i64 i = 0; i < n; ++i) r32[i] = (float)r[i];
+    double itol = inner_tol;
+    if (theta * tol * bnorm / rn > itol) itol = theta * tol * bnorm / rn;
     i64 steps = solver == 0
-        ? cg_f32(n, rp, ci, v32, r32, d32, (float)inner_tol, max_inner)
-        : gmres_f32(n, rp, ci, v32, r32, d32, (float)inner_tol, m, max_inner);
+        ? cg_f32(n, rp, ci, v32, r32, d32, (float)itol, max_inner)
+        : gmres_f32(n, rp, ci, v32, r32, d32, (float)itol, m, max_inner);
     *inner_total += steps;
     for (i64 i = 0; i < n; ++i) x[i] += (double)d32[i];
     ++outer;

@@ -74,7 +74,7 @@ class SolveOpts(Structure):
                 ("precision", c_int32), ("inner_tol", c_double), ("max_outer", c_int32),
                 ("check_every", c_int32), ("profile", c_int32), ("iteration_kernel", c_int32),
                 ("force", POINTER(Config)), ("wait_limit_ms", c_double),
-                ("persist_chunk", c_int32), ("gmres_orth", c_int32)]
+                ("persist_chunk", c_int32), ("gmres_orth", c_int32), ("ir_theta", c_double)]
 
 
 class SolveInfo(Structure):
@@ -138,7 +138,7 @@ class ServerOpts(Structure):
     _fields_ = [("tol", c_double), ("inner_tol", c_double), ("restart", c_int32),
                 ("maxit", c_int32), ("small_max_n", c_int32), ("max_batch", c_int32),
                 ("lanes", c_int32), ("mode", c_int32), ("mem_budget", c_int64),
-                ("small_max_n_gmres", c_int32)]
+                ("small_max_n_gmres", c_int32), ("ir_theta", c_double)]
 
 
 class Request(Structure):

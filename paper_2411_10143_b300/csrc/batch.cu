@@ -48,6 +48,7 @@ struct BatchOut {
 struct BatchParams {
   double tol, inner_tol;
   int max_outer, max_inner, m;
+  double theta;  // an inner solve also stops at residual theta tol ||b||
 };
 
 // ------------------------------------------------------------------ block helpers
@@ -148,7 +149,8 @@ __device__ __forceinline__ void spmv32(const BatchSys& S, const float* v, float*
 
 // ------------------------------------------------------------------ inner CG (FP32)
 template <int BT, int TPV>
-__device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, double* red) {
+__device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, double* red,
+                        double floor2 /* (theta tol ||b||)^2 */) {
   const int64_t n = S.n;
   float* r = S.w32;
   float* d = r + n;
@@ -163,7 +165,7 @@ __device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, dou
     rr = fma((double)ri, (double)ri, rr);
   }
   rr = bsum<BT>(rr, red);
-  const double stop = P.inner_tol * P.inner_tol * rr;
+  const double stop = fmax(P.inner_tol * P.inner_tol * rr, floor2);
   int it = 0;
   // Each thread accumulates its share of a dot product in FP32 (a few dozen
   // terms at most: the inner solve is FP32 throughout); the block adds the
@@ -201,7 +203,8 @@ __device__ int inner_cg(const BatchSys& S, const BatchParams& P, int budget, dou
 template <int BT, int TPV>
 __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, double* red,
                            double* Hs /*(m+1)*m*/, double* gs /*m+1*/, double* cs, double* sn,
-                           double* hv /*m+1*/, float* acc_red /*32*(BT/32)*/) {
+                           double* hv /*m+1*/, float* acc_red /*32*(BT/32)*/,
+                           double floor2 /* (theta tol ||b||)^2 */) {
   const int64_t n = S.n;
   const int m = P.m;
   float* V = S.w32;               // (m+1) columns of n
@@ -216,7 +219,7 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
     bb = fma((double)ri, (double)ri, bb);
   }
   bb = bsum<BT>(bb, red);
-  const double stop = P.inner_tol * sqrt(bb);
+  const double stop = fmax(P.inner_tol * sqrt(bb), sqrt(floor2));
   int it = 0;
   double beta = sqrt(bb);
   bool first = true;
@@ -373,9 +376,11 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
       }
       __syncthreads();
       const int budget = P.max_inner - inner;
+      const double floor2 = P.theta * P.theta * P.tol * P.tol * bb;
       int got = S.solver == 0
-                    ? inner_cg<BT, TPV>(S, P, budget, red)
-                    : inner_gmres<BT, TPV>(S, P, budget, red, Hs, gs, cs, sn, hv, acc_red);
+                    ? inner_cg<BT, TPV>(S, P, budget, red, floor2)
+                    : inner_gmres<BT, TPV>(S, P, budget, red, Hs, gs, cs, sn, hv, acc_red,
+                                           floor2);
       if (got < 0) {
         status = CP_ERR_BREAKDOWN;
         inner += -got - 1;
@@ -578,6 +583,8 @@ static void batch_prepare(cp_ctx* ctx, BatchJob& J, int nsys, cp_mat* const* mat
              "bad batch arguments");
   CP_REQUIRE(opt.restart >= 1 && opt.restart <= kBatchMaxM, CP_ERR_INVALID,
              "batched GMRES restart must be in 1..%d", kBatchMaxM);
+  CP_REQUIRE(opt.ir_theta >= 0.0 && opt.ir_theta < 1.0, CP_ERR_INVALID,
+             "ir_theta must be in [0, 1)");
   cudaStream_t s = J.s;
   cp_config csr;
   cp_config_default(&csr);
@@ -627,7 +634,7 @@ static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& 
   cudaStream_t s = J.s;
   if (J.xs) CP_CUDA(cudaMemsetAsync(J.xs, 0, J.total_rows * sizeof(double), s));
   CP_CUDA(cudaMemsetAsync(J.d_order + nsys, 0, sizeof(int), s));
-  BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart};
+  BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart, opt.ir_theta};
   return launch_batch_cfg(sc.threads, sc.tpv, ctx, J.d_sys, nsys, J.d_order, J.d_order + nsys, P,
                           J.d_out, s);
 }

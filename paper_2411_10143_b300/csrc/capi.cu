@@ -97,6 +97,7 @@ void cp_solve_opts_default(cp_solve_opts* o) {
   o->wait_limit_ms = 0.0;
   o->persist_chunk = 0;
   o->gmres_orth = 0;
+  o->ir_theta = 0.5;
 }
 
 const char* cp_last_error(void) { return g_err; }

@@ -1198,10 +1198,14 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
 // ------------------------------------------------------------------ iterative refinement
 // x0 = the caller's x.  Loop: r = b - A x in FP64 with the configuration in
 // force; stop at ||r|| <= tol ||b||; else solve A d = r in FP32 (values and r
-// rounded to nearest) to relative inner_tol, starting from d = 0, and x += d.
+// rounded to nearest), starting from d = 0, and x += d.  The inner solve runs
+// to relative max(inner_tol, theta tol ||b|| / ||r||): it stops at inner_tol,
+// or once its residual is theta tol ||b||, a correction that already brings the
+// outer residual under the target (up to FP32 rounding of A and r).
 static LoopResult run_ir(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const double* b,
-                         double* x, double tol, double inner_tol, int max_outer, int maxit,
-                         int depth, bool gmres, int mrest, double* relres, int* outer_out) {
+                         double* x, double tol, double inner_tol, double theta, int max_outer,
+                         int maxit, int depth, bool gmres, int mrest, double* relres,
+                         int* outer_out) {
   cp_mat* m = cs.m;
   const int64_t n = m->nrows;
   cudaStream_t s = ctx->main;
@@ -1243,9 +1247,10 @@ static LoopResult run_ir(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const dou
     }
     CP_LAUNCH(ctx, (k_cast<double, float>), G, kBlock, 0, s, n, r, r32);
     CP_CUDA(cudaMemsetAsync(d32, 0, n * sizeof(float), s));
-    LoopResult in = gmres ? run_gmres<float>(ctx, cs, ws, r32, d32, true, inner_tol, mrest,
+    const double itol = std::max(inner_tol, theta * tol / rel);
+    LoopResult in = gmres ? run_gmres<float>(ctx, cs, ws, r32, d32, true, itol, mrest,
                                              maxit - inner_total, depth, false, nullptr)
-                          : run_cg<float>(ctx, cs, ws, r32, d32, true, inner_tol,
+                          : run_cg<float>(ctx, cs, ws, r32, d32, true, itol,
                                           maxit - inner_total, depth, false, nullptr);
     inner_total += in.iters;
     if (in.status == CP_ERR_BREAKDOWN) {
@@ -1272,6 +1277,8 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
              "GMRES restart must be in 1..%d", kMaxRestart);
   CP_REQUIRE(opt.precision == CP_PREC_FP64 || opt.precision == CP_PREC_FP32_IR, CP_ERR_INVALID,
              "unknown precision %d", opt.precision);
+  CP_REQUIRE(opt.ir_theta >= 0.0 && opt.ir_theta < 1.0, CP_ERR_INVALID,
+             "ir_theta must be in [0, 1)");
   CP_REQUIRE(opt.mode >= CP_MODE_PLAIN && opt.mode <= CP_MODE_ASYNC, CP_ERR_INVALID,
              "unknown mode %d", opt.mode);
   CP_REQUIRE(m->nrows == m->ncols, CP_ERR_INVALID, "solvers need a square matrix");
@@ -1338,8 +1345,8 @@ void solve(cp_ctx* ctx, cp_mat* m, const double* b, double* x, const cp_solve_op
                   : run_cg<double>(ctx, cs, ws, b, x, false, opt.tol, opt.maxit, depth, true,
                                    &relres);
     } else {
-      res = run_ir(ctx, cs, ws, b, x, opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, depth,
-                   gmres, opt.restart, &relres, &outer);
+      res = run_ir(ctx, cs, ws, b, x, opt.tol, opt.inner_tol, opt.ir_theta, opt.max_outer,
+                   opt.maxit, depth, gmres, opt.restart, &relres, &outer);
     }
     CP_CUDA(cudaStreamSynchronize(ctx->main));
   } catch (...) {

@@ -78,6 +78,7 @@ static void run_job(cp_server* S, int lane, cp_server::Job& job) {
   cp_solve_opts_default(&o);
   o.tol = S->opts.tol;
   o.inner_tol = S->opts.inner_tol;
+  o.ir_theta = S->opts.ir_theta;
   o.restart = S->opts.restart > 0 ? S->opts.restart : 30;
   o.precision = CP_PREC_FP32_IR;
   o.maxit = S->opts.maxit > 0 ? S->opts.maxit : 100000;
@@ -254,6 +255,7 @@ void cp_server_opts_default(cp_server_opts* o) {
   o->lanes = 4;
   o->mem_budget = int64_t(16) << 30;
   o->mode = CP_MODE_ASYNC;
+  o->ir_theta = 0.5;
 }
 
 cp_status cp_server_create(cp_ctx* ctx, const cp_server_opts* opts, cp_server** out) {
@@ -264,7 +266,8 @@ cp_status cp_server_create(cp_ctx* ctx, const cp_server_opts* opts, cp_server** 
     cp_server_opts_default(&S->opts);
     if (opts) S->opts = *opts;
     CP_REQUIRE(S->opts.lanes >= 1 && S->opts.lanes <= 32 && S->opts.max_batch >= 1 &&
-                   S->opts.restart >= 1 && S->opts.restart <= 32 && S->opts.mem_budget > 0,
+                   S->opts.restart >= 1 && S->opts.restart <= 32 && S->opts.mem_budget > 0 &&
+                   S->opts.ir_theta >= 0.0 && S->opts.ir_theta < 1.0,
                CP_ERR_INVALID, "bad server options");
     S->parent = ctx;
     // the lanes share this process's loaded kernels: load them once, before the

@@ -127,3 +127,35 @@ def test_batch_threads_per_row_matches_oracle(tpv):
         assert info.status == 0 and rel <= 1e-10, (A.name, rel)
         assert np.linalg.norm(xh - ref.x) <= 1e-7 * np.linalg.norm(ref.x), A.name
     ctx.close()
+
+
+def test_batch_inexact_inner_stop():
+    """ir_theta in the batched kernel.  With inner solves to 1e-4 every system
+    takes three outer steps; with theta 0.5 the third inner solve stops once it
+    has brought the residual to half the target, so each system takes fewer
+    inner steps.  Every system still meets the target and the oracle's
+    solution, in the oracle's outer steps."""
+    ctx = C.Context(0)
+    sys = [(W.poisson3d(9), 0), (W.spd_powerlaw(3000, seed=3000), 0), (W.convdiff3d(9), 1),
+           (W.poisson2d(33), 0)]
+    mats = [ctx.load(A) for A, _ in sys]
+    rhs = [oracle.spmv(A, W.vector(A.nrows, q + 40)) for q, (A, _) in enumerate(sys)]
+    bs = [torch.as_tensor(b, device="cuda") for b in rhs]
+    steps = {}
+    for th in (0.0, 0.5):
+        xs = [torch.zeros(A.nrows, dtype=torch.float64, device="cuda") for A, _ in sys]
+        infos = ctx.batch_solve(mats, [s for _, s in sys], bs, xs,
+                                C.default_opts(tol=1e-10, inner_tol=1e-4, restart=30,
+                                               precision=C.PREC_FP32_IR, ir_theta=th), 256)
+        steps[th] = [info.iters for info in infos]
+        for (A, s), b, x, info in zip(sys, rhs, xs, infos):
+            xh = x.cpu().numpy()
+            rel = np.linalg.norm(b - oracle.spmv(A, xh)) / np.linalg.norm(b)
+            ref = oracle.ir_solve(A, b, solver="cg" if s == 0 else "gmres", tol=1e-10,
+                                  inner_tol=1e-4, theta=th)
+            ref64 = (oracle.cg if s == 0 else oracle.gmres)(A, b, tol=1e-10)
+            assert info.status == 0 and rel <= 1e-10, (A.name, th, rel)
+            assert np.linalg.norm(xh - ref64.x) <= 1e-7 * np.linalg.norm(ref64.x), A.name
+            assert info.outer_iters == ref.outer == 3, (A.name, th)
+    assert all(a < b for a, b in zip(steps[0.5], steps[0.0])), steps
+    ctx.close()

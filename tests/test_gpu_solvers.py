@@ -117,6 +117,39 @@ def test_fp32_inner_refinement(ctx, kind, make):
     assert ref.status == 0
 
 
+@pytest.mark.parametrize("kind,make", [("cg", lambda: W.poisson3d(16)),
+                                       ("gmres", lambda: W.convdiff3d(14)),
+                                       ("cg", lambda: W.spd_powerlaw(8000, seed=2))])
+def test_fp32_refinement_inexact_inner_stop(ctx, kind, make):
+    """ir_theta.  With inner solves to 1e-4, refinement to 1e-10 takes three
+    outer steps, the second leaving a residual near 1e-8 ||b||.  The third
+    inner solve then needs a reduction of about 1e-2, so with theta 0.5 it
+    stops long before 1e-4.  Both settings reach the target and the FP64
+    oracle's solution, in the oracle's outer steps, and theta 0.5 takes fewer
+    inner steps on both sides."""
+    A = make()
+    b = rhs(A, 7)
+    ref64 = (oracle.cg if kind == "cg" else oracle.gmres)(A, b, tol=1e-10)
+    steps = {}
+    for th in (0.0, 0.5):
+        x, info = gpu_solve(ctx, A, b, kind=kind, tol=1e-10, precision=C.PREC_FP32_IR,
+                            inner_tol=1e-4, ir_theta=th)
+        ref = oracle.ir_solve(A, b, solver=kind, tol=1e-10, inner_tol=1e-4, theta=th)
+        assert info.status == 0 and ref.status == 0
+        assert true_relres(A, x, b) <= 1e-10
+        assert np.linalg.norm(x - ref64.x) <= 1e-7 * np.linalg.norm(ref64.x)
+        assert info.outer_iters == ref.outer == 3
+        steps[th] = (info.iters, ref.inner_total)
+    assert steps[0.5][0] < steps[0.0][0] and steps[0.5][1] < steps[0.0][1]
+
+
+def test_ir_theta_out_of_range_is_rejected(ctx):
+    A = W.poisson2d(10)
+    for th in (-0.1, 1.0):
+        with pytest.raises(C.CascadeError):
+            gpu_solve(ctx, A, rhs(A, 1), precision=C.PREC_FP32_IR, ir_theta=th)
+
+
 def test_edge_cases(ctx):
     A = W.poisson2d(10)
     x, info = gpu_solve(ctx, A, np.zeros(100))

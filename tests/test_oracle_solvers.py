@@ -183,3 +183,50 @@ def test_ir_reaches_fp64_residual(solver, make):
     assert r.outer >= 2  # one FP32 inner solve cannot reach 1e-10 on its own
     ref = np.linalg.solve(D, b)
     assert np.linalg.norm(r.x - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+# The inexact inner stop: each FP32 inner solve runs to relative
+# max(inner_tol, theta tol ||b|| / ||r_k||).  On 2D Poisson 40^2 refinement to
+# 1e-10 needs three outer steps; the third starts just above the target, so
+# only its inner solve may stop early.
+def test_ir_theta_stops_only_the_last_inner_solve_early():
+    A = W.poisson2d(40)
+    b = W.vector(A.nrows, 11)
+    D = dense(A)
+    ref = np.linalg.solve(D, b)
+    full = oracle.ir_solve(A, b, tol=1e-10, inner_tol=1e-5, theta=0.0)
+    early = oracle.ir_solve(A, b, tol=1e-10, inner_tol=1e-5, theta=0.5)
+    assert full.outer == early.outer == 3
+    for r in (full, early):
+        res = np.linalg.norm(b - D @ r.x) / np.linalg.norm(b)
+        assert r.status == 0 and res <= 1e-10
+        assert np.linalg.norm(r.x - ref) <= 1e-7 * np.linalg.norm(ref)
+    # the third inner solve only has to take the residual from just above
+    # 1e-10 ||b|| to half of that: a few steps instead of a fifth of the rest
+    assert early.inner_total < full.inner_total - 50
+    # the first two outer steps need reductions below inner_tol, so theta
+    # leaves them alone: stopped after two, both runs hold the same iterate
+    two_full = oracle.ir_solve(A, b, tol=1e-10, inner_tol=1e-5, theta=0.0, max_outer=2)
+    two_early = oracle.ir_solve(A, b, tol=1e-10, inner_tol=1e-5, theta=0.5, max_outer=2)
+    assert two_full.status == two_early.status == 4
+    assert two_full.inner_total == two_early.inner_total
+    assert np.array_equal(two_full.x, two_early.x)
+
+
+@pytest.mark.parametrize("solver,make", [("cg", lambda: W.poisson2d(40)),
+                                         ("gmres", lambda: W.convdiff3d(8))])
+def test_ir_theta_monotone_and_scale_free(solver, make):
+    A = make()
+    b = W.vector(A.nrows, 11)
+    runs = [oracle.ir_solve(A, b, solver=solver, tol=1e-10, theta=t) for t in (0.0, 0.5, 0.9)]
+    D = dense(A)
+    for r in runs:
+        assert r.status == 0
+        assert np.linalg.norm(b - D @ r.x) <= 1e-10 * np.linalg.norm(b)
+    # a larger theta never asks an inner solve for more
+    assert runs[2].inner_total <= runs[1].inner_total <= runs[0].inner_total
+    # the rule is relative to ||b||: scaling b by a power of two scales every
+    # FP64 and FP32 quantity exactly, so the steps and the iterate follow
+    s = oracle.ir_solve(A, b * 1024.0, solver=solver, tol=1e-10, theta=0.5)
+    assert (s.outer, s.inner_total) == (runs[1].outer, runs[1].inner_total)
+    assert np.array_equal(s.x, runs[1].x * 1024.0)
