@@ -100,6 +100,12 @@ cp_status cp_destroy(cp_ctx* ctx);
 /* Message describing the last error of the calling thread ("" if none). */
 const char* cp_last_error(void);
 
+/* Size in bytes of a public struct of this header, for bindings that mirror
+ * them: which = 0 cp_config, 1 cp_solve_opts, 2 cp_solve_info, 3 cp_gate,
+ * 4 cp_server_opts, 5 cp_request, 6 cp_result; -1 for any other value.  Host
+ * only, needs no device. */
+int64_t cp_abi_sizeof(int32_t which);
+
 /* Number of kernels this context has launched since creation (all streams). */
 cp_status cp_ctx_launch_count(cp_ctx* ctx, int64_t* count);
 

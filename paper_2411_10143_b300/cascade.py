@@ -153,10 +153,14 @@ class Result(Structure):
 
 
 _p = c_void_p
+# the ctypes mirrors of the header's structs, in cp_abi_sizeof's order
+ABI_STRUCTS = (Config, SolveOpts, SolveInfo, Gate, ServerOpts, Request, Result)
+
 _SIGS = {
     "cp_config_default": (None, [POINTER(Config)]),
     "cp_solve_opts_default": (None, [POINTER(SolveOpts)]),
     "cp_last_error": (c_char_p, []),
+    "cp_abi_sizeof": (c_int64, [c_int32]),
     "cp_create": (c_int32, [POINTER(_p), c_int32, _p, _p]),
     "cp_destroy": (c_int32, [_p]),
     "cp_ctx_launch_count": (c_int32, [_p, POINTER(c_int64)]),
@@ -223,6 +227,12 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        for which, cls in enumerate(ABI_STRUCTS):
+            want = L.cp_abi_sizeof(which)
+            if want != ctypes.sizeof(cls):
+                raise CascadeError(ERR_INVALID, f"{cls.__name__} is {ctypes.sizeof(cls)} bytes, "
+                                                f"the library's struct {want}: rebuild or fix "
+                                                "the binding")
         _lib = L
     return _lib
 

@@ -102,6 +102,19 @@ void cp_solve_opts_default(cp_solve_opts* o) {
 
 const char* cp_last_error(void) { return g_err; }
 
+int64_t cp_abi_sizeof(int32_t which) {
+  switch (which) {
+    case 0: return (int64_t)sizeof(cp_config);
+    case 1: return (int64_t)sizeof(cp_solve_opts);
+    case 2: return (int64_t)sizeof(cp_solve_info);
+    case 3: return (int64_t)sizeof(cp_gate);
+    case 4: return (int64_t)sizeof(cp_server_opts);
+    case 5: return (int64_t)sizeof(cp_request);
+    case 6: return (int64_t)sizeof(cp_result);
+    default: return -1;
+  }
+}
+
 cp_status cp_create(cp_ctx** out, int32_t device, void* main_stream, void* side_stream) {
   return guard([&] {
     CP_REQUIRE(out, CP_ERR_INVALID, "out is NULL");

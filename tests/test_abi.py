@@ -33,3 +33,16 @@ def test_library_builds_and_exports_every_symbol():
 def test_binding_covers_every_symbol():
     from paper_2411_10143_b300 import cascade
     assert set(declared_functions()) <= set(cascade._SIGS)
+
+
+def test_binding_structs_match_the_header():
+    """Each ctypes mirror has the size of the header's struct (a field added on
+    one side only would shift every field after it)."""
+    from paper_2411_10143_b300 import build, cascade
+    lib = ctypes.CDLL(str(build.build()))
+    lib.cp_abi_sizeof.restype = ctypes.c_int64
+    lib.cp_abi_sizeof.argtypes = [ctypes.c_int32]
+    for which, cls in enumerate(cascade.ABI_STRUCTS):
+        assert lib.cp_abi_sizeof(which) == ctypes.sizeof(cls), cls.__name__
+    assert lib.cp_abi_sizeof(len(cascade.ABI_STRUCTS)) == -1
+    cascade.lib()  # the loader's own check passes
