@@ -296,8 +296,16 @@ def default_opts(**kw) -> SolveOpts:
     for k, v in kw.items():
         if k == "force":
             continue
-        setattr(o, k, v)
+        _set_field(o, k, v)
     return o
+
+
+def _set_field(o, k, v):
+    """Sets a field of a ctypes struct; an unknown name is an error rather than
+    a new Python attribute the library would never see."""
+    if k not in {f[0] for f in type(o)._fields_}:
+        raise TypeError(f"{type(o).__name__} has no field {k!r}")
+    setattr(o, k, v)
 
 
 class _Ordered:
@@ -625,7 +633,7 @@ class Server:
         o = ServerOpts()
         lib().cp_server_opts_default(byref(o))
         for k, v in opts.items():
-            setattr(o, k, v)
+            _set_field(o, k, v)
         self.opts = o
         self._h = c_void_p()
         _check(lib().cp_server_create(ctx.handle, byref(o), byref(self._h)))
