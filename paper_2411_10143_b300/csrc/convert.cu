@@ -99,6 +99,30 @@ __device__ __forceinline__ void mark_diag(unsigned* bitmap, int64_t off) {
   if (!(*(volatile unsigned*)w & bit)) atomicOr(w, bit);
 }
 
+// A thread's last kDiagCache marked offsets.  The rows of a structured matrix
+// repeat the same offsets (a stencil's rows all carry its few diagonals), so
+// most marks end on a register compare and no memory request; offsets that
+// miss go through mark_diag.
+constexpr int kDiagCache = 16;
+struct DiagCache {
+  uint32_t o[kDiagCache];
+  __device__ __forceinline__ DiagCache() {
+#pragma unroll
+    for (int k = 0; k < kDiagCache; ++k) o[k] = 0xffffffffu;
+  }
+  // off = col - row + nrows - 1 < 2^32 (nrows, ncols < 2^31)
+  __device__ __forceinline__ void mark(unsigned* bitmap, uint32_t off) {
+    bool hit = false;
+#pragma unroll
+    for (int k = 0; k < kDiagCache; ++k) hit |= o[k] == off;
+    if (hit) return;
+#pragma unroll
+    for (int k = kDiagCache - 1; k > 0; --k) o[k] = o[k - 1];
+    o[0] = off;
+    mark_diag(bitmap, off);
+  }
+};
+
 template <typename U>
 __device__ __forceinline__ U warp_sum_u(U v) {
 #pragma unroll
@@ -114,6 +138,7 @@ __global__ void __launch_bounds__(kBlock) k_features_rows(int64_t n, const int32
                                                           FeatAcc* acc) {
   unsigned long long r2 = 0, dist = 0, clus = 0;
   unsigned mx = 0, mn = UINT_MAX;
+  DiagCache dc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = rp[i], e = rp[i + 1];
@@ -125,12 +150,12 @@ __global__ void __launch_bounds__(kBlock) k_features_rows(int64_t n, const int32
     int32_t prev = ci[s];
     dist += (unsigned long long)(ci[e - 1] - prev);
     unsigned run = 1, best = 1;
-    mark_diag(bitmap, (int64_t)prev - i + (n - 1));
+    dc.mark(bitmap, (uint32_t)((int64_t)prev - i + (n - 1)));
     for (int64_t k = s + 1; k < e; ++k) {
       const int32_t c = ci[k];
       run = (c == prev + 1) ? run + 1 : 1;
       best = max(best, run);
-      mark_diag(bitmap, (int64_t)c - i + (n - 1));
+      dc.mark(bitmap, (uint32_t)((int64_t)c - i + (n - 1)));
       prev = c;
     }
     clus += best;
@@ -294,15 +319,17 @@ void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15) {
   const int64_t n = m->nrows;
   const int64_t words = (n + m->ncols - 1 + 31) / 32;
   void* scratch = nullptr;
-  const size_t bytes = sizeof(FeatAcc) + 15 * sizeof(double) + words * sizeof(unsigned);
+  unsigned* bm = nullptr;  // kept for the DIA conversion (m->diag_bm)
+  const size_t bytes = sizeof(FeatAcc) + 15 * sizeof(double);
   trace("features: start n=%lld", (long long)n);
   CP_CUDA(cudaMallocAsync(&scratch, bytes, s));
   trace("features: scratch allocated");
   FeatAcc* acc = static_cast<FeatAcc*>(scratch);
   double* f = reinterpret_cast<double*>(static_cast<char*>(scratch) + sizeof(FeatAcc));
-  unsigned* bm = reinterpret_cast<unsigned*>(f + 15);
   try {
+    bm = dalloc_async<unsigned>(words, s);
     CP_CUDA(cudaMemsetAsync(scratch, 0, bytes, s));
+    CP_CUDA(cudaMemsetAsync(bm, 0, words * sizeof(unsigned), s));
     CP_CUDA(cudaMemsetAsync(&acc->minr, 0xff, sizeof(unsigned), s));
     const int g = grid_cap(ctx, n);
     CP_LAUNCH(ctx, k_features_rows, g, kBlock, 0, s, n, m->rowptr, m->col, bm, acc);
@@ -310,13 +337,15 @@ void compute_features(cp_ctx* ctx, cp_mat* m, cudaStream_t s, double* out15) {
     CP_LAUNCH(ctx, k_popcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, acc);
     CP_LAUNCH(ctx, k_features_final, 1, 1, 0, s, n, m->ncols, m->nnz, acc, f);
     trace("features: kernels queued");
-    d2h_small(ctx, m->features, f, 15 * sizeof(double), s);
+    d2h_small(ctx, m->features, f, 15 * sizeof(double), s);  // waits for the kernels
     trace("features: done");
     CP_CUDA(cudaFreeAsync(scratch, s));
   } catch (...) {
     cudaFreeAsync(scratch, s);
+    dfree_async(bm, s);
     throw;
   }
+  if (unsigned* old = m->diag_bm.exchange(bm)) dfree_async(old, s);
   m->has_features = true;
   std::memcpy(out15, m->features, sizeof(m->features));
 }
@@ -554,9 +583,11 @@ __global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __res
 __global__ void __launch_bounds__(kBlock) k_dia_mark(int64_t n, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ ci,
                                                      unsigned* __restrict__ bm) {
+  DiagCache dc;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) mark_diag(bm, (int64_t)ci[k] - i + (n - 1));
+    for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+      dc.mark(bm, (uint32_t)((int64_t)ci[k] - i + (n - 1)));
 }
 
 __global__ void k_dia_wordcount(int64_t words, const unsigned* __restrict__ bm,
@@ -724,6 +755,7 @@ void free_formats(cp_mat* m) {
   free_ell(m->hyb_ell);
   free_coo(m->hyb_coo);
   free_dia(m->dia);
+  dfree(m->diag_bm.exchange(nullptr));
   m->has_coo = m->has_ell = m->has_sell = m->has_hyb = m->has_dia = false;
   dfree(m->merge_carry_row);
   dfree(m->merge_carry_val);
@@ -883,17 +915,22 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   const int64_t span = n + m->ncols - 1;
   const int64_t words = (span + 31) / 32;
   DiaPart d;
-  unsigned* bm = nullptr;
+  // the offsets present: the feature pass's bitmap when it ran (complete once
+  // published), else marked here
+  unsigned* const have = m->diag_bm.load();
+  unsigned* bm = have;
   int64_t *cnt = nullptr, *pos = nullptr;
   int32_t* lut = nullptr;
   try {
-    bm = dalloc_async<unsigned>(words, s);
     cnt = dalloc_async<int64_t>(words, s);
     pos = dalloc_async<int64_t>(words + 1, s);
     lut = dalloc_async<int32_t>(span, s);
     d.offs = dalloc_async<int32_t>(kDiaMax, s);
-    CP_CUDA(cudaMemsetAsync(bm, 0, words * sizeof(unsigned), s));
-    CP_LAUNCH(ctx, k_dia_mark, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, bm);
+    if (!have) {
+      bm = dalloc_async<unsigned>(words, s);
+      CP_CUDA(cudaMemsetAsync(bm, 0, words * sizeof(unsigned), s));
+      CP_LAUNCH(ctx, k_dia_mark, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, bm);
+    }
     CP_LAUNCH(ctx, k_dia_wordcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, cnt);
     exclusive_scan_i64(ctx, cnt, pos, words, s);
     CP_LAUNCH(ctx, k_dia_compact, grid_cap(ctx, words), kBlock, 0, s, n, words, bm, pos, d.offs,
@@ -909,14 +946,14 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
               d.val);
     CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
-    dfree_async(bm, s);
+    if (!have) dfree_async(bm, s);
     dfree_async(cnt, s);
     dfree_async(pos, s);
     dfree_async(lut, s);
     free_dia(d);
     throw;
   }
-  dfree_async(bm, s);
+  if (!have) dfree_async(bm, s);
   dfree_async(cnt, s);
   dfree_async(pos, s);
   dfree_async(lut, s);

@@ -271,6 +271,9 @@ struct cp_mat {
   cp::DiaPart dia;
   bool has_features = false;
   double features[15] = {0};
+  // the diagonal offsets present (bit col - row + nrows - 1), left by the
+  // feature pass for the DIA conversion; published once complete
+  std::atomic<unsigned*> diag_bm{nullptr};
   // merge-path scratch: one carry (row, value) per tile
   int32_t* merge_carry_row = nullptr;
   double* merge_carry_val = nullptr;
