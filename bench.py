@@ -691,6 +691,7 @@ def async_by_size(ctx, grids=(24, 32, 48, 64, 96, 128), reps=5, log_fn=log):
                 row["async_switch_iter"] = list(info.switch_iter)
                 row["iters"] = info.iters
                 row["final_cfg"] = repr(info.final_cfg)
+                row["gate_declined"] = info.gate_declined
         row["async_vs_sequential"] = row["sequential_ms"] / row["async_ms"]
         row["async_vs_plain"] = row["plain_ms"] / row["async_ms"]
         out[f"poisson3d_{N}"] = row

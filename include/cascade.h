@@ -478,6 +478,31 @@ cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate);
 int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t iters, double res0,
                        double res, double target, double* remaining, double* cost_spmvs);
 
+/* Speedups for the gate that follow the matrix.  speedup[f] of cp_gate is one
+ * figure per format (the median over the training matrices labelled f), while a
+ * format's gain varies with the matrix: on 3D stencils of about 10^5 rows SELL's
+ * SpMV is 1.05x CSR-scalar's, against 1.16x for the SELL-labelled matrices, and
+ * a switch made on the larger figure costs more than it saves.  With neighbours installed, the tier-one gate (features known) takes
+ * for format f the median, over the k training matrices nearest to the matrix,
+ * of their best measured SpMV speedup of f over the default kernel; the first
+ * tier keeps cp_gate's figures.
+ *
+ * cp_gate_knn_speedup (host only): that estimate.  count training matrices:
+ * z (count x 15 floats, row-major) their features standardised as the cascade's
+ * inputs are, z = (log1p(f) - mu) / sd; speedup (count x 6 floats, CP_FMT_*
+ * order, 0 where the format could not be built) their speedups.  features: the
+ * matrix's 15 Table IV features.  Nearest by Euclidean distance in z, ties to
+ * the lower index; the median of an even number of values is the mean of the
+ * middle two.  k is clamped to count.  Writes *out; errors: CP_ERR_INVALID
+ * (NULL pointer, count < 1, k < 1, fmt outside 0..5, sd <= 0). */
+cp_status cp_gate_knn_speedup(int32_t count, int32_t k, const double* mu, const double* sd,
+                              const float* z, const float* speedup, const double* features,
+                              int32_t fmt, double* out);
+/* Installs such neighbours in ctx (copied; count = 0 removes them, and the
+ * gate uses cp_gate.speedup again).  Errors: CP_ERR_INVALID. */
+cp_status cp_gate_set_neighbours(cp_ctx* ctx, int32_t count, int32_t k, const double* mu,
+                                 const double* sd, const float* z, const float* speedup);
+
 /* cp_solve_cg: CG (Sec. I) for SPD A.  b, x: device FP64 arrays of nrows
  * entries; x is read as x0 and overwritten with the solution.  info (host) may
  * be NULL.  Returns CP_OK when the true relative residual <= tol,

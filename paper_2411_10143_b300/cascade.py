@@ -134,6 +134,25 @@ def gate_decide(gate: Gate, fmt, nnz, iters, res0, res, target):
     return bool(go), rem.value, cost.value
 
 
+def _neighbours(z, speedup, mu, sd):
+    z = _np(z, np.float32).reshape(-1, 15)
+    speedup = _np(speedup, np.float32).reshape(-1, 6)
+    if len(z) != len(speedup):
+        raise ValueError("z and speedup must have one row per training matrix")
+    return z, speedup, _np(mu, np.float64).reshape(15), _np(sd, np.float64).reshape(15)
+
+
+def gate_knn_speedup(z, speedup, mu, sd, features, fmt, k=7) -> float:
+    """cp_gate_knn_speedup (host only): format fmt's median speedup over the k
+    training matrices nearest to `features` (15 Table IV features)."""
+    z, speedup, mu, sd = _neighbours(z, speedup, mu, sd)
+    f = _np(features, np.float64).reshape(15)
+    out = c_double(0.0)
+    _check(lib().cp_gate_knn_speedup(len(z), int(k), _ptr(mu), _ptr(sd), _ptr(z), _ptr(speedup),
+                                     _ptr(f), int(fmt), byref(out)))
+    return out.value
+
+
 class ServerOpts(Structure):
     _fields_ = [("tol", c_double), ("inner_tol", c_double), ("restart", c_int32),
                 ("maxit", c_int32), ("small_max_n", c_int32), ("max_batch", c_int32),
@@ -202,6 +221,9 @@ _SIGS = {
     "cp_fp64_fma_rate": (c_int32, [_p, POINTER(c_double)]),
     "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
                                  POINTER(c_double), POINTER(c_double)]),
+    "cp_gate_knn_speedup": (c_int32, [c_int32, c_int32, _p, _p, _p, _p, _p, c_int32,
+                                      POINTER(c_double)]),
+    "cp_gate_set_neighbours": (c_int32, [_p, c_int32, c_int32, _p, _p, _p, _p]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
                                 POINTER(c_int32), _p]),
     "cp_batch_schedule": (c_int32, [_p, c_int64, c_int32, POINTER(c_int32), POINTER(c_int32)]),
@@ -523,6 +545,15 @@ class Context:
     def gate_set(self, gate: "Gate"):
         """cp_gate_set: install (gate.enabled = 1) or disable the cost-aware switch."""
         _check(lib().cp_gate_set(self._h, byref(gate)))
+
+    def gate_set_neighbours(self, z=None, speedup=None, mu=None, sd=None, k=7):
+        """cp_gate_set_neighbours: per-matrix speedups for the gate (None removes them)."""
+        if z is None:
+            _check(lib().cp_gate_set_neighbours(self._h, 0, 0, None, None, None, None))
+            return
+        z, speedup, mu, sd = _neighbours(z, speedup, mu, sd)
+        _check(lib().cp_gate_set_neighbours(self._h, len(z), int(k), _ptr(mu), _ptr(sd), _ptr(z),
+                                            _ptr(speedup)))
 
     def batch_schedule(self, mean_rows, has_gmres=False):
         """(threads per system, threads per row) cp_batch_solve(threads=0) uses for

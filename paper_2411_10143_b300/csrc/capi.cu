@@ -433,6 +433,46 @@ cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate) {
   });
 }
 
+static void check_neighbours(int32_t count, int32_t k, const double* mu, const double* sd,
+                             const float* z, const float* speedup) {
+  CP_REQUIRE(count >= 1 && k >= 1, CP_ERR_INVALID, "count and k must be >= 1");
+  CP_REQUIRE(mu && sd && z && speedup, CP_ERR_INVALID, "NULL argument");
+  for (int i = 0; i < 15; ++i)
+    CP_REQUIRE(std::isfinite(mu[i]) && sd[i] > 0.0 && std::isfinite(sd[i]), CP_ERR_INVALID,
+               "mu must be finite and sd positive");
+}
+
+cp_status cp_gate_knn_speedup(int32_t count, int32_t k, const double* mu, const double* sd,
+                              const float* z, const float* speedup, const double* features,
+                              int32_t fmt, double* out) {
+  return guard([&] {
+    check_neighbours(count, k, mu, sd, z, speedup);
+    CP_REQUIRE(features && out, CP_ERR_INVALID, "NULL argument");
+    CP_REQUIRE(fmt >= 0 && fmt < CP_NUM_FMT, CP_ERR_INVALID, "fmt must be in 0..%d",
+               CP_NUM_FMT - 1);
+    *out = gate_knn_speedup(count, k, mu, sd, z, speedup, features, fmt);
+  });
+}
+
+cp_status cp_gate_set_neighbours(cp_ctx* ctx, int32_t count, int32_t k, const double* mu,
+                                 const double* sd, const float* z, const float* speedup) {
+  return guard([&] {
+    CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
+    cp_ctx::GateNeighbours nb;
+    if (count != 0) {
+      check_neighbours(count, k, mu, sd, z, speedup);
+      nb.count = count;
+      nb.k = k < count ? k : count;
+      std::memcpy(nb.mu, mu, sizeof(nb.mu));
+      std::memcpy(nb.sd, sd, sizeof(nb.sd));
+      nb.z.assign(z, z + (int64_t)count * 15);
+      nb.speedup.assign(speedup, speedup + (int64_t)count * CP_NUM_FMT);
+    }
+    std::lock_guard<std::mutex> lock(ctx->gate_mu);
+    ctx->gate_nb = std::move(nb);
+  });
+}
+
 int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t iters, double res0,
                        double res, double target, double* remaining, double* cost_spmvs) {
   if (!gate) return 1;

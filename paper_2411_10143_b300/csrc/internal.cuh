@@ -247,6 +247,14 @@ struct cp_ctx {
   void* pin_main = nullptr;
   void* pin_side = nullptr;
   cp_gate gate{};  // cost-aware switching (disabled until installed)
+  // per-matrix speedups for the gate (cp_gate_set_neighbours): the training
+  // matrices' standardised features and per-format speedups
+  struct GateNeighbours {
+    int count = 0, k = 0;
+    double mu[15] = {0}, sd[15] = {0};
+    std::vector<float> z, speedup;
+  } gate_nb;
+  std::mutex gate_mu;  // guards gate_nb (installed by the caller, read by the side thread)
   std::atomic<int> inject_side_fail{-1};  // host fault injection point (tests), -1: none
   cp::SideWorker* side_worker = nullptr;
   cp::MappedPool mapped;  // host-mapped pages reused by the solves
@@ -377,6 +385,10 @@ struct Channel {
 // stream s; publishes into ch after every stage that changes the
 // configuration.  Runs until done or ch->cancel is set.
 void run_cascade(cp_ctx* ctx, cp_mat* m, cudaStream_t s, Channel* ch);
+// the median speedup of format fmt over the k training matrices nearest to
+// features (cp_gate_knn_speedup); arguments already checked
+double gate_knn_speedup(int count, int k, const double* mu, const double* sd, const float* z,
+                        const float* speedup, const double* features, int fmt);
 // the cost-aware gate's rule (see cp_gate_decide)
 int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, double res,
                 double target, double* remaining, double* cost);

@@ -459,6 +459,28 @@ static int tpv_heuristic(const double* f) {
   return t;
 }
 
+double gate_knn_speedup(int count, int k, const double* mu, const double* sd, const float* z,
+                        const float* speedup, const double* features, int fmt) {
+  if (k > count) k = count;
+  double q[kFeat];
+  for (int i = 0; i < kFeat; ++i) q[i] = (std::log1p(std::max(features[i], 0.0)) - mu[i]) / sd[i];
+  // squared distances, then the k smallest (ties to the lower index)
+  std::vector<std::pair<double, int>> d(count);
+  for (int j = 0; j < count; ++j) {
+    double s2 = 0.0;
+    for (int i = 0; i < kFeat; ++i) {
+      const double t = (double)z[(int64_t)j * kFeat + i] - q[i];
+      s2 += t * t;
+    }
+    d[j] = {s2, j};
+  }
+  std::partial_sort(d.begin(), d.begin() + k, d.end());
+  std::vector<double> v(k);
+  for (int j = 0; j < k; ++j) v[j] = speedup[(int64_t)d[j].second * CP_NUM_FMT + fmt];
+  std::sort(v.begin(), v.end());
+  return (k & 1) ? v[k / 2] : 0.5 * (v[k / 2 - 1] + v[k / 2]);
+}
+
 int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, double res,
                 double target, double* remaining, double* cost) {
   double rem = -1.0, kappa = -1.0;
@@ -545,11 +567,24 @@ static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
     ~Idle() { c->side_gpu_idle.store(false, std::memory_order_release); }
   } idle(ch);
   double rem = -1.0, cost = -1.0;
+  // with the features known and neighbours installed, format fmt's speedup for
+  // this matrix: the median over the nearest training matrices
+  cp_gate g = ctx->gate;
+  if (fmt > 0 && m->has_features) {
+    std::lock_guard<std::mutex> lock(ctx->gate_mu);
+    const auto& nb = ctx->gate_nb;
+    if (nb.count > 0) {
+      g.speedup[fmt] = gate_knn_speedup(nb.count, nb.k, nb.mu, nb.sd, nb.z.data(),
+                                        nb.speedup.data(), m->features, fmt);
+      trace("cascade: gate speedup of format %d from %d neighbours: %.3f", fmt, nb.k,
+            g.speedup[fmt]);
+    }
+  }
   wait_progress(ch, 2, 5.0);  // two iterations of history (the GPU's own count)
   if (ch->cancel.load()) return false;
   const Progress p = progress(ch);
   const double target = ch->tol * p.bnorm;
-  int go = gate_decide(ctx->gate, fmt, m->nnz, p.iters, p.res0, p.res, target, &rem, &cost);
+  int go = gate_decide(g, fmt, m->nnz, p.iters, p.res0, p.res, target, &rem, &cost);
   ch->gate_remaining = (float)rem;
   ch->gate_cost = (float)cost;
   trace("cascade: gate (tier %d, format %d): %d iterations left, cost %.1f SpMVs -> %s", tier,
@@ -568,7 +603,7 @@ static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
     if (ch->cancel.load()) return false;
     const Progress q = progress(ch);
     if (q.iters <= k1) return false;
-    go = gate_decide(ctx->gate, fmt, m->nnz, q.iters - k1, r1, q.res, target, &rem, &cost);
+    go = gate_decide(g, fmt, m->nnz, q.iters - k1, r1, q.res, target, &rem, &cost);
     ch->gate_remaining = (float)rem;
     ch->gate_cost = (float)cost;
     trace("cascade: gate window %d..%d: %d iterations left -> %s", k1, q.iters, (int)rem,

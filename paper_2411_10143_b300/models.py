@@ -62,6 +62,10 @@ def install(ctx, models: dict) -> list:
     if models.get("_gate"):  # the cost-aware switch's figures, measured with the labels
         ctx.gate_set(C.Gate.from_dict(models["_gate"]))
         done.append("GATE")
+        nb = models["_gate"].get("neighbours")
+        if nb:  # per-matrix speedups from the nearest training matrices
+            ctx.gate_set_neighbours(nb["z"], nb["speedup"], nb["mu"], nb["sd"], nb["k"])
+            done.append("GATE_NEIGHBOURS")
     return done
 
 

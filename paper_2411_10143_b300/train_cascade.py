@@ -179,6 +179,38 @@ def gate_figures(T, CV, NNZ, L):
                 spmv_b_ms=spmv_b, feat_a_ms=feat_a, feat_b_ms=feat_b, small_rows=100_000)
 
 
+GATE_K = 7  # training matrices whose speedups the gate's per-matrix estimate takes
+
+
+def neighbour_figures(F, T, mu, sd, k=GATE_K):
+    """The gate's per-matrix speedups (cp_gate_set_neighbours): the training
+    matrices' features standardised as the cascade's inputs (log1p, then the
+    FORMAT model's mu and sd) and each format's best SpMV speedup over
+    CSR-scalar (0 where the format could not be built)."""
+    mu = np.asarray(mu, np.float64)
+    sd = np.asarray(sd, np.float64)
+    z = (np.log1p(np.maximum(np.asarray(F, np.float64), 0.0)) - mu) / sd
+    sp = []
+    for t in T:
+        fb = format_best(t)
+        sp.append([t["CSR-scalar"] / fb[f] if np.isfinite(fb[f]) else 0.0 for f in range(6)])
+    return dict(k=int(k), mu=mu.tolist(), sd=sd.tolist(),
+                z=np.round(z.astype(np.float32), 5).tolist(),
+                speedup=np.round(np.asarray(sp, np.float32), 5).tolist())
+
+
+def add_neighbours(weights: Path, dataset: Path, k=GATE_K):
+    """Adds the gate's neighbour figures to a trained weights file from its
+    stored dataset (the training split only); needs no GPU."""
+    data = json.loads(weights.read_text())
+    F, _, T, _, _, _, test = load_dataset(dataset)
+    fm = data["stages"]["FORMAT"]
+    idx = np.flatnonzero(~np.asarray(test, bool))
+    data["meta"]["gate"]["neighbours"] = neighbour_figures(
+        np.asarray(F)[idx], [T[i] for i in idx], fm["mu"], fm["sd"], k)
+    weights.write_text(json.dumps(data))
+
+
 def _argmin_tie(cands):
     """cands: list of (time, tiebreak key, label); ties within 2 % go to the smaller key."""
     best = min(t for t, _, _ in cands)
@@ -350,7 +382,12 @@ def main():
     ap.add_argument("--dataset", default=None,
                     help="train on a stored dataset.npz instead of timing the suite again")
     ap.add_argument("--out", default=str(models.WEIGHTS))
+    ap.add_argument("--neighbours-only", action="store_true",
+                    help="add the gate's neighbour figures to --out from --dataset (no GPU)")
     args = ap.parse_args()
+    if args.neighbours_only:
+        add_neighbours(Path(args.out), Path(args.dataset or Path(args.out).with_name("dataset.npz")))
+        return
     ctx = C.Context(0)
     if args.dataset:
         F, L, T, CV, NNZ, names, test = load_dataset(args.dataset)
@@ -379,6 +416,8 @@ def main():
                 gate=gate_figures([T[i] for i in np.flatnonzero(~test)],
                                   [CV[i] for i in np.flatnonzero(~test)],
                                   [NNZ[i] for i in np.flatnonzero(~test)], L[~test]))
+    meta["gate"]["neighbours"] = neighbour_figures(
+        F[~test], [T[i] for i in np.flatnonzero(~test)], mdl["FORMAT"]["mu"], mdl["FORMAT"]["sd"])
     models.save(mdl, Path(args.out), meta)
     np.savez_compressed(Path(args.out).with_name("dataset.npz"), features=F, labels=L,
                         names=np.array(names), test=test, nnz=np.array(NNZ),

@@ -80,3 +80,86 @@ def test_first_tier_uses_the_best_case_and_the_feature_cost():
     assert not go and cost == pytest.approx(15.0, rel=1e-12)
     assert rem == pytest.approx(19.0, rel=1e-9)
     assert C.gate_decide(g, -1, 10**4, 4, 1.0, r, r * rate ** 21)[0]
+
+
+# ---------------------------------------------------------------- per-matrix speedups
+# cp_gate_knn_speedup: the median of format f's speedup over the k training
+# matrices nearest to the matrix, in the cascade's standardised feature space.
+
+def _knn_case(seed=5, count=40):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(6.0, 9.0, 15)  # log1p(f) = mu + sd z stays positive: features are >= 0
+    sd = rng.uniform(0.5, 2.0, 15)
+    z = rng.standard_normal((count, 15)).astype(np.float32)
+    sp = rng.uniform(0.5, 3.0, (count, 6)).astype(np.float32)
+    return mu, sd, z, sp
+
+
+def _features_at(z_row, mu, sd):
+    """Raw features whose standardised image is z_row: log1p(f) = mu + sd z."""
+    import numpy as np
+    return np.expm1(mu + sd * np.asarray(z_row, np.float64))
+
+
+def test_knn_speedup_on_a_training_point_with_k1_is_its_own():
+    mu, sd, z, sp = _knn_case()
+    for j in (0, 7, 39):
+        f = _features_at(z[j], mu, sd)
+        for fmt in range(6):
+            got = C.gate_knn_speedup(z, sp, mu, sd, f, fmt, k=1)
+            assert got == pytest.approx(float(sp[j, fmt]), rel=1e-6)
+
+
+def test_knn_speedup_is_the_median_of_the_nearest():
+    import numpy as np
+    mu, sd, z, sp = _knn_case(seed=9)
+    rng = np.random.default_rng(1)
+    for trial in range(20):
+        q = rng.standard_normal(15) * 0.8
+        f = _features_at(q, mu, sd)
+        d = ((z.astype(np.float64) - q) ** 2).sum(axis=1)
+        for k in (1, 4, 7):
+            near = np.argsort(d, kind="stable")[:k]
+            fmt = trial % 6
+            assert C.gate_knn_speedup(z, sp, mu, sd, f, fmt, k=k) == pytest.approx(
+                float(np.median(sp[near, fmt].astype(np.float64))), rel=1e-6)
+
+
+def test_knn_speedup_ties_go_to_the_lower_index_and_k_is_clamped():
+    import numpy as np
+    mu, sd = np.zeros(15), np.ones(15)
+    z = np.zeros((3, 15), np.float32)  # three equidistant training points
+    sp = np.array([[1, 2, 2, 2, 2, 2], [1, 4, 4, 4, 4, 4], [1, 9, 9, 9, 9, 9]], np.float32)
+    f = np.zeros(15)
+    assert C.gate_knn_speedup(z, sp, mu, sd, f, 1, k=1) == 2.0
+    assert C.gate_knn_speedup(z, sp, mu, sd, f, 1, k=2) == 3.0   # mean of the middle two
+    assert C.gate_knn_speedup(z, sp, mu, sd, f, 1, k=50) == 4.0  # k clamped to 3
+
+
+def test_knn_speedup_rejects_bad_arguments():
+    import numpy as np
+    mu, sd, z, sp = _knn_case()
+    f = np.ones(15)
+    with pytest.raises(C.CascadeError):
+        C.gate_knn_speedup(z, sp, mu, sd, f, 6)
+    with pytest.raises(C.CascadeError):
+        C.gate_knn_speedup(z, sp, mu, np.zeros(15), f, 1)
+    with pytest.raises(C.CascadeError):
+        C.gate_knn_speedup(z, sp, mu, sd, f, 1, k=0)
+
+
+def test_shipped_neighbours_are_consistent():
+    """The figures in the shipped weights: one standardised feature row and six
+    speedups per training matrix, standardised with the FORMAT model's own
+    mu and sd."""
+    import json
+    import numpy as np
+    from paper_2411_10143_b300 import models
+    data = json.loads(models.WEIGHTS.read_text())
+    nb = data["meta"]["gate"]["neighbours"]
+    z, sp = np.asarray(nb["z"]), np.asarray(nb["speedup"])
+    assert z.shape[1] == 15 and sp.shape == (len(z), 6) and nb["k"] >= 1
+    assert np.allclose(nb["mu"], data["stages"]["FORMAT"]["mu"])
+    assert np.allclose(nb["sd"], data["stages"]["FORMAT"]["sd"])
+    assert (sp >= 0).all() and np.allclose(sp[:, 0] >= 1.0 - 1e-6, True)

@@ -393,6 +393,54 @@ def test_cost_aware_gate_switches_on_a_long_solve():
     c.close()
 
 
+def test_gate_neighbours_decide_with_the_matrix_own_speedup():
+    """With neighbours installed the gate takes the predicted format's speedup
+    from the training matrices nearest to this one.  The long solve above
+    switches on the global 2x; told by its neighbours that ELL gains 1 %, the
+    gate keeps CSR-scalar (about 2,000 iterations x 0.01 is below the 100-SpMV
+    conversion); told 3x, it switches; with the neighbours removed, the global
+    figure applies again."""
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    c.gate_set(fixed_gate())
+    A = W.poisson2d(512)
+    b = rhs(A, 32)
+    z = np.random.default_rng(3).standard_normal((9, 15)).astype(np.float32)
+    mu, sd = np.zeros(15), np.ones(15)
+    for s_ell, keeps in ((1.01, True), (3.0, False)):
+        sp = np.ones((9, 6), np.float32)
+        sp[:, C.FMT_ELL] = s_ell
+        c.gate_set_neighbours(z, sp, mu, sd, k=5)
+        x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+        assert true_relres(A, x, b) <= 1e-10
+        diag = (s_ell, info.gate_declined, info.gate_remaining, info.gate_cost_spmvs)
+        if keeps:
+            assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR, diag
+        else:
+            assert info.gate_declined == 0 and info.final_cfg.fmt == C.FMT_ELL, diag
+    c.gate_set_neighbours(None)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert info.gate_declined == 0 and info.final_cfg.fmt == C.FMT_ELL
+    c.close()
+
+
+def test_shipped_gate_keeps_csr_where_the_predicted_format_barely_gains():
+    """The shipped cascade picks SELL for 3D Poisson 48^3 (n 110,592), whose SpMV
+    is about 1.05x CSR-scalar's there: over the 100-odd iterations left that
+    saves less than the conversion costs, and the gate, with the shipped
+    neighbours, keeps CSR-scalar."""
+    from paper_2411_10143_b300 import models
+    c = C.Context(0)
+    assert "GATE_NEIGHBOURS" in models.load_default(c)
+    A = W.poisson3d(48)
+    b = rhs(A, 34)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert true_relres(A, x, b) <= 1e-10
+    diag = (info.gate_declined, info.gate_remaining, info.gate_cost_spmvs, repr(info.final_cfg))
+    assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR, diag
+    c.close()
+
+
 def test_two_tier_features_skip_the_feature_pass_on_a_short_small_solve():
     """Below small_rows rows the side thread first asks whether even the best
     format could pay for the O(nnz) feature pass plus a conversion; on a
