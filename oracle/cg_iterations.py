@@ -1,7 +1,7 @@
 """Run the oracle's CG to convergence on the benchmark system (3D Poisson 128^3,
 b = A x*, x* ~ U[-1, 1] seed 2002, x0 = 0, tol 1e-10) and store its iteration
-count and single-core time in cg_iterations_poisson3d_128.json, which the
-benchmark's CPU-baseline leg uses to scale its bounded samples.  Calls only the
+count and single-core time in cg_iterations_poisson3d_128.json, against which
+the full-size GPU test checks the library's iteration count.  Calls only the
 oracle and the input generators."""
 import json
 import sys
