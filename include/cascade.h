@@ -477,6 +477,16 @@ cp_status cp_gate_set(cp_ctx* ctx, const cp_gate* gate);
  * estimates (-1: unknown). */
 int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t iters, double res0,
                        double res, double target, double* remaining, double* cost_spmvs);
+/* The payback of the same rule (host only): the number of default-kernel
+ * iterations after which a switch to format fmt has saved what its conversion
+ * cost, cost_spmvs / (1 - 1/speedup) -- the break-even of cp_gate_decide's
+ * "iterations left".  HUGE_VAL when no gain is expected (speedup <= 1); 0 when
+ * the rule does not apply (gate NULL or disabled, fmt = 0 or >= 6).  fmt < 0 is
+ * the first tier's best case.  When the payback is at most four iterations and
+ * the solve is still more than 1e3 times above its target, the side thread
+ * switches without waiting for the two iterations of residual history the rule
+ * otherwise reads. */
+double cp_gate_payback(const cp_gate* gate, int32_t fmt, int64_t nnz);
 
 /* Speedups for the gate that follow the matrix.  speedup[f] of cp_gate is one
  * figure per format (the median over the training matrices labelled f), while a

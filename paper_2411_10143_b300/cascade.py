@@ -134,6 +134,12 @@ def gate_decide(gate: Gate, fmt, nnz, iters, res0, res, target):
     return bool(go), rem.value, cost.value
 
 
+def gate_payback(gate: Gate, fmt, nnz):
+    """cp_gate_payback (host only): default-kernel iterations to pay back the
+    conversion to ``fmt``."""
+    return lib().cp_gate_payback(byref(gate), int(fmt), int(nnz))
+
+
 def _neighbours(z, speedup, mu, sd):
     z = _np(z, np.float32).reshape(-1, 15)
     speedup = _np(speedup, np.float32).reshape(-1, 6)
@@ -221,6 +227,7 @@ _SIGS = {
     "cp_fp64_fma_rate": (c_int32, [_p, POINTER(c_double)]),
     "cp_gate_decide": (c_int32, [_p, c_int32, c_int64, c_int32, c_double, c_double, c_double,
                                  POINTER(c_double), POINTER(c_double)]),
+    "cp_gate_payback": (c_double, [_p, c_int32, c_int64]),
     "cp_gate_knn_speedup": (c_int32, [c_int32, c_int32, _p, _p, _p, _p, _p, c_int32,
                                       POINTER(c_double)]),
     "cp_gate_set_neighbours": (c_int32, [_p, c_int32, c_int32, _p, _p, _p, _p]),

@@ -479,6 +479,11 @@ int32_t cp_gate_decide(const cp_gate* gate, int32_t fmt, int64_t nnz, int32_t it
   return gate_decide(*gate, fmt, nnz, iters, res0, res, target, remaining, cost_spmvs);
 }
 
+double cp_gate_payback(const cp_gate* gate, int32_t fmt, int64_t nnz) {
+  if (!gate) return 0.0;
+  return gate_payback(*gate, fmt, nnz);
+}
+
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                         const double* const* b, const cp_solve_opts* opts,
                         int32_t* best_threads, int32_t* best_threads_per_row, float* ms) {

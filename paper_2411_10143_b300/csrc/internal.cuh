@@ -392,6 +392,9 @@ double gate_knn_speedup(int count, int k, const double* mu, const double* sd, co
 // the cost-aware gate's rule (see cp_gate_decide)
 int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, double res,
                 double target, double* remaining, double* cost);
+// default-kernel iterations after which switching to fmt has paid for its
+// conversion (see cp_gate_payback)
+double gate_payback(const cp_gate& g, int fmt, int64_t nnz);
 // One cascade stage's classifier on the features: returns the arg-max class,
 // or -1 when the stage has no model.
 // One cascade stage's classifier (k_mlp_infer) on a feature vector: returns the

@@ -750,11 +750,13 @@ struct ConfigSource {
 // How many one-launch-per-step iterations the host keeps queued.  A newly
 // published configuration applies only to iterations not yet queued, so while
 // the cascade may still publish, the queue holds about kQueueAheadUs of device
-// time (at least two iterations, at most depth), from the host's pace while it
+// time (at least one iteration, at most depth), from the host's pace while it
 // waits for the device (about one iteration's device time per loop).  Slow
 // default-kernel iterations (CSR-scalar on power-law rows: hundreds of us)
-// then switch within a few iterations instead of depth; otherwise the queue
-// is depth deep.
+// then switch within an iteration or two instead of depth; otherwise the
+// queue is depth deep.  With one iteration queued the device may idle for the
+// host's reaction time between iterations, which costs less than running one
+// more slow iteration after a publication.
 struct QueueLimit {
   static constexpr double kQueueAheadUs = 300.0;
   int depth, lim;
@@ -774,7 +776,7 @@ struct QueueLimit {
       const double dt = std::chrono::duration<double, std::micro>(now - last).count();
       ema_us = ema_us > 0.0 ? 0.5 * ema_us + 0.5 * dt : dt;
       const int want = (int)std::ceil(kQueueAheadUs / std::max(ema_us, 1.0));
-      lim = std::max(std::min(2, depth), std::min(depth, want));
+      lim = std::max(1, std::min(depth, want));
     }
     last = now;
     have_last = true;

@@ -481,27 +481,43 @@ double gate_knn_speedup(int count, int k, const double* mu, const double* sd, co
   return (k & 1) ? v[k / 2] : 0.5 * (v[k / 2 - 1] + v[k / 2]);
 }
 
+// The rule's two figures for format fmt (fmt < 0: the first tier's best
+// case): the conversion's cost in default-kernel SpMVs (kappa) and the SpMV
+// speedup (s).
+static void gate_terms(const cp_gate& g, int fmt, int64_t nnz, double* kappa, double* speedup) {
+  const double mnnz = (double)nnz * 1e-6;
+  const double t_spmv = g.spmv_a_ms + g.spmv_b_ms * mnnz;
+  double t_conv, s;
+  if (fmt > 0) {
+    t_conv = g.conv_a_ms[fmt] + g.conv_b_ms[fmt] * mnnz;
+    s = g.speedup[fmt];
+  } else {  // first tier: the best case over the formats, features included
+    t_conv = 1e300;
+    s = 1.0;
+    for (int f = 1; f < CP_NUM_FMT; ++f) {
+      t_conv = std::min(t_conv, g.conv_a_ms[f] + g.conv_b_ms[f] * mnnz);
+      s = std::max(s, g.speedup[f]);
+    }
+    t_conv += g.feat_a_ms + g.feat_b_ms * mnnz;
+  }
+  *kappa = t_spmv > 0.0 ? t_conv / t_spmv : 1e300;
+  *speedup = s;
+}
+
+double gate_payback(const cp_gate& g, int fmt, int64_t nnz) {
+  if (!g.enabled || fmt >= CP_NUM_FMT || fmt == 0) return 0.0;  // the rule does not apply
+  double kappa, s;
+  gate_terms(g, fmt, nnz, &kappa, &s);
+  return s > 1.0 ? kappa / (1.0 - 1.0 / s) : HUGE_VAL;
+}
+
 int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, double res,
                 double target, double* remaining, double* cost) {
   double rem = -1.0, kappa = -1.0;
   int go = 1;
   if (g.enabled && fmt < CP_NUM_FMT && fmt != 0) {
-    const double mnnz = (double)nnz * 1e-6;
-    const double t_spmv = g.spmv_a_ms + g.spmv_b_ms * mnnz;
-    double t_conv, s;
-    if (fmt > 0) {
-      t_conv = g.conv_a_ms[fmt] + g.conv_b_ms[fmt] * mnnz;
-      s = g.speedup[fmt];
-    } else {  // first tier: the best case over the formats, features included
-      t_conv = 1e300;
-      s = 1.0;
-      for (int f = 1; f < CP_NUM_FMT; ++f) {
-        t_conv = std::min(t_conv, g.conv_a_ms[f] + g.conv_b_ms[f] * mnnz);
-        s = std::max(s, g.speedup[f]);
-      }
-      t_conv += g.feat_a_ms + g.feat_b_ms * mnnz;
-    }
-    kappa = t_spmv > 0.0 ? t_conv / t_spmv : 1e300;
+    double s;
+    gate_terms(g, fmt, nnz, &kappa, &s);
     if (!(s > 1.0)) {
       go = 0;  // no gain expected from the format
     } else if (iters >= 2 && res0 > 0.0 && res > 0.0 && target > 0.0) {
@@ -524,6 +540,8 @@ int gate_decide(const cp_gate& g, int fmt, int64_t nnz, int iters, double res0, 
 
 constexpr int kGateWindow = 8;  // first window over which a "keep" verdict is re-examined
 constexpr int kGateRounds = 6;  // windows at most (8, 16, ... iterations)
+constexpr double kGateQuick = 4.0;          // payback (iterations) that needs no history
+constexpr double kGateQuickMargin = 1e3;    // residual over its target for the quick go
 
 // The solve's progress as its GPU has written it: iterations done (-1: not
 // started), latest and initial residual norm, ||b||.
@@ -560,12 +578,6 @@ static void wait_progress(Channel* ch, int iters, double max_ms) {
 // true to go on; records the estimates in ch; sets ch->gate_declined to `tier`
 // while keeping.
 static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
-  // only host waits follow until the verdict: the solve may use the whole GPU
-  struct Idle {
-    Channel* c;
-    explicit Idle(Channel* ch) : c(ch) { c->side_gpu_idle.store(true, std::memory_order_release); }
-    ~Idle() { c->side_gpu_idle.store(false, std::memory_order_release); }
-  } idle(ch);
   double rem = -1.0, cost = -1.0;
   // with the features known and neighbours installed, format fmt's speedup for
   // this matrix: the median over the nearest training matrices
@@ -578,6 +590,23 @@ static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
                                         nb.speedup.data(), m->features, fmt);
       trace("cascade: gate speedup of format %d from %d neighbours: %.3f", fmt, nb.k,
             g.speedup[fmt]);
+    }
+  }
+  // A switch that pays for itself within kGateQuick default iterations is
+  // taken without waiting for history: a solve to the tolerance asked for
+  // that ends sooner than that (residual still above kGateQuickMargin x its
+  // target) is rare, and a wrong "go" then costs at most about the conversion.
+  const double payback = gate_payback(g, fmt, m->nnz);
+  {
+    const Progress p0 = progress(ch);
+    const double target0 = ch->tol * p0.bnorm;
+    if (payback <= kGateQuick && (p0.iters < 0 || p0.res > kGateQuickMargin * target0)) {
+      gate_decide(g, fmt, m->nnz, 0, 0.0, 0.0, 0.0, &rem, &cost);
+      ch->gate_remaining = (float)rem;
+      ch->gate_cost = (float)cost;
+      trace("cascade: gate (tier %d, format %d): pays back within %.1f iterations -> go", tier,
+            fmt, payback);
+      return true;
     }
   }
   wait_progress(ch, 2, 5.0);  // two iterations of history (the GPU's own count)
@@ -595,6 +624,13 @@ static bool gate_pass(cp_ctx* ctx, cp_mat* m, Channel* ch, int fmt, int tier) {
   // while the estimate of the iterations left keeps growing (by more than a
   // quarter per window); a steady estimate makes it final
   ch->gate_declined = tier;
+  // only host waits follow until the verdict: the solve may use the whole GPU
+  // (the persistent kernel), and is asked to return if the verdict turns to go
+  struct Idle {
+    Channel* c;
+    explicit Idle(Channel* ch) : c(ch) { c->side_gpu_idle.store(true, std::memory_order_release); }
+    ~Idle() { c->side_gpu_idle.store(false, std::memory_order_release); }
+  } idle(ch);
   int k1 = p.iters;
   double r1 = p.res, est = rem;
   int w = std::max(kGateWindow, k1);

@@ -163,3 +163,33 @@ def test_shipped_neighbours_are_consistent():
     assert np.allclose(nb["mu"], data["stages"]["FORMAT"]["mu"])
     assert np.allclose(nb["sd"], data["stages"]["FORMAT"]["sd"])
     assert (sp >= 0).all() and np.allclose(sp[:, 0] >= 1.0 - 1e-6, True)
+
+
+def test_payback_is_the_break_even_of_the_rule():
+    # cost 100 SpMVs at speedup 1.5 (1/3 SpMV saved an iteration): 300 iterations
+    g = gate(speedup=1.5)
+    pb = C.gate_payback(g, C.FMT_HYB, 10**6)
+    assert pb == pytest.approx(300.0, rel=1e-12)
+    # the rule switches just above the payback and keeps just below it
+    rate = 0.9
+    r = rate ** 10
+    assert C.gate_decide(g, C.FMT_HYB, 10**6, 10, 1.0, r, r * rate ** (pb * 1.01))[0]
+    assert not C.gate_decide(g, C.FMT_HYB, 10**6, 10, 1.0, r, r * rate ** (pb * 0.99))[0]
+    # a 16x format with a 2.5-SpMV conversion pays back within 2.67 iterations
+    g16 = C.Gate.from_dict({"speedup": [1.0] + [16.0] * 5, "conv_a_ms": [0.0] + [0.125] * 5,
+                            "conv_b_ms": [0.0] * 6, "spmv_a_ms": 0.05, "spmv_b_ms": 0.0})
+    assert C.gate_payback(g16, C.FMT_HYB, 10**6) == pytest.approx(2.5 / (1 - 1 / 16), rel=1e-12)
+
+
+def test_payback_without_gain_or_without_the_rule():
+    assert C.gate_payback(gate(speedup=1.0), C.FMT_ELL, 10**6) == math.inf
+    assert C.gate_payback(gate(enabled=False), C.FMT_ELL, 10**6) == 0.0
+    assert C.gate_payback(gate(), C.FMT_CSR, 10**6) == 0.0
+
+
+def test_first_tier_payback_takes_the_best_case_and_the_features():
+    g = C.Gate.from_dict({"speedup": [1.0, 1.2, 3.0, 1.1, 1.1, 1.1],
+                          "conv_a_ms": [0.0, 1.0, 4.0, 0.5, 2.0, 2.0], "conv_b_ms": [0.0] * 6,
+                          "spmv_a_ms": 0.1, "spmv_b_ms": 0.0, "feat_a_ms": 0.5, "feat_b_ms": 0.0})
+    # best speedup 3 (1/3 kept), cheapest conversion 0.5 ms + features 0.5 ms = 10 SpMVs
+    assert C.gate_payback(g, -1, 10**6) == pytest.approx(10.0 / (1 - 1 / 3), rel=1e-12)
