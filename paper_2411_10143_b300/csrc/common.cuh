@@ -178,9 +178,24 @@ __device__ __forceinline__ double partials_sum0(const double* __restrict__ parti
 // Sum of P block partials written by other blocks of the same kernel, by one
 // warp (lane l adds partials l, l + 32, ... in order, then a fixed shuffle
 // tree): every lane holds the same value, and every block gets the same bits.
+// Up to 32 * kPartialsPerLane partials (one per SM of a persistent grid), a
+// lane issues all of its loads before its first add, so the sum waits for one
+// L2 round trip rather than one per load; the order of the adds is the same.
+constexpr int kPartialsPerLane = 5;
 __device__ __forceinline__ double warp_partials_cg(const double* __restrict__ partials, int P) {
+  const int lane = threadIdx.x & 31;
   double s = 0.0;
-  for (int i = threadIdx.x & 31; i < P; i += 32) s += __ldcg(partials + i);
+  if (P <= 32 * kPartialsPerLane) {
+    double v[kPartialsPerLane];
+#pragma unroll
+    for (int k = 0; k < kPartialsPerLane; ++k)
+      v[k] = lane + 32 * k < P ? __ldcg(partials + lane + 32 * k) : 0.0;
+#pragma unroll
+    for (int k = 0; k < kPartialsPerLane; ++k)
+      if (lane + 32 * k < P) s += v[k];
+  } else {
+    for (int i = lane; i < P; i += 32) s += __ldcg(partials + i);
+  }
   return warp_sum(s);
 }
 
