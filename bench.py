@@ -816,14 +816,28 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     tuned = []
     for _ in range(3 if len(small) >= 32 else 0):
         grp = [small[i] for i in rng.choice(len(small), 32, replace=False)]
+        bopts = C.default_opts(tol=TOL, inner_tol=1e-5, restart=30, precision=C.PREC_FP32_IR)
         best, ms = ctx.batch_tune([g[2] for g in grp], [g[3] for g in grp], [g[4] for g in grp],
-                                  C.default_opts(tol=TOL, inner_tol=1e-5, restart=30,
-                                                 precision=C.PREC_FP32_IR))
+                                  bopts)
+        # the same batch at the tuned block size with every system's threads per
+        # row from the BATCH_TPR classifier (the server's default), launch time
+        # as the tuner measures it (median of three after one warm-up)
+        per = []
+        for _ in range(4):
+            xs = [torch.zeros(g[1].nrows, dtype=torch.float64, device="cuda") for g in grp]
+            infos = ctx.batch_solve([g[2] for g in grp], [g[3] for g in grp],
+                                    [g[4] for g in grp], xs, bopts, best[0], 0)
+            per.append(infos[0].t_total_ms)
+        picks = [ctx.batch_tpr(g[2]) for g in grp]
         tuned.append({"mean_rows": int(np.mean([g[1].nrows for g in grp])),
                       "gmres": any(g[3] for g in grp), "threads": best[0],
                       "threads_per_row": best[1],
-                      "ms": {f"{t}x{r}": round(v, 3) for (t, r), v in ms.items()}})
-    log_fn(f"serve: batch autotuner picks {[(t['threads'], t['threads_per_row']) for t in tuned]}")
+                      "ms": {f"{t}x{r}": round(v, 3) for (t, r), v in ms.items()},
+                      "per_system_classifier_ms": round(float(np.median(per[1:])), 3),
+                      "per_system_threads_per_row": {str(r): picks.count(r) for r in (1, 4, 16)}})
+    log_fn(f"serve: batch autotuner picks {[(t['threads'], t['threads_per_row']) for t in tuned]}, "
+           f"tuned {[round(min(t['ms'].values()), 2) for t in tuned]} ms, per-system classifier "
+           f"{[t['per_system_classifier_ms'] for t in tuned]} ms")
     # sequential service rate on a sample
     srv = C.Server(ctx, lanes=1)
     sample = items[: min(24, len(items))]

@@ -242,11 +242,16 @@ cp_status cp_spmv_csr_merge_noalloc(int64_t nrows, int64_t ncols, int64_t nnz,
  *   CP_STAGE_CSR_ALGO   k = 3: scalar, vector, merge      (used if FORMAT = CSR)
  *   CP_STAGE_CSR_TPV    k = 5: TpV 2, 4, 8, 16, 32        (used if ALGO = vector)
  *   CP_STAGE_SELL_SIGMA k = 4: sigma 1, 32, 1024, 8192    (used if FORMAT = SELL)
+ * and one classifier outside the cascade, for the batched solve (the batching
+ * pattern; the paper has no counterpart), trained on labels that the batching
+ * autotuner (cp_batch_tune) measures:
+ *   CP_STAGE_BATCH_TPR  k = 3: threads per row 1, 4, 16 of a system in
+ *                       cp_batch_solve's kernel
  * Flat parameter layout (FP32): W1[h1][d], b1[h1], W2[h2][h1], b2[h2],
  * W3[k][h2], b3[k].  d = 15, h1, h2 <= 64. */
 enum {
   CP_STAGE_FORMAT = 0, CP_STAGE_CSR_ALGO = 1, CP_STAGE_CSR_TPV = 2, CP_STAGE_SELL_SIGMA = 3,
-  CP_NUM_STAGES = 4
+  CP_STAGE_BATCH_TPR = 4, CP_NUM_STAGES = 5
 };
 /* Install the weights of one stage (host arrays, copied).  Without a model a
  * stage keeps the current choice (plain CSR is the fallback). */
@@ -542,10 +547,14 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
  *    the batch's class (the autotuner's choice, see cp_batch_tune, else a rule
  *    on the mean system size with a thread per row);
  *  - threads_per_row: 1 (CSR-scalar rows), 4 or 16 (groups of lanes share a
- *    row and add with shuffles, for long rows); 0 = the class's schedule when
- *    threads = 0, else 1.
+ *    row and add with shuffles, for long rows), for every system; 0 = each
+ *    system its own: the CP_STAGE_BATCH_TPR classifier's pick for its matrix
+ *    when that stage has a model (see cp_batch_tpr), else the class's
+ *    schedule when threads = 0, else 1.
  * infos (host array of nsys, may be NULL) receives per-system iterations,
- * relres_true, status.  Returns the first non-OK system status, else CP_OK.
+ * relres_true, status, and in t_total_ms the device time of the whole batched
+ * launch (the same for every system).  Returns the first non-OK system status,
+ * else CP_OK.
  * (The batching pattern; the paper's solver handles one system at a time.) */
 cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                          const double* const* b, double* const* x, const cp_solve_opts* opts,
@@ -567,6 +576,13 @@ cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const i
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                         const double* const* b, const cp_solve_opts* opts,
                         int32_t* best_threads, int32_t* best_threads_per_row, float* ms);
+/* cp_batch_tpr: the threads per row cp_batch_solve(threads_per_row = 0) gives
+ * the systems of matrix m when the CP_STAGE_BATCH_TPR stage has a model: the
+ * classifier's pick on m's Table IV features (computed on the main stream if m
+ * has none yet), kept with m for later batches.  *tpr (host int32) receives 1,
+ * 4 or 16, or 0 when the stage has no model.  Synchronises the main stream the
+ * first time for m.  Errors: CP_ERR_INVALID (NULL argument). */
+cp_status cp_batch_tpr(cp_ctx* ctx, cp_mat* m, int32_t* tpr);
 /* The launch shape cp_batch_solve(threads = 0) uses for a batch with mean_rows
  * rows per system (has_gmres: the batch holds a GMRES system): the tuned shape
  * of that class, else 128 / 256 / 512 / 1024 threads for mean rows below

@@ -30,8 +30,9 @@ ALGO_SCALAR, ALGO_VECTOR, ALGO_MERGE = range(3)
 MODE_PLAIN, MODE_SEQUENTIAL, MODE_ASYNC = range(3)
 PREC_FP64, PREC_FP32_IR = range(2)
 DTYPE_F64, DTYPE_F32 = range(2)
-STAGE_FORMAT, STAGE_CSR_ALGO, STAGE_CSR_TPV, STAGE_SELL_SIGMA = range(4)
-STAGE_CLASSES = (6, 3, 5, 4)
+STAGE_FORMAT, STAGE_CSR_ALGO, STAGE_CSR_TPV, STAGE_SELL_SIGMA, STAGE_BATCH_TPR = range(5)
+STAGE_CLASSES = (6, 3, 5, 4, 3)
+BATCH_TPR_CLASSES = (1, 4, 16)  # threads per row of the batched solve, by class
 TPV_CLASSES = (2, 4, 8, 16, 32)
 SIGMA_CLASSES = (1, 32, 1024, 8192)
 ARR = dict(COO_ROW=0, ELL_COL=1, ELL_VAL=2, SELL_PERM=3, SELL_CHUNK_LEN=4, SELL_CHUNK_PTR=5,
@@ -234,6 +235,7 @@ _SIGS = {
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
                                 POINTER(c_int32), _p]),
     "cp_batch_schedule": (c_int32, [_p, c_int64, c_int32, POINTER(c_int32), POINTER(c_int32)]),
+    "cp_batch_tpr": (c_int32, [_p, _p, POINTER(c_int32)]),
     "cp_server_opts_default": (None, [POINTER(ServerOpts)]),
     "cp_server_create": (c_int32, [_p, POINTER(ServerOpts), POINTER(_p)]),
     "cp_server_submit": (c_int32, [_p, POINTER(Request)]),
@@ -561,6 +563,14 @@ class Context:
         z, speedup, mu, sd = _neighbours(z, speedup, mu, sd)
         _check(lib().cp_gate_set_neighbours(self._h, len(z), int(k), _ptr(mu), _ptr(sd), _ptr(z),
                                             _ptr(speedup)))
+
+    def batch_tpr(self, mat):
+        """cp_batch_tpr: the threads per row the BATCH_TPR classifier gives the
+        systems of ``mat`` in a batched solve (0 without a model)."""
+        t = c_int32(0)
+        with self.ordered():
+            _check(lib().cp_batch_tpr(self._h, mat._h, byref(t)))
+        return t.value
 
     def batch_schedule(self, mean_rows, has_gmres=False):
         """(threads per system, threads per row) cp_batch_solve(threads=0) uses for

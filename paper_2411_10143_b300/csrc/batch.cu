@@ -36,6 +36,7 @@ struct BatchSys {
   double* r;     // [n] FP64 residual
   float* w32;    // FP32 workspace: CG 4n (r, d, p, ap); GMRES (m + 2) n (V, d)
   int solver;    // 0 CG, 1 GMRES
+  int tpr;       // threads per row of this system's row loops: 1, 4 or 16
 };
 
 struct BatchOut {
@@ -339,7 +340,61 @@ __device__ int inner_gmres(const BatchSys& S, const BatchParams& P, int budget, 
 }
 
 // ------------------------------------------------------------------ the persistent kernel
+// Shared-memory work areas of one block, handed to the per-system solve.
+struct BatchSmem {
+  double* red;
+  double* Hs;
+  double *gs, *cs, *sn, *hv;
+  float* acc_red;
+};
+
+// One system, start to finish, with TPV threads per row.
 template <int BT, int TPV>
+__device__ void solve_system(const BatchSys& S, const BatchParams& P, const BatchSmem& W,
+                             BatchOut* out, int id) {
+  double* red = W.red;
+  double bb = 0.0;
+  for (int64_t i = threadIdx.x; i < S.n; i += BT) bb = fma(S.b[i], S.b[i], bb);
+  bb = bsum<BT>(bb, red);
+  int outer = 0, inner = 0, status = CP_OK;
+  double rr = 0.0;
+  for (;;) {
+    __syncthreads();
+    rr = resid64<BT, TPV>(S, red);
+    if (bb == 0.0 || rr <= P.tol * P.tol * bb) break;
+    if (!isfinite(rr)) {
+      status = CP_ERR_BREAKDOWN;
+      break;
+    }
+    if (outer >= P.max_outer || inner >= P.max_inner) {
+      status = CP_ERR_NOT_CONVERGED;
+      break;
+    }
+    __syncthreads();
+    const int budget = P.max_inner - inner;
+    const double floor2 = P.theta * P.theta * P.tol * P.tol * bb;
+    int got = S.solver == 0 ? inner_cg<BT, TPV>(S, P, budget, red, floor2)
+                            : inner_gmres<BT, TPV>(S, P, budget, red, W.Hs, W.gs, W.cs, W.sn,
+                                                   W.hv, W.acc_red, floor2);
+    if (got < 0) {
+      status = CP_ERR_BREAKDOWN;
+      inner += -got - 1;
+      break;
+    }
+    inner += got;
+    ++outer;
+  }
+  if (threadIdx.x == 0) {
+    out[id].status = status;
+    out[id].outer = outer;
+    out[id].inner = inner;
+    out[id].relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+}
+
+// Every system carries its own threads per row (a block-uniform branch), so
+// one launch can mix systems of short and of long rows.
+template <int BT>
 __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__ sys, int nsys,
                                                     const int* __restrict__ order,
                                                     int* __restrict__ next, BatchParams P,
@@ -349,6 +404,7 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
   __shared__ double gs[kBatchMaxM + 1], cs[kBatchMaxM], sn[kBatchMaxM], hv[kBatchMaxM + 1];
   __shared__ float acc_red[kBatchMaxM * (BT / 32)];
   __shared__ int s_id;
+  const BatchSmem W{red, Hs, gs, cs, sn, hv, acc_red};
   for (;;) {
     if (threadIdx.x == 0) s_id = atomicAdd(next, 1);
     __syncthreads();
@@ -357,44 +413,9 @@ __global__ void __launch_bounds__(BT) k_batch_solve(const BatchSys* __restrict__
     if (q >= nsys) break;
     const int id = order[q];
     const BatchSys S = sys[id];
-    double bb = 0.0;
-    for (int64_t i = threadIdx.x; i < S.n; i += BT) bb = fma(S.b[i], S.b[i], bb);
-    bb = bsum<BT>(bb, red);
-    int outer = 0, inner = 0, status = CP_OK;
-    double rr = 0.0;
-    for (;;) {
-      __syncthreads();
-      rr = resid64<BT, TPV>(S, red);
-      if (bb == 0.0 || rr <= P.tol * P.tol * bb) break;
-      if (!isfinite(rr)) {
-        status = CP_ERR_BREAKDOWN;
-        break;
-      }
-      if (outer >= P.max_outer || inner >= P.max_inner) {
-        status = CP_ERR_NOT_CONVERGED;
-        break;
-      }
-      __syncthreads();
-      const int budget = P.max_inner - inner;
-      const double floor2 = P.theta * P.theta * P.tol * P.tol * bb;
-      int got = S.solver == 0
-                    ? inner_cg<BT, TPV>(S, P, budget, red, floor2)
-                    : inner_gmres<BT, TPV>(S, P, budget, red, Hs, gs, cs, sn, hv, acc_red,
-                                           floor2);
-      if (got < 0) {
-        status = CP_ERR_BREAKDOWN;
-        inner += -got - 1;
-        break;
-      }
-      inner += got;
-      ++outer;
-    }
-    if (threadIdx.x == 0) {
-      out[id].status = status;
-      out[id].outer = outer;
-      out[id].inner = inner;
-      out[id].relres = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-    }
+    if (S.tpr == 16) solve_system<BT, 16>(S, P, W, out, id);
+    else if (S.tpr == 4) solve_system<BT, 4>(S, P, W, out, id);
+    else solve_system<BT, 1>(S, P, W, out, id);
     __syncthreads();
   }
 }
@@ -418,7 +439,7 @@ struct cp::BatchGraphs {
     cudaGraphNode_t node = nullptr;
     cudaGraphExec_t exec = nullptr;
   };
-  One by_cfg[4][3];  // [threads per system][threads per row]
+  One by_bt[4];  // by threads per system
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
 
@@ -427,11 +448,10 @@ namespace cp {
 void batch_graphs_release(cp_ctx* ctx) {
   BatchGraphs* G = ctx->batch_graphs;
   if (!G) return;
-  for (auto& row : G->by_cfg)
-    for (auto& o : row) {
-      if (o.exec) cudaGraphExecDestroy(o.exec);
-      if (o.graph) cudaGraphDestroy(o.graph);
-    }
+  for (auto& o : G->by_bt) {
+    if (o.exec) cudaGraphExecDestroy(o.exec);
+    if (o.graph) cudaGraphDestroy(o.graph);
+  }
   if (G->e0) cudaEventDestroy(G->e0);
   if (G->e1) cudaEventDestroy(G->e1);
   delete G;
@@ -439,15 +459,15 @@ void batch_graphs_release(cp_ctx* ctx) {
 }
 
 static int bt_slot(int bt) { return bt == 128 ? 0 : bt == 256 ? 1 : bt == 512 ? 2 : 3; }
-static int tpv_slot(int tpv) { return tpv == 1 ? 0 : tpv == 4 ? 1 : 2; }
 
-// Runs one batch with BT threads per system and TPV threads per row; returns
-// the launch's time (ms, CUDA events around the graph launch on s).
-template <int BT, int TPV>
+// Runs one batch with BT threads per system (each system's threads per row
+// are in its descriptor); returns the launch's time (ms, CUDA events around
+// the graph launch on s).
+template <int BT>
 static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const int* d_order,
                           int* d_next, const BatchParams& P, BatchOut* d_out, cudaStream_t s) {
   int per_sm = 0;
-  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT, TPV>, BT, 0));
+  CP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_solve<BT>, BT, 0));
   int grid = ctx->num_sms * std::max(per_sm, 1);
   if (grid > nsys) grid = nsys;
   if (!ctx->batch_graphs) {
@@ -460,7 +480,7 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
     }
     ctx->batch_graphs = G;
   }
-  BatchGraphs::One& g = ctx->batch_graphs->by_cfg[bt_slot(BT)][tpv_slot(TPV)];
+  BatchGraphs::One& g = ctx->batch_graphs->by_bt[bt_slot(BT)];
   BatchSys const* a_sys = d_sys;
   int a_nsys = nsys;
   const int* a_order = d_order;
@@ -469,7 +489,7 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
   BatchOut* a_out = d_out;
   void* args[] = {&a_sys, &a_nsys, &a_order, &a_next, &a_p, &a_out};
   cudaKernelNodeParams kp{};
-  kp.func = reinterpret_cast<void*>(k_batch_solve<BT, TPV>);
+  kp.func = reinterpret_cast<void*>(k_batch_solve<BT>);
   kp.gridDim = dim3(grid);
   kp.blockDim = dim3(BT);
   kp.sharedMemBytes = 0;
@@ -496,25 +516,14 @@ static float launch_batch(cp_ctx* ctx, const BatchSys* d_sys, int nsys, const in
   return ms;
 }
 
-template <int BT>
-static float launch_batch_tpv(int tpv, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
-                              const int* d_order, int* d_next, const BatchParams& P,
-                              BatchOut* d_out, cudaStream_t s) {
-  switch (tpv) {
-    case 1: return launch_batch<BT, 1>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    case 4: return launch_batch<BT, 4>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    default: return launch_batch<BT, 16>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-  }
-}
-
-static float launch_batch_cfg(int bt, int tpv, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
+static float launch_batch_cfg(int bt, cp_ctx* ctx, const BatchSys* d_sys, int nsys,
                               const int* d_order, int* d_next, const BatchParams& P,
                               BatchOut* d_out, cudaStream_t s) {
   switch (bt) {
-    case 128: return launch_batch_tpv<128>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    case 256: return launch_batch_tpv<256>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    case 512: return launch_batch_tpv<512>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
-    default: return launch_batch_tpv<1024>(tpv, ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 128: return launch_batch<128>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 256: return launch_batch<256>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    case 512: return launch_batch<512>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
+    default: return launch_batch<1024>(ctx, d_sys, nsys, d_order, d_next, P, d_out, s);
   }
 }
 
@@ -609,7 +618,7 @@ static void batch_prepare(cp_ctx* ctx, BatchJob& J, int nsys, cp_mat* const* mat
   for (int i = 0; i < nsys; ++i) {
     cp_mat* m = mats[i];
     J.hs[i] = BatchSys{m->nrows, m->rowptr, m->col, m->val, m->val32, b[i],
-                       scratch_x ? J.xs + o64 : x[i], J.d64 + o64, J.d32 + o32, solver[i]};
+                       scratch_x ? J.xs + o64 : x[i], J.d64 + o64, J.d32 + o32, solver[i], 1};
     o64 += m->nrows;
     o32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
   }
@@ -622,21 +631,45 @@ static void batch_prepare(cp_ctx* ctx, BatchJob& J, int nsys, cp_mat* const* mat
   J.d_sys = dalloc_async<BatchSys>(nsys, s);
   J.d_order = dalloc_async<int>(nsys + 1, s);
   J.d_out = dalloc_async<BatchOut>(nsys, s);
-  // the host arrays outlive the copies: the job synchronises before it is destroyed
-  CP_CUDA(cudaMemcpyAsync(J.d_sys, J.hs.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
-                          s));
+  // the host array outlives the copy: the job synchronises before it is destroyed
   CP_CUDA(cudaMemcpyAsync(J.d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
   CP_CUDA(cudaStreamSynchronize(s));
 }
 
-static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& opt,
-                       BatchSchedule sc) {
+// One launch of the batch with `threads` threads per system and tpr[i]
+// threads per row for system i (the descriptors go to the device first; the
+// launch synchronises, so J.hs may change before the next run).
+static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& opt, int threads,
+                       const std::vector<int>& tpr) {
   cudaStream_t s = J.s;
+  for (int i = 0; i < nsys; ++i) J.hs[i].tpr = tpr[i];
+  CP_CUDA(cudaMemcpyAsync(J.d_sys, J.hs.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
+                          s));
   if (J.xs) CP_CUDA(cudaMemsetAsync(J.xs, 0, J.total_rows * sizeof(double), s));
   CP_CUDA(cudaMemsetAsync(J.d_order + nsys, 0, sizeof(int), s));
   BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart, opt.ir_theta};
-  return launch_batch_cfg(sc.threads, sc.tpv, ctx, J.d_sys, nsys, J.d_order, J.d_order + nsys, P,
-                          J.d_out, s);
+  return launch_batch_cfg(threads, ctx, J.d_sys, nsys, J.d_order, J.d_order + nsys, P, J.d_out,
+                          s);
+}
+
+// The CP_STAGE_BATCH_TPR classifier's threads per row for matrix m (1, 4 or
+// 16), or 0 without a model.  The pick is kept with m, tagged with the model
+// installation it came from.
+int batch_tpr_of(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
+  const uint64_t gen = model_generation(ctx, CP_STAGE_BATCH_TPR);
+  if (!gen) return 0;
+  {
+    std::lock_guard<std::mutex> lock(m->feat_mu);
+    if (m->batch_tpr_gen == gen) return m->batch_tpr;
+  }
+  double f[15];
+  compute_features(ctx, m, s, f);
+  const int k = infer_stage(ctx, CP_STAGE_BATCH_TPR, f, s);
+  const int tpr = k == 2 ? 16 : k == 1 ? 4 : 1;
+  std::lock_guard<std::mutex> lock(m->feat_mu);
+  m->batch_tpr = tpr;
+  m->batch_tpr_gen = gen;
+  return tpr;
 }
 
 void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
@@ -652,12 +685,16 @@ void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solv
   BatchJob J;
   J.s = ctx->main;
   batch_prepare(ctx, J, nsys, mats, solver, b, x, opt, false);
-  // threads = 0: the tuned (or default) schedule of the batch's class, whose
-  // threads per row apply unless tpv is given
+  // threads = 0: the tuned (or default) schedule of the batch's class.  Threads
+  // per row: tpv for every system when given, else each system's from the
+  // BATCH_TPR classifier when it has a model, else the schedule's
   BatchSchedule sc = batch_schedule(ctx, J.total_rows / nsys, J.has_gmres);
   if (threads) sc = BatchSchedule{threads, 1};
-  if (tpv) sc.tpv = tpv;
-  batch_run(ctx, J, nsys, opt, sc);
+  std::vector<int> tpr(nsys, tpv ? tpv : sc.tpv);
+  if (!tpv)
+    for (int i = 0; i < nsys; ++i)
+      if (const int t = batch_tpr_of(ctx, mats[i], J.s)) tpr[i] = t;
+  const float launch_ms = batch_run(ctx, J, nsys, opt, sc.threads, tpr);
   std::vector<BatchOut> out(nsys);
   CP_CUDA(cudaMemcpyAsync(out.data(), J.d_out, nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost,
                           J.s));
@@ -674,6 +711,7 @@ void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solv
       infos[i].status = out[i].status;
       infos[i].switch_iter[0] = infos[i].switch_iter[1] = infos[i].switch_iter[2] = -1;
       infos[i].final_cfg = csr;
+      infos[i].t_total_ms = launch_ms;  // the whole batch's launch
     }
     if (out[i].status != CP_OK && worst == CP_OK) worst = out[i].status;
   }
@@ -694,8 +732,9 @@ BatchSchedule batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32
   for (int c = 0; c < 4; ++c)
     for (int v = 0; v < 3; ++v) {
       const BatchSchedule sc{kBatchThreads[c], kBatchTpv[v]};
-      batch_run(ctx, J, nsys, opt, sc);  // warm-up: module load, caches
-      const float ms = batch_run(ctx, J, nsys, opt, sc);
+      const std::vector<int> tpr(nsys, sc.tpv);
+      batch_run(ctx, J, nsys, opt, sc.threads, tpr);  // warm-up: module load, caches
+      const float ms = batch_run(ctx, J, nsys, opt, sc.threads, tpr);
       if (ms12) ms12[c * 3 + v] = ms;
       if (!best.threads || ms < best_ms) {
         best = sc;

@@ -320,6 +320,7 @@ cp_status cp_mat_reset(cp_mat* m) {
     std::lock_guard<std::mutex> lock(m->mu);
     free_formats(m);
     m->has_features = false;
+    m->batch_tpr_gen = 0;
   });
 }
 
@@ -493,6 +494,14 @@ cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const in
     const BatchSchedule best = batch_tune(ctx, nsys, mats, solver, b, opts, ms);
     if (best_threads) *best_threads = best.threads;
     if (best_threads_per_row) *best_threads_per_row = best.tpv;
+  });
+}
+
+cp_status cp_batch_tpr(cp_ctx* ctx, cp_mat* m, int32_t* tpr) {
+  return guard([&] {
+    CP_REQUIRE(ctx && m && tpr, CP_ERR_INVALID, "NULL argument");
+    use_device(ctx);
+    *tpr = batch_tpr_of(ctx, m, ctx->main);
   });
 }
 

@@ -91,6 +91,7 @@ constexpr int kMergeWarpTile = 32 * kMergeItems;  // warp tile (the matrix path'
 struct ModelSlot {
   bool loaded = false;
   int h1 = 0, h2 = 0, k = 0;
+  uint64_t gen = 0;           // installation number, unique in the process
   float* d_params = nullptr;  // device, flat layout of cascade.h
   float* d_mu = nullptr;      // device [15]
   float* d_sd = nullptr;      // device [15]
@@ -279,6 +280,10 @@ struct cp_mat {
   cp::DiaPart dia;
   bool has_features = false;
   double features[15] = {0};
+  // the batched solve's threads per row for this matrix, from the BATCH_TPR
+  // classifier installation numbered batch_tpr_gen (0: none yet); under feat_mu
+  int batch_tpr = 0;
+  uint64_t batch_tpr_gen = 0;
   // the diagonal offsets present (bit col - row + nrows - 1), left by the
   // feature pass for the DIA conversion; published once complete
   std::atomic<unsigned*> diag_bm{nullptr};
@@ -443,6 +448,11 @@ BatchSchedule batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32
                          const double* const* b, const cp_solve_opts* o, float* ms12);
 // the schedule cp_batch_solve uses for a batch class (tuned, else by size)
 BatchSchedule batch_schedule(cp_ctx* ctx, int64_t mean_rows, bool has_gmres);
+// the BATCH_TPR classifier's threads per row for m (cp_batch_tpr), 0 without a model
+int batch_tpr_of(cp_ctx* ctx, cp_mat* m, cudaStream_t s);
+// a number that changes whenever a model is installed for `stage` in ctx (0:
+// the stage has no model)
+uint64_t model_generation(cp_ctx* ctx, int stage);
 
 // The solve entry (CG or GMRES; FP64 or FP32-inner refinement; plain,
 // sequential or asynchronous prediction).

@@ -7,6 +7,7 @@
 // one GPU block on the side stream, and training runs on the GPU with the
 // forward / backward / Adam kernels below.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <thread>
@@ -309,7 +310,7 @@ void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* p
   CP_REQUIRE(stage >= 0 && stage < CP_NUM_STAGES, CP_ERR_INVALID, "bad stage %d", stage);
   const MlpDims D{kFeat, h1, h2, k};
   check_dims(D);
-  static const int expect_k[CP_NUM_STAGES] = {CP_NUM_FMT, CP_NUM_ALGO, 5, 4};
+  static const int expect_k[CP_NUM_STAGES] = {CP_NUM_FMT, CP_NUM_ALGO, 5, 4, 3};
   CP_REQUIRE(k == expect_k[stage], CP_ERR_INVALID, "stage %d needs %d classes, got %d", stage,
              expect_k[stage], k);
   ModelSlot fresh;
@@ -324,6 +325,8 @@ void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* p
   CP_CUDA(cudaMemcpyAsync(fresh.d_sd, sd_dev, kFeat * 4, cudaMemcpyDefault, s));
   CP_CUDA(cudaStreamSynchronize(s));
   fresh.loaded = true;
+  static std::atomic<uint64_t> installs{0};
+  fresh.gen = installs.fetch_add(1) + 1;
   std::lock_guard<std::mutex> lock(ctx->model_mu);
   ModelSlot& old = ctx->models[stage];
   dfree(old.d_params);
@@ -352,6 +355,11 @@ int infer_stage(cp_ctx* ctx, int stage, const double* f15, cudaStream_t s, float
   CP_CUDA(cudaFreeAsync(d_out, s));
   if (logits) std::memcpy(logits, h_out + 1, sizeof(float) * slot.k);
   return h_out[0];
+}
+
+uint64_t model_generation(cp_ctx* ctx, int stage) {
+  std::lock_guard<std::mutex> lock(ctx->model_mu);
+  return ctx->models[stage].loaded ? ctx->models[stage].gen : 0;
 }
 
 int stage_classes(cp_ctx* ctx, int stage) {

@@ -64,7 +64,8 @@ extern "C" cp_status cp_warmup(cp_ctx* ctx) {
     check(cp_features(ctx, m, feat));
     cp_config pred;
     bool have_models = true;
-    for (int s = 0; s < CP_NUM_STAGES; ++s) have_models = have_models && ctx->models[s].loaded;
+    for (int s = CP_STAGE_FORMAT; s <= CP_STAGE_SELL_SIGMA; ++s)  // the cascade's stages
+      have_models = have_models && ctx->models[s].loaded;
     if (have_models) check(cp_predict(ctx, m, &pred, nullptr));
 
     std::vector<cp_config> cfgs;

@@ -14,7 +14,8 @@ from pathlib import Path
 import numpy as np
 
 WEIGHTS = Path(__file__).resolve().parent / "weights" / "cascade.json"
-STAGE_NAMES = ("FORMAT", "CSR_ALGO", "CSR_TPV", "SELL_SIGMA")
+STAGE_NAMES = ("FORMAT", "CSR_ALGO", "CSR_TPV", "SELL_SIGMA", "BATCH_TPR")
+CASCADE_STAGES = STAGE_NAMES[:4]  # the cascade proper; BATCH_TPR serves the batched solve
 
 
 def save(models: dict, path: Path = WEIGHTS, meta: dict | None = None) -> None:
@@ -28,6 +29,22 @@ def save(models: dict, path: Path = WEIGHTS, meta: dict | None = None) -> None:
             "sd": [float(v) for v in np.asarray(m["sd"], np.float32)],
         }
     path.write_text(json.dumps(out))
+
+
+def merge(path: Path, stages: dict, meta: dict) -> None:
+    """Write the given stages and meta entries into the weights file at path,
+    keeping every other stage and meta entry it holds."""
+    data = json.loads(path.read_text()) if path.exists() else {"meta": {}, "stages": {}}
+    for name, m in stages.items():
+        data["stages"][name] = {
+            "dims": [int(v) for v in m["dims"]],
+            "params": [float(v) for v in np.asarray(m["params"], np.float32)],
+            "mu": [float(v) for v in np.asarray(m["mu"], np.float32)],
+            "sd": [float(v) for v in np.asarray(m["sd"], np.float32)],
+        }
+    data["meta"].update(meta)
+    path.parent.mkdir(parents=True, exist_ok=True)
+    path.write_text(json.dumps(data))
 
 
 def load(path: Path = WEIGHTS) -> dict:

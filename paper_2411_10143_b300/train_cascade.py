@@ -17,6 +17,12 @@ costs 3 %.  The labels remain for the accuracy report.
 Usage: python -m paper_2411_10143_b300.train_cascade [--count N] [--reps R]
 writes weights/cascade.json (and weights/dataset.npz with features, times and
 labels).
+
+With --batch it trains, instead, the classifier that picks the batched solve's
+threads per row (the BATCH_TPR stage), on labels from the batching autotuner:
+cp_batch_tune times batches of small SPD systems (workloads.batch_suite) at
+every launch shape, and those times become the soft targets.  It writes that
+stage into the same weights file and weights/batch_dataset.npz.
 """
 from __future__ import annotations
 
@@ -306,7 +312,7 @@ def train_all(ctx, F, L, h=32, epochs=3000, lr=3e-3, seed=7, targets=None):
     """One classifier per stage, on the labels L, or on soft targets (a list of
     four [N][k] arrays) when given."""
     out = {}
-    for stage, name in enumerate(models.STAGE_NAMES):
+    for stage, name in enumerate(models.CASCADE_STAGES):
         if targets is not None:
             loss = ctx.model_train_soft(stage, F, targets[stage], h1=h, h2=h, epochs=epochs,
                                         lr=lr, seed=seed + stage)
@@ -322,19 +328,90 @@ def train_all(ctx, F, L, h=32, epochs=3000, lr=3e-3, seed=7, targets=None):
 def predict_classes(ctx, mdl, F):
     """Per-stage arg-max classes of the trained models, batch-evaluated on the GPU
     (cp_mlp_forward) for the training report."""
+    return np.stack([stage_picks(ctx, mdl[name], F) for name in models.CASCADE_STAGES], 1)
+
+
+def stage_picks(ctx, m, F):
+    """Arg-max classes of one stage's model on the feature rows F (cp_mlp_forward)."""
     import torch
-    preds = []
-    for name in models.STAGE_NAMES:
-        m = mdl[name]
-        d, h1, h2, k = m["dims"]
-        z = (np.log1p(F) - np.asarray(m["mu"], np.float64)) / np.asarray(m["sd"], np.float64)
-        X = torch.as_tensor(z.astype(np.float32), device="cuda")
-        P = torch.as_tensor(np.asarray(m["params"], np.float32), device="cuda")
-        logits = torch.zeros((len(F), k), device="cuda")
-        scratch = torch.zeros(C.Context.mlp_scratch_floats(len(F), d, h1, h2, k), device="cuda")
-        ctx.mlp_forward((d, h1, h2, k), P, X, logits, scratch)
-        preds.append(logits.argmax(1).cpu().numpy())
-    return np.stack(preds, 1)
+    d, h1, h2, k = m["dims"]
+    z = (np.log1p(F) - np.asarray(m["mu"], np.float64)) / np.asarray(m["sd"], np.float64)
+    X = torch.as_tensor(z.astype(np.float32), device="cuda")
+    P = torch.as_tensor(np.asarray(m["params"], np.float32), device="cuda")
+    logits = torch.zeros((len(F), k), device="cuda")
+    scratch = torch.zeros(C.Context.mlp_scratch_floats(len(F), d, h1, h2, k), device="cuda")
+    ctx.mlp_forward((d, h1, h2, k), P, X, logits, scratch)
+    return logits.argmax(1).cpu().numpy()
+
+
+# ------------------------------------------------------------------ batched solve
+BATCH_SYSTEMS = 16  # systems in one labelling batch (one matrix, seeded right-hand sides)
+
+
+def batch_labels(ctx, suite, nsys=BATCH_SYSTEMS, log=print):
+    """Labels of the BATCH_TPR stage from the batching autotuner: for every
+    matrix of the suite, a batch of nsys CG systems on it (b = A x*, x* seeded;
+    FP32 inner solves in FP64 refinement to 1e-10, as the server batches them)
+    goes through cp_batch_tune, which times every launch shape.  A class's time
+    is its best over the four block sizes.  Returns the Table IV features
+    [N][15], the times [N][3] (ms; threads per row 1, 4, 16) and the names."""
+    import torch
+    F, T, names = [], [], []
+    opts = C.default_opts(tol=1e-10, inner_tol=1e-5, precision=C.PREC_FP32_IR)
+    t0 = time.time()
+    for i, (name, make) in enumerate(suite):
+        A = make()
+        M = ctx.load(A)
+        f = M.features()
+        bs = []
+        for k in range(nsys):
+            xs = torch.as_tensor(W.vector(A.nrows, 5000 + k), device="cuda")
+            b = torch.empty(A.nrows, dtype=torch.float64, device="cuda")
+            M.spmv(xs, b)
+            bs.append(b)
+        _, ms = ctx.batch_tune([M] * nsys, [0] * nsys, bs, opts)
+        T.append([min(ms[(t, r)] for t in C.Context.BATCH_THREADS) for r in C.BATCH_TPR_CLASSES])
+        F.append(f)
+        names.append(name)
+        M.free()
+        if log and i % 20 == 0:
+            log(f"[{i}/{len(suite)}] {name} n={A.nrows} nnz={A.nnz} ms={np.round(T[-1], 3)} "
+                f"({time.time() - t0:.0f}s)")
+    return np.array(F), np.array(T, np.float64), names
+
+
+def batch_soft_targets(T, tau):
+    """Target distributions over threads per row (1, 4, 16) from measured batch
+    times: exp(-(t / t_best - 1) / tau), normalised per matrix."""
+    T = np.asarray(T, np.float64)
+    w = np.exp(-(T / T.min(1, keepdims=True) - 1.0) / tau)
+    return w / w.sum(1, keepdims=True)
+
+
+def batch_evaluate(T, picks):
+    """Regret of the picks against the measured best, and their speedup over a
+    thread per row everywhere (the untuned rule), geometric means."""
+    T = np.asarray(T, np.float64)
+    t_pick = T[np.arange(len(T)), picks]
+    g = lambda v: float(np.exp(np.mean(np.log(v))))
+    return dict(mean_regret=g(t_pick / T.min(1)), speedup_vs_one_thread_per_row=g(T[:, 0] / t_pick),
+                picks_within_2pct=int((t_pick <= T.min(1) * TIE).sum()), n=len(T))
+
+
+def train_batch_stage(ctx, F, T, test, tau=0.02, h=32, epochs=3000, seed=11):
+    """The BATCH_TPR classifier on soft targets from the autotuner's times;
+    returns the model and its evaluation on the held-out and training rows."""
+    loss = ctx.model_train_soft(C.STAGE_BATCH_TPR, F[~test], batch_soft_targets(T[~test], tau),
+                                h1=h, h2=h, epochs=epochs, lr=3e-3, seed=seed)
+    m = ctx.model_get(C.STAGE_BATCH_TPR)
+    mdl = dict(dims=m["dims"], params=m["params"], mu=m["mu"], sd=m["sd"], loss=loss)
+    picks = stage_picks(ctx, mdl, F)
+    ev = dict(test=batch_evaluate(T[test], picks[test]), train=batch_evaluate(T[~test], picks[~test]),
+              test_accuracy=float((picks[test] == T[test].argmin(1)).mean()),
+              label_counts=np.bincount(T.argmin(1), minlength=3).tolist(), loss=loss,
+              matrices=len(F), held_out=int(test.sum()), systems_per_batch=BATCH_SYSTEMS,
+              tau=tau, seed=seed)
+    return mdl, ev
 
 
 def evaluate(times_list, picks):
@@ -384,7 +461,28 @@ def main():
     ap.add_argument("--out", default=str(models.WEIGHTS))
     ap.add_argument("--neighbours-only", action="store_true",
                     help="add the gate's neighbour figures to --out from --dataset (no GPU)")
+    ap.add_argument("--batch", action="store_true",
+                    help="label the batched solve's threads per row with the batching "
+                         "autotuner and train the BATCH_TPR stage into --out (the cascade's "
+                         "stages are kept)")
+    ap.add_argument("--batch-count", type=int, default=240)
     args = ap.parse_args()
+    if args.batch:
+        ctx = C.Context(0)
+        out = Path(args.out)
+        ds = out.with_name("batch_dataset.npz")
+        if args.dataset:
+            d = np.load(args.dataset)
+            F, T, names, test = d["features"], d["times"], d["names"].tolist(), d["test"]
+        else:
+            F, T, names = batch_labels(ctx, W.batch_suite(count=args.batch_count))
+            test = np.random.default_rng(1).random(len(F)) < 0.2
+            np.savez_compressed(ds, features=F, times=T, names=np.array(names), test=test)
+        mdl, ev = train_batch_stage(ctx, F, T, test, tau=args.tau if args.tau > 0 else 0.02,
+                                    h=args.hidden, epochs=args.epochs)
+        models.merge(out, {"BATCH_TPR": mdl}, {"batch_tpr": ev})
+        print(json.dumps(ev, indent=1))
+        return
     if args.neighbours_only:
         add_neighbours(Path(args.out), Path(args.dataset or Path(args.out).with_name("dataset.npz")))
         return
@@ -404,7 +502,8 @@ def main():
     mdl = train_all(ctx, F[~test], L[~test], h=args.hidden, epochs=args.epochs, seed=args.seed,
                     targets=targets)
     picks = predict_classes(ctx, mdl, F)
-    acc = {n: float((picks[test, i] == L[test, i]).mean()) for i, n in enumerate(models.STAGE_NAMES)}
+    acc = {n: float((picks[test, i] == L[test, i]).mean())
+           for i, n in enumerate(models.CASCADE_STAGES)}
     ev_test = evaluate([T[i] for i in np.flatnonzero(test)], picks[test])
     ev_train = evaluate([T[i] for i in np.flatnonzero(~test)], picks[~test])
     import torch
@@ -418,6 +517,11 @@ def main():
                                   [NNZ[i] for i in np.flatnonzero(~test)], L[~test]))
     meta["gate"]["neighbours"] = neighbour_figures(
         F[~test], [T[i] for i in np.flatnonzero(~test)], mdl["FORMAT"]["mu"], mdl["FORMAT"]["sd"])
+    # the batched solve's stage is trained separately (--batch): keep it
+    prev = json.loads(Path(args.out).read_text()) if Path(args.out).exists() else {}
+    if "BATCH_TPR" in prev.get("stages", {}):
+        mdl["BATCH_TPR"] = prev["stages"]["BATCH_TPR"]
+        meta["batch_tpr"] = prev.get("meta", {}).get("batch_tpr", {})
     models.save(mdl, Path(args.out), meta)
     np.savez_compressed(Path(args.out).with_name("dataset.npz"), features=F, labels=L,
                         names=np.array(names), test=test, nnz=np.array(NNZ),

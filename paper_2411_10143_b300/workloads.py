@@ -256,6 +256,37 @@ def diagonally_dominant(A: Matrix, margin: float = 1.0) -> Matrix:
     return _from_rows_cols(n, A.ncols, r3[order], c3[order], v3[order], A.name + "_dd")
 
 
+def spd_variant(A: Matrix) -> Matrix:
+    """An SPD system on a square matrix's pattern, as spd_powerlaw builds one:
+    the off-diagonal entries of A + A^T (coincident entries summed; the pattern
+    becomes symmetric), diag_i = sum_j |off-diagonal_ij| + 1 (strict dominance,
+    so CG applies)."""
+    n = A.nrows
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(A.rowptr))
+    cols = A.col.astype(np.int64)
+    off = cols != rows
+    r, c, v = rows[off], cols[off], A.val[off]
+    r2 = np.concatenate([r, c])
+    c2 = np.concatenate([c, r])
+    v2 = np.concatenate([v, v])
+    k2 = r2 * n + c2
+    order = np.argsort(k2, kind="stable")
+    k2, v2 = k2[order], v2[order]
+    first = np.ones(k2.size, bool)
+    first[1:] = k2[1:] != k2[:-1]
+    key = k2[first]
+    v = np.add.reduceat(v2, np.flatnonzero(first)) if k2.size else np.zeros(0)
+    r, c = key // n, key % n
+    diag = np.zeros(n)
+    np.add.at(diag, r, np.abs(v))
+    diag += 1.0
+    r3 = np.concatenate([r, np.arange(n)])
+    c3 = np.concatenate([c, np.arange(n)])
+    v3 = np.concatenate([v, diag])
+    order = np.lexsort((c3, r3))
+    return _from_rows_cols(n, n, r3[order], c3[order], v3[order], A.name + "_spd")
+
+
 def random_csr(nrows: int, ncols: int, lens, seed: int, int_values: bool = False) -> Matrix:
     """Small random CSR with given per-row lengths (capped at ncols), distinct sorted columns.
 
@@ -363,6 +394,45 @@ def training_suite(seed: int = 77, count: int = 240):
             m = float(rng.uniform(4, 12))
             out.append((f"bimodal_{n}_{m:.1f}",
                         lambda n=n, a=a, m=m, s=s: powerlaw(n, a, m, min(n, 4096), s)))
+    return out
+
+
+def batch_suite(seed: int = 79, count: int = 240, log2_min: float = 10.0,
+                log2_max: float = 15.0):
+    """Small systems for labelling the batched solve's threads per row: the
+    training suite's families at 2^10 to 2^15 rows (the sizes a batch holds),
+    each as its SPD variant (spd_variant), so one CG batch times every pattern.
+    Yields (name, builder)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        fam = i % 6
+        n = int(2 ** rng.uniform(log2_min, log2_max))
+        s = int(rng.integers(0, 2**31 - 1))
+        if fam == 0:
+            N = max(8, int(round(n ** 0.5)))
+            out.append((f"p2d_{N}", lambda N=N, s=s: spd_variant(poisson2d(N, "uniform", s))))
+        elif fam == 1:
+            N = max(4, int(round(n ** (1 / 3))))
+            out.append((f"p3d_{N}", lambda N=N, s=s: spd_variant(poisson3d(N, "uniform", s))))
+        elif fam == 2:
+            a = float(rng.uniform(1.5, 2.6))
+            m = float(rng.uniform(3, 40))
+            lm = int(min(n, 2 ** rng.uniform(6, 14)))
+            out.append((f"pl_{n}_{a:.2f}_{m:.1f}_{lm}",
+                        lambda n=n, a=a, m=m, lm=lm, s=s: spd_variant(powerlaw(n, a, m, lm, s))))
+        elif fam == 3:
+            k = int(rng.integers(2, 48))
+            out.append((f"uni_{n}_{k}", lambda n=n, k=k, s=s: spd_variant(uniform_random(n, k, s))))
+        elif fam == 4:
+            w = int(rng.choice([4, 8, 16, 32, 64, 128]))
+            f = float(rng.uniform(0.2, 1.0))
+            out.append((f"band_{n}_{w}_{f:.2f}",
+                        lambda n=n, w=w, f=f, s=s: spd_variant(banded(n, w, f, s))))
+        else:
+            m = float(rng.uniform(4, 12))
+            out.append((f"bimodal_{n}_{m:.1f}",
+                        lambda n=n, m=m, s=s: spd_variant(powerlaw(n, 1.2, m, min(n, 4096), s))))
     return out
 
 

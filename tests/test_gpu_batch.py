@@ -159,3 +159,66 @@ def test_batch_inexact_inner_stop():
             assert info.outer_iters == ref.outer == 3, (A.name, th)
     assert all(a < b for a, b in zip(steps[0.5], steps[0.0])), steps
     ctx.close()
+
+
+def row_length_model(ctx, threshold):
+    """A BATCH_TPR classifier written by hand: class 2 (16 threads per row) when
+    the longest row (feature 7, max) exceeds `threshold`, else class 0 (one
+    thread per row).  With mu = 0 and sd = 1 the input is z = log(1 + f); hidden
+    unit 0 is relu(z_7 - log(1 + threshold)), unit 1 relu(log(1 + threshold) -
+    z_7), both passed through the second layer to the logits of classes 2 and
+    0.  Returns (params, dims)."""
+    d, h1, h2, k = 15, 2, 2, 3
+    P = np.zeros(C.Context.mlp_nparams(d, h1, h2, k), np.float32)
+    c = np.log1p(threshold)
+    W1 = P[:h1 * d].reshape(h1, d)
+    W1[0, 7], W1[1, 7] = 1.0, -1.0
+    o = h1 * d
+    P[o], P[o + 1] = -c, c  # b1
+    o += h1
+    W2 = P[o:o + h2 * h1].reshape(h2, h1)
+    W2[0, 0] = W2[1, 1] = 1.0
+    o += h2 * h1 + h2  # b2 = 0
+    W3 = P[o:o + k * h2].reshape(k, h2)
+    W3[2, 0] = W3[0, 1] = 1.0
+    ctx.model_load(C.STAGE_BATCH_TPR, h1, h2, k, P, np.zeros(15), np.ones(15))
+    return P, (d, h1, h2, k)
+
+
+def test_batch_threads_per_row_per_system_from_the_classifier():
+    """With a BATCH_TPR model installed, cp_batch_solve(threads_per_row = 0) gives
+    each system the classifier's pick for its matrix (cp_batch_tpr: the oracle's
+    forward pass on the matrix's features picks the same), so one launch mixes
+    systems at 1 and at 16 threads per row.  Every system meets the oracle, and
+    its result equals that of a batch of one at its own threads per row.  A new
+    installation replaces the picks kept with the matrices."""
+    ctx = C.Context(0)
+    P, dims = row_length_model(ctx, 30)
+    sys = systems()
+    mats = [ctx.load(A) for A, _ in sys]
+    picks = [ctx.batch_tpr(M) for M in mats]
+    for (A, _), M, t in zip(sys, mats, picks):
+        lg = oracle.mlp_forward(P, oracle.mlp_input(M.features(), np.zeros(15), np.ones(15)), dims)
+        assert t == C.BATCH_TPR_CLASSES[int(np.argmax(lg))], A.name
+        assert t == (16 if np.diff(A.rowptr).max() > 30 else 1), A.name
+    assert 1 in picks and 16 in picks, picks
+    _, mixed = check(ctx, sys, 256)
+    for k in (0, picks.index(16), len(sys) - 1):
+        bs = [torch.as_tensor(oracle.spmv(sys[k][0], W.vector(sys[k][0].nrows, k + 40)),
+                              device="cuda")]
+        xs = [torch.zeros(sys[k][0].nrows, dtype=torch.float64, device="cuda")]
+        ctx.batch_solve([mats[k]], [sys[k][1]], bs, xs,
+                        C.default_opts(tol=1e-10, inner_tol=1e-5, restart=30,
+                                       precision=C.PREC_FP32_IR), 256, picks[k])
+        alone = xs[0].cpu().numpy()
+        assert np.linalg.norm(alone - mixed[k]) <= 1e-12 * np.linalg.norm(mixed[k]), k
+    row_length_model(ctx, 1e9)  # every row is short now
+    assert all(ctx.batch_tpr(M) == 1 for M in mats)
+    ctx.close()
+
+
+def test_batch_threads_per_row_without_a_model_is_the_schedule():
+    ctx = C.Context(0)
+    M = ctx.load(W.poisson2d(20))
+    assert ctx.batch_tpr(M) == 0
+    ctx.close()

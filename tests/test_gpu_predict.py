@@ -83,6 +83,24 @@ def test_every_stage_on_the_training_features(ctx):
     assert decided >= 0.9 * 4 * len(F)
 
 
+def test_batch_stage_on_its_training_features(ctx):
+    """The batched solve's classifier (BATCH_TPR, trained on the batching
+    autotuner's times) through the same kernel, against the oracle; and
+    cp_batch_tpr's pick for a matrix is the oracle's arg-max on the GPU
+    features of that matrix."""
+    F = np.load(models.WEIGHTS.parent / "batch_dataset.npz")["features"]
+    assert F.shape[1] == 15 and F.shape[0] >= 200
+    decided = sum(check_stage(ctx, C.STAGE_BATCH_TPR, f)[1] for f in F)
+    assert decided >= 0.9 * len(F)
+    for A in (W.spd_powerlaw(6000, seed=6), W.poisson3d(20), W.convdiff3d(14),
+              W.spd_variant(W.banded(9000, 64, 0.8, 5))):
+        M = ctx.load(A)
+        ref, ok = check_stage(ctx, C.STAGE_BATCH_TPR, M.features())
+        if ok:
+            assert ctx.batch_tpr(M) == C.BATCH_TPR_CLASSES[int(np.argmax(ref))], A.name
+        M.free()
+
+
 def test_stage_rejects_a_stage_without_model():
     c = C.Context(0)
     with pytest.raises(C.CascadeError) as e:

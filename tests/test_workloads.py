@@ -126,3 +126,33 @@ def test_request_stream_mix_sizes_and_arrivals():
         A = W.request_matrix(r) if r.n < 30000 else None
         if A is not None:
             assert 0.5 * r.n <= A.nrows <= 2.0 * r.n, (r.kind, r.n, A.nrows)
+
+
+def test_spd_variant_is_symmetric_and_strictly_dominant():
+    import scipy.sparse as sp
+    A = W.powerlaw(3000, 1.8, 10.0, 400, 3)
+    S = W.spd_variant(A)
+    Ss = sp.csr_matrix((S.val, S.col, S.rowptr), shape=(S.nrows, S.ncols))
+    assert abs(Ss - Ss.T).max() == 0
+    diag = Ss.diagonal()
+    off = np.asarray(abs(Ss).sum(1)).ravel() - np.abs(diag)
+    assert np.allclose(diag, off + 1.0, rtol=1e-13, atol=0)  # sums in another order
+    # the off-diagonal pattern is that of A + A^T
+    As = sp.csr_matrix((np.ones(A.nnz), A.col, A.rowptr), shape=(A.nrows, A.ncols))
+    As.setdiag(0)
+    As.eliminate_zeros()
+    pa = ((As + As.T) != 0).astype(np.int8)
+    Sp = sp.csr_matrix((np.ones(S.nnz), S.col, S.rowptr), shape=(S.nrows, S.ncols))
+    Sp.setdiag(0)
+    Sp.eliminate_zeros()
+    assert (pa != (Sp != 0).astype(np.int8)).nnz == 0
+
+
+def test_batch_suite_sizes_and_families():
+    suite = W.batch_suite(count=12)
+    fams = [name.split("_")[0] for name, _ in suite]
+    assert fams[:6] == ["p2d", "p3d", "pl", "uni", "band", "bimodal"]
+    for name, make in suite[:6]:
+        A = make()
+        assert 2 ** 9 <= A.nrows <= 2 ** 15 + 2000, (name, A.nrows)
+        assert A.nrows == A.ncols
