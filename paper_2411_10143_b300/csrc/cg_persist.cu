@@ -58,6 +58,14 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
       tmark = now;
     }
   };
+  // Thread 0 keeps ||b||^2 and the current (r, r) in shared memory (every
+  // block's thread 0 forms the same values from the same partials), so no step
+  // waits on an L2 round trip for them.
+  __shared__ double bb, rr_cur;
+  if (threadIdx.x == 0) {
+    bb = ld_cg(&st->bb);
+    rr_cur = ld_cg(&st->rr[a.it0 & 1]);
+  }
   V* x2 = reinterpret_cast<V*>(a.x);
   V* r2 = reinterpret_cast<V*>(a.r);
   V* p2 = reinterpret_cast<V*>(a.p);
@@ -65,6 +73,10 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
   V* qc2 = reinterpret_cast<V*>(a.apc);
   for (int it = a.it0; it < a.itmax; ++it) {
     const int slot = it & 1;
+    // the host's request, read (host-mapped, a bus round trip) before the SpMV
+    // so that phase 2 does not wait for it
+    int yield = 0;
+    if (lead) yield = *a.yield;
     // ---- phase 1: Ap = A p, partials of (p, Ap)
     {
       T acc = persist_spmv<T, F, TPV, false, true>(a, so, a.p, a.ap, T(1), T(0), a.p);
@@ -82,7 +94,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
       const double pap = warp_partials_cg(a.pa, gridDim.x);
       if (threadIdx.x == 0) {
         const bool bad = !(pap > 0.0) || !isfinite(pap);  // A not SPD, or overflow / NaN
-        const double alpha_d = bad ? 0.0 : ld_cg(&st->rr[slot]) / pap;
+        const double alpha_d = bad ? 0.0 : rr_cur / pap;
         sc_val = alpha_d;
         sc_flag = bad;
         if (lead) {
@@ -95,7 +107,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
             st->pap = pap;
             st->alpha = alpha_d;
           }
-          st->stop = *a.yield;  // the host's request, published to all blocks by the barrier
+          st->stop = yield;  // the host's request, published to all blocks by the barrier
         }
       }
     }
@@ -153,12 +165,16 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
     if (!grid_barrier(&st->bar_count, &st->bar_err, bar_target, a.barrier_timeout_ns)) break;
     lap(3);
     // ---- phase 3: beta; convergence; x += alpha p; p = r + beta p
+    // block 0 published the host's request before the barrier; the load is
+    // issued here, with the partials', and used at the end of the phase
+    const int stop = *(volatile int*)&st->stop;
     if (threadIdx.x < 32) {
       const double rr_new = warp_partials_cg(a.pb, gridDim.x);
       if (threadIdx.x == 0) {
         const bool bad = !isfinite(rr_new);
-        const bool conv = rr_new <= a.tol2 * ld_cg(&st->bb);
-        const double beta_d = rr_new / ld_cg(&st->rr[slot]);
+        const bool conv = rr_new <= a.tol2 * bb;
+        const double beta_d = rr_new / rr_cur;
+        rr_cur = rr_new;
         sc_val = beta_d;
         sc_flag = conv || bad;
         if (lead) {
@@ -237,7 +253,6 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_cg_persist(PersistArgs<T> 
       a.x[i] = fma(alpha, pi, ld_cg(a.x + i));
       a.p[i] = fma(beta, pi, ld_cg(a.r + i));
     }
-    const int stop = *(volatile int*)&st->stop;
     if (stop) break;  // every block read the same value after the last barrier
     lap(4);
     bar_target += gridDim.x;

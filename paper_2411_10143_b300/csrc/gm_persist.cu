@@ -467,6 +467,10 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
   for (;;) {
     T* w = V + (int64_t)(j + 1) * ldv;
     int second = 0;
+    // the host's request (host-mapped, a bus round trip), read before the
+    // SpMV so that the reduction that publishes it does not wait for it
+    int yield = 0;
+    if (lead) yield = *a.yield;
     if (a.mgs) {
       // ---- 1-3 (modified Gram-Schmidt in groups of GS): w = A v_j; per group
       // B_k = [GS k, GS k + R_k) one grid reduction of (v_c, w), then h_B = T_k (V_B^T w)
@@ -502,7 +506,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
           ok = false;
           break;
         }
-        if (k == 0 && lead) st->stop = *a.yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
+        if (k == 0 && lead) st->stop = yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
         if (threadIdx.x < 32 * GS) {  // one warp per value
           const double t = warp_partials_cg(pr + (int64_t)(threadIdx.x >> 5) * gridDim.x,
                                             gridDim.x);
@@ -576,7 +580,7 @@ __global__ void __launch_bounds__(kPersistBlock, 1) k_gm_persist(GmPersistArgs<T
       // ---- 2. first subtraction
       // the host's request (or the end of the launch's chunk of steps), published
       // to every block by the next barrier
-      if (lead) st->stop = *a.yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
+      if (lead) st->stop = yield || (a.chunk > 0 && iters + 1 - iters0 >= a.chunk);
       sum_items(a.part, j + 2, h);
       for (int c = threadIdx.x; c <= j; c += blockDim.x) {
         const double hc = h[c] * sc[c];  // (v_c, w)
