@@ -393,6 +393,26 @@ def test_cost_aware_gate_switches_on_a_long_solve():
     c.close()
 
 
+def test_gate_switches_at_once_when_the_conversion_pays_back_within_a_few_iterations():
+    """A 16x format whose conversion costs 2.5 default SpMVs pays back within 2.7
+    iterations (cp_gate_payback): the side thread converts without waiting for
+    residual history, so the gate makes no estimate of the iterations left (-1)
+    and the solve switches mid-run."""
+    c = C.Context(0)
+    one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
+    g = fixed_gate(speedup=16.0, conv_ms=0.125)
+    assert C.gate_payback(g, C.FMT_ELL, 10**6) == pytest.approx(2.5 / (1 - 1 / 16))
+    c.gate_set(g)
+    A = W.poisson2d(512)
+    b = rhs(A, 33)
+    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
+    assert true_relres(A, x, b) <= 1e-10
+    assert info.gate_declined == 0 and info.final_cfg.fmt == C.FMT_ELL
+    assert info.switch_iter[0] >= 0
+    assert info.gate_remaining == -1.0 and info.gate_cost_spmvs == pytest.approx(2.5)
+    c.close()
+
+
 def test_gate_neighbours_decide_with_the_matrix_own_speedup():
     """With neighbours installed the gate takes the predicted format's speedup
     from the training matrices nearest to this one.  The long solve above
