@@ -425,8 +425,10 @@ void mlp_loss_grad(cp_ctx* ctx, int64_t N, MlpDims D, const float* P, const floa
                    cudaStream_t s);
 void adam_step(cp_ctx* ctx, int64_t np, float* P, const float* G, float* m, float* v, int t,
                float lr, float b1, float b2, float eps, cudaStream_t s);
+// gen: the installation number to record (0: a new one; a copy of another
+// context's model passes that model's, so picks kept with a matrix stay valid)
 void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* params,
-                   const float* mu, const float* sd, cudaStream_t s);
+                   const float* mu, const float* sd, cudaStream_t s, uint64_t gen = 0);
 void model_train(cp_ctx* ctx, int stage, int64_t N, const double* F_host,
                  const int32_t* lab_host, const float* q_host, int h1, int h2, int k, int epochs,
                  float lr, uint64_t seed, float* final_loss);

@@ -306,7 +306,7 @@ void adam_step(cp_ctx* ctx, int64_t np, float* P, const float* G, float* m, floa
 
 // ------------------------------------------------------------------ host: models
 void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* params_dev,
-                   const float* mu_dev, const float* sd_dev, cudaStream_t s) {
+                   const float* mu_dev, const float* sd_dev, cudaStream_t s, uint64_t gen) {
   CP_REQUIRE(stage >= 0 && stage < CP_NUM_STAGES, CP_ERR_INVALID, "bad stage %d", stage);
   const MlpDims D{kFeat, h1, h2, k};
   check_dims(D);
@@ -326,7 +326,7 @@ void model_install(cp_ctx* ctx, int stage, int h1, int h2, int k, const float* p
   CP_CUDA(cudaStreamSynchronize(s));
   fresh.loaded = true;
   static std::atomic<uint64_t> installs{0};
-  fresh.gen = installs.fetch_add(1) + 1;
+  fresh.gen = gen ? gen : installs.fetch_add(1) + 1;
   std::lock_guard<std::mutex> lock(ctx->model_mu);
   ModelSlot& old = ctx->models[stage];
   dfree(old.d_params);

@@ -295,7 +295,7 @@ cp_status cp_server_create(cp_ctx* ctx, const cp_server_opts* opts, cp_server** 
       for (int k = 0; k < CP_NUM_STAGES; ++k) {
         const ModelSlot& ms = ctx->models[k];
         if (ms.loaded) model_install(c, k, ms.h1, ms.h2, ms.k, ms.d_params, ms.d_mu, ms.d_sd,
-                                     c->main);
+                                     c->main, ms.gen);
       }
       S->lane_ctx.push_back(c);
     }
