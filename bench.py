@@ -817,8 +817,8 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
     for _ in range(3 if len(small) >= 32 else 0):
         grp = [small[i] for i in rng.choice(len(small), 32, replace=False)]
         bopts = C.default_opts(tol=TOL, inner_tol=1e-5, restart=30, precision=C.PREC_FP32_IR)
-        best, ms = ctx.batch_tune([g[2] for g in grp], [g[3] for g in grp], [g[4] for g in grp],
-                                  bopts)
+        best, ms, (order, ms_order) = ctx.batch_tune([g[2] for g in grp], [g[3] for g in grp],
+                                                     [g[4] for g in grp], bopts, with_order=True)
         # the same batch at the tuned block size with every system's threads per
         # row from the BATCH_TPR classifier (the server's default), launch time
         # as the tuner measures it (median of three after one warm-up)
@@ -833,6 +833,8 @@ def serve_bench(ctx, count, seed=3000, lanes=4, log_fn=log):
                       "gmres": any(g[3] for g in grp), "threads": best[0],
                       "threads_per_row": best[1],
                       "ms": {f"{t}x{r}": round(v, 3) for (t, r), v in ms.items()},
+                      "packing_order": "caller's order" if order else "largest first",
+                      "caller_order_ms": round(ms_order, 3),
                       "per_system_classifier_ms": round(float(np.median(per[1:])), 3),
                       "per_system_threads_per_row": {str(r): picks.count(r) for r in (1, 4, 16)}})
     log_fn(f"serve: batch autotuner picks {[(t['threads'], t['threads_per_row']) for t in tuned]}, "

@@ -535,7 +535,8 @@ cp_status cp_solve_gmres(cp_ctx* ctx, cp_mat* mat, const double* b, double* x,
 /* cp_batch_solve: solve nsys small systems A_i x_i = b_i in one persistent
  * launch held in a CUDA graph (each context instantiates the graph of each
  * launch shape once and updates its kernel node per batch).  One thread block
- * per system at a time, systems taken largest first from a device work queue.
+ * per system at a time, systems taken from a device work queue, largest first
+ * (or in the caller's order where the class's tuned schedule says so).
  * Every system runs FP64 iterative refinement to opts->tol around FP32 inner
  * solves to opts->inner_tol (stopping early as opts->ir_theta allows):
  * solver[i] = 0 for CG (SPD A_i), 1 for
@@ -567,15 +568,21 @@ cp_status cp_batch_solve(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const i
  * system, each with 1, 4 and 16 threads per row -- after one warm-up each,
  * timing each launch with CUDA events.  It records the fastest shape in a
  * per-device schedule under the batch's class: whether the batch holds a GMRES
- * system, and floor(log2(mean rows)).  cp_batch_solve with threads = 0 then
- * uses that shape for batches of the class.  Arguments as cp_batch_solve.
- * best_threads / best_threads_per_row (may be NULL) receive the choice; ms (may
- * be NULL, 12 floats) the times of the shapes, ms[3 t + r] for threads index t
- * (128, 256, 512, 1024) and threads-per-row index r (1, 4, 16).  Any system that
- * fails to converge returns its status. */
+ * system, and floor(log2(mean rows)).  The shapes are timed with the largest
+ * systems dequeued first; the best shape is then timed once more with the
+ * systems dequeued in the caller's order (the packing schedule), and the faster
+ * order is recorded with it.  cp_batch_solve with threads = 0 then uses that
+ * shape and order for batches of the class.  Arguments as cp_batch_solve.
+ * best_threads / best_threads_per_row / best_order (may be NULL) receive the
+ * choice (order 0: largest first, 1: the caller's order); ms (may be NULL, 12
+ * floats) the times of the shapes, ms[3 t + r] for threads index t (128, 256,
+ * 512, 1024) and threads-per-row index r (1, 4, 16); ms_order (may be NULL) the
+ * best shape's time in the caller's order.  Any system that fails to converge
+ * returns its status. */
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                         const double* const* b, const cp_solve_opts* opts,
-                        int32_t* best_threads, int32_t* best_threads_per_row, float* ms);
+                        int32_t* best_threads, int32_t* best_threads_per_row,
+                        int32_t* best_order, float* ms, float* ms_order);
 /* cp_batch_tpr: the threads per row cp_batch_solve(threads_per_row = 0) gives
  * the systems of matrix m when the CP_STAGE_BATCH_TPR stage has a model: the
  * classifier's pick on m's Table IV features (computed on the main stream if m
@@ -585,11 +592,12 @@ cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const in
 cp_status cp_batch_tpr(cp_ctx* ctx, cp_mat* m, int32_t* tpr);
 /* The launch shape cp_batch_solve(threads = 0) uses for a batch with mean_rows
  * rows per system (has_gmres: the batch holds a GMRES system): the tuned shape
- * of that class, else 128 / 256 / 512 / 1024 threads for mean rows below
- * 512 / 2048 / 8192 / above, with 1 thread per row.  threads, threads_per_row:
- * host int32.  Errors: CP_ERR_INVALID (NULL argument). */
+ * and packing order of that class, else 128 / 256 / 512 / 1024 threads for mean
+ * rows below 512 / 2048 / 8192 / above, with 1 thread per row, largest systems
+ * first.  threads, threads_per_row, order (may be NULL; 0 largest first, 1 the
+ * caller's order): host int32.  Errors: CP_ERR_INVALID (NULL argument). */
 cp_status cp_batch_schedule(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres, int32_t* threads,
-                            int32_t* threads_per_row);
+                            int32_t* threads_per_row, int32_t* order);
 
 /* ------------------------------------------------------------------ serving */
 /* A continuous-batching solve server.  Requests carry a matrix already loaded

@@ -233,8 +233,9 @@ _SIGS = {
                                       POINTER(c_double)]),
     "cp_gate_set_neighbours": (c_int32, [_p, c_int32, c_int32, _p, _p, _p, _p]),
     "cp_batch_tune": (c_int32, [_p, c_int32, _p, _p, _p, POINTER(SolveOpts), POINTER(c_int32),
-                                POINTER(c_int32), _p]),
-    "cp_batch_schedule": (c_int32, [_p, c_int64, c_int32, POINTER(c_int32), POINTER(c_int32)]),
+                                POINTER(c_int32), POINTER(c_int32), _p, POINTER(c_float)]),
+    "cp_batch_schedule": (c_int32, [_p, c_int64, c_int32, POINTER(c_int32), POINTER(c_int32),
+                                    POINTER(c_int32)]),
     "cp_batch_tpr": (c_int32, [_p, _p, POINTER(c_int32)]),
     "cp_server_opts_default": (None, [POINTER(ServerOpts)]),
     "cp_server_create": (c_int32, [_p, POINTER(ServerOpts), POINTER(_p)]),
@@ -515,23 +516,29 @@ class Context:
     BATCH_THREADS = (128, 256, 512, 1024)
     BATCH_TPV = (1, 4, 16)
 
-    def batch_tune(self, mats, solvers, bs, opts=None):
+    def batch_tune(self, mats, solvers, bs, opts=None, with_order=False):
         """cp_batch_tune: time every launch shape (128/256/512/1024 threads per
-        system x 1/4/16 threads per row) on this batch (scratch solutions) and
-        record the fastest for its class.  Returns ((threads, threads per row),
-        {(threads, threads per row): ms})."""
+        system x 1/4/16 threads per row) on this batch (scratch solutions), then
+        the best shape in the caller's order, and record the fastest for its
+        class.  Returns ((threads, threads per row), {(threads, threads per row):
+        ms}); with_order adds (packing order, ms of the best shape in the
+        caller's order)."""
         n = len(mats)
         hm = (c_void_p * n)(*[m._h.value for m in mats])
         hs = np.ascontiguousarray(solvers, np.int32)
         hb = (c_void_p * n)(*[t.data_ptr() for t in bs])
-        best, best_tpv = c_int32(0), c_int32(0)
+        best, best_tpv, best_order = c_int32(0), c_int32(0), c_int32(0)
         ms = np.zeros(12, np.float32)
+        ms_order = c_float(0.0)
         o = opts if opts is not None else default_opts(precision=PREC_FP32_IR)
         with self.ordered():
             _check(lib().cp_batch_tune(self._h, n, hm, _ptr(hs), hb, byref(o), byref(best),
-                                       byref(best_tpv), _ptr(ms)))
+                                       byref(best_tpv), byref(best_order), _ptr(ms),
+                                       byref(ms_order)))
         times = {(t, r): float(ms[3 * i + j]) for i, t in enumerate(self.BATCH_THREADS)
                  for j, r in enumerate(self.BATCH_TPV)}
+        if with_order:
+            return (best.value, best_tpv.value), times, (best_order.value, ms_order.value)
         return (best.value, best_tpv.value), times
 
     def fp64_fma_rate(self):
@@ -572,13 +579,14 @@ class Context:
             _check(lib().cp_batch_tpr(self._h, mat._h, byref(t)))
         return t.value
 
-    def batch_schedule(self, mean_rows, has_gmres=False):
+    def batch_schedule(self, mean_rows, has_gmres=False, with_order=False):
         """(threads per system, threads per row) cp_batch_solve(threads=0) uses for
-        a batch class."""
-        t, r = c_int32(0), c_int32(0)
+        a batch class; with_order adds the packing order (0: largest first, 1:
+        the caller's order)."""
+        t, r, o = c_int32(0), c_int32(0), c_int32(0)
         _check(lib().cp_batch_schedule(self._h, int(mean_rows), 1 if has_gmres else 0, byref(t),
-                                       byref(r)))
-        return t.value, r.value
+                                       byref(r), byref(o)))
+        return (t.value, r.value, o.value) if with_order else (t.value, r.value)
 
     @staticmethod
     def mlp_nparams(d, h1, h2, k):

@@ -573,6 +573,7 @@ struct BatchJob {
   BatchSys* d_sys = nullptr;
   int* d_order = nullptr;  // nsys entries + the work counter
   BatchOut* d_out = nullptr;
+  std::vector<int> order[2];  // largest systems first; the caller's order
   int64_t total_rows = 0;
   bool has_gmres = false;
   ~BatchJob() {
@@ -622,29 +623,32 @@ static void batch_prepare(cp_ctx* ctx, BatchJob& J, int nsys, cp_mat* const* mat
     o64 += m->nrows;
     o32 += (solver[i] == 0 ? 4 : opt.restart + 2) * m->nrows;
   }
-  // largest systems first, so the dynamic queue ends with short jobs
-  std::vector<int> order(nsys);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+  // packing orders of the dynamic queue: largest systems first (so the queue
+  // ends with short jobs), or the caller's order
+  J.order[1].resize(nsys);
+  std::iota(J.order[1].begin(), J.order[1].end(), 0);
+  J.order[0] = J.order[1];
+  std::stable_sort(J.order[0].begin(), J.order[0].end(), [&](int a, int c) {
     return J.hs[a].n * (J.hs[a].solver ? 3 : 1) > J.hs[c].n * (J.hs[c].solver ? 3 : 1);
   });
   J.d_sys = dalloc_async<BatchSys>(nsys, s);
   J.d_order = dalloc_async<int>(nsys + 1, s);
   J.d_out = dalloc_async<BatchOut>(nsys, s);
-  // the host array outlives the copy: the job synchronises before it is destroyed
-  CP_CUDA(cudaMemcpyAsync(J.d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice, s));
   CP_CUDA(cudaStreamSynchronize(s));
 }
 
-// One launch of the batch with `threads` threads per system and tpr[i]
-// threads per row for system i (the descriptors go to the device first; the
-// launch synchronises, so J.hs may change before the next run).
+// One launch of the batch with `threads` threads per system, tpr[i] threads
+// per row for system i and packing order `order` (the descriptors and the
+// order go to the device first; the launch synchronises, so J.hs may change
+// before the next run).
 static float batch_run(cp_ctx* ctx, BatchJob& J, int nsys, const cp_solve_opts& opt, int threads,
-                       const std::vector<int>& tpr) {
+                       const std::vector<int>& tpr, int order) {
   cudaStream_t s = J.s;
   for (int i = 0; i < nsys; ++i) J.hs[i].tpr = tpr[i];
   CP_CUDA(cudaMemcpyAsync(J.d_sys, J.hs.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice,
                           s));
+  CP_CUDA(cudaMemcpyAsync(J.d_order, J.order[order ? 1 : 0].data(), nsys * sizeof(int),
+                          cudaMemcpyHostToDevice, s));
   if (J.xs) CP_CUDA(cudaMemsetAsync(J.xs, 0, J.total_rows * sizeof(double), s));
   CP_CUDA(cudaMemsetAsync(J.d_order + nsys, 0, sizeof(int), s));
   BatchParams P{opt.tol, opt.inner_tol, opt.max_outer, opt.maxit, opt.restart, opt.ir_theta};
@@ -689,12 +693,12 @@ void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solv
   // per row: tpv for every system when given, else each system's from the
   // BATCH_TPR classifier when it has a model, else the schedule's
   BatchSchedule sc = batch_schedule(ctx, J.total_rows / nsys, J.has_gmres);
-  if (threads) sc = BatchSchedule{threads, 1};
+  if (threads) sc = BatchSchedule{threads, 1, 0};
   std::vector<int> tpr(nsys, tpv ? tpv : sc.tpv);
   if (!tpv)
     for (int i = 0; i < nsys; ++i)
       if (const int t = batch_tpr_of(ctx, mats[i], J.s)) tpr[i] = t;
-  const float launch_ms = batch_run(ctx, J, nsys, opt, sc.threads, tpr);
+  const float launch_ms = batch_run(ctx, J, nsys, opt, sc.threads, tpr, sc.order);
   std::vector<BatchOut> out(nsys);
   CP_CUDA(cudaMemcpyAsync(out.data(), J.d_out, nsys * sizeof(BatchOut), cudaMemcpyDeviceToHost,
                           J.s));
@@ -720,27 +724,36 @@ void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solv
 }
 
 BatchSchedule batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
-                         const double* const* b, const cp_solve_opts* o, float* ms12) {
+                         const double* const* b, const cp_solve_opts* o, float* ms12,
+                         float* ms_order) {
   cp_solve_opts opt;
   cp_solve_opts_default(&opt);
   if (o) opt = *o;
   BatchJob J;
   J.s = ctx->main;
   batch_prepare(ctx, J, nsys, mats, solver, b, nullptr, opt, true);
-  BatchSchedule best{0, 1};
+  BatchSchedule best{0, 1, 0};
   float best_ms = 0.f;
   for (int c = 0; c < 4; ++c)
     for (int v = 0; v < 3; ++v) {
-      const BatchSchedule sc{kBatchThreads[c], kBatchTpv[v]};
+      const BatchSchedule sc{kBatchThreads[c], kBatchTpv[v], 0};
       const std::vector<int> tpr(nsys, sc.tpv);
-      batch_run(ctx, J, nsys, opt, sc.threads, tpr);  // warm-up: module load, caches
-      const float ms = batch_run(ctx, J, nsys, opt, sc.threads, tpr);
+      batch_run(ctx, J, nsys, opt, sc.threads, tpr, 0);  // warm-up: module load, caches
+      const float ms = batch_run(ctx, J, nsys, opt, sc.threads, tpr, 0);
       if (ms12) ms12[c * 3 + v] = ms;
       if (!best.threads || ms < best_ms) {
         best = sc;
         best_ms = ms;
       }
     }
+  // the packing order at the best shape: the caller's order against largest first
+  {
+    const std::vector<int> tpr(nsys, best.tpv);
+    batch_run(ctx, J, nsys, opt, best.threads, tpr, 1);
+    const float ms = batch_run(ctx, J, nsys, opt, best.threads, tpr, 1);
+    if (ms_order) *ms_order = ms;
+    if (ms < best_ms) best.order = 1;
+  }
   CP_CUDA(cudaStreamSynchronize(J.s));
   if (ctx->device >= 0 && ctx->device < kSchedDevices) {
     std::lock_guard<std::mutex> lock(g_sched_mu);

@@ -487,13 +487,15 @@ double cp_gate_payback(const cp_gate* gate, int32_t fmt, int64_t nnz) {
 
 cp_status cp_batch_tune(cp_ctx* ctx, int32_t nsys, cp_mat* const* mats, const int32_t* solver,
                         const double* const* b, const cp_solve_opts* opts,
-                        int32_t* best_threads, int32_t* best_threads_per_row, float* ms) {
+                        int32_t* best_threads, int32_t* best_threads_per_row,
+                        int32_t* best_order, float* ms, float* ms_order) {
   return guard([&] {
     CP_REQUIRE(ctx, CP_ERR_INVALID, "NULL context");
     use_device(ctx);
-    const BatchSchedule best = batch_tune(ctx, nsys, mats, solver, b, opts, ms);
+    const BatchSchedule best = batch_tune(ctx, nsys, mats, solver, b, opts, ms, ms_order);
     if (best_threads) *best_threads = best.threads;
     if (best_threads_per_row) *best_threads_per_row = best.tpv;
+    if (best_order) *best_order = best.order;
   });
 }
 
@@ -506,12 +508,13 @@ cp_status cp_batch_tpr(cp_ctx* ctx, cp_mat* m, int32_t* tpr) {
 }
 
 cp_status cp_batch_schedule(cp_ctx* ctx, int64_t mean_rows, int32_t has_gmres, int32_t* threads,
-                            int32_t* threads_per_row) {
+                            int32_t* threads_per_row, int32_t* order) {
   return guard([&] {
     CP_REQUIRE(ctx && threads && threads_per_row, CP_ERR_INVALID, "NULL argument");
     const BatchSchedule sc = batch_schedule(ctx, mean_rows, has_gmres != 0);
     *threads = sc.threads;
     *threads_per_row = sc.tpv;
+    if (order) *order = sc.order;
   });
 }
 

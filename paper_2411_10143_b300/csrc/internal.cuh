@@ -438,16 +438,20 @@ int64_t scratch_floats_api(int64_t N, int d, int h1, int h2, int k);
 struct BatchSchedule {
   int threads;
   int tpv;
+  int order = 0;  // packing: 0 = largest systems first, 1 = in the caller's order
 };
 // threads / tpv = 0: the schedule of the batch's class (tuned, else by size)
 void batch_solve(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
                  const double* const* b, double* const* x, const cp_solve_opts* o,
                  cp_solve_info* infos, int threads, int tpv);
 // the autotuner: times 128/256/512/1024 threads per system x 1/4/16 threads per
-// row on this batch (scratch solutions), records the fastest for the batch's
-// class, returns it; ms12[threads index * 3 + tpv index]
+// row on this batch (scratch solutions, largest systems first), then the best
+// shape in the caller's order; records the fastest for the batch's class,
+// returns it; ms12[threads index * 3 + tpv index], ms_order (may be null) the
+// best shape in the caller's order
 BatchSchedule batch_tune(cp_ctx* ctx, int nsys, cp_mat* const* mats, const int32_t* solver,
-                         const double* const* b, const cp_solve_opts* o, float* ms12);
+                         const double* const* b, const cp_solve_opts* o, float* ms12,
+                         float* ms_order);
 // the schedule cp_batch_solve uses for a batch class (tuned, else by size)
 BatchSchedule batch_schedule(cp_ctx* ctx, int64_t mean_rows, bool has_gmres);
 // the BATCH_TPR classifier's threads per row for m (cp_batch_tpr), 0 without a model

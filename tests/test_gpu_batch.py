@@ -93,16 +93,21 @@ def test_autotuner_times_every_candidate_and_its_choice_is_used():
     rhs = [oracle.spmv(A, W.vector(A.nrows, q + 70)) for q, (A, _) in enumerate(sys)]
     bs = [torch.as_tensor(b, device="cuda") for b in rhs]
     opts = C.default_opts(tol=1e-10, inner_tol=1e-5, precision=C.PREC_FP32_IR)
-    best, ms = ctx.batch_tune(mats, [s for _, s in sys], bs, opts)
+    best, ms, (order, ms_order) = ctx.batch_tune(mats, [s for _, s in sys], bs, opts,
+                                                 with_order=True)
     assert best[0] in (128, 256, 512, 1024) and best[1] in (1, 4, 16)
     assert len(ms) == 12 and all(t > 0 for t in ms.values())
     assert ms[best] == min(ms.values())
+    # the packing order: the caller's order is kept only where it timed faster
+    assert ms_order > 0 and order == (1 if ms_order < ms[best] else 0)
     mean = sum(A.nrows for A, _ in sys) // len(sys)
     assert ctx.batch_schedule(mean, False) == best
+    assert ctx.batch_schedule(mean, False, with_order=True) == best + (order,)
     # a class that was not tuned keeps the size rule, a thread per row
     assert ctx.batch_schedule(100, True) == (128, 1)
     assert ctx.batch_schedule(200000, True) == (1024, 1)
     assert ctx.batch_schedule(1000, True) == (256, 1) and ctx.batch_schedule(4000, True) == (512, 1)
+    assert ctx.batch_schedule(4000, True, with_order=True) == (512, 1, 0)
     check(ctx, sys, 0, seeds=[q + 30 for q in range(len(sys))])
     ctx.close()
 
