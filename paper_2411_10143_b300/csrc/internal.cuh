@@ -261,6 +261,11 @@ struct cp_ctx {
   cp::MappedPool mapped;  // host-mapped pages reused by the solves
   cp::EventPool events;   // CUDA events reused by the solves
   cp::BatchGraphs* batch_graphs = nullptr;  // instantiated batched-solve graphs (batch.cu)
+  // a serving lane's context: the server's count of lanes holding a job.  Its
+  // solves use the persistent (cooperative) kernels only while it is the one
+  // busy lane, and ask a running one to return when another lane gets work, so
+  // no two cooperative grids ever share the device (null: not a serving lane)
+  const std::atomic<int>* lanes_busy = nullptr;
 };
 
 struct cp_mat {

@@ -783,6 +783,12 @@ struct QueueLimit {
   }
 };
 
+// Whether this solve has the device to itself as far as the persistent
+// kernels go: always, except in a serving lane while another lane holds a job.
+static bool device_to_ourselves(const cp_ctx* ctx) {
+  return !ctx->lanes_busy || ctx->lanes_busy->load(std::memory_order_acquire) <= 1;
+}
+
 // SpMV of the configuration in force (T selects FP64 or FP32 values).
 template <typename T>
 static int spmv_cur(ConfigSource& cs, const T* x, T* y, const T* dotv, double* part,
@@ -853,7 +859,8 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
       // interleaving with the side kernels.
       const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire) ||
                              cs.ch->side_gpu_idle.load(std::memory_order_acquire);
-      if (cs.persistent_now() && side_idle && persist_supported<T>(m, cs.cur)) {
+      if (cs.persistent_now() && side_idle && device_to_ourselves(ctx) &&
+          persist_supported<T>(m, cs.cur)) {
         // one cooperative launch runs iterations [it, maxit) until convergence, a
         // breakdown, or the host asks it to return at an iteration boundary
         // because the cascade published a new configuration
@@ -892,11 +899,13 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
           if (q == cudaSuccess) break;
           if (q != cudaErrorNotReady) CP_CUDA(q);
           // return at the next iteration boundary when a configuration was
-          // published, or when the side thread needs the GPU again
-          if (cs.ch && !*ws.yield_h &&
-              (cs.ch->count.load(std::memory_order_acquire) > cs.applied ||
-               (!cs.ch->finished.load(std::memory_order_acquire) &&
-                !cs.ch->side_gpu_idle.load(std::memory_order_acquire))))
+          // published, when the side thread needs the GPU again, or when
+          // another serving lane got work
+          if (!*ws.yield_h &&
+              ((cs.ch && (cs.ch->count.load(std::memory_order_acquire) > cs.applied ||
+                          (!cs.ch->finished.load(std::memory_order_acquire) &&
+                           !cs.ch->side_gpu_idle.load(std::memory_order_acquire)))) ||
+               !device_to_ourselves(ctx)))
             *(volatile int*)ws.yield_h = 1;
           std::this_thread::sleep_for(std::chrono::microseconds(20));
         }
@@ -1047,7 +1056,8 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
       // because a new configuration was published or the side needs the GPU.
       const bool side_idle = !cs.ch || cs.ch->finished.load(std::memory_order_acquire) ||
                              cs.ch->side_gpu_idle.load(std::memory_order_acquire);
-      if (cs.persistent_now() && side_idle && gm_persist_supported<T>(m, cs.cur, mrest)) {
+      if (cs.persistent_now() && side_idle && device_to_ourselves(ctx) &&
+          gm_persist_supported<T>(m, cs.cur, mrest)) {
         int* yield_d = ws.yield();
         *(volatile int*)ws.yield_h = 0;
         ws.mir->exit_kind = 0;
@@ -1091,10 +1101,11 @@ static LoopResult run_gmres(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const 
           const cudaError_t q = cudaEventQuery(e1);
           if (q == cudaSuccess) break;
           if (q != cudaErrorNotReady) CP_CUDA(q);
-          if (cs.ch && !*ws.yield_h &&
-              (cs.ch->count.load(std::memory_order_acquire) > cs.applied ||
-               (!cs.ch->finished.load(std::memory_order_acquire) &&
-                !cs.ch->side_gpu_idle.load(std::memory_order_acquire))))
+          if (!*ws.yield_h &&
+              ((cs.ch && (cs.ch->count.load(std::memory_order_acquire) > cs.applied ||
+                          (!cs.ch->finished.load(std::memory_order_acquire) &&
+                           !cs.ch->side_gpu_idle.load(std::memory_order_acquire)))) ||
+               !device_to_ourselves(ctx)))
             *(volatile int*)ws.yield_h = 1;
           std::this_thread::sleep_for(std::chrono::microseconds(20));
         }

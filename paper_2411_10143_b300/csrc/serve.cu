@@ -13,6 +13,7 @@
 // Requests that arrive while others run are admitted as soon as a lane and
 // memory free up.  Every completion records submit / start / done times.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -42,6 +43,7 @@ struct cp_server {
   };
   std::vector<std::deque<Job>> lane_jobs;
   std::vector<int> lane_busy;
+  std::atomic<int> busy{0};  // lanes holding a job (read by the lanes' solves)
   std::deque<double> pending_submit;  // submit time of every pending request
   std::vector<cp_result> done;
   int64_t in_use_bytes = 0;
@@ -113,9 +115,11 @@ static void run_job(cp_server* S, int lane, cp_server::Job& job) {
     } else {
       const cp_request& r = job.reqs[0];
       o.mode = S->opts.mode;
-      // lanes run concurrently: cooperative grids sized for the whole device
-      // must not share it, so every lane uses one launch per step
-      o.iteration_kernel = 1;
+      // lanes run concurrently and cooperative grids sized for the whole
+      // device must not share it: the solve takes the persistent kernels only
+      // while this is the one busy lane, and a running one returns at its next
+      // iteration boundary once another lane gets work (ctx->lanes_busy)
+      o.iteration_kernel = 0;
       cp_solve_info info;
       std::memset(&info, 0, sizeof(info));
       cp_status st = CP_OK;
@@ -145,6 +149,7 @@ static void run_job(cp_server* S, int lane, cp_server::Job& job) {
   S->in_use_bytes -= job.bytes;
   S->inflight -= (int64_t)job.reqs.size();
   S->lane_busy[lane] = 0;
+  S->busy.fetch_sub(1, std::memory_order_acq_rel);
   S->cv.notify_all();
 }
 
@@ -231,6 +236,7 @@ static void scheduler_loop(cp_server* S) {
     }
     S->in_use_bytes += job.bytes;
     S->lane_busy[lane] = 1;
+    S->busy.fetch_add(1, std::memory_order_acq_rel);  // before the job can start
     S->lane_jobs[lane].push_back(std::move(job));
     S->lane_cv.notify_all();
   }
@@ -297,6 +303,7 @@ cp_status cp_server_create(cp_ctx* ctx, const cp_server_opts* opts, cp_server** 
         if (ms.loaded) model_install(c, k, ms.h1, ms.h2, ms.k, ms.d_params, ms.d_mu, ms.d_sd,
                                      c->main, ms.gen);
       }
+      c->lanes_busy = &S->busy;
       S->lane_ctx.push_back(c);
     }
     for (int l = 0; l < L; ++l) S->workers.emplace_back(worker_loop, S, l);
