@@ -978,9 +978,13 @@ static LoopResult run_cg(cp_ctx* ctx, ConfigSource& cs, Workspace& ws, const T* 
     unsigned long long tn[6];
     CP_CUDA(cudaMemcpy(tn, st->t_ns, sizeof(tn), cudaMemcpyDeviceToHost));
     const double k = 1e-3 / (cs.persist_iters - persist_iters0);
-    trace("persistent CG per iteration (us): spmv %.2f bar %.2f update %.2f bar %.2f "
-          "direction %.2f bar %.2f", tn[0] * k, tn[1] * k, tn[2] * k, tn[3] * k, tn[4] * k,
-          tn[5] * k);
+    if (tn[4] == 0 && tn[5] == 0)  // the two-barrier kernel (FP32)
+      trace("persistent CG per iteration (us): spmv+direction %.2f bar %.2f update %.2f "
+            "bar %.2f", tn[0] * k, tn[1] * k, tn[2] * k, tn[3] * k);
+    else
+      trace("persistent CG per iteration (us): spmv %.2f bar %.2f update %.2f bar %.2f "
+            "direction %.2f bar %.2f", tn[0] * k, tn[1] * k, tn[2] * k, tn[3] * k, tn[4] * k,
+            tn[5] * k);
   }
   return res;
 }

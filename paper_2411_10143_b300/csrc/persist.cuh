@@ -130,29 +130,32 @@ struct PersistMat {
   int coo_vec = 0;  // all three 16-byte aligned: vector loads of 8 entries
 };
 
-// y = alpha A x + beta y (GEN) or y = A x over the rows of the format's
-// grid-stride mapping; returns the thread's share of (y, dotv) when DOT.  x is
-// read through L2 (the persistent kernels rewrite it between phases).
-template <typename T, int F, int TPV, bool GEN, bool DOT>
+// y = alpha A x + beta y (GEN = kRowGen) or y = A x (kRowSolve) over the rows
+// of the format's grid-stride mapping; returns the thread's share of (A x, dotv)
+// when DOT.  GEN = kRowCgRec: the two-barrier CG kernel's fused direction step
+// (spmv_rows.cuh), pw being p.  x is read through L2 (the persistent kernels
+// rewrite it between phases).
+template <typename T, int F, int TPV, int GEN, bool DOT>
 __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t* so,
-                                          const T* x, T* y, T alpha, T beta, const T* dotv) {
+                                          const T* x, T* y, T alpha, T beta, const T* dotv,
+                                          T* pw = nullptr) {
   const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   if constexpr (F == kPersistCsrScalar)
     return csr_scalar_rows<T, GEN, DOT, true>(a.n, a.rp, a.ci, a.v, x, y, alpha, beta, dotv,
-                                              tid, stride);
+                                              tid, stride, pw);
   else if constexpr (F == kPersistCsrVector)
     return csr_vector_rows<T, TPV, GEN, DOT, true>(a.n, a.rp, a.ci, a.v, x, y, alpha, beta,
-                                                   dotv, tid >> 5, stride >> 5);
+                                                   dotv, tid >> 5, stride >> 5, pw);
   else if constexpr (F == kPersistEll || F == kPersistHyb)  // (HYB: the ELL rows here)
     return ell_rows<T, GEN, DOT, true>(a.n, a.K, a.ld, a.ec, a.ev, x, y, alpha, beta, dotv, tid,
-                                       stride);
+                                       stride, pw);
   else if constexpr (F == kPersistSell)
     return sell_chunks<T, GEN, DOT, true>(a.n, a.nchunks, a.perm, a.clen, a.cptr, a.sc, a.sv, x,
-                                          y, alpha, beta, dotv, tid >> 5, stride >> 5);
+                                          y, alpha, beta, dotv, tid >> 5, stride >> 5, pw);
   else
     return dia_rows<T, GEN, DOT, true>(a.n, a.n, a.ndiag, so, a.dv, x, y, alpha, beta, dotv,
-                                       tid, stride);
+                                       tid, stride, pw);
 }
 
 // HYB's COO tail in a persistent SpMV phase: yc[row] += val * x[col] for every

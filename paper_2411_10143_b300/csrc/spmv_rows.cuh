@@ -1,11 +1,12 @@
 // Row loops of the row-parallel SpMV formats (CSR-scalar, CSR-vector, ELL,
 // SELL-C-sigma, DIA).  Each walks its rows grid-stride from the caller's
 // thread (or warp) index, writes y = A x (or alpha A x + beta y) and returns the
-// thread's share of sum_i y_i * dotv_i when DOT is set.  The SpMV kernels of
-// spmv.cu wrap them one launch each; the persistent CG kernel runs them as the
-// SpMV phase of every iteration with COH set, so the x and dot vectors (which
-// that kernel rewrites every iteration) are read through L2, never from a
-// possibly stale L1 or read-only-cache line.
+// thread's share of sum_i (A x)_i * dotv_i when DOT is set; the two-barrier
+// persistent CG kernel also runs its direction update in them (kRowCgRec).  The
+// SpMV kernels of spmv.cu wrap them one launch each; the persistent CG kernels
+// run them as the SpMV phase of every iteration with COH set, so the x and dot
+// vectors (which those kernels rewrite every iteration) are read through L2,
+// never from a possibly stale L1 or read-only-cache line.
 #pragma once
 
 #include "common.cuh"
@@ -25,16 +26,42 @@ __device__ __forceinline__ void store_row(T* y, int64_t i, T s, T alpha, T beta)
   }
 }
 
+// What a row loop does with a finished row sum s = (A x)_i (its GEN argument):
+constexpr int kRowSolve = 0;  // y_i = s; DOT: the share of sum s dotv_i
+constexpr int kRowGen = 1;    // y_i = alpha s + beta y_i; DOT: the share of sum s dotv_i
+// The persistent CG kernel's fused direction step, x being r+ and y the
+// previous A p: y_i = s + beta y_i (A p+ = A r+ + beta A p), pw_i = r+_i +
+// beta pw_i (p+ = r+ + beta p); returns the share of (p+, A p+).  Every value
+// goes through L2 (the kernel's other phases write them on other SMs).
+constexpr int kRowCgRec = 2;
+
+template <typename T, int GEN, bool DOT, bool COH>
+__device__ __forceinline__ T finish_row(T* __restrict__ y, int64_t i, T s, T alpha, T beta,
+                                        const T* __restrict__ dotv, const T* __restrict__ x,
+                                        T* __restrict__ pw, T acc) {
+  if constexpr (GEN == kRowCgRec) {
+    const T q = fma(beta, ld_cg(y + i), s);
+    const T p = fma(beta, ld_cg(pw + i), ld_cg(x + i));
+    y[i] = q;
+    pw[i] = p;
+    return fma(p, q, acc);
+  } else {
+    store_row<T, GEN != kRowSolve>(y, i, s, alpha, beta);
+    if (DOT) acc = fma(s, COH ? ld_cg(dotv + i) : dotv[i], acc);
+    return acc;
+  }
+}
+
 // ------------------------------------------------------------------ CSR scalar
 // One thread per row; entries in chunks of 4 so the 8 index / value loads are
 // independent, then 4 gathers.
-template <typename T, bool GEN, bool DOT, bool COH = false>
+template <typename T, int GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T csr_scalar_rows(int64_t n, const int32_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci,
                                              const T* __restrict__ v, const T* __restrict__ x,
                                              T* __restrict__ y, T alpha, T beta,
                                              const T* __restrict__ dotv, int64_t tid,
-                                             int64_t stride) {
+                                             int64_t stride, T* __restrict__ pw = nullptr) {
   T acc = 0;
   for (int64_t i = tid; i < n; i += stride) {
     const int s = rp[i], e = rp[i + 1];
@@ -52,8 +79,7 @@ __device__ __forceinline__ T csr_scalar_rows(int64_t n, const int32_t* __restric
       for (int u = 0; u < 4; ++u)
         if (k0 + u < e) sum = fma(w[u], ld_x<COH>(x + c[u]), sum);
     }
-    store_row<T, GEN>(y, i, sum, alpha, beta);
-    if (DOT) acc = fma(sum, COH ? ld_cg(dotv + i) : dotv[i], acc);
+    acc = finish_row<T, GEN, DOT, COH>(y, i, sum, alpha, beta, dotv, x, pw, acc);
   }
   return acc;
 }
@@ -62,13 +88,13 @@ __device__ __forceinline__ T csr_scalar_rows(int64_t n, const int32_t* __restric
 // TPV lanes per row; the warp walks its rows in lock step so the shuffles of
 // the row reduction always see the full warp.  warp / nwarps: global warp index
 // and count.
-template <typename T, int TPV, bool GEN, bool DOT, bool COH = false>
+template <typename T, int TPV, int GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T csr_vector_rows(int64_t n, const int32_t* __restrict__ rp,
                                              const int32_t* __restrict__ ci,
                                              const T* __restrict__ v, const T* __restrict__ x,
                                              T* __restrict__ y, T alpha, T beta,
                                              const T* __restrict__ dotv, int64_t warp,
-                                             int64_t nwarps) {
+                                             int64_t nwarps, T* __restrict__ pw = nullptr) {
   constexpr int RPW = 32 / TPV;  // rows per warp step
   const int lane = threadIdx.x & 31;
   const int sub = lane % TPV;
@@ -91,8 +117,7 @@ __device__ __forceinline__ T csr_vector_rows(int64_t n, const int32_t* __restric
 #pragma unroll
     for (int o = TPV / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (sub == 0 && i < n) {
-      store_row<T, GEN>(y, i, sum, alpha, beta);
-      if (DOT) acc = fma(sum, COH ? ld_cg(dotv + i) : dotv[i], acc);
+      acc = finish_row<T, GEN, DOT, COH>(y, i, sum, alpha, beta, dotv, x, pw, acc);
     }
   }
   return acc;
@@ -155,11 +180,12 @@ __device__ __forceinline__ void for_slots_t(int64_t w, F&& f) {
 // Thread per row pair (i and i + stride); chunks of 4 slots give 16 independent
 // coalesced loads before the gathers; padding (col -1) only follows a row's
 // entries, so once both rows show padding the pair is done.
-template <typename T, bool GEN, bool DOT, bool COH = false>
+template <typename T, int GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T ell_rows(int64_t n, int64_t K, int64_t ld,
                                       const int32_t* __restrict__ ec, const T* __restrict__ ev,
                                       const T* __restrict__ x, T* __restrict__ y, T alpha, T beta,
-                                      const T* __restrict__ dotv, int64_t tid, int64_t stride) {
+                                      const T* __restrict__ dotv, int64_t tid, int64_t stride,
+                                      T* __restrict__ pw = nullptr) {
   T acc = 0;
   for (int64_t i0 = tid; i0 < n; i0 += 2 * stride) {
     const int64_t i1 = i0 + stride;
@@ -183,11 +209,9 @@ __device__ __forceinline__ T ell_rows(int64_t n, int64_t K, int64_t ld,
       }
       return c0[r - 1] < 0 && c1[r - 1] < 0;
     });
-    store_row<T, GEN>(y, i0, s0, alpha, beta);
-    if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
+    acc = finish_row<T, GEN, DOT, COH>(y, i0, s0, alpha, beta, dotv, x, pw, acc);
     if (has1) {
-      store_row<T, GEN>(y, i1, s1, alpha, beta);
-      if (DOT) acc = fma(s1, COH ? ld_cg(dotv + i1) : dotv[i1], acc);
+      acc = finish_row<T, GEN, DOT, COH>(y, i1, s1, alpha, beta, dotv, x, pw, acc);
     }
   }
   return acc;
@@ -196,7 +220,7 @@ __device__ __forceinline__ T ell_rows(int64_t n, int64_t K, int64_t ld,
 // ------------------------------------------------------------------ SELL-C-sigma (C = 32)
 // One warp per chunk, lane r on slot r: every load of the chunk is one
 // contiguous 128-byte (col) and 256-byte (FP64 val) transaction.
-template <typename T, bool GEN, bool DOT, bool COH = false>
+template <typename T, int GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
                                          const int32_t* __restrict__ perm,
                                          const int32_t* __restrict__ clen,
@@ -205,7 +229,7 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
                                          const T* __restrict__ sv, const T* __restrict__ x,
                                          T* __restrict__ y, T alpha, T beta,
                                          const T* __restrict__ dotv, int64_t warp,
-                                         int64_t nwarps) {
+                                         int64_t nwarps, T* __restrict__ pw = nullptr) {
   const int lane = threadIdx.x & 31;
   T acc = 0;
   for (int64_t c = warp; c < nchunks; c += nwarps) {
@@ -228,8 +252,7 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
     const int64_t s = c * 32 + lane;
     if (s < n) {
       const int64_t row = perm ? perm[s] : s;
-      store_row<T, GEN>(y, row, sum, alpha, beta);
-      if (DOT) acc = fma(sum, COH ? ld_cg(dotv + row) : dotv[row], acc);
+      acc = finish_row<T, GEN, DOT, COH>(y, row, sum, alpha, beta, dotv, x, pw, acc);
     }
   }
   return acc;
@@ -240,11 +263,12 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
 // holds the offsets (in shared memory); values and x are read contiguously
 // across the warp (no index arrays, no gather).  Every diagonal slot is real
 // (exact remainder chunk), since FP64 FMAs are as scarce as bytes here.
-template <typename T, bool GEN, bool DOT, bool COH = false>
+template <typename T, int GEN, bool DOT, bool COH = false>
 __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const int32_t* so,
                                       const T* __restrict__ dv, const T* __restrict__ x,
                                       T* __restrict__ y, T alpha, T beta,
-                                      const T* __restrict__ dotv, int64_t tid, int64_t stride) {
+                                      const T* __restrict__ dotv, int64_t tid, int64_t stride,
+                                      T* __restrict__ pw = nullptr) {
   T acc = 0;
   // rows i with every i + offset inside [0, ncols) (all but a band at each end
   // for a stencil) take a loop without per-slot bounds checks
@@ -303,11 +327,9 @@ __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const
         return false;
       });
     }
-    store_row<T, GEN>(y, i0, s0, alpha, beta);
-    if (DOT) acc = fma(s0, COH ? ld_cg(dotv + i0) : dotv[i0], acc);
+    acc = finish_row<T, GEN, DOT, COH>(y, i0, s0, alpha, beta, dotv, x, pw, acc);
     if (has1) {
-      store_row<T, GEN>(y, i1, s1, alpha, beta);
-      if (DOT) acc = fma(s1, COH ? ld_cg(dotv + i1) : dotv[i1], acc);
+      acc = finish_row<T, GEN, DOT, COH>(y, i1, s1, alpha, beta, dotv, x, pw, acc);
     }
   }
   return acc;

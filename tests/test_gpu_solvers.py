@@ -469,7 +469,10 @@ def test_two_tier_features_skip_the_feature_pass_on_a_short_small_solve():
     c = C.Context(0)
     one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
     c.gate_set(fixed_gate(feat_ms=20.0, small_rows=100_000))
-    A = W.diagonally_dominant(W.poisson2d(300), margin=0.5)  # n 90,000: tens of iterations
+    # n 90,000: about 120 iterations, far fewer than the 500 SpMVs the features and
+    # a conversion cost, yet long enough (a few ms) for the side thread's verdict to
+    # land before the solve ends
+    A = W.diagonally_dominant(W.poisson2d(300), margin=0.05)
     b = rhs(A, 33)
     x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
     assert true_relres(A, x, b) <= 1e-10
