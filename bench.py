@@ -181,8 +181,8 @@ def cg_iteration_bytes(A, fmt=None):
 # profiles/k_cg_persist_dia_poisson3d_128.md.
 PERSIST_KERNEL_SOURCES = ("cg_persist.cu", "persist.cuh", "spmv_rows.cuh", "common.cuh")
 PERSIST_TRAFFIC = {"format": "DIA", "n": 2097152,
-                   "sha256": "c68c0e3bd5e3bdb1b487a8f0a09ee45d61314e7149cd0a94c50826520c654c8a",
-                   "dram_bytes_per_iteration": 166558684.2}
+                   "sha256": "43c87cd8b5ac0c937ca7a7e08fce210f74996a49dbda0ec2d44b7743c881d11c",
+                   "dram_bytes_per_iteration": 165685131.6}
 
 
 def persist_sources_sha256():

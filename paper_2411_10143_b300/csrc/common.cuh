@@ -25,10 +25,18 @@ template <typename T>
 __device__ __forceinline__ T ld_cg(const T* p) {
   return __ldcg(p);
 }
-// x gathers: read-only path in ordinary kernels, L2 in persistent ones.
-template <bool COH, typename T>
+// x gathers: read-only path in ordinary kernels.  Persistent kernels rewrite x
+// between phases, so the read-only path is out; they load through L1
+// (ld.global.ca), which is coherent enough here: every read of x follows the
+// grid barrier's acquire (thread 0's ld.acquire.gpu, then the block barrier),
+// and a weak load ordered after an acquire sees every write ordered before the
+// matching release (the PTX memory model), whichever SM made it.  L2ONLY keeps
+// a persistent kernel's gathers in L2 (ld.global.cg), for a loop where reuse in
+// L1 measured no gain.
+template <bool COH, bool L2ONLY = false, typename T>
 __device__ __forceinline__ T ld_x(const T* p) {
-  if constexpr (COH) return __ldcg(p);
+  if constexpr (COH && L2ONLY) return __ldcg(p);
+  else if constexpr (COH) return __ldca(p);
   else return __ldg(p);
 }
 

@@ -133,8 +133,8 @@ struct PersistMat {
 // y = alpha A x + beta y (GEN = kRowGen) or y = A x (kRowSolve) over the rows
 // of the format's grid-stride mapping; returns the thread's share of (A x, dotv)
 // when DOT.  GEN = kRowCgRec: the two-barrier CG kernel's fused direction step
-// (spmv_rows.cuh), pw being p.  x is read through L2 (the persistent kernels
-// rewrite it between phases).
+// (spmv_rows.cuh), pw being p.  x is never read through the read-only path (the
+// persistent kernels rewrite it between phases; ld_x).
 template <typename T, int F, int TPV, int GEN, bool DOT>
 __device__ __forceinline__ T persist_spmv(const PersistMat<T>& a, const int32_t* so,
                                           const T* x, T* y, T alpha, T beta, const T* dotv,

@@ -3,10 +3,11 @@
 // thread (or warp) index, writes y = A x (or alpha A x + beta y) and returns the
 // thread's share of sum_i (A x)_i * dotv_i when DOT is set; the two-barrier
 // persistent CG kernel also runs its direction update in them (kRowCgRec).  The
-// SpMV kernels of spmv.cu wrap them one launch each; the persistent CG kernels
-// run them as the SpMV phase of every iteration with COH set, so the x and dot
-// vectors (which those kernels rewrite every iteration) are read through L2,
-// never from a possibly stale L1 or read-only-cache line.
+// SpMV kernels of spmv.cu wrap them one launch each; the persistent kernels run
+// them as the SpMV phase of every iteration with COH set, so the x and dot
+// vectors (which those kernels rewrite every iteration) never come from the
+// read-only path: x through L1 after the grid barrier's acquire (ld_x), the
+// dot vector through L2.
 #pragma once
 
 #include "common.cuh"
@@ -259,6 +260,13 @@ __device__ __forceinline__ T sell_chunks(int64_t n, int64_t nchunks,
 }
 
 // ------------------------------------------------------------------ DIA
+// Persistent kernels gather x through L1 (ld_x), except in FP64: there the FP64
+// pipe bounds the loop, and the reuse of the neighbouring diagonals' lines in
+// L1 measured 0.4 % slower than L2 alone (3D Poisson 128^3, FP64 CG: 59.5
+// against 59.2 us an iteration; FP32 inner CG 27.1 against 27.5 us).
+template <typename T>
+constexpr bool kDiaL2 = sizeof(T) == 8;
+
 // Thread per row pair (i and i + stride, so twice the loads in flight); so[]
 // holds the offsets (in shared memory); values and x are read contiguously
 // across the warp (no index arrays, no gather).  Every diagonal slot is real
@@ -292,9 +300,9 @@ __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const
           const int64_t off = so[d0 + u];
           const int64_t base = (d0 + u) * n;
           w0[u] = ld_stream(dv + base + i0);
-          x0[u] = ld_x<COH>(x + i0 + off);
+          x0[u] = ld_x<COH, kDiaL2<T>>(x + i0 + off);
           w1[u] = ld_stream(dv + base + i1);
-          x1[u] = ld_x<COH>(x + i1 + off);
+          x1[u] = ld_x<COH, kDiaL2<T>>(x + i1 + off);
         }
 #pragma unroll
         for (int u = 0; u < r; ++u) {
@@ -315,9 +323,9 @@ __device__ __forceinline__ T dia_rows(int64_t n, int64_t ncols, int ndiag, const
           const bool in1 = has1 && c1 >= 0 && c1 < ncols;
           const int64_t base = (d0 + u) * n;
           w0[u] = in0 ? ld_stream(dv + base + i0) : T(0);
-          x0[u] = in0 ? ld_x<COH>(x + c0) : T(0);
+          x0[u] = in0 ? ld_x<COH, kDiaL2<T>>(x + c0) : T(0);
           w1[u] = in1 ? ld_stream(dv + base + i1) : T(0);
-          x1[u] = in1 ? ld_x<COH>(x + c1) : T(0);
+          x1[u] = in1 ? ld_x<COH, kDiaL2<T>>(x + c1) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < r; ++u) {

@@ -357,6 +357,21 @@ def fixed_gate(speedup=2.0, conv_ms=5.0, spmv_ms=0.05, feat_ms=0.0, small_rows=0
                              "feat_a_ms": feat_ms, "feat_b_ms": 0.0, "small_rows": small_rows})
 
 
+def solve_until_the_gate_decides(ctx, A, b, tries=3, **kw):
+    """An asynchronous solve, repeated (up to `tries` times) until the side
+    thread's gate verdict landed before the solve ended.  On a solve of a few
+    milliseconds the host may schedule the side thread late enough that the
+    solve converges first and no verdict is recorded (gate_remaining stays -1);
+    that says nothing about the verdict, so the test looks at the first solve
+    that has one."""
+    for _ in range(tries):
+        x, info = gpu_solve(ctx, A, b, mode=C.MODE_ASYNC, **kw)
+        assert true_relres(A, x, b) <= kw.get("tol", 1e-10)
+        if info.gate_remaining >= 0.0 or info.gate_declined > 0:
+            break
+    return x, info
+
+
 def test_cost_aware_gate_keeps_the_default_on_a_short_solve():
     """A well-conditioned system converges in a few dozen iterations: with a
     conversion worth 100 default SpMVs and a 2x predicted speedup the gate keeps
@@ -369,8 +384,7 @@ def test_cost_aware_gate_keeps_the_default_on_a_short_solve():
     c.gate_set(fixed_gate())
     A = W.diagonally_dominant(W.poisson2d(1024), margin=0.5)  # a few dozen iterations
     b = rhs(A, 31)
-    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
-    assert true_relres(A, x, b) <= 1e-10
+    x, info = solve_until_the_gate_decides(c, A, b, tol=1e-10)
     diag = (info.gate_declined, info.gate_remaining, info.gate_cost_spmvs, info.iters)
     assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR, diag
     assert max(info.switch_iter) == -1 and info.t_convert_ms == 0.0
@@ -454,8 +468,7 @@ def test_shipped_gate_keeps_csr_where_the_predicted_format_barely_gains():
     assert "GATE_NEIGHBOURS" in models.load_default(c)
     A = W.poisson3d(48)
     b = rhs(A, 34)
-    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
-    assert true_relres(A, x, b) <= 1e-10
+    x, info = solve_until_the_gate_decides(c, A, b, tol=1e-10)
     diag = (info.gate_declined, info.gate_remaining, info.gate_cost_spmvs, repr(info.final_cfg))
     assert info.gate_declined == 1 and info.final_cfg.fmt == C.FMT_CSR, diag
     c.close()
@@ -470,12 +483,11 @@ def test_two_tier_features_skip_the_feature_pass_on_a_short_small_solve():
     one_hot_model(c, C.STAGE_FORMAT, C.FMT_ELL)
     c.gate_set(fixed_gate(feat_ms=20.0, small_rows=100_000))
     # n 90,000: about 120 iterations, far fewer than the 500 SpMVs the features and
-    # a conversion cost, yet long enough (a few ms) for the side thread's verdict to
-    # land before the solve ends
+    # a conversion cost, yet long enough (a few ms) that the side thread's verdict
+    # usually lands before the solve ends
     A = W.diagonally_dominant(W.poisson2d(300), margin=0.05)
     b = rhs(A, 33)
-    x, info = gpu_solve(c, A, b, tol=1e-10, mode=C.MODE_ASYNC)
-    assert true_relres(A, x, b) <= 1e-10
+    x, info = solve_until_the_gate_decides(c, A, b, tol=1e-10)
     diag = (info.gate_declined, info.gate_remaining, info.gate_cost_spmvs, info.iters)
     assert info.gate_declined == 2 and info.t_features_ms == 0.0, diag
     assert info.final_cfg.fmt == C.FMT_CSR and max(info.switch_iter) == -1
