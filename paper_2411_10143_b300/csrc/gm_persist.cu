@@ -13,7 +13,7 @@
 // each block then folds into its own rows.)
 //
 // Step j of a cycle, w = column j + 1 of V, orthogonalised by modified
-// Gram-Schmidt in groups of g columns (g = 4 in FP64, 8 in FP32; see the
+// Gram-Schmidt in groups of g columns (g = 4 in FP64, 16 in FP32; see the
 // grouped passes below) while the block's rows of w fit in shared memory:
 //   1. w = A v_j; the block keeps its rows of w in shared memory and forms the
 //      partials of (v_c, w) for the first group
@@ -249,17 +249,18 @@ __device__ __forceinline__ T block_sub(const BlockRows& br, T* V, int64_t ldv, i
 // the next (or, after the last group, ||w||^2 and the new column's inner
 // products with the columns of its own group, the entries of L its group will
 // need).  G = 4 in FP64 (a pass holds 2G values a row in registers, and FP64
-// halves what fits) and 8 in FP32, where the rounds' synchronisation, not the
-// passes, is the larger cost.
+// halves what fits) and 16 in FP32, where the rounds' synchronisation, not the
+// passes, is the larger cost: against groups of 8, 45.6 against 46.7 us a step
+// on convection-diffusion 96^3 with DIA, 49.2 against 49.8 with ELL, although
+// the FP32 passes spill about twice as much.
 constexpr int kMgsThreads = 512;  // threads of a block that run the passes: half the
                                   // FP64 partials to reduce of 1024, and still
                                   // enough loads in flight (512 measured fastest of
                                   // 256 / 512 / 1024 on 884,736 rows)
-constexpr int kMgsGroupMax = 8;   // the Gram entries' stride in the solver state
 
 template <typename T>
 struct MgsGroup {
-  static constexpr int value = sizeof(T) == 4 ? 8 : 4;
+  static constexpr int value = sizeof(T) == 4 ? 16 : 4;
 };
 
 // Calls f(IntC<r>) for the runtime r in [R, MAX] (group sizes: exact register
@@ -382,8 +383,8 @@ struct GmSmem {
         coef(h2 + M + 2),
         wp(coef + M + 2),  // coef: M + 2 values of T (at most a double each)
         red(wp + 32 * (int64_t)(M + 2 > 4 ? M + 2 : 4)),  // wp: at least 128
-        G(red + kPersistBlock + 4),  // G: (M + 1) x 8 group inner products
-        w(G + 8 * (int64_t)(M + 1)),
+        G(red + kPersistBlock + 4),  // G: (M + 1) x kMgsGroupMax group inner products
+        w(G + kMgsGroupMax * (int64_t)(M + 1)),
         total(w + wdoubles) {}
 };
 

@@ -11,17 +11,21 @@ constexpr int kMaxRestart = 64;  // largest GMRES restart length
 // GMRES(m) state of one solve (Sec. I; Saad, Alg. 6.9): the rotated Hessenberg
 // matrix, the Givens rotations and the rotated right-hand side g of the current
 // cycle, written by the per-step kernels and by the persistent kernel's block 0.
+// Stride of the Gram entries G below: the largest group of the persistent
+// kernel's modified Gram-Schmidt.
+constexpr int kMgsGroupMax = 16;
+
 struct GmState {
   double h1[kMaxRestart + 1], h2[kMaxRestart + 1];
   double H[(kMaxRestart + 1) * kMaxRestart];  // rotated Hessenberg, H[i * kMaxRestart + j]
   double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
   // inner products (v_q, v_c) of column q with the columns c before it in its
-  // aligned group of g columns (g = 4 in FP64, 8 in FP32), G[q * 8 + (c - g
+  // aligned group of g columns (g = 4 in FP64, 16 in FP32), G[q * kMgsGroupMax + (c - g
   // floor(q / g))]: the persistent kernel's modified Gram-Schmidt applies a
   // group's projections in one pass with them.  Zero for columns made by the
   // per-step kernels (orthogonal to working precision by the second
   // Gram-Schmidt pass).
-  double G[(kMaxRestart + 1) * 8];
+  double G[(kMaxRestart + 1) * kMgsGroupMax];
   double bb, beta, inv;  // ||b||^2, cycle start ||r||, 1 / current norm
   int done;              // converged (true residual of a cycle start)
   int halt;              // no further steps in this cycle

@@ -484,7 +484,7 @@ __global__ void k_gm_start(const double* __restrict__ part, int P, GmState* st, 
   st->jdone = 0;
   st->conv_est = 0;
   for (int i = 0; i <= kMaxRestart; ++i) st->g[i] = 0.0;
-  for (int i = 0; i < (kMaxRestart + 1) * 8; ++i) st->G[i] = 0.0;
+  for (int i = 0; i < (kMaxRestart + 1) * kMgsGroupMax; ++i) st->G[i] = 0.0;
   st->g[0] = beta;
   st->inv = beta > 0.0 ? 1.0 / beta : 0.0;
   const bool conv = st->bb == 0.0 || rr <= tol2 * st->bb;
