@@ -283,6 +283,34 @@ def test_persistent_cg_matches_per_step_launches(ctx, cfg, precision):
     assert abs(out[0][1].iters - out[1][1].iters) <= 2
 
 
+@pytest.mark.parametrize("cfg", [C.config("CSR"), C.config("CSR", C.ALGO_VECTOR, tpv=4),
+                                 C.config("ELL"), C.config("SELL", sigma=32), C.config("DIA")],
+                         ids=repr)
+def test_two_barrier_fp32_cg_on_an_odd_order_grid(ctx, cfg):
+    """The FP32 inner solves' persistent CG (two grid barriers an iteration, A p
+    carried by its recurrence) on a 3D Poisson grid of odd order (n = 9261, so the
+    vector loops have an odd last element), in launches of 7 iterations that
+    alternate with per-step launches: every launch starts from q = A p, returns
+    with p = r + beta p at its iteration limit, and the per-step path carries on
+    from that state.  Against the one-launch-per-step solve and the oracle."""
+    A = W.poisson3d(21)
+    b = rhs(A, 15)
+    ref = oracle.cg(A, b, tol=1e-10)
+    runs = {}
+    for mode, chunk in ((0, 0), (1, 0), (2, 7)):
+        x, info = gpu_solve(ctx, A, b, tol=1e-10, force=cfg, precision=C.PREC_FP32_IR,
+                            inner_tol=1e-5, iteration_kernel=mode, persist_chunk=chunk)
+        assert info.status == 0 and true_relres(A, x, b) <= 1e-10, (repr(cfg), mode)
+        assert np.linalg.norm(x - ref.x) <= 1e-7 * np.linalg.norm(ref.x)
+        runs[mode] = info
+    assert runs[0].persist_iters > 0 and runs[1].persist_iters == 0
+    assert runs[2].persist_iters > 0 and runs[2].persist_launches >= 2
+    # the same iteration up to rounding: inner iteration counts within two a
+    # refinement step of the per-step path's
+    assert abs(runs[0].outer_iters - runs[1].outer_iters) <= 1
+    assert abs(runs[0].iters - runs[1].iters) <= 2 * max(runs[0].outer_iters, 1)
+
+
 @pytest.mark.parametrize("make,fmt,hyb_k", [(lambda: W.spd_powerlaw(8000, seed=2), "HYB", 0),
                                              (lambda: W.spd_powerlaw(8000, seed=2), "HYB", 2),
                                              (lambda: W.spd_powerlaw(8000, seed=2), "COO", 0),
