@@ -578,8 +578,8 @@ __global__ void k_cast_f32(int64_t n, const double* __restrict__ a, float* __res
 }
 
 // DIA conversion: mark the offsets present, compact them in ascending order
-// (word popcounts -> exclusive scan -> each word writes its bits), then scatter
-// every entry to its diagonal through an offset -> diagonal lookup table.
+// (word popcounts -> exclusive scan -> each word writes its bits), then fill
+// every slot of every row once.
 __global__ void __launch_bounds__(kBlock) k_dia_mark(int64_t n, const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ ci,
                                                      unsigned* __restrict__ bm) {
@@ -599,7 +599,7 @@ __global__ void k_dia_wordcount(int64_t words, const unsigned* __restrict__ bm,
 
 __global__ void k_dia_compact(int64_t n, int64_t words, const unsigned* __restrict__ bm,
                               const int64_t* __restrict__ pos, int32_t* __restrict__ offs,
-                              int32_t* __restrict__ lut, int64_t cap) {
+                              int64_t cap) {
   for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < words;
        w += (int64_t)gridDim.x * blockDim.x) {
     unsigned bits = bm[w];
@@ -608,26 +608,42 @@ __global__ void k_dia_compact(int64_t n, int64_t words, const unsigned* __restri
       const int b = __ffs(bits) - 1;
       bits &= bits - 1;
       const int64_t o = w * 32 + b;  // offset + (n - 1)
-      if (q < cap) {
-        offs[q] = (int32_t)(o - (n - 1));
-        lut[o] = (int32_t)q;
-      }
+      if (q < cap) offs[q] = (int32_t)(o - (n - 1));
       ++q;
     }
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_dia_fill(int64_t n, const int32_t* __restrict__ rp,
+// A thread per row walks the row's entries (ascending columns) and the
+// diagonals (ascending offsets, in shared memory) together and writes every
+// slot of the row once: the entry on that diagonal, or zero.  Every entry lies
+// on a diagonal that was marked, so the walk takes each entry in turn; no slot
+// is written twice (no zero fill of the whole array first) and no offset ->
+// diagonal table is read per entry.
+__global__ void __launch_bounds__(kBlock) k_dia_fill(int64_t n, int ndiag,
+                                                     const int32_t* __restrict__ offs,
+                                                     const int32_t* __restrict__ rp,
                                                      const int32_t* __restrict__ ci,
                                                      const double* __restrict__ v,
-                                                     const int32_t* __restrict__ lut,
                                                      double* __restrict__ data) {
+  __shared__ int32_t so[kDiaMax];
+  for (int d = threadIdx.x; d < ndiag; d += blockDim.x) so[d] = offs[d];
+  __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-      const int64_t d = lut[(int64_t)ci[k] - i + (n - 1)];
-      data[d * n + i] = v[k];
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t k = rp[i];
+    const int64_t e = rp[i + 1];
+    int64_t c = k < e ? (int64_t)ci[k] : INT64_MAX;  // the next entry's column
+    for (int d = 0; d < ndiag; ++d) {
+      double val = 0.0;
+      if (c == i + so[d]) {
+        val = v[k];
+        ++k;
+        c = k < e ? (int64_t)ci[k] : INT64_MAX;
+      }
+      data[(int64_t)d * n + i] = val;
     }
+  }
 }
 
 // ------------------------------------------------------------------ host side
@@ -920,11 +936,9 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
   unsigned* const have = m->diag_bm.load();
   unsigned* bm = have;
   int64_t *cnt = nullptr, *pos = nullptr;
-  int32_t* lut = nullptr;
   try {
     cnt = dalloc_async<int64_t>(words, s);
     pos = dalloc_async<int64_t>(words + 1, s);
-    lut = dalloc_async<int32_t>(span, s);
     d.offs = dalloc_async<int32_t>(kDiaMax, s);
     if (!have) {
       bm = dalloc_async<unsigned>(words, s);
@@ -934,29 +948,26 @@ static void convert_dia(cp_ctx* ctx, cp_mat* m, cudaStream_t s) {
     CP_LAUNCH(ctx, k_dia_wordcount, grid_cap(ctx, words), kBlock, 0, s, words, bm, cnt);
     exclusive_scan_i64(ctx, cnt, pos, words, s);
     CP_LAUNCH(ctx, k_dia_compact, grid_cap(ctx, words), kBlock, 0, s, n, words, bm, pos, d.offs,
-              lut, (int64_t)kDiaMax);
+              (int64_t)kDiaMax);
     d2h_small(ctx, &d.ndiag, pos + words, sizeof(int64_t), s);
     CP_REQUIRE(d.ndiag <= kDiaMax, CP_ERR_FOOTPRINT,
                "DIA needs %lld diagonals, more than the %d it accepts", (long long)d.ndiag,
                kDiaMax);
     check_budget(ctx, d.ndiag * n * 8, "DIA");
     d.val = dalloc_async<double>(d.ndiag * n, s);
-    CP_CUDA(cudaMemsetAsync(d.val, 0, d.ndiag * n * sizeof(double), s));
-    CP_LAUNCH(ctx, k_dia_fill, grid_cap(ctx, n), kBlock, 0, s, n, m->rowptr, m->col, m->val, lut,
-              d.val);
+    CP_LAUNCH(ctx, k_dia_fill, grid_cap(ctx, n), kBlock, 0, s, n, (int)d.ndiag, d.offs,
+              m->rowptr, m->col, m->val, d.val);
     CP_CUDA(cudaStreamSynchronize(s));
   } catch (...) {
     if (!have) dfree_async(bm, s);
     dfree_async(cnt, s);
     dfree_async(pos, s);
-    dfree_async(lut, s);
     free_dia(d);
     throw;
   }
   if (!have) dfree_async(bm, s);
   dfree_async(cnt, s);
   dfree_async(pos, s);
-  dfree_async(lut, s);
   m->dia = d;
   m->has_dia = true;
 }
